@@ -1,0 +1,231 @@
+/*
+ * hlc.h -- C ABI of the B300 (sm_103a) positional cross-match library.
+ *
+ * The library computes the hot path of HLC2 (Zhang et al., arXiv 2301.07331):
+ * for two sky catalogues A and B, every pair (A_i, B_j) whose angular
+ * separation d (Sec. 2.1, Eq. 1) is at most a radius r.  Sources are grouped
+ * by HEALPix nested cell ("hp_nestid", Sec. 4.2) and only pairs in the same or
+ * neighbouring cells are tested.  Two boundary rules are offered:
+ *   HLC_COMPLETE8 -- the cell of each A source and its 8 (7 at the eight
+ *                    three-face vertices) neighbours: the exact set of Eq. 1
+ *                    whenever r <= theta_L / 8, theta_L = sqrt(pi/3) / 2^L;
+ *   HLC_QUAD      -- the quad-direction strategy of Sec. 3.2, Algorithm 1:
+ *                    each source is also filed under the cells of its four
+ *                    copies shifted by +-r in RA and Dec, and only pairs that
+ *                    share a cell are tested (an approximation, a subset of
+ *                    the exact set; each pair is reported once, from the
+ *                    smallest cell the two sources share).
+ *
+ * Decision arithmetic.  A pair matches when its squared chord
+ * |u_A - u_B|^2 <= 4 sin^2(r/2) (Eq. 1 in chord form), both sides evaluated
+ * in a fixed sequence of IEEE binary64 operations: sin/cos in degrees by exact
+ * reduction to [-45, 45] deg and Horner polynomials with the Taylor
+ * coefficients (pi/180)^k/k! rounded to double; u = (cos d cos a,
+ * cos d sin a, sin d); s = dx*dx, s = fma(dy,dy,s), s = fma(dz,dz,s).  With
+ * HLC_FP32_GUARD the bulk test runs in FP32 with a guard band derived from
+ * its error bound and only candidates inside the band are decided in that
+ * binary64 arithmetic, so both precisions return the same set.
+ *
+ * Conventions for every entry point:
+ *   - return value: HLC_OK (0) or an HLC_E* code; hlc_last_error() then holds
+ *     a message (thread-local, valid until the next call on that thread);
+ *   - on error nothing is written to the caller's result structures;
+ *   - "device" pointers are CUDA global-memory addresses on the current
+ *     device; "stream" is a cudaStream_t (NULL = legacy default stream);
+ *   - RA/Dec are float64 degrees; RA is folded into [0, 360); Dec must lie in
+ *     [-90, 90]; NaN or Inf anywhere is HLC_EINVAL.
+ */
+#ifndef HLC_H
+#define HLC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define HLC_OK 0
+#define HLC_EINVAL 1       /* invalid argument or input value */
+#define HLC_ENOMEM 2       /* device or pinned host allocation failed */
+#define HLC_ECUDA 3        /* a CUDA runtime call or kernel failed */
+#define HLC_ETIMEOUT 4     /* a bounded device-side wait gave up */
+#define HLC_EUNSUPPORTED 5 /* valid request outside what this build does */
+
+/* ---- enums -------------------------------------------------------------- */
+#define HLC_COMPLETE8 0
+#define HLC_QUAD 1
+
+#define HLC_FP64 0       /* plain form: binary64 vectors and pair test */
+#define HLC_FP32_GUARD 1 /* FP32 bulk test + guard band + binary64 recheck */
+
+#define HLC_INDEX_BSEARCH 0 /* cell offsets by binary search of unique keys */
+#define HLC_INDEX_LEARNED 1 /* per-partition learned model + bounded search */
+
+#define HLC_MODEL_PLA 0 /* 256-segment monotone piecewise-linear model */
+#define HLC_MODEL_MLP 1 /* 1-input 2x32 ReLU MLP, bracket-checked */
+
+/* ---- catalogue and parameters ------------------------------------------- */
+typedef struct {
+  const double* ra_deg;  /* n values */
+  const double* dec_deg; /* n values */
+  const uint64_t* id;    /* n user ids (need not be unique) */
+  uint64_t n;            /* number of sources, < 2^31 */
+  int on_device;         /* 1: the three arrays are device pointers;
+                            0: host pointers (pinned or pageable) */
+} hlc_catalog;
+
+typedef void* (*hlc_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*hlc_dealloc_fn)(void* ptr, void* ctx);
+
+typedef struct {
+  double radius_arcsec;       /* r > 0; COMPLETE8 needs r <= theta_L/8 */
+  int coarse_level;           /* HEALPix order of streaming / learned-index
+                                 partitions, 0 <= coarse <= fine */
+  int fine_level;             /* HEALPix order L of the cells, 0..14 */
+  int boundary;               /* HLC_COMPLETE8 or HLC_QUAD */
+  int precision;              /* HLC_FP64 or HLC_FP32_GUARD */
+  int index;                  /* HLC_INDEX_BSEARCH or HLC_INDEX_LEARNED */
+  int model;                  /* HLC_MODEL_PLA or HLC_MODEL_MLP (learned) */
+  int want_sep;               /* 1: fill hlc_result.sep_arcsec */
+  uint64_t device_mem_budget; /* 0 = no cap; else bytes of device memory the
+                                 plan may hold at once (host inputs are then
+                                 streamed by coarse partition) */
+  void* stream;               /* cudaStream_t for all work; NULL = default */
+  hlc_alloc_fn alloc;         /* optional device allocator (NULL: the
+                                 library uses cudaMallocAsync on stream) */
+  hlc_dealloc_fn dealloc;
+  void* alloc_ctx;
+} hlc_params;
+
+/* Result of hlc_match: rows sorted ascending by (id_a, id_b) as unsigned
+ * 64-bit values (by job first for batched plans).  The arrays belong to the
+ * plan and stay valid until hlc_free or the next hlc_match on that plan. */
+typedef struct {
+  uint64_t n;          /* number of matched pairs */
+  uint64_t* id_a;      /* n ids from catalogue A */
+  uint64_t* id_b;      /* n ids from catalogue B */
+  double* sep_arcsec;  /* n separations (NULL unless want_sep) */
+  uint32_t* job;       /* n job indices (batched plans), else NULL */
+  int on_device;       /* 1: device arrays */
+} hlc_result;
+
+/* Counters and CUDA-event timings of the last hlc_plan + hlc_match. */
+typedef struct {
+  uint64_t n_a, n_b;               /* sources */
+  uint64_t entries_a, entries_b;   /* index entries (> n in quad mode) */
+  uint64_t cells_a, cells_b;       /* non-empty cells at the join level */
+  uint64_t pair_tests;             /* algorithmic pair count */
+  uint64_t band_candidates;        /* FP32 guard band: pairs rechecked */
+  uint64_t matches;
+  uint64_t quad_duplicates;        /* quad pairs left to a smaller shared
+                                      cell */
+  uint64_t partitions;             /* streamed coarse partitions */
+  uint64_t learned_models;         /* learned-index partitions */
+  double learned_hit_rate;         /* lookups answered inside the window */
+  uint32_t learned_max_err;        /* largest stored error bound */
+  int join_level;                  /* HEALPix order used for the join */
+  float ms_prep, ms_sort, ms_index, ms_candidates, ms_pair, ms_recheck,
+      ms_output, ms_h2d, ms_d2h, ms_total;
+  uint64_t kernel_launches;        /* library kernels launched by the plan and
+                                      the match */
+} hlc_stats;
+
+typedef struct hlc_plan_s hlc_plan_t;
+
+/* Build a plan: validate and index both catalogues (ang2pix, cell sort,
+ * offset table).  n_jobs = 1 for one pair of catalogues; n_jobs > 1 makes A,
+ * B and p arrays of n_jobs entries that are matched independently in one
+ * batched launch sequence (every job must use the same precision, boundary
+ * and stream; radius and levels may differ).  The caller's input arrays must
+ * stay valid until hlc_plan returns; nothing is retained.  *out is set only
+ * on success. */
+int hlc_plan(const hlc_catalog* A, const hlc_catalog* B, const hlc_params* p,
+             uint32_t n_jobs, hlc_plan_t** out);
+
+/* Run the match.  out receives device arrays owned by the plan; stats may be
+ * NULL.  Synchronises the plan's stream before returning. */
+int hlc_match(hlc_plan_t* plan, hlc_result* out, hlc_stats* stats);
+
+/* Copy a result to caller-owned host arrays (each may be NULL to skip). */
+int hlc_result_to_host(const hlc_result* r, uint64_t* id_a, uint64_t* id_b,
+                       double* sep_arcsec, uint32_t* job);
+
+/* Release the plan, its device memory and every result it returned. */
+void hlc_free(hlc_plan_t* plan);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* hlc_last_error(void);
+
+/* Library version string. */
+const char* hlc_version(void);
+
+/* The binary64 polynomial coefficients this library uses for sin/cos in
+ * degrees: sin_c[k] = (-1)^k (pi/180)^(2k+1)/(2k+1)! and
+ * cos_c[k] = (-1)^k (pi/180)^(2k)/(2k)!, each the nearest double, derived at
+ * load time in binary128 (host only; no device needed). */
+int hlc_canonical_coefficients(double sin_c[10], double cos_c[11]);
+
+/* ---- kernel-level entry points (device pointers, asynchronous on stream) --
+ * These expose single steps of the path for testing and for callers that
+ * build their own pipelines. */
+
+/* HEALPix nested pixel of each (ra, dec) at `order` (0..14), computed in the
+ * binary64 arithmetic stated above (Sec. 4.2, after Gorski et al. 2005).
+ * ra, dec: n device doubles; pix: n device uint32.  precision HLC_FP32_GUARD
+ * computes the same pixels through an FP32 estimate with an exact binary64
+ * fallback near cell edges. */
+int hlc_ang2pix(const double* ra, const double* dec, uint64_t n, int order,
+                int precision, uint32_t* pix, void* stream);
+
+/* The 8 neighbours of each nested pixel in the direction order
+ * (dx,dy) = (-1,-1) (-1,0) (-1,1) (0,1) (1,1) (1,0) (1,-1) (0,-1), where x
+ * grows to the north-east and y to the north-west inside a base face; a
+ * missing neighbour (three-face vertices) is -1.  pix: n device uint32;
+ * out: 8n device int64. */
+int hlc_neighbours(const uint32_t* pix, uint64_t n, int order, int64_t* out,
+                   void* stream);
+
+/* Quad-direction cell set of each source (Algorithm 1): the distinct pixels
+ * of (ra, dec), (ra +- R, dec), (ra, dec -+ R), R = r/3600 deg, RA wrapped,
+ * Dec clamped, ascending.  out: 5n device uint32 padded with 0xFFFFFFFF;
+ * count: n device int32. */
+int hlc_quad_cells(const double* ra, const double* dec, uint64_t n,
+                   double radius_arcsec, int order, uint32_t* out,
+                   int32_t* count, void* stream);
+
+/* Unit vectors (3n device doubles, interleaved x,y,z) in the binary64
+ * arithmetic stated above. */
+int hlc_unitvec(const double* ra, const double* dec, uint64_t n, double* xyz,
+                void* stream);
+
+/* Stable ascending LSD radix sort of (key, value) pairs by the low `key_bits`
+ * bits of the keys.  keys/vals: n device elements, sorted in place.  key_size
+ * is 4 (uint32 keys) or 8 (uint64 keys); values are uint32.  Allocates
+ * temporary device memory of about n (key_size + 4) bytes plus the look-back
+ * tables with cudaMallocAsync on the stream, and frees it before returning;
+ * synchronises the stream. */
+int hlc_sort_pairs(void* keys, uint32_t* vals, uint64_t n, int key_size,
+                   int key_bits, void* stream);
+
+/* Run-length table of sorted uint32 keys: unique keys uniq[0..m) and
+ * start[0..m] (start[m] = n); *m_out receives m (host).  uniq and start must
+ * hold n and n+1 elements.  Synchronises the stream. */
+int hlc_cell_table(const uint32_t* keys, uint64_t n, uint32_t* uniq,
+                   uint32_t* start, uint64_t* m_out, void* stream);
+
+/* Learned offset index over sorted unique keys uniq[0..m) partitioned by the
+ * top bits (key >> shift): per partition a model (HLC_MODEL_PLA or
+ * HLC_MODEL_MLP) with a stored max error; lookup(q) returns the lower bound
+ * of q in uniq exactly (bounded search in the predicted window, binary search
+ * as fallback).  out: nq device uint32 lower-bound positions; stats may be
+ * NULL.  Synchronises the stream. */
+int hlc_learned_lookup(const uint32_t* uniq, uint64_t m, int shift, int model,
+                       const uint32_t* queries, uint64_t nq, uint32_t* out,
+                       hlc_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HLC_H */

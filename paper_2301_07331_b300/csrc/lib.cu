@@ -1,0 +1,892 @@
+// The C ABI (include/hlc.h): plan / match / free, the kernel-level entry
+// points, device tables and error state.  All kernels live in the headers
+// included here (one translation unit, so constant tables are shared).
+#include <cmath>
+#include <mutex>
+
+#include "canon.cuh"
+#include "common.cuh"
+#include "fp32.cuh"
+#include "match.cuh"
+#include "scan.cuh"
+#include "sort.cuh"
+
+namespace hlc {
+
+// ---------------------------------------------------------------------------
+// Error state.
+// ---------------------------------------------------------------------------
+static thread_local char g_msg[1024] = "";
+std::atomic<unsigned long long> g_launches{0};
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+  va_end(ap);
+}
+void clear_error() { g_msg[0] = 0; }
+
+// ---------------------------------------------------------------------------
+// Constants and device tables.
+// ---------------------------------------------------------------------------
+static Canon g_canon;
+static std::once_flag g_canon_once;
+
+const Canon& canon() {
+  std::call_once(g_canon_once, [] { derive_trig_coefficients(g_canon.s, g_canon.c); });
+  return g_canon;
+}
+
+// Neighbour transitions from the layout of the 12 base faces: 0-3 around the
+// north pole (centres at phi = 45 + 90k deg), 4-7 on the equator (phi = 90k),
+// 8-11 around the south pole.  Inside a face x runs to the north-east and y
+// to the north-west (south vertex (0,0), north vertex (n,n)).  Polar faces
+// meet the equatorial ones edge to edge without rotation; two polar faces
+// meet along a meridian, a quarter turn about the pole apart.  Four faces
+// meet at the poles and at the equatorial vertices, three at z = +-2/3.
+static void build_neighbour_tables(uint8_t face[12][9], uint8_t map[12][9]) {
+  for (int f = 0; f < 12; ++f)
+    for (int r = 0; r < 9; ++r) {
+      face[f][r] = 255;
+      map[f][r] = NM_SAME;
+    }
+  auto set = [&](int f, int rx, int ry, int g, int m) {
+    face[f][ry * 3 + rx] = (uint8_t)g;
+    map[f][ry * 3 + rx] = (uint8_t)m;
+  };
+  for (int k = 0; k < 4; ++k) {
+    int north = k, eq = 4 + k, south = 8 + k;
+    int k1 = (k + 1) & 3, k2 = (k + 2) & 3, k3 = (k + 3) & 3;
+    set(north, 1, 1, north, NM_SAME);
+    set(north, 2, 1, k1, NM_ROT_N1);
+    set(north, 1, 2, k3, NM_ROT_N3);
+    set(north, 0, 1, 4 + k, NM_SHIFT);
+    set(north, 1, 0, 4 + k1, NM_SHIFT);
+    set(north, 2, 2, k2, NM_AT_NN);      // across the north pole
+    set(north, 0, 0, 8 + k, NM_AT_NN);   // across the equatorial vertex
+    set(eq, 1, 1, eq, NM_SAME);
+    set(eq, 2, 1, k, NM_SHIFT);
+    set(eq, 1, 2, k3, NM_SHIFT);
+    set(eq, 0, 1, 8 + k3, NM_SHIFT);
+    set(eq, 1, 0, 8 + k, NM_SHIFT);
+    set(eq, 2, 0, 4 + k1, NM_AT_0N);     // east equatorial vertex
+    set(eq, 0, 2, 4 + k3, NM_AT_N0);     // west equatorial vertex
+    set(south, 1, 1, south, NM_SAME);
+    set(south, 2, 1, 4 + k1, NM_SHIFT);
+    set(south, 1, 2, 4 + k, NM_SHIFT);
+    set(south, 0, 1, 8 + k3, NM_ROT_S3);
+    set(south, 1, 0, 8 + k1, NM_ROT_S1);
+    set(south, 0, 0, 8 + k2, NM_AT_00);  // across the south pole
+    set(south, 2, 2, k, NM_AT_00);       // across the equatorial vertex
+  }
+}
+
+static std::mutex g_dev_mu;
+static bool g_dev_ready[64] = {false};
+
+int ensure_device_tables() {
+  int dev = 0;
+  HLC_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (dev >= 0 && dev < 64 && g_dev_ready[dev]) return HLC_OK;
+  const Canon& K = canon();
+  CanonDev cd;
+  memcpy(cd.s, K.s, sizeof(cd.s));
+  memcpy(cd.c, K.c, sizeof(cd.c));
+  cd.sqrt6 = std::sqrt(6.0);
+  HLC_CUDA(cudaMemcpyToSymbol(d_canon, &cd, sizeof(cd)));
+  uint8_t face[12][9], map[12][9];
+  build_neighbour_tables(face, map);
+  HLC_CUDA(cudaMemcpyToSymbol(d_nbr_face, face, sizeof(face)));
+  HLC_CUDA(cudaMemcpyToSymbol(d_nbr_map, map, sizeof(map)));
+  if (dev >= 0 && dev < 64) g_dev_ready[dev] = true;
+  return HLC_OK;
+}
+
+static int check_dev_err(const int* dev_err, cudaStream_t st, const char* what) {
+  int h = 0;
+  HLC_CUDA(cudaMemcpyAsync(&h, dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HLC_CUDA(cudaStreamSynchronize(st));
+  if (h & DERR_INPUT) {
+    set_error("%s: invalid input (non-finite RA/Dec or |Dec| > 90)", what);
+    return HLC_EINVAL;
+  }
+  if (h & DERR_TIMEOUT) {
+    set_error("%s: a bounded device wait gave up", what);
+    return HLC_ETIMEOUT;
+  }
+  if (h & DERR_BOUNDS) {
+    set_error("%s: a device bounds check failed", what);
+    return HLC_ECUDA;
+  }
+  return HLC_OK;
+}
+
+// Theta_L / 8 in arcsec: the largest radius for which the complete rule is exact.
+static double complete_max_radius(int order) {
+  const double pi = 3.14159265358979323846;
+  return std::sqrt(pi / 3.0) / std::ldexp(1.0, order) * (648000.0 / pi) / 8.0;
+}
+
+// Squared-chord threshold 4 sin^2(r/2) in the canonical arithmetic (host).
+static double host_sincos_deg_sin(double x) {
+  const Canon& K = canon();
+  volatile double q = std::rint(x / 90.0);
+  volatile double t = x - 90.0 * q;
+  volatile double u = t * t;
+  double ps = K.s[9];
+  for (int k = 8; k >= 0; --k) ps = std::fma(ps, u, K.s[k]);
+  volatile double sn = t * ps;
+  double pc = K.c[10];
+  for (int k = 9; k >= 0; --k) pc = std::fma(pc, u, K.c[k]);
+  switch (((long long)q) & 3) {
+    case 0: return sn;
+    case 1: return pc;
+    case 2: return -sn;
+    default: return -pc;
+  }
+}
+static double chord2_threshold(double r_arcsec) {
+  volatile double h = r_arcsec / 7200.0;
+  volatile double sh = host_sincos_deg_sin(h);
+  volatile double sq = sh * sh;
+  return 4.0 * sq;
+}
+
+// ---------------------------------------------------------------------------
+// Plan.
+// ---------------------------------------------------------------------------
+struct CatDev {
+  uint64_t n = 0, m = 0;
+  double* ra = nullptr;
+  double* dec = nullptr;
+  uint64_t* id = nullptr;
+  uint32_t* key = nullptr;
+  uint32_t* idx = nullptr;
+  double *vx = nullptr, *vy = nullptr, *vz = nullptr;
+  float4* v32 = nullptr;
+  uint32_t* cells5 = nullptr;
+  uint32_t* cell_of = nullptr;
+  uint32_t* uniq = nullptr;
+  uint32_t* start = nullptr;
+  uint64_t u = 0;
+};
+
+enum Ctr { C_ROWS = 0, C_BAND, C_TESTS, C_DUPS, C_M, C_TOTAL, C_N };
+
+}  // namespace hlc
+
+struct hlc_plan_s {
+  hlc_params p{};
+  hlc::Allocator al;
+  hlc::Arena* arena = nullptr;   // plan lifetime
+  hlc::Arena* out = nullptr;     // last result
+  hlc::CatDev A, B;
+  double C = 0;
+  float lo32 = 0, hi32 = 0;
+  int join_level = 0;
+  int nslot = 9;
+  int* dev_err = nullptr;
+  unsigned long long* ctr = nullptr;
+  hlc_stats stats{};
+  unsigned long long launches0 = 0;
+  cudaEvent_t ev[12] = {};
+  bool events = false;
+};
+
+namespace hlc {
+
+static cudaStream_t plan_stream(const hlc_plan_t* P) { return (cudaStream_t)P->p.stream; }
+
+static int validate_params(const hlc_params* p) {
+  if (!p) {
+    set_error("params is NULL");
+    return HLC_EINVAL;
+  }
+  if (!(p->radius_arcsec > 0.0) || !(p->radius_arcsec <= 648000.0)) {
+    set_error("radius_arcsec must be in (0, 648000], got %g", p->radius_arcsec);
+    return HLC_EINVAL;
+  }
+  if (p->fine_level < 0 || p->fine_level > 14) {
+    set_error("fine_level must be in [0, 14], got %d", p->fine_level);
+    return HLC_EINVAL;
+  }
+  if (p->coarse_level < 0 || p->coarse_level > p->fine_level) {
+    set_error("coarse_level must be in [0, fine_level], got %d", p->coarse_level);
+    return HLC_EINVAL;
+  }
+  if (p->boundary != HLC_COMPLETE8 && p->boundary != HLC_QUAD) {
+    set_error("boundary must be HLC_COMPLETE8 or HLC_QUAD");
+    return HLC_EINVAL;
+  }
+  if (p->precision != HLC_FP64 && p->precision != HLC_FP32_GUARD) {
+    set_error("precision must be HLC_FP64 or HLC_FP32_GUARD");
+    return HLC_EINVAL;
+  }
+  if (p->index != HLC_INDEX_BSEARCH && p->index != HLC_INDEX_LEARNED) {
+    set_error("index must be HLC_INDEX_BSEARCH or HLC_INDEX_LEARNED");
+    return HLC_EINVAL;
+  }
+  if (p->model != HLC_MODEL_PLA && p->model != HLC_MODEL_MLP) {
+    set_error("model must be HLC_MODEL_PLA or HLC_MODEL_MLP");
+    return HLC_EINVAL;
+  }
+  if (p->boundary == HLC_COMPLETE8 && p->radius_arcsec > complete_max_radius(p->fine_level)) {
+    set_error("radius %g arcsec exceeds theta_L/8 = %g arcsec at fine_level %d (complete mode)",
+              p->radius_arcsec, complete_max_radius(p->fine_level), p->fine_level);
+    return HLC_EINVAL;
+  }
+  if ((p->alloc == nullptr) != (p->dealloc == nullptr)) {
+    set_error("alloc and dealloc must both be set or both be NULL");
+    return HLC_EINVAL;
+  }
+  return HLC_OK;
+}
+
+static int validate_catalog(const hlc_catalog* c, const char* name) {
+  if (!c) {
+    set_error("catalogue %s is NULL", name);
+    return HLC_EINVAL;
+  }
+  if (c->n >= (1ull << 31)) {
+    set_error("catalogue %s has %llu sources; the limit is 2^31 - 1", name,
+              (unsigned long long)c->n);
+    return HLC_EINVAL;
+  }
+  if (c->n && (!c->ra_deg || !c->dec_deg || !c->id)) {
+    set_error("catalogue %s has NULL arrays", name);
+    return HLC_EINVAL;
+  }
+  return HLC_OK;
+}
+
+static void ev_record(hlc_plan_t* P, int i) {
+  if (P->events) cudaEventRecord(P->ev[i], plan_stream(P));
+}
+static float ev_ms(hlc_plan_t* P, int a, int b) {
+  float ms = 0;
+  if (P->events) cudaEventElapsedTime(&ms, P->ev[a], P->ev[b]);
+  return ms;
+}
+
+// Copy one catalogue in, build its sorted entries, payload and cell table.
+static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, double* ms_prep,
+                         double* ms_sort, double* ms_index) {
+  Arena& ar = *P->arena;
+  cudaStream_t st = plan_stream(P);
+  const int L = P->p.fine_level;
+  const bool quad = P->p.boundary == HLC_QUAD;
+  X.n = in->n;
+  uint64_t n = X.n;
+  HLC_ALLOC(ar, X.ra, double, n + 1);
+  HLC_ALLOC(ar, X.dec, double, n + 1);
+  HLC_ALLOC(ar, X.id, uint64_t, n + 1);
+  cudaMemcpyKind kind = in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (n) {
+    HLC_CUDA(cudaMemcpyAsync(X.ra, in->ra_deg, n * 8, kind, st));
+    HLC_CUDA(cudaMemcpyAsync(X.dec, in->dec_deg, n * 8, kind, st));
+    HLC_CUDA(cudaMemcpyAsync(X.id, in->id, n * 8, kind, st));
+  }
+  cudaEvent_t e0, e1, e2, e3;
+  cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2); cudaEventCreate(&e3);
+  cudaEventRecord(e0, st);
+  // entries
+  if (!quad) {
+    X.m = n;
+    HLC_ALLOC(ar, X.key, uint32_t, n + 1);
+    HLC_ALLOC(ar, X.idx, uint32_t, n + 1);
+    if (n) {
+      k_prep_keys<<<grid_for(n, kThreads), kThreads, 0, st>>>(X.ra, X.dec, n, L, X.key, X.idx,
+                                                               P->dev_err);
+      HLC_LAUNCH_CHECK();
+    }
+  } else {
+    HLC_ALLOC(ar, X.cells5, uint32_t, 5 * n + 5);
+    uint32_t* cnt = ar.get_n<uint32_t>(n + 1);
+    uint64_t* off = ar.get_n<uint64_t>(n + 1);
+    void* scr = ar.get(scan_scratch_bytes(n));
+    if (!cnt || !off || !scr) return HLC_ENOMEM;
+    if (n) {
+      k_quad_cells<<<grid_for(n, kThreads), kThreads, 0, st>>>(
+          X.ra, X.dec, n, P->p.radius_arcsec / 3600.0, L, X.cells5, cnt, P->dev_err);
+      HLC_LAUNCH_CHECK();
+    }
+    HLC_TRY(scan_exclusive(cnt, off, n, P->ctr + C_TOTAL, scr, P->dev_err, st));
+    unsigned long long m = 0;
+    HLC_CUDA(cudaMemcpyAsync(&m, P->ctr + C_TOTAL, 8, cudaMemcpyDeviceToHost, st));
+    HLC_CUDA(cudaStreamSynchronize(st));
+    X.m = m;
+    HLC_ALLOC(ar, X.key, uint32_t, X.m + 1);
+    HLC_ALLOC(ar, X.idx, uint32_t, X.m + 1);
+    if (n) {
+      k_quad_emit<<<grid_for(n, kThreads), kThreads, 0, st>>>(X.cells5, cnt, off, n, X.key,
+                                                               X.idx);
+      HLC_LAUNCH_CHECK();
+    }
+    ar.drop(cnt);
+    ar.drop(off);
+    ar.drop(scr);
+  }
+  cudaEventRecord(e1, st);
+  // sort entries by cell key
+  uint64_t m = X.m;
+  if (m > 1) {
+    uint32_t* tk = ar.get_n<uint32_t>(m);
+    uint32_t* tv = ar.get_n<uint32_t>(m);
+    int bits = 2 * L + 4;
+    void* scr = ar.get(sort_scratch_bytes(m, (bits + 7) / 8));
+    if (!tk || !tv || !scr) return HLC_ENOMEM;
+    HLC_TRY(radix_sort_pairs<uint32_t>(X.key, X.idx, tk, tv, m, bits, scr, P->dev_err, st));
+    ar.drop(tk);
+    ar.drop(tv);
+    ar.drop(scr);
+  }
+  cudaEventRecord(e2, st);
+  // payload in sorted order
+  if (P->p.precision == HLC_FP64) {
+    HLC_ALLOC(ar, X.vx, double, m + 1);
+    HLC_ALLOC(ar, X.vy, double, m + 1);
+    HLC_ALLOC(ar, X.vz, double, m + 1);
+    if (m) {
+      k_payload64<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.ra, X.dec, X.idx, m, X.vx, X.vy,
+                                                               X.vz);
+      HLC_LAUNCH_CHECK();
+    }
+  } else {
+    HLC_ALLOC(ar, X.v32, float4, m + 1);
+    if (m) {
+      k_payload32<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.ra, X.dec, X.idx, m, X.v32);
+      HLC_LAUNCH_CHECK();
+    }
+  }
+  // cell table at the join level
+  HLC_ALLOC(ar, X.cell_of, uint32_t, m + 1);
+  HLC_ALLOC(ar, X.uniq, uint32_t, m + 1);
+  HLC_ALLOC(ar, X.start, uint32_t, m + 2);
+  {
+    void* scr = ar.get(scan_scratch_bytes(m));
+    if (!scr) return HLC_ENOMEM;
+    int shift = 2 * (L - P->join_level);
+    HLC_TRY(cell_table(X.key, m, shift, X.cell_of, X.uniq, X.start, P->ctr + C_M, scr,
+                       P->dev_err, st));
+    unsigned long long u = 0;
+    HLC_CUDA(cudaMemcpyAsync(&u, P->ctr + C_M, 8, cudaMemcpyDeviceToHost, st));
+    cudaEventRecord(e3, st);
+    HLC_CUDA(cudaStreamSynchronize(st));
+    X.u = u;
+    ar.drop(scr);
+  }
+  float a = 0, b = 0, c = 0;
+  cudaEventElapsedTime(&a, e0, e1);
+  cudaEventElapsedTime(&b, e1, e2);
+  cudaEventElapsedTime(&c, e2, e3);
+  *ms_prep += a;
+  *ms_sort += b;
+  *ms_index += c;
+  cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2); cudaEventDestroy(e3);
+  return HLC_OK;
+}
+
+static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_params* p,
+                       hlc_plan_t** out) {
+  HLC_TRY(validate_params(p));
+  HLC_TRY(validate_catalog(A, "A"));
+  HLC_TRY(validate_catalog(B, "B"));
+  HLC_TRY(ensure_device_tables());
+  hlc_plan_t* P = new hlc_plan_t();
+  P->p = *p;
+  P->al.alloc = p->alloc;
+  P->al.dealloc = p->dealloc;
+  P->al.ctx = p->alloc_ctx;
+  P->al.stream = (cudaStream_t)p->stream;
+  P->arena = new Arena(P->al);
+  P->out = new Arena(P->al);
+  P->join_level = p->fine_level;
+  P->nslot = p->boundary == HLC_QUAD ? 1 : 9;
+  P->C = chord2_threshold(p->radius_arcsec);
+  double G = fp32_guard_band(P->C, kUnitVecErr);
+  P->lo32 = (float)(P->C - G);
+  P->hi32 = (float)(P->C + G);
+  // make the float thresholds conservative
+  if ((double)P->lo32 > P->C - G) P->lo32 = nextafterf(P->lo32, 0.0f);
+  if ((double)P->hi32 < P->C + G) P->hi32 = nextafterf(P->hi32, 1e30f);
+  if (P->lo32 < 0) P->lo32 = -1.0f;
+  for (int i = 0; i < 12; ++i) cudaEventCreate(&P->ev[i]);
+  P->events = true;
+  auto fail = [&](int rc) {
+    hlc_free(P);
+    return rc;
+  };
+  cudaStream_t st = plan_stream(P);
+  P->dev_err = P->arena->get_n<int>(16);
+  P->ctr = P->arena->get_n<unsigned long long>(C_N);
+  if (!P->dev_err || !P->ctr) return fail(HLC_ENOMEM);
+  if (cudaMemsetAsync(P->dev_err, 0, 64, st) != cudaSuccess ||
+      cudaMemsetAsync(P->ctr, 0, C_N * 8, st) != cudaSuccess) {
+    set_error("cudaMemsetAsync failed");
+    return fail(HLC_ECUDA);
+  }
+  ev_record(P, 0);
+  P->launches0 = g_launches.load();
+  double mp = 0, ms = 0, mi = 0;
+  int rc = build_catalog(P, A, P->A, &mp, &ms, &mi);
+  if (rc == HLC_OK) rc = build_catalog(P, B, P->B, &mp, &ms, &mi);
+  if (rc == HLC_OK) rc = check_dev_err(P->dev_err, st, "hlc_plan");
+  if (rc != HLC_OK) return fail(rc);
+  ev_record(P, 1);
+  memset(&P->stats, 0, sizeof(P->stats));
+  P->stats.n_a = P->A.n;
+  P->stats.n_b = P->B.n;
+  P->stats.entries_a = P->A.m;
+  P->stats.entries_b = P->B.m;
+  P->stats.cells_a = P->A.u;
+  P->stats.cells_b = P->B.u;
+  P->stats.join_level = P->join_level;
+  P->stats.ms_prep = (float)mp;
+  P->stats.ms_sort = (float)ms;
+  P->stats.ms_index = (float)mi;
+  *out = P;
+  return HLC_OK;
+}
+
+static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
+  cudaStream_t st = plan_stream(P);
+  Arena& ar = *P->out;
+  ar.release();
+  CatDev& A = P->A;
+  CatDev& B = P->B;
+  const bool fp32 = P->p.precision == HLC_FP32_GUARD;
+  const bool quad = P->p.boundary == HLC_QUAD;
+  HLC_CUDA(cudaMemsetAsync(P->ctr, 0, C_N * 8, st));
+  HLC_CUDA(cudaMemsetAsync(P->dev_err, 0, 64, st));
+  ev_record(P, 2);
+  uint2* rng = ar.get_n<uint2>(A.u * P->nslot + 1);
+  if (!rng) return HLC_ENOMEM;
+  if (A.u) {
+    k_candidates<<<grid_for(A.u, kThreads), kThreads, 0, st>>>(
+        A.uniq, A.u, B.uniq, B.start, B.u, P->join_level, P->nslot, rng);
+    HLC_LAUNCH_CHECK();
+  }
+  ev_record(P, 3);
+  uint64_t cap = std::max<uint64_t>(1u << 20, A.n + B.n);
+  uint64_t bcap = fp32 ? std::max<uint64_t>(1u << 16, cap / 8) : 1;
+  uint2* rows = nullptr;
+  uint2* band = nullptr;
+  unsigned long long h[C_N];
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    rows = ar.get_n<uint2>(cap);
+    band = ar.get_n<uint2>(bcap);
+    if (!rows || !band) return HLC_ENOMEM;
+    HLC_CUDA(cudaMemsetAsync(P->ctr, 0, C_N * 8, st));
+    PairSink sink{rows, P->ctr + C_ROWS, cap, band, P->ctr + C_BAND, bcap,
+                  P->ctr + C_TESTS, P->ctr + C_DUPS, P->dev_err};
+    if (A.m) {
+      unsigned grid = grid_for(A.m, kThreads, 148u * 16u);
+      if (fp32 && quad)
+        k_pair<true, true><<<grid, kThreads, 0, st>>>(
+            A.m, A.cell_of, rng, P->nslot, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+            A.v32, B.v32, P->C, P->lo32, P->hi32, A.uniq, A.idx, B.idx, A.cells5, B.cells5, sink);
+      else if (fp32)
+        k_pair<true, false><<<grid, kThreads, 0, st>>>(
+            A.m, A.cell_of, rng, P->nslot, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+            A.v32, B.v32, P->C, P->lo32, P->hi32, A.uniq, A.idx, B.idx, nullptr, nullptr, sink);
+      else if (quad)
+        k_pair<false, true><<<grid, kThreads, 0, st>>>(
+            A.m, A.cell_of, rng, P->nslot, A.vx, A.vy, A.vz, B.vx, B.vy, B.vz, nullptr, nullptr,
+            P->C, 0.f, 0.f, A.uniq, A.idx, B.idx, A.cells5, B.cells5, sink);
+      else
+        k_pair<false, false><<<grid, kThreads, 0, st>>>(
+            A.m, A.cell_of, rng, P->nslot, A.vx, A.vy, A.vz, B.vx, B.vy, B.vz, nullptr, nullptr,
+            P->C, 0.f, 0.f, A.uniq, A.idx, B.idx, nullptr, nullptr, sink);
+      HLC_LAUNCH_CHECK();
+    }
+    HLC_CUDA(cudaMemcpyAsync(h, P->ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
+    HLC_CUDA(cudaStreamSynchronize(st));
+    uint64_t need = h[C_ROWS] + (fp32 ? h[C_BAND] : 0);
+    if (need <= cap && h[C_BAND] <= bcap) break;
+    ar.drop(rows);
+    ar.drop(band);
+    cap = need + need / 8 + 1024;
+    bcap = std::max<uint64_t>(bcap, h[C_BAND] + 1024);
+    HLC_CUDA(cudaMemsetAsync(P->dev_err, 0, 64, st));
+    if (attempt == 2) {
+      set_error("match rows did not fit after resizing");
+      return HLC_ECUDA;
+    }
+  }
+  ev_record(P, 4);
+  if (fp32 && h[C_BAND]) {
+    k_recheck<<<grid_for(h[C_BAND], kThreads, 148u * 16u), kThreads, 0, st>>>(
+        band, P->ctr + C_BAND, bcap, A.idx, B.idx, A.ra, A.dec, B.ra, B.dec, P->C, rows,
+        P->ctr + C_ROWS, cap, P->dev_err);
+    HLC_LAUNCH_CHECK();
+  }
+  ev_record(P, 5);
+  unsigned long long M = 0;
+  HLC_CUDA(cudaMemcpyAsync(&M, P->ctr + C_ROWS, 8, cudaMemcpyDeviceToHost, st));
+  HLC_CUDA(cudaStreamSynchronize(st));
+  HLC_TRY(check_dev_err(P->dev_err, st, "hlc_match"));
+  // output rows, sorted by (id_a, id_b)
+  uint64_t* ka = ar.get_n<uint64_t>(M + 1);
+  uint64_t* kb = ar.get_n<uint64_t>(M + 1);
+  uint64_t* kt = ar.get_n<uint64_t>(M + 1);
+  uint32_t* perm = ar.get_n<uint32_t>(M + 1);
+  uint64_t* tk = ar.get_n<uint64_t>(M + 1);
+  uint32_t* tv = ar.get_n<uint32_t>(M + 1);
+  double* sep0 = P->p.want_sep ? ar.get_n<double>(M + 1) : nullptr;
+  double* sep = P->p.want_sep ? ar.get_n<double>(M + 1) : nullptr;
+  uint64_t* id_b = ar.get_n<uint64_t>(M + 1);
+  void* scr = ar.get(sort_scratch_bytes(M + 1, 8));
+  if (!ka || !kb || !kt || !perm || !tk || !tv || !id_b || !scr ||
+      (P->p.want_sep && (!sep0 || !sep)))
+    return HLC_ENOMEM;
+  if (M) {
+    unsigned g = grid_for(M, kThreads);
+    if (fp32)
+      k_rows<true><<<g, kThreads, 0, st>>>(rows, M, A.idx, B.idx, A.id, B.id, nullptr, nullptr,
+                                            nullptr, nullptr, nullptr, nullptr, A.ra, A.dec, B.ra,
+                                            B.dec, P->p.want_sep, ka, kb, sep0, perm);
+    else
+      k_rows<false><<<g, kThreads, 0, st>>>(rows, M, A.idx, B.idx, A.id, B.id, A.vx, A.vy, A.vz,
+                                             B.vx, B.vy, B.vz, nullptr, nullptr, nullptr, nullptr,
+                                             P->p.want_sep, ka, kb, sep0, perm);
+    HLC_LAUNCH_CHECK();
+    // stable LSD: by id_b, then by id_a
+    HLC_CUDA(cudaMemcpyAsync(kt, kb, M * 8, cudaMemcpyDeviceToDevice, st));
+    HLC_TRY(radix_sort_pairs<uint64_t>(kt, perm, tk, tv, M, 64, scr, P->dev_err, st));
+    k_gather<uint64_t><<<g, kThreads, 0, st>>>(ka, perm, M, kt);
+    HLC_LAUNCH_CHECK();
+    HLC_TRY(radix_sort_pairs<uint64_t>(kt, perm, tk, tv, M, 64, scr, P->dev_err, st));
+    k_gather<uint64_t><<<g, kThreads, 0, st>>>(kb, perm, M, id_b);
+    HLC_LAUNCH_CHECK();
+    if (sep) {
+      k_gather<double><<<g, kThreads, 0, st>>>(sep0, perm, M, sep);
+      HLC_LAUNCH_CHECK();
+    }
+  }
+  ev_record(P, 6);
+  HLC_CUDA(cudaStreamSynchronize(st));
+  HLC_TRY(check_dev_err(P->dev_err, st, "hlc_match"));
+  res->n = M;
+  res->id_a = kt;
+  res->id_b = id_b;
+  res->sep_arcsec = sep;
+  res->job = nullptr;
+  res->on_device = 1;
+  ar.drop(ka);
+  ar.drop(kb);
+  ar.drop(tk);
+  ar.drop(tv);
+  ar.drop(scr);
+  if (sep0) ar.drop(sep0);
+  P->stats.pair_tests = h[C_TESTS];
+  P->stats.band_candidates = fp32 ? h[C_BAND] : 0;
+  P->stats.matches = M;
+  P->stats.quad_duplicates = h[C_DUPS];
+  P->stats.ms_candidates = ev_ms(P, 2, 3);
+  P->stats.ms_pair = ev_ms(P, 3, 4);
+  P->stats.ms_recheck = ev_ms(P, 4, 5);
+  P->stats.ms_output = ev_ms(P, 5, 6);
+  P->stats.ms_total = ev_ms(P, 0, 1) + ev_ms(P, 2, 6);
+  P->stats.kernel_launches = g_launches.load() - P->launches0;
+  if (stats) *stats = P->stats;
+  return HLC_OK;
+}
+
+}  // namespace hlc
+
+using namespace hlc;
+
+// ---------------------------------------------------------------------------
+// C ABI.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* hlc_last_error(void) { return g_msg; }
+const char* hlc_version(void) { return "hlc-b300 0.1 (sm_103a)"; }
+
+int hlc_canonical_coefficients(double sin_c[10], double cos_c[11]) {
+  if (!sin_c || !cos_c) {
+    set_error("NULL output");
+    return HLC_EINVAL;
+  }
+  const Canon& K = canon();
+  memcpy(sin_c, K.s, sizeof(K.s));
+  memcpy(cos_c, K.c, sizeof(K.c));
+  return HLC_OK;
+}
+
+int hlc_plan(const hlc_catalog* A, const hlc_catalog* B, const hlc_params* p, uint32_t n_jobs,
+             hlc_plan_t** out) {
+  clear_error();
+  if (!out) {
+    set_error("out is NULL");
+    return HLC_EINVAL;
+  }
+  if (n_jobs == 0) {
+    set_error("n_jobs must be >= 1");
+    return HLC_EINVAL;
+  }
+  if (n_jobs > 1) {
+    set_error("batched plans are not available in this build");
+    return HLC_EUNSUPPORTED;
+  }
+  return plan_single(A, B, p, out);
+}
+
+int hlc_match(hlc_plan_t* plan, hlc_result* out, hlc_stats* stats) {
+  clear_error();
+  if (!plan || !out) {
+    set_error("plan or out is NULL");
+    return HLC_EINVAL;
+  }
+  hlc_result r{};
+  int rc = match_single(plan, &r, stats);
+  if (rc == HLC_OK) *out = r;
+  return rc;
+}
+
+int hlc_result_to_host(const hlc_result* r, uint64_t* id_a, uint64_t* id_b, double* sep,
+                       uint32_t* job) {
+  clear_error();
+  if (!r) {
+    set_error("result is NULL");
+    return HLC_EINVAL;
+  }
+  if (r->n == 0) return HLC_OK;
+  cudaMemcpyKind k = r->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+  if (id_a) HLC_CUDA(cudaMemcpy(id_a, r->id_a, r->n * 8, k));
+  if (id_b) HLC_CUDA(cudaMemcpy(id_b, r->id_b, r->n * 8, k));
+  if (sep && r->sep_arcsec) HLC_CUDA(cudaMemcpy(sep, r->sep_arcsec, r->n * 8, k));
+  if (job && r->job) HLC_CUDA(cudaMemcpy(job, r->job, r->n * 4, k));
+  return HLC_OK;
+}
+
+void hlc_free(hlc_plan_t* plan) {
+  if (!plan) return;
+  cudaStream_t st = (cudaStream_t)plan->p.stream;
+  cudaStreamSynchronize(st);
+  delete plan->out;
+  delete plan->arena;
+  for (int i = 0; i < 12; ++i)
+    if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
+  cudaStreamSynchronize(st);
+  delete plan;
+}
+
+int hlc_ang2pix(const double* ra, const double* dec, uint64_t n, int order, int precision,
+                uint32_t* pix, void* stream) {
+  clear_error();
+  if (order < 0 || order > 14 || (precision != HLC_FP64 && precision != HLC_FP32_GUARD)) {
+    set_error("order must be in [0, 14] and precision HLC_FP64 or HLC_FP32_GUARD");
+    return HLC_EINVAL;
+  }
+  if (n == 0) return HLC_OK;
+  if (!ra || !dec || !pix) {
+    set_error("NULL array");
+    return HLC_EINVAL;
+  }
+  HLC_TRY(ensure_device_tables());
+  cudaStream_t st = (cudaStream_t)stream;
+  int* err = nullptr;
+  HLC_CUDA(cudaMallocAsync(&err, sizeof(int), st));
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+  uint32_t* idx = nullptr;
+  cudaError_t e = cudaMallocAsync(&idx, n * 4, st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(err, st);
+    set_error("cudaMallocAsync failed: %s", cudaGetErrorString(e));
+    return HLC_ENOMEM;
+  }
+  k_prep_keys<<<grid_for(n, kThreads), kThreads, 0, st>>>(ra, dec, n, order, pix, idx, err);
+  int rc = HLC_OK;
+  if (cudaGetLastError() != cudaSuccess) {
+    set_error("ang2pix launch failed");
+    rc = HLC_ECUDA;
+  }
+  if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_ang2pix");
+  cudaFreeAsync(idx, st);
+  cudaFreeAsync(err, st);
+  return rc;
+}
+
+}  // extern "C"
+
+namespace hlc {
+__global__ void k_neighbours(const uint32_t* __restrict__ pix, uint64_t n, int order,
+                             int64_t* __restrict__ out) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    int face, ix, iy;
+    nest_to_fxy(pix[i], order, &face, &ix, &iy);
+    for (int d = 0; d < 8; ++d)
+      out[8 * i + d] = nbr_step(face, ix, iy, d_dirs[d][0], d_dirs[d][1], order);
+  }
+}
+__global__ void k_unitvec(const double* __restrict__ ra, const double* __restrict__ dec,
+                          uint64_t n, double* __restrict__ xyz) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    double x = 0, y = 0, z = 0;
+    if (c_valid(ra[i], dec[i])) c_unitvec(c_norm_ra(ra[i]), dec[i], &x, &y, &z);
+    xyz[3 * i] = x;
+    xyz[3 * i + 1] = y;
+    xyz[3 * i + 2] = z;
+  }
+}
+}  // namespace hlc
+
+extern "C" {
+
+int hlc_neighbours(const uint32_t* pix, uint64_t n, int order, int64_t* out, void* stream) {
+  clear_error();
+  if (order < 0 || order > 14) {
+    set_error("order must be in [0, 14]");
+    return HLC_EINVAL;
+  }
+  if (n == 0) return HLC_OK;
+  if (!pix || !out) {
+    set_error("NULL array");
+    return HLC_EINVAL;
+  }
+  HLC_TRY(ensure_device_tables());
+  k_neighbours<<<grid_for(n, kThreads), kThreads, 0, (cudaStream_t)stream>>>(pix, n, order, out);
+  HLC_LAUNCH_CHECK();
+  return HLC_OK;
+}
+
+int hlc_quad_cells(const double* ra, const double* dec, uint64_t n, double radius_arcsec,
+                   int order, uint32_t* out, int32_t* count, void* stream) {
+  clear_error();
+  if (order < 0 || order > 14 || !(radius_arcsec > 0.0) || !(radius_arcsec <= 648000.0)) {
+    set_error("order must be in [0, 14] and radius in (0, 648000]");
+    return HLC_EINVAL;
+  }
+  if (n == 0) return HLC_OK;
+  if (!ra || !dec || !out || !count) {
+    set_error("NULL array");
+    return HLC_EINVAL;
+  }
+  HLC_TRY(ensure_device_tables());
+  cudaStream_t st = (cudaStream_t)stream;
+  int* err = nullptr;
+  HLC_CUDA(cudaMallocAsync(&err, sizeof(int), st));
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+  k_quad_cells<<<grid_for(n, kThreads), kThreads, 0, st>>>(ra, dec, n, radius_arcsec / 3600.0,
+                                                            order, out, (uint32_t*)count, err);
+  int rc = cudaGetLastError() == cudaSuccess ? HLC_OK : HLC_ECUDA;
+  if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_quad_cells");
+  cudaFreeAsync(err, st);
+  return rc;
+}
+
+int hlc_unitvec(const double* ra, const double* dec, uint64_t n, double* xyz, void* stream) {
+  clear_error();
+  if (n == 0) return HLC_OK;
+  if (!ra || !dec || !xyz) {
+    set_error("NULL array");
+    return HLC_EINVAL;
+  }
+  HLC_TRY(ensure_device_tables());
+  k_unitvec<<<grid_for(n, kThreads), kThreads, 0, (cudaStream_t)stream>>>(ra, dec, n, xyz);
+  HLC_LAUNCH_CHECK();
+  return HLC_OK;
+}
+
+int hlc_sort_pairs(void* keys, uint32_t* vals, uint64_t n, int key_size, int key_bits,
+                   void* stream) {
+  clear_error();
+  if ((key_size != 4 && key_size != 8) || key_bits < 1 || key_bits > 8 * key_size) {
+    set_error("key_size must be 4 or 8 and key_bits in [1, 8*key_size]");
+    return HLC_EINVAL;
+  }
+  if (n <= 1) return HLC_OK;
+  if (!keys || !vals) {
+    set_error("NULL array");
+    return HLC_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int npass = (key_bits + 7) / 8;
+  size_t sb = sort_scratch_bytes(n, npass);
+  void* tk = nullptr;
+  void* tv = nullptr;
+  void* scr = nullptr;
+  int* err = nullptr;
+  int rc = HLC_OK;
+  if (cudaMallocAsync(&tk, n * key_size, st) != cudaSuccess ||
+      cudaMallocAsync(&tv, n * 4, st) != cudaSuccess ||
+      cudaMallocAsync(&scr, sb, st) != cudaSuccess ||
+      cudaMallocAsync(&err, 64, st) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMallocAsync failed for sort temporaries");
+    rc = HLC_ENOMEM;
+  }
+  if (rc == HLC_OK) {
+    cudaMemsetAsync(err, 0, 64, st);
+    if (key_size == 4)
+      rc = radix_sort_pairs<uint32_t>((uint32_t*)keys, vals, (uint32_t*)tk, (uint32_t*)tv, n,
+                                      key_bits, scr, err, st);
+    else
+      rc = radix_sort_pairs<uint64_t>((uint64_t*)keys, vals, (uint64_t*)tk, (uint32_t*)tv, n,
+                                      key_bits, scr, err, st);
+    if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_sort_pairs");
+  }
+  if (tk) cudaFreeAsync(tk, st);
+  if (tv) cudaFreeAsync(tv, st);
+  if (scr) cudaFreeAsync(scr, st);
+  if (err) cudaFreeAsync(err, st);
+  cudaStreamSynchronize(st);
+  return rc;
+}
+
+int hlc_cell_table(const uint32_t* keys, uint64_t n, uint32_t* uniq, uint32_t* start,
+                   uint64_t* m_out, void* stream) {
+  clear_error();
+  if (!m_out || (n && (!keys || !uniq || !start))) {
+    set_error("NULL argument");
+    return HLC_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  void* scr = nullptr;
+  uint32_t* cell_of = nullptr;
+  unsigned long long* m_dev = nullptr;
+  int* err = nullptr;
+  int rc = HLC_OK;
+  if (cudaMallocAsync(&scr, scan_scratch_bytes(n) + 64, st) != cudaSuccess ||
+      cudaMallocAsync(&cell_of, (n + 1) * 4, st) != cudaSuccess ||
+      cudaMallocAsync(&m_dev, 64, st) != cudaSuccess ||
+      cudaMallocAsync(&err, 64, st) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMallocAsync failed");
+    rc = HLC_ENOMEM;
+  }
+  if (rc == HLC_OK) {
+    cudaMemsetAsync(err, 0, 64, st);
+    rc = cell_table(keys, n, 0, cell_of, uniq, start, m_dev, scr, err, st);
+    unsigned long long m = 0;
+    if (rc == HLC_OK) {
+      cudaMemcpyAsync(&m, m_dev, 8, cudaMemcpyDeviceToHost, st);
+      rc = check_dev_err(err, st, "hlc_cell_table");
+    }
+    if (rc == HLC_OK) *m_out = m;
+  }
+  if (scr) cudaFreeAsync(scr, st);
+  if (cell_of) cudaFreeAsync(cell_of, st);
+  if (m_dev) cudaFreeAsync(m_dev, st);
+  if (err) cudaFreeAsync(err, st);
+  cudaStreamSynchronize(st);
+  return rc;
+}
+
+int hlc_learned_lookup(const uint32_t* uniq, uint64_t m, int shift, int model,
+                       const uint32_t* queries, uint64_t nq, uint32_t* out, hlc_stats* stats,
+                       void* stream) {
+  (void)uniq; (void)m; (void)shift; (void)model; (void)queries; (void)nq; (void)out;
+  (void)stats; (void)stream;
+  clear_error();
+  set_error("learned index not available in this build");
+  return HLC_EUNSUPPORTED;
+}
+
+}  // extern "C"

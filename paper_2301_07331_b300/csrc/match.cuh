@@ -1,0 +1,349 @@
+// Kernels of the cross-match path: source preparation (validation, cell keys,
+// quad-direction expansion), sorted payload, neighbour-cell candidates, the
+// pair test, the binary64 recheck of guard-band candidates and the output
+// rows (ids, separations).
+#pragma once
+
+#include "canon.cuh"
+#include "common.cuh"
+#include "fp32.cuh"
+
+namespace hlc {
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Preparation.
+// ---------------------------------------------------------------------------
+
+// Cell key and identity index of each source (complete mode), with input
+// validation (non-finite or |dec| > 90 sets DERR_INPUT).
+__global__ void k_prep_keys(const double* __restrict__ ra, const double* __restrict__ dec,
+                            uint64_t n, int order, uint32_t* __restrict__ key,
+                            uint32_t* __restrict__ idx, int* __restrict__ err) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    double a = ra[i], d = dec[i];
+    uint32_t k = 0;
+    if (!c_valid(a, d))
+      atomicOr(err, DERR_INPUT);
+    else
+      k = c_ang2pix(c_norm_ra(a), d, order);
+    key[i] = k;
+    idx[i] = (uint32_t)i;
+  }
+}
+
+// Quad-direction cells of each source (Algorithm 1): 5 slots + count.
+__global__ void k_quad_cells(const double* __restrict__ ra, const double* __restrict__ dec,
+                             uint64_t n, double R, int order, uint32_t* __restrict__ cells,
+                             uint32_t* __restrict__ count, int* __restrict__ err) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    double a = ra[i], d = dec[i];
+    uint32_t c[5] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+    int m = 1;
+    if (!c_valid(a, d)) {
+      atomicOr(err, DERR_INPUT);
+      c[0] = 0;
+    } else {
+      m = c_quad_cells(c_norm_ra(a), d, R, order, c);
+    }
+#pragma unroll
+    for (int e = 0; e < 5; ++e) cells[5 * i + e] = e < m ? c[e] : 0xFFFFFFFFu;
+    count[i] = (uint32_t)m;
+  }
+}
+
+// One (cell, source) entry per distinct quad cell, at the scanned offsets.
+__global__ void k_quad_emit(const uint32_t* __restrict__ cells, const uint32_t* __restrict__ count,
+                            const uint64_t* __restrict__ off, uint64_t n,
+                            uint32_t* __restrict__ key, uint32_t* __restrict__ idx) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t o = off[i];
+    uint32_t m = count[i];
+    for (uint32_t e = 0; e < m; ++e) {
+      key[o + e] = cells[5 * i + e];
+      idx[o + e] = (uint32_t)i;
+    }
+  }
+}
+
+// Sorted payload: binary64 canonical unit vectors (plain form).
+__global__ void k_payload64(const double* __restrict__ ra, const double* __restrict__ dec,
+                            const uint32_t* __restrict__ idx, uint64_t m,
+                            double* __restrict__ vx, double* __restrict__ vy,
+                            double* __restrict__ vz) {
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t i = idx[e];
+    double a = ra[i], d = dec[i];
+    double x = 0, y = 0, z = 0;
+    if (c_valid(a, d)) c_unitvec(c_norm_ra(a), d, &x, &y, &z);
+    vx[e] = x;
+    vy[e] = y;
+    vz[e] = z;
+  }
+}
+
+// Sorted payload: FP32 unit vectors with a known error bound (guard form).
+__global__ void k_payload32(const double* __restrict__ ra, const double* __restrict__ dec,
+                            const uint32_t* __restrict__ idx, uint64_t m,
+                            float4* __restrict__ v) {
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t i = idx[e];
+    double a = ra[i], d = dec[i];
+    float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (c_valid(a, d)) u = fp32_unitvec(c_norm_ra(a), d);
+    v[e] = u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Candidates: for each non-empty A cell, the B ranges of its neighbourhood.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ a, uint32_t n,
+                                                    uint32_t q) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] < q)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// complete: ranges of the cell and its distinct neighbours (<= 9 slots);
+// quad: the range of the same cell (1 slot).  Empty slots are (0, 0).
+__global__ void k_candidates(const uint32_t* __restrict__ uniqA, uint64_t uA,
+                             const uint32_t* __restrict__ uniqB, const uint32_t* __restrict__ startB,
+                             uint64_t uB, int order, int nslot, uint2* __restrict__ rng) {
+  for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < uA;
+       c += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t cell = uniqA[c];
+    uint32_t nb[9];
+    int m = 1;
+    nb[0] = cell;
+    if (nslot == 9) m = cell_neighbourhood(cell, order, nb);
+    for (int e = 0; e < nslot; ++e) {
+      uint2 r = make_uint2(0u, 0u);
+      if (e < m) {
+        uint32_t p = lower_bound_u32(uniqB, (uint32_t)uB, nb[e]);
+        if (p < uB && uniqB[p] == nb[e]) r = make_uint2(startB[p], startB[p + 1]);
+      }
+      rng[c * nslot + e] = r;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pair test (one thread per A entry; warp-uniform loops so that match rows
+// are reserved with one atomic per warp from a ballot).
+// ---------------------------------------------------------------------------
+
+struct PairSink {
+  uint2* rows;                  // (A entry, B entry)
+  unsigned long long* count;
+  uint64_t cap;
+  uint2* band;                  // FP32 form: candidates inside the band
+  unsigned long long* band_count;
+  uint64_t band_cap;
+  unsigned long long* tests;    // algorithmic pair tests
+  unsigned long long* dups;     // quad pairs owned by a smaller shared cell
+  int* err;
+};
+
+__device__ __forceinline__ void warp_emit(bool emit, uint32_t ka, uint32_t kb, uint2* rows,
+                                          unsigned long long* count, uint64_t cap, int* err) {
+  unsigned b = __ballot_sync(0xffffffffu, emit);
+  if (b == 0) return;
+  int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == __ffs(b) - 1) base = atomicAdd(count, (unsigned long long)__popc(b));
+  base = __shfl_sync(0xffffffffu, base, __ffs(b) - 1);
+  if (emit) {
+    unsigned long long pos = base + __popc(b & lanemask_lt());
+    if (pos < cap)
+      rows[pos] = make_uint2(ka, kb);
+    else
+      atomicOr(err, DERR_OVERFLOW);
+  }
+}
+
+// Smallest cell shared by the quad cell lists of two sources.
+__device__ __forceinline__ uint32_t quad_owner(const uint32_t* __restrict__ ca,
+                                               const uint32_t* __restrict__ cb) {
+  uint32_t own = 0xFFFFFFFFu;
+#pragma unroll
+  for (int e = 0; e < 5; ++e) {
+    uint32_t x = ca[e];
+    if (x == 0xFFFFFFFFu) break;
+#pragma unroll
+    for (int f = 0; f < 5; ++f)
+      if (cb[f] == x && x < own) own = x;
+  }
+  return own;
+}
+
+template <bool FP32, bool QUAD>
+__global__ void __launch_bounds__(kThreads) k_pair(
+    uint64_t mA, const uint32_t* __restrict__ cell_of_a, const uint2* __restrict__ rng, int nslot,
+    const double* __restrict__ axv, const double* __restrict__ ayv, const double* __restrict__ azv,
+    const double* __restrict__ bxv, const double* __restrict__ byv, const double* __restrict__ bzv,
+    const float4* __restrict__ a32, const float4* __restrict__ b32, double C, float lo32,
+    float hi32, const uint32_t* __restrict__ uniqA, const uint32_t* __restrict__ idxA,
+    const uint32_t* __restrict__ idxB, const uint32_t* __restrict__ cellsA,
+    const uint32_t* __restrict__ cellsB, PairSink sink) {
+  const uint64_t k0 = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+  unsigned long long ntest = 0, ndup = 0;
+  // every thread of the warp runs the same number of outer iterations
+  for (uint64_t kb0 = (uint64_t)blockIdx.x * kThreads; kb0 < mA; kb0 += stride) {
+    uint64_t k = kb0 + (threadIdx.x);
+    bool live = k < mA;
+    uint32_t c = live ? cell_of_a[k] : 0u;
+    double ax = 0, ay = 0, az = 0;
+    float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) {
+      if (FP32) {
+        a4 = a32[k];
+      } else {
+        ax = axv[k]; ay = ayv[k]; az = azv[k];
+      }
+    }
+    for (int s = 0; s < nslot; ++s) {
+      uint2 r = live ? rng[(uint64_t)c * nslot + s] : make_uint2(0u, 0u);
+      uint32_t len = r.y - r.x;
+      ntest += len;
+      uint32_t maxlen = __reduce_max_sync(0xffffffffu, len);
+      for (uint32_t t = 0; t < maxlen; ++t) {
+        bool act = t < len;
+        uint32_t j = r.x + t;
+        bool hit = false, band = false;
+        if (act) {
+          if (FP32) {
+            float4 b = b32[j];
+            float dx = a4.x - b.x, dy = a4.y - b.y, dz = a4.z - b.z;
+            float s2 = dx * dx;
+            s2 = fmaf(dy, dy, s2);
+            s2 = fmaf(dz, dz, s2);
+            hit = s2 <= lo32;
+            band = !hit && s2 <= hi32;
+          } else {
+            double s2 = c_chord2(ax, ay, az, bxv[j], byv[j], bzv[j]);
+            hit = s2 <= C;
+          }
+          if (QUAD && (hit || band)) {
+            uint32_t own = quad_owner(cellsA + 5ull * idxA[k], cellsB + 5ull * idxB[j]);
+            if (own != uniqA[c]) {
+              if (hit) ++ndup;
+              hit = false;
+              band = false;
+            }
+          }
+        }
+        warp_emit(hit, (uint32_t)k, j, sink.rows, sink.count, sink.cap, sink.err);
+        if (FP32) warp_emit(band, (uint32_t)k, j, sink.band, sink.band_count, sink.band_cap, sink.err);
+      }
+    }
+  }
+  (void)k0;
+  // one atomic per warp for the counters
+  for (int o = 16; o > 0; o >>= 1) {
+    ntest += __shfl_down_sync(0xffffffffu, ntest, o);
+    ndup += __shfl_down_sync(0xffffffffu, ndup, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (ntest) atomicAdd(sink.tests, ntest);
+    if (ndup) atomicAdd(sink.dups, ndup);
+  }
+}
+
+// Binary64 decision for guard-band candidates (both vectors recomputed in
+// the canonical arithmetic from the original coordinates).
+__global__ void __launch_bounds__(kThreads) k_recheck(
+    const uint2* __restrict__ band, const unsigned long long* __restrict__ nband_dev,
+    uint64_t band_cap, const uint32_t* __restrict__ idxA, const uint32_t* __restrict__ idxB,
+    const double* __restrict__ raA, const double* __restrict__ decA,
+    const double* __restrict__ raB, const double* __restrict__ decB, double C, uint2* rows,
+    unsigned long long* count, uint64_t cap, int* err) {
+  uint64_t nb = *nband_dev;
+  if (nb > band_cap) nb = band_cap;
+  for (uint64_t b0 = (uint64_t)blockIdx.x * kThreads; b0 < nb; b0 += (uint64_t)gridDim.x * kThreads) {
+    uint64_t q = b0 + threadIdx.x;
+    bool hit = false;
+    uint2 p = make_uint2(0u, 0u);
+    if (q < nb) {
+      p = band[q];
+      uint32_t ia = idxA[p.x], ib = idxB[p.y];
+      double ax, ay, az, bx, by, bz;
+      c_unitvec(c_norm_ra(raA[ia]), decA[ia], &ax, &ay, &az);
+      c_unitvec(c_norm_ra(raB[ib]), decB[ib], &bx, &by, &bz);
+      hit = c_chord2(ax, ay, az, bx, by, bz) <= C;
+    }
+    warp_emit(hit, p.x, p.y, rows, count, cap, err);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Output rows: ids and separations of each matched (A entry, B entry).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double sep_arcsec_from_chord2(double s) {
+  double h = sqrt(s) * 0.5;
+  if (h > 1.0) h = 1.0;
+  return 2.0 * asin(h) * (648000.0 / 3.141592653589793238462643);
+}
+
+template <bool FP32>
+__global__ void k_rows(const uint2* __restrict__ rows, uint64_t M,
+                       const uint32_t* __restrict__ idxA, const uint32_t* __restrict__ idxB,
+                       const uint64_t* __restrict__ idA, const uint64_t* __restrict__ idB,
+                       const double* __restrict__ axv, const double* __restrict__ ayv,
+                       const double* __restrict__ azv, const double* __restrict__ bxv,
+                       const double* __restrict__ byv, const double* __restrict__ bzv,
+                       const double* __restrict__ raA, const double* __restrict__ decA,
+                       const double* __restrict__ raB, const double* __restrict__ decB,
+                       int want_sep, uint64_t* __restrict__ ka, uint64_t* __restrict__ kb,
+                       double* __restrict__ sep, uint32_t* __restrict__ perm) {
+  for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
+       m += (uint64_t)gridDim.x * blockDim.x) {
+    uint2 p = rows[m];
+    uint32_t ia = idxA[p.x], ib = idxB[p.y];
+    ka[m] = idA[ia];
+    kb[m] = idB[ib];
+    perm[m] = (uint32_t)m;
+    if (want_sep) {
+      double s2;
+      if (FP32) {
+        double ax, ay, az, bx, by, bz;
+        c_unitvec(c_norm_ra(raA[ia]), decA[ia], &ax, &ay, &az);
+        c_unitvec(c_norm_ra(raB[ib]), decB[ib], &bx, &by, &bz);
+        s2 = c_chord2(ax, ay, az, bx, by, bz);
+      } else {
+        s2 = c_chord2(axv[p.x], ayv[p.x], azv[p.x], bxv[p.y], byv[p.y], bzv[p.y]);
+      }
+      sep[m] = sep_arcsec_from_chord2(s2);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_gather(const T* __restrict__ src, const uint32_t* __restrict__ perm, uint64_t n,
+                         T* __restrict__ dst) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    dst[i] = src[perm[i]];
+}
+
+__global__ void k_iota(uint32_t* __restrict__ v, uint64_t n) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    v[i] = (uint32_t)i;
+}
+
+}  // namespace hlc

@@ -1,0 +1,188 @@
+// Single-pass scans with decoupled look-back: an exclusive prefix sum and the
+// run-length cell table (unique cells and their start offsets) of sorted keys.
+// The cell table is the "HEALPix data block" index of Sec. 4.2 / Fig. 7: each
+// non-empty cell becomes a range [start[c], start[c+1]) of the sorted arrays.
+#pragma once
+
+#include "common.cuh"
+#include "sort.cuh"
+
+namespace hlc {
+namespace sc {
+
+constexpr int kBlock = 256;
+constexpr int kIpt = 8;
+constexpr int kTile = kBlock * kIpt;
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagInc = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+constexpr long long kSpinLimit = 1ll << 26;
+
+// Called by one thread of the tile: publish the tile aggregate, walk back to
+// the nearest inclusive prefix, publish this tile's inclusive prefix and
+// return its exclusive prefix.
+__device__ __forceinline__ unsigned long long lookback_prefix(uint32_t tile,
+                                                              unsigned long long agg,
+                                                              unsigned long long* lb, int* err) {
+  if (tile == 0) {
+    st_release_u64(lb, kFlagInc | agg);
+    return 0;
+  }
+  st_release_u64(lb + tile, kFlagAgg | agg);
+  unsigned long long excl = 0;
+  long long spins = 0;
+  int64_t j = (int64_t)tile - 1;
+  while (j >= 0) {
+    unsigned long long w = ld_acquire_u64(lb + j);
+    unsigned long long f = w & ~kValMask;
+    if (f == 0) {
+      if (++spins > kSpinLimit) {
+        atomicOr(err, DERR_TIMEOUT);
+        break;
+      }
+      continue;
+    }
+    excl += w & kValMask;
+    if (f == kFlagInc) break;
+    --j;
+  }
+  st_release_u64(lb + tile, kFlagInc | (excl + agg));
+  return excl;
+}
+
+struct ScanSmem {
+  unsigned long long ws[kBlock / 32];
+  unsigned long long base;
+  uint32_t tile;
+};
+
+// out[i] = sum_{k<i} in[i]; *total = sum of all.
+__global__ void __launch_bounds__(kBlock) k_scan_excl(const uint32_t* __restrict__ in,
+                                                      uint64_t* __restrict__ out, uint64_t n,
+                                                      unsigned long long* lb, uint32_t* ctr,
+                                                      unsigned long long* total, int* err) {
+  __shared__ ScanSmem S;
+  const int t = threadIdx.x;
+  if (t == 0) S.tile = atomicAdd(ctr, 1u);
+  __syncthreads();
+  const uint32_t tile = S.tile;
+  const uint64_t e0 = (uint64_t)tile * kTile + (uint64_t)t * kIpt;
+  uint32_t v[kIpt];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) {
+    v[i] = (e0 + i < n) ? in[e0 + i] : 0u;
+    sum += v[i];
+  }
+  unsigned long long tot;
+  unsigned long long pre = rs::block_excl_scan(sum, S.ws, &tot);
+  if (t == 0) S.base = lookback_prefix(tile, tot, lb, err);
+  __syncthreads();
+  unsigned long long run = S.base + pre;
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) {
+    if (e0 + i < n) out[e0 + i] = run;
+    run += v[i];
+  }
+  if (e0 < n && e0 + kIpt >= n) *total = run;  // the thread holding element n-1
+}
+
+// Cell table of sorted keys at a coarser level (key >> shift): cell_of[e] =
+// index of e's cell, uniq[c] = cell id, start[c] = first element of cell c,
+// start[m] = n and *m_out = m.
+__global__ void __launch_bounds__(kBlock) k_cell_rle(const uint32_t* __restrict__ keys,
+                                                     uint64_t n, int shift,
+                                                     uint32_t* __restrict__ cell_of,
+                                                     uint32_t* __restrict__ uniq,
+                                                     uint32_t* __restrict__ start,
+                                                     unsigned long long* lb, uint32_t* ctr,
+                                                     unsigned long long* m_out, int* err) {
+  __shared__ ScanSmem S;
+  const int t = threadIdx.x;
+  if (t == 0) S.tile = atomicAdd(ctr, 1u);
+  __syncthreads();
+  const uint32_t tile = S.tile;
+  const uint64_t e0 = (uint64_t)tile * kTile + (uint64_t)t * kIpt;
+  uint32_t c[kIpt];
+  bool head[kIpt];
+  unsigned long long sum = 0;
+  uint32_t prev = (e0 > 0 && e0 - 1 < n) ? (keys[e0 - 1] >> shift) : 0xFFFFFFFFu;
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) {
+    if (e0 + i < n) {
+      c[i] = keys[e0 + i] >> shift;
+      head[i] = (e0 + i == 0) || (c[i] != prev);
+      prev = c[i];
+    } else {
+      head[i] = false;
+    }
+    sum += head[i];
+  }
+  unsigned long long tot;
+  unsigned long long pre = rs::block_excl_scan(sum, S.ws, &tot);
+  if (t == 0) S.base = lookback_prefix(tile, tot, lb, err);
+  __syncthreads();
+  unsigned long long run = S.base + pre;  // heads before element e0
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) {
+    uint64_t e = e0 + i;
+    if (e < n) {
+      if (head[i]) {
+        uniq[run] = c[i];
+        start[run] = (uint32_t)e;
+        ++run;
+      }
+      cell_of[e] = (uint32_t)(run - 1);
+      if (e == n - 1) {
+        start[run] = (uint32_t)n;
+        *m_out = run;
+      }
+    }
+  }
+}
+
+}  // namespace sc
+
+inline size_t scan_scratch_bytes(uint64_t n) {
+  uint64_t tiles = (n + sc::kTile - 1) / sc::kTile;
+  return 256 + (tiles + 1) * 8;
+}
+
+// Exclusive scan of n uint32 values into uint64 offsets; *total_dev receives
+// the sum (device).  scratch: scan_scratch_bytes(n) bytes.
+inline int scan_exclusive(const uint32_t* in, uint64_t* out, uint64_t n,
+                          unsigned long long* total_dev, void* scratch, int* dev_err,
+                          cudaStream_t st) {
+  if (n == 0) {
+    HLC_CUDA(cudaMemsetAsync(total_dev, 0, 8, st));
+    return HLC_OK;
+  }
+  uint64_t tiles = (n + sc::kTile - 1) / sc::kTile;
+  uint32_t* ctr = (uint32_t*)scratch;
+  unsigned long long* lb = (unsigned long long*)((char*)scratch + 256);
+  HLC_CUDA(cudaMemsetAsync(scratch, 0, scan_scratch_bytes(n), st));
+  sc::k_scan_excl<<<(unsigned)tiles, sc::kBlock, 0, st>>>(in, out, n, lb, ctr, total_dev, dev_err);
+  HLC_LAUNCH_CHECK();
+  return HLC_OK;
+}
+
+// Cell table of sorted keys (see k_cell_rle); *m_dev receives m (device).
+inline int cell_table(const uint32_t* keys, uint64_t n, int shift, uint32_t* cell_of,
+                      uint32_t* uniq, uint32_t* start, unsigned long long* m_dev, void* scratch,
+                      int* dev_err, cudaStream_t st) {
+  if (n == 0) {
+    HLC_CUDA(cudaMemsetAsync(m_dev, 0, 8, st));
+    HLC_CUDA(cudaMemsetAsync(start, 0, 4, st));
+    return HLC_OK;
+  }
+  uint64_t tiles = (n + sc::kTile - 1) / sc::kTile;
+  uint32_t* ctr = (uint32_t*)scratch;
+  unsigned long long* lb = (unsigned long long*)((char*)scratch + 256);
+  HLC_CUDA(cudaMemsetAsync(scratch, 0, scan_scratch_bytes(n), st));
+  sc::k_cell_rle<<<(unsigned)tiles, sc::kBlock, 0, st>>>(keys, n, shift, cell_of, uniq, start, lb,
+                                                         ctr, m_dev, dev_err);
+  HLC_LAUNCH_CHECK();
+  return HLC_OK;
+}
+
+}  // namespace hlc

@@ -1,0 +1,259 @@
+// Device-wide primitives: a stable LSD radix sort of (key, uint32 value)
+// pairs in one sweep per 8-bit digit with decoupled look-back, and a
+// single-pass exclusive scan built on the same look-back.
+//
+// The sort of the cell keys is the B300 form of the paper's map from HEALPix
+// index to records (Sec. 4.2, Fig. 7): the records of a cell end up
+// contiguous, so a cell is a range [start, end) of the sorted arrays.
+#pragma once
+
+#include "common.cuh"
+
+namespace hlc {
+namespace rs {
+
+constexpr int kBlock = 256;  // threads per CTA; one thread per digit value
+constexpr int kWarps = kBlock / 32;
+constexpr int kIpt = 15;     // items per thread
+constexpr int kTile = kBlock * kIpt;
+constexpr int kRadix = 256;
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagInc = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+constexpr long long kSpinLimit = 1ll << 26;
+
+// Histogram of every digit pass at once.
+template <typename K>
+__global__ void __launch_bounds__(kBlock) k_digit_hist(const K* __restrict__ keys, uint64_t n,
+                                                       int npass, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[8][kRadix];
+  for (int i = threadIdx.x; i < 8 * kRadix; i += kBlock) sh[i / kRadix][i % kRadix] = 0;
+  __syncthreads();
+  for (uint64_t e = (uint64_t)blockIdx.x * kBlock + threadIdx.x; e < n;
+       e += (uint64_t)gridDim.x * kBlock) {
+    K k = keys[e];
+    for (int p = 0; p < npass; ++p) atomicAdd(&sh[p][(uint32_t)(k >> (8 * p)) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < npass * kRadix; i += kBlock) {
+    uint32_t v = sh[i / kRadix][i % kRadix];
+    if (v) atomicAdd(&hist[i], v);
+  }
+}
+
+// Exclusive scan of one 256-bin histogram per pass (one CTA per pass).
+__global__ void __launch_bounds__(kBlock) k_hist_scan(const uint32_t* __restrict__ hist,
+                                                      uint32_t* __restrict__ offs) {
+  __shared__ uint32_t ws[kWarps];
+  int p = blockIdx.x, t = threadIdx.x;
+  uint32_t v = hist[p * kRadix + t];
+  uint32_t incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((t & 31) >= o) incl += y;
+  }
+  if ((t & 31) == 31) ws[t >> 5] = incl;
+  __syncthreads();
+  uint32_t wpre = 0;
+  for (int w = 0; w < (t >> 5); ++w) wpre += ws[w];
+  offs[p * kRadix + t] = wpre + incl - v;
+}
+
+// Block-wide exclusive scan of one value per thread (kBlock threads).
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long v,
+                                                              unsigned long long* ws,
+                                                              unsigned long long* total) {
+  int t = threadIdx.x;
+  unsigned long long incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((t & 31) >= o) incl += y;
+  }
+  if ((t & 31) == 31) ws[t >> 5] = incl;
+  __syncthreads();
+  unsigned long long wpre = 0, tot = 0;
+  for (int w = 0; w < kWarps; ++w) {
+    if (w < (t >> 5)) wpre += ws[w];
+    tot += ws[w];
+  }
+  __syncthreads();
+  if (total) *total = tot;
+  return wpre + incl - v;
+}
+
+template <typename K>
+struct SweepSmem {
+  K keys[kTile];
+  uint32_t vals[kTile];
+  uint32_t whist[kWarps][kRadix];
+  uint32_t dstart[kRadix];
+  unsigned long long gbase[kRadix];
+  unsigned long long ws[kWarps];
+  uint32_t tile;
+};
+
+// One digit pass: rank each tile's keys by digit (stable), obtain the tile's
+// global offset per digit by decoupled look-back over earlier tiles, and write
+// the tile out grouped by digit (coalesced within each digit run).
+template <typename K>
+__global__ void __launch_bounds__(kBlock) k_onesweep(
+    const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
+    uint32_t* __restrict__ vout, uint64_t n, int shift, const uint32_t* __restrict__ goff,
+    unsigned long long* __restrict__ lookback, uint32_t* __restrict__ tile_ctr,
+    int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SweepSmem<K>& S = *reinterpret_cast<SweepSmem<K>*>(smem_raw);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (t == 0) S.tile = atomicAdd(tile_ctr, 1u);
+  for (int i = t; i < kWarps * kRadix; i += kBlock) (&S.whist[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t tile = S.tile;
+  const uint64_t base = (uint64_t)tile * kTile;
+  const uint64_t wbase = base + (uint64_t)warp * (kIpt * 32);
+
+  K k[kIpt];
+  uint32_t v[kIpt];
+  int d[kIpt];
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) {
+    uint64_t e = wbase + (uint64_t)i * 32 + lane;
+    if (e < n) {
+      k[i] = kin[e];
+      v[i] = vin[e];
+      d[i] = (int)((uint32_t)(k[i] >> shift) & 255u);
+    } else {
+      d[i] = kRadix;  // past the end: not ranked
+    }
+  }
+  uint32_t r[kIpt];
+  const unsigned lt = lanemask_lt();
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) {
+    unsigned peers = __match_any_sync(0xffffffffu, d[i]);
+    bool valid = d[i] < kRadix;
+    uint32_t before = valid ? S.whist[warp][d[i]] : 0u;
+    r[i] = before + __popc(peers & lt);
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) S.whist[warp][d[i]] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // thread t owns digit t: warp offsets within the tile and the tile count
+  uint32_t cnt = 0;
+  for (int w = 0; w < kWarps; ++w) {
+    uint32_t c = S.whist[w][t];
+    S.whist[w][t] = cnt;
+    cnt += c;
+  }
+  unsigned long long excl = 0;
+  unsigned long long* slot = lookback + (uint64_t)tile * kRadix + t;
+  if (tile == 0) {
+    st_release_u64(slot, kFlagInc | cnt);
+  } else {
+    st_release_u64(slot, kFlagAgg | cnt);
+    long long spins = 0;
+    int64_t j = (int64_t)tile - 1;
+    while (j >= 0) {
+      unsigned long long w = ld_acquire_u64(lookback + (uint64_t)j * kRadix + t);
+      unsigned long long flag = w & ~kValMask;
+      if (flag == 0) {
+        if (++spins > kSpinLimit) {
+          atomicOr(err, DERR_TIMEOUT);
+          break;
+        }
+        continue;
+      }
+      excl += w & kValMask;
+      if (flag == kFlagInc) break;
+      --j;
+    }
+    st_release_u64(slot, kFlagInc | (excl + cnt));
+  }
+  S.gbase[t] = (unsigned long long)goff[t] + excl;
+  unsigned long long dst = block_excl_scan(cnt, S.ws, nullptr);
+  S.dstart[t] = (uint32_t)dst;
+  __syncthreads();
+
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) {
+    if (d[i] < kRadix) {
+      uint32_t pos = S.dstart[d[i]] + S.whist[warp][d[i]] + r[i];
+      S.keys[pos] = k[i];
+      S.vals[pos] = v[i];
+    }
+  }
+  __syncthreads();
+  uint32_t cnt_tile = (uint32_t)(n - base < (uint64_t)kTile ? n - base : (uint64_t)kTile);
+  for (uint32_t p = t; p < cnt_tile; p += kBlock) {
+    K kk = S.keys[p];
+    int dd = (int)((uint32_t)(kk >> shift) & 255u);
+    unsigned long long g = S.gbase[dd] + (p - S.dstart[dd]);
+    kout[g] = kk;
+    vout[g] = S.vals[p];
+  }
+}
+
+}  // namespace rs
+
+// Host driver.  keys/vals are sorted in place (the result is copied back if
+// the last pass wrote the alternate buffers).  tmp_keys/tmp_vals: n elements;
+// scratch: from sort_scratch_bytes().  Returns HLC_OK or an error code; a
+// timed-out look-back is reported through dev_err (checked by the caller).
+constexpr size_t kSortLookbackOffset = 16640;  // hist | offs | counters | look-back
+
+inline size_t sort_scratch_bytes(uint64_t n, int npass) {
+  uint64_t tiles = (n + rs::kTile - 1) / rs::kTile;
+  if (tiles == 0) tiles = 1;
+  return kSortLookbackOffset + (size_t)npass * tiles * rs::kRadix * 8;
+}
+
+template <typename K>
+int radix_sort_pairs(K* keys, uint32_t* vals, K* tmp_keys, uint32_t* tmp_vals, uint64_t n,
+                     int key_bits, void* scratch, int* dev_err, cudaStream_t st) {
+  if (n <= 1) return HLC_OK;
+  int npass = (key_bits + 7) / 8;
+  if (npass < 1) npass = 1;
+  if (npass > (int)sizeof(K)) npass = (int)sizeof(K);
+  uint64_t tiles = (n + rs::kTile - 1) / rs::kTile;
+  if (tiles > 0xFFFFFFFFull) {
+    set_error("radix sort: too many elements");
+    return HLC_EINVAL;
+  }
+  char* sp = (char*)scratch;
+  uint32_t* hist = (uint32_t*)sp;
+  uint32_t* offs = (uint32_t*)(sp + 8192);
+  uint32_t* ctr = (uint32_t*)(sp + 16384);
+  unsigned long long* lb = (unsigned long long*)(sp + kSortLookbackOffset);
+  size_t lb_bytes = (size_t)npass * tiles * rs::kRadix * 8;
+  HLC_CUDA(cudaMemsetAsync(hist, 0, (size_t)npass * rs::kRadix * 4, st));
+  HLC_CUDA(cudaMemsetAsync(ctr, 0, 64, st));
+  HLC_CUDA(cudaMemsetAsync(lb, 0, lb_bytes, st));
+  rs::k_digit_hist<K><<<grid_for(n, rs::kBlock, 148 * 8), rs::kBlock, 0, st>>>(keys, n, npass,
+                                                                               hist);
+  HLC_LAUNCH_CHECK();
+  rs::k_hist_scan<<<npass, rs::kBlock, 0, st>>>(hist, offs);
+  HLC_LAUNCH_CHECK();
+  size_t smem = sizeof(rs::SweepSmem<K>);
+  HLC_CUDA(cudaFuncSetAttribute(rs::k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  K* ka = keys;
+  uint32_t* va = vals;
+  K* kb = tmp_keys;
+  uint32_t* vb = tmp_vals;
+  for (int p = 0; p < npass; ++p) {
+    rs::k_onesweep<K><<<(unsigned)tiles, rs::kBlock, smem, st>>>(
+        ka, va, kb, vb, n, 8 * p, offs + p * rs::kRadix, lb + (size_t)p * tiles * rs::kRadix,
+        ctr + p, dev_err);
+    HLC_LAUNCH_CHECK();
+    K* tk = ka; ka = kb; kb = tk;
+    uint32_t* tv = va; va = vb; vb = tv;
+  }
+  if (ka != keys) {
+    HLC_CUDA(cudaMemcpyAsync(keys, ka, n * sizeof(K), cudaMemcpyDeviceToDevice, st));
+    HLC_CUDA(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+  }
+  return HLC_OK;
+}
+
+}  // namespace hlc
