@@ -215,10 +215,12 @@ def _catalog(ra, dec, ids):
 def hlc_plan(A, B, radius_arcsec: float, fine_level: int, coarse_level: int | None = None,
              boundary: int = HLC_COMPLETE8, precision: int = HLC_FP32_GUARD,
              index: int = HLC_INDEX_BSEARCH, model: int = HLC_MODEL_PLA, want_sep: bool = True,
-             device_mem_budget: int = 0, stream=None, torch_alloc: bool = True) -> Plan:
+             device_mem_budget: int = 0, stream=None, torch_alloc: bool = False) -> Plan:
     """Index two catalogues.  A and B are (ra, dec, id) triples (torch tensors
     on the device or host, or numpy arrays on the host) or objects with .ra,
-    .dec, .id.  Returns a Plan for hlc_match."""
+    .dec, .id.  Device memory comes from the library's stream-ordered pool,
+    or from torch's caching allocator with torch_alloc=True.  Returns a Plan
+    for hlc_match."""
     _require_cuda()
     L = lib()
     cA, keepA = _catalog(*(_triple(A)))

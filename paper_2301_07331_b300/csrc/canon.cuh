@@ -66,6 +66,7 @@ __device__ __forceinline__ void c_sincos_deg(double x, double* s, double* c) {
 }
 
 __device__ __forceinline__ double c_norm_ra(double ra) {
+  if (ra >= 0.0 && ra < 360.0) return ra;  // fmod would return it unchanged
   double a = fmod(ra, 360.0);
   if (a < 0.0) a = __dadd_rn(a, 360.0);
   if (a >= 360.0) a = __dsub_rn(a, 360.0);

@@ -14,9 +14,13 @@
 namespace hlc {
 
 // Bound on |component error| of fp32_unitvec against the exact unit vector.
-// (1.5 ulp per factor + 0.5 ulp per product, with ulp <= 2^-24 near 1, plus
-// the 1e-16 of the binary64 inputs: about 2.1e-7; stated with margin.)
-constexpr double kUnitVecErr = 2.5e-7;
+// Each sine/cosine factor is within ~5e-8 of the truth (polynomial roundings
+// below one ulp of 2^-24, truncation below 2e-9, the float-float argument
+// within 1e-15); a product adds half an ulp (3e-8): about 1.3e-7 per
+// component; stated with margin.
+constexpr double kUnitVecErr = 1.6e-7;
+// Bound on |sin(dec) - fp32 sine| used by the guarded ang2pix.
+constexpr float kSinErr = 1.2e-7f;
 
 __device__ __forceinline__ void fp32_sincos_reduced(float p, float e, float* s, float* c) {
   // p + e radians, |p| <= pi/4 + tiny, |e| <= 2^-24 |p|
@@ -63,6 +67,12 @@ __device__ __forceinline__ void fp32_sincos_deg(double x, float* s, float* c) {
   }
 }
 
+__device__ __forceinline__ float fp32_sin_deg(double x) {
+  float s, c;
+  fp32_sincos_deg(x, &s, &c);
+  return s;
+}
+
 __device__ __forceinline__ float4 fp32_unitvec(double ra, double dec) {
   float sd, cd, sa, ca;
   fp32_sincos_deg(dec, &sd, &cd);
@@ -79,7 +89,7 @@ inline double fp32_guard_band(double C, double comp_err) {
   double delta = 2.0 * comp_err * (1.0 + u) + D * u;  // per-component error
   double err = 2.0 * sqrt(3.0) * delta * D + 3.0 * delta * delta;
   err += 4.0 * u * (C + err);  // roundings of the sum of squares
-  return 2.0 * err;            // margin factor 2
+  return 1.5 * err;            // margin factor 1.5
 }
 
 }  // namespace hlc

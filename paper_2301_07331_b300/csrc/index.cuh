@@ -1,0 +1,81 @@
+// Cell offset index of a sorted key array (the calculation-block index of
+// Sec. 4.2 / Fig. 7, in B300 form).
+//
+// The entries of a catalogue are sorted by fine cell key, so every cell is a
+// contiguous range.  A dense table T at a coarser order Lt holds, for every
+// coarse cell Q, the first entry whose key lies in Q or after it:
+// T[Q] = #{entries with key >> s < Q}, s = 2 (L - Lt).  The range of a fine
+// cell q is then found by a short binary search of the keys inside
+// [T[q >> s], T[(q >> s) + 1]).  Lt is chosen so that the table has about as
+// many slots as entries (one to a few keys per window).
+#pragma once
+
+#include "common.cuh"
+
+namespace hlc {
+
+struct CellIndex {
+  const uint32_t* keys = nullptr;  // sorted fine keys
+  const uint32_t* table = nullptr; // 12 * 4^Lt + 1 offsets
+  int shift = 0;                   // 2 (L - Lt)
+};
+
+// Counts per coarse cell and the number of distinct fine keys (heads).
+__global__ void k_coarse_hist(const uint32_t* __restrict__ keys, uint64_t n, int shift,
+                              uint32_t* __restrict__ hist, unsigned long long* __restrict__ heads) {
+  unsigned long long h = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t k = keys[i];
+    if (hist) atomicAdd(&hist[k >> shift], 1u);
+    h += (i == 0 || keys[i - 1] != k);
+  }
+  for (int o = 16; o > 0; o >>= 1) h += __shfl_down_sync(0xffffffffu, h, o);
+  if ((threadIdx.x & 31) == 0 && h) atomicAdd(heads, h);
+}
+
+// [begin, end) of the entries with key q.
+__device__ __forceinline__ uint2 cell_range(const CellIndex& ix, uint32_t q) {
+  uint32_t Q = q >> ix.shift;
+  uint32_t lo = __ldg(ix.table + Q), hi = __ldg(ix.table + Q + 1);
+  uint32_t a = lo, b = hi;
+  while (a < b) {  // lower bound of q
+    uint32_t mid = (a + b) >> 1;
+    if (__ldg(ix.keys + mid) < q)
+      a = mid + 1;
+    else
+      b = mid;
+  }
+  uint32_t first = a;
+  b = hi;
+  while (a < b) {  // upper bound of q
+    uint32_t mid = (a + b) >> 1;
+    if (__ldg(ix.keys + mid) <= q)
+      a = mid + 1;
+    else
+      b = mid;
+  }
+  return make_uint2(first, a);
+}
+
+// Order of the coarse table for m entries at fine order L.
+inline int coarse_table_order(uint64_t m, int L) {
+  int lt = 0;
+  while (lt < L && 12ull * (1ull << (2 * lt)) < m) ++lt;
+  return lt;
+}
+
+// Highest bit in which the ids differ (OR of id ^ id[0]).
+__global__ void k_id_diff(const uint64_t* __restrict__ id, uint64_t n,
+                          unsigned long long* __restrict__ out) {
+  unsigned long long acc = 0;
+  if (n == 0) return;
+  uint64_t first = id[0];
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    acc |= id[i] ^ first;
+  for (int o = 16; o > 0; o >>= 1) acc |= __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicOr(out, acc);
+}
+
+}  // namespace hlc

@@ -7,7 +7,9 @@
 #include "canon.cuh"
 #include "common.cuh"
 #include "fp32.cuh"
+#include "index.cuh"
 #include "match.cuh"
+#include "output.cuh"
 #include "scan.cuh"
 #include "sort.cuh"
 
@@ -100,6 +102,13 @@ int ensure_device_tables() {
   build_neighbour_tables(face, map);
   HLC_CUDA(cudaMemcpyToSymbol(d_nbr_face, face, sizeof(face)));
   HLC_CUDA(cudaMemcpyToSymbol(d_nbr_map, map, sizeof(map)));
+  // keep freed stream-ordered allocations cached in the device's default pool
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
   if (dev >= 0 && dev < 64) g_dev_ready[dev] = true;
   return HLC_OK;
 }
@@ -162,18 +171,19 @@ struct CatDev {
   double* ra = nullptr;
   double* dec = nullptr;
   uint64_t* id = nullptr;
-  uint32_t* key = nullptr;
-  uint32_t* idx = nullptr;
+  uint32_t* key = nullptr;   // sorted cell keys of the entries
+  uint32_t* idx = nullptr;   // source of each sorted entry
   double *vx = nullptr, *vy = nullptr, *vz = nullptr;
   float4* v32 = nullptr;
-  uint32_t* cells5 = nullptr;
-  uint32_t* cell_of = nullptr;
-  uint32_t* uniq = nullptr;
-  uint32_t* start = nullptr;
-  uint64_t u = 0;
+  uint32_t* cells5 = nullptr;  // quad: cell set of each source
+  uint32_t* table = nullptr;   // coarse offset table (catalogue B)
+  int table_shift = 0;
+  int table_order = 0;
+  uint64_t cells = 0;
 };
 
-enum Ctr { C_ROWS = 0, C_BAND, C_TESTS, C_DUPS, C_M, C_TOTAL, C_N };
+enum Ctr { C_ROWS = 0, C_BAND, C_TESTS, C_DUPS, C_M, C_TOTAL, C_HEADS_A, C_HEADS_B,
+           C_IDDIFF, C_MAXB, C_N };
 
 }  // namespace hlc
 
@@ -191,6 +201,9 @@ struct hlc_plan_s {
   unsigned long long* ctr = nullptr;
   hlc_stats stats{};
   unsigned long long launches0 = 0;
+  int id_high_bit = -1;
+  uint64_t row_cap = 0;
+  unsigned long long plan_launches = 0;
   cudaEvent_t ev[12] = {};
   bool events = false;
 };
@@ -270,13 +283,15 @@ static float ev_ms(hlc_plan_t* P, int a, int b) {
   return ms;
 }
 
-// Copy one catalogue in, build its sorted entries, payload and cell table.
-static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, double* ms_prep,
-                         double* ms_sort, double* ms_index) {
+// Copy one catalogue in, build its sorted entries, payload and (for B) the
+// coarse offset table.  No host synchronisation in complete mode.
+static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool is_b,
+                         cudaEvent_t ev[4]) {
   Arena& ar = *P->arena;
   cudaStream_t st = plan_stream(P);
   const int L = P->p.fine_level;
   const bool quad = P->p.boundary == HLC_QUAD;
+  const bool fp32 = P->p.precision == HLC_FP32_GUARD;
   X.n = in->n;
   uint64_t n = X.n;
   HLC_ALLOC(ar, X.ra, double, n + 1);
@@ -288,17 +303,18 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, double
     HLC_CUDA(cudaMemcpyAsync(X.dec, in->dec_deg, n * 8, kind, st));
     HLC_CUDA(cudaMemcpyAsync(X.id, in->id, n * 8, kind, st));
   }
-  cudaEvent_t e0, e1, e2, e3;
-  cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2); cudaEventCreate(&e3);
-  cudaEventRecord(e0, st);
-  // entries
+  cudaEventRecord(ev[0], st);
   if (!quad) {
     X.m = n;
     HLC_ALLOC(ar, X.key, uint32_t, n + 1);
     HLC_ALLOC(ar, X.idx, uint32_t, n + 1);
     if (n) {
-      k_prep_keys<<<grid_for(n, kThreads), kThreads, 0, st>>>(X.ra, X.dec, n, L, X.key, X.idx,
-                                                               P->dev_err);
+      if (fp32)
+        k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(X.ra, X.dec, n, L, X.key,
+                                                                      X.idx, P->dev_err);
+      else
+        k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(X.ra, X.dec, n, L, X.key,
+                                                                       X.idx, P->dev_err);
       HLC_LAUNCH_CHECK();
     }
   } else {
@@ -308,11 +324,15 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, double
     void* scr = ar.get(scan_scratch_bytes(n));
     if (!cnt || !off || !scr) return HLC_ENOMEM;
     if (n) {
-      k_quad_cells<<<grid_for(n, kThreads), kThreads, 0, st>>>(
-          X.ra, X.dec, n, P->p.radius_arcsec / 3600.0, L, X.cells5, cnt, P->dev_err);
+      if (fp32)
+        k_quad_cells<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+            X.ra, X.dec, n, P->p.radius_arcsec / 3600.0, L, X.cells5, cnt, P->dev_err);
+      else
+        k_quad_cells<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+            X.ra, X.dec, n, P->p.radius_arcsec / 3600.0, L, X.cells5, cnt, P->dev_err);
       HLC_LAUNCH_CHECK();
     }
-    HLC_TRY(scan_exclusive(cnt, off, n, P->ctr + C_TOTAL, scr, P->dev_err, st));
+    HLC_TRY(scan_exclusive<uint64_t>(cnt, off, n, P->ctr + C_TOTAL, scr, P->dev_err, st));
     unsigned long long m = 0;
     HLC_CUDA(cudaMemcpyAsync(&m, P->ctr + C_TOTAL, 8, cudaMemcpyDeviceToHost, st));
     HLC_CUDA(cudaStreamSynchronize(st));
@@ -328,8 +348,7 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, double
     ar.drop(off);
     ar.drop(scr);
   }
-  cudaEventRecord(e1, st);
-  // sort entries by cell key
+  cudaEventRecord(ev[1], st);
   uint64_t m = X.m;
   if (m > 1) {
     uint32_t* tk = ar.get_n<uint32_t>(m);
@@ -342,9 +361,8 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, double
     ar.drop(tv);
     ar.drop(scr);
   }
-  cudaEventRecord(e2, st);
-  // payload in sorted order
-  if (P->p.precision == HLC_FP64) {
+  cudaEventRecord(ev[2], st);
+  if (!fp32) {
     HLC_ALLOC(ar, X.vx, double, m + 1);
     HLC_ALLOC(ar, X.vy, double, m + 1);
     HLC_ALLOC(ar, X.vz, double, m + 1);
@@ -360,31 +378,30 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, double
       HLC_LAUNCH_CHECK();
     }
   }
-  // cell table at the join level
-  HLC_ALLOC(ar, X.cell_of, uint32_t, m + 1);
-  HLC_ALLOC(ar, X.uniq, uint32_t, m + 1);
-  HLC_ALLOC(ar, X.start, uint32_t, m + 2);
-  {
-    void* scr = ar.get(scan_scratch_bytes(m));
-    if (!scr) return HLC_ENOMEM;
-    int shift = 2 * (L - P->join_level);
-    HLC_TRY(cell_table(X.key, m, shift, X.cell_of, X.uniq, X.start, P->ctr + C_M, scr,
-                       P->dev_err, st));
-    unsigned long long u = 0;
-    HLC_CUDA(cudaMemcpyAsync(&u, P->ctr + C_M, 8, cudaMemcpyDeviceToHost, st));
-    cudaEventRecord(e3, st);
-    HLC_CUDA(cudaStreamSynchronize(st));
-    X.u = u;
+  unsigned long long* heads = P->ctr + (is_b ? C_HEADS_B : C_HEADS_A);
+  if (is_b) {
+    X.table_order = coarse_table_order(m, L);
+    X.table_shift = 2 * (L - X.table_order);
+    uint64_t tsize = 12ull << (2 * X.table_order);
+    uint32_t* hist = ar.get_n<uint32_t>(tsize + 1);
+    HLC_ALLOC(ar, X.table, uint32_t, tsize + 1);
+    void* scr = ar.get(scan_scratch_bytes(tsize + 1));
+    if (!hist || !scr) return HLC_ENOMEM;
+    HLC_CUDA(cudaMemsetAsync(hist, 0, (tsize + 1) * 4, st));
+    if (m) {
+      k_coarse_hist<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.key, m, X.table_shift, hist,
+                                                                 heads);
+      HLC_LAUNCH_CHECK();
+    }
+    HLC_TRY(scan_exclusive<uint32_t>(hist, X.table, tsize + 1, P->ctr + C_TOTAL, scr,
+                                     P->dev_err, st));
+    ar.drop(hist);
     ar.drop(scr);
+  } else if (m) {
+    k_coarse_hist<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.key, m, 0, nullptr, heads);
+    HLC_LAUNCH_CHECK();
   }
-  float a = 0, b = 0, c = 0;
-  cudaEventElapsedTime(&a, e0, e1);
-  cudaEventElapsedTime(&b, e1, e2);
-  cudaEventElapsedTime(&c, e2, e3);
-  *ms_prep += a;
-  *ms_sort += b;
-  *ms_index += c;
-  cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2); cudaEventDestroy(e3);
+  cudaEventRecord(ev[3], st);
   return HLC_OK;
 }
 
@@ -429,24 +446,85 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   }
   ev_record(P, 0);
   P->launches0 = g_launches.load();
-  double mp = 0, ms = 0, mi = 0;
-  int rc = build_catalog(P, A, P->A, &mp, &ms, &mi);
-  if (rc == HLC_OK) rc = build_catalog(P, B, P->B, &mp, &ms, &mi);
+  cudaEvent_t ea[4], eb[4];
+  for (int i = 0; i < 4; ++i) {
+    cudaEventCreate(&ea[i]);
+    cudaEventCreate(&eb[i]);
+  }
+  int rc = build_catalog(P, A, P->A, false, ea);
+  if (rc == HLC_OK) rc = build_catalog(P, B, P->B, true, eb);
+  if (rc == HLC_OK && P->A.n) {
+    k_id_diff<<<grid_for(P->A.n, kThreads, 148u * 8u), kThreads, 0, st>>>(P->A.id, P->A.n,
+                                                                          P->ctr + C_IDDIFF);
+    if (cudaGetLastError() != cudaSuccess) rc = HLC_ECUDA;
+  }
+  unsigned long long hc[C_N] = {0};
+  if (rc == HLC_OK && cudaMemcpyAsync(hc, P->ctr, sizeof(hc), cudaMemcpyDeviceToHost, st) !=
+                          cudaSuccess)
+    rc = HLC_ECUDA;
   if (rc == HLC_OK) rc = check_dev_err(P->dev_err, st, "hlc_plan");
+  float t[6] = {0};
+  if (rc == HLC_OK) {
+    cudaEventElapsedTime(&t[0], ea[0], ea[1]);
+    cudaEventElapsedTime(&t[1], eb[0], eb[1]);
+    cudaEventElapsedTime(&t[2], ea[1], ea[2]);
+    cudaEventElapsedTime(&t[3], eb[1], eb[2]);
+    cudaEventElapsedTime(&t[4], ea[2], ea[3]);
+    cudaEventElapsedTime(&t[5], eb[2], eb[3]);
+  }
+  for (int i = 0; i < 4; ++i) {
+    cudaEventDestroy(ea[i]);
+    cudaEventDestroy(eb[i]);
+  }
   if (rc != HLC_OK) return fail(rc);
   ev_record(P, 1);
+  unsigned long long diff = hc[C_IDDIFF];
+  P->id_high_bit = diff ? 63 - __builtin_clzll(diff) : -1;
   memset(&P->stats, 0, sizeof(P->stats));
   P->stats.n_a = P->A.n;
   P->stats.n_b = P->B.n;
   P->stats.entries_a = P->A.m;
   P->stats.entries_b = P->B.m;
-  P->stats.cells_a = P->A.u;
-  P->stats.cells_b = P->B.u;
+  P->stats.cells_a = hc[C_HEADS_A];
+  P->stats.cells_b = hc[C_HEADS_B];
   P->stats.join_level = P->join_level;
-  P->stats.ms_prep = (float)mp;
-  P->stats.ms_sort = (float)ms;
-  P->stats.ms_index = (float)mi;
+  P->stats.ms_prep = t[0] + t[1];
+  P->stats.ms_sort = t[2] + t[3];
+  P->stats.ms_index = t[4] + t[5];
+  P->plan_launches = g_launches.load() - P->launches0;
   *out = P;
+  return HLC_OK;
+}
+
+// Sort rows (ka, kb, sep) by (id_a, id_b) with two stable LSD radix sorts;
+// results in (oa, ob, os).
+static int sort_rows_lsd(hlc_plan_t* P, uint64_t M, uint64_t* ka, uint64_t* kb, double* sep,
+                         uint64_t* oa, uint64_t* ob, double* os) {
+  Arena& ar = *P->out;
+  cudaStream_t st = plan_stream(P);
+  uint32_t* perm = ar.get_n<uint32_t>(M + 1);
+  uint64_t* tk = ar.get_n<uint64_t>(M + 1);
+  uint32_t* tv = ar.get_n<uint32_t>(M + 1);
+  void* scr = ar.get(sort_scratch_bytes(M + 1, 8));
+  if (!perm || !tk || !tv || !scr) return HLC_ENOMEM;
+  unsigned g = grid_for(M, kThreads);
+  k_iota<<<g, kThreads, 0, st>>>(perm, M);
+  HLC_LAUNCH_CHECK();
+  HLC_CUDA(cudaMemcpyAsync(oa, kb, M * 8, cudaMemcpyDeviceToDevice, st));
+  HLC_TRY(radix_sort_pairs<uint64_t>(oa, perm, tk, tv, M, 64, scr, P->dev_err, st));
+  k_gather<uint64_t><<<g, kThreads, 0, st>>>(ka, perm, M, oa);
+  HLC_LAUNCH_CHECK();
+  HLC_TRY(radix_sort_pairs<uint64_t>(oa, perm, tk, tv, M, 64, scr, P->dev_err, st));
+  k_gather<uint64_t><<<g, kThreads, 0, st>>>(kb, perm, M, ob);
+  HLC_LAUNCH_CHECK();
+  if (sep) {
+    k_gather<double><<<g, kThreads, 0, st>>>(sep, perm, M, os);
+    HLC_LAUNCH_CHECK();
+  }
+  ar.drop(perm);
+  ar.drop(tk);
+  ar.drop(tv);
+  ar.drop(scr);
   return HLC_OK;
 }
 
@@ -458,19 +536,16 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   CatDev& B = P->B;
   const bool fp32 = P->p.precision == HLC_FP32_GUARD;
   const bool quad = P->p.boundary == HLC_QUAD;
-  HLC_CUDA(cudaMemsetAsync(P->ctr, 0, C_N * 8, st));
+  const unsigned long long launches_match0 = g_launches.load();
   HLC_CUDA(cudaMemsetAsync(P->dev_err, 0, 64, st));
   ev_record(P, 2);
-  uint2* rng = ar.get_n<uint2>(A.u * P->nslot + 1);
-  if (!rng) return HLC_ENOMEM;
-  if (A.u) {
-    k_candidates<<<grid_for(A.u, kThreads), kThreads, 0, st>>>(
-        A.uniq, A.u, B.uniq, B.start, B.u, P->join_level, P->nslot, rng);
-    HLC_LAUNCH_CHECK();
-  }
   ev_record(P, 3);
-  uint64_t cap = std::max<uint64_t>(1u << 20, A.n + B.n);
-  uint64_t bcap = fp32 ? std::max<uint64_t>(1u << 16, cap / 8) : 1;
+  CellIndex bix;
+  bix.keys = B.key;
+  bix.table = B.table;
+  bix.shift = B.table_shift;
+  uint64_t cap = P->row_cap ? P->row_cap : std::max<uint64_t>(1u << 20, A.n + B.n);
+  uint64_t bcap = fp32 ? std::max<uint64_t>(1u << 16, cap / 4) : 1;
   uint2* rows = nullptr;
   uint2* band = nullptr;
   unsigned long long h[C_N];
@@ -481,24 +556,25 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
     HLC_CUDA(cudaMemsetAsync(P->ctr, 0, C_N * 8, st));
     PairSink sink{rows, P->ctr + C_ROWS, cap, band, P->ctr + C_BAND, bcap,
                   P->ctr + C_TESTS, P->ctr + C_DUPS, P->dev_err};
-    if (A.m) {
+    if (A.m && B.m) {
       unsigned grid = grid_for(A.m, kThreads, 148u * 16u);
+      const int L = P->join_level;
       if (fp32 && quad)
         k_pair<true, true><<<grid, kThreads, 0, st>>>(
-            A.m, A.cell_of, rng, P->nslot, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-            A.v32, B.v32, P->C, P->lo32, P->hi32, A.uniq, A.idx, B.idx, A.cells5, B.cells5, sink);
+            A.m, A.key, bix, L, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, A.v32,
+            B.v32, P->C, P->lo32, P->hi32, A.idx, B.idx, A.cells5, B.cells5, sink);
       else if (fp32)
         k_pair<true, false><<<grid, kThreads, 0, st>>>(
-            A.m, A.cell_of, rng, P->nslot, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-            A.v32, B.v32, P->C, P->lo32, P->hi32, A.uniq, A.idx, B.idx, nullptr, nullptr, sink);
+            A.m, A.key, bix, L, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, A.v32,
+            B.v32, P->C, P->lo32, P->hi32, A.idx, B.idx, nullptr, nullptr, sink);
       else if (quad)
         k_pair<false, true><<<grid, kThreads, 0, st>>>(
-            A.m, A.cell_of, rng, P->nslot, A.vx, A.vy, A.vz, B.vx, B.vy, B.vz, nullptr, nullptr,
-            P->C, 0.f, 0.f, A.uniq, A.idx, B.idx, A.cells5, B.cells5, sink);
+            A.m, A.key, bix, L, A.vx, A.vy, A.vz, B.vx, B.vy, B.vz, nullptr, nullptr, P->C, 0.f,
+            0.f, A.idx, B.idx, A.cells5, B.cells5, sink);
       else
         k_pair<false, false><<<grid, kThreads, 0, st>>>(
-            A.m, A.cell_of, rng, P->nslot, A.vx, A.vy, A.vz, B.vx, B.vy, B.vz, nullptr, nullptr,
-            P->C, 0.f, 0.f, A.uniq, A.idx, B.idx, nullptr, nullptr, sink);
+            A.m, A.key, bix, L, A.vx, A.vy, A.vz, B.vx, B.vy, B.vz, nullptr, nullptr, P->C, 0.f,
+            0.f, A.idx, B.idx, nullptr, nullptr, sink);
       HLC_LAUNCH_CHECK();
     }
     HLC_CUDA(cudaMemcpyAsync(h, P->ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -515,6 +591,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
       return HLC_ECUDA;
     }
   }
+  P->row_cap = std::max<uint64_t>(P->row_cap, cap);
   ev_record(P, 4);
   if (fp32 && h[C_BAND]) {
     k_recheck<<<grid_for(h[C_BAND], kThreads, 148u * 16u), kThreads, 0, st>>>(
@@ -523,63 +600,96 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
     HLC_LAUNCH_CHECK();
   }
   ev_record(P, 5);
-  unsigned long long M = 0;
-  HLC_CUDA(cudaMemcpyAsync(&M, P->ctr + C_ROWS, 8, cudaMemcpyDeviceToHost, st));
-  HLC_CUDA(cudaStreamSynchronize(st));
+  unsigned long long M = h[C_ROWS];
+  if (fp32 && h[C_BAND]) {
+    HLC_CUDA(cudaMemcpyAsync(&M, P->ctr + C_ROWS, 8, cudaMemcpyDeviceToHost, st));
+    HLC_CUDA(cudaStreamSynchronize(st));
+  }
   HLC_TRY(check_dev_err(P->dev_err, st, "hlc_match"));
-  // output rows, sorted by (id_a, id_b)
+  ar.drop(band);
+  // rows: ids, separations, bucket histogram of id_a
+  const bool want_sep = P->p.want_sep != 0;
   uint64_t* ka = ar.get_n<uint64_t>(M + 1);
   uint64_t* kb = ar.get_n<uint64_t>(M + 1);
-  uint64_t* kt = ar.get_n<uint64_t>(M + 1);
-  uint32_t* perm = ar.get_n<uint32_t>(M + 1);
-  uint64_t* tk = ar.get_n<uint64_t>(M + 1);
-  uint32_t* tv = ar.get_n<uint32_t>(M + 1);
-  double* sep0 = P->p.want_sep ? ar.get_n<double>(M + 1) : nullptr;
-  double* sep = P->p.want_sep ? ar.get_n<double>(M + 1) : nullptr;
-  uint64_t* id_b = ar.get_n<uint64_t>(M + 1);
-  void* scr = ar.get(sort_scratch_bytes(M + 1, 8));
-  if (!ka || !kb || !kt || !perm || !tk || !tv || !id_b || !scr ||
-      (P->p.want_sep && (!sep0 || !sep)))
-    return HLC_ENOMEM;
+  double* sep = want_sep ? ar.get_n<double>(M + 1) : nullptr;
+  uint64_t* ta = ar.get_n<uint64_t>(M + 1);
+  uint64_t* tb = ar.get_n<uint64_t>(M + 1);
+  double* ts = want_sep ? ar.get_n<double>(M + 1) : nullptr;
+  if (!ka || !kb || !ta || !tb || (want_sep && (!sep || !ts))) return HLC_ENOMEM;
+  int hb = P->id_high_bit;
+  int nbits = 1;
+  while (nbits < 22 && (M >> (nbits + 6)) > 0) ++nbits;  // about 64 rows per bucket
+  if (hb >= 0 && nbits > hb + 1) nbits = hb + 1;
+  const bool bucketed = M > 1 && hb >= 0;
+  const int bshift = bucketed ? hb + 1 - nbits : 0;
+  const uint32_t nbk = 1u << nbits;
+  const uint32_t bmask = nbk - 1;
+  uint32_t* bhist = nullptr;
+  uint32_t* boff = nullptr;
+  if (bucketed) {
+    bhist = ar.get_n<uint32_t>(nbk + 1);
+    boff = ar.get_n<uint32_t>(nbk + 1);
+    if (!bhist || !boff) return HLC_ENOMEM;
+    HLC_CUDA(cudaMemsetAsync(bhist, 0, (nbk + 1) * 4, st));
+  }
   if (M) {
     unsigned g = grid_for(M, kThreads);
     if (fp32)
       k_rows<true><<<g, kThreads, 0, st>>>(rows, M, A.idx, B.idx, A.id, B.id, nullptr, nullptr,
                                             nullptr, nullptr, nullptr, nullptr, A.ra, A.dec, B.ra,
-                                            B.dec, P->p.want_sep, ka, kb, sep0, perm);
+                                            B.dec, want_sep, ka, kb, sep, bshift, bmask, bhist);
     else
       k_rows<false><<<g, kThreads, 0, st>>>(rows, M, A.idx, B.idx, A.id, B.id, A.vx, A.vy, A.vz,
                                              B.vx, B.vy, B.vz, nullptr, nullptr, nullptr, nullptr,
-                                             P->p.want_sep, ka, kb, sep0, perm);
+                                             want_sep, ka, kb, sep, bshift, bmask, bhist);
     HLC_LAUNCH_CHECK();
-    // stable LSD: by id_b, then by id_a
-    HLC_CUDA(cudaMemcpyAsync(kt, kb, M * 8, cudaMemcpyDeviceToDevice, st));
-    HLC_TRY(radix_sort_pairs<uint64_t>(kt, perm, tk, tv, M, 64, scr, P->dev_err, st));
-    k_gather<uint64_t><<<g, kThreads, 0, st>>>(ka, perm, M, kt);
+  }
+  ar.drop(rows);
+  uint64_t* oa = ka;
+  uint64_t* ob = kb;
+  double* os = sep;
+  bool done = M <= 1;
+  if (bucketed) {
+    void* scr = ar.get(scan_scratch_bytes(nbk + 1));
+    if (!scr) return HLC_ENOMEM;
+    HLC_TRY(scan_exclusive<uint32_t>(bhist, boff, nbk + 1, P->ctr + C_TOTAL, scr, P->dev_err,
+                                     st));
+    HLC_CUDA(cudaMemsetAsync(P->ctr + C_MAXB, 0, 8, st));
+    k_max_u32<<<grid_for(nbk, kThreads, 1024), kThreads, 0, st>>>(bhist, nbk,
+                                                                  (uint32_t*)(P->ctr + C_MAXB));
     HLC_LAUNCH_CHECK();
-    HLC_TRY(radix_sort_pairs<uint64_t>(kt, perm, tk, tv, M, 64, scr, P->dev_err, st));
-    k_gather<uint64_t><<<g, kThreads, 0, st>>>(kb, perm, M, id_b);
-    HLC_LAUNCH_CHECK();
-    if (sep) {
-      k_gather<double><<<g, kThreads, 0, st>>>(sep0, perm, M, sep);
+    unsigned long long maxb = 0;
+    HLC_CUDA(cudaMemcpyAsync(&maxb, P->ctr + C_MAXB, 8, cudaMemcpyDeviceToHost, st));
+    HLC_CUDA(cudaStreamSynchronize(st));
+    maxb &= 0xFFFFFFFFull;
+    if (maxb <= (unsigned long long)kBucketCap) {
+      // cursor: reuse the histogram buffer as the running offsets
+      HLC_CUDA(cudaMemcpyAsync(bhist, boff, (size_t)nbk * 4, cudaMemcpyDeviceToDevice, st));
+      unsigned g = grid_for(M, kThreads);
+      k_bucket_scatter<<<g, kThreads, 0, st>>>(ka, kb, sep, M, bshift, bmask, bhist, ta, tb, ts);
       HLC_LAUNCH_CHECK();
+      k_bucket_sort<<<std::min<uint32_t>(nbk, 148u * 32u), kBucketThreads, 0, st>>>(
+          ta, tb, ts, boff, nbk, ka, kb, sep, P->dev_err);
+      HLC_LAUNCH_CHECK();
+      done = true;
     }
+    ar.drop(scr);
+  }
+  if (!done) {
+    HLC_TRY(sort_rows_lsd(P, M, ka, kb, sep, ta, tb, ts));
+    oa = ta;
+    ob = tb;
+    os = ts;
   }
   ev_record(P, 6);
   HLC_CUDA(cudaStreamSynchronize(st));
   HLC_TRY(check_dev_err(P->dev_err, st, "hlc_match"));
   res->n = M;
-  res->id_a = kt;
-  res->id_b = id_b;
-  res->sep_arcsec = sep;
+  res->id_a = oa;
+  res->id_b = ob;
+  res->sep_arcsec = want_sep ? os : nullptr;
   res->job = nullptr;
   res->on_device = 1;
-  ar.drop(ka);
-  ar.drop(kb);
-  ar.drop(tk);
-  ar.drop(tv);
-  ar.drop(scr);
-  if (sep0) ar.drop(sep0);
   P->stats.pair_tests = h[C_TESTS];
   P->stats.band_candidates = fp32 ? h[C_BAND] : 0;
   P->stats.matches = M;
@@ -589,7 +699,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   P->stats.ms_recheck = ev_ms(P, 4, 5);
   P->stats.ms_output = ev_ms(P, 5, 6);
   P->stats.ms_total = ev_ms(P, 0, 1) + ev_ms(P, 2, 6);
-  P->stats.kernel_launches = g_launches.load() - P->launches0;
+  P->stats.kernel_launches = (g_launches.load() - launches_match0) + P->plan_launches;
   if (stats) *stats = P->stats;
   return HLC_OK;
 }
@@ -699,7 +809,10 @@ int hlc_ang2pix(const double* ra, const double* dec, uint64_t n, int order, int 
     set_error("cudaMallocAsync failed: %s", cudaGetErrorString(e));
     return HLC_ENOMEM;
   }
-  k_prep_keys<<<grid_for(n, kThreads), kThreads, 0, st>>>(ra, dec, n, order, pix, idx, err);
+  if (precision == HLC_FP32_GUARD)
+    k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(ra, dec, n, order, pix, idx, err);
+  else
+    k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(ra, dec, n, order, pix, idx, err);
   int rc = HLC_OK;
   if (cudaGetLastError() != cudaSuccess) {
     set_error("ang2pix launch failed");
@@ -773,8 +886,8 @@ int hlc_quad_cells(const double* ra, const double* dec, uint64_t n, double radiu
   int* err = nullptr;
   HLC_CUDA(cudaMallocAsync(&err, sizeof(int), st));
   cudaMemsetAsync(err, 0, sizeof(int), st);
-  k_quad_cells<<<grid_for(n, kThreads), kThreads, 0, st>>>(ra, dec, n, radius_arcsec / 3600.0,
-                                                            order, out, (uint32_t*)count, err);
+  k_quad_cells<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+      ra, dec, n, radius_arcsec / 3600.0, order, out, (uint32_t*)count, err);
   int rc = cudaGetLastError() == cudaSuccess ? HLC_OK : HLC_ECUDA;
   if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_quad_cells");
   cudaFreeAsync(err, st);

@@ -6,7 +6,9 @@
 
 #include "canon.cuh"
 #include "common.cuh"
+#include "fastpix.cuh"
 #include "fp32.cuh"
+#include "index.cuh"
 
 namespace hlc {
 
@@ -17,7 +19,9 @@ constexpr int kThreads = 256;
 // ---------------------------------------------------------------------------
 
 // Cell key and identity index of each source (complete mode), with input
-// validation (non-finite or |dec| > 90 sets DERR_INPUT).
+// validation (non-finite or |dec| > 90 sets DERR_INPUT).  FAST: guarded FP32
+// evaluation with binary64 fallback (same pixels).
+template <bool FAST>
 __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restrict__ dec,
                             uint64_t n, int order, uint32_t* __restrict__ key,
                             uint32_t* __restrict__ idx, int* __restrict__ err) {
@@ -28,13 +32,14 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
     if (!c_valid(a, d))
       atomicOr(err, DERR_INPUT);
     else
-      k = c_ang2pix(c_norm_ra(a), d, order);
+      k = FAST ? g_ang2pix(c_norm_ra(a), d, order) : c_ang2pix(c_norm_ra(a), d, order);
     key[i] = k;
     idx[i] = (uint32_t)i;
   }
 }
 
 // Quad-direction cells of each source (Algorithm 1): 5 slots + count.
+template <bool FAST>
 __global__ void k_quad_cells(const double* __restrict__ ra, const double* __restrict__ dec,
                              uint64_t n, double R, int order, uint32_t* __restrict__ cells,
                              uint32_t* __restrict__ count, int* __restrict__ err) {
@@ -47,7 +52,8 @@ __global__ void k_quad_cells(const double* __restrict__ ra, const double* __rest
       atomicOr(err, DERR_INPUT);
       c[0] = 0;
     } else {
-      m = c_quad_cells(c_norm_ra(a), d, R, order, c);
+      m = FAST ? g_quad_cells(c_norm_ra(a), d, R, order, c)
+               : c_quad_cells(c_norm_ra(a), d, R, order, c);
     }
 #pragma unroll
     for (int e = 0; e < 5; ++e) cells[5 * i + e] = e < m ? c[e] : 0xFFFFFFFFu;
@@ -101,10 +107,6 @@ __global__ void k_payload32(const double* __restrict__ ra, const double* __restr
   }
 }
 
-// ---------------------------------------------------------------------------
-// Candidates: for each non-empty A cell, the B ranges of its neighbourhood.
-// ---------------------------------------------------------------------------
-
 __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ a, uint32_t n,
                                                     uint32_t q) {
   uint32_t lo = 0, hi = n;
@@ -118,32 +120,12 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__
   return lo;
 }
 
-// complete: ranges of the cell and its distinct neighbours (<= 9 slots);
-// quad: the range of the same cell (1 slot).  Empty slots are (0, 0).
-__global__ void k_candidates(const uint32_t* __restrict__ uniqA, uint64_t uA,
-                             const uint32_t* __restrict__ uniqB, const uint32_t* __restrict__ startB,
-                             uint64_t uB, int order, int nslot, uint2* __restrict__ rng) {
-  for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < uA;
-       c += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t cell = uniqA[c];
-    uint32_t nb[9];
-    int m = 1;
-    nb[0] = cell;
-    if (nslot == 9) m = cell_neighbourhood(cell, order, nb);
-    for (int e = 0; e < nslot; ++e) {
-      uint2 r = make_uint2(0u, 0u);
-      if (e < m) {
-        uint32_t p = lower_bound_u32(uniqB, (uint32_t)uB, nb[e]);
-        if (p < uB && uniqB[p] == nb[e]) r = make_uint2(startB[p], startB[p + 1]);
-      }
-      rng[c * nslot + e] = r;
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
-// Pair test (one thread per A entry; warp-uniform loops so that match rows
-// are reserved with one atomic per warp from a ballot).
+// Candidates and pair test (one thread per A entry): the neighbourhood of the
+// entry's cell (complete mode) or the cell itself (quad mode) is looked up in
+// B's cell index and every B entry of those cells is tested.  Loops are
+// warp-uniform so that match rows are reserved with one atomic per warp from
+// a ballot.
 // ---------------------------------------------------------------------------
 
 struct PairSink {
@@ -192,21 +174,19 @@ __device__ __forceinline__ uint32_t quad_owner(const uint32_t* __restrict__ ca,
 
 template <bool FP32, bool QUAD>
 __global__ void __launch_bounds__(kThreads) k_pair(
-    uint64_t mA, const uint32_t* __restrict__ cell_of_a, const uint2* __restrict__ rng, int nslot,
+    uint64_t mA, const uint32_t* __restrict__ keyA, CellIndex bix, int order,
     const double* __restrict__ axv, const double* __restrict__ ayv, const double* __restrict__ azv,
     const double* __restrict__ bxv, const double* __restrict__ byv, const double* __restrict__ bzv,
     const float4* __restrict__ a32, const float4* __restrict__ b32, double C, float lo32,
-    float hi32, const uint32_t* __restrict__ uniqA, const uint32_t* __restrict__ idxA,
-    const uint32_t* __restrict__ idxB, const uint32_t* __restrict__ cellsA,
-    const uint32_t* __restrict__ cellsB, PairSink sink) {
-  const uint64_t k0 = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    float hi32, const uint32_t* __restrict__ idxA, const uint32_t* __restrict__ idxB,
+    const uint32_t* __restrict__ cellsA, const uint32_t* __restrict__ cellsB, PairSink sink) {
   const uint64_t stride = (uint64_t)gridDim.x * kThreads;
   unsigned long long ntest = 0, ndup = 0;
   // every thread of the warp runs the same number of outer iterations
   for (uint64_t kb0 = (uint64_t)blockIdx.x * kThreads; kb0 < mA; kb0 += stride) {
     uint64_t k = kb0 + (threadIdx.x);
     bool live = k < mA;
-    uint32_t c = live ? cell_of_a[k] : 0u;
+    uint32_t cell = live ? keyA[k] : 0u;
     double ax = 0, ay = 0, az = 0;
     float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (live) {
@@ -216,8 +196,20 @@ __global__ void __launch_bounds__(kThreads) k_pair(
         ax = axv[k]; ay = ayv[k]; az = azv[k];
       }
     }
+    // neighbourhood of the A cell (complete) or the cell itself (quad)
+    uint32_t nb[9];
+    int m = 0;
+    if (live) {
+      if (QUAD) {
+        nb[0] = cell;
+        m = 1;
+      } else {
+        m = cell_neighbourhood(cell, order, nb);
+      }
+    }
+    const int nslot = QUAD ? 1 : 9;
     for (int s = 0; s < nslot; ++s) {
-      uint2 r = live ? rng[(uint64_t)c * nslot + s] : make_uint2(0u, 0u);
+      uint2 r = s < m ? cell_range(bix, nb[s]) : make_uint2(0u, 0u);
       uint32_t len = r.y - r.x;
       ntest += len;
       uint32_t maxlen = __reduce_max_sync(0xffffffffu, len);
@@ -240,7 +232,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(
           }
           if (QUAD && (hit || band)) {
             uint32_t own = quad_owner(cellsA + 5ull * idxA[k], cellsB + 5ull * idxB[j]);
-            if (own != uniqA[c]) {
+            if (own != cell) {
               if (hit) ++ndup;
               hit = false;
               band = false;
@@ -252,7 +244,6 @@ __global__ void __launch_bounds__(kThreads) k_pair(
       }
     }
   }
-  (void)k0;
   // one atomic per warp for the counters
   for (int o = 16; o > 0; o >>= 1) {
     ntest += __shfl_down_sync(0xffffffffu, ntest, o);
@@ -287,48 +278,6 @@ __global__ void __launch_bounds__(kThreads) k_recheck(
       hit = c_chord2(ax, ay, az, bx, by, bz) <= C;
     }
     warp_emit(hit, p.x, p.y, rows, count, cap, err);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Output rows: ids and separations of each matched (A entry, B entry).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double sep_arcsec_from_chord2(double s) {
-  double h = sqrt(s) * 0.5;
-  if (h > 1.0) h = 1.0;
-  return 2.0 * asin(h) * (648000.0 / 3.141592653589793238462643);
-}
-
-template <bool FP32>
-__global__ void k_rows(const uint2* __restrict__ rows, uint64_t M,
-                       const uint32_t* __restrict__ idxA, const uint32_t* __restrict__ idxB,
-                       const uint64_t* __restrict__ idA, const uint64_t* __restrict__ idB,
-                       const double* __restrict__ axv, const double* __restrict__ ayv,
-                       const double* __restrict__ azv, const double* __restrict__ bxv,
-                       const double* __restrict__ byv, const double* __restrict__ bzv,
-                       const double* __restrict__ raA, const double* __restrict__ decA,
-                       const double* __restrict__ raB, const double* __restrict__ decB,
-                       int want_sep, uint64_t* __restrict__ ka, uint64_t* __restrict__ kb,
-                       double* __restrict__ sep, uint32_t* __restrict__ perm) {
-  for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
-       m += (uint64_t)gridDim.x * blockDim.x) {
-    uint2 p = rows[m];
-    uint32_t ia = idxA[p.x], ib = idxB[p.y];
-    ka[m] = idA[ia];
-    kb[m] = idB[ib];
-    perm[m] = (uint32_t)m;
-    if (want_sep) {
-      double s2;
-      if (FP32) {
-        double ax, ay, az, bx, by, bz;
-        c_unitvec(c_norm_ra(raA[ia]), decA[ia], &ax, &ay, &az);
-        c_unitvec(c_norm_ra(raB[ib]), decB[ib], &bx, &by, &bz);
-        s2 = c_chord2(ax, ay, az, bx, by, bz);
-      } else {
-        s2 = c_chord2(axv[p.x], ayv[p.x], azv[p.x], bxv[p.y], byv[p.y], bzv[p.y]);
-      }
-      sep[m] = sep_arcsec_from_chord2(s2);
-    }
   }
 }
 

@@ -1,0 +1,178 @@
+// Output rows of the match: ids and separations of each matched pair, then
+// the rows in ascending (id_a, id_b) order.
+//
+// Ordering: the rows are distributed into 2^b buckets by the b bits of id_a
+// just below its highest varying bit (a counting scatter), and every bucket,
+// a few dozen rows on average, is sorted in shared memory by a bitonic
+// network on (id_a, id_b, separation bits).  When a bucket would not fit in
+// shared memory (strongly clustered ids) the caller falls back to two stable
+// LSD radix sorts (by id_b, then by id_a).
+#pragma once
+
+#include "canon.cuh"
+#include "common.cuh"
+
+namespace hlc {
+
+constexpr int kBucketCap = 2048;
+constexpr int kBucketThreads = 128;
+
+__device__ __forceinline__ double sep_arcsec_from_chord2(double s) {
+  double h = sqrt(s) * 0.5;
+  if (h > 1.0) h = 1.0;
+  return 2.0 * asin(h) * (648000.0 / 3.141592653589793238462643);
+}
+
+// Separation from the original coordinates by the haversine form
+// hav(d) = sin^2(dDec/2) + cos(Dec_a) cos(Dec_b) sin^2(dRA/2), with
+// cos(Dec_a) cos(Dec_b) = cos^2(mean Dec) - sin^2(dDec/2): one binary64
+// cosine per row; short series for the small angles.  Rows whose RA or Dec
+// difference exceeds 1 degree (near the poles) use the unit vectors.
+__device__ __forceinline__ double sep_arcsec_haversine(double ra1, double dec1, double ra2,
+                                                       double dec2) {
+  double dd = dec2 - dec1;
+  double da = ra2 - ra1;
+  if (da > 180.0) da -= 360.0;
+  if (da < -180.0) da += 360.0;
+  if (fabs(da) > 1.0 || fabs(dd) > 1.0) {
+    double ax, ay, az, bx, by, bz;
+    c_unitvec(ra1, dec1, &ax, &ay, &az);
+    c_unitvec(ra2, dec2, &bx, &by, &bz);
+    return sep_arcsec_from_chord2(c_chord2(ax, ay, az, bx, by, bz));
+  }
+  double sm, cm;
+  c_sincos_deg(0.5 * (dec1 + dec2), &sm, &cm);
+  const double half_rad = 3.141592653589793238462643 / 360.0;
+  double x = dd * half_rad, y = da * half_rad;
+  double x2 = x * x, y2 = y * y;
+  double sx = x * (1.0 - x2 * (1.0 / 6.0 - x2 * (1.0 / 120.0)));
+  double sy = y * (1.0 - y2 * (1.0 / 6.0 - y2 * (1.0 / 120.0)));
+  double K = cm * cm - sx * sx;
+  double hav = fma(K, sy * sy, sx * sx);
+  double v = sqrt(hav);
+  double v2 = v * v;
+  double as = v * (1.0 + v2 * (1.0 / 6.0 + v2 * (3.0 / 40.0)));
+  return 2.0 * as * (648000.0 / 3.141592653589793238462643);
+}
+
+// ids + separation of each row, and the bucket histogram of id_a.
+template <bool FP32>
+__global__ void k_rows(const uint2* __restrict__ rows, uint64_t M,
+                       const uint32_t* __restrict__ idxA, const uint32_t* __restrict__ idxB,
+                       const uint64_t* __restrict__ idA, const uint64_t* __restrict__ idB,
+                       const double* __restrict__ axv, const double* __restrict__ ayv,
+                       const double* __restrict__ azv, const double* __restrict__ bxv,
+                       const double* __restrict__ byv, const double* __restrict__ bzv,
+                       const double* __restrict__ raA, const double* __restrict__ decA,
+                       const double* __restrict__ raB, const double* __restrict__ decB,
+                       int want_sep, uint64_t* __restrict__ ka, uint64_t* __restrict__ kb,
+                       double* __restrict__ sep, int bshift, uint32_t bmask,
+                       uint32_t* __restrict__ bhist) {
+  for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
+       m += (uint64_t)gridDim.x * blockDim.x) {
+    uint2 p = rows[m];
+    uint32_t ia = idxA[p.x], ib = idxB[p.y];
+    uint64_t a = idA[ia];
+    ka[m] = a;
+    kb[m] = idB[ib];
+    if (bhist) atomicAdd(&bhist[(uint32_t)(a >> bshift) & bmask], 1u);
+    if (want_sep) {
+      double sv;
+      if (FP32)
+        sv = sep_arcsec_haversine(c_norm_ra(raA[ia]), decA[ia], c_norm_ra(raB[ib]), decB[ib]);
+      else
+        sv = sep_arcsec_from_chord2(
+            c_chord2(axv[p.x], ayv[p.x], azv[p.x], bxv[p.y], byv[p.y], bzv[p.y]));
+      sep[m] = sv;
+    }
+  }
+}
+
+__global__ void k_max_u32(const uint32_t* __restrict__ v, uint64_t n, uint32_t* __restrict__ out) {
+  uint32_t m = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    m = max(m, v[i]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+__global__ void k_bucket_scatter(const uint64_t* __restrict__ ka, const uint64_t* __restrict__ kb,
+                                 const double* __restrict__ sep, uint64_t M, int bshift,
+                                 uint32_t bmask, uint32_t* __restrict__ cursor,
+                                 uint64_t* __restrict__ ta, uint64_t* __restrict__ tb,
+                                 double* __restrict__ ts) {
+  for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
+       m += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t a = ka[m];
+    uint32_t pos = atomicAdd(&cursor[(uint32_t)(a >> bshift) & bmask], 1u);
+    ta[pos] = a;
+    tb[pos] = kb[m];
+    if (sep) ts[pos] = sep[m];
+  }
+}
+
+__device__ __forceinline__ bool row_less(uint64_t a1, uint64_t b1, uint64_t s1, uint64_t a2,
+                                         uint64_t b2, uint64_t s2) {
+  if (a1 != a2) return a1 < a2;
+  if (b1 != b2) return b1 < b2;
+  return s1 < s2;
+}
+
+// One CTA per bucket: bitonic sort of <= kBucketCap rows in shared memory.
+__global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(
+    const uint64_t* __restrict__ ta, const uint64_t* __restrict__ tb,
+    const double* __restrict__ ts, const uint32_t* __restrict__ boff, uint32_t nbuckets,
+    uint64_t* __restrict__ oa, uint64_t* __restrict__ ob, double* __restrict__ os,
+    int* __restrict__ err) {
+  __shared__ uint64_t A[kBucketCap], B[kBucketCap], S[kBucketCap];
+  for (uint32_t bk = blockIdx.x; bk < nbuckets; bk += gridDim.x) {
+    uint32_t lo = boff[bk], hi = boff[bk + 1];
+    uint32_t n = hi - lo;
+    if (n == 0) continue;
+    if (n > kBucketCap) {  // the host checked; never taken
+      if (threadIdx.x == 0) atomicOr(err, DERR_BOUNDS);
+      continue;
+    }
+    uint32_t np = 1;
+    while (np < n) np <<= 1;
+    for (uint32_t i = threadIdx.x; i < np; i += kBucketThreads) {
+      if (i < n) {
+        A[i] = ta[lo + i];
+        B[i] = tb[lo + i];
+        S[i] = ts ? (uint64_t)__double_as_longlong(ts[lo + i]) : 0ull;
+      } else {
+        A[i] = ~0ull;
+        B[i] = ~0ull;
+        S[i] = ~0ull;
+      }
+    }
+    __syncthreads();
+    for (uint32_t k = 2; k <= np; k <<= 1) {
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        for (uint32_t i = threadIdx.x; i < np; i += kBucketThreads) {
+          uint32_t l = i ^ j;
+          if (l > i) {
+            bool up = (i & k) == 0;
+            bool gt = row_less(A[l], B[l], S[l], A[i], B[i], S[i]);
+            if (gt == up) {
+              uint64_t t;
+              t = A[i]; A[i] = A[l]; A[l] = t;
+              t = B[i]; B[i] = B[l]; B[l] = t;
+              t = S[i]; S[i] = S[l]; S[l] = t;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (uint32_t i = threadIdx.x; i < n; i += kBucketThreads) {
+      oa[lo + i] = A[i];
+      ob[lo + i] = B[i];
+      if (os) os[lo + i] = __longlong_as_double((long long)S[i]);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace hlc

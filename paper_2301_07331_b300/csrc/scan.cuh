@@ -57,8 +57,9 @@ struct ScanSmem {
 };
 
 // out[i] = sum_{k<i} in[i]; *total = sum of all.
+template <typename OutT>
 __global__ void __launch_bounds__(kBlock) k_scan_excl(const uint32_t* __restrict__ in,
-                                                      uint64_t* __restrict__ out, uint64_t n,
+                                                      OutT* __restrict__ out, uint64_t n,
                                                       unsigned long long* lb, uint32_t* ctr,
                                                       unsigned long long* total, int* err) {
   __shared__ ScanSmem S;
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(kBlock) k_scan_excl(const uint32_t* __restrict
   unsigned long long run = S.base + pre;
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
-    if (e0 + i < n) out[e0 + i] = run;
+    if (e0 + i < n) out[e0 + i] = (OutT)run;
     run += v[i];
   }
   if (e0 < n && e0 + kIpt >= n) *total = run;  // the thread holding element n-1
@@ -148,9 +149,10 @@ inline size_t scan_scratch_bytes(uint64_t n) {
   return 256 + (tiles + 1) * 8;
 }
 
-// Exclusive scan of n uint32 values into uint64 offsets; *total_dev receives
-// the sum (device).  scratch: scan_scratch_bytes(n) bytes.
-inline int scan_exclusive(const uint32_t* in, uint64_t* out, uint64_t n,
+// Exclusive scan of n uint32 values into uint64 (or uint32) offsets;
+// *total_dev receives the sum (device).  scratch: scan_scratch_bytes(n) bytes.
+template <typename OutT>
+inline int scan_exclusive(const uint32_t* in, OutT* out, uint64_t n,
                           unsigned long long* total_dev, void* scratch, int* dev_err,
                           cudaStream_t st) {
   if (n == 0) {
@@ -161,7 +163,8 @@ inline int scan_exclusive(const uint32_t* in, uint64_t* out, uint64_t n,
   uint32_t* ctr = (uint32_t*)scratch;
   unsigned long long* lb = (unsigned long long*)((char*)scratch + 256);
   HLC_CUDA(cudaMemsetAsync(scratch, 0, scan_scratch_bytes(n), st));
-  sc::k_scan_excl<<<(unsigned)tiles, sc::kBlock, 0, st>>>(in, out, n, lb, ctr, total_dev, dev_err);
+  sc::k_scan_excl<OutT><<<(unsigned)tiles, sc::kBlock, 0, st>>>(in, out, n, lb, ctr, total_dev,
+                                                                dev_err);
   HLC_LAUNCH_CHECK();
   return HLC_OK;
 }

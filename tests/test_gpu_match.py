@@ -116,6 +116,12 @@ def test_pairs_a_hair_from_the_radius(prec):
 
 
 @pytest.mark.parametrize("prec", [hlc.HLC_FP64, hlc.HLC_FP32_GUARD])
+def test_torch_allocator_callback(prec):
+    A, B = synth.patch_pair(na=8000, nb=8000)
+    _check(A.numpy(), B.numpy(), 1.0, 13, hlc.HLC_COMPLETE8, prec, torch_alloc=True)
+
+
+@pytest.mark.parametrize("prec", [hlc.HLC_FP64, hlc.HLC_FP32_GUARD])
 def test_self_match_and_host_inputs(prec):
     A, _ = synth.patch_pair(na=5000, nb=10)
     X = A.numpy()
@@ -167,3 +173,21 @@ def test_duplicate_ids_and_unsorted_ra():
     for k in set(key[:500]):
         m = key == k
         np.testing.assert_allclose(np.sort(sep[m]), np.sort(want["sep"][m]), atol=SEP_TOL, rtol=0)
+
+
+@pytest.mark.parametrize("prec", [hlc.HLC_FP64, hlc.HLC_FP32_GUARD])
+def test_output_order_fallbacks(prec):
+    """Row ordering when the id buckets do not apply: one A source matched by
+    3000 B sources (a bucket larger than shared memory), and all A ids equal."""
+    rng = np.random.default_rng(5)
+    nb = 3000
+    ra_b = 10.0 + rng.uniform(-1, 1, nb) * 0.3 / 3600
+    dec_b = 20.0 + rng.uniform(-1, 1, nb) * 0.3 / 3600
+    idb = rng.integers(0, 2 ** 63, nb).astype(np.uint64)
+    ra_a = np.concatenate([[10.0], rng.uniform(0, 360, 2000)])
+    dec_a = np.concatenate([[20.0], rng.uniform(-60, 60, 2000)])
+    ida = rng.integers(0, 2 ** 63, ra_a.size).astype(np.uint64)
+    want, st = _check((ra_a, dec_a, ida), (ra_b, dec_b, idb), 1.0, 12, hlc.HLC_COMPLETE8, prec)
+    assert want["id_a"].size >= nb
+    same = np.full(ra_a.size, 12345, dtype=np.uint64)
+    _check((ra_a, dec_a, same), (ra_b, dec_b, idb), 1.0, 12, hlc.HLC_COMPLETE8, prec)
