@@ -2,11 +2,14 @@
 //
 // Every discrete decision of the binary64 ang2pix (zone |z| <= 2/3, the two
 // floor()s that give the edge-line indices, floor(tt) in the caps) is taken
-// from an FP32/FP64-mixed estimate whose distance to the canonical operand is
-// bounded; when the estimate lies farther than that bound from the decision
-// threshold the decision equals the canonical one, otherwise the source falls
-// back to the binary64 path.  The pixel is therefore always the canonical
-// pixel; only about 2e-7 * 2^order of the sources take the slow path.
+// from an FP32 / float-float estimate whose distance to the canonical operand
+// is bounded; when the estimate lies farther than that bound from the
+// decision threshold the decision equals the canonical one, otherwise the
+// source falls back to the binary64 path.  The pixel is therefore always the
+// canonical pixel.  The fast path issues no FP64 instruction (the double
+// inputs are split into float pairs with integer operations): on B300 the
+// FP64 pipe runs at a small fraction of the FP32 rate.  About 8e-7 * 2^order
+// of the sources take the slow path.
 #pragma once
 
 #include "canon.cuh"
@@ -21,57 +24,86 @@ struct FastDec {
   bool ok;    // zone decided with certainty
 };
 
-__device__ __forceinline__ FastDec f_dec_part(double dec) {
+__device__ __forceinline__ FastDec f_dec_part(f2 dec) {
   FastDec d;
-  d.z = fp32_sin_deg(dec);
+  float c_unused;
+  fp32_sincos_deg2(dec.hi, dec.lo, &d.z, &c_unused);
   float za = fabsf(d.z);
   d.ok = fabsf(za - 0.666666667f) > kSinErr + 1e-7f;
   d.polar = za > 0.666666667f;
   d.cap = 0.f;
   if (d.polar) {
-    double w = 90.0 - fabs(dec);
-    d.cap = 2.44948974f * fp32_sin_deg(0.5 * w);
+    // (90 - |dec|) / 2 as a float pair; 90 - |hi| is exact or within 2^-24
+    float ah = fabsf(dec.hi), al = dec.hi < 0.f ? -dec.lo : dec.lo;
+    f2 w = two_sum(90.0f, -ah);
+    w.lo -= al;
+    float sw, cw;
+    fp32_sincos_deg2(0.5f * w.hi, 0.5f * w.lo, &sw, &cw);
+    d.cap = 2.44948974f * sw;
   }
   return d;
 }
 
-// Floor of v when v is farther than e from an integer; false otherwise.
-__device__ __forceinline__ bool sure_floor(double v, float e, int* out) {
-  double f = floor(v);
-  float r = (float)(v - f);
+// floor(v) as an int when v lies farther than e from an integer.
+__device__ __forceinline__ bool sure_floorf(float v, float e, int* out) {
+  float f = floorf(v);
+  float r = v - f;
   *out = (int)f;
   return r > e && r < 1.0f - e;
 }
 
-// Canonical pixel of (ra, dec), ra in [0, 360), if the FP32 estimate decides
-// it with certainty; false when the caller must use the binary64 path.
-__device__ __forceinline__ bool f_pix(double ra, const FastDec& d, int order, uint32_t* out) {
+struct PixConst {
+  float kh, kl;  // 2^order / 90 as a float pair
+  float inv90h, inv90l;
+};
+
+__host__ __device__ inline PixConst pix_const(int order) {
+  PixConst c;
+  double k = (double)(1u << order) / 90.0;
+  c.kh = (float)k;
+  c.kl = (float)(k - (double)c.kh);
+  c.inv90h = (float)(1.0 / 90.0);
+  c.inv90l = (float)(1.0 / 90.0 - (double)c.inv90h);
+  return c;
+}
+
+// Canonical pixel of (ra, dec), ra in [0, 360) given as a float pair, if the
+// estimate decides it with certainty; false when the caller must use the
+// binary64 path.
+__device__ __forceinline__ bool f_pix(f2 ra, const FastDec& d, int order, const PixConst& K,
+                                      uint32_t* out) {
   if (!d.ok) return false;
-  const double ns = (double)(1u << order);
+  const float ns = (float)(1u << order);
   const int nsi = 1 << order;
   int face, ix, iy;
   if (!d.polar) {
-    double t1 = fma(ra, ns * (1.0 / 90.0), 0.5 * ns);
-    double t2 = (double)((float)ns * 0.75f * d.z);
-    const float e = (float)(ns * 2e-7) + 1e-9f;
-    int jp, jm;
-    if (!sure_floor(t1 - t2, e, &jp)) return false;
-    if (!sure_floor(t1 + t2, e, &jm)) return false;
+    // ns (0.5 + ra/90) -/+ ns 0.75 z, split into integer and fraction
+    f2 t = f2_mul(ra, f2{K.kh, K.kl});
+    float ih = floorf(t.hi);
+    float a = (t.hi - ih) + t.lo;  // fraction of ns ra / 90
+    float t2 = ns * 0.75f * d.z;
+    const float e = ns * 4e-7f + 4e-7f;
+    int f1, f2i;
+    if (!sure_floorf(a + (0.5f * ns - t2), e, &f1)) return false;
+    if (!sure_floorf(a + (0.5f * ns + t2), e, &f2i)) return false;
+    int jp = (int)ih + f1, jm = (int)ih + f2i;
     int ifp = jp >> order, ifm = jm >> order;
     face = (ifp == ifm) ? (ifp | 4) : (ifp < ifm ? ifp : ifm + 8);
     ix = jm & (nsi - 1);
     iy = nsi - (jp & (nsi - 1)) - 1;
   } else {
-    double tt = ra * (1.0 / 90.0);
-    int ntt;
-    if (!sure_floor(tt, 1e-9f, &ntt)) return false;
+    f2 tt = f2_mul(ra, f2{K.inv90h, K.inv90l});
+    float fh = floorf(tt.hi);
+    float fr = (tt.hi - fh) + tt.lo;
+    if (!(fr > 1e-6f && fr < 1.0f - 1e-6f)) return false;
+    int ntt = (int)fh;
     if (ntt >= 4) ntt = 3;
-    double tp = tt - (double)ntt;
-    double tmp = (double)((float)ns * d.cap);
-    const float e = (float)(ns * 2.5e-7) + 1e-9f;
+    float tp = fr + (fh - (float)ntt);
+    float tmp = ns * d.cap;
+    const float e = ns * 6e-7f + 4e-7f;
     int jp, jm;
-    if (!sure_floor(tp * tmp, e, &jp)) return false;
-    if (!sure_floor((1.0 - tp) * tmp, e, &jm)) return false;
+    if (!sure_floorf(tp * tmp, e, &jp)) return false;
+    if (!sure_floorf((1.0f - tp) * tmp, e, &jm)) return false;
     jp = min(jp, nsi - 1);
     jm = min(jm, nsi - 1);
     if (d.z > 0.f) {
@@ -88,28 +120,31 @@ __device__ __forceinline__ bool f_pix(double ra, const FastDec& d, int order, ui
   return true;
 }
 
-__device__ __forceinline__ uint32_t g_ang2pix(double ra, double dec, int order) {
+// ra already normalised to [0, 360).
+__device__ __forceinline__ uint32_t g_ang2pix(double ra, double dec, int order,
+                                              const PixConst& K) {
   uint32_t p;
-  FastDec fd = f_dec_part(dec);
-  if (f_pix(ra, fd, order, &p)) return p;
+  FastDec fd = f_dec_part(split_f64(dec));
+  if (f_pix(split_f64(ra), fd, order, K, &p)) return p;
   return c_ang2pix(ra, dec, order);
 }
 
-// Quad-direction cells (Algorithm 1) through the guarded pixel function.
+// Quad-direction cells (Algorithm 1) through the guarded pixel function.  The
+// shifted coordinates are formed exactly as in the binary64 statement.
 __device__ __forceinline__ int g_quad_cells(double ra, double dec, double R, int order,
-                                            uint32_t out[5]) {
-  double dp_ = dec + R;
+                                            const PixConst& K, uint32_t out[5]) {
+  double dp_ = __dadd_rn(dec, R);
   if (dp_ > 90.0) dp_ = 90.0;
-  double dm_ = dec - R;
+  double dm_ = __dsub_rn(dec, R);
   if (dm_ < -90.0) dm_ = -90.0;
-  FastDec f0 = f_dec_part(dec);
+  FastDec f0 = f_dec_part(split_f64(dec));
   uint32_t p[5];
   double ras[3] = {ra, wrap_ra(__dadd_rn(ra, R)), wrap_ra(__dsub_rn(ra, R))};
   bool have_c0 = false;
   DecPart c0;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    if (!f_pix(ras[i], f0, order, &p[i])) {
+    if (!f_pix(split_f64(ras[i]), f0, order, K, &p[i])) {
       if (!have_c0) {
         c0 = c_dec_part(dec);
         have_c0 = true;
@@ -117,8 +152,8 @@ __device__ __forceinline__ int g_quad_cells(double ra, double dec, double R, int
       p[i] = c_pix(ras[i], c0, order);
     }
   }
-  p[3] = g_ang2pix(ra, dm_, order);
-  p[4] = g_ang2pix(ra, dp_, order);
+  p[3] = g_ang2pix(ra, dm_, order, K);
+  p[4] = g_ang2pix(ra, dp_, order, K);
 #pragma unroll
   for (int i = 1; i < 5; ++i) {
     uint32_t v = p[i];

@@ -22,6 +22,76 @@ constexpr double kUnitVecErr = 1.6e-7;
 // Bound on |sin(dec) - fp32 sine| used by the guarded ang2pix.
 constexpr float kSinErr = 1.2e-7f;
 
+// ---- float-float helpers (error-free transformations on the FP32 pipe) ----
+struct f2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ f2 two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+__device__ __forceinline__ f2 fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ f2 f2_mulf(f2 a, float b) {
+  float p = a.hi * b;
+  float e = fmaf(a.hi, b, -p);
+  e = fmaf(a.lo, b, e);
+  return fast_two_sum(p, e);
+}
+
+// x = hi + lo exactly up to 2^-53 |x| (lo rounded), with integer operations
+// only: hi keeps the top 24 significand bits, lo the next 29 (rounded to 24).
+// |x| < 2^-70 (and 0) gives (0, 0); x must be finite.
+__device__ __forceinline__ f2 split_f64(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  int e = (int)((b >> 52) & 0x7FFu) - 1023;
+  if (e < -70) return {0.f, 0.f};
+  unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;  // 53 bits
+  unsigned mh = (unsigned)(m >> 29);                                      // 24 bits
+  unsigned ml = (unsigned)(m & 0x1FFFFFFFu);                              // 29 bits
+  float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (mh & 0x7FFFFFu));
+  float lo = 0.f;
+  if (ml) {
+    int lz = __clz(ml);        // >= 3
+    int top = 31 - lz;         // position of the leading one
+    unsigned mant = top > 23 ? (ml >> (top - 23)) : (ml << (23 - top));
+    int ex = e - 52 + top;     // exponent of the leading one
+    lo = __uint_as_float(sign | ((unsigned)(ex + 127) << 23) | (mant & 0x7FFFFFu));
+  }
+  return {hi, lo};
+}
+
+// Bit-level checks on binary64 values (no FP64 instructions).
+__device__ __forceinline__ bool bits_finite(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7FF0000000000000ull) !=
+         0x7FF0000000000000ull;
+}
+__device__ __forceinline__ bool bits_abs_le(double x, double lim) {  // |x| <= lim (finite)
+  return ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) <=
+         (unsigned long long)__double_as_longlong(lim);
+}
+__device__ __forceinline__ bool bits_in_ra_range(double x) {  // 0 <= x < 360 (or -0)
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return b < 0x4076800000000000ull || b == 0x8000000000000000ull;  // 360.0 = 0x4076800000000000
+}
+
 __device__ __forceinline__ void fp32_sincos_reduced(float p, float e, float* s, float* c) {
   // p + e radians, |p| <= pi/4 + tiny, |e| <= 2^-24 |p|
   float p2 = p * p;
@@ -38,12 +108,10 @@ __device__ __forceinline__ void fp32_sincos_reduced(float p, float e, float* s, 
   *c = fmaf(-sn, e, cs);
 }
 
-// sin and cos of x degrees (|x| < 1e4), fp32 results.
-__device__ __forceinline__ void fp32_sincos_deg(double x, float* s, float* c) {
-  float xh = (float)x;
-  float xl = (float)(x - (double)xh);          // exact split: x = xh + xl (+ <1e-22)
+// sin and cos of (xh + xl) degrees, |x| < 1e4, fp32 results.
+__device__ __forceinline__ void fp32_sincos_deg2(float xh, float xl, float* s, float* c) {
   float q = rintf(xh * (1.0f / 90.0f));
-  float th = fmaf(-90.0f, q, xh);              // exact
+  float th = fmaf(-90.0f, q, xh);              // exact (Sterbenz)
   // radians as a float-float pair: (th + xl) * (R_hi + R_lo)
   const float R_hi = 1.745329238e-2f;          // float nearest pi/180
   const float R_lo = 1.351996015e-10f;         // pi/180 - R_hi
@@ -67,6 +135,11 @@ __device__ __forceinline__ void fp32_sincos_deg(double x, float* s, float* c) {
   }
 }
 
+__device__ __forceinline__ void fp32_sincos_deg(double x, float* s, float* c) {
+  f2 v = split_f64(x);
+  fp32_sincos_deg2(v.hi, v.lo, s, c);
+}
+
 __device__ __forceinline__ float fp32_sin_deg(double x) {
   float s, c;
   fp32_sincos_deg(x, &s, &c);
@@ -78,6 +151,41 @@ __device__ __forceinline__ float4 fp32_unitvec(double ra, double dec) {
   fp32_sincos_deg(dec, &sd, &cd);
   fp32_sincos_deg(ra, &sa, &ca);
   return make_float4(cd * ca, cd * sa, sd, 0.0f);
+}
+
+// sin and cos of a reduced float-float angle p (radians, |p| <= pi/4 + tiny)
+// to about 2e-8 relative: the leading Taylor terms are summed in float-float,
+// only the small tail is evaluated in float.
+__device__ __forceinline__ void f2_sincos_reduced(f2 p, f2* s, f2* c) {
+  float x = p.hi;
+  float x2 = x * x;
+  float ts = fmaf(x2, 2.75573192e-6f, -1.98412698e-4f);
+  ts = fmaf(x2, ts, 8.33333333e-3f);
+  ts = fmaf(x2, ts, -1.66666667e-1f);
+  float tail_s = x * x2 * ts;                       // sin - x
+  *s = f2_add(p, f2{tail_s, 0.f});
+  f2 h = f2_mul(p, p);                              // p^2 in float-float
+  float tc = fmaf(x2, -2.75573192e-7f, 2.48015873e-5f);
+  tc = fmaf(x2, tc, -1.38888889e-3f);
+  tc = fmaf(x2, tc, 4.16666667e-2f);
+  float tail_c = x2 * x2 * tc;                      // cos - 1 + p^2/2
+  f2 c0 = f2_add(f2{1.0f, 0.f}, f2{-0.5f * h.hi, -0.5f * h.lo});
+  *c = f2_add(c0, f2{tail_c, 0.f});
+}
+
+// cos of an angle given as a float-float number of degrees, |x| <= 90,
+// to about 3e-8 relative (evaluated as sin(90 - |x|)).
+__device__ __forceinline__ f2 f2_cos_deg(f2 x) {
+  float ah = fabsf(x.hi), al = x.hi < 0.f ? -x.lo : x.lo;
+  f2 w = two_sum(90.0f, -ah);  // 90 - |x| in degrees
+  w = fast_two_sum(w.hi, w.lo - al);
+  bool big = w.hi > 45.0f;
+  if (big) w = fast_two_sum(w.hi - 90.0f, w.lo);  // exact (Sterbenz)
+  const f2 R = {1.745329238e-2f, 1.351996015e-10f};
+  f2 p = f2_mul(w, R);
+  f2 sn, cs;
+  f2_sincos_reduced(p, &sn, &cs);
+  return big ? cs : sn;
 }
 
 // Guard band for an FP32 squared chord computed from such vectors as

@@ -310,10 +310,10 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     HLC_ALLOC(ar, X.idx, uint32_t, n + 1);
     if (n) {
       if (fp32)
-        k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(X.ra, X.dec, n, L, X.key,
+        k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(X.ra, X.dec, n, L, pix_const(L), X.key,
                                                                       X.idx, P->dev_err);
       else
-        k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(X.ra, X.dec, n, L, X.key,
+        k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(X.ra, X.dec, n, L, pix_const(L), X.key,
                                                                        X.idx, P->dev_err);
       HLC_LAUNCH_CHECK();
     }
@@ -326,10 +326,10 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     if (n) {
       if (fp32)
         k_quad_cells<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            X.ra, X.dec, n, P->p.radius_arcsec / 3600.0, L, X.cells5, cnt, P->dev_err);
+            X.ra, X.dec, n, P->p.radius_arcsec / 3600.0, L, pix_const(L), X.cells5, cnt, P->dev_err);
       else
         k_quad_cells<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            X.ra, X.dec, n, P->p.radius_arcsec / 3600.0, L, X.cells5, cnt, P->dev_err);
+            X.ra, X.dec, n, P->p.radius_arcsec / 3600.0, L, pix_const(L), X.cells5, cnt, P->dev_err);
       HLC_LAUNCH_CHECK();
     }
     HLC_TRY(scan_exclusive<uint64_t>(cnt, off, n, P->ctr + C_TOTAL, scr, P->dev_err, st));
@@ -618,7 +618,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   if (!ka || !kb || !ta || !tb || (want_sep && (!sep || !ts))) return HLC_ENOMEM;
   int hb = P->id_high_bit;
   int nbits = 1;
-  while (nbits < 22 && (M >> (nbits + 6)) > 0) ++nbits;  // about 64 rows per bucket
+  while (nbits < 24 && (M >> (nbits + 1)) > 0) ++nbits;  // about two rows per bucket
   if (hb >= 0 && nbits > hb + 1) nbits = hb + 1;
   const bool bucketed = M > 1 && hb >= 0;
   const int bshift = bucketed ? hb + 1 - nbits : 0;
@@ -668,9 +668,14 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
       unsigned g = grid_for(M, kThreads);
       k_bucket_scatter<<<g, kThreads, 0, st>>>(ka, kb, sep, M, bshift, bmask, bhist, ta, tb, ts);
       HLC_LAUNCH_CHECK();
-      k_bucket_sort<<<std::min<uint32_t>(nbk, 148u * 32u), kBucketThreads, 0, st>>>(
-          ta, tb, ts, boff, nbk, ka, kb, sep, P->dev_err);
+      k_bucket_small<<<grid_for(nbk, kThreads), kThreads, 0, st>>>(ta, tb, ts, boff, nbk, ka, kb,
+                                                                    sep);
       HLC_LAUNCH_CHECK();
+      if (maxb > kSmallBucket) {
+        k_bucket_sort<<<std::min<uint32_t>(nbk, 148u * 32u), kBucketThreads, 0, st>>>(
+            ta, tb, ts, boff, nbk, ka, kb, sep, P->dev_err);
+        HLC_LAUNCH_CHECK();
+      }
       done = true;
     }
     ar.drop(scr);
@@ -810,9 +815,9 @@ int hlc_ang2pix(const double* ra, const double* dec, uint64_t n, int order, int 
     return HLC_ENOMEM;
   }
   if (precision == HLC_FP32_GUARD)
-    k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(ra, dec, n, order, pix, idx, err);
+    k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(ra, dec, n, order, pix_const(order), pix, idx, err);
   else
-    k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(ra, dec, n, order, pix, idx, err);
+    k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(ra, dec, n, order, pix_const(order), pix, idx, err);
   int rc = HLC_OK;
   if (cudaGetLastError() != cudaSuccess) {
     set_error("ang2pix launch failed");
@@ -887,7 +892,7 @@ int hlc_quad_cells(const double* ra, const double* dec, uint64_t n, double radiu
   HLC_CUDA(cudaMallocAsync(&err, sizeof(int), st));
   cudaMemsetAsync(err, 0, sizeof(int), st);
   k_quad_cells<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-      ra, dec, n, radius_arcsec / 3600.0, order, out, (uint32_t*)count, err);
+      ra, dec, n, radius_arcsec / 3600.0, order, pix_const(order), out, (uint32_t*)count, err);
   int rc = cudaGetLastError() == cudaSuccess ? HLC_OK : HLC_ECUDA;
   if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_quad_cells");
   cudaFreeAsync(err, st);

@@ -13,6 +13,8 @@
 namespace hlc {
 
 constexpr int kThreads = 256;
+// Entries of B in a table cell below which the join uses the table order.
+constexpr uint32_t kSparseCell = 16;
 
 // ---------------------------------------------------------------------------
 // Preparation.
@@ -23,16 +25,25 @@ constexpr int kThreads = 256;
 // evaluation with binary64 fallback (same pixels).
 template <bool FAST>
 __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restrict__ dec,
-                            uint64_t n, int order, uint32_t* __restrict__ key,
+                            uint64_t n, int order, PixConst K, uint32_t* __restrict__ key,
                             uint32_t* __restrict__ idx, int* __restrict__ err) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
     double a = ra[i], d = dec[i];
     uint32_t k = 0;
-    if (!c_valid(a, d))
-      atomicOr(err, DERR_INPUT);
-    else
-      k = FAST ? g_ang2pix(c_norm_ra(a), d, order) : c_ang2pix(c_norm_ra(a), d, order);
+    if (FAST) {
+      if (!(bits_finite(a) && bits_abs_le(d, 90.0))) {
+        atomicOr(err, DERR_INPUT);
+      } else {
+        if (!bits_in_ra_range(a)) a = c_norm_ra(a);
+        k = g_ang2pix(a, d, order, K);
+      }
+    } else {
+      if (!c_valid(a, d))
+        atomicOr(err, DERR_INPUT);
+      else
+        k = c_ang2pix(c_norm_ra(a), d, order);
+    }
     key[i] = k;
     idx[i] = (uint32_t)i;
   }
@@ -41,7 +52,8 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
 // Quad-direction cells of each source (Algorithm 1): 5 slots + count.
 template <bool FAST>
 __global__ void k_quad_cells(const double* __restrict__ ra, const double* __restrict__ dec,
-                             uint64_t n, double R, int order, uint32_t* __restrict__ cells,
+                             uint64_t n, double R, int order, PixConst K,
+                             uint32_t* __restrict__ cells,
                              uint32_t* __restrict__ count, int* __restrict__ err) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
@@ -52,7 +64,7 @@ __global__ void k_quad_cells(const double* __restrict__ ra, const double* __rest
       atomicOr(err, DERR_INPUT);
       c[0] = 0;
     } else {
-      m = FAST ? g_quad_cells(c_norm_ra(a), d, R, order, c)
+      m = FAST ? g_quad_cells(c_norm_ra(a), d, R, order, K, c)
                : c_quad_cells(c_norm_ra(a), d, R, order, c);
     }
 #pragma unroll
@@ -102,7 +114,10 @@ __global__ void k_payload32(const double* __restrict__ ra, const double* __restr
     uint32_t i = idx[e];
     double a = ra[i], d = dec[i];
     float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (c_valid(a, d)) u = fp32_unitvec(c_norm_ra(a), d);
+    if (bits_finite(a) && bits_abs_le(d, 90.0)) {
+      if (!bits_in_ra_range(a)) a = c_norm_ra(a);
+      u = fp32_unitvec(a, d);
+    }
     v[e] = u;
   }
 }
@@ -196,20 +211,31 @@ __global__ void __launch_bounds__(kThreads) k_pair(
         ax = axv[k]; ay = ayv[k]; az = azv[k];
       }
     }
-    // neighbourhood of the A cell (complete) or the cell itself (quad)
+    // neighbourhood of the A cell (complete) or the cell itself (quad).  In
+    // complete mode a sparse region is joined at the order of B's offset
+    // table instead: the 3x3 block of table cells around the A cell's parent
+    // covers the fine 3x3 block (a superset of candidates, so the same
+    // exact set), and each of its ranges is read straight from the table.
     uint32_t nb[9];
     int m = 0;
+    bool coarse = false;
     if (live) {
       if (QUAD) {
         nb[0] = cell;
         m = 1;
       } else {
-        m = cell_neighbourhood(cell, order, nb);
+        uint32_t P = cell >> bix.shift;
+        coarse = bix.shift > 0 && __ldg(bix.table + P + 1) - __ldg(bix.table + P) <= kSparseCell;
+        m = coarse ? cell_neighbourhood(P, order - bix.shift / 2, nb)
+                   : cell_neighbourhood(cell, order, nb);
       }
     }
     const int nslot = QUAD ? 1 : 9;
     for (int s = 0; s < nslot; ++s) {
-      uint2 r = s < m ? cell_range(bix, nb[s]) : make_uint2(0u, 0u);
+      uint2 r = make_uint2(0u, 0u);
+      if (s < m)
+        r = coarse ? make_uint2(__ldg(bix.table + nb[s]), __ldg(bix.table + nb[s] + 1))
+                   : cell_range(bix, nb[s]);
       uint32_t len = r.y - r.x;
       ntest += len;
       uint32_t maxlen = __reduce_max_sync(0xffffffffu, len);

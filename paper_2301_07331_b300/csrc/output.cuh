@@ -2,15 +2,17 @@
 // the rows in ascending (id_a, id_b) order.
 //
 // Ordering: the rows are distributed into 2^b buckets by the b bits of id_a
-// just below its highest varying bit (a counting scatter), and every bucket,
-// a few dozen rows on average, is sorted in shared memory by a bitonic
-// network on (id_a, id_b, separation bits).  When a bucket would not fit in
-// shared memory (strongly clustered ids) the caller falls back to two stable
-// LSD radix sorts (by id_b, then by id_a).
+// just below its highest varying bit (a counting scatter, about two rows per
+// bucket), then every bucket is sorted on (id_a, id_b, separation bits): by
+// one thread (insertion) when small, by a CTA's bitonic network in shared
+// memory when larger.  When a bucket would not fit in shared memory (one id
+// matched thousands of times, or all ids equal) the caller falls back to two
+// stable LSD radix sorts (by id_b, then by id_a).
 #pragma once
 
 #include "canon.cuh"
 #include "common.cuh"
+#include "fp32.cuh"
 
 namespace hlc {
 
@@ -55,6 +57,44 @@ __device__ __forceinline__ double sep_arcsec_haversine(double ra1, double dec1, 
   return 2.0 * as * (648000.0 / 3.141592653589793238462643);
 }
 
+// Separation of two nearby sources (ra in [0, 360)) in float-float arithmetic
+// on the FP32 pipe: haversine form with the angle differences formed exactly
+// from the split binary64 inputs and cos(Dec) to ~3e-8 relative, so the
+// relative error of the result is below 1e-7 (5e-7 arcsec at 5 arcsec).
+// Returns a negative value when the pair is not "nearby" (differences above
+// 20 arcsec), in which case the caller uses the binary64 unit vectors.
+__device__ __forceinline__ double sep_arcsec_f2(double ra1, double dec1, double ra2,
+                                                double dec2) {
+  f2 a1 = split_f64(ra1), d1 = split_f64(dec1), a2 = split_f64(ra2), d2 = split_f64(dec2);
+  f2 dd = f2_add(d2, f2{-d1.hi, -d1.lo});
+  f2 da = f2_add(a2, f2{-a1.hi, -a1.lo});
+  if (da.hi > 180.f) da = f2_add(da, f2{-360.f, 0.f});
+  if (da.hi < -180.f) da = f2_add(da, f2{360.f, 0.f});
+  const float lim = 20.0f / 3600.0f;
+  if (fabsf(dd.hi) > lim || fabsf(da.hi) > lim) return -1.0;
+  f2 c1 = f2_cos_deg(d1), c2 = f2_cos_deg(d2);
+  f2 K = f2_mul(c1, c2);
+  const f2 HR = {8.726646192e-3f, 6.759980075e-11f};  // pi/360 as a float pair
+  f2 x = f2_mul(dd, HR), y = f2_mul(da, HR);         // half differences, radians
+  // sin of the half differences: x - x^3/6 (x <= 5e-5 rad: next term < 1e-19)
+  f2 sx = f2_add(x, f2{-x.hi * x.hi * x.hi * (1.0f / 6.0f), 0.f});
+  f2 sy = f2_add(y, f2{-y.hi * y.hi * y.hi * (1.0f / 6.0f), 0.f});
+  f2 hav = f2_add(f2_mul(sx, sx), f2_mul(K, f2_mul(sy, sy)));
+  // v = sqrt(hav) with one float-float Newton correction
+  float v0 = sqrtf(hav.hi);
+  f2 v = {v0, 0.f};
+  if (v0 > 0.f) {
+    f2 sq = f2_mul(v, v);
+    f2 rem = f2_add(hav, f2{-sq.hi, -sq.lo});
+    v = fast_two_sum(v0, rem.hi / (2.0f * v0));
+  }
+  // asin(v) = v + v^3/6 (+ 3v^5/40 < 1e-22 relative here)
+  f2 as = f2_add(v, f2{v.hi * v.hi * v.hi * (1.0f / 6.0f), 0.f});
+  const f2 SC = {412529.625f, -1.2505806983e-2f};  // 2 * 648000 / pi as a float pair
+  f2 r = f2_mul(as, SC);
+  return (double)r.hi + (double)r.lo;
+}
+
 // ids + separation of each row, and the bucket histogram of id_a.
 template <bool FP32>
 __global__ void k_rows(const uint2* __restrict__ rows, uint64_t M,
@@ -78,8 +118,13 @@ __global__ void k_rows(const uint2* __restrict__ rows, uint64_t M,
     if (bhist) atomicAdd(&bhist[(uint32_t)(a >> bshift) & bmask], 1u);
     if (want_sep) {
       double sv;
-      if (FP32)
-        sv = sep_arcsec_haversine(c_norm_ra(raA[ia]), decA[ia], c_norm_ra(raB[ib]), decB[ib]);
+      if (FP32) {
+        double a1 = raA[ia], a2 = raB[ib];
+        if (!bits_in_ra_range(a1)) a1 = c_norm_ra(a1);
+        if (!bits_in_ra_range(a2)) a2 = c_norm_ra(a2);
+        sv = sep_arcsec_f2(a1, decA[ia], a2, decB[ib]);
+        if (sv < 0.0) sv = sep_arcsec_haversine(a1, decA[ia], a2, decB[ib]);
+      }
       else
         sv = sep_arcsec_from_chord2(
             c_chord2(axv[p.x], ayv[p.x], azv[p.x], bxv[p.y], byv[p.y], bzv[p.y]));
@@ -119,7 +164,42 @@ __device__ __forceinline__ bool row_less(uint64_t a1, uint64_t b1, uint64_t s1, 
   return s1 < s2;
 }
 
-// One CTA per bucket: bitonic sort of <= kBucketCap rows in shared memory.
+// One thread per small bucket (<= kSmallBucket rows): insertion sort into the
+// output arrays.
+constexpr uint32_t kSmallBucket = 32;
+
+__global__ void k_bucket_small(const uint64_t* __restrict__ ta, const uint64_t* __restrict__ tb,
+                               const double* __restrict__ ts, const uint32_t* __restrict__ boff,
+                               uint32_t nbuckets, uint64_t* __restrict__ oa,
+                               uint64_t* __restrict__ ob, double* __restrict__ os) {
+  for (uint32_t bk = blockIdx.x * blockDim.x + threadIdx.x; bk < nbuckets;
+       bk += gridDim.x * blockDim.x) {
+    uint32_t lo = boff[bk], hi = boff[bk + 1];
+    uint32_t n = hi - lo;
+    if (n == 0 || n > kSmallBucket) continue;
+    for (uint32_t i = 0; i < n; ++i) {
+      uint64_t a = ta[lo + i], b = tb[lo + i];
+      double sv = ts ? ts[lo + i] : 0.0;
+      uint64_t sb = (uint64_t)__double_as_longlong(sv);
+      uint32_t j = i;
+      while (j > 0) {
+        uint64_t pa = oa[lo + j - 1], pb = ob[lo + j - 1];
+        uint64_t ps = os ? (uint64_t)__double_as_longlong(os[lo + j - 1]) : 0ull;
+        if (!row_less(a, b, sb, pa, pb, ps)) break;
+        oa[lo + j] = pa;
+        ob[lo + j] = pb;
+        if (os) os[lo + j] = os[lo + j - 1];
+        --j;
+      }
+      oa[lo + j] = a;
+      ob[lo + j] = b;
+      if (os) os[lo + j] = sv;
+    }
+  }
+}
+
+// One CTA per larger bucket (kSmallBucket < rows <= kBucketCap): bitonic
+// sort in shared memory.
 __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(
     const uint64_t* __restrict__ ta, const uint64_t* __restrict__ tb,
     const double* __restrict__ ts, const uint32_t* __restrict__ boff, uint32_t nbuckets,
@@ -129,7 +209,7 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(
   for (uint32_t bk = blockIdx.x; bk < nbuckets; bk += gridDim.x) {
     uint32_t lo = boff[bk], hi = boff[bk + 1];
     uint32_t n = hi - lo;
-    if (n == 0) continue;
+    if (n <= kSmallBucket) continue;
     if (n > kBucketCap) {  // the host checked; never taken
       if (threadIdx.x == 0) atomicOr(err, DERR_BOUNDS);
       continue;

@@ -129,8 +129,15 @@ __global__ void __launch_bounds__(kBlock) k_onesweep(
   const unsigned lt = lanemask_lt();
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
-    unsigned peers = __match_any_sync(0xffffffffu, d[i]);
+    // lanes holding the same digit: intersect the 8 bit-plane ballots
     bool valid = d[i] < kRadix;
+    unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      bool bit = (d[i] >> b) & 1;
+      unsigned bb = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? bb : ~bb;
+    }
     uint32_t before = valid ? S.whist[warp][d[i]] : 0u;
     r[i] = before + __popc(peers & lt);
     __syncwarp();
