@@ -45,10 +45,11 @@ __device__ __forceinline__ FastDec f_dec_part(f2 dec) {
 }
 
 // floor(v) as an int when v lies farther than e from an integer.
+// (0 <= v < 2^23.)
 __device__ __forceinline__ bool sure_floorf(float v, float e, int* out) {
-  float f = floorf(v);
+  float f = floor_pos(v);
   float r = v - f;
-  *out = (int)f;
+  *out = ifloor_pos(v);
   return r > e && r < 1.0f - e;
 }
 
@@ -73,32 +74,36 @@ __host__ __device__ inline PixConst pix_const(int order) {
 __device__ __forceinline__ bool f_pix(f2 ra, const FastDec& d, int order, const PixConst& K,
                                       uint32_t* out) {
   if (!d.ok) return false;
-  const float ns = (float)(1u << order);
+  const float ns = pow2f(order);
   const int nsi = 1 << order;
   int face, ix, iy;
   if (!d.polar) {
     // ns (0.5 + ra/90) -/+ ns 0.75 z, split into integer and fraction
     f2 t = f2_mul(ra, f2{K.kh, K.kl});
-    float ih = floorf(t.hi);
+    float ih = floor_pos(t.hi);
+    int iih = ifloor_pos(t.hi);
     float a = (t.hi - ih) + t.lo;  // fraction of ns ra / 90
     float t2 = ns * 0.75f * d.z;
     const float e = ns * 4e-7f + 4e-7f;
     int f1, f2i;
     if (!sure_floorf(a + (0.5f * ns - t2), e, &f1)) return false;
     if (!sure_floorf(a + (0.5f * ns + t2), e, &f2i)) return false;
-    int jp = (int)ih + f1, jm = (int)ih + f2i;
+    int jp = iih + f1, jm = iih + f2i;
     int ifp = jp >> order, ifm = jm >> order;
     face = (ifp == ifm) ? (ifp | 4) : (ifp < ifm ? ifp : ifm + 8);
     ix = jm & (nsi - 1);
     iy = nsi - (jp & (nsi - 1)) - 1;
   } else {
     f2 tt = f2_mul(ra, f2{K.inv90h, K.inv90l});
-    float fh = floorf(tt.hi);
+    float fh = floor_pos(tt.hi);
     float fr = (tt.hi - fh) + tt.lo;
     if (!(fr > 1e-6f && fr < 1.0f - 1e-6f)) return false;
-    int ntt = (int)fh;
-    if (ntt >= 4) ntt = 3;
-    float tp = fr + (fh - (float)ntt);
+    int ntt = ifloor_pos(tt.hi);
+    float tp = fr;
+    if (ntt >= 4) {
+      ntt = 3;
+      tp = fr + (fh - 3.0f);
+    }
     float tmp = ns * d.cap;
     const float e = ns * 6e-7f + 4e-7f;
     int jp, jm;
@@ -131,6 +136,7 @@ __device__ __forceinline__ uint32_t g_ang2pix(double ra, double dec, int order,
 
 // Quad-direction cells (Algorithm 1) through the guarded pixel function.  The
 // shifted coordinates are formed exactly as in the binary64 statement.
+// Returns the number of cells, or 0 when some pixel needs the binary64 path.
 __device__ __forceinline__ int g_quad_cells(double ra, double dec, double R, int order,
                                             const PixConst& K, uint32_t out[5]) {
   double dp_ = __dadd_rn(dec, R);
@@ -138,22 +144,16 @@ __device__ __forceinline__ int g_quad_cells(double ra, double dec, double R, int
   double dm_ = __dsub_rn(dec, R);
   if (dm_ < -90.0) dm_ = -90.0;
   FastDec f0 = f_dec_part(split_f64(dec));
+  FastDec fm = f_dec_part(split_f64(dm_));
+  FastDec fp = f_dec_part(split_f64(dp_));
   uint32_t p[5];
-  double ras[3] = {ra, wrap_ra(__dadd_rn(ra, R)), wrap_ra(__dsub_rn(ra, R))};
-  bool have_c0 = false;
-  DecPart c0;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    if (!f_pix(split_f64(ras[i]), f0, order, K, &p[i])) {
-      if (!have_c0) {
-        c0 = c_dec_part(dec);
-        have_c0 = true;
-      }
-      p[i] = c_pix(ras[i], c0, order);
-    }
-  }
-  p[3] = g_ang2pix(ra, dm_, order, K);
-  p[4] = g_ang2pix(ra, dp_, order, K);
+  f2 r0 = split_f64(ra);
+  bool ok = f_pix(r0, f0, order, K, &p[0]);
+  ok = ok && f_pix(split_f64(wrap_ra(__dadd_rn(ra, R))), f0, order, K, &p[1]);
+  ok = ok && f_pix(split_f64(wrap_ra(__dsub_rn(ra, R))), f0, order, K, &p[2]);
+  ok = ok && f_pix(r0, fm, order, K, &p[3]);
+  ok = ok && f_pix(r0, fp, order, K, &p[4]);
+  if (!ok) return 0;
 #pragma unroll
   for (int i = 1; i < 5; ++i) {
     uint32_t v = p[i];

@@ -168,13 +168,12 @@ static double chord2_threshold(double r_arcsec) {
 // ---------------------------------------------------------------------------
 struct CatDev {
   uint64_t n = 0, m = 0;
-  double* ra = nullptr;
-  double* dec = nullptr;
-  uint64_t* id = nullptr;
   uint32_t* key = nullptr;   // sorted cell keys of the entries
   uint32_t* idx = nullptr;   // source of each sorted entry
   double *vx = nullptr, *vy = nullptr, *vz = nullptr;
   float4* v32 = nullptr;
+  double2* rd = nullptr;       // entry-ordered (ra, dec), guard form
+  uint64_t* id_s = nullptr;    // entry-ordered ids
   uint32_t* cells5 = nullptr;  // quad: cell set of each source
   uint32_t* table = nullptr;   // coarse offset table (catalogue B)
   int table_shift = 0;
@@ -183,7 +182,7 @@ struct CatDev {
 };
 
 enum Ctr { C_ROWS = 0, C_BAND, C_TESTS, C_DUPS, C_M, C_TOTAL, C_HEADS_A, C_HEADS_B,
-           C_IDDIFF, C_MAXB, C_N };
+           C_IDDIFF, C_MAXB, C_SLOW, C_N };
 
 }  // namespace hlc
 
@@ -203,6 +202,7 @@ struct hlc_plan_s {
   unsigned long long launches0 = 0;
   int id_high_bit = -1;
   uint64_t row_cap = 0;
+  uint32_t sparse_cell = hlc::kSparseCell;
   unsigned long long plan_launches = 0;
   cudaEvent_t ev[12] = {};
   bool events = false;
@@ -294,14 +294,25 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
   const bool fp32 = P->p.precision == HLC_FP32_GUARD;
   X.n = in->n;
   uint64_t n = X.n;
-  HLC_ALLOC(ar, X.ra, double, n + 1);
-  HLC_ALLOC(ar, X.dec, double, n + 1);
-  HLC_ALLOC(ar, X.id, uint64_t, n + 1);
-  cudaMemcpyKind kind = in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (n) {
-    HLC_CUDA(cudaMemcpyAsync(X.ra, in->ra_deg, n * 8, kind, st));
-    HLC_CUDA(cudaMemcpyAsync(X.dec, in->dec_deg, n * 8, kind, st));
-    HLC_CUDA(cudaMemcpyAsync(X.id, in->id, n * 8, kind, st));
+  // device inputs are read in place (only until this call returns); host
+  // inputs are staged in temporary device buffers
+  const double* ra = in->ra_deg;
+  const double* dec = in->dec_deg;
+  const uint64_t* id = in->id;
+  double *tra = nullptr, *tdec = nullptr;
+  uint64_t* tid = nullptr;
+  if (!in->on_device) {
+    HLC_ALLOC(ar, tra, double, n + 1);
+    HLC_ALLOC(ar, tdec, double, n + 1);
+    HLC_ALLOC(ar, tid, uint64_t, n + 1);
+    if (n) {
+      HLC_CUDA(cudaMemcpyAsync(tra, in->ra_deg, n * 8, cudaMemcpyHostToDevice, st));
+      HLC_CUDA(cudaMemcpyAsync(tdec, in->dec_deg, n * 8, cudaMemcpyHostToDevice, st));
+      HLC_CUDA(cudaMemcpyAsync(tid, in->id, n * 8, cudaMemcpyHostToDevice, st));
+    }
+    ra = tra;
+    dec = tdec;
+    id = tid;
   }
   cudaEventRecord(ev[0], st);
   if (!quad) {
@@ -309,13 +320,21 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     HLC_ALLOC(ar, X.key, uint32_t, n + 1);
     HLC_ALLOC(ar, X.idx, uint32_t, n + 1);
     if (n) {
-      if (fp32)
-        k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(X.ra, X.dec, n, L, pix_const(L), X.key,
-                                                                      X.idx, P->dev_err);
-      else
-        k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(X.ra, X.dec, n, L, pix_const(L), X.key,
-                                                                       X.idx, P->dev_err);
-      HLC_LAUNCH_CHECK();
+      if (fp32) {
+        uint32_t* slow = ar.get_n<uint32_t>(n + 1);
+        if (!slow) return HLC_ENOMEM;
+        HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st));
+        k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+            ra, dec, n, L, pix_const(L), X.key, X.idx, slow, P->ctr + C_SLOW, P->dev_err);
+        HLC_LAUNCH_CHECK();
+        k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key);
+        HLC_LAUNCH_CHECK();
+        ar.drop(slow);
+      } else {
+        k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+            ra, dec, n, L, pix_const(L), X.key, X.idx, nullptr, nullptr, P->dev_err);
+        HLC_LAUNCH_CHECK();
+      }
     }
   } else {
     HLC_ALLOC(ar, X.cells5, uint32_t, 5 * n + 5);
@@ -324,13 +343,23 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     void* scr = ar.get(scan_scratch_bytes(n));
     if (!cnt || !off || !scr) return HLC_ENOMEM;
     if (n) {
-      if (fp32)
+      const double R = P->p.radius_arcsec / 3600.0;
+      if (fp32) {
+        uint32_t* slow = ar.get_n<uint32_t>(n + 1);
+        if (!slow) return HLC_ENOMEM;
+        HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st));
         k_quad_cells<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            X.ra, X.dec, n, P->p.radius_arcsec / 3600.0, L, pix_const(L), X.cells5, cnt, P->dev_err);
-      else
+            ra, dec, n, R, L, pix_const(L), X.cells5, cnt, slow, P->ctr + C_SLOW, P->dev_err);
+        HLC_LAUNCH_CHECK();
+        k_quad_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, R, L, slow, P->ctr + C_SLOW,
+                                                      X.cells5, cnt);
+        HLC_LAUNCH_CHECK();
+        ar.drop(slow);
+      } else {
         k_quad_cells<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            X.ra, X.dec, n, P->p.radius_arcsec / 3600.0, L, pix_const(L), X.cells5, cnt, P->dev_err);
-      HLC_LAUNCH_CHECK();
+            ra, dec, n, R, L, pix_const(L), X.cells5, cnt, nullptr, nullptr, P->dev_err);
+        HLC_LAUNCH_CHECK();
+      }
     }
     HLC_TRY(scan_exclusive<uint64_t>(cnt, off, n, P->ctr + C_TOTAL, scr, P->dev_err, st));
     unsigned long long m = 0;
@@ -366,17 +395,26 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     HLC_ALLOC(ar, X.vx, double, m + 1);
     HLC_ALLOC(ar, X.vy, double, m + 1);
     HLC_ALLOC(ar, X.vz, double, m + 1);
+    HLC_ALLOC(ar, X.id_s, uint64_t, m + 1);
     if (m) {
-      k_payload64<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.ra, X.dec, X.idx, m, X.vx, X.vy,
-                                                               X.vz);
+      k_payload64<<<grid_for(m, kThreads), kThreads, 0, st>>>(ra, dec, id, X.idx, m, X.vx, X.vy,
+                                                               X.vz, X.id_s);
       HLC_LAUNCH_CHECK();
     }
   } else {
     HLC_ALLOC(ar, X.v32, float4, m + 1);
+    HLC_ALLOC(ar, X.rd, double2, m + 1);
+    HLC_ALLOC(ar, X.id_s, uint64_t, m + 1);
     if (m) {
-      k_payload32<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.ra, X.dec, X.idx, m, X.v32);
+      k_payload32<<<grid_for(m, kThreads), kThreads, 0, st>>>(ra, dec, id, X.idx, m, X.v32,
+                                                               X.rd, X.id_s);
       HLC_LAUNCH_CHECK();
     }
+  }
+  if (tra) {
+    ar.drop(tra);
+    ar.drop(tdec);
+    ar.drop(tid);
   }
   unsigned long long* heads = P->ctr + (is_b ? C_HEADS_B : C_HEADS_A);
   if (is_b) {
@@ -453,8 +491,8 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   }
   int rc = build_catalog(P, A, P->A, false, ea);
   if (rc == HLC_OK) rc = build_catalog(P, B, P->B, true, eb);
-  if (rc == HLC_OK && P->A.n) {
-    k_id_diff<<<grid_for(P->A.n, kThreads, 148u * 8u), kThreads, 0, st>>>(P->A.id, P->A.n,
+  if (rc == HLC_OK && P->A.m) {
+    k_id_diff<<<grid_for(P->A.m, kThreads, 148u * 8u), kThreads, 0, st>>>(P->A.id_s, P->A.m,
                                                                           P->ctr + C_IDDIFF);
     if (cudaGetLastError() != cudaSuccess) rc = HLC_ECUDA;
   }
@@ -562,19 +600,19 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
       if (fp32 && quad)
         k_pair<true, true><<<grid, kThreads, 0, st>>>(
             A.m, A.key, bix, L, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, A.v32,
-            B.v32, P->C, P->lo32, P->hi32, A.idx, B.idx, A.cells5, B.cells5, sink);
+            B.v32, P->C, P->lo32, P->hi32, A.idx, B.idx, A.cells5, B.cells5, sink, P->sparse_cell);
       else if (fp32)
         k_pair<true, false><<<grid, kThreads, 0, st>>>(
             A.m, A.key, bix, L, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, A.v32,
-            B.v32, P->C, P->lo32, P->hi32, A.idx, B.idx, nullptr, nullptr, sink);
+            B.v32, P->C, P->lo32, P->hi32, A.idx, B.idx, nullptr, nullptr, sink, P->sparse_cell);
       else if (quad)
         k_pair<false, true><<<grid, kThreads, 0, st>>>(
             A.m, A.key, bix, L, A.vx, A.vy, A.vz, B.vx, B.vy, B.vz, nullptr, nullptr, P->C, 0.f,
-            0.f, A.idx, B.idx, A.cells5, B.cells5, sink);
+            0.f, A.idx, B.idx, A.cells5, B.cells5, sink, P->sparse_cell);
       else
         k_pair<false, false><<<grid, kThreads, 0, st>>>(
             A.m, A.key, bix, L, A.vx, A.vy, A.vz, B.vx, B.vy, B.vz, nullptr, nullptr, P->C, 0.f,
-            0.f, A.idx, B.idx, nullptr, nullptr, sink);
+            0.f, A.idx, B.idx, nullptr, nullptr, sink, P->sparse_cell);
       HLC_LAUNCH_CHECK();
     }
     HLC_CUDA(cudaMemcpyAsync(h, P->ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -595,8 +633,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   ev_record(P, 4);
   if (fp32 && h[C_BAND]) {
     k_recheck<<<grid_for(h[C_BAND], kThreads, 148u * 16u), kThreads, 0, st>>>(
-        band, P->ctr + C_BAND, bcap, A.idx, B.idx, A.ra, A.dec, B.ra, B.dec, P->C, rows,
-        P->ctr + C_ROWS, cap, P->dev_err);
+        band, P->ctr + C_BAND, bcap, A.rd, B.rd, P->C, rows, P->ctr + C_ROWS, cap, P->dev_err);
     HLC_LAUNCH_CHECK();
   }
   ev_record(P, 5);
@@ -635,13 +672,13 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   if (M) {
     unsigned g = grid_for(M, kThreads);
     if (fp32)
-      k_rows<true><<<g, kThreads, 0, st>>>(rows, M, A.idx, B.idx, A.id, B.id, nullptr, nullptr,
-                                            nullptr, nullptr, nullptr, nullptr, A.ra, A.dec, B.ra,
-                                            B.dec, want_sep, ka, kb, sep, bshift, bmask, bhist);
+      k_rows<true><<<g, kThreads, 0, st>>>(rows, M, A.id_s, B.id_s, nullptr, nullptr, nullptr,
+                                            nullptr, nullptr, nullptr, A.rd, B.rd, want_sep, ka,
+                                            kb, sep, bshift, bmask, bhist);
     else
-      k_rows<false><<<g, kThreads, 0, st>>>(rows, M, A.idx, B.idx, A.id, B.id, A.vx, A.vy, A.vz,
-                                             B.vx, B.vy, B.vz, nullptr, nullptr, nullptr, nullptr,
-                                             want_sep, ka, kb, sep, bshift, bmask, bhist);
+      k_rows<false><<<g, kThreads, 0, st>>>(rows, M, A.id_s, B.id_s, A.vx, A.vy, A.vz, B.vx,
+                                             B.vy, B.vz, nullptr, nullptr, want_sep, ka, kb, sep,
+                                             bshift, bmask, bhist);
     HLC_LAUNCH_CHECK();
   }
   ar.drop(rows);
@@ -814,16 +851,34 @@ int hlc_ang2pix(const double* ra, const double* dec, uint64_t n, int order, int 
     set_error("cudaMallocAsync failed: %s", cudaGetErrorString(e));
     return HLC_ENOMEM;
   }
-  if (precision == HLC_FP32_GUARD)
-    k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(ra, dec, n, order, pix_const(order), pix, idx, err);
-  else
-    k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(ra, dec, n, order, pix_const(order), pix, idx, err);
+  uint32_t* slow = nullptr;
+  unsigned long long* nslow = nullptr;
+  if (precision == HLC_FP32_GUARD) {
+    if (cudaMallocAsync(&slow, n * 4, st) != cudaSuccess ||
+        cudaMallocAsync(&nslow, 8, st) != cudaSuccess) {
+      cudaGetLastError();
+      if (slow) cudaFreeAsync(slow, st);
+      cudaFreeAsync(idx, st);
+      cudaFreeAsync(err, st);
+      set_error("cudaMallocAsync failed");
+      return HLC_ENOMEM;
+    }
+    cudaMemsetAsync(nslow, 0, 8, st);
+    k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+        ra, dec, n, order, pix_const(order), pix, idx, slow, nslow, err);
+    k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, order, slow, nslow, pix);
+  } else {
+    k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+        ra, dec, n, order, pix_const(order), pix, idx, nullptr, nullptr, err);
+  }
   int rc = HLC_OK;
   if (cudaGetLastError() != cudaSuccess) {
     set_error("ang2pix launch failed");
     rc = HLC_ECUDA;
   }
   if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_ang2pix");
+  if (slow) cudaFreeAsync(slow, st);
+  if (nslow) cudaFreeAsync(nslow, st);
   cudaFreeAsync(idx, st);
   cudaFreeAsync(err, st);
   return rc;
@@ -892,7 +947,8 @@ int hlc_quad_cells(const double* ra, const double* dec, uint64_t n, double radiu
   HLC_CUDA(cudaMallocAsync(&err, sizeof(int), st));
   cudaMemsetAsync(err, 0, sizeof(int), st);
   k_quad_cells<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-      ra, dec, n, radius_arcsec / 3600.0, order, pix_const(order), out, (uint32_t*)count, err);
+      ra, dec, n, radius_arcsec / 3600.0, order, pix_const(order), out, (uint32_t*)count,
+      nullptr, nullptr, err);
   int rc = cudaGetLastError() == cudaSuccess ? HLC_OK : HLC_ECUDA;
   if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_quad_cells");
   cudaFreeAsync(err, st);

@@ -13,8 +13,12 @@
 namespace hlc {
 
 constexpr int kThreads = 256;
-// Entries of B in a table cell below which the join uses the table order.
-constexpr uint32_t kSparseCell = 16;
+// Number of B entries in a table cell up to which the FP32 join uses the
+// table order (sparse regions).
+#ifndef HLC_SPARSE_CELL
+#define HLC_SPARSE_CELL 32
+#endif
+constexpr uint32_t kSparseCell = HLC_SPARSE_CELL;
 
 // ---------------------------------------------------------------------------
 // Preparation.
@@ -23,52 +27,121 @@ constexpr uint32_t kSparseCell = 16;
 // Cell key and identity index of each source (complete mode), with input
 // validation (non-finite or |dec| > 90 sets DERR_INPUT).  FAST: guarded FP32
 // evaluation with binary64 fallback (same pixels).
+// (FAST: sources the guarded estimate cannot decide are queued and finished
+// by k_prep_fallback, so that warps do not diverge into the binary64 path.)
 template <bool FAST>
 __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restrict__ dec,
                             uint64_t n, int order, PixConst K, uint32_t* __restrict__ key,
-                            uint32_t* __restrict__ idx, int* __restrict__ err) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    double a = ra[i], d = dec[i];
-    uint32_t k = 0;
-    if (FAST) {
-      if (!(bits_finite(a) && bits_abs_le(d, 90.0))) {
-        atomicOr(err, DERR_INPUT);
+                            uint32_t* __restrict__ idx, uint32_t* __restrict__ slow,
+                            unsigned long long* __restrict__ nslow, int* __restrict__ err) {
+  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n;
+       i0 += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t i = i0 + threadIdx.x;
+    bool live = i < n;
+    bool defer = false;
+    if (live) {
+      double a = ra[i], d = dec[i];
+      uint32_t k = 0;
+      if (FAST) {
+        if (!(bits_finite(a) && bits_abs_le(d, 90.0))) {
+          atomicOr(err, DERR_INPUT);
+        } else {
+          if (!bits_in_ra_range(a)) a = c_norm_ra(a);
+          FastDec fd = f_dec_part(split_f64(d));
+          defer = !f_pix(split_f64(a), fd, order, K, &k);
+        }
       } else {
-        if (!bits_in_ra_range(a)) a = c_norm_ra(a);
-        k = g_ang2pix(a, d, order, K);
+        if (!c_valid(a, d))
+          atomicOr(err, DERR_INPUT);
+        else
+          k = c_ang2pix(c_norm_ra(a), d, order);
       }
-    } else {
-      if (!c_valid(a, d))
-        atomicOr(err, DERR_INPUT);
-      else
-        k = c_ang2pix(c_norm_ra(a), d, order);
+      key[i] = k;
+      idx[i] = (uint32_t)i;
     }
-    key[i] = k;
-    idx[i] = (uint32_t)i;
+    if (FAST) {
+      unsigned b = __ballot_sync(0xffffffffu, defer);
+      if (b) {
+        int lane = threadIdx.x & 31;
+        unsigned long long base = 0;
+        if (lane == __ffs(b) - 1) base = atomicAdd(nslow, (unsigned long long)__popc(b));
+        base = __shfl_sync(0xffffffffu, base, __ffs(b) - 1);
+        if (defer) slow[base + __popc(b & lanemask_lt())] = (uint32_t)i;
+      }
+    }
+  }
+}
+
+// Binary64 ang2pix of the queued sources.
+__global__ void k_prep_fallback(const double* __restrict__ ra, const double* __restrict__ dec,
+                                int order, const uint32_t* __restrict__ slow,
+                                const unsigned long long* __restrict__ nslow,
+                                uint32_t* __restrict__ key) {
+  uint64_t ns = *nslow;
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns;
+       q += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t i = slow[q];
+    key[i] = c_ang2pix(c_norm_ra(ra[i]), dec[i], order);
   }
 }
 
 // Quad-direction cells of each source (Algorithm 1): 5 slots + count.
+// (FAST: sources with an undecided pixel are queued for k_quad_fallback.)
 template <bool FAST>
 __global__ void k_quad_cells(const double* __restrict__ ra, const double* __restrict__ dec,
                              uint64_t n, double R, int order, PixConst K,
-                             uint32_t* __restrict__ cells,
-                             uint32_t* __restrict__ count, int* __restrict__ err) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    double a = ra[i], d = dec[i];
-    uint32_t c[5] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-    int m = 1;
-    if (!c_valid(a, d)) {
-      atomicOr(err, DERR_INPUT);
-      c[0] = 0;
-    } else {
-      m = FAST ? g_quad_cells(c_norm_ra(a), d, R, order, K, c)
-               : c_quad_cells(c_norm_ra(a), d, R, order, c);
-    }
+                             uint32_t* __restrict__ cells, uint32_t* __restrict__ count,
+                             uint32_t* __restrict__ slow, unsigned long long* __restrict__ nslow,
+                             int* __restrict__ err) {
+  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n;
+       i0 += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t i = i0 + threadIdx.x;
+    bool defer = false;
+    if (i < n) {
+      double a = ra[i], d = dec[i];
+      uint32_t c[5] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+      int m = 1;
+      if (!c_valid(a, d)) {
+        atomicOr(err, DERR_INPUT);
+        c[0] = 0;
+      } else if (FAST) {
+        m = g_quad_cells(c_norm_ra(a), d, R, order, K, c);
+        if (m == 0) {
+          defer = true;
+          m = 1;
+        }
+      } else {
+        m = c_quad_cells(c_norm_ra(a), d, R, order, c);
+      }
 #pragma unroll
-    for (int e = 0; e < 5; ++e) cells[5 * i + e] = e < m ? c[e] : 0xFFFFFFFFu;
+      for (int e = 0; e < 5; ++e) cells[5 * i + e] = e < m ? c[e] : 0xFFFFFFFFu;
+      count[i] = (uint32_t)m;
+    }
+    if (FAST) {
+      unsigned b = __ballot_sync(0xffffffffu, defer);
+      if (b) {
+        int lane = threadIdx.x & 31;
+        unsigned long long base = 0;
+        if (lane == __ffs(b) - 1) base = atomicAdd(nslow, (unsigned long long)__popc(b));
+        base = __shfl_sync(0xffffffffu, base, __ffs(b) - 1);
+        if (defer) slow[base + __popc(b & lanemask_lt())] = (uint32_t)i;
+      }
+    }
+  }
+}
+
+__global__ void k_quad_fallback(const double* __restrict__ ra, const double* __restrict__ dec,
+                                double R, int order, const uint32_t* __restrict__ slow,
+                                const unsigned long long* __restrict__ nslow,
+                                uint32_t* __restrict__ cells, uint32_t* __restrict__ count) {
+  uint64_t ns = *nslow;
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns;
+       q += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t i = slow[q];
+    uint32_t c[5] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+    int m = c_quad_cells(c_norm_ra(ra[i]), dec[i], R, order, c);
+#pragma unroll
+    for (int e = 0; e < 5; ++e) cells[5ull * i + e] = e < m ? c[e] : 0xFFFFFFFFu;
     count[i] = (uint32_t)m;
   }
 }
@@ -88,11 +161,11 @@ __global__ void k_quad_emit(const uint32_t* __restrict__ cells, const uint32_t* 
   }
 }
 
-// Sorted payload: binary64 canonical unit vectors (plain form).
+// Sorted payload: binary64 canonical unit vectors (plain form) and ids.
 __global__ void k_payload64(const double* __restrict__ ra, const double* __restrict__ dec,
-                            const uint32_t* __restrict__ idx, uint64_t m,
-                            double* __restrict__ vx, double* __restrict__ vy,
-                            double* __restrict__ vz) {
+                            const uint64_t* __restrict__ id, const uint32_t* __restrict__ idx,
+                            uint64_t m, double* __restrict__ vx, double* __restrict__ vy,
+                            double* __restrict__ vz, uint64_t* __restrict__ id_s) {
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
        e += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t i = idx[e];
@@ -102,13 +175,17 @@ __global__ void k_payload64(const double* __restrict__ ra, const double* __restr
     vx[e] = x;
     vy[e] = y;
     vz[e] = z;
+    id_s[e] = id[i];
   }
 }
 
-// Sorted payload: FP32 unit vectors with a known error bound (guard form).
+// Sorted payload of the guard form: FP32 unit vectors with a known error
+// bound, the normalised coordinates (for the binary64 recheck and the
+// separations) and the ids, all in entry order.
 __global__ void k_payload32(const double* __restrict__ ra, const double* __restrict__ dec,
-                            const uint32_t* __restrict__ idx, uint64_t m,
-                            float4* __restrict__ v) {
+                            const uint64_t* __restrict__ id, const uint32_t* __restrict__ idx,
+                            uint64_t m, float4* __restrict__ v, double2* __restrict__ rd,
+                            uint64_t* __restrict__ id_s) {
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
        e += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t i = idx[e];
@@ -119,6 +196,8 @@ __global__ void k_payload32(const double* __restrict__ ra, const double* __restr
       u = fp32_unitvec(a, d);
     }
     v[e] = u;
+    rd[e] = make_double2(a, d);
+    id_s[e] = id[i];
   }
 }
 
@@ -194,7 +273,8 @@ __global__ void __launch_bounds__(kThreads) k_pair(
     const double* __restrict__ bxv, const double* __restrict__ byv, const double* __restrict__ bzv,
     const float4* __restrict__ a32, const float4* __restrict__ b32, double C, float lo32,
     float hi32, const uint32_t* __restrict__ idxA, const uint32_t* __restrict__ idxB,
-    const uint32_t* __restrict__ cellsA, const uint32_t* __restrict__ cellsB, PairSink sink) {
+    const uint32_t* __restrict__ cellsA, const uint32_t* __restrict__ cellsB, PairSink sink,
+    uint32_t sparse_cell) {
   const uint64_t stride = (uint64_t)gridDim.x * kThreads;
   unsigned long long ntest = 0, ndup = 0;
   // every thread of the warp runs the same number of outer iterations
@@ -225,48 +305,70 @@ __global__ void __launch_bounds__(kThreads) k_pair(
         m = 1;
       } else {
         uint32_t P = cell >> bix.shift;
-        coarse = bix.shift > 0 && __ldg(bix.table + P + 1) - __ldg(bix.table + P) <= kSparseCell;
+        coarse = FP32 && bix.shift > 0 &&
+                 __ldg(bix.table + P + 1) - __ldg(bix.table + P) <= sparse_cell;
         m = coarse ? cell_neighbourhood(P, order - bix.shift / 2, nb)
                    : cell_neighbourhood(cell, order, nb);
       }
     }
-    const int nslot = QUAD ? 1 : 9;
-    for (int s = 0; s < nslot; ++s) {
+    // all ranges first (independent loads in flight together), then one
+    // warp-uniform loop over the lane's concatenated candidate list
+    constexpr int NS = QUAD ? 1 : 9;
+    uint32_t rb[NS], re[NS];
+    uint32_t total = 0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
       uint2 r = make_uint2(0u, 0u);
       if (s < m)
         r = coarse ? make_uint2(__ldg(bix.table + nb[s]), __ldg(bix.table + nb[s] + 1))
                    : cell_range(bix, nb[s]);
-      uint32_t len = r.y - r.x;
-      ntest += len;
-      uint32_t maxlen = __reduce_max_sync(0xffffffffu, len);
-      for (uint32_t t = 0; t < maxlen; ++t) {
-        bool act = t < len;
-        uint32_t j = r.x + t;
-        bool hit = false, band = false;
-        if (act) {
-          if (FP32) {
-            float4 b = b32[j];
-            float dx = a4.x - b.x, dy = a4.y - b.y, dz = a4.z - b.z;
-            float s2 = dx * dx;
-            s2 = fmaf(dy, dy, s2);
-            s2 = fmaf(dz, dz, s2);
-            hit = s2 <= lo32;
-            band = !hit && s2 <= hi32;
-          } else {
-            double s2 = c_chord2(ax, ay, az, bxv[j], byv[j], bzv[j]);
-            hit = s2 <= C;
+      rb[s] = r.x;
+      re[s] = r.y;
+      total += r.y - r.x;
+    }
+    ntest += total;
+    const uint32_t maxT = __reduce_max_sync(0xffffffffu, total);
+    uint32_t cur = rb[0], end = re[0];
+    for (uint32_t t = 0; t < maxT; ++t) {
+      bool act = t < total;
+      uint32_t j = 0;
+      bool hit = false, band = false;
+      if (act) {
+        while (cur >= end) {  // next non-empty range (constant-index shift)
+#pragma unroll
+          for (int i = 0; i + 1 < NS; ++i) {
+            rb[i] = rb[i + 1];
+            re[i] = re[i + 1];
           }
-          if (QUAD && (hit || band)) {
-            uint32_t own = quad_owner(cellsA + 5ull * idxA[k], cellsB + 5ull * idxB[j]);
-            if (own != cell) {
-              if (hit) ++ndup;
-              hit = false;
-              band = false;
-            }
+          cur = rb[0];
+          end = re[0];
+        }
+        j = cur++;
+        if (FP32) {
+          float4 b = __ldg(b32 + j);
+          float dx = a4.x - b.x, dy = a4.y - b.y, dz = a4.z - b.z;
+          float s2 = dx * dx;
+          s2 = fmaf(dy, dy, s2);
+          s2 = fmaf(dz, dz, s2);
+          hit = s2 <= lo32;
+          band = !hit && s2 <= hi32;
+        } else {
+          double s2 = c_chord2(ax, ay, az, bxv[j], byv[j], bzv[j]);
+          hit = s2 <= C;
+        }
+        if (QUAD && (hit || band)) {
+          uint32_t own = quad_owner(cellsA + 5ull * idxA[k], cellsB + 5ull * idxB[j]);
+          if (own != cell) {
+            if (hit) ++ndup;
+            hit = false;
+            band = false;
           }
         }
+      }
+      if (__any_sync(0xffffffffu, hit || band)) {
         warp_emit(hit, (uint32_t)k, j, sink.rows, sink.count, sink.cap, sink.err);
-        if (FP32) warp_emit(band, (uint32_t)k, j, sink.band, sink.band_count, sink.band_cap, sink.err);
+        if (FP32)
+          warp_emit(band, (uint32_t)k, j, sink.band, sink.band_count, sink.band_cap, sink.err);
       }
     }
   }
@@ -285,10 +387,8 @@ __global__ void __launch_bounds__(kThreads) k_pair(
 // the canonical arithmetic from the original coordinates).
 __global__ void __launch_bounds__(kThreads) k_recheck(
     const uint2* __restrict__ band, const unsigned long long* __restrict__ nband_dev,
-    uint64_t band_cap, const uint32_t* __restrict__ idxA, const uint32_t* __restrict__ idxB,
-    const double* __restrict__ raA, const double* __restrict__ decA,
-    const double* __restrict__ raB, const double* __restrict__ decB, double C, uint2* rows,
-    unsigned long long* count, uint64_t cap, int* err) {
+    uint64_t band_cap, const double2* __restrict__ rdA, const double2* __restrict__ rdB,
+    double C, uint2* rows, unsigned long long* count, uint64_t cap, int* err) {
   uint64_t nb = *nband_dev;
   if (nb > band_cap) nb = band_cap;
   for (uint64_t b0 = (uint64_t)blockIdx.x * kThreads; b0 < nb; b0 += (uint64_t)gridDim.x * kThreads) {
@@ -297,10 +397,10 @@ __global__ void __launch_bounds__(kThreads) k_recheck(
     uint2 p = make_uint2(0u, 0u);
     if (q < nb) {
       p = band[q];
-      uint32_t ia = idxA[p.x], ib = idxB[p.y];
+      double2 a = rdA[p.x], b = rdB[p.y];
       double ax, ay, az, bx, by, bz;
-      c_unitvec(c_norm_ra(raA[ia]), decA[ia], &ax, &ay, &az);
-      c_unitvec(c_norm_ra(raB[ib]), decB[ib], &bx, &by, &bz);
+      c_unitvec(a.x, a.y, &ax, &ay, &az);
+      c_unitvec(b.x, b.y, &bx, &by, &bz);
       hit = c_chord2(ax, ay, az, bx, by, bz) <= C;
     }
     warp_emit(hit, p.x, p.y, rows, count, cap, err);

@@ -95,39 +95,35 @@ __device__ __forceinline__ double sep_arcsec_f2(double ra1, double dec1, double 
   return (double)r.hi + (double)r.lo;
 }
 
-// ids + separation of each row, and the bucket histogram of id_a.
+// ids + separation of each row (from the entry-ordered arrays, which rows
+// visit with good locality), and the bucket histogram of id_a.
 template <bool FP32>
 __global__ void k_rows(const uint2* __restrict__ rows, uint64_t M,
-                       const uint32_t* __restrict__ idxA, const uint32_t* __restrict__ idxB,
                        const uint64_t* __restrict__ idA, const uint64_t* __restrict__ idB,
                        const double* __restrict__ axv, const double* __restrict__ ayv,
                        const double* __restrict__ azv, const double* __restrict__ bxv,
                        const double* __restrict__ byv, const double* __restrict__ bzv,
-                       const double* __restrict__ raA, const double* __restrict__ decA,
-                       const double* __restrict__ raB, const double* __restrict__ decB,
+                       const double2* __restrict__ rdA, const double2* __restrict__ rdB,
                        int want_sep, uint64_t* __restrict__ ka, uint64_t* __restrict__ kb,
                        double* __restrict__ sep, int bshift, uint32_t bmask,
                        uint32_t* __restrict__ bhist) {
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
        m += (uint64_t)gridDim.x * blockDim.x) {
     uint2 p = rows[m];
-    uint32_t ia = idxA[p.x], ib = idxB[p.y];
-    uint64_t a = idA[ia];
+    uint64_t a = idA[p.x];
     ka[m] = a;
-    kb[m] = idB[ib];
+    kb[m] = idB[p.y];
     if (bhist) atomicAdd(&bhist[(uint32_t)(a >> bshift) & bmask], 1u);
     if (want_sep) {
       double sv;
       if (FP32) {
-        double a1 = raA[ia], a2 = raB[ib];
-        if (!bits_in_ra_range(a1)) a1 = c_norm_ra(a1);
-        if (!bits_in_ra_range(a2)) a2 = c_norm_ra(a2);
-        sv = sep_arcsec_f2(a1, decA[ia], a2, decB[ib]);
-        if (sv < 0.0) sv = sep_arcsec_haversine(a1, decA[ia], a2, decB[ib]);
-      }
-      else
+        double2 u = rdA[p.x], w = rdB[p.y];
+        sv = sep_arcsec_f2(u.x, u.y, w.x, w.y);
+        if (sv < 0.0) sv = sep_arcsec_haversine(u.x, u.y, w.x, w.y);
+      } else {
         sv = sep_arcsec_from_chord2(
             c_chord2(axv[p.x], ayv[p.x], azv[p.x], bxv[p.y], byv[p.y], bzv[p.y]));
+      }
       sep[m] = sv;
     }
   }

@@ -95,8 +95,19 @@ struct SweepSmem {
 // One digit pass: rank each tile's keys by digit (stable), obtain the tile's
 // global offset per digit by decoupled look-back over earlier tiles, and write
 // the tile out grouped by digit (coalesced within each digit run).
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// (The look-back words carry their value and flag in one 64-bit word, so
+// relaxed accesses suffice: no other data is published through them.)
 template <typename K>
-__global__ void __launch_bounds__(kBlock) k_onesweep(
+__global__ void __launch_bounds__(kBlock, 4) k_onesweep(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, uint64_t n, int shift, const uint32_t* __restrict__ goff,
     unsigned long long* __restrict__ lookback, uint32_t* __restrict__ tile_ctr,
@@ -112,36 +123,29 @@ __global__ void __launch_bounds__(kBlock) k_onesweep(
   const uint64_t wbase = base + (uint64_t)warp * (kIpt * 32);
 
   K k[kIpt];
-  uint32_t v[kIpt];
-  int d[kIpt];
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
     uint64_t e = wbase + (uint64_t)i * 32 + lane;
-    if (e < n) {
-      k[i] = kin[e];
-      v[i] = vin[e];
-      d[i] = (int)((uint32_t)(k[i] >> shift) & 255u);
-    } else {
-      d[i] = kRadix;  // past the end: not ranked
-    }
+    k[i] = e < n ? kin[e] : K(0);
   }
   uint32_t r[kIpt];
   const unsigned lt = lanemask_lt();
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
     // lanes holding the same digit: intersect the 8 bit-plane ballots
-    bool valid = d[i] < kRadix;
+    bool valid = wbase + (uint64_t)i * 32 + lane < n;
+    uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
     unsigned peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
-      bool bit = (d[i] >> b) & 1;
+      bool bit = (d >> b) & 1;
       unsigned bb = __ballot_sync(0xffffffffu, bit);
       peers &= bit ? bb : ~bb;
     }
-    uint32_t before = valid ? S.whist[warp][d[i]] : 0u;
+    uint32_t before = valid ? S.whist[warp][d] : 0u;
     r[i] = before + __popc(peers & lt);
     __syncwarp();
-    if (valid && lane == __ffs(peers) - 1) S.whist[warp][d[i]] = before + __popc(peers);
+    if (valid && lane == __ffs(peers) - 1) S.whist[warp][d] = before + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
@@ -156,13 +160,13 @@ __global__ void __launch_bounds__(kBlock) k_onesweep(
   unsigned long long excl = 0;
   unsigned long long* slot = lookback + (uint64_t)tile * kRadix + t;
   if (tile == 0) {
-    st_release_u64(slot, kFlagInc | cnt);
+    st_relaxed_u64(slot, kFlagInc | cnt);
   } else {
-    st_release_u64(slot, kFlagAgg | cnt);
+    st_relaxed_u64(slot, kFlagAgg | cnt);
     long long spins = 0;
     int64_t j = (int64_t)tile - 1;
     while (j >= 0) {
-      unsigned long long w = ld_acquire_u64(lookback + (uint64_t)j * kRadix + t);
+      unsigned long long w = ld_relaxed_u64(lookback + (uint64_t)j * kRadix + t);
       unsigned long long flag = w & ~kValMask;
       if (flag == 0) {
         if (++spins > kSpinLimit) {
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(kBlock) k_onesweep(
       if (flag == kFlagInc) break;
       --j;
     }
-    st_release_u64(slot, kFlagInc | (excl + cnt));
+    st_relaxed_u64(slot, kFlagInc | (excl + cnt));
   }
   S.gbase[t] = (unsigned long long)goff[t] + excl;
   unsigned long long dst = block_excl_scan(cnt, S.ws, nullptr);
@@ -184,10 +188,12 @@ __global__ void __launch_bounds__(kBlock) k_onesweep(
 
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
-    if (d[i] < kRadix) {
-      uint32_t pos = S.dstart[d[i]] + S.whist[warp][d[i]] + r[i];
+    uint64_t e = wbase + (uint64_t)i * 32 + lane;
+    if (e < n) {
+      uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
+      uint32_t pos = S.dstart[d] + S.whist[warp][d] + r[i];
       S.keys[pos] = k[i];
-      S.vals[pos] = v[i];
+      S.vals[pos] = vin[e];
     }
   }
   __syncthreads();
