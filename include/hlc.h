@@ -209,6 +209,28 @@ int hlc_unitvec(const double* ra, const double* dec, uint64_t n, double* xyz,
 int hlc_sort_pairs(void* keys, uint32_t* vals, uint64_t n, int key_size,
                    int key_bits, void* stream);
 
+/* Allocation-free variant of hlc_sort_pairs (the paper has no counterpart;
+ * this is a service for callers).  Some callers must not allocate device
+ * memory on the call path: a host application that reserves all device
+ * memory up front for its own allocator, or a latency-critical loop in which
+ * a cudaMalloc/cudaFree (which can synchronise the device) is not acceptable.
+ * This entry point performs the same stable sort, with the same arguments
+ * and results, but takes every temporary buffer from one fixed device array
+ * built into the library (about 17 MB, present on every device that loads
+ * the library until the process exits) and never allocates or frees memory.
+ *   - n is limited to 1,048,576 elements; larger n returns HLC_EINVAL with a
+ *     message naming the limit (use hlc_sort_pairs instead);
+ *   - the first call on a device looks up the array's device address (with
+ *     that device current), so make the first call on each device before any
+ *     stream capture;
+ *   - all calls share the one array: calls that overlap on the GPU (other
+ *     streams, other host threads) race and corrupt each other's results;
+ *     the array keeps the last call's contents, and each call clears what
+ *     must start at zero;
+ *   - synchronises the stream before returning. */
+int hlc_sort_pairs_noalloc(void* keys, uint32_t* vals, uint64_t n, int key_size,
+                           int key_bits, void* stream);
+
 /* Run-length table of sorted uint32 keys: unique keys uniq[0..m) and
  * start[0..m] (start[m] = n); *m_out receives m (host).  uniq and start must
  * hold n and n+1 elements.  Synchronises the stream. */

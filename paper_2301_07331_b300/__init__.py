@@ -109,6 +109,7 @@ def lib():
     L.hlc_quad_cells.argtypes = [P, P, u64, d, i32, P, P, P]
     L.hlc_unitvec.argtypes = [P, P, u64, P, P]
     L.hlc_sort_pairs.argtypes = [P, P, u64, i32, i32, P]
+    L.hlc_sort_pairs_noalloc.argtypes = [P, P, u64, i32, i32, P]
     L.hlc_cell_table.argtypes = [P, u64, P, P, C.POINTER(C.c_uint64), P]
     L.hlc_learned_lookup.argtypes = [P, u64, i32, i32, P, u64, P, P, P]
     _lib = L
@@ -344,6 +345,18 @@ def hlc_sort_pairs(keys: torch.Tensor, vals: torch.Tensor, key_bits: int, stream
     ks = keys.element_size()
     _check(lib().hlc_sort_pairs(_dptr(keys), _dptr(vals), keys.numel(), ks, int(key_bits),
                                 _stream_ptr(stream)))
+    return keys, vals
+
+
+def hlc_sort_pairs_noalloc(keys: torch.Tensor, vals: torch.Tensor, key_bits: int, stream=None):
+    """Same sort as hlc_sort_pairs without any device allocation: for callers
+    that must not allocate on the call path (all temporaries come from a fixed
+    array inside the library; at most 1,048,576 elements; concurrent calls
+    race)."""
+    _require_cuda()
+    ks = keys.element_size()
+    _check(lib().hlc_sort_pairs_noalloc(_dptr(keys), _dptr(vals), keys.numel(), ks,
+                                        int(key_bits), _stream_ptr(stream)))
     return keys, vals
 
 

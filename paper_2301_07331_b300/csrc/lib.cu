@@ -1064,3 +1064,87 @@ int hlc_learned_lookup(const uint32_t* uniq, uint64_t m, int shift, int model,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free radix sort: the same sort as hlc_sort_pairs, with every
+// temporary (alternate key/value buffers, histograms, look-back words and the
+// error word) carved out of one fixed device array compiled into the library.
+// ---------------------------------------------------------------------------
+namespace hlc {
+
+constexpr uint64_t kNoAllocMaxN = 1ull << 20;  // elements per call
+constexpr size_t kNoAllocKeyBytes = kNoAllocMaxN * 8;
+constexpr size_t kNoAllocValBytes = kNoAllocMaxN * 4;
+constexpr size_t kNoAllocSortBytes =
+    kSortLookbackOffset +
+    8ull * ((kNoAllocMaxN + rs::kTile - 1) / rs::kTile) * rs::kRadix * 8;
+constexpr size_t kNoAllocBytes = 256 + kNoAllocKeyBytes + kNoAllocValBytes + kNoAllocSortBytes;
+
+// Lives on every device that loads the library, until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once
+// per device, with that device current).
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  HLC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal %d out of range", dev);
+    return HLC_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+      return HLC_ECUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return HLC_OK;
+}
+
+}  // namespace hlc
+
+extern "C" int hlc_sort_pairs_noalloc(void* keys, uint32_t* vals, uint64_t n, int key_size,
+                                      int key_bits, void* stream) {
+  clear_error();
+  if ((key_size != 4 && key_size != 8) || key_bits < 1 || key_bits > 8 * key_size) {
+    set_error("key_size must be 4 or 8 and key_bits in [1, 8*key_size]");
+    return HLC_EINVAL;
+  }
+  if (n > kNoAllocMaxN) {
+    set_error("hlc_sort_pairs_noalloc: n = %llu exceeds the fixed scratch capacity of %llu "
+              "elements; use hlc_sort_pairs",
+              (unsigned long long)n, (unsigned long long)kNoAllocMaxN);
+    return HLC_EINVAL;
+  }
+  if (n <= 1) return HLC_OK;
+  if (!keys || !vals) {
+    set_error("NULL array");
+    return HLC_EINVAL;
+  }
+  void* base = nullptr;
+  HLC_TRY(noalloc_scratch(&base));
+  cudaStream_t st = (cudaStream_t)stream;
+  char* b = (char*)base;
+  int* err = (int*)b;  // first 256 bytes: the device error word
+  void* tk = b + 256;
+  uint32_t* tv = (uint32_t*)(b + 256 + kNoAllocKeyBytes);
+  void* scr = b + 256 + kNoAllocKeyBytes + kNoAllocValBytes;
+  HLC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  int rc;
+  if (key_size == 4)
+    rc = radix_sort_pairs<uint32_t>((uint32_t*)keys, vals, (uint32_t*)tk, tv, n, key_bits, scr,
+                                    err, st);
+  else
+    rc = radix_sort_pairs<uint64_t>((uint64_t*)keys, vals, (uint64_t*)tk, tv, n, key_bits, scr,
+                                    err, st);
+  if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_sort_pairs_noalloc");
+  return rc;
+}
