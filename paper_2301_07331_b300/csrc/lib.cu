@@ -8,6 +8,7 @@
 #include "common.cuh"
 #include "fp32.cuh"
 #include "index.cuh"
+#include "learned.cuh"
 #include "match.cuh"
 #include "output.cuh"
 #include "scan.cuh"
@@ -102,6 +103,9 @@ int ensure_device_tables() {
   build_neighbour_tables(face, map);
   HLC_CUDA(cudaMemcpyToSymbol(d_nbr_face, face, sizeof(face)));
   HLC_CUDA(cudaMemcpyToSymbol(d_nbr_map, map, sizeof(map)));
+  MlpFixed mf;
+  mlp_fixed_weights(&mf);
+  HLC_CUDA(cudaMemcpyToSymbol(d_mlp, &mf, sizeof(mf)));
   // keep freed stream-ordered allocations cached in the device's default pool
   cudaMemPool_t pool;
   if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
@@ -179,10 +183,16 @@ struct CatDev {
   int table_shift = 0;
   int table_order = 0;
   uint64_t cells = 0;
+  // learned index (catalogue B, HLC_INDEX_LEARNED)
+  uint32_t* uniq = nullptr;
+  uint32_t* start = nullptr;
+  uint64_t u = 0;
+  LearnedIndex learned;
+  uint64_t parts = 0;
 };
 
 enum Ctr { C_ROWS = 0, C_BAND, C_TESTS, C_DUPS, C_M, C_TOTAL, C_HEADS_A, C_HEADS_B,
-           C_IDDIFF, C_MAXB, C_SLOW, C_N };
+           C_IDDIFF, C_MAXB, C_SLOW, C_LHITS, C_LLOOK, C_LMAXERR, C_SCRATCH, C_N };
 
 }  // namespace hlc
 
@@ -281,6 +291,60 @@ static float ev_ms(hlc_plan_t* P, int a, int b) {
   float ms = 0;
   if (P->events) cudaEventElapsedTime(&ms, P->ev[a], P->ev[b]);
   return ms;
+}
+
+// Learned index over sorted unique keys uniq[0..m): partition offsets, the
+// per-partition model and its stored error bound.  P = number of partitions.
+static int build_learned(Arena& ar, const uint32_t* uniq, uint64_t m, int shift, int model,
+                         uint64_t P, unsigned long long* total_dev,
+                         unsigned long long* scratch_ctr, int* dev_err, cudaStream_t st,
+                         LearnedIndex* out) {
+  uint32_t* hist = ar.get_n<uint32_t>(P + 1);
+  uint32_t* part = ar.get_n<uint32_t>(P + 1);
+  uint32_t* err = ar.get_n<uint32_t>(P + 1);
+  void* scr = ar.get(scan_scratch_bytes(P + 1));
+  if (!hist || !part || !err || !scr) return HLC_ENOMEM;
+  HLC_CUDA(cudaMemsetAsync(hist, 0, (P + 1) * 4, st));
+  HLC_CUDA(cudaMemsetAsync(err, 0, (P + 1) * 4, st));
+  if (m) {
+    k_coarse_hist<<<grid_for(m, kThreads), kThreads, 0, st>>>(uniq, m, shift, hist, scratch_ctr);
+    HLC_LAUNCH_CHECK();
+  }
+  HLC_TRY(scan_exclusive<uint32_t>(hist, part, P + 1, total_dev, scr, dev_err, st));
+  ar.drop(hist);
+  ar.drop(scr);
+  LearnedIndex L;
+  L.uniq = uniq;
+  L.part = part;
+  L.err = err;
+  L.shift = shift;
+  L.model = model;
+  L.nparts = P;
+  if (model == HLC_MODEL_PLA) {
+    float* knots = ar.get_n<float>(P * (kPlaSeg + 1) + 1);
+    if (!knots) return HLC_ENOMEM;
+    HLC_CUDA(cudaMemsetAsync(knots, 0, (P * (kPlaSeg + 1) + 1) * 4, st));
+    if (m) {
+      k_pla_hist<<<grid_for(m, kThreads), kThreads, 0, st>>>(uniq, m, shift, knots);
+      HLC_LAUNCH_CHECK();
+    }
+    k_pla_knots<<<grid_for(P, kThreads), kThreads, 0, st>>>(knots, P);
+    HLC_LAUNCH_CHECK();
+    L.knots = knots;
+  } else {
+    float* w3 = ar.get_n<float>(P * (kMlpH + 1) + 1);
+    if (!w3) return HLC_ENOMEM;
+    k_mlp_fit<<<(unsigned)std::min<uint64_t>(P, 148u * 8u), 256, 0, st>>>(uniq, part, P, shift,
+                                                                          w3);
+    HLC_LAUNCH_CHECK();
+    L.w3 = w3;
+  }
+  if (m) {
+    k_learned_err<<<grid_for(m, kThreads), kThreads, 0, st>>>(L, m, err);
+    HLC_LAUNCH_CHECK();
+  }
+  *out = L;
+  return HLC_OK;
 }
 
 // Copy one catalogue in, build its sorted entries, payload and (for B) the
@@ -417,7 +481,33 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     ar.drop(tid);
   }
   unsigned long long* heads = P->ctr + (is_b ? C_HEADS_B : C_HEADS_A);
-  if (is_b) {
+  if (is_b && P->p.index == HLC_INDEX_LEARNED) {
+    // unique cells of B, then the per-partition models over them
+    HLC_ALLOC(ar, X.uniq, uint32_t, m + 1);
+    HLC_ALLOC(ar, X.start, uint32_t, m + 2);
+    uint32_t* cell_of = ar.get_n<uint32_t>(m + 1);
+    void* scr = ar.get(scan_scratch_bytes(m));
+    if (!cell_of || !scr) return HLC_ENOMEM;
+    HLC_TRY(cell_table(X.key, m, 0, cell_of, X.uniq, X.start, P->ctr + C_M, scr, P->dev_err, st));
+    unsigned long long u = 0;
+    HLC_CUDA(cudaMemcpyAsync(&u, P->ctr + C_M, 8, cudaMemcpyDeviceToHost, st));
+    HLC_CUDA(cudaStreamSynchronize(st));
+    X.u = u;
+    ar.drop(cell_of);
+    ar.drop(scr);
+    const int Lc = P->p.coarse_level;
+    X.parts = 12ull << (2 * Lc);
+    HLC_TRY(build_learned(ar, X.uniq, X.u, 2 * (L - Lc), P->p.model, X.parts, P->ctr + C_TOTAL,
+                          P->ctr + C_SCRATCH, P->dev_err, st, &X.learned));
+    HLC_CUDA(cudaMemsetAsync(P->ctr + C_LMAXERR, 0, 8, st));
+    k_max_u32<<<grid_for(X.parts, kThreads, 1024), kThreads, 0, st>>>(
+        X.learned.err, X.parts, (uint32_t*)(P->ctr + C_LMAXERR));
+    HLC_LAUNCH_CHECK();
+    if (m) {
+      k_coarse_hist<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.key, m, 0, nullptr, heads);
+      HLC_LAUNCH_CHECK();
+    }
+  } else if (is_b) {
     X.table_order = coarse_table_order(m, L);
     X.table_shift = 2 * (L - X.table_order);
     uint64_t tsize = 12ull << (2 * X.table_order);
@@ -525,6 +615,8 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   P->stats.entries_b = P->B.m;
   P->stats.cells_a = hc[C_HEADS_A];
   P->stats.cells_b = hc[C_HEADS_B];
+  P->stats.learned_models = P->p.index == HLC_INDEX_LEARNED ? P->B.parts : 0;
+  P->stats.learned_max_err = (uint32_t)hc[C_LMAXERR];
   P->stats.join_level = P->join_level;
   P->stats.ms_prep = t[0] + t[1];
   P->stats.ms_sort = t[2] + t[3];
@@ -596,23 +688,41 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
                   P->ctr + C_TESTS, P->ctr + C_DUPS, P->dev_err};
     if (A.m && B.m) {
       unsigned grid = grid_for(A.m, kThreads, 148u * 16u);
-      const int L = P->join_level;
-      if (fp32 && quad)
-        k_pair<true, true><<<grid, kThreads, 0, st>>>(
-            A.m, A.key, bix, L, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, A.v32,
-            B.v32, P->C, P->lo32, P->hi32, A.idx, B.idx, A.cells5, B.cells5, sink, P->sparse_cell);
-      else if (fp32)
-        k_pair<true, false><<<grid, kThreads, 0, st>>>(
-            A.m, A.key, bix, L, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, A.v32,
-            B.v32, P->C, P->lo32, P->hi32, A.idx, B.idx, nullptr, nullptr, sink, P->sparse_cell);
-      else if (quad)
-        k_pair<false, true><<<grid, kThreads, 0, st>>>(
-            A.m, A.key, bix, L, A.vx, A.vy, A.vz, B.vx, B.vy, B.vz, nullptr, nullptr, P->C, 0.f,
-            0.f, A.idx, B.idx, A.cells5, B.cells5, sink, P->sparse_cell);
-      else
-        k_pair<false, false><<<grid, kThreads, 0, st>>>(
-            A.m, A.key, bix, L, A.vx, A.vy, A.vz, B.vx, B.vy, B.vz, nullptr, nullptr, P->C, 0.f,
-            0.f, A.idx, B.idx, nullptr, nullptr, sink, P->sparse_cell);
+      PairArgs pa;
+      pa.mA = A.m;
+      pa.keyA = A.key;
+      pa.bix = bix;
+      pa.lix = B.learned;
+      pa.uniqB = B.uniq;
+      pa.startB = B.start;
+      pa.uB = B.u;
+      pa.order = P->join_level;
+      pa.axv = A.vx; pa.ayv = A.vy; pa.azv = A.vz;
+      pa.bxv = B.vx; pa.byv = B.vy; pa.bzv = B.vz;
+      pa.a32 = A.v32;
+      pa.b32 = B.v32;
+      pa.C = P->C;
+      pa.lo32 = P->lo32;
+      pa.hi32 = P->hi32;
+      pa.idxA = A.idx;
+      pa.idxB = B.idx;
+      pa.cellsA = A.cells5;
+      pa.cellsB = B.cells5;
+      pa.sparse_cell = P->sparse_cell;
+      pa.lhits = P->ctr + C_LHITS;
+      pa.llook = P->ctr + C_LLOOK;
+      const bool learned = P->p.index == HLC_INDEX_LEARNED;
+#define HLC_PAIR(F, Q, LR) k_pair<F, Q, LR><<<grid, kThreads, 0, st>>>(pa, sink)
+      if (fp32 && quad) {
+        if (learned) HLC_PAIR(true, true, true); else HLC_PAIR(true, true, false);
+      } else if (fp32) {
+        if (learned) HLC_PAIR(true, false, true); else HLC_PAIR(true, false, false);
+      } else if (quad) {
+        if (learned) HLC_PAIR(false, true, true); else HLC_PAIR(false, true, false);
+      } else {
+        if (learned) HLC_PAIR(false, false, true); else HLC_PAIR(false, false, false);
+      }
+#undef HLC_PAIR
       HLC_LAUNCH_CHECK();
     }
     HLC_CUDA(cudaMemcpyAsync(h, P->ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -736,6 +846,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   P->stats.band_candidates = fp32 ? h[C_BAND] : 0;
   P->stats.matches = M;
   P->stats.quad_duplicates = h[C_DUPS];
+  P->stats.learned_hit_rate = h[C_LLOOK] ? (double)h[C_LHITS] / (double)h[C_LLOOK] : 0.0;
   P->stats.ms_candidates = ev_ms(P, 2, 3);
   P->stats.ms_pair = ev_ms(P, 3, 4);
   P->stats.ms_recheck = ev_ms(P, 4, 5);
@@ -1056,11 +1167,67 @@ int hlc_cell_table(const uint32_t* keys, uint64_t n, uint32_t* uniq, uint32_t* s
 int hlc_learned_lookup(const uint32_t* uniq, uint64_t m, int shift, int model,
                        const uint32_t* queries, uint64_t nq, uint32_t* out, hlc_stats* stats,
                        void* stream) {
-  (void)uniq; (void)m; (void)shift; (void)model; (void)queries; (void)nq; (void)out;
-  (void)stats; (void)stream;
   clear_error();
-  set_error("learned index not available in this build");
-  return HLC_EUNSUPPORTED;
+  if (shift < 0 || shift > 24 || (model != HLC_MODEL_PLA && model != HLC_MODEL_MLP)) {
+    set_error("shift must be in [0, 24] and model HLC_MODEL_PLA or HLC_MODEL_MLP");
+    return HLC_EINVAL;
+  }
+  if ((m && !uniq) || (nq && (!queries || !out))) {
+    set_error("NULL array");
+    return HLC_EINVAL;
+  }
+  HLC_TRY(ensure_device_tables());
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t last = 0;
+  if (m) {
+    HLC_CUDA(cudaMemcpyAsync(&last, uniq + m - 1, 4, cudaMemcpyDeviceToHost, st));
+    HLC_CUDA(cudaStreamSynchronize(st));
+  }
+  uint64_t P = (uint64_t)(last >> shift) + 1;
+  Allocator al;
+  al.stream = st;
+  Arena ar(al);
+  int* err = ar.get_n<int>(16);
+  unsigned long long* ctr = ar.get_n<unsigned long long>(8);
+  if (!err || !ctr) return HLC_ENOMEM;
+  HLC_CUDA(cudaMemsetAsync(err, 0, 64, st));
+  HLC_CUDA(cudaMemsetAsync(ctr, 0, 64, st));
+  cudaEvent_t e0, e1, e2;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventCreate(&e2);
+  cudaEventRecord(e0, st);
+  LearnedIndex L;
+  int rc = build_learned(ar, uniq, m, shift, model, P, ctr, ctr + 1, err, st, &L);
+  cudaEventRecord(e1, st);
+  if (rc == HLC_OK && nq) {
+    k_learned_lookup<<<grid_for(nq, kThreads), kThreads, 0, st>>>(L, queries, nq, out, ctr + 2);
+    if (cudaGetLastError() != cudaSuccess) rc = HLC_ECUDA;
+  }
+  cudaEventRecord(e2, st);
+  unsigned long long h[8] = {0};
+  uint32_t maxerr = 0;
+  if (rc == HLC_OK) {
+    HLC_CUDA(cudaMemsetAsync(ctr + 3, 0, 8, st));
+    k_max_u32<<<grid_for(P, kThreads, 1024), kThreads, 0, st>>>(L.err, P, (uint32_t*)(ctr + 3));
+    HLC_CUDA(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
+    rc = check_dev_err(err, st, "hlc_learned_lookup");
+    maxerr = (uint32_t)h[3];
+  }
+  if (rc == HLC_OK && stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->learned_models = P;
+    stats->learned_max_err = maxerr;
+    stats->learned_hit_rate = nq ? (double)h[2] / (double)nq : 1.0;
+    cudaEventElapsedTime(&stats->ms_index, e0, e1);
+    cudaEventElapsedTime(&stats->ms_candidates, e1, e2);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  ar.release();
+  cudaStreamSynchronize(st);
+  return rc;
 }
 
 }  // extern "C"

@@ -9,6 +9,7 @@
 #include "fastpix.cuh"
 #include "fp32.cuh"
 #include "index.cuh"
+#include "learned.cuh"
 
 namespace hlc {
 
@@ -266,15 +267,46 @@ __device__ __forceinline__ uint32_t quad_owner(const uint32_t* __restrict__ ca,
   return own;
 }
 
-template <bool FP32, bool QUAD>
-__global__ void __launch_bounds__(kThreads) k_pair(
-    uint64_t mA, const uint32_t* __restrict__ keyA, CellIndex bix, int order,
-    const double* __restrict__ axv, const double* __restrict__ ayv, const double* __restrict__ azv,
-    const double* __restrict__ bxv, const double* __restrict__ byv, const double* __restrict__ bzv,
-    const float4* __restrict__ a32, const float4* __restrict__ b32, double C, float lo32,
-    float hi32, const uint32_t* __restrict__ idxA, const uint32_t* __restrict__ idxB,
-    const uint32_t* __restrict__ cellsA, const uint32_t* __restrict__ cellsB, PairSink sink,
-    uint32_t sparse_cell) {
+struct PairArgs {
+  uint64_t mA;
+  const uint32_t* keyA;
+  CellIndex bix;          // offset table of B (table index)
+  LearnedIndex lix;       // learned index over B's unique cells
+  const uint32_t* uniqB;  // (learned index) unique cells of B
+  const uint32_t* startB; // (learned index) their first entries
+  uint64_t uB;
+  int order;
+  const double *axv, *ayv, *azv, *bxv, *byv, *bzv;
+  const float4 *a32, *b32;
+  double C;
+  float lo32, hi32;
+  const uint32_t *idxA, *idxB, *cellsA, *cellsB;
+  uint32_t sparse_cell;
+  unsigned long long *lhits, *llook;
+};
+
+template <bool FP32, bool QUAD, bool LEARNED>
+__global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink sink) {
+  const uint64_t mA = pa.mA;
+  const uint32_t* __restrict__ keyA = pa.keyA;
+  const CellIndex bix = pa.bix;
+  const int order = pa.order;
+  const double* __restrict__ axv = pa.axv;
+  const double* __restrict__ ayv = pa.ayv;
+  const double* __restrict__ azv = pa.azv;
+  const double* __restrict__ bxv = pa.bxv;
+  const double* __restrict__ byv = pa.byv;
+  const double* __restrict__ bzv = pa.bzv;
+  const float4* __restrict__ a32 = pa.a32;
+  const float4* __restrict__ b32 = pa.b32;
+  const double C = pa.C;
+  const float lo32 = pa.lo32, hi32 = pa.hi32;
+  const uint32_t* __restrict__ idxA = pa.idxA;
+  const uint32_t* __restrict__ idxB = pa.idxB;
+  const uint32_t* __restrict__ cellsA = pa.cellsA;
+  const uint32_t* __restrict__ cellsB = pa.cellsB;
+  const uint32_t sparse_cell = pa.sparse_cell;
+  unsigned long long nlhit = 0, nllook = 0;
   const uint64_t stride = (uint64_t)gridDim.x * kThreads;
   unsigned long long ntest = 0, ndup = 0;
   // every thread of the warp runs the same number of outer iterations
@@ -305,7 +337,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(
         m = 1;
       } else {
         uint32_t P = cell >> bix.shift;
-        coarse = FP32 && bix.shift > 0 &&
+        coarse = FP32 && !LEARNED && bix.shift > 0 &&
                  __ldg(bix.table + P + 1) - __ldg(bix.table + P) <= sparse_cell;
         m = coarse ? cell_neighbourhood(P, order - bix.shift / 2, nb)
                    : cell_neighbourhood(cell, order, nb);
@@ -319,9 +351,19 @@ __global__ void __launch_bounds__(kThreads) k_pair(
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       uint2 r = make_uint2(0u, 0u);
-      if (s < m)
-        r = coarse ? make_uint2(__ldg(bix.table + nb[s]), __ldg(bix.table + nb[s] + 1))
-                   : cell_range(bix, nb[s]);
+      if (s < m) {
+        if (LEARNED) {
+          bool hit;
+          uint32_t pos = learned_lower_bound(pa.lix, nb[s], &hit);
+          nlhit += hit;
+          ++nllook;
+          if (pos < pa.uB && __ldg(pa.uniqB + pos) == nb[s])
+            r = make_uint2(__ldg(pa.startB + pos), __ldg(pa.startB + pos + 1));
+        } else {
+          r = coarse ? make_uint2(__ldg(bix.table + nb[s]), __ldg(bix.table + nb[s] + 1))
+                     : cell_range(bix, nb[s]);
+        }
+      }
       rb[s] = r.x;
       re[s] = r.y;
       total += r.y - r.x;
@@ -376,10 +418,18 @@ __global__ void __launch_bounds__(kThreads) k_pair(
   for (int o = 16; o > 0; o >>= 1) {
     ntest += __shfl_down_sync(0xffffffffu, ntest, o);
     ndup += __shfl_down_sync(0xffffffffu, ndup, o);
+    if (LEARNED) {
+      nlhit += __shfl_down_sync(0xffffffffu, nlhit, o);
+      nllook += __shfl_down_sync(0xffffffffu, nllook, o);
+    }
   }
   if ((threadIdx.x & 31) == 0) {
     if (ntest) atomicAdd(sink.tests, ntest);
     if (ndup) atomicAdd(sink.dups, ndup);
+    if (LEARNED && nllook) {
+      atomicAdd(pa.lhits, nlhit);
+      atomicAdd(pa.llook, nllook);
+    }
   }
 }
 
