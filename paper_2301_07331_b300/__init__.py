@@ -241,6 +241,37 @@ def hlc_plan(A, B, radius_arcsec: float, fine_level: int, coarse_level: int | No
     return Plan(h, p, alloc, (keepA, keepB))
 
 
+def hlc_plan_batched(jobs, precision: int = HLC_FP32_GUARD, want_sep: bool = True,
+                     stream=None, torch_alloc: bool = False) -> Plan:
+    """One plan over many independent jobs.  jobs: sequence of dicts with keys
+    A, B ((ra, dec, id) triples or catalogue objects), radius_arcsec and
+    fine_level (-1 = chosen by the library from the job's density)."""
+    _require_cuda()
+    L = lib()
+    n = len(jobs)
+    cats_a = (Catalog * n)()
+    cats_b = (Catalog * n)()
+    params = (Params * n)()
+    keep = []
+    st = _stream_ptr(stream)
+    dev = torch.cuda.current_device()
+    alloc = _TorchAllocator(dev, st) if torch_alloc else None
+    for i, jb in enumerate(jobs):
+        ca, ka = _catalog(*_triple(jb["A"]))
+        cb, kb = _catalog(*_triple(jb["B"]))
+        cats_a[i] = ca
+        cats_b[i] = cb
+        keep.append((ka, kb))
+        fl = int(jb.get("fine_level", -1))
+        params[i] = Params(float(jb["radius_arcsec"]), 0, fl, HLC_COMPLETE8, int(precision),
+                           HLC_INDEX_BSEARCH, HLC_MODEL_PLA, int(bool(want_sep)), 0, st,
+                           alloc.alloc if alloc else _ALLOC_FN(),
+                           alloc.dealloc if alloc else _DEALLOC_FN(), None)
+    h = C.c_void_p()
+    _check(L.hlc_plan(cats_a, cats_b, params, n, C.byref(h)))
+    return Plan(h, params[0], alloc, (keep, cats_a, cats_b, params))
+
+
 def _triple(X):
     if isinstance(X, (tuple, list)):
         return X

@@ -1,0 +1,451 @@
+// Batched cross-match: many independent (A, B, r, order) jobs of uneven size
+// matched by one fixed launch sequence.
+//
+// Every entry carries a composite key (job << cell_bits) | cell, so one radix
+// sort groups all jobs' entries by job and, inside a job, by cell.  Catalogue
+// B of job j gets its own offset table over the cell range it actually
+// occupies, at order L_j - k_j with k_j chosen so the table has about as many
+// slots as the job has sources; all tables live in one array whose global
+// exclusive scan gives absolute entry offsets directly.  The pair test is one
+// persistent launch in which warps pull chunks of A entries from an atomic
+// work counter, so heavy and light jobs share the GPU without per-job
+// launches.  Complete 8-neighbour mode.
+#pragma once
+
+#include "canon.cuh"
+#include "common.cuh"
+#include "fastpix.cuh"
+#include "fp32.cuh"
+#include "match.cuh"
+#include "output.cuh"
+
+namespace hlc {
+
+struct JobDev {
+  const double* ra[2];   // [0] = A, [1] = B
+  const double* dec[2];
+  const uint64_t* id[2];
+  uint64_t n[2];         // sources of A and B
+  uint64_t off[2];       // first global entry of A and B
+  int L;                 // fine order of the job
+  PixConst K;
+  double C;              // canonical chord^2 threshold
+  float lo32, hi32;      // guard band
+  uint64_t toff;         // first slot of the job's B table
+  uint32_t tbase;        // first coarse cell covered (order L - tk)
+  uint32_t tsize;        // coarse cells covered + 1
+  int tk;                // table order = L - tk
+};
+
+// Job of global entry i on side s (offsets ascending, njobs + 1 of them).
+__device__ __forceinline__ uint32_t job_of(const uint64_t* __restrict__ off, uint32_t njobs,
+                                           uint64_t i) {
+  uint32_t lo = 0, hi = njobs;  // find last j with off[j] <= i
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= i)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+template <bool FAST>
+__global__ void k_bprep_keys(const JobDev* __restrict__ jobs, const uint64_t* __restrict__ off,
+                             uint32_t njobs, int side, uint64_t total, int cell_bits,
+                             uint64_t* __restrict__ key, uint32_t* __restrict__ idx,
+                             uint32_t* __restrict__ slow, unsigned long long* __restrict__ nslow,
+                             int* __restrict__ err) {
+  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < total;
+       i0 += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t i = i0 + threadIdx.x;
+    bool defer = false;
+    if (i < total) {
+      uint32_t j = job_of(off, njobs, i);
+      const JobDev& J = jobs[j];
+      uint64_t l = i - J.off[side];
+      double a = J.ra[side][l], d = J.dec[side][l];
+      uint32_t k = 0;
+      if (!(bits_finite(a) && bits_abs_le(d, 90.0))) {
+        atomicOr(err, DERR_INPUT);
+      } else {
+        if (!bits_in_ra_range(a)) a = c_norm_ra(a);
+        if (FAST) {
+          FastDec fd = f_dec_part(split_f64(d));
+          defer = !f_pix(split_f64(a), fd, J.L, J.K, &k);
+        } else {
+          k = c_ang2pix(a, d, J.L);
+        }
+      }
+      key[i] = ((uint64_t)j << cell_bits) | k;
+      idx[i] = (uint32_t)i;
+    }
+    if (FAST) {
+      unsigned b = __ballot_sync(0xffffffffu, defer);
+      if (b) {
+        int lane = threadIdx.x & 31;
+        unsigned long long base = 0;
+        if (lane == __ffs(b) - 1) base = atomicAdd(nslow, (unsigned long long)__popc(b));
+        base = __shfl_sync(0xffffffffu, base, __ffs(b) - 1);
+        if (defer) slow[base + __popc(b & lanemask_lt())] = (uint32_t)i;
+      }
+    }
+  }
+}
+
+__global__ void k_bprep_fallback(const JobDev* __restrict__ jobs, const uint64_t* __restrict__ off,
+                                 uint32_t njobs, int side, int cell_bits,
+                                 const uint32_t* __restrict__ slow,
+                                 const unsigned long long* __restrict__ nslow,
+                                 uint64_t* __restrict__ key) {
+  uint64_t ns = *nslow;
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns;
+       q += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t i = slow[q];
+    uint32_t j = job_of(off, njobs, i);
+    const JobDev& J = jobs[j];
+    uint64_t l = i - J.off[side];
+    key[i] = ((uint64_t)j << cell_bits) | c_ang2pix(c_norm_ra(J.ra[side][l]), J.dec[side][l], J.L);
+  }
+}
+
+template <bool FP32>
+__global__ void k_bpayload(const JobDev* __restrict__ jobs, const uint64_t* __restrict__ off,
+                           uint32_t njobs, int side, const uint32_t* __restrict__ idx, uint64_t m,
+                           float4* __restrict__ v32, double2* __restrict__ rd,
+                           double* __restrict__ vx, double* __restrict__ vy,
+                           double* __restrict__ vz, uint64_t* __restrict__ id_s) {
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t i = idx[e];
+    uint32_t j = job_of(off, njobs, i);
+    const JobDev& J = jobs[j];
+    uint64_t l = i - J.off[side];
+    double a = J.ra[side][l], d = J.dec[side][l];
+    if (!bits_in_ra_range(a)) a = c_norm_ra(a);
+    if (FP32) {
+      v32[e] = fp32_unitvec(a, d);
+      rd[e] = make_double2(a, d);
+    } else {
+      double x, y, z;
+      c_unitvec(a, d, &x, &y, &z);
+      vx[e] = x;
+      vy[e] = y;
+      vz[e] = z;
+    }
+    id_s[e] = J.id[side][l];
+  }
+}
+
+// Autotuner inputs, per job: the sum of the B unit vectors (FP32) and, in a
+// second pass, the smallest cosine between a B source and the job's mean
+// direction -- the spherical cap the job's B catalogue occupies.
+__global__ void k_bjob_mean(const JobDev* __restrict__ jobs, const uint64_t* __restrict__ off,
+                            uint32_t njobs, uint64_t total, float* __restrict__ acc) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t j = job_of(off, njobs, i);
+    const JobDev& J = jobs[j];
+    uint64_t l = i - J.off[1];
+    double a = J.ra[1][l], d = J.dec[1][l];
+    if (!(bits_finite(a) && bits_abs_le(d, 90.0))) continue;
+    if (!bits_in_ra_range(a)) a = c_norm_ra(a);
+    float4 u = fp32_unitvec(a, d);
+    atomicAdd(acc + 3 * j, u.x);
+    atomicAdd(acc + 3 * j + 1, u.y);
+    atomicAdd(acc + 3 * j + 2, u.z);
+  }
+}
+
+// (mind: a float's bit pattern orders like the value for non-negative
+// floats; 1 - cos is stored, so the maximum is taken with integer atomics)
+__global__ void k_bjob_cap(const JobDev* __restrict__ jobs, const uint64_t* __restrict__ off,
+                           uint32_t njobs, uint64_t total, const float* __restrict__ dir,
+                           unsigned int* __restrict__ cap) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t j = job_of(off, njobs, i);
+    const JobDev& J = jobs[j];
+    uint64_t l = i - J.off[1];
+    double a = J.ra[1][l], d = J.dec[1][l];
+    if (!(bits_finite(a) && bits_abs_le(d, 90.0))) continue;
+    if (!bits_in_ra_range(a)) a = c_norm_ra(a);
+    float4 u = fp32_unitvec(a, d);
+    float c = u.x * dir[3 * j] + u.y * dir[3 * j + 1] + u.z * dir[3 * j + 2];
+    float om = fmaxf(1.0f - c, 0.0f);
+    atomicMax(cap + j, __float_as_uint(om));
+  }
+}
+
+// ---- per-job B offset tables -------------------------------------------------
+__global__ void k_btable_hist(const uint64_t* __restrict__ key, uint64_t m, int cell_bits,
+                              const JobDev* __restrict__ jobs, uint32_t* __restrict__ counts) {
+  const uint64_t cmask = (1ull << cell_bits) - 1;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t k = key[e];
+    uint32_t j = (uint32_t)(k >> cell_bits);
+    const JobDev& J = jobs[j];
+    uint32_t c = (uint32_t)((k & cmask) >> (2 * J.tk)) - J.tbase;
+    atomicAdd(counts + J.toff + c, 1u);
+  }
+}
+
+// The fields of a job the pair test needs, held in registers.
+struct JobTab {
+  int L, tk;
+  uint32_t tbase, tsize;
+  uint64_t toff;
+  double C;
+  float lo32, hi32;
+};
+
+__device__ __forceinline__ JobTab load_job(const JobDev* __restrict__ jobs, uint32_t j) {
+  const JobDev* J = jobs + j;
+  JobTab t;
+  t.L = J->L;
+  t.tk = J->tk;
+  t.tbase = J->tbase;
+  t.tsize = J->tsize;
+  t.toff = J->toff;
+  t.C = J->C;
+  t.lo32 = J->lo32;
+  t.hi32 = J->hi32;
+  return t;
+}
+
+// [begin, end) of the B entries of job j in fine cell q (composite keys).
+__device__ __forceinline__ uint2 bcell_range(const uint64_t* __restrict__ keyB,
+                                             const uint32_t* __restrict__ table,
+                                             const JobTab& J, uint32_t j, int cell_bits,
+                                             uint32_t q) {
+  uint32_t Q = q >> (2 * J.tk);
+  if (Q < J.tbase || Q - J.tbase + 1 >= J.tsize) return make_uint2(0u, 0u);
+  uint64_t slot = J.toff + (Q - J.tbase);
+  uint32_t a = __ldg(table + slot), hi = __ldg(table + slot + 1), b = hi;
+  uint64_t kq = ((uint64_t)j << cell_bits) | q;
+  while (a < b) {
+    uint32_t mid = (a + b) >> 1;
+    if (__ldg(keyB + mid) < kq)
+      a = mid + 1;
+    else
+      b = mid;
+  }
+  uint32_t first = a;
+  b = hi;
+  while (a < b) {
+    uint32_t mid = (a + b) >> 1;
+    if (__ldg(keyB + mid) <= kq)
+      a = mid + 1;
+    else
+      b = mid;
+  }
+  return make_uint2(first, a);
+}
+
+struct BPairArgs {
+  uint64_t mA;
+  const uint64_t* keyA;
+  const uint64_t* keyB;
+  const uint32_t* table;
+  const JobDev* jobs;
+  int cell_bits;
+  const double *axv, *ayv, *azv, *bxv, *byv, *bzv;
+  const float4 *a32, *b32;
+  uint32_t sparse_cell;
+  unsigned long long* work;  // chunk counter
+};
+
+// Persistent pair test: each warp takes chunks of 32 A entries from an atomic
+// work counter until all entries of all jobs are done.
+template <bool FP32>
+__global__ void __launch_bounds__(kThreads) k_bpair(const BPairArgs pa, PairSink sink) {
+  const uint64_t nchunks = (pa.mA + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  const uint64_t cmask = (1ull << pa.cell_bits) - 1;
+  unsigned long long ntest = 0;
+  for (;;) {
+    unsigned long long chunk = 0;
+    if (lane == 0) chunk = atomicAdd(pa.work, 1ull);
+    chunk = __shfl_sync(0xffffffffu, chunk, 0);
+    if (chunk >= nchunks) break;
+    uint64_t k = chunk * 32 + lane;
+    bool live = k < pa.mA;
+    uint32_t j = 0, cell = 0;
+    JobTab J = {0, 0, 0u, 0u, 0ull, 0.0, 0.f, 0.f};
+    if (live) {
+      uint64_t key = pa.keyA[k];
+      j = (uint32_t)(key >> pa.cell_bits);
+      cell = (uint32_t)(key & cmask);
+      J = load_job(pa.jobs, j);
+    }
+    double ax = 0, ay = 0, az = 0;
+    float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) {
+      if (FP32)
+        a4 = pa.a32[k];
+      else {
+        ax = pa.axv[k]; ay = pa.ayv[k]; az = pa.azv[k];
+      }
+    }
+    uint32_t nb[9];
+    int m = 0;
+    bool coarse = false;
+    if (live) {
+      uint32_t Q = cell >> (2 * J.tk);
+      if (FP32 && J.tk > 0 && Q >= J.tbase && Q - J.tbase + 1 < J.tsize) {
+        uint64_t slot = J.toff + (Q - J.tbase);
+        coarse = __ldg(pa.table + slot + 1) - __ldg(pa.table + slot) <= pa.sparse_cell;
+      }
+      m = coarse ? cell_neighbourhood(Q, J.L - J.tk, nb) : cell_neighbourhood(cell, J.L, nb);
+    }
+    uint32_t rb[9], re[9];
+    uint32_t total = 0;
+#pragma unroll
+    for (int s = 0; s < 9; ++s) {
+      uint2 r = make_uint2(0u, 0u);
+      if (s < m) {
+        if (coarse) {
+          uint32_t c = nb[s];
+          if (c >= J.tbase && c - J.tbase + 1 < J.tsize) {
+            uint64_t slot = J.toff + (c - J.tbase);
+            r = make_uint2(__ldg(pa.table + slot), __ldg(pa.table + slot + 1));
+          }
+        } else {
+          r = bcell_range(pa.keyB, pa.table, J, j, pa.cell_bits, nb[s]);
+        }
+      }
+      rb[s] = r.x;
+      re[s] = r.y;
+      total += r.y - r.x;
+    }
+    ntest += total;
+    const uint32_t maxT = __reduce_max_sync(0xffffffffu, total);
+    uint32_t cur = rb[0], end = re[0];
+    for (uint32_t t = 0; t < maxT; ++t) {
+      bool act = t < total;
+      uint32_t jb = 0;
+      bool hit = false, band = false;
+      if (act) {
+        while (cur >= end) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            rb[i] = rb[i + 1];
+            re[i] = re[i + 1];
+          }
+          cur = rb[0];
+          end = re[0];
+        }
+        jb = cur++;
+        if (FP32) {
+          float4 b = __ldg(pa.b32 + jb);
+          float dx = a4.x - b.x, dy = a4.y - b.y, dz = a4.z - b.z;
+          float s2 = dx * dx;
+          s2 = fmaf(dy, dy, s2);
+          s2 = fmaf(dz, dz, s2);
+          hit = s2 <= J.lo32;
+          band = !hit && s2 <= J.hi32;
+        } else {
+          hit = c_chord2(ax, ay, az, pa.bxv[jb], pa.byv[jb], pa.bzv[jb]) <= J.C;
+        }
+      }
+      if (__any_sync(0xffffffffu, hit || band)) {
+        warp_emit(hit, (uint32_t)k, jb, sink.rows, sink.count, sink.cap, sink.err);
+        if (FP32)
+          warp_emit(band, (uint32_t)k, jb, sink.band, sink.band_count, sink.band_cap, sink.err);
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) ntest += __shfl_down_sync(0xffffffffu, ntest, o);
+  if (lane == 0 && ntest) atomicAdd(sink.tests, ntest);
+}
+
+__global__ void __launch_bounds__(kThreads) k_brecheck(
+    const uint2* __restrict__ band, const unsigned long long* __restrict__ nband_dev,
+    uint64_t band_cap, const uint64_t* __restrict__ keyA, int cell_bits,
+    const JobDev* __restrict__ jobs, const double2* __restrict__ rdA,
+    const double2* __restrict__ rdB, uint2* rows, unsigned long long* count, uint64_t cap,
+    int* err) {
+  uint64_t nb = *nband_dev;
+  if (nb > band_cap) nb = band_cap;
+  for (uint64_t b0 = (uint64_t)blockIdx.x * kThreads; b0 < nb; b0 += (uint64_t)gridDim.x * kThreads) {
+    uint64_t q = b0 + threadIdx.x;
+    bool hit = false;
+    uint2 p = make_uint2(0u, 0u);
+    if (q < nb) {
+      p = band[q];
+      double C = jobs[keyA[p.x] >> cell_bits].C;
+      double2 a = rdA[p.x], b = rdB[p.y];
+      double ax, ay, az, bx, by, bz;
+      c_unitvec(a.x, a.y, &ax, &ay, &az);
+      c_unitvec(b.x, b.y, &bx, &by, &bz);
+      hit = c_chord2(ax, ay, az, bx, by, bz) <= C;
+    }
+    warp_emit(hit, p.x, p.y, rows, count, cap, err);
+  }
+}
+
+// Rows of a batched match: ids, separation, job; bucket = (job, id_a bits).
+template <bool FP32>
+__global__ void k_brows(const uint2* __restrict__ rows, uint64_t M,
+                        const uint64_t* __restrict__ keyA, int cell_bits,
+                        const uint64_t* __restrict__ idA, const uint64_t* __restrict__ idB,
+                        const double* __restrict__ axv, const double* __restrict__ ayv,
+                        const double* __restrict__ azv, const double* __restrict__ bxv,
+                        const double* __restrict__ byv, const double* __restrict__ bzv,
+                        const double2* __restrict__ rdA, const double2* __restrict__ rdB,
+                        int want_sep, uint64_t* __restrict__ ka, uint64_t* __restrict__ kb,
+                        double* __restrict__ sep, uint32_t* __restrict__ job, int nb,
+                        int bshift, uint32_t bmask, uint32_t* __restrict__ bhist) {
+  for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
+       m += (uint64_t)gridDim.x * blockDim.x) {
+    uint2 p = rows[m];
+    uint64_t a = idA[p.x];
+    uint32_t jj = (uint32_t)(keyA[p.x] >> cell_bits);
+    ka[m] = a;
+    kb[m] = idB[p.y];
+    job[m] = jj;
+    if (bhist) atomicAdd(&bhist[((uint64_t)jj << nb) | ((uint32_t)(a >> bshift) & bmask)], 1u);
+    if (want_sep) {
+      double sv;
+      if (FP32) {
+        double2 u = rdA[p.x], w = rdB[p.y];
+        sv = sep_arcsec_f2(u.x, u.y, w.x, w.y);
+        if (sv < 0.0) sv = sep_arcsec_haversine(u.x, u.y, w.x, w.y);
+      } else {
+        sv = sep_arcsec_from_chord2(
+            c_chord2(axv[p.x], ayv[p.x], azv[p.x], bxv[p.y], byv[p.y], bzv[p.y]));
+      }
+      sep[m] = sv;
+    }
+  }
+}
+
+__global__ void k_bbucket_scatter(const uint64_t* __restrict__ ka, const uint64_t* __restrict__ kb,
+                                  const double* __restrict__ sep, const uint32_t* __restrict__ job,
+                                  uint64_t M, int nb, int bshift, uint32_t bmask,
+                                  uint32_t* __restrict__ cursor, uint64_t* __restrict__ ta,
+                                  uint64_t* __restrict__ tb, double* __restrict__ ts) {
+  for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
+       m += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t a = ka[m];
+    uint64_t bk = ((uint64_t)job[m] << nb) | ((uint32_t)(a >> bshift) & bmask);
+    uint32_t pos = atomicAdd(&cursor[bk], 1u);
+    ta[pos] = a;
+    tb[pos] = kb[m];
+    if (sep) ts[pos] = sep[m];
+  }
+}
+
+// job column of the ordered rows, from the bucket each row landed in
+__global__ void k_bucket_jobs(const uint32_t* __restrict__ boff, uint64_t nbuckets, int nb,
+                              uint32_t* __restrict__ job) {
+  for (uint64_t bk = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; bk < nbuckets;
+       bk += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t j = (uint32_t)(bk >> nb);
+    for (uint32_t i = boff[bk]; i < boff[bk + 1]; ++i) job[i] = j;
+  }
+}
+
+}  // namespace hlc

@@ -11,6 +11,7 @@
 #include "learned.cuh"
 #include "match.cuh"
 #include "output.cuh"
+#include "batch.cuh"
 #include "scan.cuh"
 #include "sort.cuh"
 
@@ -212,6 +213,20 @@ struct hlc_plan_s {
   unsigned long long launches0 = 0;
   int id_high_bit = -1;
   uint64_t row_cap = 0;
+  // batched plans
+  uint32_t njobs = 1;
+  int cell_bits = 0;
+  std::vector<hlc::JobDev> jobs_h;
+  hlc::JobDev* jobs_d = nullptr;
+  uint64_t* offA_d = nullptr;
+  uint64_t* offB_d = nullptr;
+  uint64_t* keyA64 = nullptr;
+  uint64_t* keyB64 = nullptr;
+  uint32_t* btable = nullptr;
+  cudaGraphExec_t pair_graph = nullptr;
+  uint64_t graph_cap = 0, graph_bcap = 0;
+  void* graph_rows = nullptr;
+  void* graph_band = nullptr;
   uint32_t sparse_cell = hlc::kSparseCell;
   unsigned long long plan_launches = 0;
   cudaEvent_t ev[12] = {};
@@ -857,6 +872,618 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   return HLC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batched plans (n_jobs > 1).
+// ---------------------------------------------------------------------------
+
+// Autotuned order of a job: the finest order at which the job's B density
+// (sources over the spherical cap they occupy) leaves about kTargetPerCell
+// sources per cell, no finer than the completeness limit r <= theta_L / 8.
+constexpr double kTargetPerCell = 2.0;
+
+static int auto_order(double nb, double cap_one_minus_cos, double r_arcsec) {
+  const double pi = 3.14159265358979323846;
+  double area = 2.0 * pi * std::max(cap_one_minus_cos, 1e-12);  // sr
+  double density = std::max(nb, 1.0) / area;
+  double cells = 4.0 * pi * density / (12.0 * kTargetPerCell);  // 4^L
+  int L = cells > 1.0 ? (int)std::floor(std::log(cells) / std::log(4.0) + 0.5) : 0;
+  int Lmax = 0;
+  while (Lmax < 14 && r_arcsec <= complete_max_radius(Lmax + 1)) ++Lmax;
+  return std::max(0, std::min(L, Lmax));
+}
+
+static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_params* p,
+                        uint32_t njobs, hlc_plan_t** out) {
+  for (uint32_t j = 0; j < njobs; ++j) {
+    hlc_params q = p[j];
+    if (q.fine_level < 0) q.fine_level = 0;  // checked again once the order is chosen
+    if (q.coarse_level > q.fine_level) q.coarse_level = q.fine_level;
+    HLC_TRY(validate_params(&q));
+    HLC_TRY(validate_catalog(A + j, "A"));
+    HLC_TRY(validate_catalog(B + j, "B"));
+    if (p[j].boundary != HLC_COMPLETE8 || p[j].index != HLC_INDEX_BSEARCH) {
+      set_error("batched plans support the complete boundary with the table index");
+      return HLC_EUNSUPPORTED;
+    }
+    if (p[j].precision != p[0].precision || p[j].stream != p[0].stream ||
+        p[j].want_sep != p[0].want_sep || p[j].alloc != p[0].alloc) {
+      set_error("all jobs of a batched plan must share precision, stream, want_sep and "
+                "allocator");
+      return HLC_EINVAL;
+    }
+    if (A[j].on_device != A[0].on_device || B[j].on_device != A[0].on_device) {
+      set_error("all catalogues of a batched plan must be on the device or all on the host");
+      return HLC_EINVAL;
+    }
+  }
+  if (njobs > (1u << 16)) {
+    set_error("at most 65536 jobs per batched plan");
+    return HLC_EINVAL;
+  }
+  HLC_TRY(ensure_device_tables());
+  hlc_plan_t* P = new hlc_plan_t();
+  P->p = p[0];
+  P->njobs = njobs;
+  P->al.alloc = p[0].alloc;
+  P->al.dealloc = p[0].dealloc;
+  P->al.ctx = p[0].alloc_ctx;
+  P->al.stream = (cudaStream_t)p[0].stream;
+  P->arena = new Arena(P->al);
+  P->out = new Arena(P->al);
+  for (int i = 0; i < 12; ++i) cudaEventCreate(&P->ev[i]);
+  P->events = true;
+  auto fail = [&](int rc) {
+    hlc_free(P);
+    return rc;
+  };
+  cudaStream_t st = plan_stream(P);
+  Arena& ar = *P->arena;
+  const bool fp32 = p[0].precision == HLC_FP32_GUARD;
+  P->dev_err = ar.get_n<int>(16);
+  P->ctr = ar.get_n<unsigned long long>(C_N);
+  if (!P->dev_err || !P->ctr) return fail(HLC_ENOMEM);
+  cudaMemsetAsync(P->dev_err, 0, 64, st);
+  cudaMemsetAsync(P->ctr, 0, C_N * 8, st);
+  ev_record(P, 0);
+  P->launches0 = g_launches.load();
+  // job table and offsets; host inputs are staged job by job
+  std::vector<JobDev>& J = P->jobs_h;
+  J.assign(njobs, JobDev{});
+  std::vector<uint64_t> offA(njobs + 1, 0), offB(njobs + 1, 0);
+  for (uint32_t j = 0; j < njobs; ++j) {
+    offA[j + 1] = offA[j] + A[j].n;
+    offB[j + 1] = offB[j] + B[j].n;
+  }
+  const uint64_t NA = offA[njobs], NB = offB[njobs];
+  if (NA >= (1ull << 32) || NB >= (1ull << 32)) {
+    set_error("a batched plan holds fewer than 2^32 sources per side");
+    return fail(HLC_EINVAL);
+  }
+  double *sra[2] = {nullptr, nullptr}, *sdec[2] = {nullptr, nullptr};
+  uint64_t* sid[2] = {nullptr, nullptr};
+  if (!A[0].on_device) {
+    for (int s = 0; s < 2; ++s) {
+      uint64_t N = s ? NB : NA;
+      sra[s] = ar.get_n<double>(N + 1);
+      sdec[s] = ar.get_n<double>(N + 1);
+      sid[s] = ar.get_n<uint64_t>(N + 1);
+      if (!sra[s] || !sdec[s] || !sid[s]) return fail(HLC_ENOMEM);
+    }
+  }
+  for (uint32_t j = 0; j < njobs; ++j) {
+    const hlc_catalog* C2[2] = {A + j, B + j};
+    const uint64_t o[2] = {offA[j], offB[j]};
+    for (int s = 0; s < 2; ++s) {
+      J[j].n[s] = C2[s]->n;
+      J[j].off[s] = o[s];
+      if (C2[s]->on_device) {
+        J[j].ra[s] = C2[s]->ra_deg;
+        J[j].dec[s] = C2[s]->dec_deg;
+        J[j].id[s] = C2[s]->id;
+      } else {
+        uint64_t n = C2[s]->n;
+        if (n) {
+          if (cudaMemcpyAsync(sra[s] + o[s], C2[s]->ra_deg, n * 8, cudaMemcpyHostToDevice, st) !=
+                  cudaSuccess ||
+              cudaMemcpyAsync(sdec[s] + o[s], C2[s]->dec_deg, n * 8, cudaMemcpyHostToDevice,
+                              st) != cudaSuccess ||
+              cudaMemcpyAsync(sid[s] + o[s], C2[s]->id, n * 8, cudaMemcpyHostToDevice, st) !=
+                  cudaSuccess) {
+            set_error("host to device copy failed");
+            return fail(HLC_ECUDA);
+          }
+        }
+        // staged arrays are indexed by (global - off), so point at the job's slice
+        J[j].ra[s] = sra[s] + o[s];
+        J[j].dec[s] = sdec[s] + o[s];
+        J[j].id[s] = sid[s] + o[s];
+      }
+    }
+    J[j].L = p[j].fine_level;
+  }
+  P->jobs_d = ar.get_n<JobDev>(njobs);
+  P->offA_d = ar.get_n<uint64_t>(njobs + 1);
+  P->offB_d = ar.get_n<uint64_t>(njobs + 1);
+  if (!P->jobs_d || !P->offA_d || !P->offB_d) return fail(HLC_ENOMEM);
+  auto upload_jobs = [&]() -> int {
+    HLC_CUDA(cudaMemcpyAsync(P->jobs_d, J.data(), njobs * sizeof(JobDev),
+                             cudaMemcpyHostToDevice, st));
+    return HLC_OK;
+  };
+  if (cudaMemcpyAsync(P->offA_d, offA.data(), (njobs + 1) * 8, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(P->offB_d, offB.data(), (njobs + 1) * 8, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess)
+    return fail(HLC_ECUDA);
+  int rc = upload_jobs();
+  if (rc) return fail(rc);
+  // autotuned orders (jobs with fine_level < 0)
+  bool need_auto = false;
+  for (uint32_t j = 0; j < njobs; ++j) need_auto |= p[j].fine_level < 0;
+  if (need_auto && NB) {
+    float* acc = ar.get_n<float>(3 * njobs + 3);
+    unsigned* cap = ar.get_n<unsigned>(njobs + 1);
+    if (!acc || !cap) return fail(HLC_ENOMEM);
+    cudaMemsetAsync(acc, 0, (3 * njobs + 3) * 4, st);
+    cudaMemsetAsync(cap, 0, (njobs + 1) * 4, st);
+    k_bjob_mean<<<grid_for(NB, kThreads), kThreads, 0, st>>>(P->jobs_d, P->offB_d, njobs, NB, acc);
+    std::vector<float> h(3 * njobs);
+    if (cudaMemcpyAsync(h.data(), acc, 3 * njobs * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return fail(HLC_ECUDA);
+    for (uint32_t j = 0; j < njobs; ++j) {
+      double x = h[3 * j], y = h[3 * j + 1], z = h[3 * j + 2];
+      double nrm = std::sqrt(x * x + y * y + z * z);
+      if (nrm > 0) {
+        h[3 * j] = (float)(x / nrm);
+        h[3 * j + 1] = (float)(y / nrm);
+        h[3 * j + 2] = (float)(z / nrm);
+      }
+    }
+    cudaMemcpyAsync(acc, h.data(), 3 * njobs * 4, cudaMemcpyHostToDevice, st);
+    k_bjob_cap<<<grid_for(NB, kThreads), kThreads, 0, st>>>(P->jobs_d, P->offB_d, njobs, NB, acc,
+                                                             cap);
+    std::vector<unsigned> hc(njobs);
+    if (cudaMemcpyAsync(hc.data(), cap, njobs * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return fail(HLC_ECUDA);
+    for (uint32_t j = 0; j < njobs; ++j) {
+      if (p[j].fine_level >= 0) continue;
+      float om;
+      memcpy(&om, &hc[j], 4);
+      J[j].L = auto_order((double)B[j].n, (double)om, p[j].radius_arcsec);
+    }
+  } else {
+    for (uint32_t j = 0; j < njobs; ++j)
+      if (J[j].L < 0) J[j].L = 0;
+  }
+  int maxL = 0;
+  for (uint32_t j = 0; j < njobs; ++j) {
+    if (p[j].boundary == HLC_COMPLETE8 && p[j].radius_arcsec > complete_max_radius(J[j].L)) {
+      set_error("job %u: radius %g arcsec exceeds theta_L/8 at order %d", j, p[j].radius_arcsec,
+                J[j].L);
+      return fail(HLC_EINVAL);
+    }
+    maxL = std::max(maxL, J[j].L);
+    J[j].K = pix_const(J[j].L);
+    J[j].C = chord2_threshold(p[j].radius_arcsec);
+    double G = fp32_guard_band(J[j].C, kUnitVecErr);
+    float lo = (float)(J[j].C - G), hi = (float)(J[j].C + G);
+    if ((double)lo > J[j].C - G) lo = nextafterf(lo, 0.0f);
+    if ((double)hi < J[j].C + G) hi = nextafterf(hi, 1e30f);
+    if (lo < 0) lo = -1.0f;
+    J[j].lo32 = lo;
+    J[j].hi32 = hi;
+  }
+  P->cell_bits = 2 * maxL + 4;
+  int job_bits = 0;
+  while ((1u << job_bits) < njobs) ++job_bits;
+  const int key_bits = P->cell_bits + job_bits;
+  rc = upload_jobs();
+  if (rc) return fail(rc);
+  // per side: composite keys, sort, payload
+  CatDev* X2[2] = {&P->A, &P->B};
+  uint64_t* keys[2] = {nullptr, nullptr};
+  const uint64_t N2[2] = {NA, NB};
+  uint64_t* offd[2] = {P->offA_d, P->offB_d};
+  cudaEvent_t ev[2][4];
+  for (int s = 0; s < 2; ++s)
+    for (int i = 0; i < 4; ++i) cudaEventCreate(&ev[s][i]);
+  for (int s = 0; s < 2 && rc == HLC_OK; ++s) {
+    CatDev& X = *X2[s];
+    uint64_t n = N2[s];
+    X.n = X.m = n;
+    keys[s] = ar.get_n<uint64_t>(n + 1);
+    X.idx = ar.get_n<uint32_t>(n + 1);
+    uint32_t* slow = ar.get_n<uint32_t>(n + 1);
+    if (!keys[s] || !X.idx || !slow) return fail(HLC_ENOMEM);
+    cudaEventRecord(ev[s][0], st);
+    if (n) {
+      cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st);
+      if (fp32) {
+        k_bprep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+            P->jobs_d, offd[s], njobs, s, n, P->cell_bits, keys[s], X.idx, slow, P->ctr + C_SLOW,
+            P->dev_err);
+        k_bprep_fallback<<<148 * 4, kThreads, 0, st>>>(P->jobs_d, offd[s], njobs, s, P->cell_bits,
+                                                       slow, P->ctr + C_SLOW, keys[s]);
+      } else {
+        k_bprep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+            P->jobs_d, offd[s], njobs, s, n, P->cell_bits, keys[s], X.idx, nullptr, nullptr,
+            P->dev_err);
+      }
+      g_launches += fp32 ? 2 : 1;
+    }
+    ar.drop(slow);
+    cudaEventRecord(ev[s][1], st);
+    if (n > 1) {
+      uint64_t* tk = ar.get_n<uint64_t>(n);
+      uint32_t* tv = ar.get_n<uint32_t>(n);
+      void* scr = ar.get(sort_scratch_bytes(n, (key_bits + 7) / 8));
+      if (!tk || !tv || !scr) return fail(HLC_ENOMEM);
+      rc = radix_sort_pairs<uint64_t>(keys[s], X.idx, tk, tv, n, key_bits, scr, P->dev_err, st);
+      if (rc) return fail(rc);
+      ar.drop(tk);
+      ar.drop(tv);
+      ar.drop(scr);
+    }
+    cudaEventRecord(ev[s][2], st);
+    X.id_s = ar.get_n<uint64_t>(n + 1);
+    if (!X.id_s) return fail(HLC_ENOMEM);
+    if (fp32) {
+      X.v32 = ar.get_n<float4>(n + 1);
+      X.rd = ar.get_n<double2>(n + 1);
+      if (!X.v32 || !X.rd) return fail(HLC_ENOMEM);
+      if (n)
+        k_bpayload<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+            P->jobs_d, offd[s], njobs, s, X.idx, n, X.v32, X.rd, nullptr, nullptr, nullptr,
+            X.id_s);
+    } else {
+      X.vx = ar.get_n<double>(n + 1);
+      X.vy = ar.get_n<double>(n + 1);
+      X.vz = ar.get_n<double>(n + 1);
+      if (!X.vx || !X.vy || !X.vz) return fail(HLC_ENOMEM);
+      if (n)
+        k_bpayload<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+            P->jobs_d, offd[s], njobs, s, X.idx, n, nullptr, nullptr, X.vx, X.vy, X.vz, X.id_s);
+    }
+    if (n) ++g_launches;
+    cudaEventRecord(ev[s][3], st);
+  }
+  P->keyA64 = keys[0];
+  P->keyB64 = keys[1];
+  // per-job B tables over the occupied cell range
+  if (rc == HLC_OK && NB) {
+    // gather the first and last composite key of every job
+    uint64_t* fl = ar.get_n<uint64_t>(2 * njobs + 2);
+    if (!fl) return fail(HLC_ENOMEM);
+    for (uint32_t j = 0; j < njobs; ++j) {
+      if (!B[j].n) continue;
+      cudaMemcpyAsync(fl + 2 * j, keys[1] + offB[j], 8, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(fl + 2 * j + 1, keys[1] + offB[j + 1] - 1, 8, cudaMemcpyDeviceToDevice, st);
+    }
+    std::vector<uint64_t> h(2 * njobs, 0);
+    if (cudaMemcpyAsync(h.data(), fl, 2 * njobs * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return fail(HLC_ECUDA);
+    const uint64_t cmask = (1ull << P->cell_bits) - 1;
+    uint64_t toff = 0;
+    for (uint32_t j = 0; j < njobs; ++j) {
+      uint32_t kmin = (uint32_t)(h[2 * j] & cmask), kmax = (uint32_t)(h[2 * j + 1] & cmask);
+      if (!B[j].n) kmin = kmax = 0;
+      int tk = 0;
+      uint64_t target = std::max<uint64_t>(2 * B[j].n, 16);
+      while (tk < J[j].L && ((uint64_t)(kmax >> (2 * tk)) - (kmin >> (2 * tk)) + 1) > target) ++tk;
+      J[j].tk = tk;
+      J[j].tbase = kmin >> (2 * tk);
+      J[j].tsize = (uint32_t)((kmax >> (2 * tk)) - J[j].tbase + 2);
+      J[j].toff = toff;
+      toff += J[j].tsize;
+    }
+    rc = upload_jobs();
+    if (rc) return fail(rc);
+    uint32_t* counts = ar.get_n<uint32_t>(toff + 1);
+    P->btable = ar.get_n<uint32_t>(toff + 1);
+    void* scr = ar.get(scan_scratch_bytes(toff + 1));
+    if (!counts || !P->btable || !scr) return fail(HLC_ENOMEM);
+    cudaMemsetAsync(counts, 0, (toff + 1) * 4, st);
+    k_btable_hist<<<grid_for(NB, kThreads), kThreads, 0, st>>>(keys[1], NB, P->cell_bits,
+                                                                P->jobs_d, counts);
+    ++g_launches;
+    rc = scan_exclusive<uint32_t>(counts, P->btable, toff + 1, P->ctr + C_TOTAL, scr, P->dev_err,
+                                  st);
+    if (rc) return fail(rc);
+    ar.drop(counts);
+    ar.drop(scr);
+  }
+  if (rc == HLC_OK && NA) {
+    k_id_diff<<<grid_for(NA, kThreads, 148u * 8u), kThreads, 0, st>>>(P->A.id_s, NA,
+                                                                      P->ctr + C_IDDIFF);
+    ++g_launches;
+  }
+  unsigned long long hc[C_N] = {0};
+  if (rc == HLC_OK &&
+      cudaMemcpyAsync(hc, P->ctr, sizeof(hc), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    rc = HLC_ECUDA;
+  if (rc == HLC_OK) rc = check_dev_err(P->dev_err, st, "hlc_plan");
+  if (cudaGetLastError() != cudaSuccess && rc == HLC_OK) {
+    set_error("a batched plan kernel failed to launch");
+    rc = HLC_ECUDA;
+  }
+  float t[6] = {0};
+  if (rc == HLC_OK) {
+    for (int s = 0; s < 2; ++s) {
+      float a = 0, b = 0, c = 0;
+      cudaEventElapsedTime(&a, ev[s][0], ev[s][1]);
+      cudaEventElapsedTime(&b, ev[s][1], ev[s][2]);
+      cudaEventElapsedTime(&c, ev[s][2], ev[s][3]);
+      t[0] += a;
+      t[1] += b;
+      t[2] += c;
+    }
+  }
+  for (int s = 0; s < 2; ++s)
+    for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[s][i]);
+  if (rc != HLC_OK) return fail(rc);
+  ev_record(P, 1);
+  unsigned long long diff = hc[C_IDDIFF];
+  P->id_high_bit = diff ? 63 - __builtin_clzll(diff) : -1;
+  memset(&P->stats, 0, sizeof(P->stats));
+  P->stats.n_a = NA;
+  P->stats.n_b = NB;
+  P->stats.entries_a = NA;
+  P->stats.entries_b = NB;
+  P->stats.join_level = maxL;
+  P->stats.ms_prep = t[0];
+  P->stats.ms_sort = t[1];
+  P->stats.ms_index = t[2];
+  P->plan_launches = g_launches.load() - P->launches0;
+  *out = P;
+  return HLC_OK;
+}
+
+// The pair test of a batched plan as a CUDA graph (counter resets + the one
+// persistent launch), captured once per output capacity and replayed.
+static int batched_pair_graph(hlc_plan_t* P, uint2* rows, uint64_t cap, uint2* band,
+                              uint64_t bcap) {
+  cudaStream_t st = plan_stream(P);
+  const bool fp32 = P->p.precision == HLC_FP32_GUARD;
+  if (P->pair_graph && P->graph_rows == (void*)rows && P->graph_band == (void*)band &&
+      P->graph_cap == cap && P->graph_bcap == bcap) {
+    ++g_launches;
+    HLC_CUDA(cudaGraphLaunch(P->pair_graph, st));
+    return HLC_OK;
+  }
+  if (P->pair_graph) {
+    cudaGraphExecDestroy(P->pair_graph);
+    P->pair_graph = nullptr;
+  }
+  cudaStream_t cs;
+  HLC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaMemsetAsync(P->ctr, 0, C_N * 8, cs);
+    PairSink sink{rows, P->ctr + C_ROWS, cap, band, P->ctr + C_BAND, bcap,
+                  P->ctr + C_TESTS, P->ctr + C_DUPS, P->dev_err};
+    BPairArgs pa;
+    pa.mA = P->A.m;
+    pa.keyA = P->keyA64;
+    pa.keyB = P->keyB64;
+    pa.table = P->btable;
+    pa.jobs = P->jobs_d;
+    pa.cell_bits = P->cell_bits;
+    pa.axv = P->A.vx; pa.ayv = P->A.vy; pa.azv = P->A.vz;
+    pa.bxv = P->B.vx; pa.byv = P->B.vy; pa.bzv = P->B.vz;
+    pa.a32 = P->A.v32;
+    pa.b32 = P->B.v32;
+    pa.sparse_cell = P->sparse_cell;
+    pa.work = P->ctr + C_SCRATCH;
+    if (P->A.m && P->B.m) {
+      if (fp32)
+        k_bpair<true><<<148 * 8, kThreads, 0, cs>>>(pa, sink);
+      else
+        k_bpair<false><<<148 * 8, kThreads, 0, cs>>>(pa, sink);
+    }
+    e = cudaStreamEndCapture(cs, &g);
+  }
+  if (e == cudaSuccess) {
+    e = cudaGraphInstantiate(&P->pair_graph, g, 0);
+    cudaGraphDestroy(g);
+  }
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    set_error("pair graph capture failed: %s", cudaGetErrorString(e));
+    return HLC_ECUDA;
+  }
+  P->graph_rows = rows;
+  P->graph_band = band;
+  P->graph_cap = cap;
+  P->graph_bcap = bcap;
+  ++g_launches;
+  HLC_CUDA(cudaGraphLaunch(P->pair_graph, st));
+  return HLC_OK;
+}
+
+static int match_batched(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
+  cudaStream_t st = plan_stream(P);
+  Arena& ar = *P->out;
+  ar.release();
+  if (P->pair_graph) {  // its buffers were released with the previous result
+    cudaGraphExecDestroy(P->pair_graph);
+    P->pair_graph = nullptr;
+  }
+  CatDev& A = P->A;
+  CatDev& B = P->B;
+  const bool fp32 = P->p.precision == HLC_FP32_GUARD;
+  const unsigned long long launches_match0 = g_launches.load();
+  HLC_CUDA(cudaMemsetAsync(P->dev_err, 0, 64, st));
+  ev_record(P, 2);
+  ev_record(P, 3);
+  uint64_t cap = P->row_cap ? P->row_cap : std::max<uint64_t>(1u << 20, A.n + B.n);
+  uint64_t bcap = fp32 ? std::max<uint64_t>(1u << 16, cap / 4) : 1;
+  uint2* rows = nullptr;
+  uint2* band = nullptr;
+  unsigned long long h[C_N];
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    rows = ar.get_n<uint2>(cap);
+    band = ar.get_n<uint2>(bcap);
+    if (!rows || !band) return HLC_ENOMEM;
+    HLC_TRY(batched_pair_graph(P, rows, cap, band, bcap));
+    HLC_CUDA(cudaMemcpyAsync(h, P->ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
+    HLC_CUDA(cudaStreamSynchronize(st));
+    uint64_t need = h[C_ROWS] + (fp32 ? h[C_BAND] : 0);
+    if (need <= cap && h[C_BAND] <= bcap) break;
+    cudaGraphExecDestroy(P->pair_graph);
+    P->pair_graph = nullptr;
+    ar.drop(rows);
+    ar.drop(band);
+    cap = need + need / 8 + 1024;
+    bcap = std::max<uint64_t>(bcap, h[C_BAND] + 1024);
+    HLC_CUDA(cudaMemsetAsync(P->dev_err, 0, 64, st));
+    if (attempt == 2) {
+      set_error("match rows did not fit after resizing");
+      return HLC_ECUDA;
+    }
+  }
+  P->row_cap = std::max<uint64_t>(P->row_cap, cap);
+  ev_record(P, 4);
+  if (fp32 && h[C_BAND]) {
+    k_brecheck<<<grid_for(h[C_BAND], kThreads, 148u * 16u), kThreads, 0, st>>>(
+        band, P->ctr + C_BAND, bcap, P->keyA64, P->cell_bits, P->jobs_d, A.rd, B.rd, rows,
+        P->ctr + C_ROWS, cap, P->dev_err);
+    HLC_LAUNCH_CHECK();
+  }
+  ev_record(P, 5);
+  unsigned long long M = h[C_ROWS];
+  if (fp32 && h[C_BAND]) {
+    HLC_CUDA(cudaMemcpyAsync(&M, P->ctr + C_ROWS, 8, cudaMemcpyDeviceToHost, st));
+    HLC_CUDA(cudaStreamSynchronize(st));
+  }
+  HLC_TRY(check_dev_err(P->dev_err, st, "hlc_match"));
+  const bool want_sep = P->p.want_sep != 0;
+  uint64_t* ka = ar.get_n<uint64_t>(M + 1);
+  uint64_t* kb = ar.get_n<uint64_t>(M + 1);
+  double* sep = want_sep ? ar.get_n<double>(M + 1) : nullptr;
+  uint32_t* job = ar.get_n<uint32_t>(M + 1);
+  uint64_t* ta = ar.get_n<uint64_t>(M + 1);
+  uint64_t* tb = ar.get_n<uint64_t>(M + 1);
+  double* ts = want_sep ? ar.get_n<double>(M + 1) : nullptr;
+  uint32_t* tj = ar.get_n<uint32_t>(M + 1);
+  if (!ka || !kb || !job || !ta || !tb || !tj || (want_sep && (!sep || !ts))) return HLC_ENOMEM;
+  // buckets: (job, bits of id_a), about four rows per bucket
+  int hb = P->id_high_bit;
+  int nb = 0;
+  while (nb < 20 && ((uint64_t)P->njobs << (nb + 3)) < M) ++nb;
+  if (nb > hb + 1) nb = std::max(hb + 1, 0);
+  const int bshift = hb >= 0 ? hb + 1 - nb : 0;
+  const uint64_t nbk = (uint64_t)P->njobs << nb;
+  const uint32_t bmask = nb ? ((1u << nb) - 1) : 0u;
+  uint32_t* bhist = ar.get_n<uint32_t>(nbk + 1);
+  uint32_t* boff = ar.get_n<uint32_t>(nbk + 1);
+  if (!bhist || !boff) return HLC_ENOMEM;
+  HLC_CUDA(cudaMemsetAsync(bhist, 0, (nbk + 1) * 4, st));
+  if (M) {
+    unsigned g = grid_for(M, kThreads);
+    if (fp32)
+      k_brows<true><<<g, kThreads, 0, st>>>(rows, M, P->keyA64, P->cell_bits, A.id_s, B.id_s,
+                                             nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                             A.rd, B.rd, want_sep, ka, kb, sep, job, nb, bshift,
+                                             bmask, bhist);
+    else
+      k_brows<false><<<g, kThreads, 0, st>>>(rows, M, P->keyA64, P->cell_bits, A.id_s, B.id_s,
+                                              A.vx, A.vy, A.vz, B.vx, B.vy, B.vz, nullptr,
+                                              nullptr, want_sep, ka, kb, sep, job, nb, bshift,
+                                              bmask, bhist);
+    HLC_LAUNCH_CHECK();
+  }
+  ar.drop(rows);
+  ar.drop(band);
+  uint64_t* oa = ka;
+  uint64_t* ob = kb;
+  double* os = sep;
+  uint32_t* oj = job;
+  bool done = M <= 1;
+  if (M > 1) {
+    void* scr = ar.get(scan_scratch_bytes(nbk + 1));
+    if (!scr) return HLC_ENOMEM;
+    HLC_TRY(scan_exclusive<uint32_t>(bhist, boff, nbk + 1, P->ctr + C_TOTAL, scr, P->dev_err, st));
+    HLC_CUDA(cudaMemsetAsync(P->ctr + C_MAXB, 0, 8, st));
+    k_max_u32<<<grid_for(nbk, kThreads, 1024), kThreads, 0, st>>>(bhist, nbk,
+                                                                  (uint32_t*)(P->ctr + C_MAXB));
+    HLC_LAUNCH_CHECK();
+    unsigned long long maxb = 0;
+    HLC_CUDA(cudaMemcpyAsync(&maxb, P->ctr + C_MAXB, 8, cudaMemcpyDeviceToHost, st));
+    HLC_CUDA(cudaStreamSynchronize(st));
+    maxb &= 0xFFFFFFFFull;
+    if (maxb <= (unsigned long long)kBucketCap && nbk < (1ull << 31)) {
+      HLC_CUDA(cudaMemcpyAsync(bhist, boff, (size_t)nbk * 4, cudaMemcpyDeviceToDevice, st));
+      unsigned g = grid_for(M, kThreads);
+      k_bbucket_scatter<<<g, kThreads, 0, st>>>(ka, kb, sep, job, M, nb, bshift, bmask, bhist, ta,
+                                                tb, ts);
+      HLC_LAUNCH_CHECK();
+      k_bucket_small<<<grid_for(nbk, kThreads), kThreads, 0, st>>>(ta, tb, ts, boff,
+                                                                    (uint32_t)nbk, ka, kb, sep);
+      HLC_LAUNCH_CHECK();
+      if (maxb > kSmallBucket) {
+        k_bucket_sort<<<(unsigned)std::min<uint64_t>(nbk, 148u * 32u), kBucketThreads, 0, st>>>(
+            ta, tb, ts, boff, (uint32_t)nbk, ka, kb, sep, P->dev_err);
+        HLC_LAUNCH_CHECK();
+      }
+      k_bucket_jobs<<<grid_for(nbk, kThreads), kThreads, 0, st>>>(boff, nbk, nb, job);
+      HLC_LAUNCH_CHECK();
+      done = true;
+    }
+    ar.drop(scr);
+  }
+  if (!done) {
+    // stable LSD: id_b, then id_a, then job
+    uint32_t* perm = ar.get_n<uint32_t>(M + 1);
+    uint64_t* tk = ar.get_n<uint64_t>(M + 1);
+    uint32_t* tv = ar.get_n<uint32_t>(M + 1);
+    void* scr = ar.get(sort_scratch_bytes(M + 1, 8));
+    if (!perm || !tk || !tv || !scr) return HLC_ENOMEM;
+    unsigned g = grid_for(M, kThreads);
+    k_iota<<<g, kThreads, 0, st>>>(perm, M);
+    HLC_CUDA(cudaMemcpyAsync(ta, kb, M * 8, cudaMemcpyDeviceToDevice, st));
+    HLC_TRY(radix_sort_pairs<uint64_t>(ta, perm, tk, tv, M, 64, scr, P->dev_err, st));
+    k_gather<uint64_t><<<g, kThreads, 0, st>>>(ka, perm, M, ta);
+    HLC_TRY(radix_sort_pairs<uint64_t>(ta, perm, tk, tv, M, 64, scr, P->dev_err, st));
+    k_gather<uint32_t><<<g, kThreads, 0, st>>>(job, perm, M, tj);
+    HLC_CUDA(cudaMemcpyAsync(tv, tj, M * 4, cudaMemcpyDeviceToDevice, st));
+    HLC_TRY(radix_sort_pairs<uint32_t>(tv, perm, (uint32_t*)tk, (uint32_t*)tk + M + 1, M, 16, scr,
+                                       P->dev_err, st));
+    k_gather<uint64_t><<<g, kThreads, 0, st>>>(ka, perm, M, ta);
+    k_gather<uint64_t><<<g, kThreads, 0, st>>>(kb, perm, M, tb);
+    if (sep) k_gather<double><<<g, kThreads, 0, st>>>(sep, perm, M, ts);
+    k_gather<uint32_t><<<g, kThreads, 0, st>>>(job, perm, M, tj);
+    HLC_LAUNCH_CHECK();
+    oa = ta;
+    ob = tb;
+    os = ts;
+    oj = tj;
+  }
+  ev_record(P, 6);
+  HLC_CUDA(cudaStreamSynchronize(st));
+  HLC_TRY(check_dev_err(P->dev_err, st, "hlc_match"));
+  res->n = M;
+  res->id_a = oa;
+  res->id_b = ob;
+  res->sep_arcsec = want_sep ? os : nullptr;
+  res->job = oj;
+  res->on_device = 1;
+  P->stats.pair_tests = h[C_TESTS];
+  P->stats.band_candidates = fp32 ? h[C_BAND] : 0;
+  P->stats.matches = M;
+  P->stats.ms_candidates = 0;
+  P->stats.ms_pair = ev_ms(P, 3, 4);
+  P->stats.ms_recheck = ev_ms(P, 4, 5);
+  P->stats.ms_output = ev_ms(P, 5, 6);
+  P->stats.ms_total = ev_ms(P, 0, 1) + ev_ms(P, 2, 6);
+  P->stats.kernel_launches = (g_launches.load() - launches_match0) + P->plan_launches;
+  if (stats) *stats = P->stats;
+  return HLC_OK;
+}
+
 }  // namespace hlc
 
 using namespace hlc;
@@ -891,10 +1518,11 @@ int hlc_plan(const hlc_catalog* A, const hlc_catalog* B, const hlc_params* p, ui
     set_error("n_jobs must be >= 1");
     return HLC_EINVAL;
   }
-  if (n_jobs > 1) {
-    set_error("batched plans are not available in this build");
-    return HLC_EUNSUPPORTED;
+  if (!A || !B || !p) {
+    set_error("A, B or params is NULL");
+    return HLC_EINVAL;
   }
+  if (n_jobs > 1) return plan_batched(A, B, p, n_jobs, out);
   return plan_single(A, B, p, out);
 }
 
@@ -905,7 +1533,7 @@ int hlc_match(hlc_plan_t* plan, hlc_result* out, hlc_stats* stats) {
     return HLC_EINVAL;
   }
   hlc_result r{};
-  int rc = match_single(plan, &r, stats);
+  int rc = plan->njobs > 1 ? match_batched(plan, &r, stats) : match_single(plan, &r, stats);
   if (rc == HLC_OK) *out = r;
   return rc;
 }
@@ -930,6 +1558,7 @@ void hlc_free(hlc_plan_t* plan) {
   if (!plan) return;
   cudaStream_t st = (cudaStream_t)plan->p.stream;
   cudaStreamSynchronize(st);
+  if (plan->pair_graph) cudaGraphExecDestroy(plan->pair_graph);
   delete plan->out;
   delete plan->arena;
   for (int i = 0; i < 12; ++i)
