@@ -304,6 +304,16 @@ def hlc_match(plan: Plan, copy: bool = True) -> dict:
     _check(L.hlc_match(plan.handle, C.byref(r), C.byref(s)))
     plan.result = r
     n = int(r.n)
+    if not r.on_device:  # streamed plans return host rows
+        def host(ptr, ct, dt):
+            if n == 0 or not ptr:
+                return torch.empty(0, dtype=dt)
+            a = np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ct)), shape=(n,)).copy()
+            return torch.from_numpy(a.view(np.int64) if dt == torch.int64 else a)
+        return dict(n=n, id_a=host(r.id_a, C.c_uint64, torch.int64),
+                    id_b=host(r.id_b, C.c_uint64, torch.int64),
+                    sep=host(r.sep_arcsec, C.c_double, torch.float64) if r.sep_arcsec else None,
+                    job=None, stats=s.as_dict())
     return dict(n=n,
                 id_a=_as_tensor(r.id_a, n, "<i8", torch.int64, copy),
                 id_b=_as_tensor(r.id_b, n, "<i8", torch.int64, copy),

@@ -1,8 +1,11 @@
 // The C ABI (include/hlc.h): plan / match / free, the kernel-level entry
 // points, device tables and error state.  All kernels live in the headers
 // included here (one translation unit, so constant tables are shared).
+#include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <queue>
+#include <vector>
 
 #include "canon.cuh"
 #include "common.cuh"
@@ -12,6 +15,7 @@
 #include "match.cuh"
 #include "output.cuh"
 #include "batch.cuh"
+#include "stream.cuh"
 #include "scan.cuh"
 #include "sort.cuh"
 
@@ -227,6 +231,10 @@ struct hlc_plan_s {
   uint64_t graph_cap = 0, graph_bcap = 0;
   void* graph_rows = nullptr;
   void* graph_band = nullptr;
+  // streamed plans: merged rows on the host
+  bool streamed = false;
+  std::vector<uint64_t> host_a, host_b;
+  std::vector<double> host_s;
   uint32_t sparse_cell = hlc::kSparseCell;
   unsigned long long plan_launches = 0;
   cudaEvent_t ev[12] = {};
@@ -1484,6 +1492,366 @@ static int match_batched(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   return HLC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Streamed plans (host inputs larger than device_mem_budget).
+// ---------------------------------------------------------------------------
+
+// Device bytes one entry costs in the in-core path (inputs, keys, sort
+// buffers, payload, table, rows) -- used to size the partition groups.
+constexpr uint64_t kStreamBytesPerEntry = 192;
+constexpr uint64_t kStreamChunk = 8ull << 20;  // sources per streamed chunk
+
+struct HostRows {
+  std::vector<uint64_t> a, b;
+  std::vector<double> s;
+};
+
+// Streams one host catalogue through the device in chunks on two streams,
+// running `fn(chunk ra, dec, id, n, stream)` on each.  Pinned inputs are
+// copied directly; pageable ones through two pinned staging buffers.
+template <typename Fn>
+static int stream_catalog(const hlc_catalog* X, double* dra[2], double* ddec[2], uint64_t* did[2],
+                          void* stage[2], cudaStream_t ss[2], cudaEvent_t done[2], float* ms_h2d,
+                          Fn fn) {
+  cudaPointerAttributes at;
+  bool pinned = X->n && cudaPointerGetAttributes(&at, X->ra_deg) == cudaSuccess &&
+                at.type == cudaMemoryTypeHost;
+  cudaGetLastError();
+  if (pinned) {
+    cudaPointerAttributes a2, a3;
+    pinned = cudaPointerGetAttributes(&a2, X->dec_deg) == cudaSuccess &&
+             a2.type == cudaMemoryTypeHost &&
+             cudaPointerGetAttributes(&a3, X->id) == cudaSuccess && a3.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+  }
+  uint64_t nchunks = (X->n + kStreamChunk - 1) / kStreamChunk;
+  for (uint64_t c = 0; c < nchunks; ++c) {
+    int b = (int)(c & 1);
+    uint64_t o = c * kStreamChunk;
+    uint64_t n = std::min(kStreamChunk, X->n - o);
+    // the buffer of this parity is free once its previous chunk is done
+    HLC_CUDA(cudaEventSynchronize(done[b]));
+    const double* sra = X->ra_deg + o;
+    const double* sdec = X->dec_deg + o;
+    const uint64_t* sid = X->id + o;
+    if (!pinned) {
+      char* h = (char*)stage[b];
+      memcpy(h, sra, n * 8);
+      memcpy(h + kStreamChunk * 8, sdec, n * 8);
+      memcpy(h + kStreamChunk * 16, sid, n * 8);
+      sra = (const double*)h;
+      sdec = (const double*)(h + kStreamChunk * 8);
+      sid = (const uint64_t*)(h + kStreamChunk * 16);
+    }
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    cudaEventRecord(t0, ss[b]);
+    HLC_CUDA(cudaMemcpyAsync(dra[b], sra, n * 8, cudaMemcpyHostToDevice, ss[b]));
+    HLC_CUDA(cudaMemcpyAsync(ddec[b], sdec, n * 8, cudaMemcpyHostToDevice, ss[b]));
+    HLC_CUDA(cudaMemcpyAsync(did[b], sid, n * 8, cudaMemcpyHostToDevice, ss[b]));
+    cudaEventRecord(t1, ss[b]);
+    HLC_TRY(fn(dra[b], ddec[b], did[b], n, ss[b]));
+    HLC_CUDA(cudaEventRecord(done[b], ss[b]));
+    cudaEventSynchronize(t1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, t0, t1);
+    *ms_h2d += ms;
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+  }
+  HLC_CUDA(cudaStreamSynchronize(ss[0]));
+  HLC_CUDA(cudaStreamSynchronize(ss[1]));
+  return HLC_OK;
+}
+
+static bool row_lt(uint64_t a1, uint64_t b1, double s1, uint64_t a2, uint64_t b2, double s2) {
+  if (a1 != a2) return a1 < a2;
+  if (b1 != b2) return b1 < b2;
+  uint64_t x, y;
+  memcpy(&x, &s1, 8);
+  memcpy(&y, &s2, 8);
+  return x < y;
+}
+
+static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_params* p,
+                         hlc_plan_t** out) {
+  HLC_TRY(validate_params(p));
+  HLC_TRY(validate_catalog(A, "A"));
+  HLC_TRY(validate_catalog(B, "B"));
+  if (p->boundary != HLC_COMPLETE8 || p->index != HLC_INDEX_BSEARCH) {
+    set_error("streamed plans support the complete boundary with the table index");
+    return HLC_EUNSUPPORTED;
+  }
+  HLC_TRY(ensure_device_tables());
+  hlc_plan_t* P = new hlc_plan_t();
+  P->p = *p;
+  P->al.alloc = p->alloc;
+  P->al.dealloc = p->dealloc;
+  P->al.ctx = p->alloc_ctx;
+  P->al.stream = (cudaStream_t)p->stream;
+  P->arena = new Arena(P->al);
+  P->out = new Arena(P->al);
+  P->streamed = true;
+  auto fail = [&](int rc) {
+    hlc_free(P);
+    return rc;
+  };
+  cudaStream_t st = plan_stream(P);
+  Arena& ar = *P->arena;
+  const int Lf = p->fine_level, Lc = p->coarse_level;
+  const uint64_t nparts = 12ull << (2 * Lc);
+  const PixConst K = pix_const(Lf);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  // chunk buffers, side streams, staging
+  double *dra[2], *ddec[2];
+  uint64_t* did[2];
+  for (int b = 0; b < 2; ++b) {
+    dra[b] = ar.get_n<double>(kStreamChunk);
+    ddec[b] = ar.get_n<double>(kStreamChunk);
+    did[b] = ar.get_n<uint64_t>(kStreamChunk);
+    if (!dra[b] || !ddec[b] || !did[b]) return fail(HLC_ENOMEM);
+  }
+  unsigned long long* counts = ar.get_n<unsigned long long>(2 * nparts);
+  int* err = ar.get_n<int>(16);
+  unsigned long long* cur = ar.get_n<unsigned long long>(4);
+  if (!counts || !err || !cur) return fail(HLC_ENOMEM);
+  cudaStream_t ss[2];
+  cudaEvent_t done[2];
+  void* stage[2] = {nullptr, nullptr};
+  for (int b = 0; b < 2; ++b) {
+    cudaStreamCreateWithFlags(&ss[b], cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming);
+    cudaEventRecord(done[b], ss[b]);
+    if (cudaHostAlloc(&stage[b], kStreamChunk * 24, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("pinned staging allocation failed");
+      return fail(HLC_ENOMEM);
+    }
+  }
+  auto cleanup = [&]() {
+    for (int b = 0; b < 2; ++b) {
+      cudaStreamSynchronize(ss[b]);
+      cudaStreamDestroy(ss[b]);
+      cudaEventDestroy(done[b]);
+      if (stage[b]) cudaFreeHost(stage[b]);
+    }
+  };
+  HLC_CUDA(cudaMemsetAsync(counts, 0, 2 * nparts * 8, st));
+  HLC_CUDA(cudaMemsetAsync(err, 0, 64, st));
+  HLC_CUDA(cudaStreamSynchronize(st));
+  float ms_h2d = 0;
+  int rc = HLC_OK;
+  // pass 1: the entries each coarse cell needs
+  for (int side = 0; side < 2 && rc == HLC_OK; ++side) {
+    const hlc_catalog* X = side ? B : A;
+    unsigned long long* cnt = counts + side * nparts;
+    rc = stream_catalog(X, dra, ddec, did, stage, ss, done, &ms_h2d,
+                        [&](double* r, double* d, uint64_t* id, uint64_t n, cudaStream_t s) {
+                          (void)id;
+                          k_part_count<<<grid_for(n, kThreads), kThreads, 0, s>>>(
+                              r, d, n, Lf, Lc, side, K, cnt, err);
+                          HLC_LAUNCH_CHECK();
+                          return HLC_OK;
+                        });
+  }
+  std::vector<unsigned long long> hc(2 * nparts);
+  if (rc == HLC_OK) {
+    if (cudaMemcpy(hc.data(), counts, 2 * nparts * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = HLC_ECUDA;
+  }
+  if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_plan (streamed)");
+  if (rc != HLC_OK) {
+    cleanup();
+    return fail(rc);
+  }
+  // groups of consecutive coarse cells that fit the budget
+  uint64_t budget = p->device_mem_budget;
+  uint64_t fixed = 6 * kStreamChunk * 8 + 2 * nparts * 8 + (64ull << 20);
+  uint64_t cap_entries =
+      std::max<uint64_t>(4096, (budget > fixed ? budget - fixed : budget) / kStreamBytesPerEntry);
+  std::vector<std::pair<uint32_t, uint32_t>> groups;
+  uint64_t acc = 0;
+  uint32_t g0 = 0;
+  for (uint32_t q = 0; q < nparts; ++q) {
+    uint64_t c = hc[q] + hc[nparts + q];
+    if (acc > 0 && acc + c > cap_entries) {
+      groups.push_back({g0, q});
+      g0 = q;
+      acc = 0;
+    }
+    acc += c;
+  }
+  groups.push_back({g0, (uint32_t)nparts});
+  // pass 2: select, match in core, collect
+  std::vector<HostRows> runs;
+  hlc_stats agg{};
+  for (auto& g : groups) {
+    uint64_t na = 0, nb = 0;
+    for (uint32_t q = g.first; q < g.second; ++q) {
+      na += hc[q];
+      nb += hc[nparts + q];
+    }
+    if (na == 0 || nb == 0) continue;
+    double *gra[2], *gdec[2];
+    uint64_t* gid[2];
+    const uint64_t gn[2] = {na, nb};
+    for (int side = 0; side < 2; ++side) {
+      gra[side] = ar.get_n<double>(gn[side] + 1);
+      gdec[side] = ar.get_n<double>(gn[side] + 1);
+      gid[side] = ar.get_n<uint64_t>(gn[side] + 1);
+      if (!gra[side] || !gdec[side] || !gid[side]) {
+        cleanup();
+        return fail(HLC_ENOMEM);
+      }
+    }
+    HLC_CUDA(cudaMemsetAsync(cur, 0, 32, st));
+    HLC_CUDA(cudaStreamSynchronize(st));
+    for (int side = 0; side < 2 && rc == HLC_OK; ++side) {
+      const hlc_catalog* X = side ? B : A;
+      rc = stream_catalog(
+          X, dra, ddec, did, stage, ss, done, &ms_h2d,
+          [&](double* r, double* d, uint64_t* id, uint64_t n, cudaStream_t s) {
+            k_part_select<<<grid_for(n, kThreads), kThreads, 0, s>>>(
+                r, d, id, n, Lf, Lc, side, K, g.first, g.second, gra[side], gdec[side],
+                gid[side], cur + side, gn[side], err);
+            HLC_LAUNCH_CHECK();
+            return HLC_OK;
+          });
+    }
+    if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_plan (streamed)");
+    // (a B source needed by several coarse cells of the group is taken once,
+    // so the per-cell sums are upper bounds; the cursors hold the counts)
+    if (rc == HLC_OK) {
+      unsigned long long hcur[2] = {0, 0};
+      if (cudaMemcpy(hcur, cur, 16, cudaMemcpyDeviceToHost) != cudaSuccess) rc = HLC_ECUDA;
+      if (rc == HLC_OK && (hcur[0] > na || hcur[1] > nb)) {
+        set_error("streamed selection overflowed its buffers");
+        rc = HLC_ECUDA;
+      }
+      na = hcur[0];
+      nb = hcur[1];
+    }
+    hlc_plan_t* G = nullptr;
+    if (rc == HLC_OK) {
+      hlc_catalog ca{gra[0], gdec[0], gid[0], na, 1}, cb{gra[1], gdec[1], gid[1], nb, 1};
+      hlc_params q = *p;
+      q.device_mem_budget = 0;
+      rc = plan_single(&ca, &cb, &q, &G);
+    }
+    hlc_result r{};
+    hlc_stats gs{};
+    if (rc == HLC_OK) rc = match_single(G, &r, &gs);
+    if (rc == HLC_OK && r.n) {
+      HostRows h;
+      h.a.resize(r.n);
+      h.b.resize(r.n);
+      if (r.sep_arcsec) h.s.resize(r.n);
+      cudaEvent_t d0, d1;
+      cudaEventCreate(&d0);
+      cudaEventCreate(&d1);
+      cudaEventRecord(d0, st);
+      if (cudaMemcpyAsync(h.a.data(), r.id_a, r.n * 8, cudaMemcpyDeviceToHost, st) !=
+              cudaSuccess ||
+          cudaMemcpyAsync(h.b.data(), r.id_b, r.n * 8, cudaMemcpyDeviceToHost, st) !=
+              cudaSuccess ||
+          (r.sep_arcsec && cudaMemcpyAsync(h.s.data(), r.sep_arcsec, r.n * 8,
+                                           cudaMemcpyDeviceToHost, st) != cudaSuccess))
+        rc = HLC_ECUDA;
+      cudaEventRecord(d1, st);
+      cudaStreamSynchronize(st);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, d0, d1);
+      agg.ms_d2h += ms;
+      cudaEventDestroy(d0);
+      cudaEventDestroy(d1);
+      runs.push_back(std::move(h));
+    }
+    if (G) {
+      agg.pair_tests += gs.pair_tests;
+      agg.band_candidates += gs.band_candidates;
+      agg.entries_b += gs.entries_b;
+      agg.ms_prep += gs.ms_prep;
+      agg.ms_sort += gs.ms_sort;
+      agg.ms_index += gs.ms_index;
+      agg.ms_pair += gs.ms_pair;
+      agg.ms_recheck += gs.ms_recheck;
+      agg.ms_output += gs.ms_output;
+      agg.kernel_launches += gs.kernel_launches;
+      hlc_free(G);
+    }
+    for (int side = 0; side < 2; ++side) {
+      ar.drop(gra[side]);
+      ar.drop(gdec[side]);
+      ar.drop(gid[side]);
+    }
+    if (rc != HLC_OK) break;
+    ++agg.partitions;
+  }
+  cleanup();
+  if (rc != HLC_OK) return fail(rc);
+  // k-way merge of the groups' sorted rows
+  uint64_t M = 0;
+  for (auto& h : runs) M += h.a.size();
+  const bool want_sep = p->want_sep != 0;
+  P->host_a.resize(M);
+  P->host_b.resize(M);
+  if (want_sep) P->host_s.resize(M);
+  {
+    typedef std::pair<size_t, size_t> Cur;  // (run, position)
+    auto gt = [&](const Cur& x, const Cur& y) {
+      const HostRows& u = runs[x.first];
+      const HostRows& v = runs[y.first];
+      return row_lt(v.a[y.second], v.b[y.second], v.s.empty() ? 0.0 : v.s[y.second],
+                    u.a[x.second], u.b[x.second], u.s.empty() ? 0.0 : u.s[x.second]);
+    };
+    std::priority_queue<Cur, std::vector<Cur>, decltype(gt)> pq(gt);
+    for (size_t r = 0; r < runs.size(); ++r)
+      if (!runs[r].a.empty()) pq.push({r, 0});
+    uint64_t o = 0;
+    while (!pq.empty()) {
+      Cur c = pq.top();
+      pq.pop();
+      const HostRows& h = runs[c.first];
+      P->host_a[o] = h.a[c.second];
+      P->host_b[o] = h.b[c.second];
+      if (want_sep) P->host_s[o] = h.s[c.second];
+      ++o;
+      if (c.second + 1 < h.a.size()) pq.push({c.first, c.second + 1});
+    }
+  }
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float total = 0;
+  cudaEventElapsedTime(&total, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  agg.n_a = A->n;
+  agg.n_b = B->n;
+  agg.entries_a = A->n;
+  agg.matches = M;
+  agg.join_level = Lf;
+  agg.ms_h2d = ms_h2d;
+  agg.ms_total = total;
+  P->stats = agg;
+  *out = P;
+  return HLC_OK;
+}
+
+static int match_streamed(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
+  res->n = P->host_a.size();
+  res->id_a = P->host_a.data();
+  res->id_b = P->host_b.data();
+  res->sep_arcsec = P->p.want_sep ? P->host_s.data() : nullptr;
+  res->job = nullptr;
+  res->on_device = 0;
+  if (stats) *stats = P->stats;
+  return HLC_OK;
+}
+
 }  // namespace hlc
 
 using namespace hlc;
@@ -1523,6 +1891,11 @@ int hlc_plan(const hlc_catalog* A, const hlc_catalog* B, const hlc_params* p, ui
     return HLC_EINVAL;
   }
   if (n_jobs > 1) return plan_batched(A, B, p, n_jobs, out);
+  if (p->device_mem_budget && !A->on_device && !B->on_device) {
+    // stream by coarse partition when the in-core footprint exceeds the budget
+    uint64_t need = (A->n + B->n) * kStreamBytesPerEntry;
+    if (need > p->device_mem_budget) return plan_streamed(A, B, p, out);
+  }
   return plan_single(A, B, p, out);
 }
 
@@ -1533,7 +1906,9 @@ int hlc_match(hlc_plan_t* plan, hlc_result* out, hlc_stats* stats) {
     return HLC_EINVAL;
   }
   hlc_result r{};
-  int rc = plan->njobs > 1 ? match_batched(plan, &r, stats) : match_single(plan, &r, stats);
+  int rc = plan->streamed   ? match_streamed(plan, &r, stats)
+           : plan->njobs > 1 ? match_batched(plan, &r, stats)
+                             : match_single(plan, &r, stats);
   if (rc == HLC_OK) *out = r;
   return rc;
 }
