@@ -395,18 +395,18 @@ __global__ void k_brows(const uint2* __restrict__ rows, uint64_t M,
                         const double* __restrict__ azv, const double* __restrict__ bxv,
                         const double* __restrict__ byv, const double* __restrict__ bzv,
                         const double2* __restrict__ rdA, const double2* __restrict__ rdB,
-                        int want_sep, uint64_t* __restrict__ ka, uint64_t* __restrict__ kb,
-                        double* __restrict__ sep, uint32_t* __restrict__ job, int nb,
-                        int bshift, uint32_t bmask, uint32_t* __restrict__ bhist) {
+                        int want_sep, OutRow* __restrict__ out, int nb, int bshift,
+                        uint32_t bmask, uint32_t* __restrict__ bhist) {
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
        m += (uint64_t)gridDim.x * blockDim.x) {
     uint2 p = rows[m];
-    uint64_t a = idA[p.x];
-    uint32_t jj = (uint32_t)(keyA[p.x] >> cell_bits);
-    ka[m] = a;
-    kb[m] = idB[p.y];
-    job[m] = jj;
-    if (bhist) atomicAdd(&bhist[((uint64_t)jj << nb) | ((uint32_t)(a >> bshift) & bmask)], 1u);
+    OutRow o;
+    o.a = idA[p.x];
+    o.b = idB[p.y];
+    o.job = (uint32_t)(keyA[p.x] >> cell_bits);
+    o.pad = 0;
+    o.s = 0.0;
+    if (bhist) atomicAdd(&bhist[((uint64_t)o.job << nb) | ((uint32_t)(o.a >> bshift) & bmask)], 1u);
     if (want_sep) {
       double sv;
       if (FP32) {
@@ -417,34 +417,9 @@ __global__ void k_brows(const uint2* __restrict__ rows, uint64_t M,
         sv = sep_arcsec_from_chord2(
             c_chord2(axv[p.x], ayv[p.x], azv[p.x], bxv[p.y], byv[p.y], bzv[p.y]));
       }
-      sep[m] = sv;
+      o.s = sv;
     }
-  }
-}
-
-__global__ void k_bbucket_scatter(const uint64_t* __restrict__ ka, const uint64_t* __restrict__ kb,
-                                  const double* __restrict__ sep, const uint32_t* __restrict__ job,
-                                  uint64_t M, int nb, int bshift, uint32_t bmask,
-                                  uint32_t* __restrict__ cursor, uint64_t* __restrict__ ta,
-                                  uint64_t* __restrict__ tb, double* __restrict__ ts) {
-  for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
-       m += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t a = ka[m];
-    uint64_t bk = ((uint64_t)job[m] << nb) | ((uint32_t)(a >> bshift) & bmask);
-    uint32_t pos = atomicAdd(&cursor[bk], 1u);
-    ta[pos] = a;
-    tb[pos] = kb[m];
-    if (sep) ts[pos] = sep[m];
-  }
-}
-
-// job column of the ordered rows, from the bucket each row landed in
-__global__ void k_bucket_jobs(const uint32_t* __restrict__ boff, uint64_t nbuckets, int nb,
-                              uint32_t* __restrict__ job) {
-  for (uint64_t bk = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; bk < nbuckets;
-       bk += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t j = (uint32_t)(bk >> nb);
-    for (uint32_t i = boff[bk]; i < boff[bk + 1]; ++i) job[i] = j;
+    out[m] = o;
   }
 }
 

@@ -22,8 +22,10 @@ __constant__ CanonDev d_canon;
 // Neighbour transition table: for base face f and the 3x3 region
 // (x below / inside / above the face) x (y below / inside / above), the face
 // reached and the coordinate map (see NbrMap).  255 = no neighbour there.
-__constant__ uint8_t d_nbr_face[12][9];
-__constant__ uint8_t d_nbr_map[12][9];
+// (Global memory, read through the read-only cache: lanes of a warp index it
+// with different faces, which constant memory would serialise.)
+__device__ uint8_t d_nbr_face[12][9];
+__device__ uint8_t d_nbr_map[12][9];
 
 enum NbrMap : uint8_t {
   NM_SAME = 0,    // inside the face
@@ -194,10 +196,10 @@ __device__ __forceinline__ long long nbr_step(int face, int ix, int iy, int dx, 
   int rx = x < 0 ? 0 : (x >= n ? 2 : 1);
   int ry = y < 0 ? 0 : (y >= n ? 2 : 1);
   int r = ry * 3 + rx;
-  int f2 = d_nbr_face[face][r];
+  int f2 = __ldg(&d_nbr_face[face][r]);
   if (f2 == 255) return -1;
   int x2, y2;
-  switch (d_nbr_map[face][r]) {
+  switch (__ldg(&d_nbr_map[face][r])) {
     case NM_SAME: x2 = x; y2 = y; break;
     case NM_SHIFT:
       x2 = x < 0 ? x + n : (x >= n ? x - n : x);

@@ -20,15 +20,32 @@ struct CellIndex {
   int shift = 0;                   // 2 (L - Lt)
 };
 
-// Counts per coarse cell and the number of distinct fine keys (heads).
+// Counts per coarse cell and the number of distinct fine keys (heads).  The
+// keys are sorted, so equal coarse cells are contiguous: each warp adds one
+// count per run of lanes that share a cell.
 __global__ void k_coarse_hist(const uint32_t* __restrict__ keys, uint64_t n, int shift,
                               uint32_t* __restrict__ hist, unsigned long long* __restrict__ heads) {
   unsigned long long h = 0;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t k = keys[i];
-    if (hist) atomicAdd(&hist[k >> shift], 1u);
-    h += (i == 0 || keys[i - 1] != k);
+  const int lane = threadIdx.x & 31;
+  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n;
+       i0 += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t i = i0 + threadIdx.x;
+    bool live = i < n;
+    uint32_t k = live ? keys[i] : 0xFFFFFFFFu;
+    uint32_t prev = __shfl_up_sync(0xffffffffu, k, 1);
+    if (live) h += (i == 0 || (lane > 0 ? prev : keys[i - 1]) != k);
+    if (hist) {
+      uint32_t q = k >> shift;
+      uint32_t qp = __shfl_up_sync(0xffffffffu, q, 1);
+      bool head = live && (lane == 0 || qp != q);
+      unsigned hm = __ballot_sync(0xffffffffu, head);
+      unsigned lm = __ballot_sync(0xffffffffu, live);
+      if (head) {
+        unsigned later = hm & ~((2u << lane) - 1u);  // next run head after this lane
+        int end = later ? __ffs(later) - 1 : 32 - __clz(lm);
+        atomicAdd(&hist[q], (uint32_t)(end - lane));
+      }
+    }
   }
   for (int o = 16; o > 0; o >>= 1) h += __shfl_down_sync(0xffffffffu, h, o);
   if ((threadIdx.x & 31) == 0 && h) atomicAdd(heads, h);

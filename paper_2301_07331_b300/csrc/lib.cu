@@ -181,8 +181,9 @@ struct CatDev {
   uint32_t* idx = nullptr;   // source of each sorted entry
   double *vx = nullptr, *vy = nullptr, *vz = nullptr;
   float4* v32 = nullptr;
-  double2* rd = nullptr;       // entry-ordered (ra, dec), guard form
-  uint64_t* id_s = nullptr;    // entry-ordered ids
+  double2* rd = nullptr;       // entry-ordered (ra, dec) (batched plans)
+  uint64_t* id_s = nullptr;    // entry-ordered ids (batched plans)
+  SrcRec* rec = nullptr;       // (ra, dec, id) of each source, input order
   uint32_t* cells5 = nullptr;  // quad: cell set of each source
   uint32_t* table = nullptr;   // coarse offset table (catalogue B)
   int table_shift = 0;
@@ -402,6 +403,7 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     id = tid;
   }
   cudaEventRecord(ev[0], st);
+  HLC_ALLOC(ar, X.rec, SrcRec, n + 1);
   if (!quad) {
     X.m = n;
     HLC_ALLOC(ar, X.key, uint32_t, n + 1);
@@ -412,14 +414,15 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
         if (!slow) return HLC_ENOMEM;
         HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st));
         k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            ra, dec, n, L, pix_const(L), X.key, X.idx, slow, P->ctr + C_SLOW, P->dev_err);
+            ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, slow, P->ctr + C_SLOW,
+            P->dev_err);
         HLC_LAUNCH_CHECK();
         k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key);
         HLC_LAUNCH_CHECK();
         ar.drop(slow);
       } else {
         k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            ra, dec, n, L, pix_const(L), X.key, X.idx, nullptr, nullptr, P->dev_err);
+            ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, nullptr, nullptr, P->dev_err);
         HLC_LAUNCH_CHECK();
       }
     }
@@ -436,7 +439,8 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
         if (!slow) return HLC_ENOMEM;
         HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st));
         k_quad_cells<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            ra, dec, n, R, L, pix_const(L), X.cells5, cnt, slow, P->ctr + C_SLOW, P->dev_err);
+            ra, dec, id, n, R, L, pix_const(L), X.cells5, cnt, X.rec, slow, P->ctr + C_SLOW,
+            P->dev_err);
         HLC_LAUNCH_CHECK();
         k_quad_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, R, L, slow, P->ctr + C_SLOW,
                                                       X.cells5, cnt);
@@ -444,7 +448,8 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
         ar.drop(slow);
       } else {
         k_quad_cells<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            ra, dec, n, R, L, pix_const(L), X.cells5, cnt, nullptr, nullptr, P->dev_err);
+            ra, dec, id, n, R, L, pix_const(L), X.cells5, cnt, X.rec, nullptr, nullptr,
+            P->dev_err);
         HLC_LAUNCH_CHECK();
       }
     }
@@ -482,19 +487,14 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     HLC_ALLOC(ar, X.vx, double, m + 1);
     HLC_ALLOC(ar, X.vy, double, m + 1);
     HLC_ALLOC(ar, X.vz, double, m + 1);
-    HLC_ALLOC(ar, X.id_s, uint64_t, m + 1);
     if (m) {
-      k_payload64<<<grid_for(m, kThreads), kThreads, 0, st>>>(ra, dec, id, X.idx, m, X.vx, X.vy,
-                                                               X.vz, X.id_s);
+      k_payload64<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.rec, X.idx, m, X.vx, X.vy, X.vz);
       HLC_LAUNCH_CHECK();
     }
   } else {
     HLC_ALLOC(ar, X.v32, float4, m + 1);
-    HLC_ALLOC(ar, X.rd, double2, m + 1);
-    HLC_ALLOC(ar, X.id_s, uint64_t, m + 1);
     if (m) {
-      k_payload32<<<grid_for(m, kThreads), kThreads, 0, st>>>(ra, dec, id, X.idx, m, X.v32,
-                                                               X.rd, X.id_s);
+      k_payload32<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.rec, X.idx, m, X.v32);
       HLC_LAUNCH_CHECK();
     }
   }
@@ -604,9 +604,9 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   }
   int rc = build_catalog(P, A, P->A, false, ea);
   if (rc == HLC_OK) rc = build_catalog(P, B, P->B, true, eb);
-  if (rc == HLC_OK && P->A.m) {
-    k_id_diff<<<grid_for(P->A.m, kThreads, 148u * 8u), kThreads, 0, st>>>(P->A.id_s, P->A.m,
-                                                                          P->ctr + C_IDDIFF);
+  if (rc == HLC_OK && P->A.n) {
+    k_id_diff_rec<<<grid_for(P->A.n, kThreads, 148u * 8u), kThreads, 0, st>>>(P->A.rec, P->A.n,
+                                                                              P->ctr + C_IDDIFF);
     if (cudaGetLastError() != cudaSuccess) rc = HLC_ECUDA;
   }
   unsigned long long hc[C_N] = {0};
@@ -678,6 +678,96 @@ static int sort_rows_lsd(hlc_plan_t* P, uint64_t M, uint64_t* ka, uint64_t* kb, 
   ar.drop(tk);
   ar.drop(tv);
   ar.drop(scr);
+  return HLC_OK;
+}
+
+// Orders M packed rows by (job, id_a, id_b, sep) into result columns: the
+// bucket scatter + per-bucket sorts, or two or three stable radix sorts when
+// a bucket would not fit in shared memory.  nb_job < 0: single job.
+static int order_rows(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_t* bhist,
+                      uint32_t* boff, uint64_t nbk, int nb_job, int bshift, uint32_t bmask,
+                      bool bucketed, bool want_sep, uint64_t** oa, uint64_t** ob, double** os,
+                      uint32_t** oj) {
+  Arena& ar = *P->out;
+  cudaStream_t st = plan_stream(P);
+  const bool batched = nb_job >= 0;
+  uint64_t* a = ar.get_n<uint64_t>(M + 1);
+  uint64_t* b = ar.get_n<uint64_t>(M + 1);
+  double* sp = want_sep ? ar.get_n<double>(M + 1) : nullptr;
+  uint32_t* jb = batched ? ar.get_n<uint32_t>(M + 1) : nullptr;
+  if (!a || !b || (want_sep && !sp) || (batched && !jb)) return HLC_ENOMEM;
+  *oa = a;
+  *ob = b;
+  *os = sp;
+  *oj = jb;
+  if (M == 0) return HLC_OK;
+  unsigned g = grid_for(M, kThreads);
+  if (M == 1) {
+    k_rows_split<<<1, 32, 0, st>>>(rows32, M, a, b, sp, jb);
+    HLC_LAUNCH_CHECK();
+    return HLC_OK;
+  }
+  if (bucketed && nbk < (1ull << 31)) {
+    void* scr = ar.get(scan_scratch_bytes(nbk + 1));
+    if (!scr) return HLC_ENOMEM;
+    HLC_TRY(scan_exclusive<uint32_t>(bhist, boff, nbk + 1, P->ctr + C_TOTAL, scr, P->dev_err, st));
+    HLC_CUDA(cudaMemsetAsync(P->ctr + C_MAXB, 0, 8, st));
+    k_max_u32<<<grid_for(nbk, kThreads, 1024), kThreads, 0, st>>>(bhist, nbk,
+                                                                  (uint32_t*)(P->ctr + C_MAXB));
+    HLC_LAUNCH_CHECK();
+    unsigned long long maxb = 0;
+    HLC_CUDA(cudaMemcpyAsync(&maxb, P->ctr + C_MAXB, 8, cudaMemcpyDeviceToHost, st));
+    HLC_CUDA(cudaStreamSynchronize(st));
+    ar.drop(scr);
+    maxb &= 0xFFFFFFFFull;
+    if (maxb <= (unsigned long long)kBucketCap) {
+      OutRow* t = ar.get_n<OutRow>(M + 1);
+      if (!t) return HLC_ENOMEM;
+      HLC_CUDA(cudaMemcpyAsync(bhist, boff, (size_t)nbk * 4, cudaMemcpyDeviceToDevice, st));
+      k_bucket_scatter<<<g, kThreads, 0, st>>>(rows32, M, bshift, bmask, nb_job, bhist, t);
+      HLC_LAUNCH_CHECK();
+      k_bucket_small<<<grid_for(nbk, kThreads), kThreads, 0, st>>>(t, boff, (uint32_t)nbk, a, b,
+                                                                    sp, jb);
+      HLC_LAUNCH_CHECK();
+      if (maxb > kSmallBucket) {
+        k_bucket_sort<<<(unsigned)std::min<uint64_t>(nbk, 148u * 32u), kBucketThreads, 0, st>>>(
+            t, boff, (uint32_t)nbk, want_sep ? 1 : 0, a, b, sp, jb, P->dev_err);
+        HLC_LAUNCH_CHECK();
+      }
+      ar.drop(t);
+      return HLC_OK;
+    }
+  }
+  // fallback: stable LSD radix sorts by id_b, id_a (and job)
+  uint64_t* ua = ar.get_n<uint64_t>(M + 1);
+  uint64_t* ub = ar.get_n<uint64_t>(M + 1);
+  double* us = want_sep ? ar.get_n<double>(M + 1) : nullptr;
+  uint32_t* uj = batched ? ar.get_n<uint32_t>(M + 1) : nullptr;
+  uint32_t* perm = ar.get_n<uint32_t>(M + 1);
+  uint64_t* tk = ar.get_n<uint64_t>(M + 1);
+  uint32_t* tv = ar.get_n<uint32_t>(M + 1);
+  void* scr = ar.get(sort_scratch_bytes(M + 1, 8));
+  if (!ua || !ub || (want_sep && !us) || (batched && !uj) || !perm || !tk || !tv || !scr)
+    return HLC_ENOMEM;
+  k_rows_split<<<g, kThreads, 0, st>>>(rows32, M, ua, ub, us, uj);
+  k_iota<<<g, kThreads, 0, st>>>(perm, M);
+  HLC_LAUNCH_CHECK();
+  HLC_CUDA(cudaMemcpyAsync(a, ub, M * 8, cudaMemcpyDeviceToDevice, st));
+  HLC_TRY(radix_sort_pairs<uint64_t>(a, perm, tk, tv, M, 64, scr, P->dev_err, st));
+  k_gather<uint64_t><<<g, kThreads, 0, st>>>(ua, perm, M, a);
+  HLC_LAUNCH_CHECK();
+  HLC_TRY(radix_sort_pairs<uint64_t>(a, perm, tk, tv, M, 64, scr, P->dev_err, st));
+  if (batched) {
+    k_gather<uint32_t><<<g, kThreads, 0, st>>>(uj, perm, M, jb);
+    HLC_LAUNCH_CHECK();
+    HLC_TRY(radix_sort_pairs<uint32_t>(jb, perm, (uint32_t*)tk, (uint32_t*)tk + M + 1, M, 16, scr,
+                                       P->dev_err, st));
+    k_gather<uint32_t><<<g, kThreads, 0, st>>>(uj, perm, M, jb);
+  }
+  k_gather<uint64_t><<<g, kThreads, 0, st>>>(ua, perm, M, a);
+  k_gather<uint64_t><<<g, kThreads, 0, st>>>(ub, perm, M, b);
+  if (want_sep) k_gather<double><<<g, kThreads, 0, st>>>(us, perm, M, sp);
+  HLC_LAUNCH_CHECK();
   return HLC_OK;
 }
 
@@ -766,7 +856,8 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   ev_record(P, 4);
   if (fp32 && h[C_BAND]) {
     k_recheck<<<grid_for(h[C_BAND], kThreads, 148u * 16u), kThreads, 0, st>>>(
-        band, P->ctr + C_BAND, bcap, A.rd, B.rd, P->C, rows, P->ctr + C_ROWS, cap, P->dev_err);
+        band, P->ctr + C_BAND, bcap, A.idx, B.idx, A.rec, B.rec, P->C, rows, P->ctr + C_ROWS,
+        cap, P->dev_err);
     HLC_LAUNCH_CHECK();
   }
   ev_record(P, 5);
@@ -777,23 +868,18 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   }
   HLC_TRY(check_dev_err(P->dev_err, st, "hlc_match"));
   ar.drop(band);
-  // rows: ids, separations, bucket histogram of id_a
+  // rows: ids, separations, bucket histogram of id_a (about four rows per bucket)
   const bool want_sep = P->p.want_sep != 0;
-  uint64_t* ka = ar.get_n<uint64_t>(M + 1);
-  uint64_t* kb = ar.get_n<uint64_t>(M + 1);
-  double* sep = want_sep ? ar.get_n<double>(M + 1) : nullptr;
-  uint64_t* ta = ar.get_n<uint64_t>(M + 1);
-  uint64_t* tb = ar.get_n<uint64_t>(M + 1);
-  double* ts = want_sep ? ar.get_n<double>(M + 1) : nullptr;
-  if (!ka || !kb || !ta || !tb || (want_sep && (!sep || !ts))) return HLC_ENOMEM;
+  OutRow* rows32 = ar.get_n<OutRow>(M + 1);
+  if (!rows32) return HLC_ENOMEM;
   int hb = P->id_high_bit;
   int nbits = 1;
-  while (nbits < 24 && (M >> (nbits + 1)) > 0) ++nbits;  // about two rows per bucket
+  while (nbits < 24 && (M >> (nbits + 2)) > 0) ++nbits;
   if (hb >= 0 && nbits > hb + 1) nbits = hb + 1;
   const bool bucketed = M > 1 && hb >= 0;
   const int bshift = bucketed ? hb + 1 - nbits : 0;
-  const uint32_t nbk = 1u << nbits;
-  const uint32_t bmask = nbk - 1;
+  const uint64_t nbk = 1ull << nbits;
+  const uint32_t bmask = (uint32_t)(nbk - 1);
   uint32_t* bhist = nullptr;
   uint32_t* boff = nullptr;
   if (bucketed) {
@@ -805,56 +891,25 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   if (M) {
     unsigned g = grid_for(M, kThreads);
     if (fp32)
-      k_rows<true><<<g, kThreads, 0, st>>>(rows, M, A.id_s, B.id_s, nullptr, nullptr, nullptr,
-                                            nullptr, nullptr, nullptr, A.rd, B.rd, want_sep, ka,
-                                            kb, sep, bshift, bmask, bhist);
+      k_rows<true><<<g, kThreads, 0, st>>>(rows, M, A.idx, B.idx, A.rec, B.rec, nullptr, nullptr,
+                                            nullptr, nullptr, nullptr, nullptr, want_sep, rows32,
+                                            bshift, bmask, bhist);
     else
-      k_rows<false><<<g, kThreads, 0, st>>>(rows, M, A.id_s, B.id_s, A.vx, A.vy, A.vz, B.vx,
-                                             B.vy, B.vz, nullptr, nullptr, want_sep, ka, kb, sep,
-                                             bshift, bmask, bhist);
+      k_rows<false><<<g, kThreads, 0, st>>>(rows, M, A.idx, B.idx, A.rec, B.rec, A.vx, A.vy,
+                                             A.vz, B.vx, B.vy, B.vz, want_sep, rows32, bshift,
+                                             bmask, bhist);
     HLC_LAUNCH_CHECK();
   }
   ar.drop(rows);
-  uint64_t* oa = ka;
-  uint64_t* ob = kb;
-  double* os = sep;
-  bool done = M <= 1;
-  if (bucketed) {
-    void* scr = ar.get(scan_scratch_bytes(nbk + 1));
-    if (!scr) return HLC_ENOMEM;
-    HLC_TRY(scan_exclusive<uint32_t>(bhist, boff, nbk + 1, P->ctr + C_TOTAL, scr, P->dev_err,
-                                     st));
-    HLC_CUDA(cudaMemsetAsync(P->ctr + C_MAXB, 0, 8, st));
-    k_max_u32<<<grid_for(nbk, kThreads, 1024), kThreads, 0, st>>>(bhist, nbk,
-                                                                  (uint32_t*)(P->ctr + C_MAXB));
-    HLC_LAUNCH_CHECK();
-    unsigned long long maxb = 0;
-    HLC_CUDA(cudaMemcpyAsync(&maxb, P->ctr + C_MAXB, 8, cudaMemcpyDeviceToHost, st));
-    HLC_CUDA(cudaStreamSynchronize(st));
-    maxb &= 0xFFFFFFFFull;
-    if (maxb <= (unsigned long long)kBucketCap) {
-      // cursor: reuse the histogram buffer as the running offsets
-      HLC_CUDA(cudaMemcpyAsync(bhist, boff, (size_t)nbk * 4, cudaMemcpyDeviceToDevice, st));
-      unsigned g = grid_for(M, kThreads);
-      k_bucket_scatter<<<g, kThreads, 0, st>>>(ka, kb, sep, M, bshift, bmask, bhist, ta, tb, ts);
-      HLC_LAUNCH_CHECK();
-      k_bucket_small<<<grid_for(nbk, kThreads), kThreads, 0, st>>>(ta, tb, ts, boff, nbk, ka, kb,
-                                                                    sep);
-      HLC_LAUNCH_CHECK();
-      if (maxb > kSmallBucket) {
-        k_bucket_sort<<<std::min<uint32_t>(nbk, 148u * 32u), kBucketThreads, 0, st>>>(
-            ta, tb, ts, boff, nbk, ka, kb, sep, P->dev_err);
-        HLC_LAUNCH_CHECK();
-      }
-      done = true;
-    }
-    ar.drop(scr);
-  }
-  if (!done) {
-    HLC_TRY(sort_rows_lsd(P, M, ka, kb, sep, ta, tb, ts));
-    oa = ta;
-    ob = tb;
-    os = ts;
+  uint64_t *oa = nullptr, *ob = nullptr;
+  double* os = nullptr;
+  uint32_t* oj = nullptr;
+  HLC_TRY(order_rows(P, rows32, M, bhist, boff, nbk, -1, bshift, bmask, bucketed, want_sep, &oa,
+                     &ob, &os, &oj));
+  ar.drop(rows32);
+  if (bhist) {
+    ar.drop(bhist);
+    ar.drop(boff);
   }
   ev_record(P, 6);
   HLC_CUDA(cudaStreamSynchronize(st));
@@ -1369,19 +1424,12 @@ static int match_batched(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   }
   HLC_TRY(check_dev_err(P->dev_err, st, "hlc_match"));
   const bool want_sep = P->p.want_sep != 0;
-  uint64_t* ka = ar.get_n<uint64_t>(M + 1);
-  uint64_t* kb = ar.get_n<uint64_t>(M + 1);
-  double* sep = want_sep ? ar.get_n<double>(M + 1) : nullptr;
-  uint32_t* job = ar.get_n<uint32_t>(M + 1);
-  uint64_t* ta = ar.get_n<uint64_t>(M + 1);
-  uint64_t* tb = ar.get_n<uint64_t>(M + 1);
-  double* ts = want_sep ? ar.get_n<double>(M + 1) : nullptr;
-  uint32_t* tj = ar.get_n<uint32_t>(M + 1);
-  if (!ka || !kb || !job || !ta || !tb || !tj || (want_sep && (!sep || !ts))) return HLC_ENOMEM;
+  OutRow* rows32 = ar.get_n<OutRow>(M + 1);
+  if (!rows32) return HLC_ENOMEM;
   // buckets: (job, bits of id_a), about four rows per bucket
   int hb = P->id_high_bit;
   int nb = 0;
-  while (nb < 20 && ((uint64_t)P->njobs << (nb + 3)) < M) ++nb;
+  while (nb < 20 && ((uint64_t)P->njobs << (nb + 2)) < M) ++nb;
   if (nb > hb + 1) nb = std::max(hb + 1, 0);
   const int bshift = hb >= 0 ? hb + 1 - nb : 0;
   const uint64_t nbk = (uint64_t)P->njobs << nb;
@@ -1395,81 +1443,24 @@ static int match_batched(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
     if (fp32)
       k_brows<true><<<g, kThreads, 0, st>>>(rows, M, P->keyA64, P->cell_bits, A.id_s, B.id_s,
                                              nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                             A.rd, B.rd, want_sep, ka, kb, sep, job, nb, bshift,
-                                             bmask, bhist);
+                                             A.rd, B.rd, want_sep, rows32, nb, bshift, bmask,
+                                             bhist);
     else
       k_brows<false><<<g, kThreads, 0, st>>>(rows, M, P->keyA64, P->cell_bits, A.id_s, B.id_s,
                                               A.vx, A.vy, A.vz, B.vx, B.vy, B.vz, nullptr,
-                                              nullptr, want_sep, ka, kb, sep, job, nb, bshift,
-                                              bmask, bhist);
+                                              nullptr, want_sep, rows32, nb, bshift, bmask, bhist);
     HLC_LAUNCH_CHECK();
   }
   ar.drop(rows);
   ar.drop(band);
-  uint64_t* oa = ka;
-  uint64_t* ob = kb;
-  double* os = sep;
-  uint32_t* oj = job;
-  bool done = M <= 1;
-  if (M > 1) {
-    void* scr = ar.get(scan_scratch_bytes(nbk + 1));
-    if (!scr) return HLC_ENOMEM;
-    HLC_TRY(scan_exclusive<uint32_t>(bhist, boff, nbk + 1, P->ctr + C_TOTAL, scr, P->dev_err, st));
-    HLC_CUDA(cudaMemsetAsync(P->ctr + C_MAXB, 0, 8, st));
-    k_max_u32<<<grid_for(nbk, kThreads, 1024), kThreads, 0, st>>>(bhist, nbk,
-                                                                  (uint32_t*)(P->ctr + C_MAXB));
-    HLC_LAUNCH_CHECK();
-    unsigned long long maxb = 0;
-    HLC_CUDA(cudaMemcpyAsync(&maxb, P->ctr + C_MAXB, 8, cudaMemcpyDeviceToHost, st));
-    HLC_CUDA(cudaStreamSynchronize(st));
-    maxb &= 0xFFFFFFFFull;
-    if (maxb <= (unsigned long long)kBucketCap && nbk < (1ull << 31)) {
-      HLC_CUDA(cudaMemcpyAsync(bhist, boff, (size_t)nbk * 4, cudaMemcpyDeviceToDevice, st));
-      unsigned g = grid_for(M, kThreads);
-      k_bbucket_scatter<<<g, kThreads, 0, st>>>(ka, kb, sep, job, M, nb, bshift, bmask, bhist, ta,
-                                                tb, ts);
-      HLC_LAUNCH_CHECK();
-      k_bucket_small<<<grid_for(nbk, kThreads), kThreads, 0, st>>>(ta, tb, ts, boff,
-                                                                    (uint32_t)nbk, ka, kb, sep);
-      HLC_LAUNCH_CHECK();
-      if (maxb > kSmallBucket) {
-        k_bucket_sort<<<(unsigned)std::min<uint64_t>(nbk, 148u * 32u), kBucketThreads, 0, st>>>(
-            ta, tb, ts, boff, (uint32_t)nbk, ka, kb, sep, P->dev_err);
-        HLC_LAUNCH_CHECK();
-      }
-      k_bucket_jobs<<<grid_for(nbk, kThreads), kThreads, 0, st>>>(boff, nbk, nb, job);
-      HLC_LAUNCH_CHECK();
-      done = true;
-    }
-    ar.drop(scr);
-  }
-  if (!done) {
-    // stable LSD: id_b, then id_a, then job
-    uint32_t* perm = ar.get_n<uint32_t>(M + 1);
-    uint64_t* tk = ar.get_n<uint64_t>(M + 1);
-    uint32_t* tv = ar.get_n<uint32_t>(M + 1);
-    void* scr = ar.get(sort_scratch_bytes(M + 1, 8));
-    if (!perm || !tk || !tv || !scr) return HLC_ENOMEM;
-    unsigned g = grid_for(M, kThreads);
-    k_iota<<<g, kThreads, 0, st>>>(perm, M);
-    HLC_CUDA(cudaMemcpyAsync(ta, kb, M * 8, cudaMemcpyDeviceToDevice, st));
-    HLC_TRY(radix_sort_pairs<uint64_t>(ta, perm, tk, tv, M, 64, scr, P->dev_err, st));
-    k_gather<uint64_t><<<g, kThreads, 0, st>>>(ka, perm, M, ta);
-    HLC_TRY(radix_sort_pairs<uint64_t>(ta, perm, tk, tv, M, 64, scr, P->dev_err, st));
-    k_gather<uint32_t><<<g, kThreads, 0, st>>>(job, perm, M, tj);
-    HLC_CUDA(cudaMemcpyAsync(tv, tj, M * 4, cudaMemcpyDeviceToDevice, st));
-    HLC_TRY(radix_sort_pairs<uint32_t>(tv, perm, (uint32_t*)tk, (uint32_t*)tk + M + 1, M, 16, scr,
-                                       P->dev_err, st));
-    k_gather<uint64_t><<<g, kThreads, 0, st>>>(ka, perm, M, ta);
-    k_gather<uint64_t><<<g, kThreads, 0, st>>>(kb, perm, M, tb);
-    if (sep) k_gather<double><<<g, kThreads, 0, st>>>(sep, perm, M, ts);
-    k_gather<uint32_t><<<g, kThreads, 0, st>>>(job, perm, M, tj);
-    HLC_LAUNCH_CHECK();
-    oa = ta;
-    ob = tb;
-    os = ts;
-    oj = tj;
-  }
+  uint64_t *oa = nullptr, *ob = nullptr;
+  double* os = nullptr;
+  uint32_t* oj = nullptr;
+  HLC_TRY(order_rows(P, rows32, M, bhist, boff, nbk, nb, bshift, bmask, true, want_sep, &oa, &ob,
+                     &os, &oj));
+  ar.drop(rows32);
+  ar.drop(bhist);
+  ar.drop(boff);
   ev_record(P, 6);
   HLC_CUDA(cudaStreamSynchronize(st));
   HLC_TRY(check_dev_err(P->dev_err, st, "hlc_match"));
@@ -1980,11 +1971,11 @@ int hlc_ang2pix(const double* ra, const double* dec, uint64_t n, int order, int 
     }
     cudaMemsetAsync(nslow, 0, 8, st);
     k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-        ra, dec, n, order, pix_const(order), pix, idx, slow, nslow, err);
+        ra, dec, nullptr, n, order, pix_const(order), pix, idx, nullptr, slow, nslow, err);
     k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, order, slow, nslow, pix);
   } else {
     k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-        ra, dec, n, order, pix_const(order), pix, idx, nullptr, nullptr, err);
+        ra, dec, nullptr, n, order, pix_const(order), pix, idx, nullptr, nullptr, nullptr, err);
   }
   int rc = HLC_OK;
   if (cudaGetLastError() != cudaSuccess) {
@@ -2062,8 +2053,8 @@ int hlc_quad_cells(const double* ra, const double* dec, uint64_t n, double radiu
   HLC_CUDA(cudaMallocAsync(&err, sizeof(int), st));
   cudaMemsetAsync(err, 0, sizeof(int), st);
   k_quad_cells<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-      ra, dec, n, radius_arcsec / 3600.0, order, pix_const(order), out, (uint32_t*)count,
-      nullptr, nullptr, err);
+      ra, dec, nullptr, n, radius_arcsec / 3600.0, order, pix_const(order), out,
+      (uint32_t*)count, nullptr, nullptr, nullptr, err);
   int rc = cudaGetLastError() == cudaSuccess ? HLC_OK : HLC_ECUDA;
   if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_quad_cells");
   cudaFreeAsync(err, st);

@@ -14,6 +14,14 @@
 namespace hlc {
 
 constexpr int kThreads = 256;
+
+// One source in 32 bytes (one DRAM sector): normalised RA, Dec, id.  Written
+// in input order by the preparation kernels so that later gathers by source
+// index touch a single sector.
+struct __align__(32) SrcRec {
+  double ra, dec;
+  uint64_t id, pad;
+};
 // Number of B entries in a table cell up to which the FP32 join uses the
 // table order (sparse regions).
 #ifndef HLC_SPARSE_CELL
@@ -32,8 +40,9 @@ constexpr uint32_t kSparseCell = HLC_SPARSE_CELL;
 // by k_prep_fallback, so that warps do not diverge into the binary64 path.)
 template <bool FAST>
 __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restrict__ dec,
-                            uint64_t n, int order, PixConst K, uint32_t* __restrict__ key,
-                            uint32_t* __restrict__ idx, uint32_t* __restrict__ slow,
+                            const uint64_t* __restrict__ id, uint64_t n, int order, PixConst K,
+                            uint32_t* __restrict__ key, uint32_t* __restrict__ idx,
+                            SrcRec* __restrict__ rec, uint32_t* __restrict__ slow,
                             unsigned long long* __restrict__ nslow, int* __restrict__ err) {
   for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n;
        i0 += (uint64_t)gridDim.x * blockDim.x) {
@@ -52,13 +61,23 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
           defer = !f_pix(split_f64(a), fd, order, K, &k);
         }
       } else {
-        if (!c_valid(a, d))
+        if (!c_valid(a, d)) {
           atomicOr(err, DERR_INPUT);
-        else
-          k = c_ang2pix(c_norm_ra(a), d, order);
+        } else {
+          a = c_norm_ra(a);
+          k = c_ang2pix(a, d, order);
+        }
       }
       key[i] = k;
       idx[i] = (uint32_t)i;
+      if (rec) {
+        SrcRec r;
+        r.ra = a;
+        r.dec = d;
+        r.id = id[i];
+        r.pad = 0;
+        rec[i] = r;
+      }
     }
     if (FAST) {
       unsigned b = __ballot_sync(0xffffffffu, defer);
@@ -90,8 +109,9 @@ __global__ void k_prep_fallback(const double* __restrict__ ra, const double* __r
 // (FAST: sources with an undecided pixel are queued for k_quad_fallback.)
 template <bool FAST>
 __global__ void k_quad_cells(const double* __restrict__ ra, const double* __restrict__ dec,
-                             uint64_t n, double R, int order, PixConst K,
-                             uint32_t* __restrict__ cells, uint32_t* __restrict__ count,
+                             const uint64_t* __restrict__ id, uint64_t n, double R, int order,
+                             PixConst K, uint32_t* __restrict__ cells,
+                             uint32_t* __restrict__ count, SrcRec* __restrict__ rec,
                              uint32_t* __restrict__ slow, unsigned long long* __restrict__ nslow,
                              int* __restrict__ err) {
   for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n;
@@ -117,6 +137,14 @@ __global__ void k_quad_cells(const double* __restrict__ ra, const double* __rest
 #pragma unroll
       for (int e = 0; e < 5; ++e) cells[5 * i + e] = e < m ? c[e] : 0xFFFFFFFFu;
       count[i] = (uint32_t)m;
+      if (rec) {
+        SrcRec r;
+        r.ra = c_valid(a, d) ? c_norm_ra(a) : a;
+        r.dec = d;
+        r.id = id[i];
+        r.pad = 0;
+        rec[i] = r;
+      }
     }
     if (FAST) {
       unsigned b = __ballot_sync(0xffffffffu, defer);
@@ -162,43 +190,31 @@ __global__ void k_quad_emit(const uint32_t* __restrict__ cells, const uint32_t* 
   }
 }
 
-// Sorted payload: binary64 canonical unit vectors (plain form) and ids.
-__global__ void k_payload64(const double* __restrict__ ra, const double* __restrict__ dec,
-                            const uint64_t* __restrict__ id, const uint32_t* __restrict__ idx,
+// Sorted payload: binary64 canonical unit vectors (plain form).
+__global__ void k_payload64(const SrcRec* __restrict__ rec, const uint32_t* __restrict__ idx,
                             uint64_t m, double* __restrict__ vx, double* __restrict__ vy,
-                            double* __restrict__ vz, uint64_t* __restrict__ id_s) {
+                            double* __restrict__ vz) {
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
        e += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t i = idx[e];
-    double a = ra[i], d = dec[i];
+    SrcRec r = rec[idx[e]];
     double x = 0, y = 0, z = 0;
-    if (c_valid(a, d)) c_unitvec(c_norm_ra(a), d, &x, &y, &z);
+    if (c_valid(r.ra, r.dec)) c_unitvec(r.ra, r.dec, &x, &y, &z);
     vx[e] = x;
     vy[e] = y;
     vz[e] = z;
-    id_s[e] = id[i];
   }
 }
 
 // Sorted payload of the guard form: FP32 unit vectors with a known error
-// bound, the normalised coordinates (for the binary64 recheck and the
-// separations) and the ids, all in entry order.
-__global__ void k_payload32(const double* __restrict__ ra, const double* __restrict__ dec,
-                            const uint64_t* __restrict__ id, const uint32_t* __restrict__ idx,
-                            uint64_t m, float4* __restrict__ v, double2* __restrict__ rd,
-                            uint64_t* __restrict__ id_s) {
+// bound, in entry order.
+__global__ void k_payload32(const SrcRec* __restrict__ rec, const uint32_t* __restrict__ idx,
+                            uint64_t m, float4* __restrict__ v) {
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
        e += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t i = idx[e];
-    double a = ra[i], d = dec[i];
+    SrcRec r = rec[idx[e]];
     float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (bits_finite(a) && bits_abs_le(d, 90.0)) {
-      if (!bits_in_ra_range(a)) a = c_norm_ra(a);
-      u = fp32_unitvec(a, d);
-    }
+    if (bits_finite(r.ra) && bits_abs_le(r.dec, 90.0)) u = fp32_unitvec(r.ra, r.dec);
     v[e] = u;
-    rd[e] = make_double2(a, d);
-    id_s[e] = id[i];
   }
 }
 
@@ -437,8 +453,9 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
 // the canonical arithmetic from the original coordinates).
 __global__ void __launch_bounds__(kThreads) k_recheck(
     const uint2* __restrict__ band, const unsigned long long* __restrict__ nband_dev,
-    uint64_t band_cap, const double2* __restrict__ rdA, const double2* __restrict__ rdB,
-    double C, uint2* rows, unsigned long long* count, uint64_t cap, int* err) {
+    uint64_t band_cap, const uint32_t* __restrict__ idxA, const uint32_t* __restrict__ idxB,
+    const SrcRec* __restrict__ recA, const SrcRec* __restrict__ recB, double C, uint2* rows,
+    unsigned long long* count, uint64_t cap, int* err) {
   uint64_t nb = *nband_dev;
   if (nb > band_cap) nb = band_cap;
   for (uint64_t b0 = (uint64_t)blockIdx.x * kThreads; b0 < nb; b0 += (uint64_t)gridDim.x * kThreads) {
@@ -447,14 +464,27 @@ __global__ void __launch_bounds__(kThreads) k_recheck(
     uint2 p = make_uint2(0u, 0u);
     if (q < nb) {
       p = band[q];
-      double2 a = rdA[p.x], b = rdB[p.y];
+      SrcRec a = recA[idxA[p.x]], b = recB[idxB[p.y]];
       double ax, ay, az, bx, by, bz;
-      c_unitvec(a.x, a.y, &ax, &ay, &az);
-      c_unitvec(b.x, b.y, &bx, &by, &bz);
+      c_unitvec(a.ra, a.dec, &ax, &ay, &az);
+      c_unitvec(b.ra, b.dec, &bx, &by, &bz);
       hit = c_chord2(ax, ay, az, bx, by, bz) <= C;
     }
     warp_emit(hit, p.x, p.y, rows, count, cap, err);
   }
+}
+
+// Highest differing bit of the source ids (OR of id ^ id[0]).
+__global__ void k_id_diff_rec(const SrcRec* __restrict__ rec, uint64_t n,
+                              unsigned long long* __restrict__ out) {
+  if (n == 0) return;
+  uint64_t first = rec[0].id;
+  unsigned long long acc = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    acc |= rec[i].id ^ first;
+  for (int o = 16; o > 0; o >>= 1) acc |= __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicOr(out, acc);
 }
 
 template <typename T>

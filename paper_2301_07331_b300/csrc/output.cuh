@@ -13,6 +13,7 @@
 #include "canon.cuh"
 #include "common.cuh"
 #include "fp32.cuh"
+#include "match.cuh"
 
 namespace hlc {
 
@@ -95,37 +96,60 @@ __device__ __forceinline__ double sep_arcsec_f2(double ra1, double dec1, double 
   return (double)r.hi + (double)r.lo;
 }
 
-// ids + separation of each row (from the entry-ordered arrays, which rows
-// visit with good locality), and the bucket histogram of id_a.
+// One output row in 32 bytes (one sector), used while the rows are ordered.
+struct __align__(32) OutRow {
+  uint64_t a, b;
+  double s;
+  uint32_t job, pad;
+};
+
+// ids + separation of each row, and the bucket histogram of id_a.
 template <bool FP32>
 __global__ void k_rows(const uint2* __restrict__ rows, uint64_t M,
-                       const uint64_t* __restrict__ idA, const uint64_t* __restrict__ idB,
+                       const uint32_t* __restrict__ idxA, const uint32_t* __restrict__ idxB,
+                       const SrcRec* __restrict__ recA, const SrcRec* __restrict__ recB,
                        const double* __restrict__ axv, const double* __restrict__ ayv,
                        const double* __restrict__ azv, const double* __restrict__ bxv,
                        const double* __restrict__ byv, const double* __restrict__ bzv,
-                       const double2* __restrict__ rdA, const double2* __restrict__ rdB,
-                       int want_sep, uint64_t* __restrict__ ka, uint64_t* __restrict__ kb,
-                       double* __restrict__ sep, int bshift, uint32_t bmask,
+                       int want_sep, OutRow* __restrict__ out, int bshift, uint32_t bmask,
                        uint32_t* __restrict__ bhist) {
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
        m += (uint64_t)gridDim.x * blockDim.x) {
     uint2 p = rows[m];
-    uint64_t a = idA[p.x];
-    ka[m] = a;
-    kb[m] = idB[p.y];
-    if (bhist) atomicAdd(&bhist[(uint32_t)(a >> bshift) & bmask], 1u);
+    SrcRec u = recA[idxA[p.x]], w = recB[idxB[p.y]];
+    OutRow o;
+    o.a = u.id;
+    o.b = w.id;
+    o.s = 0.0;
+    o.job = 0;
+    o.pad = 0;
+    if (bhist) atomicAdd(&bhist[(uint32_t)(u.id >> bshift) & bmask], 1u);
     if (want_sep) {
       double sv;
       if (FP32) {
-        double2 u = rdA[p.x], w = rdB[p.y];
-        sv = sep_arcsec_f2(u.x, u.y, w.x, w.y);
-        if (sv < 0.0) sv = sep_arcsec_haversine(u.x, u.y, w.x, w.y);
+        sv = sep_arcsec_f2(u.ra, u.dec, w.ra, w.dec);
+        if (sv < 0.0) sv = sep_arcsec_haversine(u.ra, u.dec, w.ra, w.dec);
       } else {
         sv = sep_arcsec_from_chord2(
             c_chord2(axv[p.x], ayv[p.x], azv[p.x], bxv[p.y], byv[p.y], bzv[p.y]));
       }
-      sep[m] = sv;
+      o.s = sv;
     }
+    out[m] = o;
+  }
+}
+
+// Unpack rows into the result columns (used by the radix-sort fallback).
+__global__ void k_rows_split(const OutRow* __restrict__ in, uint64_t M, uint64_t* __restrict__ a,
+                             uint64_t* __restrict__ b, double* __restrict__ s,
+                             uint32_t* __restrict__ job) {
+  for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
+       m += (uint64_t)gridDim.x * blockDim.x) {
+    OutRow o = in[m];
+    a[m] = o.a;
+    b[m] = o.b;
+    if (s) s[m] = o.s;
+    if (job) job[m] = o.job;
   }
 }
 
@@ -138,18 +162,16 @@ __global__ void k_max_u32(const uint32_t* __restrict__ v, uint64_t n, uint32_t* 
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
-__global__ void k_bucket_scatter(const uint64_t* __restrict__ ka, const uint64_t* __restrict__ kb,
-                                 const double* __restrict__ sep, uint64_t M, int bshift,
-                                 uint32_t bmask, uint32_t* __restrict__ cursor,
-                                 uint64_t* __restrict__ ta, uint64_t* __restrict__ tb,
-                                 double* __restrict__ ts) {
+__global__ void k_bucket_scatter(const OutRow* __restrict__ in, uint64_t M, int bshift,
+                                 uint32_t bmask, int nb_job, uint32_t* __restrict__ cursor,
+                                 OutRow* __restrict__ out) {
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
        m += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t a = ka[m];
-    uint32_t pos = atomicAdd(&cursor[(uint32_t)(a >> bshift) & bmask], 1u);
-    ta[pos] = a;
-    tb[pos] = kb[m];
-    if (sep) ts[pos] = sep[m];
+    OutRow o = in[m];
+    uint64_t bk = (nb_job >= 0 ? ((uint64_t)o.job << nb_job) : 0ull) |
+                  ((uint32_t)(o.a >> bshift) & bmask);
+    uint32_t pos = atomicAdd(&cursor[bk], 1u);
+    out[pos] = o;
   }
 }
 
@@ -164,32 +186,32 @@ __device__ __forceinline__ bool row_less(uint64_t a1, uint64_t b1, uint64_t s1, 
 // output arrays.
 constexpr uint32_t kSmallBucket = 32;
 
-__global__ void k_bucket_small(const uint64_t* __restrict__ ta, const uint64_t* __restrict__ tb,
-                               const double* __restrict__ ts, const uint32_t* __restrict__ boff,
+__global__ void k_bucket_small(const OutRow* __restrict__ t, const uint32_t* __restrict__ boff,
                                uint32_t nbuckets, uint64_t* __restrict__ oa,
-                               uint64_t* __restrict__ ob, double* __restrict__ os) {
+                               uint64_t* __restrict__ ob, double* __restrict__ os,
+                               uint32_t* __restrict__ oj) {
   for (uint32_t bk = blockIdx.x * blockDim.x + threadIdx.x; bk < nbuckets;
        bk += gridDim.x * blockDim.x) {
     uint32_t lo = boff[bk], hi = boff[bk + 1];
     uint32_t n = hi - lo;
     if (n == 0 || n > kSmallBucket) continue;
     for (uint32_t i = 0; i < n; ++i) {
-      uint64_t a = ta[lo + i], b = tb[lo + i];
-      double sv = ts ? ts[lo + i] : 0.0;
-      uint64_t sb = (uint64_t)__double_as_longlong(sv);
+      OutRow r = t[lo + i];
+      uint64_t sb = (uint64_t)__double_as_longlong(r.s);
       uint32_t j = i;
       while (j > 0) {
         uint64_t pa = oa[lo + j - 1], pb = ob[lo + j - 1];
         uint64_t ps = os ? (uint64_t)__double_as_longlong(os[lo + j - 1]) : 0ull;
-        if (!row_less(a, b, sb, pa, pb, ps)) break;
+        if (!row_less(r.a, r.b, os ? sb : 0ull, pa, pb, ps)) break;
         oa[lo + j] = pa;
         ob[lo + j] = pb;
         if (os) os[lo + j] = os[lo + j - 1];
         --j;
       }
-      oa[lo + j] = a;
-      ob[lo + j] = b;
-      if (os) os[lo + j] = sv;
+      oa[lo + j] = r.a;
+      ob[lo + j] = r.b;
+      if (os) os[lo + j] = r.s;
+      if (oj) oj[lo + i] = r.job;  // every row of a bucket has the same job
     }
   }
 }
@@ -197,10 +219,9 @@ __global__ void k_bucket_small(const uint64_t* __restrict__ ta, const uint64_t* 
 // One CTA per larger bucket (kSmallBucket < rows <= kBucketCap): bitonic
 // sort in shared memory.
 __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(
-    const uint64_t* __restrict__ ta, const uint64_t* __restrict__ tb,
-    const double* __restrict__ ts, const uint32_t* __restrict__ boff, uint32_t nbuckets,
-    uint64_t* __restrict__ oa, uint64_t* __restrict__ ob, double* __restrict__ os,
-    int* __restrict__ err) {
+    const OutRow* __restrict__ t, const uint32_t* __restrict__ boff, uint32_t nbuckets,
+    int use_sep, uint64_t* __restrict__ oa, uint64_t* __restrict__ ob, double* __restrict__ os,
+    uint32_t* __restrict__ oj, int* __restrict__ err) {
   __shared__ uint64_t A[kBucketCap], B[kBucketCap], S[kBucketCap];
   for (uint32_t bk = blockIdx.x; bk < nbuckets; bk += gridDim.x) {
     uint32_t lo = boff[bk], hi = boff[bk + 1];
@@ -214,9 +235,11 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(
     while (np < n) np <<= 1;
     for (uint32_t i = threadIdx.x; i < np; i += kBucketThreads) {
       if (i < n) {
-        A[i] = ta[lo + i];
-        B[i] = tb[lo + i];
-        S[i] = ts ? (uint64_t)__double_as_longlong(ts[lo + i]) : 0ull;
+        OutRow r = t[lo + i];
+        A[i] = r.a;
+        B[i] = r.b;
+        S[i] = use_sep ? (uint64_t)__double_as_longlong(r.s) : 0ull;
+        if (oj) oj[lo + i] = r.job;
       } else {
         A[i] = ~0ull;
         B[i] = ~0ull;

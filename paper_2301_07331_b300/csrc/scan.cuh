@@ -70,20 +70,36 @@ __global__ void __launch_bounds__(kBlock) k_scan_excl(const uint32_t* __restrict
   const uint64_t e0 = (uint64_t)tile * kTile + (uint64_t)t * kIpt;
   uint32_t v[kIpt];
   unsigned long long sum = 0;
+  if (e0 + kIpt <= n) {  // two 16-byte loads (the array is 256-byte aligned)
+    uint4 x = *reinterpret_cast<const uint4*>(in + e0);
+    uint4 y = *reinterpret_cast<const uint4*>(in + e0 + 4);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+  } else {
 #pragma unroll
-  for (int i = 0; i < kIpt; ++i) {
-    v[i] = (e0 + i < n) ? in[e0 + i] : 0u;
-    sum += v[i];
+    for (int i = 0; i < kIpt; ++i) v[i] = (e0 + i < n) ? in[e0 + i] : 0u;
   }
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) sum += v[i];
   unsigned long long tot;
   unsigned long long pre = rs::block_excl_scan(sum, S.ws, &tot);
   if (t == 0) S.base = lookback_prefix(tile, tot, lb, err);
   __syncthreads();
   unsigned long long run = S.base + pre;
+  OutT o[kIpt];
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
-    if (e0 + i < n) out[e0 + i] = (OutT)run;
+    o[i] = (OutT)run;
     run += v[i];
+  }
+  if (sizeof(OutT) == 4 && e0 + kIpt <= n) {
+    uint4* dst = reinterpret_cast<uint4*>(out + e0);
+    dst[0] = make_uint4((uint32_t)o[0], (uint32_t)o[1], (uint32_t)o[2], (uint32_t)o[3]);
+    dst[1] = make_uint4((uint32_t)o[4], (uint32_t)o[5], (uint32_t)o[6], (uint32_t)o[7]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < kIpt; ++i)
+      if (e0 + i < n) out[e0 + i] = o[i];
   }
   if (e0 < n && e0 + kIpt >= n) *total = run;  // the thread holding element n-1
 }
