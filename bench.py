@@ -48,7 +48,7 @@ def _dist():
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -68,6 +68,9 @@ class Clocks:
         except Exception:
             self.proc = None
 
+    def mark(self, which: str):
+        setattr(self, which, time.time())
+
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -79,16 +82,22 @@ class Clocks:
         self.f.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        t0 = getattr(self, "t0", None)
+        t1 = getattr(self, "t1", None)
         for line in open(self.path):
             p = [x.strip() for x in line.split(",")]
-            if len(p) < 9:
+            if len(p) < 10:
                 continue
             try:
-                sm.append(float(p[1]))
-                smax.append(float(p[2]))
-            except ValueError:
+                ts = time.mktime(time.strptime(p[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                ts += float("0." + p[0].split(".")[1]) if "." in p[0] else 0.0
+                if t0 is not None and t1 is not None and not (t0 - 0.15 <= ts <= t1 + 0.15):
+                    continue
+                sm.append(float(p[2]))
+                smax.append(float(p[3]))
+            except (ValueError, IndexError):
                 continue
-            for nm, v in zip(names, p[5:9]):
+            for nm, v in zip(names, p[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         if not sm:
@@ -126,7 +135,7 @@ def run_hlc(args):
         hlc.hlc_free(plan)
         return st, n
 
-    def timed(precision, K, W):
+    def timed(precision, K, W, clk=None):
         for _ in range(W):
             step(precision, A, B)
         torch.cuda.synchronize()
@@ -136,12 +145,16 @@ def run_hlc(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         stats = []
+        if clk is not None:
+            clk.mark("t0")
         e0.record(stream)
         for _ in range(K):
             st, n = step(precision, A, B)
             stats.append(st)
         e1.record(stream)
         torch.cuda.synchronize()
+        if clk is not None:
+            clk.mark("t1")
         if world > 1:
             dist.barrier()
         ms = e0.elapsed_time(e1) / K
@@ -153,7 +166,7 @@ def run_hlc(args):
 
     clocks = Clocks(local)
     clocks.start()
-    ms, stats, nmatch = timed(prec, args.steps, args.warmup)
+    ms, stats, nmatch = timed(prec, args.steps, args.warmup, clocks)
     clk = clocks.stop()
     other = hlc.HLC_FP64 if prec == hlc.HLC_FP32_GUARD else hlc.HLC_FP32_GUARD
     ms_other, stats_other, _ = timed(other, max(2, args.steps // 2), 1)
@@ -164,22 +177,32 @@ def run_hlc(args):
     sources = (na + nb) * world
     value = sources / (ms / 1e3)
     tests = stats[-1]["pair_tests"]
-    pair_rate = tests / (mean("ms_pair", stats) / 1e3) if mean("ms_pair", stats) > 0 else None
 
-    # roofline of the dominant stage (HBM-bound sort of the cell keys)
+    # roofline of the dominant kernel: the pair test (k_pair), timed live by
+    # the library's CUDA events on the launching stream
     peak, peak_kind = _peaks()
     stage_ms = {k: mean(k, stats) for k in ("ms_prep", "ms_sort", "ms_index", "ms_candidates",
                                             "ms_pair", "ms_recheck", "ms_output")}
-    m_entries = stats[-1]["entries_a"] + stats[-1]["entries_b"]
-    npass = (2 * L + 4 + 7) // 8
-    sort_bytes = m_entries * (4 + npass * 16)  # histogram read + per pass key/value r+w
-    sort_gbs = sort_bytes / (stage_ms["ms_sort"] / 1e3) / 1e9
-    roofline = {"kernel": "k_onesweep (cell-key radix sort, 4 passes) + k_digit_hist",
-                "bound": "hbm", "achieved": round(sort_gbs, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(sort_gbs / peak, 4), "traffic": None,
-                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
+    last = stats[-1]
+    mA, mB = last["entries_a"], last["entries_b"]
+    lt = 0
+    while lt < L and 12 * 4 ** lt < mB:
+        lt += 1
+    pair_bytes = (mA * (4 + 16) + mB * 16 + (12 * 4 ** lt + 1) * 4
+                  + 8 * (last["matches"] + last["band_candidates"]))
+    pair_gbs = pair_bytes / (stage_ms["ms_pair"] / 1e3) / 1e9
+    tr = TRAFFIC.get("k_pair<1,0,0>")
+    traffic = tr["bytes_per_launch"] if tr and tr["sources"] == _kernel_sources_sha() else None
+    roofline = {"kernel": "k_pair<FP32,complete> (candidates + pair test)",
+                "bound": "hbm", "achieved": round(pair_gbs, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(pair_gbs / peak, 4), "traffic": traffic,
+                "peak_source": (peak_kind + " (MEASURED_PEAKS.json hbm_gbs)")
                 if peak_kind == "measured" else "fallback 6.4 TB/s",
-                "bytes_per_launch_basis": "(4 + 16 * passes) bytes per entry"}
+                "bytes_per_launch": int(pair_bytes),
+                "bytes_basis": "20 B per A entry (key + FP32 vector), 16 B per B entry, "
+                               "4 B per offset-table slot, 8 B per emitted row",
+                "ms_per_launch": stage_ms["ms_pair"]}
+    alg = alg_pair_tests(hlc, A, B, L) if args.mode == "complete" else None
 
     # end to end: pinned host inputs in, sorted rows back to host
     e2e = None
@@ -190,7 +213,8 @@ def run_hlc(args):
                              B.id.cpu().pin_memory())
         import numpy as np
         times = []
-        for it in range(args.warmup + args.steps):
+        ke = min(args.steps, 30)
+        for it in range(args.warmup + ke):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             plan = hlc.hlc_plan(Ah, Bh, r, L, coarse_level=Lc, boundary=mode, precision=prec,
@@ -202,7 +226,7 @@ def run_hlc(args):
             if it >= args.warmup:
                 times.append(t1 - t0)
         t = sum(times) / len(times)
-        e2e = {"value": sources / t, "unit": "sources/s", "ms_per_step": t * 1e3,
+        e2e = {"value": sources / t, "unit": "sources/s", "ms_per_step": t * 1e3, "steps": ke,
                "h2d_bytes_per_step": (na + nb) * 24, "d2h_bytes_per_step": int(ia.size) * 24}
 
     # CPU oracle on a bounded sample of the same workload (rank 0 only)
@@ -225,7 +249,8 @@ def run_hlc(args):
                        "form": args.precision + " (chosen)",
                        "l2": "inputs (480 MB) larger than L2 (126 MB)",
                        "parallelism": "independent instance per GPU" if world > 1 else "1 GPU"},
-            "pair_tests_per_s": pair_rate, "pair_tests": tests, "matches": nmatch,
+            "pair_tests_per_s": (alg / (stage_ms["ms_pair"] / 1e3)) if alg else None,
+            "pair_tests_alg": alg, "pair_tests_executed": tests, "matches": nmatch,
             "band_candidates": stats[-1]["band_candidates"],
             "plain_form": {"precision": "fp64" if other == hlc.HLC_FP64 else "fp32",
                            "ms_per_step": ms_other, "value": sources / (ms_other / 1e3),
@@ -240,6 +265,40 @@ def run_hlc(args):
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+# DRAM bytes (read + write) per launch of a kernel from one ncu capture, with
+# the digest of the kernel sources it was taken on; a changed source voids it.
+TRAFFIC = {}
+
+_KERNEL_SOURCES = ("match.cuh", "canon.cuh", "index.cuh", "learned.cuh", "common.cuh",
+                   "fp32.cuh", "fastpix.cuh")
+
+
+def _kernel_sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in _KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2301_07331_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def alg_pair_tests(hlc, A, B, L):
+    """Algorithmic pair tests of complete mode: sum over A cells c of
+    n_A(c) * sum of n_B over c and its neighbours (padded or superset tests
+    not counted).  Computed outside the timed region."""
+    import torch
+    pa = hlc.hlc_ang2pix(A.ra, A.dec, L).to(torch.int64) & 0xFFFFFFFF
+    pb = hlc.hlc_ang2pix(B.ra, B.dec, L).to(torch.int64) & 0xFFFFFFFF
+    ua, ca = torch.unique(pa, return_counts=True)
+    ub, cb = torch.unique(pb, return_counts=True)
+    nb = hlc.hlc_neighbours(ua.to(torch.int32), L)
+    cells = torch.cat([ua[:, None], nb], 1)
+    idx = torch.searchsorted(ub, cells.clamp(min=0)).clamp(max=max(ub.numel() - 1, 0))
+    present = (cells >= 0) & (ub[idx] == cells)
+    nsum = torch.where(present, cb[idx], torch.zeros_like(cb[idx])).sum(1)
+    return int((ca * nsum).sum())
 
 
 def cpu_baseline(A, B, r, L):
@@ -307,8 +366,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hlc", choices=["hlc", "reference"])
     ap.add_argument("--n", type=int, default=10_000_000)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])

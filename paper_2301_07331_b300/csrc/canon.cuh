@@ -227,21 +227,79 @@ __device__ __forceinline__ void nest_to_fxy(uint32_t pix, int order, int* face, 
   *iy = (int)gather_bits(p >> 1);
 }
 
-// The cell itself followed by its distinct present neighbours; returns count.
-__device__ __forceinline__ int cell_neighbourhood(uint32_t pix, int order, uint32_t out[9]) {
+constexpr uint32_t kNoCell = 0xFFFFFFFFu;
+
+// The cell itself in slot 0 and its neighbours in slots 1..8, kNoCell where a
+// neighbour is missing (the 7-neighbour corners) or repeats an earlier slot.
+// Slot positions are fixed, so callers index the array with constants and it
+// stays in registers.  Cells away from their base face's edges take a fast
+// path: +-1 on the interleaved x (even) and y (odd) bit fields of the nested
+// index directly, with the carry or borrow run through the other field's
+// bits.
+__device__ __forceinline__ void cell_neighbourhood9(uint32_t pix, int order, uint32_t out[9]) {
+  out[0] = pix;
+  if (order > 0) {
+    const uint32_t lmask = (1u << (2 * order)) - 1u;
+    const uint32_t XM = 0x55555555u & lmask, YM = 0xAAAAAAAAu & lmask;
+    const uint32_t fb = pix & ~lmask;
+    const uint32_t xm = pix & XM, ym = pix & YM;
+    if (xm != 0 && xm != XM && ym != 0 && ym != YM) {
+      const uint32_t xs[3] = {(xm - 1u) & XM, xm, ((xm | YM) + 1u) & XM};
+      const uint32_t ys[3] = {(ym - 2u) & YM, ym, ((ym | XM) + 2u) & YM};
+      int m = 1;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          if (a != 1 || b != 1) out[m++] = fb | xs[a] | ys[b];
+      return;
+    }
+  }
   int face, ix, iy;
   nest_to_fxy(pix, order, &face, &ix, &iy);
-  int m = 0;
-  out[m++] = pix;
 #pragma unroll
   for (int d = 0; d < 8; ++d) {
     long long q = nbr_step(face, ix, iy, d_dirs[d][0], d_dirs[d][1], order);
-    if (q < 0) continue;
-    bool dup = false;
-    for (int e = 0; e < m; ++e) dup |= (out[e] == (uint32_t)q);
-    if (!dup) out[m++] = (uint32_t)q;
+    uint32_t c = q < 0 ? kNoCell : (uint32_t)q;
+#pragma unroll
+    for (int e = 0; e <= d; ++e)
+      if (out[e] == c) c = kNoCell;
+    out[d + 1] = c;
   }
+}
+
+// The cell itself followed by its distinct present neighbours; returns count.
+__device__ __forceinline__ int cell_neighbourhood(uint32_t pix, int order, uint32_t out[9]) {
+  uint32_t nb[9];
+  cell_neighbourhood9(pix, order, nb);
+  int m = 0;
+#pragma unroll
+  for (int e = 0; e < 9; ++e)
+    if (nb[e] != kNoCell) out[m++] = nb[e];
   return m;
+}
+
+// The cells of order (order - d), d >= 1, that cover the neighbourhood (the
+// cell and its 8 neighbours) of a cell away from its base face's edges: the
+// 3x3 block spans at most two parent columns and two parent rows, so slots
+// 0..3 hold (x0,y0), (x1,y0), (x0,y1), (x1,y1), kNoCell where a column or
+// row repeats.  Returns false (slots untouched) for a cell on a face edge.
+__device__ __forceinline__ bool parent_cover4(uint32_t pix, int order, int d, uint32_t out[4]) {
+  if (order <= 0 || d < 1 || d > order) return false;
+  const uint32_t lmask = (1u << (2 * order)) - 1u;
+  const uint32_t XM = 0x55555555u & lmask, YM = 0xAAAAAAAAu & lmask;
+  const uint32_t xm = pix & XM, ym = pix & YM;
+  if (xm == 0 || xm == XM || ym == 0 || ym == YM) return false;
+  const int sh = 2 * d;
+  const uint32_t fb = (pix & ~lmask) >> sh;
+  const uint32_t x0 = ((xm - 1u) & XM) >> sh, x1 = (((xm | YM) + 1u) & XM) >> sh;
+  const uint32_t y0 = ((ym - 2u) & YM) >> sh, y1 = (((ym | XM) + 2u) & YM) >> sh;
+  const bool two_x = x1 != x0, two_y = y1 != y0;
+  out[0] = fb | x0 | y0;
+  out[1] = two_x ? (fb | x1 | y0) : kNoCell;
+  out[2] = two_y ? (fb | x0 | y1) : kNoCell;
+  out[3] = two_x && two_y ? (fb | x1 | y1) : kNoCell;
+  return true;
 }
 
 // ---- quad-direction cells (Algorithm 1) --------------------------------------

@@ -51,6 +51,60 @@ __global__ void k_coarse_hist(const uint32_t* __restrict__ keys, uint64_t n, int
   if ((threadIdx.x & 31) == 0 && h) atomicAdd(heads, h);
 }
 
+// Offset table of sorted keys without atomics or a scan: T[q] = first entry
+// whose key >> shift is >= q, for q in [0, S].  Each thread fills 8
+// consecutive slots: one binary search for the first, then a gallop forward
+// for each of the others.  It also counts the distinct keys among the
+// entries of its slots.
+__device__ __forceinline__ uint64_t gallop_lb(const uint32_t* __restrict__ keys, uint64_t m,
+                                              int shift, uint64_t from, uint64_t q) {
+  uint64_t step = 1, base = from;
+  while (base + step <= m && (uint64_t)(__ldg(keys + base + step - 1) >> shift) < q) {
+    base += step;
+    step <<= 1;
+  }
+  uint64_t a = base, b = base + step <= m ? base + step : m;
+  while (a < b) {
+    uint64_t mid = (a + b) >> 1;
+    if ((uint64_t)(__ldg(keys + mid) >> shift) < q)
+      a = mid + 1;
+    else
+      b = mid;
+  }
+  return a;
+}
+
+__global__ void k_coarse_table(const uint32_t* __restrict__ keys, uint64_t m, int shift,
+                               uint64_t S, uint32_t* __restrict__ T,
+                               unsigned long long* __restrict__ heads) {
+  unsigned long long h = 0;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t * 8 <= S;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t q0 = t * 8;
+    const uint64_t qlast = q0 + 8 <= S ? q0 + 8 : S;  // slot q0 + 8 belongs to the next thread
+    uint64_t lo = 0, hi = m;
+    while (lo < hi) {
+      uint64_t mid = (lo + hi) >> 1;
+      if ((uint64_t)(__ldg(keys + mid) >> shift) < q0)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    const uint64_t e0 = lo;
+    T[q0] = (uint32_t)lo;
+    for (uint64_t q = q0 + 1; q <= qlast; ++q) {
+      lo = gallop_lb(keys, m, shift, lo, q);
+      if (q < q0 + 8) T[q] = (uint32_t)lo;
+    }
+    // entries of slots [q0, qlast): [e0, lo); at the table's end lo = m
+    if (qlast == S) lo = m;
+    for (uint64_t e = e0; e < lo; ++e)
+      h += (e == 0 || __ldg(keys + e - 1) != __ldg(keys + e));
+  }
+  for (int o = 16; o > 0; o >>= 1) h += __shfl_down_sync(0xffffffffu, h, o);
+  if ((threadIdx.x & 31) == 0 && h) atomicAdd(heads, h);
+}
+
 // [begin, end) of the entries with key q.
 __device__ __forceinline__ uint2 cell_range(const CellIndex& ix, uint32_t q) {
   uint32_t Q = q >> ix.shift;

@@ -526,30 +526,13 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     k_max_u32<<<grid_for(X.parts, kThreads, 1024), kThreads, 0, st>>>(
         X.learned.err, X.parts, (uint32_t*)(P->ctr + C_LMAXERR));
     HLC_LAUNCH_CHECK();
-    if (m) {
-      k_coarse_hist<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.key, m, 0, nullptr, heads);
-      HLC_LAUNCH_CHECK();
-    }
   } else if (is_b) {
     X.table_order = coarse_table_order(m, L);
     X.table_shift = 2 * (L - X.table_order);
     uint64_t tsize = 12ull << (2 * X.table_order);
-    uint32_t* hist = ar.get_n<uint32_t>(tsize + 1);
     HLC_ALLOC(ar, X.table, uint32_t, tsize + 1);
-    void* scr = ar.get(scan_scratch_bytes(tsize + 1));
-    if (!hist || !scr) return HLC_ENOMEM;
-    HLC_CUDA(cudaMemsetAsync(hist, 0, (tsize + 1) * 4, st));
-    if (m) {
-      k_coarse_hist<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.key, m, X.table_shift, hist,
-                                                                 heads);
-      HLC_LAUNCH_CHECK();
-    }
-    HLC_TRY(scan_exclusive<uint32_t>(hist, X.table, tsize + 1, P->ctr + C_TOTAL, scr,
-                                     P->dev_err, st));
-    ar.drop(hist);
-    ar.drop(scr);
-  } else if (m) {
-    k_coarse_hist<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.key, m, 0, nullptr, heads);
+    k_coarse_table<<<grid_for(tsize / 8 + 1, kThreads), kThreads, 0, st>>>(
+        X.key, m, X.table_shift, tsize, X.table, heads);
     HLC_LAUNCH_CHECK();
   }
   cudaEventRecord(ev[3], st);
@@ -636,8 +619,7 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   P->stats.n_b = P->B.n;
   P->stats.entries_a = P->A.m;
   P->stats.entries_b = P->B.m;
-  P->stats.cells_a = hc[C_HEADS_A];
-  P->stats.cells_b = hc[C_HEADS_B];
+  P->stats.cells_b = P->p.index == HLC_INDEX_LEARNED ? P->B.u : hc[C_HEADS_B];
   P->stats.learned_models = P->p.index == HLC_INDEX_LEARNED ? P->B.parts : 0;
   P->stats.learned_max_err = (uint32_t)hc[C_LMAXERR];
   P->stats.join_level = P->join_level;
@@ -646,38 +628,6 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   P->stats.ms_index = t[4] + t[5];
   P->plan_launches = g_launches.load() - P->launches0;
   *out = P;
-  return HLC_OK;
-}
-
-// Sort rows (ka, kb, sep) by (id_a, id_b) with two stable LSD radix sorts;
-// results in (oa, ob, os).
-static int sort_rows_lsd(hlc_plan_t* P, uint64_t M, uint64_t* ka, uint64_t* kb, double* sep,
-                         uint64_t* oa, uint64_t* ob, double* os) {
-  Arena& ar = *P->out;
-  cudaStream_t st = plan_stream(P);
-  uint32_t* perm = ar.get_n<uint32_t>(M + 1);
-  uint64_t* tk = ar.get_n<uint64_t>(M + 1);
-  uint32_t* tv = ar.get_n<uint32_t>(M + 1);
-  void* scr = ar.get(sort_scratch_bytes(M + 1, 8));
-  if (!perm || !tk || !tv || !scr) return HLC_ENOMEM;
-  unsigned g = grid_for(M, kThreads);
-  k_iota<<<g, kThreads, 0, st>>>(perm, M);
-  HLC_LAUNCH_CHECK();
-  HLC_CUDA(cudaMemcpyAsync(oa, kb, M * 8, cudaMemcpyDeviceToDevice, st));
-  HLC_TRY(radix_sort_pairs<uint64_t>(oa, perm, tk, tv, M, 64, scr, P->dev_err, st));
-  k_gather<uint64_t><<<g, kThreads, 0, st>>>(ka, perm, M, oa);
-  HLC_LAUNCH_CHECK();
-  HLC_TRY(radix_sort_pairs<uint64_t>(oa, perm, tk, tv, M, 64, scr, P->dev_err, st));
-  k_gather<uint64_t><<<g, kThreads, 0, st>>>(kb, perm, M, ob);
-  HLC_LAUNCH_CHECK();
-  if (sep) {
-    k_gather<double><<<g, kThreads, 0, st>>>(sep, perm, M, os);
-    HLC_LAUNCH_CHECK();
-  }
-  ar.drop(perm);
-  ar.drop(tk);
-  ar.drop(tv);
-  ar.drop(scr);
   return HLC_OK;
 }
 
@@ -798,7 +748,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
     if (!rows || !band) return HLC_ENOMEM;
     HLC_CUDA(cudaMemsetAsync(P->ctr, 0, C_N * 8, st));
     PairSink sink{rows, P->ctr + C_ROWS, cap, band, P->ctr + C_BAND, bcap,
-                  P->ctr + C_TESTS, P->ctr + C_DUPS, P->dev_err};
+                  P->ctr + C_TESTS, P->ctr + C_DUPS, P->ctr + C_HEADS_A, P->dev_err};
     if (A.m && B.m) {
       unsigned grid = grid_for(A.m, kThreads, 148u * 16u);
       PairArgs pa;
@@ -921,6 +871,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   res->job = nullptr;
   res->on_device = 1;
   P->stats.pair_tests = h[C_TESTS];
+  P->stats.cells_a = h[C_HEADS_A];  // counted by the pair test
   P->stats.band_candidates = fp32 ? h[C_BAND] : 0;
   P->stats.matches = M;
   P->stats.quad_duplicates = h[C_DUPS];
@@ -1327,7 +1278,7 @@ static int batched_pair_graph(hlc_plan_t* P, uint2* rows, uint64_t cap, uint2* b
   if (e == cudaSuccess) {
     cudaMemsetAsync(P->ctr, 0, C_N * 8, cs);
     PairSink sink{rows, P->ctr + C_ROWS, cap, band, P->ctr + C_BAND, bcap,
-                  P->ctr + C_TESTS, P->ctr + C_DUPS, P->dev_err};
+                  P->ctr + C_TESTS, P->ctr + C_DUPS, nullptr, P->dev_err};
     BPairArgs pa;
     pa.mA = P->A.m;
     pa.keyA = P->keyA64;

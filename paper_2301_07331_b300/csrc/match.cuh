@@ -24,6 +24,12 @@ struct __align__(32) SrcRec {
 };
 // Number of B entries in a table cell up to which the FP32 join uses the
 // table order (sparse regions).
+#ifndef HLC_PAIR_UNROLL
+#define HLC_PAIR_UNROLL 4  // candidates per lane per pair-test iteration
+#endif
+#ifndef HLC_COARSE_FP64
+#define HLC_COARSE_FP64 0  // table-order join for sparse cells in the binary64 form too
+#endif
 #ifndef HLC_SPARSE_CELL
 #define HLC_SPARSE_CELL 32
 #endif
@@ -248,6 +254,7 @@ struct PairSink {
   uint64_t band_cap;
   unsigned long long* tests;    // algorithmic pair tests
   unsigned long long* dups;     // quad pairs owned by a smaller shared cell
+  unsigned long long* heads;    // distinct A cells
   int* err;
 };
 
@@ -267,6 +274,36 @@ __device__ __forceinline__ void warp_emit(bool emit, uint32_t ka, uint32_t kb, u
       atomicOr(err, DERR_OVERFLOW);
   }
 }
+
+// Rows staged per warp in shared memory and appended to the global list in
+// batches: one atomic reservation per flush instead of one per ballot.
+template <int CAP>
+struct WarpRows {
+  uint2* buf;     // this warp's CAP slots in shared memory
+  int fill = 0;   // warp-uniform
+  __device__ __forceinline__ void add(bool emit, uint32_t ka, uint32_t kb) {
+    unsigned b = __ballot_sync(0xffffffffu, emit);
+    if (emit) buf[fill + __popc(b & lanemask_lt())] = make_uint2(ka, kb);
+    fill += __popc(b);
+  }
+  __device__ __forceinline__ void flush(uint2* rows, unsigned long long* count, uint64_t cap,
+                                        int* err) {
+    if (fill == 0) return;
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(count, (unsigned long long)fill);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int i = lane; i < fill; i += 32) {
+      if (base + i < cap)
+        rows[base + i] = buf[i];
+      else
+        atomicOr(err, DERR_OVERFLOW);
+    }
+    __syncwarp();
+    fill = 0;
+  }
+};
 
 // Smallest cell shared by the quad cell lists of two sources.
 __device__ __forceinline__ uint32_t quad_owner(const uint32_t* __restrict__ ca,
@@ -324,7 +361,12 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
   const uint32_t sparse_cell = pa.sparse_cell;
   unsigned long long nlhit = 0, nllook = 0;
   const uint64_t stride = (uint64_t)gridDim.x * kThreads;
-  unsigned long long ntest = 0, ndup = 0;
+  unsigned long long ntest = 0, ndup = 0, nhead = 0;
+  constexpr int kRowCap = 256, kBandCap = FP32 ? 128 : 32;
+  __shared__ uint2 s_rows[kThreads / 32][kRowCap];
+  __shared__ uint2 s_band[kThreads / 32][kBandCap];
+  WarpRows<kRowCap> wrows{s_rows[threadIdx.x >> 5]};
+  WarpRows<kBandCap> wband{s_band[threadIdx.x >> 5]};
   // every thread of the warp runs the same number of outer iterations
   for (uint64_t kb0 = (uint64_t)blockIdx.x * kThreads; kb0 < mA; kb0 += stride) {
     uint64_t k = kb0 + (threadIdx.x);
@@ -341,22 +383,28 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
     }
     // neighbourhood of the A cell (complete) or the cell itself (quad).  In
     // complete mode a sparse region is joined at the order of B's offset
-    // table instead: the 3x3 block of table cells around the A cell's parent
-    // covers the fine 3x3 block (a superset of candidates, so the same
-    // exact set), and each of its ranges is read straight from the table.
+    // table instead: the (at most 4) table cells that cover the fine 3x3
+    // block hold a superset of the candidates, so the exact set is the same,
+    // and each of their ranges is read straight from the table.
+    bool coarse_lane = false;
     uint32_t nb[9];
-    int m = 0;
-    bool coarse = false;
+#pragma unroll
+    for (int s = 0; s < 9; ++s) nb[s] = kNoCell;
     if (live) {
       if (QUAD) {
         nb[0] = cell;
-        m = 1;
       } else {
-        uint32_t P = cell >> bix.shift;
-        coarse = FP32 && !LEARNED && bix.shift > 0 &&
-                 __ldg(bix.table + P + 1) - __ldg(bix.table + P) <= sparse_cell;
-        m = coarse ? cell_neighbourhood(P, order - bix.shift / 2, nb)
-                   : cell_neighbourhood(cell, order, nb);
+        bool coarse = false;
+        if ((FP32 || HLC_COARSE_FP64) && !LEARNED && bix.shift > 0) {
+          uint32_t P = cell >> bix.shift;
+          if (__ldg(bix.table + P + 1) - __ldg(bix.table + P) <= sparse_cell)
+            coarse = parent_cover4(cell, order, bix.shift / 2, nb);
+        }
+        if (coarse) {
+          coarse_lane = true;
+        } else {
+          cell_neighbourhood9(cell, order, nb);
+        }
       }
     }
     // all ranges first (independent loads in flight together), then one
@@ -367,7 +415,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       uint2 r = make_uint2(0u, 0u);
-      if (s < m) {
+      if (nb[s] != kNoCell) {
         if (LEARNED) {
           bool hit;
           uint32_t pos = learned_lower_bound(pa.lix, nb[s], &hit);
@@ -376,8 +424,8 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
           if (pos < pa.uB && __ldg(pa.uniqB + pos) == nb[s])
             r = make_uint2(__ldg(pa.startB + pos), __ldg(pa.startB + pos + 1));
         } else {
-          r = coarse ? make_uint2(__ldg(bix.table + nb[s]), __ldg(bix.table + nb[s] + 1))
-                     : cell_range(bix, nb[s]);
+          r = coarse_lane ? make_uint2(__ldg(bix.table + nb[s]), __ldg(bix.table + nb[s] + 1))
+                          : cell_range(bix, nb[s]);
         }
       }
       rb[s] = r.x;
@@ -385,55 +433,96 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
       total += r.y - r.x;
     }
     ntest += total;
+    {  // distinct A cells (statistics)
+      uint32_t prev = __shfl_up_sync(0xffffffffu, cell, 1);
+      if ((threadIdx.x & 31) == 0 && live && k > 0) prev = keyA[k - 1];
+      nhead += live && (k == 0 || prev != cell);
+    }
     const uint32_t maxT = __reduce_max_sync(0xffffffffu, total);
     uint32_t cur = rb[0], end = re[0];
-    for (uint32_t t = 0; t < maxT; ++t) {
-      bool act = t < total;
-      uint32_t j = 0;
-      bool hit = false, band = false;
-      if (act) {
-        while (cur >= end) {  // next non-empty range (constant-index shift)
+    // U candidates per lane per iteration: their loads are issued together
+    constexpr int U = QUAD ? 1 : HLC_PAIR_UNROLL;
+    for (uint32_t t = 0; t < maxT; t += U) {
+      uint32_t jj[U];
+      bool act[U];
 #pragma unroll
-          for (int i = 0; i + 1 < NS; ++i) {
-            rb[i] = rb[i + 1];
-            re[i] = re[i + 1];
+      for (int u = 0; u < U; ++u) {
+        act[u] = t + u < total;
+        jj[u] = 0;
+        if (act[u]) {
+          while (cur >= end) {  // next non-empty range (constant-index shift)
+#pragma unroll
+            for (int i = 0; i + 1 < NS; ++i) {
+              rb[i] = rb[i + 1];
+              re[i] = re[i + 1];
+            }
+            cur = rb[0];
+            end = re[0];
           }
-          cur = rb[0];
-          end = re[0];
+          jj[u] = cur++;
         }
-        j = cur++;
-        if (FP32) {
-          float4 b = __ldg(b32 + j);
-          float dx = a4.x - b.x, dy = a4.y - b.y, dz = a4.z - b.z;
+      }
+      bool hit[U], band[U];
+      bool anyv = false;
+      if (FP32) {
+        float4 bb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) bb[u] = act[u] ? __ldg(b32 + jj[u]) : a4;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          float dx = a4.x - bb[u].x, dy = a4.y - bb[u].y, dz = a4.z - bb[u].z;
           float s2 = dx * dx;
           s2 = fmaf(dy, dy, s2);
           s2 = fmaf(dz, dz, s2);
-          hit = s2 <= lo32;
-          band = !hit && s2 <= hi32;
-        } else {
-          double s2 = c_chord2(ax, ay, az, bxv[j], byv[j], bzv[j]);
-          hit = s2 <= C;
+          hit[u] = act[u] && s2 <= lo32;
+          band[u] = act[u] && !hit[u] && s2 <= hi32;
+          anyv |= hit[u] || band[u];
         }
-        if (QUAD && (hit || band)) {
-          uint32_t own = quad_owner(cellsA + 5ull * idxA[k], cellsB + 5ull * idxB[j]);
-          if (own != cell) {
-            if (hit) ++ndup;
-            hit = false;
-            band = false;
-          }
+      } else {
+        double bx[U], by[U], bz[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          bx[u] = act[u] ? bxv[jj[u]] : ax;
+          by[u] = act[u] ? byv[jj[u]] : ay;
+          bz[u] = act[u] ? bzv[jj[u]] : az;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          double s2 = c_chord2(ax, ay, az, bx[u], by[u], bz[u]);
+          hit[u] = act[u] && s2 <= C;
+          band[u] = false;
+          anyv |= hit[u];
         }
       }
-      if (__any_sync(0xffffffffu, hit || band)) {
-        warp_emit(hit, (uint32_t)k, j, sink.rows, sink.count, sink.cap, sink.err);
-        if (FP32)
-          warp_emit(band, (uint32_t)k, j, sink.band, sink.band_count, sink.band_cap, sink.err);
+      if (QUAD && anyv) {
+        uint32_t own = quad_owner(cellsA + 5ull * idxA[k], cellsB + 5ull * idxB[jj[0]]);
+        if (own != cell) {
+          if (hit[0]) ++ndup;
+          hit[0] = false;
+          band[0] = false;
+          anyv = false;
+        }
+      }
+      if (__any_sync(0xffffffffu, anyv)) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          wrows.add(hit[u], (uint32_t)k, jj[u]);
+          if (FP32) wband.add(band[u], (uint32_t)k, jj[u]);
+        }
+        if (wrows.fill > kRowCap - 32 * U)
+          wrows.flush(sink.rows, sink.count, sink.cap, sink.err);
+        if (FP32 && wband.fill > kBandCap - 32 * U)
+          wband.flush(sink.band, sink.band_count, sink.band_cap, sink.err);
       }
     }
   }
+  wrows.flush(sink.rows, sink.count, sink.cap, sink.err);
+  if (FP32) wband.flush(sink.band, sink.band_count, sink.band_cap, sink.err);
   // one atomic per warp for the counters
   for (int o = 16; o > 0; o >>= 1) {
     ntest += __shfl_down_sync(0xffffffffu, ntest, o);
     ndup += __shfl_down_sync(0xffffffffu, ndup, o);
+    nhead += __shfl_down_sync(0xffffffffu, nhead, o);
     if (LEARNED) {
       nlhit += __shfl_down_sync(0xffffffffu, nlhit, o);
       nllook += __shfl_down_sync(0xffffffffu, nllook, o);
@@ -442,6 +531,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
   if ((threadIdx.x & 31) == 0) {
     if (ntest) atomicAdd(sink.tests, ntest);
     if (ndup) atomicAdd(sink.dups, ndup);
+    if (nhead) atomicAdd(sink.heads, nhead);
     if (LEARNED && nllook) {
       atomicAdd(pa.lhits, nlhit);
       atomicAdd(pa.llook, nllook);
