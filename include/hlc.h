@@ -115,8 +115,13 @@ typedef struct {
 typedef struct {
   uint64_t n_a, n_b;               /* sources */
   uint64_t entries_a, entries_b;   /* index entries (> n in quad mode) */
-  uint64_t cells_a, cells_b;       /* non-empty cells at the join level */
-  uint64_t pair_tests;             /* algorithmic pair count */
+  uint64_t cells_a;                /* distinct A cells at the join level (0 in the
+                                      FP32 complete form, whose A entries are
+                                      grouped by offset-table cell only) */
+  uint64_t cells_b;                /* non-empty cells of B's offset table (distinct
+                                      B cells with the learned index) */
+  uint64_t pair_tests;             /* pair tests executed (sparse regions are
+                                      joined over whole table cells, a superset) */
   uint64_t band_candidates;        /* FP32 guard band: pairs rechecked */
   uint64_t matches;
   uint64_t quad_duplicates;        /* quad pairs left to a smaller shared

@@ -51,11 +51,12 @@ __global__ void k_coarse_hist(const uint32_t* __restrict__ keys, uint64_t n, int
   if ((threadIdx.x & 31) == 0 && h) atomicAdd(heads, h);
 }
 
-// Offset table of sorted keys without atomics or a scan: T[q] = first entry
-// whose key >> shift is >= q, for q in [0, S].  Each thread fills 8
-// consecutive slots: one binary search for the first, then a gallop forward
-// for each of the others.  It also counts the distinct keys among the
-// entries of its slots.
+// Offset table of keys sorted by (key >> shift), without atomics or a scan:
+// T[q] = first entry whose key >> shift is >= q, for q in [0, S].  Each
+// thread fills 8 consecutive slots: one binary search for the first, then a
+// gallop forward for each of the others.  It also counts the non-empty slots
+// (heads) and, when ndense is given, the entries of slots holding more than
+// dense_above entries.
 __device__ __forceinline__ uint64_t gallop_lb(const uint32_t* __restrict__ keys, uint64_t m,
                                               int shift, uint64_t from, uint64_t q) {
   uint64_t step = 1, base = from;
@@ -76,12 +77,12 @@ __device__ __forceinline__ uint64_t gallop_lb(const uint32_t* __restrict__ keys,
 
 __global__ void k_coarse_table(const uint32_t* __restrict__ keys, uint64_t m, int shift,
                                uint64_t S, uint32_t* __restrict__ T,
-                               unsigned long long* __restrict__ heads) {
-  unsigned long long h = 0;
+                               unsigned long long* __restrict__ heads, uint32_t dense_above,
+                               unsigned long long* __restrict__ ndense) {
+  unsigned long long h = 0, nd = 0;
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t * 8 <= S;
        t += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t q0 = t * 8;
-    const uint64_t qlast = q0 + 8 <= S ? q0 + 8 : S;  // slot q0 + 8 belongs to the next thread
     uint64_t lo = 0, hi = m;
     while (lo < hi) {
       uint64_t mid = (lo + hi) >> 1;
@@ -90,29 +91,36 @@ __global__ void k_coarse_table(const uint32_t* __restrict__ keys, uint64_t m, in
       else
         hi = mid;
     }
-    const uint64_t e0 = lo;
     T[q0] = (uint32_t)lo;
-    for (uint64_t q = q0 + 1; q <= qlast; ++q) {
-      lo = gallop_lb(keys, m, shift, lo, q);
-      if (q < q0 + 8) T[q] = (uint32_t)lo;
+    // slots q0 .. q0 + 7 (the last one's end is the next thread's first)
+    for (uint64_t q = q0 + 1; q <= q0 + 8; ++q) {
+      const uint64_t nxt = q <= S ? gallop_lb(keys, m, shift, lo, q) : m;
+      if (q < q0 + 8 && q <= S) T[q] = (uint32_t)nxt;
+      if (q - 1 < S) {  // slot q - 1 holds [lo, nxt)
+        const uint64_t c = nxt - lo;
+        h += c > 0;
+        nd += c > dense_above ? c : 0;
+      }
+      lo = nxt;
     }
-    // entries of slots [q0, qlast): [e0, lo); at the table's end lo = m
-    if (qlast == S) lo = m;
-    for (uint64_t e = e0; e < lo; ++e)
-      h += (e == 0 || __ldg(keys + e - 1) != __ldg(keys + e));
   }
-  for (int o = 16; o > 0; o >>= 1) h += __shfl_down_sync(0xffffffffu, h, o);
-  if ((threadIdx.x & 31) == 0 && h) atomicAdd(heads, h);
+  for (int o = 16; o > 0; o >>= 1) {
+    h += __shfl_down_sync(0xffffffffu, h, o);
+    nd += __shfl_down_sync(0xffffffffu, nd, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (h && heads) atomicAdd(heads, h);
+    if (nd && ndense) atomicAdd(ndense, nd);
+  }
 }
 
-// [begin, end) of the entries with key q.
-__device__ __forceinline__ uint2 cell_range(const CellIndex& ix, uint32_t q) {
-  uint32_t Q = q >> ix.shift;
-  uint32_t lo = __ldg(ix.table + Q), hi = __ldg(ix.table + Q + 1);
+// [begin, end) of the entries with key q inside the sorted window [lo, hi).
+__device__ __forceinline__ uint2 cell_range_in(const uint32_t* __restrict__ keys, uint32_t lo,
+                                               uint32_t hi, uint32_t q) {
   uint32_t a = lo, b = hi;
   while (a < b) {  // lower bound of q
     uint32_t mid = (a + b) >> 1;
-    if (__ldg(ix.keys + mid) < q)
+    if (__ldg(keys + mid) < q)
       a = mid + 1;
     else
       b = mid;
@@ -121,12 +129,18 @@ __device__ __forceinline__ uint2 cell_range(const CellIndex& ix, uint32_t q) {
   b = hi;
   while (a < b) {  // upper bound of q
     uint32_t mid = (a + b) >> 1;
-    if (__ldg(ix.keys + mid) <= q)
+    if (__ldg(keys + mid) <= q)
       a = mid + 1;
     else
       b = mid;
   }
   return make_uint2(first, a);
+}
+
+// [begin, end) of the entries with key q.
+__device__ __forceinline__ uint2 cell_range(const CellIndex& ix, uint32_t q) {
+  uint32_t Q = q >> ix.shift;
+  return cell_range_in(ix.keys, __ldg(ix.table + Q), __ldg(ix.table + Q + 1), q);
 }
 
 // Order of the coarse table for m entries at fine order L.

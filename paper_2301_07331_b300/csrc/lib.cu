@@ -15,6 +15,7 @@
 #include "match.cuh"
 #include "output.cuh"
 #include "batch.cuh"
+#include "bucket.cuh"
 #include "stream.cuh"
 #include "scan.cuh"
 #include "sort.cuh"
@@ -197,7 +198,7 @@ struct CatDev {
   uint64_t parts = 0;
 };
 
-enum Ctr { C_ROWS = 0, C_BAND, C_TESTS, C_DUPS, C_M, C_TOTAL, C_HEADS_A, C_HEADS_B,
+enum Ctr { C_ROWS = 0, C_BAND, C_TESTS, C_DUPS, C_M, C_TOTAL, C_HEADS_A, C_HEADS_B, C_DENSE,
            C_IDDIFF, C_MAXB, C_SLOW, C_LHITS, C_LLOOK, C_LMAXERR, C_SCRATCH, C_N };
 
 }  // namespace hlc
@@ -237,6 +238,7 @@ struct hlc_plan_s {
   std::vector<uint64_t> host_a, host_b;
   std::vector<double> host_s;
   uint32_t sparse_cell = hlc::kSparseCell;
+  bool table_buckets = false;  // FP32 complete mode: entries bucketed by table cell
   unsigned long long plan_launches = 0;
   cudaEvent_t ev[12] = {};
   bool events = false;
@@ -371,6 +373,105 @@ static int build_learned(Arena& ar, const uint32_t* uniq, uint64_t m, int shift,
   return HLC_OK;
 }
 
+// FP32 complete-mode build: entries sorted by table cell only (the radix sort
+// runs over the key bits above the fine bits of a table cell, one pass fewer
+// at the usual orders), the FP32 payload gathered in that order, and for B
+// the offset table; then fine order inside B's dense table cells, the only
+// ones the pair test searches (sparse table cells are read whole).
+static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
+                          const double* dec, const uint64_t* id, cudaEvent_t ev[4]) {
+  Arena& ar = *P->arena;
+  cudaStream_t st = plan_stream(P);
+  const int L = P->p.fine_level;
+  const uint64_t n = X.n;
+  X.m = n;
+  X.table_order = coarse_table_order(n, L);
+  X.table_shift = 2 * (L - X.table_order);
+  const uint64_t tsize = 12ull << (2 * X.table_order);
+  const int shift = X.table_shift;
+  const int bits = 2 * L + 4;
+  HLC_ALLOC(ar, X.key, uint32_t, n + 1);
+  HLC_ALLOC(ar, X.idx, uint32_t, n + 1);
+  if (n) {
+    uint32_t* slow = ar.get_n<uint32_t>(n + 1);
+    if (!slow) return HLC_ENOMEM;
+    HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st));
+    k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+        ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, slow, P->ctr + C_SLOW, nullptr, 0,
+        is_b ? nullptr : P->ctr + C_IDDIFF, P->dev_err);
+    HLC_LAUNCH_CHECK();
+    k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key,
+                                                  nullptr, 0);
+    HLC_LAUNCH_CHECK();
+    ar.drop(slow);
+  }
+  cudaEventRecord(ev[1], st);
+  if (n > 1) {
+    uint32_t* tk = ar.get_n<uint32_t>(n);
+    uint32_t* tv = ar.get_n<uint32_t>(n);
+    void* scr = ar.get(sort_scratch_bytes(n, (bits - shift + 7) / 8));
+    if (!tk || !tv || !scr) return HLC_ENOMEM;
+    bool in_tmp = false;
+    HLC_TRY(radix_sort_pairs<uint32_t>(X.key, X.idx, tk, tv, n, bits, scr, P->dev_err, st, shift,
+                                       &in_tmp));
+    ar.drop(scr);
+    if (in_tmp) {
+      std::swap(X.key, tk);
+      std::swap(X.idx, tv);
+    }
+    ar.drop(tk);
+    ar.drop(tv);
+  }
+  HLC_ALLOC(ar, X.v32, float4, n + 1);
+  if (n) {
+    k_payload32<<<grid_for(n, kThreads), kThreads, 0, st>>>(X.rec, X.idx, n, X.v32);
+    HLC_LAUNCH_CHECK();
+  }
+  cudaEventRecord(ev[2], st);
+  if (!is_b) return HLC_OK;  // A's entries only need the table-cell grouping
+  HLC_ALLOC(ar, X.table, uint32_t, tsize + 1);
+  k_coarse_table<<<grid_for(tsize / 8 + 1, kThreads), kThreads, 0, st>>>(
+      X.key, n, shift, tsize, X.table, P->ctr + C_HEADS_B, P->sparse_cell, P->ctr + C_DENSE);
+  HLC_LAUNCH_CHECK();
+  if (n > 1) {
+    unsigned long long nd = 0;
+    HLC_CUDA(cudaMemcpyAsync(&nd, P->ctr + C_DENSE, 8, cudaMemcpyDeviceToHost, st));
+    HLC_CUDA(cudaStreamSynchronize(st));
+    if (nd > 1) {
+      uint32_t* flag = ar.get_n<uint32_t>(n + 1);
+      uint32_t* off = ar.get_n<uint32_t>(n + 1);
+      void* scr = ar.get(scan_scratch_bytes(n));
+      uint32_t* dpos = ar.get_n<uint32_t>(nd);
+      uint32_t* dkey = ar.get_n<uint32_t>(nd);
+      uint32_t* dval = ar.get_n<uint32_t>(nd);
+      uint32_t* tk = ar.get_n<uint32_t>(nd);
+      uint32_t* tv = ar.get_n<uint32_t>(nd);
+      float4* tvec = ar.get_n<float4>(nd);
+      void* sscr = ar.get(sort_scratch_bytes(nd, (bits + 7) / 8));
+      if (!flag || !off || !scr || !dpos || !dkey || !dval || !tk || !tv || !tvec || !sscr)
+        return HLC_ENOMEM;
+      k_dense_flags<<<grid_for(n, kThreads), kThreads, 0, st>>>(X.key, n, shift, X.table,
+                                                                P->sparse_cell, flag);
+      HLC_LAUNCH_CHECK();
+      HLC_TRY(scan_exclusive<uint32_t>(flag, off, n, P->ctr + C_TOTAL, scr, P->dev_err, st));
+      k_dense_compact<<<grid_for(n, kThreads), kThreads, 0, st>>>(X.key, n, flag, off, dpos,
+                                                                  dkey, dval);
+      HLC_LAUNCH_CHECK();
+      HLC_TRY(radix_sort_pairs<uint32_t>(dkey, dval, tk, tv, nd, bits, sscr, P->dev_err, st));
+      k_dense_gather<<<grid_for(nd, kThreads), kThreads, 0, st>>>(dpos, dval, nd, X.idx, X.v32,
+                                                                  tv, tvec);
+      HLC_LAUNCH_CHECK();
+      k_dense_scatter<<<grid_for(nd, kThreads), kThreads, 0, st>>>(dpos, nd, dkey, tv, tvec,
+                                                                   X.key, X.idx, X.v32);
+      HLC_LAUNCH_CHECK();
+      for (void* q : {(void*)flag, (void*)off, scr, (void*)dpos, (void*)dkey, (void*)dval,
+                      (void*)tk, (void*)tv, (void*)tvec, sscr})
+        ar.drop(q);
+    }
+  }
+  return HLC_OK;
+}
+
 // Copy one catalogue in, build its sorted entries, payload and (for B) the
 // coarse offset table.  No host synchronisation in complete mode.
 static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool is_b,
@@ -404,6 +505,16 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
   }
   cudaEventRecord(ev[0], st);
   HLC_ALLOC(ar, X.rec, SrcRec, n + 1);
+  if (P->table_buckets) {
+    HLC_TRY(bucket_catalog(P, X, is_b, ra, dec, id, ev));
+    if (tra) {
+      ar.drop(tra);
+      ar.drop(tdec);
+      ar.drop(tid);
+    }
+    cudaEventRecord(ev[3], st);
+    return HLC_OK;
+  }
   if (!quad) {
     X.m = n;
     HLC_ALLOC(ar, X.key, uint32_t, n + 1);
@@ -414,15 +525,17 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
         if (!slow) return HLC_ENOMEM;
         HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st));
         k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, slow, P->ctr + C_SLOW,
-            P->dev_err);
+            ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, slow, P->ctr + C_SLOW, nullptr,
+            0, nullptr, P->dev_err);
         HLC_LAUNCH_CHECK();
-        k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key);
+        k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key,
+                                                      nullptr, 0);
         HLC_LAUNCH_CHECK();
         ar.drop(slow);
       } else {
         k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, nullptr, nullptr, P->dev_err);
+            ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, nullptr, nullptr, nullptr, 0,
+            nullptr, P->dev_err);
         HLC_LAUNCH_CHECK();
       }
     }
@@ -532,7 +645,7 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     uint64_t tsize = 12ull << (2 * X.table_order);
     HLC_ALLOC(ar, X.table, uint32_t, tsize + 1);
     k_coarse_table<<<grid_for(tsize / 8 + 1, kThreads), kThreads, 0, st>>>(
-        X.key, m, X.table_shift, tsize, X.table, heads);
+        X.key, m, X.table_shift, tsize, X.table, heads, 0xFFFFFFFFu, nullptr);
     HLC_LAUNCH_CHECK();
   }
   cudaEventRecord(ev[3], st);
@@ -555,6 +668,8 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   P->out = new Arena(P->al);
   P->join_level = p->fine_level;
   P->nslot = p->boundary == HLC_QUAD ? 1 : 9;
+  P->table_buckets = p->boundary == HLC_COMPLETE8 && p->precision == HLC_FP32_GUARD &&
+                     p->index != HLC_INDEX_LEARNED;
   P->C = chord2_threshold(p->radius_arcsec);
   double G = fp32_guard_band(P->C, kUnitVecErr);
   P->lo32 = (float)(P->C - G);
@@ -587,7 +702,7 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   }
   int rc = build_catalog(P, A, P->A, false, ea);
   if (rc == HLC_OK) rc = build_catalog(P, B, P->B, true, eb);
-  if (rc == HLC_OK && P->A.n) {
+  if (rc == HLC_OK && P->A.n && !P->table_buckets) {
     k_id_diff_rec<<<grid_for(P->A.n, kThreads, 148u * 8u), kThreads, 0, st>>>(P->A.rec, P->A.n,
                                                                               P->ctr + C_IDDIFF);
     if (cudaGetLastError() != cudaSuccess) rc = HLC_ECUDA;
@@ -748,7 +863,8 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
     if (!rows || !band) return HLC_ENOMEM;
     HLC_CUDA(cudaMemsetAsync(P->ctr, 0, C_N * 8, st));
     PairSink sink{rows, P->ctr + C_ROWS, cap, band, P->ctr + C_BAND, bcap,
-                  P->ctr + C_TESTS, P->ctr + C_DUPS, P->ctr + C_HEADS_A, P->dev_err};
+                  P->ctr + C_TESTS, P->ctr + C_DUPS,
+                  P->table_buckets ? nullptr : P->ctr + C_HEADS_A, P->dev_err};
     if (A.m && B.m) {
       unsigned grid = grid_for(A.m, kThreads, 148u * 16u);
       PairArgs pa;
@@ -775,8 +891,10 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
       pa.lhits = P->ctr + C_LHITS;
       pa.llook = P->ctr + C_LLOOK;
       const bool learned = P->p.index == HLC_INDEX_LEARNED;
-#define HLC_PAIR(F, Q, LR) k_pair<F, Q, LR><<<grid, kThreads, 0, st>>>(pa, sink)
-      if (fp32 && quad) {
+#define HLC_PAIR(F, Q, LR) k_pair<F, Q, LR, false><<<grid, kThreads, 0, st>>>(pa, sink)
+      if (P->table_buckets) {
+        k_pair<true, false, false, true><<<grid, kThreads, 0, st>>>(pa, sink);
+      } else if (fp32 && quad) {
         if (learned) HLC_PAIR(true, true, true); else HLC_PAIR(true, true, false);
       } else if (fp32) {
         if (learned) HLC_PAIR(true, false, true); else HLC_PAIR(true, false, false);
@@ -871,7 +989,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   res->job = nullptr;
   res->on_device = 1;
   P->stats.pair_tests = h[C_TESTS];
-  P->stats.cells_a = h[C_HEADS_A];  // counted by the pair test
+  if (!P->table_buckets) P->stats.cells_a = h[C_HEADS_A];  // counted by the pair test
   P->stats.band_candidates = fp32 ? h[C_BAND] : 0;
   P->stats.matches = M;
   P->stats.quad_duplicates = h[C_DUPS];
@@ -1922,11 +2040,13 @@ int hlc_ang2pix(const double* ra, const double* dec, uint64_t n, int order, int 
     }
     cudaMemsetAsync(nslow, 0, 8, st);
     k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-        ra, dec, nullptr, n, order, pix_const(order), pix, idx, nullptr, slow, nslow, err);
-    k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, order, slow, nslow, pix);
+        ra, dec, nullptr, n, order, pix_const(order), pix, idx, nullptr, slow, nslow, nullptr, 0,
+        nullptr, err);
+    k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, order, slow, nslow, pix, nullptr, 0);
   } else {
     k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-        ra, dec, nullptr, n, order, pix_const(order), pix, idx, nullptr, nullptr, nullptr, err);
+        ra, dec, nullptr, n, order, pix_const(order), pix, idx, nullptr, nullptr, nullptr, nullptr,
+        0, nullptr, err);
   }
   int rc = HLC_OK;
   if (cudaGetLastError() != cudaSuccess) {

@@ -49,7 +49,11 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
                             const uint64_t* __restrict__ id, uint64_t n, int order, PixConst K,
                             uint32_t* __restrict__ key, uint32_t* __restrict__ idx,
                             SrcRec* __restrict__ rec, uint32_t* __restrict__ slow,
-                            unsigned long long* __restrict__ nslow, int* __restrict__ err) {
+                            unsigned long long* __restrict__ nslow, uint32_t* __restrict__ hist,
+                            int hshift, unsigned long long* __restrict__ iddiff,
+                            int* __restrict__ err) {
+  const uint64_t id0 = (iddiff && n) ? __ldg(id) : 0;
+  unsigned long long idacc = 0;
   for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n;
        i0 += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t i = i0 + threadIdx.x;
@@ -58,6 +62,7 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
     if (live) {
       double a = ra[i], d = dec[i];
       uint32_t k = 0;
+      bool ok = false;
       if (FAST) {
         if (!(bits_finite(a) && bits_abs_le(d, 90.0))) {
           atomicOr(err, DERR_INPUT);
@@ -65,6 +70,7 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
           if (!bits_in_ra_range(a)) a = c_norm_ra(a);
           FastDec fd = f_dec_part(split_f64(d));
           defer = !f_pix(split_f64(a), fd, order, K, &k);
+          ok = !defer;
         }
       } else {
         if (!c_valid(a, d)) {
@@ -72,15 +78,19 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
         } else {
           a = c_norm_ra(a);
           k = c_ang2pix(a, d, order);
+          ok = true;
         }
       }
       key[i] = k;
-      idx[i] = (uint32_t)i;
+      if (idx) idx[i] = (uint32_t)i;
+      if (hist && ok) atomicAdd(hist + (k >> hshift), 1u);
+      const uint64_t sid = id ? id[i] : 0;
+      idacc |= sid ^ id0;
       if (rec) {
         SrcRec r;
         r.ra = a;
         r.dec = d;
-        r.id = id[i];
+        r.id = sid;
         r.pad = 0;
         rec[i] = r;
       }
@@ -96,18 +106,25 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
       }
     }
   }
+  if (iddiff) {
+    for (int o = 16; o > 0; o >>= 1) idacc |= __shfl_down_sync(0xffffffffu, idacc, o);
+    if ((threadIdx.x & 31) == 0 && idacc) atomicOr(iddiff, idacc);
+  }
 }
 
 // Binary64 ang2pix of the queued sources.
 __global__ void k_prep_fallback(const double* __restrict__ ra, const double* __restrict__ dec,
                                 int order, const uint32_t* __restrict__ slow,
                                 const unsigned long long* __restrict__ nslow,
-                                uint32_t* __restrict__ key) {
+                                uint32_t* __restrict__ key, uint32_t* __restrict__ hist,
+                                int hshift) {
   uint64_t ns = *nslow;
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns;
        q += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t i = slow[q];
-    key[i] = c_ang2pix(c_norm_ra(ra[i]), dec[i], order);
+    uint32_t k = c_ang2pix(c_norm_ra(ra[i]), dec[i], order);
+    key[i] = k;
+    if (hist) atomicAdd(hist + (k >> hshift), 1u);
   }
 }
 
@@ -338,7 +355,9 @@ struct PairArgs {
   unsigned long long *lhits, *llook;
 };
 
-template <bool FP32, bool QUAD, bool LEARNED>
+// BUCKET: B is bucketed by table cell (ordered by fine key only inside dense
+// table cells); a sparse table cell is read whole, once per A entry.
+template <bool FP32, bool QUAD, bool LEARNED, bool BUCKET>
 __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink sink) {
   const uint64_t mA = pa.mA;
   const uint32_t* __restrict__ keyA = pa.keyA;
@@ -423,9 +442,23 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
           ++nllook;
           if (pos < pa.uB && __ldg(pa.uniqB + pos) == nb[s])
             r = make_uint2(__ldg(pa.startB + pos), __ldg(pa.startB + pos + 1));
+        } else if (coarse_lane) {
+          r = make_uint2(__ldg(bix.table + nb[s]), __ldg(bix.table + nb[s] + 1));
+        } else if (BUCKET) {
+          // sparse table cell: read whole (once); dense: ordered, search it
+          const uint32_t Q = nb[s] >> bix.shift;
+          const uint32_t c0 = __ldg(bix.table + Q), c1 = __ldg(bix.table + Q + 1);
+          if (c1 - c0 <= sparse_cell) {
+            bool seen = false;
+#pragma unroll
+            for (int e = 0; e < s; ++e)
+              seen |= nb[e] != kNoCell && (nb[e] >> bix.shift) == Q;
+            if (!seen) r = make_uint2(c0, c1);
+          } else {
+            r = cell_range_in(bix.keys, c0, c1, nb[s]);
+          }
         } else {
-          r = coarse_lane ? make_uint2(__ldg(bix.table + nb[s]), __ldg(bix.table + nb[s] + 1))
-                          : cell_range(bix, nb[s]);
+          r = cell_range(bix, nb[s]);
         }
       }
       rb[s] = r.x;
@@ -531,7 +564,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
   if ((threadIdx.x & 31) == 0) {
     if (ntest) atomicAdd(sink.tests, ntest);
     if (ndup) atomicAdd(sink.dups, ndup);
-    if (nhead) atomicAdd(sink.heads, nhead);
+    if (nhead && sink.heads) atomicAdd(sink.heads, nhead);
     if (LEARNED && nllook) {
       atomicAdd(pa.lhits, nlhit);
       atomicAdd(pa.llook, nllook);

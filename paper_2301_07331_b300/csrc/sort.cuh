@@ -25,14 +25,16 @@ constexpr long long kSpinLimit = 1ll << 26;
 // Histogram of every digit pass at once.
 template <typename K>
 __global__ void __launch_bounds__(kBlock) k_digit_hist(const K* __restrict__ keys, uint64_t n,
-                                                       int npass, uint32_t* __restrict__ hist) {
+                                                       int npass, int bit_lo,
+                                                       uint32_t* __restrict__ hist) {
   __shared__ uint32_t sh[8][kRadix];
   for (int i = threadIdx.x; i < 8 * kRadix; i += kBlock) sh[i / kRadix][i % kRadix] = 0;
   __syncthreads();
   for (uint64_t e = (uint64_t)blockIdx.x * kBlock + threadIdx.x; e < n;
        e += (uint64_t)gridDim.x * kBlock) {
     K k = keys[e];
-    for (int p = 0; p < npass; ++p) atomicAdd(&sh[p][(uint32_t)(k >> (8 * p)) & 255u], 1u);
+    for (int p = 0; p < npass; ++p)
+      atomicAdd(&sh[p][(uint32_t)(k >> (bit_lo + 8 * p)) & 255u], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < npass * kRadix; i += kBlock) {
@@ -221,11 +223,17 @@ inline size_t sort_scratch_bytes(uint64_t n, int npass) {
   return kSortLookbackOffset + (size_t)npass * tiles * rs::kRadix * 8;
 }
 
+// Sorts by the key bits [bit_lo, key_bits).  With in_tmp set, an odd number
+// of passes leaves the result in (tmp_keys, tmp_vals) and *in_tmp says so;
+// otherwise it is copied back.
 template <typename K>
 int radix_sort_pairs(K* keys, uint32_t* vals, K* tmp_keys, uint32_t* tmp_vals, uint64_t n,
-                     int key_bits, void* scratch, int* dev_err, cudaStream_t st) {
+                     int key_bits, void* scratch, int* dev_err, cudaStream_t st,
+                     int bit_lo = 0, bool* in_tmp = nullptr) {
+  if (in_tmp) *in_tmp = false;
   if (n <= 1) return HLC_OK;
-  int npass = (key_bits + 7) / 8;
+  if (bit_lo < 0 || bit_lo >= key_bits) bit_lo = 0;
+  int npass = (key_bits - bit_lo + 7) / 8;
   if (npass < 1) npass = 1;
   if (npass > (int)sizeof(K)) npass = (int)sizeof(K);
   uint64_t tiles = (n + rs::kTile - 1) / rs::kTile;
@@ -243,7 +251,7 @@ int radix_sort_pairs(K* keys, uint32_t* vals, K* tmp_keys, uint32_t* tmp_vals, u
   HLC_CUDA(cudaMemsetAsync(ctr, 0, 64, st));
   HLC_CUDA(cudaMemsetAsync(lb, 0, lb_bytes, st));
   rs::k_digit_hist<K><<<grid_for(n, rs::kBlock, 148 * 8), rs::kBlock, 0, st>>>(keys, n, npass,
-                                                                               hist);
+                                                                               bit_lo, hist);
   HLC_LAUNCH_CHECK();
   rs::k_hist_scan<<<npass, rs::kBlock, 0, st>>>(hist, offs);
   HLC_LAUNCH_CHECK();
@@ -256,13 +264,16 @@ int radix_sort_pairs(K* keys, uint32_t* vals, K* tmp_keys, uint32_t* tmp_vals, u
   uint32_t* vb = tmp_vals;
   for (int p = 0; p < npass; ++p) {
     rs::k_onesweep<K><<<(unsigned)tiles, rs::kBlock, smem, st>>>(
-        ka, va, kb, vb, n, 8 * p, offs + p * rs::kRadix, lb + (size_t)p * tiles * rs::kRadix,
+        ka, va, kb, vb, n, bit_lo + 8 * p, offs + p * rs::kRadix,
+        lb + (size_t)p * tiles * rs::kRadix,
         ctr + p, dev_err);
     HLC_LAUNCH_CHECK();
     K* tk = ka; ka = kb; kb = tk;
     uint32_t* tv = va; va = vb; vb = tv;
   }
-  if (ka != keys) {
+  if (ka != keys && in_tmp) {
+    *in_tmp = true;
+  } else if (ka != keys) {
     HLC_CUDA(cudaMemcpyAsync(keys, ka, n * sizeof(K), cudaMemcpyDeviceToDevice, st));
     HLC_CUDA(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
   }
