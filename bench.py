@@ -118,13 +118,12 @@ def run_hlc(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
-    na = nb = args.n
-    A, B = synth.fullsky_pair(seed=2301073311 + rank, na=na, nb=nb, device=dev)
+    A, B, r, L, Lc, wname = make_workload(args, rank, dev)
+    na, nb = A.ra.numel(), B.ra.numel()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     prec = hlc.HLC_FP32_GUARD if args.precision == "fp32" else hlc.HLC_FP64
     mode = hlc.HLC_QUAD if args.mode == "quad" else hlc.HLC_COMPLETE8
-    r, L, Lc = 1.5, 12, 4
 
     def step(precision, A_, B_):
         plan = hlc.hlc_plan(A_, B_, r, L, coarse_level=Lc, boundary=mode, precision=precision,
@@ -231,7 +230,7 @@ def run_hlc(args):
 
     # CPU oracle on a bounded sample of the same workload (rank 0 only)
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and not args.no_cpu and args.workload == "fullsky":
         cpu = cpu_baseline(A, B, r, L)
 
     if rank == 0:
@@ -241,13 +240,11 @@ def run_hlc(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == hlc.HLC_FP32_GUARD else "f64",
             "data": "synthetic (seeded, generated on device)",
-            "config": {"workload": "fullsky 10M x 10M, r=1.5 arcsec, fine order 12, coarse 4, "
-                                   + args.mode + " mode" if na == 10_000_000 else
-                                   "fullsky %d x %d (reduced)" % (na, nb),
+            "config": {"workload": wname + ", " + args.mode + " mode",
                        "n_a": na, "n_b": nb, "radius_arcsec": r, "fine_level": L,
                        "coarse_level": Lc, "boundary": args.mode,
                        "form": args.precision + " (chosen)",
-                       "l2": "inputs (480 MB) larger than L2 (126 MB)",
+                       "l2": "inputs (%d MB) larger than L2 (126 MB)" % ((na + nb) * 24 // 10**6),
                        "parallelism": "independent instance per GPU" if world > 1 else "1 GPU"},
             "pair_tests_per_s": (alg / (stage_ms["ms_pair"] / 1e3)) if alg else None,
             "pair_tests_alg": alg, "pair_tests_executed": tests, "matches": nmatch,
@@ -301,6 +298,37 @@ def alg_pair_tests(hlc, A, B, L):
     return int((ca * nsum).sum())
 
 
+def make_workload(args, rank, dev):
+    """The synthetic catalogues of a workload, generated on the device."""
+    from paper_2301_07331_b300 import synth
+    w = args.workload
+    if w == "fullsky":
+        n = args.n or 10_000_000
+        A, B = synth.fullsky_pair(seed=2301073311 + rank, na=n, nb=n, device=dev)
+        name = "fullsky %s x %s (40%% uniform + 60%% galactic disk), r=1.5 arcsec, fine order 12" % (
+            _mega(n), _mega(n))
+        return A, B, 1.5, 12, 4, name
+    if w == "clusters":
+        n = args.n or 50_000_000
+        ncl = max(1, n // 2_000_000)
+        A, B = synth.clustered_pair(seed=2301073312 + rank, na=n, nb=n * 3 // 4,
+                                    n_clusters=ncl, device=dev)
+        name = ("clusters %s x %s (galactic mixture + %d Plummer clusters, a=2 arcmin, "
+                "50k members), r=1 arcsec, fine order 13" % (_mega(n), _mega(n * 3 // 4), ncl))
+        return A, B, 1.0, 13, 3, name
+    if w == "bulge":
+        n = args.n or 100_000_000
+        A, B = synth.bulge_pair(seed=2301073314 + rank, na=n, nb=n, device=dev)
+        name = ("bulge %s x %s (0.825%% uniform + 67.8%% disk + 31.4%% Gaussian bulge "
+                "sigma 5 deg), r=1 arcsec, fine order 14" % (_mega(n), _mega(n)))
+        return A, B, 1.0, 14, 4, name
+    raise SystemExit("unknown workload " + w)
+
+
+def _mega(n):
+    return "%gM" % (n / 1e6) if n >= 1_000_000 else str(n)
+
+
 def cpu_baseline(A, B, r, L):
     """The oracle, as it stands, on the sources of both catalogues with RA in
     [0, 180) deg (half of the same synthetic sky), single-threaded."""
@@ -328,15 +356,16 @@ def run_reference(args):
     world, rank, local = _dist()
     if rank != 0:
         return
-    from paper_2301_07331_b300 import synth
     import numpy as np
 
     import oracle as O
-    A, B = synth.fullsky_pair(na=args.n, nb=args.n,
-                              device="cuda" if torch.cuda.is_available() else "cpu")
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    A, B, r, L, Lc, wname = make_workload(args, 0, dev)
+    n_a, n_b = A.ra.numel(), B.ra.numel()
     ra_a, dec_a, id_a = (x.cpu().numpy() for x in (A.ra, A.dec, A.id))
     ra_b, dec_b, id_b = (x.cpu().numpy() for x in (B.ra, B.dec, B.id))
-    width = 18.0  # deg of RA per step: ~1M sources of each catalogue
+    width = 6.0  # deg of RA per step: about 1/60 of each catalogue
+    mode = O.QUAD if args.mode == "quad" else O.COMPLETE
     times, counts = [], []
     for it in range(args.warmup + args.steps):
         lo = (it * width) % 360.0
@@ -344,7 +373,7 @@ def run_reference(args):
         sb = (ra_b >= lo) & (ra_b < lo + width)
         t0 = time.perf_counter()
         O.match(ra_a[sa], dec_a[sa], id_a[sa].view(np.uint64), ra_b[sb], dec_b[sb],
-                id_b[sb].view(np.uint64), 1.5, 12, O.COMPLETE)
+                id_b[sb].view(np.uint64), r, L, mode)
         t = time.perf_counter() - t0
         if it >= args.warmup:
             times.append(t)
@@ -354,10 +383,12 @@ def run_reference(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "fullsky 10M x 10M, r=1.5 arcsec, fine order 12, coarse 4, "
-                                   "complete mode", "n_a": args.n, "n_b": args.n},
+            "config": {"workload": wname + ", " + args.mode + " mode", "n_a": n_a, "n_b": n_b,
+                       "radius_arcsec": r, "fine_level": L, "coarse_level": Lc,
+                       "boundary": args.mode},
             "cpu_baseline": {"value": v, "unit": "sources/s", "cores": 1, "kind": "oracle",
-                             "sample": "one 18-deg RA strip of both catalogues per step"},
+                             "sample": "one 6-deg RA strip of both catalogues per step "
+                                       "(about 1/60 of the workload)"},
             "e2e": {"value": v, "unit": "sources/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -369,7 +400,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hlc", choices=["hlc", "reference"])
-    ap.add_argument("--n", type=int, default=10_000_000)
+    ap.add_argument("--workload", default="fullsky", choices=["fullsky", "clusters", "bulge"])
+    ap.add_argument("--n", type=int, default=0, help="A sources (0: the workload's size)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--mode", default="complete", choices=["complete", "quad"])
     ap.add_argument("--no-e2e", action="store_true")
