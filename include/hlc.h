@@ -135,6 +135,10 @@ typedef struct {
       ms_output, ms_h2d, ms_d2h, ms_total;
   uint64_t kernel_launches;        /* library kernels launched by the plan and
                                       the match */
+  uint64_t dense_entries_b;        /* FP32 complete form: B entries in dense
+                                      offset-table cells (kept in fine order) */
+  uint64_t tile_items;             /* dense A cells given to the tile kernel */
+  uint64_t tile_entries_a;         /* A entries in those cells */
 } hlc_stats;
 
 typedef struct hlc_plan_s hlc_plan_t;

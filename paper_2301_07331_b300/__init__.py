@@ -71,7 +71,8 @@ class Stats(C.Structure):
                 (f, C.c_float) for f in ("ms_prep", "ms_sort", "ms_index", "ms_candidates",
                                           "ms_pair", "ms_recheck", "ms_output", "ms_h2d",
                                           "ms_d2h", "ms_total")] + [
-                ("kernel_launches", C.c_uint64)]
+                ("kernel_launches", C.c_uint64), ("dense_entries_b", C.c_uint64),
+                ("tile_items", C.c_uint64), ("tile_entries_a", C.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

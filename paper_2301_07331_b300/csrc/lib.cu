@@ -16,6 +16,7 @@
 #include "output.cuh"
 #include "batch.cuh"
 #include "bucket.cuh"
+#include "tile.cuh"
 #include "stream.cuh"
 #include "scan.cuh"
 #include "sort.cuh"
@@ -196,10 +197,18 @@ struct CatDev {
   uint64_t u = 0;
   LearnedIndex learned;
   uint64_t parts = 0;
+  // FP32 complete form: entries in dense table cells of B (fine-ordered)
+  uint64_t ndense = 0;
+  // catalogue A: dense fine cells for the tile kernel
+  uint32_t* tile_cell = nullptr;
+  uint32_t* tile_start = nullptr;
+  uint32_t* tile_dpos = nullptr;
+  unsigned long long* tile_n = nullptr;  // device: number of items
+  uint8_t* tiled = nullptr;              // 1 for A entries the tile kernel takes
 };
 
 enum Ctr { C_ROWS = 0, C_BAND, C_TESTS, C_DUPS, C_M, C_TOTAL, C_HEADS_A, C_HEADS_B, C_DENSE,
-           C_IDDIFF, C_MAXB, C_SLOW, C_LHITS, C_LLOOK, C_LMAXERR, C_SCRATCH, C_N };
+           C_WORK, C_IDDIFF, C_MAXB, C_SLOW, C_LHITS, C_LLOOK, C_LMAXERR, C_SCRATCH, C_N };
 
 }  // namespace hlc
 
@@ -373,11 +382,89 @@ static int build_learned(Arena& ar, const uint32_t* uniq, uint64_t m, int shift,
   return HLC_OK;
 }
 
+// Fine order inside dense table cells: the entries flagged in `flag` (those
+// whose table cell of T holds more than sparse_cell B entries) are compacted
+// in order, radix sorted by key and written back.  With items set, the sorted
+// dense keys are also run-length encoded into the tile kernel's work items.
+static int dense_fixup(hlc_plan_t* P, CatDev& X, const uint32_t* T, int shift, bool items) {
+  Arena& ar = *P->arena;
+  cudaStream_t st = plan_stream(P);
+  const uint64_t n = X.n;
+  const int bits = 2 * P->p.fine_level + 4;
+  uint32_t* flag = ar.get_n<uint32_t>(n + 1);
+  uint32_t* off = ar.get_n<uint32_t>(n + 1);
+  void* scr = ar.get(scan_scratch_bytes(n));
+  if (!flag || !off || !scr) return HLC_ENOMEM;
+  k_dense_flags<<<grid_for(n, kThreads), kThreads, 0, st>>>(X.key, n, shift, T, P->sparse_cell,
+                                                            flag);
+  HLC_LAUNCH_CHECK();
+  HLC_TRY(scan_exclusive<uint32_t>(flag, off, n, P->ctr + C_TOTAL, scr, P->dev_err, st));
+  unsigned long long nd = 0;
+  HLC_CUDA(cudaMemcpyAsync(&nd, P->ctr + C_TOTAL, 8, cudaMemcpyDeviceToHost, st));
+  HLC_CUDA(cudaStreamSynchronize(st));
+  X.ndense = nd;
+  if (nd == 0) {
+    ar.drop(flag);
+    ar.drop(off);
+    ar.drop(scr);
+    return HLC_OK;
+  }
+  uint32_t* dpos = ar.get_n<uint32_t>(nd);
+  uint32_t* dkey = ar.get_n<uint32_t>(nd);
+  uint32_t* dval = ar.get_n<uint32_t>(nd);
+  uint32_t* tk = ar.get_n<uint32_t>(nd);
+  uint32_t* tv = ar.get_n<uint32_t>(nd);
+  float4* tvec = ar.get_n<float4>(nd);
+  void* sscr = ar.get(sort_scratch_bytes(nd, (bits + 7) / 8));
+  if (!dpos || !dkey || !dval || !tk || !tv || !tvec || !sscr) return HLC_ENOMEM;
+  k_dense_compact<<<grid_for(n, kThreads), kThreads, 0, st>>>(X.key, n, flag, off, dpos, dkey,
+                                                              dval);
+  HLC_LAUNCH_CHECK();
+  if (nd > 1)
+    HLC_TRY(radix_sort_pairs<uint32_t>(dkey, dval, tk, tv, nd, bits, sscr, P->dev_err, st));
+  k_dense_gather<<<grid_for(nd, kThreads), kThreads, 0, st>>>(dpos, dval, nd, X.idx, X.v32, tv,
+                                                              tvec);
+  HLC_LAUNCH_CHECK();
+  k_dense_scatter<<<grid_for(nd, kThreads), kThreads, 0, st>>>(dpos, nd, dkey, tv, tvec, X.key,
+                                                               X.idx, X.v32);
+  HLC_LAUNCH_CHECK();
+  for (void* q : {(void*)flag, (void*)off, scr, (void*)dval, (void*)tk, (void*)tv, (void*)tvec,
+                  sscr})
+    ar.drop(q);
+  if (!items) {
+    ar.drop(dpos);
+    ar.drop(dkey);
+    return HLC_OK;
+  }
+  // items: runs of equal key among the sorted dense entries
+  uint32_t* cell_of = ar.get_n<uint32_t>(nd + 1);
+  void* rscr = ar.get(scan_scratch_bytes(nd));
+  HLC_ALLOC(ar, X.tile_cell, uint32_t, nd + 1);
+  HLC_ALLOC(ar, X.tile_start, uint32_t, nd + 2);
+  HLC_ALLOC(ar, X.tile_n, unsigned long long, 4);
+  HLC_ALLOC(ar, X.tiled, uint8_t, n + 1);
+  if (!cell_of || !rscr) return HLC_ENOMEM;
+  HLC_CUDA(cudaMemsetAsync(X.tile_n, 0, 32, st));
+  HLC_TRY(cell_table(dkey, nd, 0, cell_of, X.tile_cell, X.tile_start, X.tile_n, rscr, P->dev_err,
+                     st));
+  HLC_CUDA(cudaMemsetAsync(X.tiled, 0, n + 1, st));
+  k_mark_tiled<<<grid_for(nd, kThreads, 148u * 8u), kThreads, 0, st>>>(X.tile_start, dpos,
+                                                                       X.tile_n, X.tiled);
+  HLC_LAUNCH_CHECK();
+  X.tile_dpos = dpos;
+  ar.drop(cell_of);
+  ar.drop(rscr);
+  ar.drop(dkey);
+  return HLC_OK;
+}
+
 // FP32 complete-mode build: entries sorted by table cell only (the radix sort
 // runs over the key bits above the fine bits of a table cell, one pass fewer
-// at the usual orders), the FP32 payload gathered in that order, and for B
-// the offset table; then fine order inside B's dense table cells, the only
-// ones the pair test searches (sparse table cells are read whole).
+// at the usual orders) and the FP32 payload gathered in that order.  B gets
+// its offset table and fine order inside its dense table cells (the only ones
+// the pair test searches; sparse table cells are read whole).  A, built after
+// B, is grouped by B's table cells and gets fine order (and tile-kernel work
+// items) where B's table cells are dense.
 static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
                           const double* dec, const uint64_t* id, cudaEvent_t ev[4]) {
   Arena& ar = *P->arena;
@@ -385,7 +472,7 @@ static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
   const int L = P->p.fine_level;
   const uint64_t n = X.n;
   X.m = n;
-  X.table_order = coarse_table_order(n, L);
+  X.table_order = is_b ? coarse_table_order(n, L) : P->B.table_order;
   X.table_shift = 2 * (L - X.table_order);
   const uint64_t tsize = 12ull << (2 * X.table_order);
   const int shift = X.table_shift;
@@ -428,7 +515,10 @@ static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
     HLC_LAUNCH_CHECK();
   }
   cudaEventRecord(ev[2], st);
-  if (!is_b) return HLC_OK;  // A's entries only need the table-cell grouping
+  if (!is_b) {
+    if (n > 1 && P->B.ndense > 0) HLC_TRY(dense_fixup(P, X, P->B.table, shift, true));
+    return HLC_OK;
+  }
   HLC_ALLOC(ar, X.table, uint32_t, tsize + 1);
   k_coarse_table<<<grid_for(tsize / 8 + 1, kThreads), kThreads, 0, st>>>(
       X.key, n, shift, tsize, X.table, P->ctr + C_HEADS_B, P->sparse_cell, P->ctr + C_DENSE);
@@ -437,37 +527,8 @@ static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
     unsigned long long nd = 0;
     HLC_CUDA(cudaMemcpyAsync(&nd, P->ctr + C_DENSE, 8, cudaMemcpyDeviceToHost, st));
     HLC_CUDA(cudaStreamSynchronize(st));
-    if (nd > 1) {
-      uint32_t* flag = ar.get_n<uint32_t>(n + 1);
-      uint32_t* off = ar.get_n<uint32_t>(n + 1);
-      void* scr = ar.get(scan_scratch_bytes(n));
-      uint32_t* dpos = ar.get_n<uint32_t>(nd);
-      uint32_t* dkey = ar.get_n<uint32_t>(nd);
-      uint32_t* dval = ar.get_n<uint32_t>(nd);
-      uint32_t* tk = ar.get_n<uint32_t>(nd);
-      uint32_t* tv = ar.get_n<uint32_t>(nd);
-      float4* tvec = ar.get_n<float4>(nd);
-      void* sscr = ar.get(sort_scratch_bytes(nd, (bits + 7) / 8));
-      if (!flag || !off || !scr || !dpos || !dkey || !dval || !tk || !tv || !tvec || !sscr)
-        return HLC_ENOMEM;
-      k_dense_flags<<<grid_for(n, kThreads), kThreads, 0, st>>>(X.key, n, shift, X.table,
-                                                                P->sparse_cell, flag);
-      HLC_LAUNCH_CHECK();
-      HLC_TRY(scan_exclusive<uint32_t>(flag, off, n, P->ctr + C_TOTAL, scr, P->dev_err, st));
-      k_dense_compact<<<grid_for(n, kThreads), kThreads, 0, st>>>(X.key, n, flag, off, dpos,
-                                                                  dkey, dval);
-      HLC_LAUNCH_CHECK();
-      HLC_TRY(radix_sort_pairs<uint32_t>(dkey, dval, tk, tv, nd, bits, sscr, P->dev_err, st));
-      k_dense_gather<<<grid_for(nd, kThreads), kThreads, 0, st>>>(dpos, dval, nd, X.idx, X.v32,
-                                                                  tv, tvec);
-      HLC_LAUNCH_CHECK();
-      k_dense_scatter<<<grid_for(nd, kThreads), kThreads, 0, st>>>(dpos, nd, dkey, tv, tvec,
-                                                                   X.key, X.idx, X.v32);
-      HLC_LAUNCH_CHECK();
-      for (void* q : {(void*)flag, (void*)off, scr, (void*)dpos, (void*)dkey, (void*)dval,
-                      (void*)tk, (void*)tv, (void*)tvec, sscr})
-        ar.drop(q);
-    }
+    X.ndense = nd;
+    if (nd > 0) HLC_TRY(dense_fixup(P, X, X.table, shift, false));
   }
   return HLC_OK;
 }
@@ -700,8 +761,12 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
     cudaEventCreate(&ea[i]);
     cudaEventCreate(&eb[i]);
   }
-  int rc = build_catalog(P, A, P->A, false, ea);
-  if (rc == HLC_OK) rc = build_catalog(P, B, P->B, true, eb);
+  // (the FP32 complete form orders A by B's table cells: B first)
+  int rc = P->table_buckets ? build_catalog(P, B, P->B, true, eb)
+                            : build_catalog(P, A, P->A, false, ea);
+  if (rc == HLC_OK)
+    rc = P->table_buckets ? build_catalog(P, A, P->A, false, ea)
+                          : build_catalog(P, B, P->B, true, eb);
   if (rc == HLC_OK && P->A.n && !P->table_buckets) {
     k_id_diff_rec<<<grid_for(P->A.n, kThreads, 148u * 8u), kThreads, 0, st>>>(P->A.rec, P->A.n,
                                                                               P->ctr + C_IDDIFF);
@@ -736,6 +801,15 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   P->stats.entries_b = P->B.m;
   P->stats.cells_b = P->p.index == HLC_INDEX_LEARNED ? P->B.u : hc[C_HEADS_B];
   P->stats.learned_models = P->p.index == HLC_INDEX_LEARNED ? P->B.parts : 0;
+  P->stats.dense_entries_b = P->B.ndense;
+  if (P->A.tile_n) {
+    unsigned long long tn[4] = {0, 0, 0, 0};
+    if (cudaMemcpyAsync(tn, P->A.tile_n, 32, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return fail(HLC_ECUDA);
+    P->stats.tile_items = tn[1];
+    P->stats.tile_entries_a = tn[2];
+  }
   P->stats.learned_max_err = (uint32_t)hc[C_LMAXERR];
   P->stats.join_level = P->join_level;
   P->stats.ms_prep = t[0] + t[1];
@@ -890,6 +964,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
       pa.sparse_cell = P->sparse_cell;
       pa.lhits = P->ctr + C_LHITS;
       pa.llook = P->ctr + C_LLOOK;
+      pa.tiled = A.tiled;
       const bool learned = P->p.index == HLC_INDEX_LEARNED;
 #define HLC_PAIR(F, Q, LR) k_pair<F, Q, LR, false><<<grid, kThreads, 0, st>>>(pa, sink)
       if (P->table_buckets) {
@@ -905,6 +980,26 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
       }
 #undef HLC_PAIR
       HLC_LAUNCH_CHECK();
+      if (P->table_buckets && A.tiled) {
+        TileArgs ta;
+        ta.cell = A.tile_cell;
+        ta.start = A.tile_start;
+        ta.dpos = A.tile_dpos;
+        ta.nitems = A.tile_n;
+        ta.work = (unsigned*)(P->ctr + C_WORK);
+        ta.a32 = A.v32;
+        ta.b32 = B.v32;
+        ta.bix = bix;
+        ta.order = P->join_level;
+        ta.lo32 = P->lo32;
+        ta.hi32 = P->hi32;
+        ta.sparse_cell = P->sparse_cell;
+        const int smem = kTileCap * 16;
+        HLC_CUDA(cudaFuncSetAttribute(k_pair_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      smem));
+        k_pair_tile<<<148 * 5, kTileThreads, smem, st>>>(ta, sink);
+        HLC_LAUNCH_CHECK();
+      }
     }
     HLC_CUDA(cudaMemcpyAsync(h, P->ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
     HLC_CUDA(cudaStreamSynchronize(st));
@@ -1841,6 +1936,9 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
       agg.ms_recheck += gs.ms_recheck;
       agg.ms_output += gs.ms_output;
       agg.kernel_launches += gs.kernel_launches;
+      agg.dense_entries_b += gs.dense_entries_b;
+      agg.tile_items += gs.tile_items;
+      agg.tile_entries_a += gs.tile_entries_a;
       hlc_free(G);
     }
     for (int side = 0; side < 2; ++side) {

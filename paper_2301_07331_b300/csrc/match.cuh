@@ -353,6 +353,7 @@ struct PairArgs {
   const uint32_t *idxA, *idxB, *cellsA, *cellsB;
   uint32_t sparse_cell;
   unsigned long long *lhits, *llook;
+  const uint8_t* tiled;   // (BUCKET) A entries taken by the tile kernel, or null
 };
 
 // BUCKET: B is bucketed by table cell (ordered by fine key only inside dense
@@ -390,6 +391,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
   for (uint64_t kb0 = (uint64_t)blockIdx.x * kThreads; kb0 < mA; kb0 += stride) {
     uint64_t k = kb0 + (threadIdx.x);
     bool live = k < mA;
+    if (BUCKET && pa.tiled && live && pa.tiled[k]) live = false;  // the tile kernel's
     uint32_t cell = live ? keyA[k] : 0u;
     double ax = 0, ay = 0, az = 0;
     float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);

@@ -279,10 +279,10 @@ def clustered_pair(seed=2301073312, na=400_000_000, nb=300_000_000,
         ras.append(r_)
         decs.append(d_)
     A = Catalogue(torch.cat(ras), torch.cat(decs), ids(seed, 1, na, device))
-    # jitter a spread of A (every k-th source) so clusters get counterparts
+    # jitter an even spread of A (indices floor(i * na / nj), covering the
+    # clusters at the end of A too) so that clusters get counterparts
     nj = int(round(nb * 0.6))
-    step = max(1, na // nj)
-    src = torch.arange(0, nj, device=device) * step
+    src = (torch.arange(0, nj, device=device, dtype=torch.int64) * na) // nj
     ra_j, dec_j = jitter(seed, 500, A.ra[src], A.dec[src], 0.5)
     ra_x, dec_x = _mixture_galactic(seed, 7, nb - nj, 0.4, device)
     B = Catalogue(torch.cat([ra_j, ra_x]), torch.cat([dec_j, dec_x]), ids(seed, 2, nb, device))
