@@ -351,6 +351,211 @@ def cpu_baseline(A, B, r, L):
                       % (n, res["id_a"].size), "seconds": t}
 
 
+def _timed_loop(fn, K, W, stream):
+    import torch
+    for _ in range(W):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = None
+    for _ in range(K):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / K, out
+
+
+def _line(args, metric, value, unit, ms, config, **extra):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded, generated on device)",
+         "config": config}
+    d.update(extra)
+    print(json.dumps(d))
+
+
+def run_learned(args):
+    """Learned offset index against the plain per-partition binary search on
+    the bulge workload's B cells (order 14, partitions at order 4): lookups of
+    every A cell, build time, hit rate and stored error bound; then the match
+    through each index."""
+    import torch
+
+    import paper_2301_07331_b300 as hlc
+    from paper_2301_07331_b300 import synth
+    dev = torch.device("cuda", 0)
+    n = args.n or 500_000_000
+    L, Lc, r = 14, 4, 1.0
+    A, B = synth.bulge_pair(na=n, nb=n, device=dev)
+    stream = torch.cuda.current_stream()
+    kb = hlc.hlc_ang2pix(B.ra, B.dec, L)
+    vb = torch.arange(kb.numel(), dtype=torch.int32, device=dev)
+    hlc.hlc_sort_pairs(kb, vb, 32)
+    uniq, _start = hlc.hlc_cell_table(kb)
+    del vb, _start
+    qa = hlc.hlc_ang2pix(A.ra, A.dec, L)
+    va = torch.arange(qa.numel(), dtype=torch.int32, device=dev)
+    hlc.hlc_sort_pairs(qa, va, 32)
+    del va
+    shift = 2 * (L - Lc)
+    res = {}
+    ref = None
+    for name, model in (("binary search", hlc.HLC_MODEL_NONE), ("pla", hlc.HLC_MODEL_PLA),
+                        ("mlp", hlc.HLC_MODEL_MLP)):
+        outs = []
+        for it in range(args.warmup + args.steps):
+            out, st = hlc.hlc_learned_lookup(uniq, shift, model, qa, stream=stream)
+            if it >= args.warmup:
+                outs.append(st)
+        if ref is None:
+            ref = out
+        exact = bool(torch.equal(out, ref))
+        ms_look = sum(s["ms_candidates"] for s in outs) / len(outs)
+        ms_build = sum(s["ms_index"] for s in outs) / len(outs)
+        res[name] = {"lookups_per_s": qa.numel() / (ms_look / 1e3), "ms_lookup": ms_look,
+                     "ms_build": ms_build, "hit_rate": outs[-1]["learned_hit_rate"],
+                     "max_err": outs[-1]["learned_max_err"], "models": outs[-1]["learned_models"],
+                     "equal_to_binary_search": exact}
+        del out
+    base = res["binary search"]["ms_lookup"]
+    for k in ("pla", "mlp"):
+        res[k]["speedup_vs_binary_search"] = base / res[k]["ms_lookup"]
+    # the whole match through each index on a slice of the same catalogues
+    nm = min(n, args.n_match)
+    Am = synth.Catalogue(A.ra[:nm], A.dec[:nm], A.id[:nm])
+    Bm = synth.Catalogue(B.ra[:nm], B.dec[:nm], B.id[:nm])
+    del qa, kb
+    match = {}
+    for name, index, model in (("binary search", hlc.HLC_INDEX_BSEARCH, hlc.HLC_MODEL_PLA),
+                               ("pla", hlc.HLC_INDEX_LEARNED, hlc.HLC_MODEL_PLA),
+                               ("mlp", hlc.HLC_INDEX_LEARNED, hlc.HLC_MODEL_MLP)):
+        def step():
+            plan = hlc.hlc_plan(Am, Bm, r, L, coarse_level=Lc, index=index, model=model,
+                                stream=stream)
+            out = hlc.hlc_match(plan, copy=False)
+            n_ = out["n"]
+            st_ = out["stats"]
+            hlc.hlc_free(plan)
+            return n_, st_
+        ms, (nmatch, st) = _timed_loop(step, max(1, args.steps), 1, stream)
+        match[name] = {"sources_per_s": 2 * nm / (ms / 1e3), "ms_per_step": ms,
+                       "matches": nmatch, "ms_pair": st["ms_pair"],
+                       "hit_rate": st["learned_hit_rate"]}
+    best = max(("pla", "mlp"), key=lambda k: res[k]["lookups_per_s"])
+    _line(args, "learned-index lookups/s (exact lower bounds of A cells in B's cells)",
+          res[best]["lookups_per_s"], "lookups/s", res[best]["ms_lookup"],
+          {"workload": "bulge %s x %s, fine order 14, partitions at order 4 (%d models), "
+                       "%d unique B cells, %d queries" % (_mega(n), _mega(n),
+                                                         res["pla"]["models"], uniq.numel(),
+                                                         n),
+           "best_model": best}, lookups=res, match_slice={"n_a": nm, "n_b": nm, **match})
+
+
+def _auto_order(nb, cone_deg, r_arcsec):
+    """The batched plan's density rule (about two B sources per cell,
+    capped by r <= theta_L / 8), for the one-plan-per-job comparison."""
+    area = 2 * math.pi * max(1 - math.cos(math.radians(cone_deg)), 1e-12)
+    cells = 4 * math.pi * max(nb, 1) / area / (12 * 2.0)
+    L = int(math.floor(math.log(cells) / math.log(4) + 0.5)) if cells > 1 else 0
+    lmax = 0
+    while lmax < 14 and r_arcsec <= math.sqrt(math.pi / 3) / 2 ** (lmax + 1) * 648000 / math.pi / 8:
+        lmax += 1
+    return max(0, min(L, lmax))
+
+
+def run_batched(args):
+    """4096 cone-pair jobs in one batched plan (one persistent graph-captured
+    pair launch, orders chosen per job by density) against one plan per job."""
+    import torch
+
+    import paper_2301_07331_b300 as hlc
+    from paper_2301_07331_b300 import synth
+    dev = torch.device("cuda", 0)
+    njobs = args.jobs
+    jobs = synth.cone_jobs(n_jobs=njobs, scale=args.scale, device=dev)
+    stream = torch.cuda.current_stream()
+    spec = [{"A": j.A, "B": j.B, "radius_arcsec": j.r_arcsec} for j in jobs]
+    total = sum(j.A.ra.numel() + j.B.ra.numel() for j in jobs)
+
+    def batched():
+        plan = hlc.hlc_plan_batched(spec, stream=stream)
+        out = hlc.hlc_match(plan, copy=False)
+        n_, st_ = out["n"], out["stats"]
+        hlc.hlc_free(plan)
+        return n_, st_
+    ms_b, (nb_, st_b) = _timed_loop(batched, args.steps, args.warmup, stream)
+    orders = [_auto_order(j.B.ra.numel(), j.cone_deg, j.r_arcsec) for j in jobs]
+
+    def per_job():
+        n_ = 0
+        for j, L in zip(jobs, orders):
+            plan = hlc.hlc_plan(j.A, j.B, j.r_arcsec, L, coarse_level=min(4, L), stream=stream)
+            n_ += hlc.hlc_match(plan, copy=False)["n"]
+            hlc.hlc_free(plan)
+        return n_
+    ms_j, nj_ = _timed_loop(per_job, 1, 1, stream)
+    _line(args, "sources matched/s, batched cone jobs", total / (ms_b / 1e3), "sources/s", ms_b,
+          {"workload": "%d cone-pair jobs (cone 0.1-2 deg, N log-uniform %g-%g per side, "
+                       "r 0.5-5 arcsec), %d sources" % (njobs, 1e3 * args.scale, 1e6 * args.scale,
+                                                       total)},
+          matches=nb_, per_job={"ms": ms_j, "sources_per_s": total / (ms_j / 1e3), "matches": nj_},
+          speedup_vs_per_job=ms_j / ms_b, pair_tests=st_b["pair_tests"],
+          gpu_launches=st_b["kernel_launches"])
+
+
+def run_streamed(args):
+    """Host-resident catalogues larger than the device budget, streamed by
+    coarse partition through pinned buffers, against the same catalogues
+    matched in core from device memory."""
+    import torch
+
+    import paper_2301_07331_b300 as hlc
+    from paper_2301_07331_b300 import synth
+    dev = torch.device("cuda", 0)
+    n = args.n or 400_000_000
+    nb = n * 3 // 4
+    ncl = max(1, n // 2_000_000)
+    A, B = synth.clustered_pair(na=n, nb=nb, n_clusters=ncl, device=dev)
+    stream = torch.cuda.current_stream()
+    r, L, Lc = 1.0, 13, 3
+    Ah = synth.Catalogue(A.ra.cpu().pin_memory(), A.dec.cpu().pin_memory(), A.id.cpu().pin_memory())
+    Bh = synth.Catalogue(B.ra.cpu().pin_memory(), B.dec.cpu().pin_memory(), B.id.cpu().pin_memory())
+    budget = args.budget_gb << 30
+
+    def streamed():
+        plan = hlc.hlc_plan(Ah, Bh, r, L, coarse_level=Lc, device_mem_budget=budget,
+                            stream=stream)
+        out = hlc.hlc_match(plan, copy=False)
+        n_, st_ = out["n"], out["stats"]
+        hlc.hlc_free(plan)
+        return n_, st_
+    t0 = time.perf_counter()
+    ms_s, (ns_, st_s) = _timed_loop(streamed, args.steps, args.warmup, stream)
+
+    def in_core():
+        plan = hlc.hlc_plan(A, B, r, L, coarse_level=Lc, stream=stream)
+        out = hlc.hlc_match(plan, copy=False)
+        n_ = out["n"]
+        hlc.hlc_free(plan)
+        return n_
+    ms_c, nc_ = _timed_loop(in_core, args.steps, args.warmup, stream)
+    _line(args, "sources matched/s, streamed from pinned host memory", (n + nb) / (ms_s / 1e3),
+          "sources/s", ms_s,
+          {"workload": "clusters %s x %s (%d Plummer clusters), r=1 arcsec, fine order 13, "
+                       "coarse order 3, device budget %d GiB" % (_mega(n), _mega(nb), ncl,
+                                                               args.budget_gb)},
+          matches=ns_, partitions=st_s["partitions"], ms_h2d=st_s["ms_h2d"],
+          phases_ms={k: st_s[k] for k in ("ms_stream_count", "ms_stream_bucket",
+                                          "ms_stream_groups", "ms_stream_merge", "ms_d2h",
+                                          "ms_prep", "ms_sort", "ms_index", "ms_pair",
+                                          "ms_recheck", "ms_output")},
+          h2d_gbs=(n + nb) * 24 / (st_s["ms_h2d"] / 1e3) / 1e9 if st_s["ms_h2d"] else None,
+          in_core={"ms": ms_c, "sources_per_s": (n + nb) / (ms_c / 1e3), "matches": nc_},
+          equal_counts=ns_ == nc_)
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle on a bounded sample per step."""
     import torch
@@ -402,7 +607,13 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hlc", choices=["hlc", "reference"])
-    ap.add_argument("--workload", default="fullsky", choices=["fullsky", "clusters", "bulge"])
+    ap.add_argument("--workload", default="fullsky",
+                    choices=["fullsky", "clusters", "bulge", "learned", "batched", "streamed"])
+    ap.add_argument("--n-match", type=int, default=100_000_000,
+                    help="learned: sources per side of the match slice")
+    ap.add_argument("--jobs", type=int, default=4096, help="batched: number of jobs")
+    ap.add_argument("--scale", type=float, default=1.0, help="batched: source-count scale")
+    ap.add_argument("--budget-gb", type=int, default=16, help="streamed: device budget")
     ap.add_argument("--n", type=int, default=0, help="A sources (0: the workload's size)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--mode", default="complete", choices=["complete", "quad"])
@@ -411,6 +622,12 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "learned":
+        run_learned(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "streamed":
+        run_streamed(args)
     else:
         run_hlc(args)
 

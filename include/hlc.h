@@ -65,6 +65,8 @@ extern "C" {
 
 #define HLC_MODEL_PLA 0 /* 256-segment monotone piecewise-linear model */
 #define HLC_MODEL_MLP 1 /* 1-input 2x32 ReLU MLP, bracket-checked */
+#define HLC_MODEL_NONE 2 /* hlc_learned_lookup only: no model, binary search
+                            inside the partition (the baseline it replaces) */
 
 /* ---- catalogue and parameters ------------------------------------------- */
 typedef struct {
@@ -139,6 +141,10 @@ typedef struct {
                                       offset-table cells (kept in fine order) */
   uint64_t tile_items;             /* dense A cells given to the tile kernel */
   uint64_t tile_entries_a;         /* A entries in those cells */
+  float ms_stream_count;           /* streamed plans (host wall time): counting pass, */
+  float ms_stream_bucket;          /*   bucketing pass into pinned host runs, */
+  float ms_stream_groups;          /*   the groups' copies in, matches and rows out, */
+  float ms_stream_merge;           /*   merge of the groups' sorted rows */
 } hlc_stats;
 
 typedef struct hlc_plan_s hlc_plan_t;
@@ -250,8 +256,11 @@ int hlc_cell_table(const uint32_t* keys, uint64_t n, uint32_t* uniq,
  * top bits (key >> shift): per partition a model (HLC_MODEL_PLA or
  * HLC_MODEL_MLP) with a stored max error; lookup(q) returns the lower bound
  * of q in uniq exactly (bounded search in the predicted window, binary search
- * as fallback).  out: nq device uint32 lower-bound positions; stats may be
- * NULL.  Synchronises the stream. */
+ * as fallback).  HLC_MODEL_NONE builds the partition offsets only and binary
+ * searches the query's partition (the plain offset table, for comparison).
+ * out: nq device uint32 lower-bound positions; stats may be NULL
+ * (learned_hit_rate, learned_max_err, ms_index = build, ms_candidates =
+ * lookups).  Synchronises the stream. */
 int hlc_learned_lookup(const uint32_t* uniq, uint64_t m, int shift, int model,
                        const uint32_t* queries, uint64_t nq, uint32_t* out,
                        hlc_stats* stats, void* stream);

@@ -26,7 +26,7 @@ HLC_OK, HLC_EINVAL, HLC_ENOMEM, HLC_ECUDA, HLC_ETIMEOUT, HLC_EUNSUPPORTED = rang
 HLC_COMPLETE8, HLC_QUAD = 0, 1
 HLC_FP64, HLC_FP32_GUARD = 0, 1
 HLC_INDEX_BSEARCH, HLC_INDEX_LEARNED = 0, 1
-HLC_MODEL_PLA, HLC_MODEL_MLP = 0, 1
+HLC_MODEL_PLA, HLC_MODEL_MLP, HLC_MODEL_NONE = 0, 1, 2
 
 _ERRNAMES = {1: "HLC_EINVAL", 2: "HLC_ENOMEM", 3: "HLC_ECUDA", 4: "HLC_ETIMEOUT",
              5: "HLC_EUNSUPPORTED"}
@@ -72,7 +72,9 @@ class Stats(C.Structure):
                                           "ms_pair", "ms_recheck", "ms_output", "ms_h2d",
                                           "ms_d2h", "ms_total")] + [
                 ("kernel_launches", C.c_uint64), ("dense_entries_b", C.c_uint64),
-                ("tile_items", C.c_uint64), ("tile_entries_a", C.c_uint64)]
+                ("tile_items", C.c_uint64), ("tile_entries_a", C.c_uint64)] + [
+                (f, C.c_float) for f in ("ms_stream_count", "ms_stream_bucket",
+                                          "ms_stream_groups", "ms_stream_merge")]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -309,7 +311,9 @@ def hlc_match(plan: Plan, copy: bool = True) -> dict:
         def host(ptr, ct, dt):
             if n == 0 or not ptr:
                 return torch.empty(0, dtype=dt)
-            a = np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ct)), shape=(n,)).copy()
+            a = np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ct)), shape=(n,))
+            if copy:  # else a view of the plan's pinned rows (valid until hlc_free)
+                a = a.copy()
             return torch.from_numpy(a.view(np.int64) if dt == torch.int64 else a)
         return dict(n=n, id_a=host(r.id_a, C.c_uint64, torch.int64),
                     id_b=host(r.id_b, C.c_uint64, torch.int64),

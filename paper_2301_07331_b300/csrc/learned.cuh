@@ -298,17 +298,22 @@ __global__ void k_learned_lookup(LearnedIndex L, const uint32_t* __restrict__ qu
   if ((threadIdx.x & 31) == 0 && h) atomicAdd(hits, h);
 }
 
-// Plain binary search over all of uniq (the reference the model replaces).
-__global__ void k_bsearch_lookup(const uint32_t* __restrict__ uniq, uint64_t m,
-                                 const uint32_t* __restrict__ queries, uint64_t nq,
-                                 uint32_t* __restrict__ out) {
+// The plain offset table the model replaces: binary search inside the
+// query's partition.
+__global__ void k_part_bsearch_lookup(LearnedIndex L, const uint32_t* __restrict__ queries,
+                                      uint64_t nq, uint32_t* __restrict__ out) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t q = queries[i];
-    uint32_t s = 0, t = (uint32_t)m;
+    const uint32_t q = queries[i];
+    const uint32_t p = q >> L.shift;
+    if (p >= L.nparts) {
+      out[i] = __ldg(L.part + L.nparts);
+      continue;
+    }
+    uint32_t s = __ldg(L.part + p), t = __ldg(L.part + p + 1);
     while (s < t) {
-      uint32_t mid = (s + t) >> 1;
-      if (__ldg(uniq + mid) < q)
+      const uint32_t mid = (s + t) >> 1;
+      if (__ldg(L.uniq + mid) < q)
         s = mid + 1;
       else
         t = mid;

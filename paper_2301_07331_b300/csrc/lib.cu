@@ -5,6 +5,11 @@
 #include <cmath>
 #include <mutex>
 #include <queue>
+#include <thread>
+#include <unistd.h>
+#include <atomic>
+#include <memory>
+#include <chrono>
 #include <vector>
 
 #include "canon.cuh"
@@ -207,6 +212,81 @@ struct CatDev {
   uint8_t* tiled = nullptr;              // 1 for A entries the tile kernel takes
 };
 
+// Pinned host memory of streamed plans (the pass-1 runs, the groups' result
+// rows, the merged output), pooled between plans: pinning tens of GB takes
+// seconds, so released blocks are kept (up to half of the host's physical
+// memory) and handed to later requests of the same or a slightly smaller
+// size.
+static std::mutex g_pin_mu;
+static std::vector<std::pair<char*, size_t>> g_pin_pool;
+static size_t g_pin_total = 0;
+
+static size_t pinned_pool_limit() {
+  const long pages = sysconf(_SC_PHYS_PAGES), psz = sysconf(_SC_PAGE_SIZE);
+  return pages > 0 && psz > 0 ? (size_t)pages * (size_t)psz / 2 : (size_t)16 << 30;
+}
+
+static char* pinned_acquire(size_t* bytes) {
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    size_t best = SIZE_MAX;
+    for (size_t i = 0; i < g_pin_pool.size(); ++i) {
+      const size_t sz = g_pin_pool[i].second;
+      if (sz >= *bytes && sz <= 2 * *bytes + (64u << 20) &&
+          (best == SIZE_MAX || sz < g_pin_pool[best].second))
+        best = i;
+    }
+    if (best != SIZE_MAX) {
+      char* p = g_pin_pool[best].first;
+      *bytes = g_pin_pool[best].second;
+      g_pin_total -= *bytes;
+      g_pin_pool.erase(g_pin_pool.begin() + best);
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaHostAlloc(&p, *bytes, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (char*)p;
+}
+
+static void pinned_release(char* p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_pool.push_back({p, bytes});
+  g_pin_total += bytes;
+  const size_t limit = pinned_pool_limit();
+  while (g_pin_total > limit && !g_pin_pool.empty()) {  // drop the oldest blocks
+    cudaFreeHost(g_pin_pool.front().first);
+    g_pin_total -= g_pin_pool.front().second;
+    g_pin_pool.erase(g_pin_pool.begin());
+  }
+}
+
+// A pooled pinned block owned by one user.
+struct PinnedBuf {
+  char* p = nullptr;
+  size_t bytes = 0;
+  PinnedBuf() = default;
+  PinnedBuf(const PinnedBuf&) = delete;
+  PinnedBuf& operator=(const PinnedBuf&) = delete;
+  PinnedBuf(PinnedBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  ~PinnedBuf() { reset(); }
+  bool get(size_t b) {
+    reset();
+    bytes = b;
+    p = pinned_acquire(&bytes);
+    return p != nullptr;
+  }
+  void reset() {
+    pinned_release(p, bytes);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
 enum Ctr { C_ROWS = 0, C_BAND, C_TESTS, C_DUPS, C_M, C_TOTAL, C_HEADS_A, C_HEADS_B, C_DENSE,
            C_WORK, C_IDDIFF, C_MAXB, C_SLOW, C_LHITS, C_LLOOK, C_LMAXERR, C_SCRATCH, C_N };
 
@@ -244,8 +324,10 @@ struct hlc_plan_s {
   void* graph_band = nullptr;
   // streamed plans: merged rows on the host
   bool streamed = false;
-  std::vector<uint64_t> host_a, host_b;
-  std::vector<double> host_s;
+  hlc::PinnedBuf host_buf;  // streamed plans: the merged rows (pinned, pooled)
+  uint64_t host_n = 0;
+  uint64_t *host_a = nullptr, *host_b = nullptr;
+  double* host_s = nullptr;
   uint32_t sparse_cell = hlc::kSparseCell;
   bool table_buckets = false;  // FP32 complete mode: entries bucketed by table cell
   unsigned long long plan_launches = 0;
@@ -355,6 +437,10 @@ static int build_learned(Arena& ar, const uint32_t* uniq, uint64_t m, int shift,
   L.shift = shift;
   L.model = model;
   L.nparts = P;
+  if (model == HLC_MODEL_NONE) {  // partition offsets only
+    *out = L;
+    return HLC_OK;
+  }
   if (model == HLC_MODEL_PLA) {
     float* knots = ar.get_n<float>(P * (kPlaSeg + 1) + 1);
     if (!knots) return HLC_ENOMEM;
@@ -1656,9 +1742,12 @@ static int match_batched(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
 constexpr uint64_t kStreamBytesPerEntry = 192;
 constexpr uint64_t kStreamChunk = 8ull << 20;  // sources per streamed chunk
 
-struct HostRows {
-  std::vector<uint64_t> a, b;
-  std::vector<double> s;
+struct HostRows {  // one group's sorted rows, in a pooled pinned block
+  PinnedBuf buf;
+  const uint64_t* a = nullptr;
+  const uint64_t* b = nullptr;
+  const double* s = nullptr;  // null without separations
+  size_t n = 0;
 };
 
 // Streams one host catalogue through the device in chunks on two streams,
@@ -1680,6 +1769,7 @@ static int stream_catalog(const hlc_catalog* X, double* dra[2], double* ddec[2],
     cudaGetLastError();
   }
   uint64_t nchunks = (X->n + kStreamChunk - 1) / kStreamChunk;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tev;  // H2D spans, read at the end
   for (uint64_t c = 0; c < nchunks; ++c) {
     int b = (int)(c & 1);
     uint64_t o = c * kStreamChunk;
@@ -1701,22 +1791,24 @@ static int stream_catalog(const hlc_catalog* X, double* dra[2], double* ddec[2],
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
+    tev.push_back({t0, t1});
     cudaEventRecord(t0, ss[b]);
     HLC_CUDA(cudaMemcpyAsync(dra[b], sra, n * 8, cudaMemcpyHostToDevice, ss[b]));
     HLC_CUDA(cudaMemcpyAsync(ddec[b], sdec, n * 8, cudaMemcpyHostToDevice, ss[b]));
     HLC_CUDA(cudaMemcpyAsync(did[b], sid, n * 8, cudaMemcpyHostToDevice, ss[b]));
     cudaEventRecord(t1, ss[b]);
-    HLC_TRY(fn(dra[b], ddec[b], did[b], n, ss[b]));
+    HLC_TRY(fn(dra[b], ddec[b], did[b], n, ss[b], c, b));
     HLC_CUDA(cudaEventRecord(done[b], ss[b]));
-    cudaEventSynchronize(t1);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, t0, t1);
-    *ms_h2d += ms;
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
   }
   HLC_CUDA(cudaStreamSynchronize(ss[0]));
   HLC_CUDA(cudaStreamSynchronize(ss[1]));
+  for (auto& e : tev) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e.first, e.second);
+    *ms_h2d += ms;
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
   return HLC_OK;
 }
 
@@ -1727,6 +1819,107 @@ static bool row_lt(uint64_t a1, uint64_t b1, double s1, uint64_t a2, uint64_t b2
   memcpy(&x, &s1, 8);
   memcpy(&y, &s2, 8);
   return x < y;
+}
+
+// Merge of sorted runs into one sorted output, in parallel: splitter rows
+// taken from the largest run cut every run at the same keys (lower bounds),
+// so the slices are independent; each thread merges its slice of every run
+// by repeatedly taking the smallest of the runs' current heads.
+static void merge_runs(const std::vector<HostRows>& runs, bool want_sep, uint64_t* oa,
+                       uint64_t* ob, double* os) {
+  const size_t R = runs.size();
+  auto lt_at = [&](size_t r, size_t i, size_t q, size_t j) {
+    const HostRows& u = runs[r];
+    const HostRows& v = runs[q];
+    return row_lt(u.a[i], u.b[i], u.s ? u.s[i] : 0.0, v.a[j], v.b[j], v.s ? v.s[j] : 0.0);
+  };
+  size_t big = 0, total = 0;
+  for (size_t r = 0; r < R; ++r) {
+    total += runs[r].n;
+    if (runs[r].n > runs[big].n) big = r;
+  }
+  if (total == 0) return;
+  unsigned T = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+  if (total < (1u << 20)) T = 1;
+  T *= 4;  // smaller slices balance better
+  // cut[t][r]: start of slice t in run r (T + 1 cuts)
+  std::vector<std::vector<size_t>> cut(T + 1, std::vector<size_t>(R, 0));
+  for (size_t r = 0; r < R; ++r) cut[T][r] = runs[r].n;
+  for (unsigned t = 1; t < T; ++t) {
+    const size_t sp = runs[big].n * t / T;  // splitter: row sp of the largest run
+    for (size_t r = 0; r < R; ++r) {
+      size_t lo = 0, hi = runs[r].n;
+      while (lo < hi) {
+        const size_t mid = (lo + hi) / 2;
+        if (lt_at(r, mid, big, sp))
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      cut[t][r] = lo;
+    }
+  }
+  std::vector<size_t> base(T + 1, 0);
+  for (unsigned t = 0; t < T; ++t) {
+    size_t n = 0;
+    for (size_t r = 0; r < R; ++r) n += cut[t + 1][r] - cut[t][r];
+    base[t + 1] = base[t] + n;
+  }
+  std::atomic<unsigned> next{0};
+  auto work = [&]() {
+    std::vector<size_t> pos(R), end(R);
+    std::vector<uint64_t> ha(R);
+    for (unsigned t; (t = next.fetch_add(1)) < T;) {
+      size_t live = 0;
+      for (size_t r = 0; r < R; ++r) {
+        pos[r] = cut[t][r];
+        end[r] = cut[t + 1][r];
+        ha[r] = pos[r] < end[r] ? runs[r].a[pos[r]] : UINT64_MAX;
+        live += pos[r] < end[r];
+      }
+      size_t o = base[t];
+      while (live) {
+        // smallest head by id_a (branch-free scan); equal id_a heads, rare
+        // across runs, are ordered by the whole key
+        uint64_t best = ha[0];
+        size_t m = 0;
+        bool tie = false;
+        for (size_t r = 1; r < R; ++r) {
+          const uint64_t v = ha[r];
+          tie |= v == best;
+          const bool lt = v < best;
+          best = lt ? v : best;
+          m = lt ? r : m;
+          tie = lt ? false : tie;
+        }
+        if (tie || pos[m] >= end[m]) {
+          m = R;
+          for (size_t r = 0; r < R; ++r) {
+            if (pos[r] >= end[r]) continue;
+            if (m == R || ha[r] < ha[m] || (ha[r] == ha[m] && lt_at(r, pos[r], m, pos[m])))
+              m = r;
+          }
+        }
+        const HostRows& h = runs[m];
+        const size_t i = pos[m]++;
+        oa[o] = h.a[i];
+        ob[o] = h.b[i];
+        if (want_sep) os[o] = h.s[i];
+        ++o;
+        if (pos[m] < end[m]) {
+          ha[m] = h.a[pos[m]];
+        } else {
+          ha[m] = UINT64_MAX;
+          --live;
+        }
+      }
+    }
+  };
+  const unsigned nth = std::min<unsigned>(T, std::max(1u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> th;
+  for (unsigned k = 1; k < nth; ++k) th.emplace_back(work);
+  work();
+  for (auto& x : th) x.join();
 }
 
 static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_params* p,
@@ -1772,16 +1965,29 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
   }
   unsigned long long* counts = ar.get_n<unsigned long long>(2 * nparts);
   int* err = ar.get_n<int>(16);
-  unsigned long long* cur = ar.get_n<unsigned long long>(4);
-  if (!counts || !err || !cur) return fail(HLC_ENOMEM);
+  if (!counts || !err) return fail(HLC_ENOMEM);
   cudaStream_t ss[2];
   cudaEvent_t done[2];
   void* stage[2] = {nullptr, nullptr};
+  // pageable inputs go through two pinned staging buffers
+  auto is_pinned = [](const hlc_catalog* X) {
+    if (!X->n) return true;
+    for (const void* q : {(const void*)X->ra_deg, (const void*)X->dec_deg, (const void*)X->id}) {
+      cudaPointerAttributes at;
+      if (cudaPointerGetAttributes(&at, q) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+        cudaGetLastError();
+        return false;
+      }
+    }
+    return true;
+  };
+  const bool need_stage = !is_pinned(A) || !is_pinned(B);
   for (int b = 0; b < 2; ++b) {
     cudaStreamCreateWithFlags(&ss[b], cudaStreamNonBlocking);
     cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming);
     cudaEventRecord(done[b], ss[b]);
-    if (cudaHostAlloc(&stage[b], kStreamChunk * 24, cudaHostAllocDefault) != cudaSuccess) {
+    if (need_stage &&
+        cudaHostAlloc(&stage[b], kStreamChunk * 24, cudaHostAllocDefault) != cudaSuccess) {
       cudaGetLastError();
       set_error("pinned staging allocation failed");
       return fail(HLC_ENOMEM);
@@ -1800,12 +2006,19 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
   HLC_CUDA(cudaStreamSynchronize(st));
   float ms_h2d = 0;
   int rc = HLC_OK;
-  // pass 1: the entries each coarse cell needs
+  auto wall = []() { return std::chrono::steady_clock::now(); };
+  auto ms_since = [](std::chrono::steady_clock::time_point t) {
+    return std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t).count();
+  };
+  auto tw = wall();
+  float w_count = 0, w_bucket = 0, w_groups = 0, w_merge = 0;
+  // pass 0: the entries each coarse cell needs
   for (int side = 0; side < 2 && rc == HLC_OK; ++side) {
     const hlc_catalog* X = side ? B : A;
     unsigned long long* cnt = counts + side * nparts;
     rc = stream_catalog(X, dra, ddec, did, stage, ss, done, &ms_h2d,
-                        [&](double* r, double* d, uint64_t* id, uint64_t n, cudaStream_t s) {
+                        [&](double* r, double* d, uint64_t* id, uint64_t n, cudaStream_t s,
+                            uint64_t, int) {
                           (void)id;
                           k_part_count<<<grid_for(n, kThreads), kThreads, 0, s>>>(
                               r, d, n, Lf, Lc, side, K, cnt, err);
@@ -1823,6 +2036,8 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
     cleanup();
     return fail(rc);
   }
+  w_count = ms_since(tw);
+  tw = wall();
   // groups of consecutive coarse cells that fit the budget
   uint64_t budget = p->device_mem_budget;
   uint64_t fixed = 6 * kStreamChunk * 8 + 2 * nparts * 8 + (64ull << 20);
@@ -1841,54 +2056,200 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
     acc += c;
   }
   groups.push_back({g0, (uint32_t)nparts});
-  // pass 2: select, match in core, collect
+  // pass 1: every chunk bucketed by group on the device (a B source once per
+  // group that needs it) and copied to pinned host runs; the per-chunk group
+  // offsets are kept on the host
+  const uint32_t ngroups = (uint32_t)groups.size();
+  if ((uint64_t)ngroups * 8 > 48 * 1024) {
+    cleanup();
+    set_error("device_mem_budget too small: %u partition groups", ngroups);
+    return fail(HLC_EUNSUPPORTED);
+  }
+  std::vector<uint32_t> c2g(nparts);
+  for (uint32_t gi = 0; gi < ngroups; ++gi)
+    for (uint32_t q = groups[gi].first; q < groups[gi].second; ++q) c2g[q] = gi;
+  uint32_t* cell2group = ar.get_n<uint32_t>(nparts);
+  uint32_t* gcnt[2];
+  uint32_t* gcur[2];
+  uint32_t* goff[2];
+  double *bra[2], *bdec[2];
+  uint64_t* bid[2];
+  uint64_t bcap[2];
+  uint32_t* hgoff_pin = nullptr;  // 2 x (ngroups + 1), pinned
+  if (!cell2group) {
+    cleanup();
+    return fail(HLC_ENOMEM);
+  }
+  for (int b = 0; b < 2; ++b) {
+    gcnt[b] = ar.get_n<uint32_t>(ngroups + 1);
+    gcur[b] = ar.get_n<uint32_t>(ngroups + 1);
+    goff[b] = ar.get_n<uint32_t>(ngroups + 1);
+    // group-ordered chunk (grown when a chunk's B halo needs more)
+    bcap[b] = std::max<uint64_t>(1024, std::min<uint64_t>(kStreamChunk,
+                                                         std::max(A->n, B->n)) * 5 / 4);
+    bra[b] = ar.get_n<double>(bcap[b]);
+    bdec[b] = ar.get_n<double>(bcap[b]);
+    bid[b] = ar.get_n<uint64_t>(bcap[b]);
+    if (!gcnt[b] || !gcur[b] || !goff[b] || !bra[b] || !bdec[b] || !bid[b]) {
+      cleanup();
+      return fail(HLC_ENOMEM);
+    }
+  }
+  if (cudaHostAlloc((void**)&hgoff_pin, 2 * (ngroups + 1) * 4, cudaHostAllocDefault) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    set_error("pinned allocation failed");
+    return fail(HLC_ENOMEM);
+  }
+  HLC_CUDA(cudaMemcpy(cell2group, c2g.data(), nparts * 4, cudaMemcpyHostToDevice));
+  // host runs: side 0 (A) holds each source once, side 1 (B) at most its
+  // per-cell count sum
+  uint64_t hcap[2] = {A->n, 0};
+  for (uint32_t q = 0; q < nparts; ++q) hcap[1] += hc[nparts + q];
+  double *hra[2] = {nullptr, nullptr}, *hdec[2] = {nullptr, nullptr};
+  uint64_t* hid[2] = {nullptr, nullptr};
+  char* run_block_owned = nullptr;  // set once the runs are carved (below)
+  size_t run_block_bytes = 0;
+  auto free_host = [&]() {
+    if (run_block_owned) pinned_release(run_block_owned, run_block_bytes);
+    run_block_owned = nullptr;
+    for (int sd = 0; sd < 2; ++sd) {
+      hra[sd] = hdec[sd] = nullptr;
+      hid[sd] = nullptr;
+    }
+    if (hgoff_pin) cudaFreeHost(hgoff_pin);
+    hgoff_pin = nullptr;
+  };
+  size_t run_bytes = 0;
+  char* run_block = nullptr;
+  {
+    const size_t b0 = (size_t)(hcap[0] + 1) * 8, b1 = (size_t)(hcap[1] + 1) * 8;
+    run_bytes = 3 * (b0 + b1);
+    run_block = (char*)pinned_acquire(&run_bytes);
+    if (!run_block) {
+      free_host();
+      cleanup();
+      set_error("pinned host runs (%zu bytes) could not be allocated", 3 * (b0 + b1));
+      return fail(HLC_ENOMEM);
+    }
+    hra[0] = (double*)run_block;
+    hdec[0] = (double*)(run_block + b0);
+    hid[0] = (uint64_t*)(run_block + 2 * b0);
+    hra[1] = (double*)(run_block + 3 * b0);
+    hdec[1] = (double*)(run_block + 3 * b0 + b1);
+    hid[1] = (uint64_t*)(run_block + 3 * b0 + 2 * b1);
+    run_block_owned = run_block;
+    run_block_bytes = run_bytes;
+  }
+  // hoff[side][chunk][g]: start of group g inside the chunk's run; hbase: run start
+  std::vector<std::vector<std::vector<uint32_t>>> hoff(2);
+  std::vector<std::vector<uint64_t>> hbase(2);
+  const size_t gsmem = 2 * (size_t)ngroups * 4;
+  for (int side = 0; side < 2 && rc == HLC_OK; ++side) {
+    const hlc_catalog* X = side ? B : A;
+    uint64_t filled = 0;
+    rc = stream_catalog(
+        X, dra, ddec, did, stage, ss, done, &ms_h2d,
+        [&](double* r, double* d, uint64_t* id, uint64_t n, cudaStream_t s, uint64_t c,
+            int b) {
+          HLC_CUDA(cudaMemsetAsync(gcnt[b], 0, (ngroups + 1) * 4, s));
+          HLC_CUDA(cudaMemsetAsync(gcur[b], 0, (ngroups + 1) * 4, s));
+          k_group_hist<<<grid_for(n, kThreads, 148u * 4u), kThreads, gsmem / 2, s>>>(
+              r, d, n, Lf, Lc, side, K, cell2group, ngroups, gcnt[b]);
+          HLC_LAUNCH_CHECK();
+          k_small_excl_scan<<<1, 1024, 0, s>>>(gcnt[b], ngroups, goff[b]);
+          HLC_LAUNCH_CHECK();
+          uint32_t* hg = hgoff_pin + b * (ngroups + 1);
+          HLC_CUDA(cudaMemcpyAsync(hg, goff[b], (ngroups + 1) * 4, cudaMemcpyDeviceToHost, s));
+          HLC_CUDA(cudaStreamSynchronize(s));
+          const uint64_t tot = hg[ngroups];
+          if (filled + tot > hcap[side]) {
+            set_error("streamed bucketing overflowed its host runs");
+            return HLC_ECUDA;
+          }
+          if (tot > bcap[b]) {  // this chunk's halo copies need a larger buffer
+            ar.drop(bra[b]);
+            ar.drop(bdec[b]);
+            ar.drop(bid[b]);
+            bcap[b] = tot + tot / 8;
+            bra[b] = ar.get_n<double>(bcap[b]);
+            bdec[b] = ar.get_n<double>(bcap[b]);
+            bid[b] = ar.get_n<uint64_t>(bcap[b]);
+            if (!bra[b] || !bdec[b] || !bid[b]) return HLC_ENOMEM;
+            HLC_CUDA(cudaStreamSynchronize(st));  // allocations are ordered on the plan stream
+          }
+          k_group_scatter<<<grid_for(n, kThreads, 148u * 4u), kThreads, gsmem, s>>>(
+              r, d, id, n, Lf, Lc, side, K, cell2group, ngroups, goff[b], gcur[b], bra[b],
+              bdec[b], bid[b], err);
+          HLC_LAUNCH_CHECK();
+          hoff[side].push_back(std::vector<uint32_t>(hg, hg + ngroups + 1));
+          hbase[side].push_back(filled);
+          if (tot) {
+            HLC_CUDA(cudaMemcpyAsync(hra[side] + filled, bra[b], tot * 8, cudaMemcpyDeviceToHost,
+                                     s));
+            HLC_CUDA(cudaMemcpyAsync(hdec[side] + filled, bdec[b], tot * 8,
+                                     cudaMemcpyDeviceToHost, s));
+            HLC_CUDA(cudaMemcpyAsync(hid[side] + filled, bid[b], tot * 8, cudaMemcpyDeviceToHost,
+                                     s));
+          }
+          filled += tot;
+          (void)c;
+          return HLC_OK;
+        });
+  }
+  if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_plan (streamed)");
+  for (int b = 0; b < 2; ++b) {
+    ar.drop(bra[b]);
+    ar.drop(bdec[b]);
+    ar.drop(bid[b]);
+  }
+  w_bucket = ms_since(tw);
+  tw = wall();
+  // pass 2: per group, its slices of every chunk's run in, match in core, rows out
   std::vector<HostRows> runs;
   hlc_stats agg{};
-  for (auto& g : groups) {
-    uint64_t na = 0, nb = 0;
-    for (uint32_t q = g.first; q < g.second; ++q) {
-      na += hc[q];
-      nb += hc[nparts + q];
-    }
+  for (uint32_t gi = 0; gi < ngroups && rc == HLC_OK; ++gi) {
+    uint64_t gn[2] = {0, 0};
+    for (int side = 0; side < 2; ++side)
+      for (auto& o : hoff[side]) gn[side] += o[gi + 1] - o[gi];
+    const uint64_t na = gn[0], nb = gn[1];
     if (na == 0 || nb == 0) continue;
-    double *gra[2], *gdec[2];
-    uint64_t* gid[2];
-    const uint64_t gn[2] = {na, nb};
+    double *gra[2] = {nullptr, nullptr}, *gdec[2] = {nullptr, nullptr};
+    uint64_t* gid[2] = {nullptr, nullptr};
     for (int side = 0; side < 2; ++side) {
       gra[side] = ar.get_n<double>(gn[side] + 1);
       gdec[side] = ar.get_n<double>(gn[side] + 1);
       gid[side] = ar.get_n<uint64_t>(gn[side] + 1);
       if (!gra[side] || !gdec[side] || !gid[side]) {
-        cleanup();
-        return fail(HLC_ENOMEM);
+        rc = HLC_ENOMEM;
+        break;
       }
-    }
-    HLC_CUDA(cudaMemsetAsync(cur, 0, 32, st));
-    HLC_CUDA(cudaStreamSynchronize(st));
-    for (int side = 0; side < 2 && rc == HLC_OK; ++side) {
-      const hlc_catalog* X = side ? B : A;
-      rc = stream_catalog(
-          X, dra, ddec, did, stage, ss, done, &ms_h2d,
-          [&](double* r, double* d, uint64_t* id, uint64_t n, cudaStream_t s) {
-            k_part_select<<<grid_for(n, kThreads), kThreads, 0, s>>>(
-                r, d, id, n, Lf, Lc, side, K, g.first, g.second, gra[side], gdec[side],
-                gid[side], cur + side, gn[side], err);
-            HLC_LAUNCH_CHECK();
-            return HLC_OK;
-          });
-    }
-    if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_plan (streamed)");
-    // (a B source needed by several coarse cells of the group is taken once,
-    // so the per-cell sums are upper bounds; the cursors hold the counts)
-    if (rc == HLC_OK) {
-      unsigned long long hcur[2] = {0, 0};
-      if (cudaMemcpy(hcur, cur, 16, cudaMemcpyDeviceToHost) != cudaSuccess) rc = HLC_ECUDA;
-      if (rc == HLC_OK && (hcur[0] > na || hcur[1] > nb)) {
-        set_error("streamed selection overflowed its buffers");
-        rc = HLC_ECUDA;
+      cudaEvent_t t0, t1;
+      cudaEventCreate(&t0);
+      cudaEventCreate(&t1);
+      cudaEventRecord(t0, st);
+      uint64_t o = 0;
+      for (size_t c = 0; c < hoff[side].size() && rc == HLC_OK; ++c) {
+        const uint64_t s0 = hbase[side][c] + hoff[side][c][gi];
+        const uint64_t len = hoff[side][c][gi + 1] - hoff[side][c][gi];
+        if (!len) continue;
+        if (cudaMemcpyAsync(gra[side] + o, hra[side] + s0, len * 8, cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(gdec[side] + o, hdec[side] + s0, len * 8, cudaMemcpyHostToDevice,
+                            st) != cudaSuccess ||
+            cudaMemcpyAsync(gid[side] + o, hid[side] + s0, len * 8, cudaMemcpyHostToDevice, st) !=
+                cudaSuccess)
+          rc = HLC_ECUDA;
+        o += len;
       }
-      na = hcur[0];
-      nb = hcur[1];
+      cudaEventRecord(t1, st);
+      cudaEventSynchronize(t1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, t0, t1);
+      ms_h2d += ms;
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
     }
     hlc_plan_t* G = nullptr;
     if (rc == HLC_OK) {
@@ -1902,27 +2263,33 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
     if (rc == HLC_OK) rc = match_single(G, &r, &gs);
     if (rc == HLC_OK && r.n) {
       HostRows h;
-      h.a.resize(r.n);
-      h.b.resize(r.n);
-      if (r.sep_arcsec) h.s.resize(r.n);
-      cudaEvent_t d0, d1;
-      cudaEventCreate(&d0);
-      cudaEventCreate(&d1);
-      cudaEventRecord(d0, st);
-      if (cudaMemcpyAsync(h.a.data(), r.id_a, r.n * 8, cudaMemcpyDeviceToHost, st) !=
-              cudaSuccess ||
-          cudaMemcpyAsync(h.b.data(), r.id_b, r.n * 8, cudaMemcpyDeviceToHost, st) !=
-              cudaSuccess ||
-          (r.sep_arcsec && cudaMemcpyAsync(h.s.data(), r.sep_arcsec, r.n * 8,
-                                           cudaMemcpyDeviceToHost, st) != cudaSuccess))
-        rc = HLC_ECUDA;
-      cudaEventRecord(d1, st);
-      cudaStreamSynchronize(st);
-      float ms = 0;
-      cudaEventElapsedTime(&ms, d0, d1);
-      agg.ms_d2h += ms;
-      cudaEventDestroy(d0);
-      cudaEventDestroy(d1);
+      const size_t rb = (size_t)r.n * 8;
+      if (!h.buf.get((r.sep_arcsec ? 3 : 2) * rb)) {
+        set_error("pinned result rows could not be allocated");
+        rc = HLC_ENOMEM;
+      } else {
+        h.n = r.n;
+        h.a = (const uint64_t*)h.buf.p;
+        h.b = (const uint64_t*)(h.buf.p + rb);
+        h.s = r.sep_arcsec ? (const double*)(h.buf.p + 2 * rb) : nullptr;
+        cudaEvent_t d0, d1;
+        cudaEventCreate(&d0);
+        cudaEventCreate(&d1);
+        cudaEventRecord(d0, st);
+        if (cudaMemcpyAsync(h.buf.p, r.id_a, rb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(h.buf.p + rb, r.id_b, rb, cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            (r.sep_arcsec && cudaMemcpyAsync(h.buf.p + 2 * rb, r.sep_arcsec, rb,
+                                             cudaMemcpyDeviceToHost, st) != cudaSuccess))
+          rc = HLC_ECUDA;
+        cudaEventRecord(d1, st);
+        cudaStreamSynchronize(st);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, d0, d1);
+        agg.ms_d2h += ms;
+        cudaEventDestroy(d0);
+        cudaEventDestroy(d1);
+      }
       runs.push_back(std::move(h));
     }
     if (G) {
@@ -1942,45 +2309,33 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
       hlc_free(G);
     }
     for (int side = 0; side < 2; ++side) {
-      ar.drop(gra[side]);
-      ar.drop(gdec[side]);
-      ar.drop(gid[side]);
+      if (gra[side]) ar.drop(gra[side]);
+      if (gdec[side]) ar.drop(gdec[side]);
+      if (gid[side]) ar.drop(gid[side]);
     }
     if (rc != HLC_OK) break;
     ++agg.partitions;
   }
+  free_host();
   cleanup();
+  w_groups = ms_since(tw);
+  tw = wall();
   if (rc != HLC_OK) return fail(rc);
   // k-way merge of the groups' sorted rows
   uint64_t M = 0;
-  for (auto& h : runs) M += h.a.size();
+  for (auto& h : runs) M += h.n;
   const bool want_sep = p->want_sep != 0;
-  P->host_a.resize(M);
-  P->host_b.resize(M);
-  if (want_sep) P->host_s.resize(M);
-  {
-    typedef std::pair<size_t, size_t> Cur;  // (run, position)
-    auto gt = [&](const Cur& x, const Cur& y) {
-      const HostRows& u = runs[x.first];
-      const HostRows& v = runs[y.first];
-      return row_lt(v.a[y.second], v.b[y.second], v.s.empty() ? 0.0 : v.s[y.second],
-                    u.a[x.second], u.b[x.second], u.s.empty() ? 0.0 : u.s[x.second]);
-    };
-    std::priority_queue<Cur, std::vector<Cur>, decltype(gt)> pq(gt);
-    for (size_t r = 0; r < runs.size(); ++r)
-      if (!runs[r].a.empty()) pq.push({r, 0});
-    uint64_t o = 0;
-    while (!pq.empty()) {
-      Cur c = pq.top();
-      pq.pop();
-      const HostRows& h = runs[c.first];
-      P->host_a[o] = h.a[c.second];
-      P->host_b[o] = h.b[c.second];
-      if (want_sep) P->host_s[o] = h.s[c.second];
-      ++o;
-      if (c.second + 1 < h.a.size()) pq.push({c.first, c.second + 1});
-    }
+  if (M && !P->host_buf.get((want_sep ? 3 : 2) * M * 8)) {
+    set_error("pinned output rows could not be allocated");
+    return fail(HLC_ENOMEM);
   }
+  P->host_n = M;
+  P->host_a = (uint64_t*)P->host_buf.p;
+  P->host_b = M ? (uint64_t*)(P->host_buf.p + M * 8) : nullptr;
+  P->host_s = want_sep && M ? (double*)(P->host_buf.p + 2 * M * 8) : nullptr;
+  merge_runs(runs, want_sep, P->host_a, P->host_b, P->host_s);
+  runs.clear();  // their blocks go back to the pool
+  w_merge = ms_since(tw);
   cudaEventRecord(e1, st);
   cudaEventSynchronize(e1);
   float total = 0;
@@ -1994,16 +2349,20 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
   agg.join_level = Lf;
   agg.ms_h2d = ms_h2d;
   agg.ms_total = total;
+  agg.ms_stream_count = w_count;
+  agg.ms_stream_bucket = w_bucket;
+  agg.ms_stream_groups = w_groups;
+  agg.ms_stream_merge = w_merge;
   P->stats = agg;
   *out = P;
   return HLC_OK;
 }
 
 static int match_streamed(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
-  res->n = P->host_a.size();
-  res->id_a = P->host_a.data();
-  res->id_b = P->host_b.data();
-  res->sep_arcsec = P->p.want_sep ? P->host_s.data() : nullptr;
+  res->n = P->host_n;
+  res->id_a = P->host_a;
+  res->id_b = P->host_b;
+  res->sep_arcsec = P->p.want_sep ? P->host_s : nullptr;
   res->job = nullptr;
   res->on_device = 0;
   if (stats) *stats = P->stats;
@@ -2332,8 +2691,9 @@ int hlc_learned_lookup(const uint32_t* uniq, uint64_t m, int shift, int model,
                        const uint32_t* queries, uint64_t nq, uint32_t* out, hlc_stats* stats,
                        void* stream) {
   clear_error();
-  if (shift < 0 || shift > 24 || (model != HLC_MODEL_PLA && model != HLC_MODEL_MLP)) {
-    set_error("shift must be in [0, 24] and model HLC_MODEL_PLA or HLC_MODEL_MLP");
+  if (shift < 0 || shift > 24 ||
+      (model != HLC_MODEL_PLA && model != HLC_MODEL_MLP && model != HLC_MODEL_NONE)) {
+    set_error("shift must be in [0, 24] and model HLC_MODEL_PLA, _MLP or _NONE");
     return HLC_EINVAL;
   }
   if ((m && !uniq) || (nq && (!queries || !out))) {
@@ -2365,7 +2725,11 @@ int hlc_learned_lookup(const uint32_t* uniq, uint64_t m, int shift, int model,
   int rc = build_learned(ar, uniq, m, shift, model, P, ctr, ctr + 1, err, st, &L);
   cudaEventRecord(e1, st);
   if (rc == HLC_OK && nq) {
-    k_learned_lookup<<<grid_for(nq, kThreads), kThreads, 0, st>>>(L, queries, nq, out, ctr + 2);
+    if (model == HLC_MODEL_NONE)
+      k_part_bsearch_lookup<<<grid_for(nq, kThreads), kThreads, 0, st>>>(L, queries, nq, out);
+    else
+      k_learned_lookup<<<grid_for(nq, kThreads), kThreads, 0, st>>>(L, queries, nq, out,
+                                                                     ctr + 2);
     if (cudaGetLastError() != cudaSuccess) rc = HLC_ECUDA;
   }
   cudaEventRecord(e2, st);
@@ -2382,7 +2746,7 @@ int hlc_learned_lookup(const uint32_t* uniq, uint64_t m, int shift, int model,
     memset(stats, 0, sizeof(*stats));
     stats->learned_models = P;
     stats->learned_max_err = maxerr;
-    stats->learned_hit_rate = nq ? (double)h[2] / (double)nq : 1.0;
+    stats->learned_hit_rate = (nq && model != HLC_MODEL_NONE) ? (double)h[2] / (double)nq : 1.0;
     cudaEventElapsedTime(&stats->ms_index, e0, e1);
     cudaEventElapsedTime(&stats->ms_candidates, e1, e2);
   }

@@ -25,7 +25,7 @@ def _keys(kind, n, bits, rng):
     return np.unique(k).astype(np.uint32)
 
 
-@pytest.mark.parametrize("model", [hlc.HLC_MODEL_PLA, hlc.HLC_MODEL_MLP])
+@pytest.mark.parametrize("model", [hlc.HLC_MODEL_PLA, hlc.HLC_MODEL_MLP, hlc.HLC_MODEL_NONE])
 @pytest.mark.parametrize("kind", ["uniform", "clustered"])
 @pytest.mark.parametrize("bits,shift", [(28, 20), (30, 24), (32, 24), (20, 8), (12, 0)])
 def test_lookup_equals_binary_search(model, kind, bits, shift):
