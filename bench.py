@@ -210,16 +210,18 @@ def run_hlc(args):
                              A.id.cpu().pin_memory())
         Bh = synth.Catalogue(B.ra.cpu().pin_memory(), B.dec.cpu().pin_memory(),
                              B.id.cpu().pin_memory())
-        import numpy as np
         times = []
         ke = min(args.steps, 30)
+        cap = 2 * max(nmatch, 1)  # pinned result buffers, allocated once
+        outb = tuple(torch.empty(cap, dtype=dt).pin_memory()
+                     for dt in (torch.int64, torch.int64, torch.float64))
         for it in range(args.warmup + ke):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             plan = hlc.hlc_plan(Ah, Bh, r, L, coarse_level=Lc, boundary=mode, precision=prec,
                                 stream=stream)
             hlc.hlc_match(plan, copy=False)
-            ia, ib, sp = hlc.hlc_result_to_host(plan)
+            ia, ib, sp = hlc.hlc_result_to_host(plan, out=outb)
             hlc.hlc_free(plan)
             t1 = time.perf_counter()
             if it >= args.warmup:

@@ -328,15 +328,26 @@ def hlc_match(plan: Plan, copy: bool = True) -> dict:
                 stats=s.as_dict())
 
 
-def hlc_result_to_host(plan: Plan):
+def hlc_result_to_host(plan: Plan, out=None):
+    """Copy the last result's rows to host memory.  out: optional (id_a, id_b,
+    sep) host buffers (numpy arrays or CPU tensors, pinned ones copy fastest)
+    with room for n rows; the returned arrays are views of their first n."""
     r = plan.result
     n = int(r.n)
-    ia = np.empty(n, np.uint64)
-    ib = np.empty(n, np.uint64)
-    sp = np.empty(n, np.float64)
+
+    def buf(i, dt):
+        if out is None:
+            return np.empty(n, dt)
+        b = out[i]
+        b = b.numpy() if isinstance(b, torch.Tensor) else b
+        if b.size < n:
+            raise ValueError("output buffer %d holds %d rows, %d needed" % (i, b.size, n))
+        return b[:n].view(dt)
+    ia, ib = buf(0, np.uint64), buf(1, np.uint64)
+    sp = buf(2, np.float64) if r.sep_arcsec else None
     _check(lib().hlc_result_to_host(C.byref(r), ia.ctypes.data, ib.ctypes.data,
-                                    sp.ctypes.data if r.sep_arcsec else None, None))
-    return ia, ib, (sp if r.sep_arcsec else None)
+                                    sp.ctypes.data if sp is not None else None, None))
+    return ia, ib, sp
 
 
 def hlc_free(plan: Plan):
