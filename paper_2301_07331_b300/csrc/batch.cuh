@@ -406,7 +406,8 @@ __global__ void k_brows(const uint2* __restrict__ rows, uint64_t M,
     o.job = (uint32_t)(keyA[p.x] >> cell_bits);
     o.pad = 0;
     o.s = 0.0;
-    if (bhist) atomicAdd(&bhist[((uint64_t)o.job << nb) | ((uint32_t)(o.a >> bshift) & bmask)], 1u);
+    if (bhist)  // the row's rank in its bucket, for the scatter
+      o.pad = atomicAdd(&bhist[((uint64_t)o.job << nb) | ((uint32_t)(o.a >> bshift) & bmask)], 1u);
     if (want_sep) {
       double sv;
       if (FP32) {

@@ -66,6 +66,7 @@ enum DevErr : int {
   DERR_TIMEOUT = 2,   // a bounded spin-wait gave up
   DERR_OVERFLOW = 4,  // an output buffer was too small (host retries)
   DERR_BOUNDS = 8,    // an index check failed (skipped access)
+  DERR_BUCKET = 16,   // an output bucket exceeded the in-block sort (host re-orders)
 };
 
 // ---------------------------------------------------------------------------

@@ -933,35 +933,28 @@ static int order_rows(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_t* bhist
     return HLC_OK;
   }
   if (bucketed && nbk < (1ull << 31)) {
+    // no host round trip: buckets above kSmallBucket rows are listed by
+    // k_bucket_small for k_bucket_sort; one above kBucketCap raises
+    // DERR_BUCKET and order_rows_checked re-orders with the radix sorts
     void* scr = ar.get(scan_scratch_bytes(nbk + 1));
-    if (!scr) return HLC_ENOMEM;
+    OutRow* t = ar.get_n<OutRow>(M + 1);
+    uint32_t* big = ar.get_n<uint32_t>(nbk + 1);
+    if (!scr || !t || !big) return HLC_ENOMEM;
     HLC_TRY(scan_exclusive<uint32_t>(bhist, boff, nbk + 1, P->ctr + C_TOTAL, scr, P->dev_err, st));
     HLC_CUDA(cudaMemsetAsync(P->ctr + C_MAXB, 0, 8, st));
-    k_max_u32<<<grid_for(nbk, kThreads, 1024), kThreads, 0, st>>>(bhist, nbk,
-                                                                  (uint32_t*)(P->ctr + C_MAXB));
+    k_bucket_scatter<<<g, kThreads, 0, st>>>(rows32, M, bshift, bmask, nb_job, boff, t);
     HLC_LAUNCH_CHECK();
-    unsigned long long maxb = 0;
-    HLC_CUDA(cudaMemcpyAsync(&maxb, P->ctr + C_MAXB, 8, cudaMemcpyDeviceToHost, st));
-    HLC_CUDA(cudaStreamSynchronize(st));
+    k_bucket_small<<<grid_for(nbk, kThreads), kThreads, 0, st>>>(
+        t, boff, (uint32_t)nbk, a, b, sp, jb, big, (uint32_t*)(P->ctr + C_MAXB), P->dev_err);
+    HLC_LAUNCH_CHECK();
+    k_bucket_sort<<<148u * 8u, kBucketThreads, 0, st>>>(t, boff, big,
+                                                         (uint32_t*)(P->ctr + C_MAXB),
+                                                         want_sep ? 1 : 0, a, b, sp, jb);
+    HLC_LAUNCH_CHECK();
     ar.drop(scr);
-    maxb &= 0xFFFFFFFFull;
-    if (maxb <= (unsigned long long)kBucketCap) {
-      OutRow* t = ar.get_n<OutRow>(M + 1);
-      if (!t) return HLC_ENOMEM;
-      HLC_CUDA(cudaMemcpyAsync(bhist, boff, (size_t)nbk * 4, cudaMemcpyDeviceToDevice, st));
-      k_bucket_scatter<<<g, kThreads, 0, st>>>(rows32, M, bshift, bmask, nb_job, bhist, t);
-      HLC_LAUNCH_CHECK();
-      k_bucket_small<<<grid_for(nbk, kThreads), kThreads, 0, st>>>(t, boff, (uint32_t)nbk, a, b,
-                                                                    sp, jb);
-      HLC_LAUNCH_CHECK();
-      if (maxb > kSmallBucket) {
-        k_bucket_sort<<<(unsigned)std::min<uint64_t>(nbk, 148u * 32u), kBucketThreads, 0, st>>>(
-            t, boff, (uint32_t)nbk, want_sep ? 1 : 0, a, b, sp, jb, P->dev_err);
-        HLC_LAUNCH_CHECK();
-      }
-      ar.drop(t);
-      return HLC_OK;
-    }
+    ar.drop(t);
+    ar.drop(big);
+    return HLC_OK;
   }
   // fallback: stable LSD radix sorts by id_b, id_a (and job)
   uint64_t* ua = ar.get_n<uint64_t>(M + 1);
@@ -993,6 +986,30 @@ static int order_rows(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_t* bhist
   k_gather<uint64_t><<<g, kThreads, 0, st>>>(ub, perm, M, b);
   if (want_sep) k_gather<double><<<g, kThreads, 0, st>>>(us, perm, M, sp);
   HLC_LAUNCH_CHECK();
+  return HLC_OK;
+}
+
+// order_rows, then (after the stream has drained) a repeat with the radix
+// sorts when a bucket was too large for the in-block sort.
+static int order_rows_checked(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_t* bhist,
+                              uint32_t* boff, uint64_t nbk, int nb_job, int bshift,
+                              uint32_t bmask, bool bucketed, bool want_sep, uint64_t** oa,
+                              uint64_t** ob, double** os, uint32_t** oj) {
+  cudaStream_t st = plan_stream(P);
+  HLC_TRY(order_rows(P, rows32, M, bhist, boff, nbk, nb_job, bshift, bmask, bucketed, want_sep,
+                     oa, ob, os, oj));
+  int h = 0;
+  HLC_CUDA(cudaMemcpyAsync(&h, P->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HLC_CUDA(cudaStreamSynchronize(st));
+  if (!(h & DERR_BUCKET)) return HLC_OK;
+  Arena& ar = *P->out;
+  for (void* q : {(void*)*oa, (void*)*ob, (void*)*os, (void*)*oj})
+    if (q) ar.drop(q);
+  h &= ~DERR_BUCKET;
+  HLC_CUDA(cudaMemcpyAsync(P->dev_err, &h, sizeof(int), cudaMemcpyHostToDevice, st));
+  HLC_TRY(order_rows(P, rows32, M, bhist, boff, nbk, nb_job, bshift, bmask, false, want_sep, oa,
+                     ob, os, oj));
+  HLC_CUDA(cudaStreamSynchronize(st));
   return HLC_OK;
 }
 
@@ -1153,8 +1170,8 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   uint64_t *oa = nullptr, *ob = nullptr;
   double* os = nullptr;
   uint32_t* oj = nullptr;
-  HLC_TRY(order_rows(P, rows32, M, bhist, boff, nbk, -1, bshift, bmask, bucketed, want_sep, &oa,
-                     &ob, &os, &oj));
+  HLC_TRY(order_rows_checked(P, rows32, M, bhist, boff, nbk, -1, bshift, bmask, bucketed,
+                             want_sep, &oa, &ob, &os, &oj));
   ar.drop(rows32);
   if (bhist) {
     ar.drop(bhist);
@@ -1706,8 +1723,8 @@ static int match_batched(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   uint64_t *oa = nullptr, *ob = nullptr;
   double* os = nullptr;
   uint32_t* oj = nullptr;
-  HLC_TRY(order_rows(P, rows32, M, bhist, boff, nbk, nb, bshift, bmask, true, want_sep, &oa, &ob,
-                     &os, &oj));
+  HLC_TRY(order_rows_checked(P, rows32, M, bhist, boff, nbk, nb, bshift, bmask, true, want_sep,
+                             &oa, &ob, &os, &oj));
   ar.drop(rows32);
   ar.drop(bhist);
   ar.drop(boff);

@@ -123,7 +123,7 @@ __global__ void k_rows(const uint2* __restrict__ rows, uint64_t M,
     o.s = 0.0;
     o.job = 0;
     o.pad = 0;
-    if (bhist) atomicAdd(&bhist[(uint32_t)(u.id >> bshift) & bmask], 1u);
+    if (bhist) o.pad = atomicAdd(&bhist[(uint32_t)(u.id >> bshift) & bmask], 1u);  // rank
     if (want_sep) {
       double sv;
       if (FP32) {
@@ -162,16 +162,17 @@ __global__ void k_max_u32(const uint32_t* __restrict__ v, uint64_t n, uint32_t* 
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
+// Rows to their buckets: offset of the bucket plus the rank the row drew
+// there (in OutRow.pad) when the histogram was built.
 __global__ void k_bucket_scatter(const OutRow* __restrict__ in, uint64_t M, int bshift,
-                                 uint32_t bmask, int nb_job, uint32_t* __restrict__ cursor,
+                                 uint32_t bmask, int nb_job, const uint32_t* __restrict__ boff,
                                  OutRow* __restrict__ out) {
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
        m += (uint64_t)gridDim.x * blockDim.x) {
     OutRow o = in[m];
     uint64_t bk = (nb_job >= 0 ? ((uint64_t)o.job << nb_job) : 0ull) |
                   ((uint32_t)(o.a >> bshift) & bmask);
-    uint32_t pos = atomicAdd(&cursor[bk], 1u);
-    out[pos] = o;
+    out[__ldg(boff + bk) + o.pad] = o;
   }
 }
 
@@ -186,15 +187,25 @@ __device__ __forceinline__ bool row_less(uint64_t a1, uint64_t b1, uint64_t s1, 
 // output arrays.
 constexpr uint32_t kSmallBucket = 32;
 
+// (Larger buckets are appended to `big` for k_bucket_sort; one above
+// kBucketCap sets DERR_BUCKET and the host orders the rows another way.)
 __global__ void k_bucket_small(const OutRow* __restrict__ t, const uint32_t* __restrict__ boff,
                                uint32_t nbuckets, uint64_t* __restrict__ oa,
                                uint64_t* __restrict__ ob, double* __restrict__ os,
-                               uint32_t* __restrict__ oj) {
+                               uint32_t* __restrict__ oj, uint32_t* __restrict__ big,
+                               uint32_t* __restrict__ nbig, int* __restrict__ err) {
   for (uint32_t bk = blockIdx.x * blockDim.x + threadIdx.x; bk < nbuckets;
        bk += gridDim.x * blockDim.x) {
     uint32_t lo = boff[bk], hi = boff[bk + 1];
     uint32_t n = hi - lo;
-    if (n == 0 || n > kSmallBucket) continue;
+    if (n > kSmallBucket) {
+      if (n > kBucketCap)
+        atomicOr(err, DERR_BUCKET);
+      else
+        big[atomicAdd(nbig, 1u)] = bk;
+      continue;
+    }
+    if (n == 0) continue;
     for (uint32_t i = 0; i < n; ++i) {
       OutRow r = t[lo + i];
       uint64_t sb = (uint64_t)__double_as_longlong(r.s);
@@ -219,18 +230,17 @@ __global__ void k_bucket_small(const OutRow* __restrict__ t, const uint32_t* __r
 // One CTA per larger bucket (kSmallBucket < rows <= kBucketCap): bitonic
 // sort in shared memory.
 __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(
-    const OutRow* __restrict__ t, const uint32_t* __restrict__ boff, uint32_t nbuckets,
-    int use_sep, uint64_t* __restrict__ oa, uint64_t* __restrict__ ob, double* __restrict__ os,
-    uint32_t* __restrict__ oj, int* __restrict__ err) {
+    const OutRow* __restrict__ t, const uint32_t* __restrict__ boff,
+    const uint32_t* __restrict__ big, const uint32_t* __restrict__ nbig, int use_sep,
+    uint64_t* __restrict__ oa, uint64_t* __restrict__ ob, double* __restrict__ os,
+    uint32_t* __restrict__ oj) {
   __shared__ uint64_t A[kBucketCap], B[kBucketCap], S[kBucketCap];
-  for (uint32_t bk = blockIdx.x; bk < nbuckets; bk += gridDim.x) {
+  const uint32_t nb = *nbig;
+  for (uint32_t q = blockIdx.x; q < nb; q += gridDim.x) {
+    const uint32_t bk = big[q];
     uint32_t lo = boff[bk], hi = boff[bk + 1];
     uint32_t n = hi - lo;
-    if (n <= kSmallBucket) continue;
-    if (n > kBucketCap) {  // the host checked; never taken
-      if (threadIdx.x == 0) atomicOr(err, DERR_BOUNDS);
-      continue;
-    }
+    if (n <= kSmallBucket || n > kBucketCap) continue;  // (listed ones are in range)
     uint32_t np = 1;
     while (np < n) np <<= 1;
     for (uint32_t i = threadIdx.x; i < np; i += kBucketThreads) {
