@@ -570,11 +570,9 @@ static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
     if (!slow) return HLC_ENOMEM;
     HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st));
     k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-        ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, slow, P->ctr + C_SLOW, nullptr, 0,
-        is_b ? nullptr : P->ctr + C_IDDIFF, P->dev_err);
+        ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, slow, P->ctr + C_SLOW, P->dev_err);
     HLC_LAUNCH_CHECK();
-    k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key,
-                                                  nullptr, 0);
+    k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key);
     HLC_LAUNCH_CHECK();
     ar.drop(slow);
   }
@@ -597,7 +595,8 @@ static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
   }
   HLC_ALLOC(ar, X.v32, float4, n + 1);
   if (n) {
-    k_payload32<<<grid_for(n, kThreads), kThreads, 0, st>>>(X.rec, X.idx, n, X.v32);
+    k_payload32<<<grid_for(n, kThreads), kThreads, 0, st>>>(X.rec, X.idx, n, X.v32,
+                                                            is_b ? nullptr : P->ctr + C_IDDIFF);
     HLC_LAUNCH_CHECK();
   }
   cudaEventRecord(ev[2], st);
@@ -672,17 +671,15 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
         if (!slow) return HLC_ENOMEM;
         HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st));
         k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, slow, P->ctr + C_SLOW, nullptr,
-            0, nullptr, P->dev_err);
+            ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, slow, P->ctr + C_SLOW,
+            P->dev_err);
         HLC_LAUNCH_CHECK();
-        k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key,
-                                                      nullptr, 0);
+        k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key);
         HLC_LAUNCH_CHECK();
         ar.drop(slow);
       } else {
         k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, nullptr, nullptr, nullptr, 0,
-            nullptr, P->dev_err);
+            ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, nullptr, nullptr, P->dev_err);
         HLC_LAUNCH_CHECK();
       }
     }
@@ -754,7 +751,7 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
   } else {
     HLC_ALLOC(ar, X.v32, float4, m + 1);
     if (m) {
-      k_payload32<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.rec, X.idx, m, X.v32);
+      k_payload32<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.rec, X.idx, m, X.v32, nullptr);
       HLC_LAUNCH_CHECK();
     }
   }
@@ -2514,13 +2511,11 @@ int hlc_ang2pix(const double* ra, const double* dec, uint64_t n, int order, int 
     }
     cudaMemsetAsync(nslow, 0, 8, st);
     k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-        ra, dec, nullptr, n, order, pix_const(order), pix, idx, nullptr, slow, nslow, nullptr, 0,
-        nullptr, err);
-    k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, order, slow, nslow, pix, nullptr, 0);
+        ra, dec, nullptr, n, order, pix_const(order), pix, idx, nullptr, slow, nslow, err);
+    k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, order, slow, nslow, pix);
   } else {
     k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-        ra, dec, nullptr, n, order, pix_const(order), pix, idx, nullptr, nullptr, nullptr, nullptr,
-        0, nullptr, err);
+        ra, dec, nullptr, n, order, pix_const(order), pix, idx, nullptr, nullptr, nullptr, err);
   }
   int rc = HLC_OK;
   if (cudaGetLastError() != cudaSuccess) {

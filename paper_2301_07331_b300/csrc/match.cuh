@@ -49,11 +49,7 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
                             const uint64_t* __restrict__ id, uint64_t n, int order, PixConst K,
                             uint32_t* __restrict__ key, uint32_t* __restrict__ idx,
                             SrcRec* __restrict__ rec, uint32_t* __restrict__ slow,
-                            unsigned long long* __restrict__ nslow, uint32_t* __restrict__ hist,
-                            int hshift, unsigned long long* __restrict__ iddiff,
-                            int* __restrict__ err) {
-  const uint64_t id0 = (iddiff && n) ? __ldg(id) : 0;
-  unsigned long long idacc = 0;
+                            unsigned long long* __restrict__ nslow, int* __restrict__ err) {
   for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n;
        i0 += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t i = i0 + threadIdx.x;
@@ -62,7 +58,6 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
     if (live) {
       double a = ra[i], d = dec[i];
       uint32_t k = 0;
-      bool ok = false;
       if (FAST) {
         if (!(bits_finite(a) && bits_abs_le(d, 90.0))) {
           atomicOr(err, DERR_INPUT);
@@ -70,7 +65,6 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
           if (!bits_in_ra_range(a)) a = c_norm_ra(a);
           FastDec fd = f_dec_part(split_f64(d));
           defer = !f_pix(split_f64(a), fd, order, K, &k);
-          ok = !defer;
         }
       } else {
         if (!c_valid(a, d)) {
@@ -78,19 +72,15 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
         } else {
           a = c_norm_ra(a);
           k = c_ang2pix(a, d, order);
-          ok = true;
         }
       }
       key[i] = k;
       if (idx) idx[i] = (uint32_t)i;
-      if (hist && ok) atomicAdd(hist + (k >> hshift), 1u);
-      const uint64_t sid = id ? id[i] : 0;
-      idacc |= sid ^ id0;
       if (rec) {
         SrcRec r;
         r.ra = a;
         r.dec = d;
-        r.id = sid;
+        r.id = id[i];
         r.pad = 0;
         rec[i] = r;
       }
@@ -106,25 +96,18 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
       }
     }
   }
-  if (iddiff) {
-    for (int o = 16; o > 0; o >>= 1) idacc |= __shfl_down_sync(0xffffffffu, idacc, o);
-    if ((threadIdx.x & 31) == 0 && idacc) atomicOr(iddiff, idacc);
-  }
 }
 
 // Binary64 ang2pix of the queued sources.
 __global__ void k_prep_fallback(const double* __restrict__ ra, const double* __restrict__ dec,
                                 int order, const uint32_t* __restrict__ slow,
                                 const unsigned long long* __restrict__ nslow,
-                                uint32_t* __restrict__ key, uint32_t* __restrict__ hist,
-                                int hshift) {
+                                uint32_t* __restrict__ key) {
   uint64_t ns = *nslow;
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns;
        q += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t i = slow[q];
-    uint32_t k = c_ang2pix(c_norm_ra(ra[i]), dec[i], order);
-    key[i] = k;
-    if (hist) atomicAdd(hist + (k >> hshift), 1u);
+    key[i] = c_ang2pix(c_norm_ra(ra[i]), dec[i], order);
   }
 }
 
@@ -230,14 +213,24 @@ __global__ void k_payload64(const SrcRec* __restrict__ rec, const uint32_t* __re
 
 // Sorted payload of the guard form: FP32 unit vectors with a known error
 // bound, in entry order.
+// (iddiff, when given, receives the OR of id ^ id of source 0 over all
+// entries: the bits in which the ids differ, for the output bucketing.)
 __global__ void k_payload32(const SrcRec* __restrict__ rec, const uint32_t* __restrict__ idx,
-                            uint64_t m, float4* __restrict__ v) {
+                            uint64_t m, float4* __restrict__ v,
+                            unsigned long long* __restrict__ iddiff) {
+  const uint64_t id0 = (iddiff && m) ? rec[0].id : 0;
+  unsigned long long acc = 0;
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
        e += (uint64_t)gridDim.x * blockDim.x) {
     SrcRec r = rec[idx[e]];
     float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
     if (bits_finite(r.ra) && bits_abs_le(r.dec, 90.0)) u = fp32_unitvec(r.ra, r.dec);
     v[e] = u;
+    acc |= r.id ^ id0;
+  }
+  if (iddiff) {
+    for (int o = 16; o > 0; o >>= 1) acc |= __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicOr(iddiff, acc);
   }
 }
 
