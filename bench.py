@@ -190,9 +190,9 @@ def run_hlc(args):
     pair_bytes = (mA * (4 + 16) + mB * 16 + (12 * 4 ** lt + 1) * 4
                   + 8 * (last["matches"] + last["band_candidates"]))
     pair_gbs = pair_bytes / (stage_ms["ms_pair"] / 1e3) / 1e9
-    tr = TRAFFIC.get("k_pair<1,0,0>")
+    tr = TRAFFIC.get("k_pair<1,0,0,1>")
     traffic = tr["bytes_per_launch"] if tr and tr["sources"] == _kernel_sources_sha() else None
-    roofline = {"kernel": "k_pair<FP32,complete> (candidates + pair test)",
+    roofline = {"kernel": "k_pair<1,0,0,1> (FP32 complete form: candidates + pair test)",
                 "bound": "hbm", "achieved": round(pair_gbs, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(pair_gbs / peak, 4), "traffic": traffic,
                 "peak_source": (peak_kind + " (MEASURED_PEAKS.json hbm_gbs)")
@@ -270,7 +270,11 @@ def run_hlc(args):
 
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture, with
 # the digest of the kernel sources it was taken on; a changed source voids it.
-TRAFFIC = {}
+TRAFFIC = {
+    # ncu --set full, full sky 10M x 10M (profiles/pair_fullsky_10Mx10M_fp32.md):
+    # 414,539,008 B read + 41,545,728 B written
+    "k_pair<1,0,0,1>": {"bytes_per_launch": 456084736, "sources": "4c75e933c3edc6a7"},
+}
 
 _KERNEL_SOURCES = ("match.cuh", "canon.cuh", "index.cuh", "learned.cuh", "common.cuh",
                    "fp32.cuh", "fastpix.cuh")
