@@ -271,7 +271,7 @@ def run_hlc(args):
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture, with
 # the digest of the kernel sources it was taken on; a changed source voids it.
 TRAFFIC = {
-    # ncu --set full, full sky 10M x 10M (profiles/pair_fullsky_10Mx10M_fp32.md):
+    # ncu --set full of the pair test in the full-sky 10M x 10M step:
     # 414,539,008 B read + 41,545,728 B written
     "k_pair<1,0,0,1>": {"bytes_per_launch": 456084736, "sources": "4c75e933c3edc6a7"},
 }
