@@ -508,7 +508,10 @@ def run_batched(args):
                                                        total)},
           matches=nb_, per_job={"ms": ms_j, "sources_per_s": total / (ms_j / 1e3), "matches": nj_},
           speedup_vs_per_job=ms_j / ms_b, pair_tests=st_b["pair_tests"],
-          gpu_launches=st_b["kernel_launches"])
+          gpu_launches=st_b["kernel_launches"], tile_items=st_b["tile_items"],
+          tile_entries_a=st_b["tile_entries_a"], band_candidates=st_b["band_candidates"],
+          stages_ms={k: st_b[k] for k in ("ms_prep", "ms_sort", "ms_index", "ms_pair",
+                                          "ms_recheck", "ms_output")})
 
 
 def run_streamed(args):

@@ -255,16 +255,25 @@ struct BPairArgs {
   const float4 *a32, *b32;
   uint32_t sparse_cell;
   unsigned long long* work;  // chunk counter
+  const uint8_t* tiled;      // A entries taken by the dense-cell kernel, or null
 };
 
 // Persistent pair test: each warp takes chunks of 32 A entries from an atomic
-// work counter until all entries of all jobs are done.
+// work counter until all entries of all jobs are done.  As in k_pair, a lane
+// in a sparse region reads the (at most 4) table cells covering its fine 3x3
+// block whole, rows are staged per warp in shared memory, and lanes whose A
+// entry the dense-cell kernel takes (tiled) stay idle.
 template <bool FP32>
 __global__ void __launch_bounds__(kThreads) k_bpair(const BPairArgs pa, PairSink sink) {
   const uint64_t nchunks = (pa.mA + 31) / 32;
   const int lane = threadIdx.x & 31;
   const uint64_t cmask = (1ull << pa.cell_bits) - 1;
   unsigned long long ntest = 0;
+  constexpr int kRowCap = 256, kBandCap = FP32 ? 128 : 32;
+  __shared__ uint2 s_rows[kThreads / 32][kRowCap];
+  __shared__ uint2 s_band[kThreads / 32][kBandCap];
+  WarpRows<kRowCap> wrows{s_rows[threadIdx.x >> 5]};
+  WarpRows<kBandCap> wband{s_band[threadIdx.x >> 5]};
   for (;;) {
     unsigned long long chunk = 0;
     if (lane == 0) chunk = atomicAdd(pa.work, 1ull);
@@ -272,6 +281,7 @@ __global__ void __launch_bounds__(kThreads) k_bpair(const BPairArgs pa, PairSink
     if (chunk >= nchunks) break;
     uint64_t k = chunk * 32 + lane;
     bool live = k < pa.mA;
+    if (live && pa.tiled && pa.tiled[k]) live = false;
     uint32_t j = 0, cell = 0;
     JobTab J = {0, 0, 0u, 0u, 0ull, 0.0, 0.f, 0.f};
     if (live) {
@@ -290,22 +300,24 @@ __global__ void __launch_bounds__(kThreads) k_bpair(const BPairArgs pa, PairSink
       }
     }
     uint32_t nb[9];
-    int m = 0;
+#pragma unroll
+    for (int s = 0; s < 9; ++s) nb[s] = kNoCell;
     bool coarse = false;
     if (live) {
       uint32_t Q = cell >> (2 * J.tk);
       if (FP32 && J.tk > 0 && Q >= J.tbase && Q - J.tbase + 1 < J.tsize) {
         uint64_t slot = J.toff + (Q - J.tbase);
-        coarse = __ldg(pa.table + slot + 1) - __ldg(pa.table + slot) <= pa.sparse_cell;
+        if (__ldg(pa.table + slot + 1) - __ldg(pa.table + slot) <= pa.sparse_cell)
+          coarse = parent_cover4(cell, J.L, J.tk, nb);
       }
-      m = coarse ? cell_neighbourhood(Q, J.L - J.tk, nb) : cell_neighbourhood(cell, J.L, nb);
+      if (!coarse) cell_neighbourhood9(cell, J.L, nb);
     }
     uint32_t rb[9], re[9];
     uint32_t total = 0;
 #pragma unroll
     for (int s = 0; s < 9; ++s) {
       uint2 r = make_uint2(0u, 0u);
-      if (s < m) {
+      if (nb[s] != kNoCell) {
         if (coarse) {
           uint32_t c = nb[s];
           if (c >= J.tbase && c - J.tbase + 1 < J.tsize) {
@@ -323,40 +335,66 @@ __global__ void __launch_bounds__(kThreads) k_bpair(const BPairArgs pa, PairSink
     ntest += total;
     const uint32_t maxT = __reduce_max_sync(0xffffffffu, total);
     uint32_t cur = rb[0], end = re[0];
-    for (uint32_t t = 0; t < maxT; ++t) {
-      bool act = t < total;
-      uint32_t jb = 0;
-      bool hit = false, band = false;
-      if (act) {
-        while (cur >= end) {
+    constexpr int U = 4;
+    for (uint32_t t = 0; t < maxT; t += U) {
+      uint32_t jj[U];
+      bool act[U];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            rb[i] = rb[i + 1];
-            re[i] = re[i + 1];
+      for (int u = 0; u < U; ++u) {
+        act[u] = t + u < total;
+        jj[u] = 0;
+        if (act[u]) {
+          while (cur >= end) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              rb[i] = rb[i + 1];
+              re[i] = re[i + 1];
+            }
+            cur = rb[0];
+            end = re[0];
           }
-          cur = rb[0];
-          end = re[0];
+          jj[u] = cur++;
         }
-        jb = cur++;
-        if (FP32) {
-          float4 b = __ldg(pa.b32 + jb);
-          float dx = a4.x - b.x, dy = a4.y - b.y, dz = a4.z - b.z;
+      }
+      bool hit[U], band[U];
+      bool anyv = false;
+      if (FP32) {
+        float4 bb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) bb[u] = act[u] ? __ldg(pa.b32 + jj[u]) : a4;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          float dx = a4.x - bb[u].x, dy = a4.y - bb[u].y, dz = a4.z - bb[u].z;
           float s2 = dx * dx;
           s2 = fmaf(dy, dy, s2);
           s2 = fmaf(dz, dz, s2);
-          hit = s2 <= J.lo32;
-          band = !hit && s2 <= J.hi32;
-        } else {
-          hit = c_chord2(ax, ay, az, pa.bxv[jb], pa.byv[jb], pa.bzv[jb]) <= J.C;
+          hit[u] = act[u] && s2 <= J.lo32;
+          band[u] = act[u] && !hit[u] && s2 <= J.hi32;
+          anyv |= hit[u] || band[u];
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          hit[u] = act[u] &&
+                   c_chord2(ax, ay, az, pa.bxv[jj[u]], pa.byv[jj[u]], pa.bzv[jj[u]]) <= J.C;
+          band[u] = false;
+          anyv |= hit[u];
         }
       }
-      if (__any_sync(0xffffffffu, hit || band)) {
-        warp_emit(hit, (uint32_t)k, jb, sink.rows, sink.count, sink.cap, sink.err);
-        if (FP32)
-          warp_emit(band, (uint32_t)k, jb, sink.band, sink.band_count, sink.band_cap, sink.err);
+      if (__any_sync(0xffffffffu, anyv)) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          wrows.add(hit[u], (uint32_t)k, jj[u]);
+          if (FP32) wband.add(band[u], (uint32_t)k, jj[u]);
+        }
+        if (wrows.fill > kRowCap - 32 * U) wrows.flush(sink.rows, sink.count, sink.cap, sink.err);
+        if (FP32 && wband.fill > kBandCap - 32 * U)
+          wband.flush(sink.band, sink.band_count, sink.band_cap, sink.err);
       }
     }
   }
+  wrows.flush(sink.rows, sink.count, sink.cap, sink.err);
+  if (FP32) wband.flush(sink.band, sink.band_count, sink.band_cap, sink.err);
   for (int o = 16; o > 0; o >>= 1) ntest += __shfl_down_sync(0xffffffffu, ntest, o);
   if (lane == 0 && ntest) atomicAdd(sink.tests, ntest);
 }

@@ -1081,7 +1081,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
 #undef HLC_PAIR
       HLC_LAUNCH_CHECK();
       if (P->table_buckets && A.tiled) {
-        TileArgs ta;
+        TileArgs ta{};
         ta.cell = A.tile_cell;
         ta.start = A.tile_start;
         ta.dpos = A.tile_dpos;
@@ -1095,9 +1095,9 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
         ta.hi32 = P->hi32;
         ta.sparse_cell = P->sparse_cell;
         const int smem = kTileCap * 16;
-        HLC_CUDA(cudaFuncSetAttribute(k_pair_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      smem));
-        k_pair_tile<<<148 * 5, kTileThreads, smem, st>>>(ta, sink);
+        HLC_CUDA(cudaFuncSetAttribute(k_pair_tile<false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_pair_tile<false><<<148 * 5, kTileThreads, smem, st>>>(ta, sink);
         HLC_LAUNCH_CHECK();
       }
     }
@@ -1527,6 +1527,32 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
                                                                       P->ctr + C_IDDIFF);
     ++g_launches;
   }
+  // dense cells of every job for the tile kernel: runs of equal (job, cell)
+  // keys among the sorted A entries (FP32 form)
+  if (rc == HLC_OK && NA > 1 && NB && P->p.precision == HLC_FP32_GUARD) {
+    uint32_t* flag = ar.get_n<uint32_t>(NA + 1);
+    uint32_t* off = ar.get_n<uint32_t>(NA + 1);
+    void* scr = ar.get(scan_scratch_bytes(NA));
+    P->A.tile_start = ar.get_n<uint32_t>(NA + 2);
+    P->A.tile_n = ar.get_n<unsigned long long>(4);
+    P->A.tiled = ar.get_n<uint8_t>(NA + 1);
+    if (!flag || !off || !scr || !P->A.tile_start || !P->A.tile_n || !P->A.tiled)
+      return fail(HLC_ENOMEM);
+    cudaMemsetAsync(P->A.tile_n, 0, 32, st);
+    cudaMemsetAsync(P->A.tiled, 0, NA + 1, st);
+    k_run_flags64<<<grid_for(NA, kThreads), kThreads, 0, st>>>(keys[0], NA, flag);
+    ++g_launches;
+    rc = scan_exclusive<uint32_t>(flag, off, NA, P->A.tile_n, scr, P->dev_err, st);
+    if (rc) return fail(rc);
+    k_run_starts<<<grid_for(NA, kThreads), kThreads, 0, st>>>(flag, off, NA, P->A.tile_n,
+                                                               P->A.tile_start);
+    k_mark_tiled<<<grid_for(NA, kThreads, 148u * 8u), kThreads, 0, st>>>(
+        P->A.tile_start, nullptr, P->A.tile_n, P->A.tiled);
+    g_launches += 2;
+    ar.drop(flag);
+    ar.drop(off);
+    ar.drop(scr);
+  }
   unsigned long long hc[C_N] = {0};
   if (rc == HLC_OK &&
       cudaMemcpyAsync(hc, P->ctr, sizeof(hc), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -1563,6 +1589,14 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
   P->stats.ms_prep = t[0];
   P->stats.ms_sort = t[1];
   P->stats.ms_index = t[2];
+  if (P->A.tile_n) {
+    unsigned long long tn[4] = {0, 0, 0, 0};
+    if (cudaMemcpyAsync(tn, P->A.tile_n, 32, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return fail(HLC_ECUDA);
+    P->stats.tile_items = tn[1];
+    P->stats.tile_entries_a = tn[2];
+  }
   P->plan_launches = g_launches.load() - P->launches0;
   *out = P;
   return HLC_OK;
@@ -1586,6 +1620,9 @@ static int batched_pair_graph(hlc_plan_t* P, uint2* rows, uint64_t cap, uint2* b
   }
   cudaStream_t cs;
   HLC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const int tile_smem = kTileCap * 16;
+  HLC_CUDA(cudaFuncSetAttribute(k_pair_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tile_smem));
   cudaGraph_t g;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
@@ -1605,11 +1642,28 @@ static int batched_pair_graph(hlc_plan_t* P, uint2* rows, uint64_t cap, uint2* b
     pa.b32 = P->B.v32;
     pa.sparse_cell = P->sparse_cell;
     pa.work = P->ctr + C_SCRATCH;
+    pa.tiled = P->A.tiled;
     if (P->A.m && P->B.m) {
       if (fp32)
         k_bpair<true><<<148 * 8, kThreads, 0, cs>>>(pa, sink);
       else
         k_bpair<false><<<148 * 8, kThreads, 0, cs>>>(pa, sink);
+      if (fp32 && P->A.tiled) {
+        TileArgs ta{};
+        ta.start = P->A.tile_start;
+        ta.dpos = nullptr;
+        ta.nitems = P->A.tile_n;
+        ta.work = (unsigned*)(P->ctr + C_WORK);
+        ta.a32 = P->A.v32;
+        ta.b32 = P->B.v32;
+        ta.sparse_cell = P->sparse_cell;
+        ta.keyA64 = P->keyA64;
+        ta.keyB64 = P->keyB64;
+        ta.btable = P->btable;
+        ta.jobs = P->jobs_d;
+        ta.cell_bits = P->cell_bits;
+        k_pair_tile<true><<<148 * 5, kTileThreads, tile_smem, cs>>>(ta, sink);
+      }
     }
     e = cudaStreamEndCapture(cs, &g);
   }

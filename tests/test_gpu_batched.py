@@ -66,3 +66,21 @@ def test_empty_jobs():
     jobs[1].A = e
     jobs[4].B = e
     _check(jobs, hlc.HLC_FP32_GUARD)
+
+
+def test_dense_jobs_use_the_tile_kernel():
+    # small cones crowded with A sources and a radius that caps the order: the
+    # A cells hold far more than 32 sources, so the dense-cell kernel (B staged
+    # in shared memory) takes them; rows still equal the oracle job by job
+    jobs = []
+    base = synth.cone_jobs(n_jobs=6, nmin=2000, nmax=20000, seed=11)
+    for i, jb in enumerate(base):
+        ra, dec = synth.cone_uniform(100 + i, 1, 20000, jb.ra_c, jb.dec_c, 0.02)
+        A = synth.Catalogue(ra, dec, synth.ids(100 + i, 1, 20000))
+        ra, dec = synth.cone_uniform(200 + i, 2, 3000, jb.ra_c, jb.dec_c, 0.02)
+        B = synth.Catalogue(ra, dec, synth.ids(200 + i, 2, 3000))
+        jobs.append(synth.ConeJob(A, B, 4.0 + 0.1 * i, 0, jb.ra_c, jb.dec_c, 0.02))
+    jobs += list(synth.cone_jobs(n_jobs=6, nmin=100, nmax=3000, seed=12))
+    assert _check(jobs, hlc.HLC_FP32_GUARD) > 1000
+    *_, st = _run(jobs, hlc.HLC_FP32_GUARD)
+    assert st["tile_items"] > 0 and st["tile_entries_a"] >= 32 * st["tile_items"]
