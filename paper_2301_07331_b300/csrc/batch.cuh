@@ -141,20 +141,51 @@ __global__ void k_bpayload(const JobDev* __restrict__ jobs, const uint64_t* __re
 // Autotuner inputs, per job: the sum of the B unit vectors (FP32) and, in a
 // second pass, the smallest cosine between a B source and the job's mean
 // direction -- the spherical cap the job's B catalogue occupies.
+// Sum (or maximum) over the lanes of a warp that share a job, entries of a
+// job being contiguous: after the loop the first lane of each run of equal
+// jobs holds the run's total, so a warp issues one atomic per job it touches.
+template <bool MAX>
+__device__ __forceinline__ float seg_reduce(float v, uint32_t j, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_down_sync(0xffffffffu, v, o);
+    const uint32_t jo = __shfl_down_sync(0xffffffffu, j, o);
+    if (lane + o < 32 && jo == j) v = MAX ? fmaxf(v, y) : v + y;
+  }
+  return v;
+}
+
+__device__ __forceinline__ bool seg_head(uint32_t j, int lane) {
+  const uint32_t jp = __shfl_up_sync(0xffffffffu, j, 1);
+  return lane == 0 || jp != j;
+}
+
 __global__ void k_bjob_mean(const JobDev* __restrict__ jobs, const uint64_t* __restrict__ off,
                             uint32_t njobs, uint64_t total, float* __restrict__ acc) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t j = job_of(off, njobs, i);
-    const JobDev& J = jobs[j];
-    uint64_t l = i - J.off[1];
-    double a = J.ra[1][l], d = J.dec[1][l];
-    if (!(bits_finite(a) && bits_abs_le(d, 90.0))) continue;
-    if (!bits_in_ra_range(a)) a = c_norm_ra(a);
-    float4 u = fp32_unitvec(a, d);
-    atomicAdd(acc + 3 * j, u.x);
-    atomicAdd(acc + 3 * j + 1, u.y);
-    atomicAdd(acc + 3 * j + 2, u.z);
+  const int lane = threadIdx.x & 31;
+  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < total;
+       i0 += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = i0 + threadIdx.x;
+    uint32_t j = 0xFFFFFFFFu;
+    float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < total) {
+      j = job_of(off, njobs, i);
+      const JobDev& J = jobs[j];
+      uint64_t l = i - J.off[1];
+      double a = J.ra[1][l], d = J.dec[1][l];
+      if (bits_finite(a) && bits_abs_le(d, 90.0)) {
+        if (!bits_in_ra_range(a)) a = c_norm_ra(a);
+        u = fp32_unitvec(a, d);
+      }
+    }
+    const float sx = seg_reduce<false>(u.x, j, lane);
+    const float sy = seg_reduce<false>(u.y, j, lane);
+    const float sz = seg_reduce<false>(u.z, j, lane);
+    if (j != 0xFFFFFFFFu && seg_head(j, lane)) {
+      atomicAdd(acc + 3 * j, sx);
+      atomicAdd(acc + 3 * j + 1, sy);
+      atomicAdd(acc + 3 * j + 2, sz);
+    }
   }
 }
 
@@ -163,32 +194,66 @@ __global__ void k_bjob_mean(const JobDev* __restrict__ jobs, const uint64_t* __r
 __global__ void k_bjob_cap(const JobDev* __restrict__ jobs, const uint64_t* __restrict__ off,
                            uint32_t njobs, uint64_t total, const float* __restrict__ dir,
                            unsigned int* __restrict__ cap) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t j = job_of(off, njobs, i);
-    const JobDev& J = jobs[j];
-    uint64_t l = i - J.off[1];
-    double a = J.ra[1][l], d = J.dec[1][l];
-    if (!(bits_finite(a) && bits_abs_le(d, 90.0))) continue;
-    if (!bits_in_ra_range(a)) a = c_norm_ra(a);
-    float4 u = fp32_unitvec(a, d);
-    float c = u.x * dir[3 * j] + u.y * dir[3 * j + 1] + u.z * dir[3 * j + 2];
-    float om = fmaxf(1.0f - c, 0.0f);
-    atomicMax(cap + j, __float_as_uint(om));
+  const int lane = threadIdx.x & 31;
+  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < total;
+       i0 += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = i0 + threadIdx.x;
+    uint32_t j = 0xFFFFFFFFu;
+    float om = 0.0f;
+    if (i < total) {
+      j = job_of(off, njobs, i);
+      const JobDev& J = jobs[j];
+      uint64_t l = i - J.off[1];
+      double a = J.ra[1][l], d = J.dec[1][l];
+      if (bits_finite(a) && bits_abs_le(d, 90.0)) {
+        if (!bits_in_ra_range(a)) a = c_norm_ra(a);
+        float4 u = fp32_unitvec(a, d);
+        float c = u.x * dir[3 * j] + u.y * dir[3 * j + 1] + u.z * dir[3 * j + 2];
+        om = fmaxf(1.0f - c, 0.0f);
+      }
+    }
+    const float m = seg_reduce<true>(om, j, lane);
+    if (j != 0xFFFFFFFFu && seg_head(j, lane)) atomicMax(cap + j, __float_as_uint(m));
+  }
+}
+
+// First and last composite key of every job's sorted B entries.
+__global__ void k_job_first_last(const uint64_t* __restrict__ key,
+                                 const uint64_t* __restrict__ off, uint32_t njobs,
+                                 uint64_t* __restrict__ fl) {
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < njobs;
+       j += gridDim.x * blockDim.x) {
+    const uint64_t a = off[j], b = off[j + 1];
+    fl[2 * j] = a < b ? key[a] : 0ull;
+    fl[2 * j + 1] = a < b ? key[b - 1] : 0ull;
   }
 }
 
 // ---- per-job B offset tables -------------------------------------------------
 __global__ void k_btable_hist(const uint64_t* __restrict__ key, uint64_t m, int cell_bits,
                               const JobDev* __restrict__ jobs, uint32_t* __restrict__ counts) {
+  // keys are sorted: equal slots are contiguous, one atomic per run of lanes
   const uint64_t cmask = (1ull << cell_bits) - 1;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-       e += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t k = key[e];
-    uint32_t j = (uint32_t)(k >> cell_bits);
-    const JobDev& J = jobs[j];
-    uint32_t c = (uint32_t)((k & cmask) >> (2 * J.tk)) - J.tbase;
-    atomicAdd(counts + J.toff + c, 1u);
+  const int lane = threadIdx.x & 31;
+  for (uint64_t e0 = (uint64_t)blockIdx.x * blockDim.x; e0 < m;
+       e0 += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t e = e0 + threadIdx.x;
+    uint32_t slot = 0xFFFFFFFFu;
+    if (e < m) {
+      uint64_t k = key[e];
+      uint32_t j = (uint32_t)(k >> cell_bits);
+      const JobDev& J = jobs[j];
+      slot = (uint32_t)(J.toff + (uint32_t)((k & cmask) >> (2 * J.tk)) - J.tbase);
+    }
+    const uint32_t sp = __shfl_up_sync(0xffffffffu, slot, 1);
+    const bool head = slot != 0xFFFFFFFFu && (lane == 0 || sp != slot);
+    const unsigned hm = __ballot_sync(0xffffffffu, head);
+    const unsigned lm = __ballot_sync(0xffffffffu, slot != 0xFFFFFFFFu);
+    if (head) {
+      const unsigned later = hm & ~((2u << lane) - 1u);
+      const int end = later ? __ffs(later) - 1 : 32 - __clz(lm);
+      atomicAdd(counts + slot, (uint32_t)(end - lane));
+    }
   }
 }
 

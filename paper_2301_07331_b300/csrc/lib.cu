@@ -208,8 +208,10 @@ struct CatDev {
   uint32_t* tile_cell = nullptr;
   uint32_t* tile_start = nullptr;
   uint32_t* tile_dpos = nullptr;
-  unsigned long long* tile_n = nullptr;  // device: number of items
+  unsigned long long* tile_n = nullptr;  // device: runs, items taken, their entries
   uint8_t* tiled = nullptr;              // 1 for A entries the tile kernel takes
+  TileItem* tile_items = nullptr;        // prepared items (B ranges found)
+  unsigned long long* tile_nprep = nullptr;
 };
 
 // Pinned host memory of streamed plans (the pass-1 runs, the groups' result
@@ -538,6 +540,26 @@ static int dense_fixup(hlc_plan_t* P, CatDev& X, const uint32_t* T, int shift, b
                                                                        X.tile_n, X.tiled);
   HLC_LAUNCH_CHECK();
   X.tile_dpos = dpos;
+  {  // the B ranges of every item, ahead of the pair test
+    const uint64_t cap = nd / kTileMinA + 1;
+    HLC_ALLOC(ar, X.tile_items, TileItem, cap);
+    HLC_ALLOC(ar, X.tile_nprep, unsigned long long, 1);
+    HLC_CUDA(cudaMemsetAsync(X.tile_nprep, 0, 8, st));
+    TileArgs ta{};
+    ta.cell = X.tile_cell;
+    ta.start = X.tile_start;
+    ta.dpos = dpos;
+    ta.nitems = X.tile_n;
+    ta.lo32 = P->lo32;
+    ta.hi32 = P->hi32;
+    ta.sparse_cell = P->sparse_cell;
+    ta.bix.keys = P->B.key;
+    ta.bix.table = P->B.table;
+    ta.bix.shift = P->B.table_shift;
+    ta.order = P->join_level;
+    k_tile_items<false><<<148u * 16u, 256, 0, st>>>(ta, X.tile_items, X.tile_nprep, cap);
+    HLC_LAUNCH_CHECK();
+  }
   ar.drop(cell_of);
   ar.drop(rscr);
   ar.drop(dkey);
@@ -1082,10 +1104,8 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
       HLC_LAUNCH_CHECK();
       if (P->table_buckets && A.tiled) {
         TileArgs ta{};
-        ta.cell = A.tile_cell;
-        ta.start = A.tile_start;
-        ta.dpos = A.tile_dpos;
-        ta.nitems = A.tile_n;
+        ta.items = A.tile_items;
+        ta.nitems = A.tile_nprep;
         ta.work = (unsigned*)(P->ctr + C_WORK);
         ta.a32 = A.v32;
         ta.b32 = B.v32;
@@ -1094,10 +1114,10 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
         ta.lo32 = P->lo32;
         ta.hi32 = P->hi32;
         ta.sparse_cell = P->sparse_cell;
-        const int smem = kTileCap * 16;
-        HLC_CUDA(cudaFuncSetAttribute(k_pair_tile<false>,
+        const int smem = 2 * kTileCap * 16;
+        HLC_CUDA(cudaFuncSetAttribute(k_pair_tile,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        k_pair_tile<false><<<148 * 5, kTileThreads, smem, st>>>(ta, sink);
+        k_pair_tile<<<148 * 3, kTileThreads + 32, smem, st>>>(ta, sink);
         HLC_LAUNCH_CHECK();
       }
     }
@@ -1483,11 +1503,8 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
     // gather the first and last composite key of every job
     uint64_t* fl = ar.get_n<uint64_t>(2 * njobs + 2);
     if (!fl) return fail(HLC_ENOMEM);
-    for (uint32_t j = 0; j < njobs; ++j) {
-      if (!B[j].n) continue;
-      cudaMemcpyAsync(fl + 2 * j, keys[1] + offB[j], 8, cudaMemcpyDeviceToDevice, st);
-      cudaMemcpyAsync(fl + 2 * j + 1, keys[1] + offB[j + 1] - 1, 8, cudaMemcpyDeviceToDevice, st);
-    }
+    k_job_first_last<<<grid_for(njobs, kThreads), kThreads, 0, st>>>(keys[1], offd[1], njobs, fl);
+    ++g_launches;
     std::vector<uint64_t> h(2 * njobs, 0);
     if (cudaMemcpyAsync(h.data(), fl, 2 * njobs * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
@@ -1549,6 +1566,21 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
     k_mark_tiled<<<grid_for(NA, kThreads, 148u * 8u), kThreads, 0, st>>>(
         P->A.tile_start, nullptr, P->A.tile_n, P->A.tiled);
     g_launches += 2;
+    const uint64_t cap = NA / kTileMinA + 1;
+    P->A.tile_items = ar.get_n<TileItem>(cap);
+    P->A.tile_nprep = ar.get_n<unsigned long long>(1);
+    if (!P->A.tile_items || !P->A.tile_nprep) return fail(HLC_ENOMEM);
+    cudaMemsetAsync(P->A.tile_nprep, 0, 8, st);
+    TileArgs tp{};
+    tp.start = P->A.tile_start;
+    tp.nitems = P->A.tile_n;
+    tp.keyA64 = keys[0];
+    tp.keyB64 = keys[1];
+    tp.btable = P->btable;
+    tp.jobs = P->jobs_d;
+    tp.cell_bits = P->cell_bits;
+    k_tile_items<true><<<148u * 16u, 256, 0, st>>>(tp, P->A.tile_items, P->A.tile_nprep, cap);
+    ++g_launches;
     ar.drop(flag);
     ar.drop(off);
     ar.drop(scr);
@@ -1620,8 +1652,8 @@ static int batched_pair_graph(hlc_plan_t* P, uint2* rows, uint64_t cap, uint2* b
   }
   cudaStream_t cs;
   HLC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  const int tile_smem = kTileCap * 16;
-  HLC_CUDA(cudaFuncSetAttribute(k_pair_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const int tile_smem = 2 * kTileCap * 16;
+  HLC_CUDA(cudaFuncSetAttribute(k_pair_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tile_smem));
   cudaGraph_t g;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
@@ -1650,9 +1682,8 @@ static int batched_pair_graph(hlc_plan_t* P, uint2* rows, uint64_t cap, uint2* b
         k_bpair<false><<<148 * 8, kThreads, 0, cs>>>(pa, sink);
       if (fp32 && P->A.tiled) {
         TileArgs ta{};
-        ta.start = P->A.tile_start;
-        ta.dpos = nullptr;
-        ta.nitems = P->A.tile_n;
+        ta.items = P->A.tile_items;
+        ta.nitems = P->A.tile_nprep;
         ta.work = (unsigned*)(P->ctr + C_WORK);
         ta.a32 = P->A.v32;
         ta.b32 = P->B.v32;
@@ -1662,7 +1693,7 @@ static int batched_pair_graph(hlc_plan_t* P, uint2* rows, uint64_t cap, uint2* b
         ta.btable = P->btable;
         ta.jobs = P->jobs_d;
         ta.cell_bits = P->cell_bits;
-        k_pair_tile<true><<<148 * 5, kTileThreads, tile_smem, cs>>>(ta, sink);
+        k_pair_tile<<<148 * 3, kTileThreads + 32, tile_smem, cs>>>(ta, sink);
       }
     }
     e = cudaStreamEndCapture(cs, &g);

@@ -6,25 +6,31 @@
 // Work items are fine cells of A holding at least kTileMinA entries (in the
 // single form: cells that lie in a dense table cell of B, where the A entries
 // were put in fine order; in the batched form: every such cell of every job,
-// A being sorted by (job, cell)).  For an item the CTA gathers the B ranges of
-// the cell and its 8 neighbours (single form: a sparse neighbour table cell
-// contributes its whole range, once), copies them round by round into shared
-// memory with cp.async.bulk on one mbarrier, and each warp takes a share of
-// the staged B vectors while its lanes hold KA A sources each: one broadcast
-// shared load per B vector and KA FP32 squared-chord tests.  Rounds are
-// padded to whole groups with vectors far from everything and dead A lanes
-// hold such a vector too, so the inner loop has no bounds tests.  A lane
-// records its candidates of a group in a bit mask; the warp walks them (a
-// ballot per step) only when one lane has any.
+// A being sorted by (job, cell)).  The CTA is warp-specialised.  Its producer
+// warp takes items from an atomic counter, finds the B ranges of the cell and
+// its 8 neighbours (single form: a sparse neighbour table cell contributes its
+// whole range, once), writes a round descriptor and copies the round's B
+// vectors into one of two stage buffers with cp.async.bulk (the TMA engine's
+// bulk mode: contiguous 16-byte vectors need no tensor map) on the buffer's
+// "full" mbarrier.  Eight consumer warps each take a share of a staged round
+// while their lanes hold KA A sources each: one broadcast shared load per B
+// vector and KA FP32 squared-chord tests; then they arrive on the buffer's
+// "empty" mbarrier.  The producer's dependent lookups for the next round thus
+// overlap the consumers' tests of the current one.  Rounds are padded to whole
+// groups with vectors far from everything and dead A lanes hold such a vector
+// too, so the inner loop has no bounds tests.  A lane records its candidates
+// of a group in a bit mask; the warp walks them (a ballot per step) only when
+// one lane has any.
 //
 // Tile shape per cell (the density rule): KA, the A sources per lane, is the
 // smallest of 1, 2, 4 that covers the cell's A sources in one pass of the 32
 // lanes (4 beyond 64 sources), which keeps lanes busy on small cells and
-// amortises each shared load over more tests on large ones; the staged round
+// amortises each shared load over more tests on large ones; a staged round
 // is min(kTileCap, the neighbourhood's B count).
 //
-// Each wait on the mbarrier is bounded: on time-out the kernel flags
-// DERR_TIMEOUT, waits (bounded) once more for its own copies and returns.
+// Every mbarrier wait is bounded: on time-out the kernel flags DERR_TIMEOUT,
+// the producer waits (bounded) once more for its last copies, and all warps
+// return.
 #pragma once
 
 #include "batch.cuh"
@@ -35,14 +41,16 @@
 
 namespace hlc {
 
-constexpr int kTileThreads = 256;
+constexpr int kTileThreads = 256;                   // consumer threads (+1 producer warp)
 constexpr int kTileWarps = kTileThreads / 32;
-constexpr int kTileCap = 2048;                      // B vectors per round (32 KB)
+constexpr int kTileCap = 1536;                      // B vectors per stage buffer (24 KB)
 constexpr uint32_t kTileMinA = 32;                  // smaller cells stay with the lane kernels
 constexpr int kTileGroup = 8;                       // B vectors per any-vote
 constexpr int kTileRowCap = 128, kTileBandCap = 64; // staged rows per warp
 constexpr long long kTileSpin = 1ll << 24;
 constexpr float kFarA = 1e30f, kFarB = -1e30f;      // padding: never within any radius
+
+struct TileItem;
 
 struct TileArgs {
   const uint32_t* cell;      // (single) item cells (fine ids)
@@ -57,6 +65,8 @@ struct TileArgs {
   // single form: B's offset table over table cells
   CellIndex bix;
   int order;
+  // the pair kernel: items prepared by k_tile_items
+  const TileItem* items;
   // batched form: composite (job, cell) keys and per-job tables
   const uint64_t* keyA64;
   const uint64_t* keyB64;
@@ -201,157 +211,255 @@ __device__ __forceinline__ void tile_round(const float4* __restrict__ sB, uint32
   }
 }
 
+// One dense A cell with the B ranges of its neighbourhood, found ahead of
+// the pair test by a warp per cell (the lookups are dependent loads; run apart
+// from the test, they overlap across the whole GPU).
+struct TileItem {
+  uint32_t a0, na;
+  float lo32, hi32;
+  uint32_t rb[9], off[10];  // B range start per slot; exclusive prefix of lengths
+  uint32_t pad[2];
+};
+
 template <bool BATCH>
-__global__ void __launch_bounds__(kTileThreads) k_pair_tile(const TileArgs ta, PairSink sink) {
-  extern __shared__ __align__(128) unsigned char tile_smem[];
-  float4* sB = reinterpret_cast<float4*>(tile_smem);
-  __shared__ uint2 s_rows[kTileWarps][kTileRowCap];
-  __shared__ uint2 s_band[kTileWarps][kTileBandCap];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ uint32_t s_rb[9], s_off[10];
-  __shared__ unsigned s_item;
-  __shared__ int s_abort;
-  WarpRows<kTileRowCap> wrows{s_rows[threadIdx.x >> 5]};
-  WarpRows<kTileBandCap> wband{s_band[threadIdx.x >> 5]};
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int t = threadIdx.x;
-  unsigned long long ntest = 0;
-  if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_abort = 0;
-  }
-  __syncthreads();
-  uint32_t phase = 0;
+__global__ void k_tile_items(const TileArgs ta, TileItem* __restrict__ out,
+                             unsigned long long* __restrict__ nout, uint64_t cap) {
+  const int lane = threadIdx.x & 31;
   const uint64_t nitems = *ta.nitems;
   const uint64_t cmask = BATCH ? (1ull << ta.cell_bits) - 1 : 0;
-  for (;;) {
-    if (t == 0) s_item = atomicAdd(ta.work, 1u);
-    __syncthreads();
-    const unsigned item = s_item;
-    if (item >= nitems || s_abort) break;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t item = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+       item < nitems; item += warps) {
     const uint32_t st0 = ta.start[item], st1 = ta.start[item + 1];
     const uint32_t na = st1 - st0;
-    if (na >= kTileMinA) {
-      const uint32_t a0 = BATCH ? st0 : ta.dpos[st0];
-      uint32_t cell, order, job = 0;
-      float lo32 = ta.lo32, hi32 = ta.hi32;
-      JobTab J = {0, 0, 0u, 0u, 0ull, 0.0, 0.f, 0.f};
-      if (BATCH) {
-        const uint64_t key = ta.keyA64[a0];
-        job = (uint32_t)(key >> ta.cell_bits);
-        cell = (uint32_t)(key & cmask);
-        J = load_job(ta.jobs, job);
-        order = (uint32_t)J.L;
-        lo32 = J.lo32;
-        hi32 = J.hi32;
-      } else {
-        cell = ta.cell[item];
-        order = (uint32_t)ta.order;
-      }
-      // B ranges of the cell and its neighbours (threads 0..8)
-      if (t < 32) {
-        uint32_t nb[9];
-        cell_neighbourhood9(cell, (int)order, nb);
-        uint32_t rb = 0, len = 0;
-        if (t < 9) {
-          uint32_t c = nb[0];
+    if (na < kTileMinA) continue;
+    const uint32_t a0 = BATCH ? st0 : ta.dpos[st0];
+    uint32_t cell, order, job = 0;
+    float lo32 = ta.lo32, hi32 = ta.hi32;
+    JobTab J = {0, 0, 0u, 0u, 0ull, 0.0, 0.f, 0.f};
+    if (BATCH) {
+      const uint64_t key = ta.keyA64[a0];
+      job = (uint32_t)(key >> ta.cell_bits);
+      cell = (uint32_t)(key & cmask);
+      J = load_job(ta.jobs, job);
+      order = (uint32_t)J.L;
+      lo32 = J.lo32;
+      hi32 = J.hi32;
+    } else {
+      cell = ta.cell[item];
+      order = (uint32_t)ta.order;
+    }
+    uint32_t nb[9];
+    cell_neighbourhood9(cell, (int)order, nb);
+    uint32_t rb = 0, len = 0;
+    if (lane < 9) {
+      uint32_t c = nb[0];
 #pragma unroll
-          for (int s = 1; s < 9; ++s)
-            if (t == s) c = nb[s];
-          if (c != kNoCell) {
-            if (BATCH) {
-              const uint2 r = bcell_range(ta.keyB64, ta.btable, J, job, ta.cell_bits, c);
-              rb = r.x;
-              len = r.y - r.x;
-            } else {
-              const uint32_t Q = c >> ta.bix.shift;
-              const uint32_t c0 = __ldg(ta.bix.table + Q), c1 = __ldg(ta.bix.table + Q + 1);
-              if (c1 - c0 <= ta.sparse_cell) {
-                bool seen = false;
+      for (int q = 1; q < 9; ++q)
+        if (lane == q) c = nb[q];
+      if (c != kNoCell) {
+        if (BATCH) {
+          const uint2 r = bcell_range(ta.keyB64, ta.btable, J, job, ta.cell_bits, c);
+          rb = r.x;
+          len = r.y - r.x;
+        } else {
+          const uint32_t Q = c >> ta.bix.shift;
+          const uint32_t c0 = __ldg(ta.bix.table + Q), c1 = __ldg(ta.bix.table + Q + 1);
+          if (c1 - c0 <= ta.sparse_cell) {
+            bool seen = false;
 #pragma unroll
-                for (int e = 0; e < 9; ++e)
-                  seen |= e < t && nb[e] != kNoCell && (nb[e] >> ta.bix.shift) == Q;
-                if (!seen) {
-                  rb = c0;
-                  len = c1 - c0;
-                }
-              } else {
-                const uint2 r = cell_range_in(ta.bix.keys, c0, c1, c);
-                rb = r.x;
-                len = r.y - r.x;
-              }
+            for (int e = 0; e < 9; ++e)
+              seen |= e < lane && nb[e] != kNoCell && (nb[e] >> ta.bix.shift) == Q;
+            if (!seen) {
+              rb = c0;
+              len = c1 - c0;
             }
+          } else {
+            const uint2 r = cell_range_in(ta.bix.keys, c0, c1, c);
+            rb = r.x;
+            len = r.y - r.x;
           }
         }
-        uint32_t incl = len;
-#pragma unroll
-        for (int o = 1; o < 16; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (t >= o) incl += y;
-        }
-        if (t < 9) {
-          s_rb[t] = rb;
-          s_off[t] = incl - len;
-        }
-        if (t == 8) s_off[9] = incl;
-      }
-      __syncthreads();
-      const uint32_t total = s_off[9];
-      const int ka = na <= 32 ? 1 : (na <= 64 ? 2 : 4);  // the density rule
-      for (uint32_t R0 = 0; R0 < total; R0 += kTileCap) {
-        const uint32_t nr = min((uint32_t)kTileCap, total - R0);
-        if (t == 0) {
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-                           smem_u32(&bar)),
-                       "r"(nr * 16u)
-                       : "memory");
-#pragma unroll 1
-          for (int s = 0; s < 9; ++s) {
-            // part of range s inside [R0, R0 + nr)
-            const uint32_t o0 = max(s_off[s], R0), o1 = min(s_off[s + 1], R0 + nr);
-            if (o1 > o0) {
-              const float4* src = ta.b32 + s_rb[s] + (o0 - s_off[s]);
-              asm volatile(
-                  "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
-                  "[%0], [%1], %2, [%3];" ::"r"(smem_u32(sB + (o0 - R0))),
-                  "l"(src), "r"((o1 - o0) * 16u), "r"(smem_u32(&bar))
-                  : "memory");
-            }
-          }
-        }
-        // pad the round to whole groups with vectors far from everything
-        const uint32_t nrp = (nr + kTileGroup - 1) / kTileGroup * kTileGroup;
-        if ((uint32_t)t < nrp - nr) sB[nr + t] = make_float4(kFarB, kFarB, kFarB, 0.f);
-        const bool landed = mbar_wait(&bar, phase);
-        if (__syncthreads_or(!landed)) {  // the same decision in every thread
-          if (t == 0) {
-            atomicOr(sink.err, DERR_TIMEOUT);
-            s_abort = 1;
-          }
-          if (landed == false) mbar_wait(&bar, phase);  // let the copies land before leaving
-          __syncthreads();
-          break;
-        }
-        phase ^= 1u;
-        if (ka == 1)
-          tile_round<1>(sB, nr, nrp, R0, s_rb, s_off, ta.a32, a0, na, lo32, hi32, lane, warp,
-                        wrows, wband, sink, ntest);
-        else if (ka == 2)
-          tile_round<2>(sB, nr, nrp, R0, s_rb, s_off, ta.a32, a0, na, lo32, hi32, lane, warp,
-                        wrows, wband, sink, ntest);
-        else
-          tile_round<4>(sB, nr, nrp, R0, s_rb, s_off, ta.a32, a0, na, lo32, hi32, lane, warp,
-                        wrows, wband, sink, ntest);
-        __syncthreads();  // the round's buffer is free again
       }
     }
-    __syncthreads();  // s_item, s_rb and s_off are rewritten for the next item
+    uint32_t incl = len;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 8);
+    if (total == 0) continue;
+    unsigned long long slot = 0;
+    if (lane == 0) slot = atomicAdd(nout, 1ull);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (slot >= cap) continue;  // sized for the worst case; never taken
+    TileItem& T = out[slot];
+    if (lane < 9) {
+      T.rb[lane] = rb;
+      T.off[lane] = incl - len;
+    }
+    if (lane == 8) T.off[9] = incl;
+    if (lane == 0) {
+      T.a0 = a0;
+      T.na = na;
+      T.lo32 = lo32;
+      T.hi32 = hi32;
+    }
+  }
+}
+
+struct TileDesc {  // one staged round, written by the producer warp
+  uint32_t a0, na, R0, nr, nrp;
+  float lo32, hi32;
+  uint32_t rb[9], off[10];
+  int done;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warp-specialised: warp 0 produces (takes items from the work counter, finds
+// the B ranges, writes a round descriptor and issues the bulk copies into one
+// of two stage buffers), warps 1..8 consume (test their share of the staged
+// B vectors against the item's A sources).  Full/empty mbarrier pairs hand the
+// buffers over, so the producer's dependent lookups for the next round
+// overlap the consumers' tests of the current one.
+__global__ void __launch_bounds__(kTileThreads + 32) k_pair_tile(const TileArgs ta,
+                                                                 PairSink sink) {
+  extern __shared__ __align__(128) unsigned char tile_smem[];
+  float4* sB0 = reinterpret_cast<float4*>(tile_smem);
+  __shared__ uint2 s_rows[kTileWarps][kTileRowCap];
+  __shared__ uint2 s_band[kTileWarps][kTileBandCap];
+  __shared__ __align__(8) uint64_t full[2], empty[2];
+  __shared__ TileDesc desc[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[b])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[b])),
+                   "r"(kTileWarps)
+                   : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    const uint64_t nitems = *ta.nitems;  // prepared items (k_tile_items)
+    uint32_t s = 0;  // rounds issued
+    bool ok = true;
+    for (;;) {
+      unsigned item = 0;
+      if (lane == 0) item = atomicAdd(ta.work, 1u);
+      item = __shfl_sync(0xffffffffu, item, 0);
+      if (item >= nitems) break;
+      const TileItem& T = ta.items[item];
+      const uint32_t a0 = T.a0, na = T.na;
+      const float lo32 = T.lo32, hi32 = T.hi32;
+      const uint32_t rb = lane < 9 ? T.rb[lane] : 0u;
+      const uint32_t excl = lane < 10 ? T.off[lane] : 0u;
+      const uint32_t incl = lane < 9 ? T.off[lane + 1] : 0u;
+      const uint32_t total = T.off[9];
+      for (uint32_t R0 = 0; R0 < total && ok; R0 += kTileCap) {
+        const uint32_t b = s & 1u, use = s >> 1;
+        if (!mbar_wait(&empty[b], (use & 1u) ^ 1u)) {  // the consumers freed it
+          ok = false;
+          break;
+        }
+        const uint32_t nr = min((uint32_t)kTileCap, total - R0);
+        const uint32_t nrp = (nr + kTileGroup - 1) / kTileGroup * kTileGroup;
+        float4* sB = sB0 + (size_t)b * kTileCap;
+        TileDesc& D = desc[b];
+        if (lane < 9) {
+          D.rb[lane] = rb;
+          D.off[lane] = excl;
+        }
+        if (lane == 8) D.off[9] = incl;
+        if (lane == 0) {
+          D.a0 = a0;
+          D.na = na;
+          D.R0 = R0;
+          D.nr = nr;
+          D.nrp = nrp;
+          D.lo32 = lo32;
+          D.hi32 = hi32;
+          D.done = 0;
+        }
+        // pad the round to whole groups with vectors far from everything
+        if ((uint32_t)lane < nrp - nr) sB[nr + lane] = make_float4(kFarB, kFarB, kFarB, 0.f);
+        __syncwarp();
+        if (lane == 0) {
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                           smem_u32(&full[b])),
+                       "r"(nr * 16u)
+                       : "memory");
+        }
+        // lanes 0..8 copy their range's part of the round
+        if (lane < 9) {
+          const uint32_t o0 = max(excl, R0), o1 = min(incl, R0 + nr);
+          if (o1 > o0) {
+            const float4* src = ta.b32 + rb + (o0 - excl);
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+                "[%0], [%1], %2, [%3];" ::"r"(smem_u32(sB + (o0 - R0))),
+                "l"(src), "r"((o1 - o0) * 16u), "r"(smem_u32(&full[b]))
+                : "memory");
+          }
+        }
+        ++s;
+      }
+      if (!ok) break;
+    }
+    // tell the consumers there is nothing more (or, after a time-out, let the
+    // last round's copies land first)
+    const uint32_t b = s & 1u, use = s >> 1;
+    if (ok && mbar_wait(&empty[b], (use & 1u) ^ 1u)) {
+      if (lane == 0) {
+        desc[b].done = 1;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], 0;" ::"r"(
+                         smem_u32(&full[b]))
+                     : "memory");
+      }
+    } else {
+      if (lane == 0) atomicOr(sink.err, DERR_TIMEOUT);
+      if (s > 0) mbar_wait(&full[(s - 1) & 1u], ((s - 1) >> 1) & 1u);
+    }
+    return;
+  }
+  // ---------------- consumers ----------------
+  const int cw = warp - 1;
+  WarpRows<kTileRowCap> wrows{s_rows[cw]};
+  WarpRows<kTileBandCap> wband{s_band[cw]};
+  unsigned long long ntest = 0;
+  for (uint32_t s = 0;; ++s) {
+    const uint32_t b = s & 1u, use = s >> 1;
+    if (!mbar_wait(&full[b], use & 1u)) {
+      if (lane == 0) atomicOr(sink.err, DERR_TIMEOUT);
+      break;
+    }
+    const TileDesc& D = desc[b];
+    if (D.done) break;
+    const uint32_t na = D.na;
+    const float4* sB = sB0 + (size_t)b * kTileCap;
+    const int ka = na <= 32 ? 1 : (na <= 64 ? 2 : 4);  // the density rule
+    if (ka == 1)
+      tile_round<1>(sB, D.nr, D.nrp, D.R0, D.rb, D.off, ta.a32, D.a0, na, D.lo32, D.hi32, lane,
+                    cw, wrows, wband, sink, ntest);
+    else if (ka == 2)
+      tile_round<2>(sB, D.nr, D.nrp, D.R0, D.rb, D.off, ta.a32, D.a0, na, D.lo32, D.hi32, lane,
+                    cw, wrows, wband, sink, ntest);
+    else
+      tile_round<4>(sB, D.nr, D.nrp, D.R0, D.rb, D.off, ta.a32, D.a0, na, D.lo32, D.hi32, lane,
+                    cw, wrows, wband, sink, ntest);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[b]);
   }
   wrows.flush(sink.rows, sink.count, sink.cap, sink.err);
   wband.flush(sink.band, sink.band_count, sink.band_cap, sink.err);
   for (int o = 16; o > 0; o >>= 1) ntest += __shfl_down_sync(0xffffffffu, ntest, o);
-  if ((t & 31) == 0 && ntest) atomicAdd(sink.tests, ntest);
+  if (lane == 0 && ntest) atomicAdd(sink.tests, ntest);
 }
 
 }  // namespace hlc
