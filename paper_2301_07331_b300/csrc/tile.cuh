@@ -6,17 +6,18 @@
 // Work items are fine cells of A holding at least kTileMinA entries (in the
 // single form: cells that lie in a dense table cell of B, where the A entries
 // were put in fine order; in the batched form: every such cell of every job,
-// A being sorted by (job, cell)).  The CTA is warp-specialised.  Its producer
-// warp takes items from an atomic counter, finds the B ranges of the cell and
-// its 8 neighbours (single form: a sparse neighbour table cell contributes its
-// whole range, once), writes a round descriptor and copies the round's B
-// vectors into one of two stage buffers with cp.async.bulk (the TMA engine's
-// bulk mode: contiguous 16-byte vectors need no tensor map) on the buffer's
-// "full" mbarrier.  Eight consumer warps each take a share of a staged round
+// A being sorted by (job, cell)).  A first pass (k_tile_items, a warp per
+// cell) finds the B ranges of each cell and its 8 neighbours (single form: a
+// sparse neighbour table cell contributes its whole range, once).  The pair
+// kernel is warp-specialised.  Its producer warp takes prepared items from an
+// atomic counter, writes a round descriptor and copies the round's B vectors
+// into one of two stage buffers with cp.async.bulk (the TMA engine's bulk
+// mode: contiguous 16-byte vectors need no tensor map) on the buffer's "full"
+// mbarrier.  Eight consumer warps each take a share of a staged round
 // while their lanes hold KA A sources each: one broadcast shared load per B
 // vector and KA FP32 squared-chord tests; then they arrive on the buffer's
-// "empty" mbarrier.  The producer's dependent lookups for the next round thus
-// overlap the consumers' tests of the current one.  Rounds are padded to whole
+// "empty" mbarrier.  The producer's copies for the next round thus overlap
+// the consumers' tests of the current one.  Rounds are padded to whole
 // groups with vectors far from everything and dead A lanes hold such a vector
 // too, so the inner loop has no bounds tests.  A lane records its candidates
 // of a group in a bit mask; the warp walks them (a ballot per step) only when
