@@ -321,12 +321,12 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Warp-specialised: warp 0 produces (takes items from the work counter, finds
-// the B ranges, writes a round descriptor and issues the bulk copies into one
-// of two stage buffers), warps 1..8 consume (test their share of the staged
-// B vectors against the item's A sources).  Full/empty mbarrier pairs hand the
-// buffers over, so the producer's dependent lookups for the next round
-// overlap the consumers' tests of the current one.
+// Warp-specialised: warp 0 produces (takes prepared items from the work
+// counter, writes a round descriptor and issues the bulk copies into one of
+// two stage buffers), warps 1..8 consume (test their share of the staged B
+// vectors against the item's A sources).  Full/empty mbarrier pairs hand the
+// buffers over, so the copies for the next round overlap the tests of the
+// current one.
 __global__ void __launch_bounds__(kTileThreads + 32) k_pair_tile(const TileArgs ta,
                                                                  PairSink sink) {
   extern __shared__ __align__(128) unsigned char tile_smem[];
