@@ -867,11 +867,65 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
     cudaEventCreate(&eb[i]);
   }
   // (the FP32 complete form orders A by B's table cells: B first)
-  int rc = P->table_buckets ? build_catalog(P, B, P->B, true, eb)
-                            : build_catalog(P, A, P->A, false, ea);
-  if (rc == HLC_OK)
-    rc = P->table_buckets ? build_catalog(P, A, P->A, false, ea)
-                          : build_catalog(P, B, P->B, true, eb);
+  const hlc_catalog* first = P->table_buckets ? B : A;
+  const hlc_catalog* second = P->table_buckets ? A : B;
+  // host inputs: both catalogues are copied in on a side stream in build
+  // order, so that building the first overlaps the copy of the second
+  hlc_catalog dv[2] = {*first, *second};
+  void* stage[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  cudaStream_t cs = nullptr;
+  cudaEvent_t cev[3] = {nullptr, nullptr, nullptr};
+  int rc = HLC_OK;
+  if (!first->on_device || !second->on_device) {
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) rc = HLC_ECUDA;
+    for (int i = 0; i < 3 && rc == HLC_OK; ++i)
+      if (cudaEventCreateWithFlags(&cev[i], cudaEventDisableTiming) != cudaSuccess) rc = HLC_ECUDA;
+    for (int i = 0; i < 2 && rc == HLC_OK; ++i) {
+      if (dv[i].on_device) continue;
+      const uint64_t n = dv[i].n;
+      for (int k = 0; k < 3; ++k) {
+        stage[i][k] = P->arena->get((n + 1) * 8);
+        if (!stage[i][k]) rc = HLC_ENOMEM;
+      }
+    }
+    if (rc == HLC_OK && (cudaEventRecord(cev[2], st) != cudaSuccess ||  // allocations done
+                         cudaStreamWaitEvent(cs, cev[2], 0) != cudaSuccess))
+      rc = HLC_ECUDA;
+    for (int i = 0; i < 2 && rc == HLC_OK; ++i) {
+      if (!dv[i].on_device && dv[i].n) {
+        const uint64_t n = dv[i].n;
+        if (cudaMemcpyAsync(stage[i][0], dv[i].ra_deg, n * 8, cudaMemcpyHostToDevice, cs) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(stage[i][1], dv[i].dec_deg, n * 8, cudaMemcpyHostToDevice, cs) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(stage[i][2], dv[i].id, n * 8, cudaMemcpyHostToDevice, cs) !=
+                cudaSuccess)
+          rc = HLC_ECUDA;
+      }
+      if (rc == HLC_OK && cudaEventRecord(cev[i], cs) != cudaSuccess) rc = HLC_ECUDA;
+      if (!dv[i].on_device) {
+        dv[i].ra_deg = (const double*)stage[i][0];
+        dv[i].dec_deg = (const double*)stage[i][1];
+        dv[i].id = (const uint64_t*)stage[i][2];
+        dv[i].on_device = 1;
+      }
+    }
+  }
+  for (int i = 0; i < 2 && rc == HLC_OK; ++i) {
+    if (cs && cudaStreamWaitEvent(st, cev[i], 0) != cudaSuccess) rc = HLC_ECUDA;
+    const bool is_b = (i == 0) == P->table_buckets;
+    if (rc == HLC_OK)
+      rc = build_catalog(P, &dv[i], is_b ? P->B : P->A, is_b, is_b ? eb : ea);
+  }
+  if (cs) {
+    cudaStreamSynchronize(cs);
+    cudaStreamDestroy(cs);
+    for (int i = 0; i < 3; ++i)
+      if (cev[i]) cudaEventDestroy(cev[i]);
+    for (int i = 0; i < 2; ++i)
+      for (int k = 0; k < 3; ++k)
+        if (stage[i][k]) P->arena->drop(stage[i][k]);
+  }
   if (rc == HLC_OK && P->A.n && !P->table_buckets) {
     k_id_diff_rec<<<grid_for(P->A.n, kThreads, 148u * 8u), kThreads, 0, st>>>(P->A.rec, P->A.n,
                                                                               P->ctr + C_IDDIFF);
