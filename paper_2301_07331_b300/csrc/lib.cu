@@ -1160,6 +1160,8 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
         TileArgs ta{};
         ta.items = A.tile_items;
         ta.nitems = A.tile_nprep;
+        ta.idxA = A.idx;
+        ta.idxB = B.idx;
         ta.work = (unsigned*)(P->ctr + C_WORK);
         ta.a32 = A.v32;
         ta.b32 = B.v32;
@@ -1192,9 +1194,11 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   P->row_cap = std::max<uint64_t>(P->row_cap, cap);
   ev_record(P, 4);
   if (fp32 && h[C_BAND]) {
+    // (the table-cell form's rows already hold source indices)
     k_recheck<<<grid_for(h[C_BAND], kThreads, 148u * 16u), kThreads, 0, st>>>(
-        band, P->ctr + C_BAND, bcap, A.idx, B.idx, A.rec, B.rec, P->C, rows, P->ctr + C_ROWS,
-        cap, P->dev_err);
+        band, P->ctr + C_BAND, bcap, P->table_buckets ? nullptr : A.idx,
+        P->table_buckets ? nullptr : B.idx, A.rec, B.rec, P->C, rows, P->ctr + C_ROWS, cap,
+        P->dev_err);
     HLC_LAUNCH_CHECK();
   }
   ev_record(P, 5);
@@ -1228,7 +1232,9 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   if (M) {
     unsigned g = grid_for(M, kThreads);
     if (fp32)
-      k_rows<true><<<g, kThreads, 0, st>>>(rows, M, A.idx, B.idx, A.rec, B.rec, nullptr, nullptr,
+      k_rows<true><<<g, kThreads, 0, st>>>(rows, M, P->table_buckets ? nullptr : A.idx,
+                                            P->table_buckets ? nullptr : B.idx, A.rec, B.rec,
+                                            nullptr, nullptr,
                                             nullptr, nullptr, nullptr, nullptr, want_sep, rows32,
                                             bshift, bmask, bhist);
     else

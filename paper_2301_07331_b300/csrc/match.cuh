@@ -467,6 +467,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
       nhead += live && (k == 0 || prev != cell);
     }
     const uint32_t maxT = __reduce_max_sync(0xffffffffu, total);
+    const uint32_t srcA = (BUCKET && live && total) ? __ldg(pa.idxA + k) : 0u;
     uint32_t cur = rb[0], end = re[0];
     // U candidates per lane per iteration: their loads are issued together
     constexpr int U = QUAD ? 1 : HLC_PAIR_UNROLL;
@@ -534,8 +535,12 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
       if (__any_sync(0xffffffffu, anyv)) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          wrows.add(hit[u], (uint32_t)k, jj[u]);
-          if (FP32) wband.add(band[u], (uint32_t)k, jj[u]);
+          // BUCKET: rows carry source indices (the output reads records)
+          const uint32_t ea = BUCKET ? srcA : (uint32_t)k;
+          const uint32_t eb =
+              BUCKET ? ((hit[u] || band[u]) ? __ldg(pa.idxB + jj[u]) : 0u) : jj[u];
+          wrows.add(hit[u], ea, eb);
+          if (FP32) wband.add(band[u], ea, eb);
         }
         if (wrows.fill > kRowCap - 32 * U)
           wrows.flush(sink.rows, sink.count, sink.cap, sink.err);
@@ -581,8 +586,8 @@ __global__ void __launch_bounds__(kThreads) k_recheck(
     bool hit = false;
     uint2 p = make_uint2(0u, 0u);
     if (q < nb) {
-      p = band[q];
-      SrcRec a = recA[idxA[p.x]], b = recB[idxB[p.y]];
+      p = band[q];  // entry indices, or source indices when idxA/idxB are null
+      SrcRec a = recA[idxA ? idxA[p.x] : p.x], b = recB[idxB ? idxB[p.y] : p.y];
       double ax, ay, az, bx, by, bz;
       c_unitvec(a.ra, a.dec, &ax, &ay, &az);
       c_unitvec(b.ra, b.dec, &bx, &by, &bz);

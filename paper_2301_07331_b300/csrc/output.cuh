@@ -115,8 +115,8 @@ __global__ void k_rows(const uint2* __restrict__ rows, uint64_t M,
                        uint32_t* __restrict__ bhist) {
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
        m += (uint64_t)gridDim.x * blockDim.x) {
-    uint2 p = rows[m];
-    SrcRec u = recA[idxA[p.x]], w = recB[idxB[p.y]];
+    uint2 p = rows[m];  // entry indices, or source indices when idxA/idxB are null
+    SrcRec u = recA[idxA ? idxA[p.x] : p.x], w = recB[idxB ? idxB[p.y] : p.y];
     OutRow o;
     o.a = u.id;
     o.b = w.id;

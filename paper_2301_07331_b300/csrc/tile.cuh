@@ -68,6 +68,7 @@ struct TileArgs {
   int order;
   // the pair kernel: items prepared by k_tile_items
   const TileItem* items;
+  const uint32_t *idxA, *idxB;  // non-null: emit source indices (entry -> source)
   // batched form: composite (job, cell) keys and per-job tables
   const uint64_t* keyA64;
   const uint64_t* keyB64;
@@ -144,6 +145,8 @@ __device__ __forceinline__ void tile_round(const float4* __restrict__ sB, uint32
                                            uint32_t a0, uint32_t na, float lo32, float hi32,
                                            int lane, int warp, WarpRows<kTileRowCap>& wrows,
                                            WarpRows<kTileBandCap>& wband, const PairSink& sink,
+                                           const uint32_t* __restrict__ idxA,
+                                           const uint32_t* __restrict__ idxB,
                                            unsigned long long& ntest) {
   const uint32_t ngroups = nrp / kTileGroup;
   const uint32_t gper = (ngroups + kTileWarps - 1) / kTileWarps;
@@ -200,7 +203,11 @@ __device__ __forceinline__ void tile_round(const float4* __restrict__ sB, uint32
             while (sgi < 8 && s_off[sgi + 1] <= o) ++sgi;
             jb = s_rb[sgi] + (o - s_off[sgi]);
           }
-          const uint32_t ka = a0 + p0 + (uint32_t)u * 32 + lane;
+          uint32_t ka = a0 + p0 + (uint32_t)u * 32 + lane;
+          if (idxA && act) {  // rows of source indices
+            ka = __ldg(idxA + ka);
+            jb = __ldg(idxB + jb);
+          }
           wrows.add(hit, ka, jb);
           wband.add(band, ka, jb);
           if (wrows.fill > kTileRowCap - 32) wrows.flush(sink.rows, sink.count, sink.cap, sink.err);
@@ -447,13 +454,13 @@ __global__ void __launch_bounds__(kTileThreads + 32) k_pair_tile(const TileArgs 
     const int ka = na <= 32 ? 1 : (na <= 64 ? 2 : 4);  // the density rule
     if (ka == 1)
       tile_round<1>(sB, D.nr, D.nrp, D.R0, D.rb, D.off, ta.a32, D.a0, na, D.lo32, D.hi32, lane,
-                    cw, wrows, wband, sink, ntest);
+                    cw, wrows, wband, sink, ta.idxA, ta.idxB, ntest);
     else if (ka == 2)
       tile_round<2>(sB, D.nr, D.nrp, D.R0, D.rb, D.off, ta.a32, D.a0, na, D.lo32, D.hi32, lane,
-                    cw, wrows, wband, sink, ntest);
+                    cw, wrows, wband, sink, ta.idxA, ta.idxB, ntest);
     else
       tile_round<4>(sB, D.nr, D.nrp, D.R0, D.rb, D.off, ta.a32, D.a0, na, D.lo32, D.hi32, lane,
-                    cw, wrows, wband, sink, ntest);
+                    cw, wrows, wband, sink, ta.idxA, ta.idxB, ntest);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[b]);
   }
