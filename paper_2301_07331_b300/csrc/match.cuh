@@ -24,12 +24,7 @@ struct __align__(32) SrcRec {
 };
 // Number of B entries in a table cell up to which the FP32 join uses the
 // table order (sparse regions).
-#ifndef HLC_PAIR_UNROLL
-#define HLC_PAIR_UNROLL 4  // candidates per lane per pair-test iteration
-#endif
-#ifndef HLC_COARSE_FP64
-#define HLC_COARSE_FP64 0  // table-order join for sparse cells in the binary64 form too
-#endif
+constexpr int kPairUnroll = 4;  // candidates per lane per pair-test iteration
 #ifndef HLC_SPARSE_CELL
 #define HLC_SPARSE_CELL 32
 #endif
@@ -409,7 +404,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
         nb[0] = cell;
       } else {
         bool coarse = false;
-        if ((FP32 || HLC_COARSE_FP64) && !LEARNED && bix.shift > 0) {
+        if (FP32 && !LEARNED && bix.shift > 0) {
           uint32_t P = cell >> bix.shift;
           if (__ldg(bix.table + P + 1) - __ldg(bix.table + P) <= sparse_cell)
             coarse = parent_cover4(cell, order, bix.shift / 2, nb);
@@ -470,7 +465,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
     const uint32_t srcA = (BUCKET && live && total) ? __ldg(pa.idxA + k) : 0u;
     uint32_t cur = rb[0], end = re[0];
     // U candidates per lane per iteration: their loads are issued together
-    constexpr int U = QUAD ? 1 : HLC_PAIR_UNROLL;
+    constexpr int U = QUAD ? 1 : kPairUnroll;
     for (uint32_t t = 0; t < maxT; t += U) {
       uint32_t jj[U];
       bool act[U];

@@ -14,13 +14,7 @@ namespace rs {
 
 constexpr int kBlock = 256;  // threads per CTA; one thread per digit value
 constexpr int kWarps = kBlock / 32;
-#ifndef HLC_SORT_IPT
-#define HLC_SORT_IPT 15
-#endif
-#ifndef HLC_SORT_MATCH
-#define HLC_SORT_MATCH 0
-#endif
-constexpr int kIpt = HLC_SORT_IPT;  // items per thread
+constexpr int kIpt = 15;     // items per thread
 constexpr int kTile = kBlock * kIpt;
 constexpr int kRadix = 256;
 constexpr unsigned long long kFlagAgg = 1ull << 62;
@@ -144,16 +138,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_onesweep(
     bool valid = wbase + (uint64_t)i * 32 + lane < n;
     uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
     unsigned peers = __ballot_sync(0xffffffffu, valid);
-#if HLC_SORT_MATCH
-    peers &= __match_any_sync(0xffffffffu, d);
-#else
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
       bool bit = (d >> b) & 1;
       unsigned bb = __ballot_sync(0xffffffffu, bit);
       peers &= bit ? bb : ~bb;
     }
-#endif
     uint32_t before = valid ? S.whist[warp][d] : 0u;
     r[i] = before + __popc(peers & lt);
     __syncwarp();

@@ -176,6 +176,7 @@ __device__ __forceinline__ void tile_round(const float4* __restrict__ sB, uint32
         }
       }
       if (__any_sync(0xffffffffu, mask != 0u)) {
+
         // slow path: each lane walks its own candidates
         const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)__popc(mask));
         for (int it = 0; it < nmax; ++it) {
