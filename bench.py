@@ -187,19 +187,27 @@ def run_hlc(args):
     lt = 0
     while lt < L and 12 * 4 ** lt < mB:
         lt += 1
-    pair_bytes = (mA * (4 + 16) + mB * 16 + (12 * 4 ** lt + 1) * 4
-                  + 8 * (last["matches"] + last["band_candidates"]))
+    quad = args.mode == "quad"
+    # complete (table-cell) form: key + vector + source index per A entry, a B
+    # vector per B entry, the offset table, a row and its B source index per
+    # emitted row; quad form: key + vector per A entry, no index translation
+    pair_bytes = (mA * (20 if quad else 24) + mB * 16 + (12 * 4 ** lt + 1) * 4
+                  + (8 if quad else 12) * (last["matches"] + last["band_candidates"]))
     pair_gbs = pair_bytes / (stage_ms["ms_pair"] / 1e3) / 1e9
-    tr = TRAFFIC.get("k_pair<1,0,0,1>")
+    kname = "k_pair<1,1,0,0>" if quad else "k_pair<1,0,0,1>"
+    tr = TRAFFIC.get(kname) if prec == hlc.HLC_FP32_GUARD else None
     traffic = tr["bytes_per_launch"] if tr and tr["sources"] == _kernel_sources_sha() else None
-    roofline = {"kernel": "k_pair<1,0,0,1> (FP32 complete form: candidates + pair test)",
+    roofline = {"kernel": kname + (" (FP32 quad form" if quad else " (FP32 complete form")
+                + ": candidates + pair test)",
                 "bound": "hbm", "achieved": round(pair_gbs, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(pair_gbs / peak, 4), "traffic": traffic,
                 "peak_source": (peak_kind + " (MEASURED_PEAKS.json hbm_gbs)")
                 if peak_kind == "measured" else "fallback 6.4 TB/s",
                 "bytes_per_launch": int(pair_bytes),
-                "bytes_basis": "20 B per A entry (key + FP32 vector), 16 B per B entry, "
-                               "4 B per offset-table slot, 8 B per emitted row",
+                "bytes_basis": ("20" if quad else "24") + " B per A entry (key + FP32 vector"
+                               + ("" if quad else " + source index") + "), 16 B per B entry, "
+                               "4 B per offset-table slot, " + ("8" if quad else "12")
+                               + " B per emitted row",
                 "ms_per_launch": stage_ms["ms_pair"]}
     alg = alg_pair_tests(hlc, A, B, L) if args.mode == "complete" else None
 
@@ -272,8 +280,8 @@ def run_hlc(args):
 # the digest of the kernel sources it was taken on; a changed source voids it.
 TRAFFIC = {
     # ncu --set full of the pair test in the full-sky 10M x 10M step:
-    # 414,539,008 B read + 41,545,728 B written
-    "k_pair<1,0,0,1>": {"bytes_per_launch": 456084736, "sources": "4c75e933c3edc6a7"},
+    # 495,411,712 B read + 41,638,144 B written
+    "k_pair<1,0,0,1>": {"bytes_per_launch": 537049856, "sources": "d0fe5925b28a6acd"},
 }
 
 _KERNEL_SOURCES = ("match.cuh", "canon.cuh", "index.cuh", "learned.cuh", "common.cuh",
