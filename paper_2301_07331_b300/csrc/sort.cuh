@@ -17,6 +17,7 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kIpt = 15;     // items per thread
 constexpr int kTile = kBlock * kIpt;
 constexpr int kRadix = 256;
+static_assert(kBlock == kRadix, "one thread per digit value");
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagInc = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
@@ -109,7 +110,7 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
 // (The look-back words carry their value and flag in one 64-bit word, so
 // relaxed accesses suffice: no other data is published through them.)
 template <typename K>
-__global__ void __launch_bounds__(kBlock, 4) k_onesweep(
+__global__ void __launch_bounds__(kBlock, sizeof(K) == 8 ? 3 : 4) k_onesweep(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, uint64_t n, int shift, const uint32_t* __restrict__ goff,
     unsigned long long* __restrict__ lookback, uint32_t* __restrict__ tile_ctr,
@@ -119,6 +120,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_onesweep(
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   if (t == 0) S.tile = atomicAdd(tile_ctr, 1u);
   for (int i = t; i < kWarps * kRadix; i += kBlock) (&S.whist[0][0])[i] = 0;
+  S.dstart[t] = 0;  // (kBlock == kRadix) the tile's digit counts first
   __syncthreads();
   const uint32_t tile = S.tile;
   const uint64_t base = (uint64_t)tile * kTile;
@@ -130,6 +132,17 @@ __global__ void __launch_bounds__(kBlock, 4) k_onesweep(
     uint64_t e = wbase + (uint64_t)i * 32 + lane;
     k[i] = e < n ? kin[e] : K(0);
   }
+  // publish this tile's digit counts before ranking, so that later tiles'
+  // look-backs do not wait for it; the look-back of its own prefix follows
+  // the ranking and finds earlier tiles published the same way
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i)
+    if (wbase + (uint64_t)i * 32 + lane < n)
+      atomicAdd(&S.dstart[(uint32_t)(k[i] >> shift) & 255u], 1u);
+  __syncthreads();
+  const uint32_t cnt = S.dstart[t];
+  unsigned long long* slot = lookback + (uint64_t)tile * kRadix + t;
+  st_relaxed_u64(slot, (tile == 0 ? kFlagInc : kFlagAgg) | cnt);
   uint32_t r[kIpt];
   const unsigned lt = lanemask_lt();
 #pragma unroll
@@ -152,19 +165,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_onesweep(
   }
   __syncthreads();
 
-  // thread t owns digit t: warp offsets within the tile and the tile count
-  uint32_t cnt = 0;
+  // thread t owns digit t: warp offsets within the tile
+  uint32_t wsum = 0;
   for (int w = 0; w < kWarps; ++w) {
     uint32_t c = S.whist[w][t];
-    S.whist[w][t] = cnt;
-    cnt += c;
+    S.whist[w][t] = wsum;
+    wsum += c;
   }
   unsigned long long excl = 0;
-  unsigned long long* slot = lookback + (uint64_t)tile * kRadix + t;
-  if (tile == 0) {
-    st_relaxed_u64(slot, kFlagInc | cnt);
-  } else {
-    st_relaxed_u64(slot, kFlagAgg | cnt);
+  if (tile != 0) {
     long long spins = 0;
     int64_t j = (int64_t)tile - 1;
     while (j >= 0) {
