@@ -177,17 +177,34 @@ def run_hlc(args):
     value = sources / (ms / 1e3)
     tests = stats[-1]["pair_tests"]
 
-    # roofline of the dominant kernel: the pair test (k_pair), timed live by
-    # the library's CUDA events on the launching stream
+    # roofline of the dominant kernel: the radix sort's digit passes
+    # (k_onesweep, the largest share of the step), timed live by the library's
+    # CUDA events on the launching stream; the pair test beside it
     peak, peak_kind = _peaks()
     stage_ms = {k: mean(k, stats) for k in ("ms_prep", "ms_sort", "ms_index", "ms_candidates",
                                             "ms_pair", "ms_recheck", "ms_output")}
     last = stats[-1]
     mA, mB = last["entries_a"], last["entries_b"]
+    peak_src = ((peak_kind + " (MEASURED_PEAKS.json hbm_gbs)") if peak_kind == "measured"
+                else "fallback 6.4 TB/s")
+    quad = args.mode == "quad"
+    roofline = None
+    npass = last["sort_passes"]
+    ms_passes = mean("ms_sort_passes", stats)
+    if npass and ms_passes > 0:
+        # each pass reads and writes a 4-byte key and a 4-byte value per entry
+        per_pass = 16 * (mA + mB) / 2
+        gbs = per_pass * npass / (ms_passes / 1e3) / 1e9
+        tr = _traffic("k_onesweep")
+        roofline = {"kernel": "k_onesweep (cell-key radix sort digit pass)", "bound": "hbm",
+                    "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(gbs / peak, 4), "traffic": tr, "peak_source": peak_src,
+                    "bytes_per_launch": int(per_pass),
+                    "bytes_basis": "16 B per entry per pass (key and value read and written)",
+                    "launches_per_step": npass, "ms_per_launch": ms_passes / npass}
     lt = 0
     while lt < L and 12 * 4 ** lt < mB:
         lt += 1
-    quad = args.mode == "quad"
     # complete (table-cell) form: key + vector + source index per A entry, a B
     # vector per B entry, the offset table, a row and its B source index per
     # emitted row; quad form: key + vector per A entry, no index translation
@@ -195,20 +212,19 @@ def run_hlc(args):
                   + (8 if quad else 12) * (last["matches"] + last["band_candidates"]))
     pair_gbs = pair_bytes / (stage_ms["ms_pair"] / 1e3) / 1e9
     kname = "k_pair<1,1,0,0>" if quad else "k_pair<1,0,0,1>"
-    tr = TRAFFIC.get(kname) if prec == hlc.HLC_FP32_GUARD else None
-    traffic = tr["bytes_per_launch"] if tr and tr["sources"] == _kernel_sources_sha() else None
-    roofline = {"kernel": kname + (" (FP32 quad form" if quad else " (FP32 complete form")
-                + ": candidates + pair test)",
-                "bound": "hbm", "achieved": round(pair_gbs, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(pair_gbs / peak, 4), "traffic": traffic,
-                "peak_source": (peak_kind + " (MEASURED_PEAKS.json hbm_gbs)")
-                if peak_kind == "measured" else "fallback 6.4 TB/s",
-                "bytes_per_launch": int(pair_bytes),
-                "bytes_basis": ("20" if quad else "24") + " B per A entry (key + FP32 vector"
-                               + ("" if quad else " + source index") + "), 16 B per B entry, "
-                               "4 B per offset-table slot, " + ("8" if quad else "12")
-                               + " B per emitted row",
-                "ms_per_launch": stage_ms["ms_pair"]}
+    roofline_pair = {"kernel": kname + (" (FP32 quad form" if quad else " (FP32 complete form")
+                     + ": candidates + pair test)",
+                     "bound": "hbm", "achieved": round(pair_gbs, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(pair_gbs / peak, 4),
+                     "traffic": _traffic(kname) if prec == hlc.HLC_FP32_GUARD else None,
+                     "peak_source": peak_src, "bytes_per_launch": int(pair_bytes),
+                     "bytes_basis": ("20" if quad else "24") + " B per A entry (key + FP32 vector"
+                                    + ("" if quad else " + source index") + "), 16 B per B entry, "
+                                    "4 B per offset-table slot, " + ("8" if quad else "12")
+                                    + " B per emitted row",
+                     "ms_per_launch": stage_ms["ms_pair"]}
+    if roofline is None:
+        roofline = roofline_pair
     alg = alg_pair_tests(hlc, A, B, L) if args.mode == "complete" else None
 
     # end to end: pinned host inputs in, sorted rows back to host
@@ -266,6 +282,7 @@ def run_hlc(args):
                            "stages_ms": {k: mean(k, stats_other) for k in stage_ms}},
             "stages_ms": stage_ms,
             "roofline": roofline,
+            "roofline_pair": roofline_pair,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
@@ -279,22 +296,30 @@ def run_hlc(args):
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture, with
 # the digest of the kernel sources it was taken on; a changed source voids it.
 TRAFFIC = {
+    # ncu --set full of one sort pass in the full-sky 10M x 10M step:
+    # 81,022,976 B read + 35,151,104 B written
+    "k_onesweep": {"bytes_per_launch": 116174080, "sources": "5f96d74c07f657ea",
+                   "files": ("sort.cuh", "common.cuh")},
     # ncu --set full of the pair test in the full-sky 10M x 10M step:
     # 495,411,712 B read + 41,638,144 B written
-    "k_pair<1,0,0,1>": {"bytes_per_launch": 537049856, "sources": "d0fe5925b28a6acd"},
+    "k_pair<1,0,0,1>": {"bytes_per_launch": 537049856, "sources": "d0fe5925b28a6acd",
+                        "files": ("match.cuh", "canon.cuh", "index.cuh", "learned.cuh",
+                                  "common.cuh", "fp32.cuh", "fastpix.cuh")},
 }
 
-_KERNEL_SOURCES = ("match.cuh", "canon.cuh", "index.cuh", "learned.cuh", "common.cuh",
-                   "fp32.cuh", "fastpix.cuh")
 
-
-def _kernel_sources_sha() -> str:
+def _sources_sha(files) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in _KERNEL_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_2301_07331_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def _traffic(name):
+    tr = TRAFFIC.get(name)
+    return tr["bytes_per_launch"] if tr and tr["sources"] == _sources_sha(tr["files"]) else None
 
 
 def alg_pair_tests(hlc, A, B, L):

@@ -145,6 +145,9 @@ typedef struct {
   float ms_stream_bucket;          /*   bucketing pass into pinned host runs, */
   float ms_stream_groups;          /*   the groups' copies in, matches and rows out, */
   float ms_stream_merge;           /*   merge of the groups' sorted rows */
+  float ms_sort_passes;            /* FP32 complete form: the radix sort's digit
+                                      passes alone (both catalogues) */
+  uint32_t sort_passes;            /*   and how many passes that was */
 } hlc_stats;
 
 typedef struct hlc_plan_s hlc_plan_t;

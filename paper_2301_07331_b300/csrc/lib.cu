@@ -332,6 +332,8 @@ struct hlc_plan_s {
   double* host_s = nullptr;
   uint32_t sparse_cell = hlc::kSparseCell;
   bool table_buckets = false;  // FP32 complete mode: entries bucketed by table cell
+  uint32_t sort_passes = 0;    // radix passes of the table-cell sorts (ev 7-8: B, 9-10: A)
+  bool sort_timed[2] = {false, false};
   unsigned long long plan_launches = 0;
   cudaEvent_t ev[12] = {};
   bool events = false;
@@ -605,8 +607,12 @@ static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
     void* scr = ar.get(sort_scratch_bytes(n, (bits - shift + 7) / 8));
     if (!tk || !tv || !scr) return HLC_ENOMEM;
     bool in_tmp = false;
+    int np = 0;
+    cudaEvent_t* pev = P->events ? P->ev + (is_b ? 7 : 9) : nullptr;
     HLC_TRY(radix_sort_pairs<uint32_t>(X.key, X.idx, tk, tv, n, bits, scr, P->dev_err, st, shift,
-                                       &in_tmp));
+                                       &in_tmp, pev, &np));
+    P->sort_passes += np;
+    if (pev) P->sort_timed[is_b ? 0 : 1] = true;
     ar.drop(scr);
     if (in_tmp) {
       std::swap(X.key, tk);
@@ -974,6 +980,9 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   P->stats.ms_prep = t[0] + t[1];
   P->stats.ms_sort = t[2] + t[3];
   P->stats.ms_index = t[4] + t[5];
+  P->stats.sort_passes = P->sort_passes;
+  for (int i = 0; i < 2; ++i)
+    if (P->sort_timed[i]) P->stats.ms_sort_passes += ev_ms(P, 7 + 2 * i, 8 + 2 * i);
   P->plan_launches = g_launches.load() - P->launches0;
   *out = P;
   return HLC_OK;

@@ -235,10 +235,12 @@ inline size_t sort_scratch_bytes(uint64_t n, int npass) {
 // Sorts by the key bits [bit_lo, key_bits).  With in_tmp set, an odd number
 // of passes leaves the result in (tmp_keys, tmp_vals) and *in_tmp says so;
 // otherwise it is copied back.
+// pass_ev, when given, receives events recorded around the digit passes.
 template <typename K>
 int radix_sort_pairs(K* keys, uint32_t* vals, K* tmp_keys, uint32_t* tmp_vals, uint64_t n,
                      int key_bits, void* scratch, int* dev_err, cudaStream_t st,
-                     int bit_lo = 0, bool* in_tmp = nullptr) {
+                     int bit_lo = 0, bool* in_tmp = nullptr, cudaEvent_t* pass_ev = nullptr,
+                     int* npass_out = nullptr) {
   if (in_tmp) *in_tmp = false;
   if (n <= 1) return HLC_OK;
   if (bit_lo < 0 || bit_lo >= key_bits) bit_lo = 0;
@@ -271,6 +273,8 @@ int radix_sort_pairs(K* keys, uint32_t* vals, K* tmp_keys, uint32_t* tmp_vals, u
   uint32_t* va = vals;
   K* kb = tmp_keys;
   uint32_t* vb = tmp_vals;
+  if (npass_out) *npass_out = npass;
+  if (pass_ev) cudaEventRecord(pass_ev[0], st);
   for (int p = 0; p < npass; ++p) {
     rs::k_onesweep<K><<<(unsigned)tiles, rs::kBlock, smem, st>>>(
         ka, va, kb, vb, n, bit_lo + 8 * p, offs + p * rs::kRadix,
@@ -280,6 +284,7 @@ int radix_sort_pairs(K* keys, uint32_t* vals, K* tmp_keys, uint32_t* tmp_vals, u
     K* tk = ka; ka = kb; kb = tk;
     uint32_t* tv = va; va = vb; vb = tv;
   }
+  if (pass_ev) cudaEventRecord(pass_ev[1], st);
   if (ka != keys && in_tmp) {
     *in_tmp = true;
   } else if (ka != keys) {
