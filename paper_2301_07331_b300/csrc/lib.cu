@@ -476,6 +476,26 @@ static int build_learned(Arena& ar, const uint32_t* uniq, uint64_t m, int shift,
 // whose table cell of T holds more than sparse_cell B entries) are compacted
 // in order, radix sorted by key and written back.  With items set, the sorted
 // dense keys are also run-length encoded into the tile kernel's work items.
+// Offset table T[0..S] of m keys sorted by (key >> shift): tile bounds,
+// then one CTA per tile of slots.
+static int offset_table(hlc_plan_t* P, const uint32_t* keys, uint64_t m, int shift, uint64_t S,
+                        uint32_t* T, unsigned long long* heads, uint32_t dense_above,
+                        unsigned long long* ndense) {
+  Arena& ar = *P->arena;
+  cudaStream_t st = plan_stream(P);
+  const uint64_t nt = (S + kTabTile) / kTabTile;  // tiles over the S + 1 slots
+  uint32_t* bnd = ar.get_n<uint32_t>(nt + 1);
+  if (!bnd) return HLC_ENOMEM;
+  k_table_bounds<<<grid_for(32 * (nt + 1), kThreads), kThreads, 0, st>>>(keys, m, shift, S, nt,
+                                                                         bnd);
+  HLC_LAUNCH_CHECK();
+  k_table_tiles<<<(unsigned)std::min<uint64_t>(nt, 148u * 64u), kTabThreads, 0, st>>>(
+      keys, m, shift, S, nt, bnd, T, heads, dense_above, ndense);
+  HLC_LAUNCH_CHECK();
+  ar.drop(bnd);
+  return HLC_OK;
+}
+
 static int dense_fixup(hlc_plan_t* P, CatDev& X, const uint32_t* T, int shift, bool items) {
   Arena& ar = *P->arena;
   cudaStream_t st = plan_stream(P);
@@ -633,9 +653,8 @@ static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
     return HLC_OK;
   }
   HLC_ALLOC(ar, X.table, uint32_t, tsize + 1);
-  k_coarse_table<<<grid_for(tsize / 8 + 1, kThreads), kThreads, 0, st>>>(
-      X.key, n, shift, tsize, X.table, P->ctr + C_HEADS_B, P->sparse_cell, P->ctr + C_DENSE);
-  HLC_LAUNCH_CHECK();
+  HLC_TRY(offset_table(P, X.key, n, shift, tsize, X.table, P->ctr + C_HEADS_B, P->sparse_cell,
+                       P->ctr + C_DENSE));
   if (n > 1) {
     unsigned long long nd = 0;
     HLC_CUDA(cudaMemcpyAsync(&nd, P->ctr + C_DENSE, 8, cudaMemcpyDeviceToHost, st));
@@ -816,9 +835,8 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     X.table_shift = 2 * (L - X.table_order);
     uint64_t tsize = 12ull << (2 * X.table_order);
     HLC_ALLOC(ar, X.table, uint32_t, tsize + 1);
-    k_coarse_table<<<grid_for(tsize / 8 + 1, kThreads), kThreads, 0, st>>>(
-        X.key, m, X.table_shift, tsize, X.table, heads, 0xFFFFFFFFu, nullptr);
-    HLC_LAUNCH_CHECK();
+    HLC_TRY(offset_table(P, X.key, m, X.table_shift, tsize, X.table, heads, 0xFFFFFFFFu,
+                         nullptr));
   }
   cudaEventRecord(ev[3], st);
   return HLC_OK;
@@ -1026,8 +1044,8 @@ static int order_rows(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_t* bhist
     HLC_CUDA(cudaMemsetAsync(P->ctr + C_MAXB, 0, 8, st));
     k_bucket_scatter<<<g, kThreads, 0, st>>>(rows32, M, bshift, bmask, nb_job, boff, t);
     HLC_LAUNCH_CHECK();
-    k_bucket_small<<<grid_for(nbk, kThreads), kThreads, 0, st>>>(
-        t, boff, (uint32_t)nbk, a, b, sp, jb, big, (uint32_t*)(P->ctr + C_MAXB), P->dev_err);
+    k_bucket_small<<<g, kThreads, 0, st>>>(t, M, bshift, bmask, nb_job, boff, a, b, sp, jb, big,
+                                           (uint32_t*)(P->ctr + C_MAXB), P->dev_err);
     HLC_LAUNCH_CHECK();
     k_bucket_sort<<<148u * 8u, kBucketThreads, 0, st>>>(t, boff, big,
                                                          (uint32_t*)(P->ctr + C_MAXB),

@@ -2,10 +2,10 @@
 // the rows in ascending (id_a, id_b) order.
 //
 // Ordering: the rows are distributed into 2^b buckets by the b bits of id_a
-// just below its highest varying bit (a counting scatter, about two rows per
-// bucket), then every bucket is sorted on (id_a, id_b, separation bits): by
-// one thread (insertion) when small, by a CTA's bitonic network in shared
-// memory when larger.  When a bucket would not fit in shared memory (one id
+// just below its highest varying bit (a counting scatter, four to eight rows
+// per bucket on average), then every bucket is sorted on (id_a, id_b,
+// separation bits): by rank counting (a thread per row) when small, by a
+// CTA's bitonic network in shared memory when larger.  When a bucket would not fit in shared memory (one id
 // matched thousands of times, or all ids equal) the caller falls back to two
 // stable LSD radix sorts (by id_b, then by id_a).
 #pragma once
@@ -164,15 +164,19 @@ __global__ void k_max_u32(const uint32_t* __restrict__ v, uint64_t n, uint32_t* 
 
 // Rows to their buckets: offset of the bucket plus the rank the row drew
 // there (in OutRow.pad) when the histogram was built.
+__device__ __forceinline__ uint64_t row_bucket(const OutRow& o, int bshift, uint32_t bmask,
+                                               int nb_job) {
+  return (nb_job >= 0 ? ((uint64_t)o.job << nb_job) : 0ull) |
+         ((uint32_t)(o.a >> bshift) & bmask);
+}
+
 __global__ void k_bucket_scatter(const OutRow* __restrict__ in, uint64_t M, int bshift,
                                  uint32_t bmask, int nb_job, const uint32_t* __restrict__ boff,
                                  OutRow* __restrict__ out) {
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
        m += (uint64_t)gridDim.x * blockDim.x) {
     OutRow o = in[m];
-    uint64_t bk = (nb_job >= 0 ? ((uint64_t)o.job << nb_job) : 0ull) |
-                  ((uint32_t)(o.a >> bshift) & bmask);
-    out[__ldg(boff + bk) + o.pad] = o;
+    out[__ldg(boff + row_bucket(o, bshift, bmask, nb_job)) + o.pad] = o;
   }
 }
 
@@ -183,47 +187,51 @@ __device__ __forceinline__ bool row_less(uint64_t a1, uint64_t b1, uint64_t s1, 
   return s1 < s2;
 }
 
-// One thread per small bucket (<= kSmallBucket rows): insertion sort into the
-// output arrays.
+// Small buckets (<= kSmallBucket rows): one thread per row counts the rows
+// of its bucket that order before it on (id_a, id_b, separation bits), ties
+// by position, and writes the row at that rank.  (The bucket's rows are
+// adjacent, so the comparisons read from L1.)
 constexpr uint32_t kSmallBucket = 32;
 
-// (Larger buckets are appended to `big` for k_bucket_sort; one above
-// kBucketCap sets DERR_BUCKET and the host orders the rows another way.)
-__global__ void k_bucket_small(const OutRow* __restrict__ t, const uint32_t* __restrict__ boff,
-                               uint32_t nbuckets, uint64_t* __restrict__ oa,
-                               uint64_t* __restrict__ ob, double* __restrict__ os,
-                               uint32_t* __restrict__ oj, uint32_t* __restrict__ big,
-                               uint32_t* __restrict__ nbig, int* __restrict__ err) {
-  for (uint32_t bk = blockIdx.x * blockDim.x + threadIdx.x; bk < nbuckets;
-       bk += gridDim.x * blockDim.x) {
-    uint32_t lo = boff[bk], hi = boff[bk + 1];
-    uint32_t n = hi - lo;
+// (The first row of each larger bucket appends it to `big` for
+// k_bucket_sort; one above kBucketCap sets DERR_BUCKET and the host orders
+// the rows another way.)
+__global__ void k_bucket_small(const OutRow* __restrict__ t, uint64_t M, int bshift,
+                               uint32_t bmask, int nb_job, const uint32_t* __restrict__ boff,
+                               uint64_t* __restrict__ oa, uint64_t* __restrict__ ob,
+                               double* __restrict__ os, uint32_t* __restrict__ oj,
+                               uint32_t* __restrict__ big, uint32_t* __restrict__ nbig,
+                               int* __restrict__ err) {
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < M;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    const OutRow r = t[p];
+    const uint64_t bk = row_bucket(r, bshift, bmask, nb_job);
+    const uint32_t lo = __ldg(boff + bk), hi = __ldg(boff + bk + 1);
+    const uint32_t n = hi - lo;
     if (n > kSmallBucket) {
-      if (n > kBucketCap)
-        atomicOr(err, DERR_BUCKET);
-      else
-        big[atomicAdd(nbig, 1u)] = bk;
+      if (p == lo) {
+        if (n > kBucketCap)
+          atomicOr(err, DERR_BUCKET);
+        else
+          big[atomicAdd(nbig, 1u)] = (uint32_t)bk;
+      }
       continue;
     }
-    if (n == 0) continue;
-    for (uint32_t i = 0; i < n; ++i) {
-      OutRow r = t[lo + i];
-      uint64_t sb = (uint64_t)__double_as_longlong(r.s);
-      uint32_t j = i;
-      while (j > 0) {
-        uint64_t pa = oa[lo + j - 1], pb = ob[lo + j - 1];
-        uint64_t ps = os ? (uint64_t)__double_as_longlong(os[lo + j - 1]) : 0ull;
-        if (!row_less(r.a, r.b, os ? sb : 0ull, pa, pb, ps)) break;
-        oa[lo + j] = pa;
-        ob[lo + j] = pb;
-        if (os) os[lo + j] = os[lo + j - 1];
-        --j;
-      }
-      oa[lo + j] = r.a;
-      ob[lo + j] = r.b;
-      if (os) os[lo + j] = r.s;
-      if (oj) oj[lo + i] = r.job;  // every row of a bucket has the same job
+    const uint64_t rs = os ? (uint64_t)__double_as_longlong(r.s) : 0ull;
+    uint32_t rank = 0;
+    for (uint32_t j = lo; j < hi; ++j) {
+      if (j == p) continue;
+      const OutRow q = t[j];
+      const uint64_t qs = os ? (uint64_t)__double_as_longlong(q.s) : 0ull;
+      if (row_less(q.a, q.b, qs, r.a, r.b, rs) ||
+          (j < p && q.a == r.a && q.b == r.b && qs == rs))
+        ++rank;
     }
+    const uint32_t dst = lo + rank;
+    oa[dst] = r.a;
+    ob[dst] = r.b;
+    if (os) os[dst] = r.s;
+    if (oj) oj[dst] = r.job;  // every row of a bucket has the same job
   }
 }
 

@@ -18,35 +18,47 @@ constexpr unsigned long long kFlagInc = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
 constexpr long long kSpinLimit = 1ll << 26;
 
-// Called by one thread of the tile: publish the tile aggregate, walk back to
-// the nearest inclusive prefix, publish this tile's inclusive prefix and
-// return its exclusive prefix.
+// Called by the 32 lanes of the tile's first warp: publish the tile
+// aggregate, walk back to the nearest inclusive prefix 32 predecessors at a
+// time (one load per lane, a ballot finds the nearest inclusive one, a warp
+// sum adds the aggregates up to it), publish this tile's inclusive prefix
+// and return its exclusive prefix (to every lane).
 __device__ __forceinline__ unsigned long long lookback_prefix(uint32_t tile,
                                                               unsigned long long agg,
                                                               unsigned long long* lb, int* err) {
+  const int lane = threadIdx.x & 31;
   if (tile == 0) {
-    st_release_u64(lb, kFlagInc | agg);
+    if (lane == 0) st_release_u64(lb, kFlagInc | agg);
     return 0;
   }
-  st_release_u64(lb + tile, kFlagAgg | agg);
+  if (lane == 0) st_release_u64(lb + tile, kFlagAgg | agg);
   unsigned long long excl = 0;
   long long spins = 0;
-  int64_t j = (int64_t)tile - 1;
-  while (j >= 0) {
-    unsigned long long w = ld_acquire_u64(lb + j);
-    unsigned long long f = w & ~kValMask;
-    if (f == 0) {
+  int64_t j = (int64_t)tile - 1;  // predecessor read by lane 0
+  while (true) {
+    const int64_t idx = j - lane;
+    // (before tile 0: an inclusive prefix of 0)
+    const unsigned long long w = idx >= 0 ? ld_acquire_u64(lb + idx) : kFlagInc;
+    const unsigned long long f = w & ~kValMask;
+    const unsigned inc = __ballot_sync(0xffffffffu, f == kFlagInc);
+    const unsigned wait = __ballot_sync(0xffffffffu, f == 0);
+    const int last = inc ? __ffs(inc) - 1 : 31;  // lanes 0..last are needed
+    const unsigned need = last == 31 ? 0xffffffffu : (2u << last) - 1u;
+    if (wait & need) {
       if (++spins > kSpinLimit) {
-        atomicOr(err, DERR_TIMEOUT);
+        if (lane == 0) atomicOr(err, DERR_TIMEOUT);
         break;
       }
       continue;
     }
-    excl += w & kValMask;
-    if (f == kFlagInc) break;
-    --j;
+    unsigned long long v = lane <= last ? (w & kValMask) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    excl += v;
+    if (inc) break;
+    j -= 32;
   }
-  st_release_u64(lb + tile, kFlagInc | (excl + agg));
+  if (lane == 0) st_release_u64(lb + tile, kFlagInc | (excl + agg));
   return excl;
 }
 
@@ -83,7 +95,10 @@ __global__ void __launch_bounds__(kBlock) k_scan_excl(const uint32_t* __restrict
   for (int i = 0; i < kIpt; ++i) sum += v[i];
   unsigned long long tot;
   unsigned long long pre = rs::block_excl_scan(sum, S.ws, &tot);
-  if (t == 0) S.base = lookback_prefix(tile, tot, lb, err);
+  if (t < 32) {
+    const unsigned long long b = lookback_prefix(tile, tot, lb, err);
+    if (t == 0) S.base = b;
+  }
   __syncthreads();
   unsigned long long run = S.base + pre;
   OutT o[kIpt];
@@ -137,7 +152,10 @@ __global__ void __launch_bounds__(kBlock) k_cell_rle(const uint32_t* __restrict_
   }
   unsigned long long tot;
   unsigned long long pre = rs::block_excl_scan(sum, S.ws, &tot);
-  if (t == 0) S.base = lookback_prefix(tile, tot, lb, err);
+  if (t < 32) {
+    const unsigned long long b = lookback_prefix(tile, tot, lb, err);
+    if (t == 0) S.base = b;
+  }
   __syncthreads();
   unsigned long long run = S.base + pre;  // heads before element e0
 #pragma unroll
