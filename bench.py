@@ -275,6 +275,7 @@ def run_hlc(args):
             "pair_tests_per_s": (alg / (stage_ms["ms_pair"] / 1e3)) if alg else None,
             "pair_tests_alg": alg, "pair_tests_executed": tests, "matches": nmatch,
             "band_candidates": stats[-1]["band_candidates"],
+            "band_fp64": stats[-1]["band_fp64"],
             "dense_entries_b": stats[-1]["dense_entries_b"],
             "tile_items": stats[-1]["tile_items"], "tile_entries_a": stats[-1]["tile_entries_a"],
             "plain_form": {"precision": "fp64" if other == hlc.HLC_FP64 else "fp32",

@@ -148,6 +148,9 @@ typedef struct {
   float ms_sort_passes;            /* FP32 complete form: the radix sort's digit
                                       passes alone (both catalogues) */
   uint32_t sort_passes;            /*   and how many passes that was */
+  uint64_t band_fp64;              /* FP32 forms: guard-band candidates the
+                                      float-float separation left undecided,
+                                      finished by the binary64 test */
 } hlc_stats;
 
 typedef struct hlc_plan_s hlc_plan_t;

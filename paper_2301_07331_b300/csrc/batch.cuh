@@ -30,6 +30,7 @@ struct JobDev {
   int L;                 // fine order of the job
   PixConst K;
   double C;              // canonical chord^2 threshold
+  double r_lo, r_hi;     // separations (arcsec) left to the binary64 recheck
   float lo32, hi32;      // guard band
   uint64_t toff;         // first slot of the job's B table
   uint32_t tbase;        // first coarse cell covered (order L - tk)
@@ -469,24 +470,33 @@ __global__ void __launch_bounds__(kThreads) k_brecheck(
     uint64_t band_cap, const uint64_t* __restrict__ keyA, int cell_bits,
     const JobDev* __restrict__ jobs, const double2* __restrict__ rdA,
     const double2* __restrict__ rdB, uint2* rows, unsigned long long* count, uint64_t cap,
-    int* err) {
+    unsigned long long* __restrict__ n64, int* err) {
   uint64_t nb = *nband_dev;
   if (nb > band_cap) nb = band_cap;
+  unsigned long long slow = 0;
   for (uint64_t b0 = (uint64_t)blockIdx.x * kThreads; b0 < nb; b0 += (uint64_t)gridDim.x * kThreads) {
     uint64_t q = b0 + threadIdx.x;
     bool hit = false;
     uint2 p = make_uint2(0u, 0u);
     if (q < nb) {
       p = band[q];
-      double C = jobs[keyA[p.x] >> cell_bits].C;
+      const JobDev* J = jobs + (keyA[p.x] >> cell_bits);
       double2 a = rdA[p.x], b = rdB[p.y];
-      double ax, ay, az, bx, by, bz;
-      c_unitvec(a.x, a.y, &ax, &ay, &az);
-      c_unitvec(b.x, b.y, &bx, &by, &bz);
-      hit = c_chord2(ax, ay, az, bx, by, bz) <= C;
+      const int d = f2_sep_decide(a.x, a.y, b.x, b.y, J->r_lo, J->r_hi);
+      if (d != 0) {
+        hit = d > 0;
+      } else {
+        ++slow;
+        double ax, ay, az, bx, by, bz;
+        c_unitvec(a.x, a.y, &ax, &ay, &az);
+        c_unitvec(b.x, b.y, &bx, &by, &bz);
+        hit = c_chord2(ax, ay, az, bx, by, bz) <= J->C;
+      }
     }
     warp_emit(hit, p.x, p.y, rows, count, cap, err);
   }
+  for (int o = 16; o > 0; o >>= 1) slow += __shfl_down_sync(0xffffffffu, slow, o);
+  if ((threadIdx.x & 31) == 0 && slow && n64) atomicAdd(n64, slow);
 }
 
 // Rows of a batched match: ids, separation, job; bucket = (job, id_a bits).

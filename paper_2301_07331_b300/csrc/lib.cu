@@ -290,7 +290,8 @@ struct PinnedBuf {
 };
 
 enum Ctr { C_ROWS = 0, C_BAND, C_TESTS, C_DUPS, C_M, C_TOTAL, C_HEADS_A, C_HEADS_B, C_DENSE,
-           C_WORK, C_IDDIFF, C_MAXB, C_SLOW, C_LHITS, C_LLOOK, C_LMAXERR, C_SCRATCH, C_N };
+           C_WORK, C_IDDIFF, C_MAXB, C_SLOW, C_LHITS, C_LLOOK, C_LMAXERR, C_SCRATCH, C_BAND64,
+           C_N };
 
 }  // namespace hlc
 
@@ -301,6 +302,7 @@ struct hlc_plan_s {
   hlc::Arena* out = nullptr;     // last result
   hlc::CatDev A, B;
   double C = 0;
+  double r_lo = 0, r_hi = 0;  // separations left to the binary64 recheck
   float lo32 = 0, hi32 = 0;
   int join_level = 0;
   int nslot = 9;
@@ -861,6 +863,7 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   P->table_buckets = p->boundary == HLC_COMPLETE8 && p->precision == HLC_FP32_GUARD &&
                      p->index != HLC_INDEX_LEARNED;
   P->C = chord2_threshold(p->radius_arcsec);
+  f2_sep_window(p->radius_arcsec, &P->r_lo, &P->r_hi);
   double G = fp32_guard_band(P->C, kUnitVecErr);
   P->lo32 = (float)(P->C - G);
   P->hi32 = (float)(P->C + G);
@@ -1224,8 +1227,8 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
     // (the table-cell form's rows already hold source indices)
     k_recheck<<<grid_for(h[C_BAND], kThreads, 148u * 16u), kThreads, 0, st>>>(
         band, P->ctr + C_BAND, bcap, P->table_buckets ? nullptr : A.idx,
-        P->table_buckets ? nullptr : B.idx, A.rec, B.rec, P->C, rows, P->ctr + C_ROWS, cap,
-        P->dev_err);
+        P->table_buckets ? nullptr : B.idx, A.rec, B.rec, P->C, P->r_lo, P->r_hi, rows,
+        P->ctr + C_ROWS, cap, P->ctr + C_BAND64, P->dev_err);
     HLC_LAUNCH_CHECK();
   }
   ev_record(P, 5);
@@ -1282,6 +1285,8 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
     ar.drop(boff);
   }
   ev_record(P, 6);
+  unsigned long long band64 = 0;
+  HLC_CUDA(cudaMemcpyAsync(&band64, P->ctr + C_BAND64, 8, cudaMemcpyDeviceToHost, st));
   HLC_CUDA(cudaStreamSynchronize(st));
   HLC_TRY(check_dev_err(P->dev_err, st, "hlc_match"));
   res->n = M;
@@ -1293,6 +1298,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   P->stats.pair_tests = h[C_TESTS];
   if (!P->table_buckets) P->stats.cells_a = h[C_HEADS_A];  // counted by the pair test
   P->stats.band_candidates = fp32 ? h[C_BAND] : 0;
+  P->stats.band_fp64 = fp32 ? band64 : 0;
   P->stats.matches = M;
   P->stats.quad_duplicates = h[C_DUPS];
   P->stats.learned_hit_rate = h[C_LLOOK] ? (double)h[C_LHITS] / (double)h[C_LLOOK] : 0.0;
@@ -1501,6 +1507,7 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
     maxL = std::max(maxL, J[j].L);
     J[j].K = pix_const(J[j].L);
     J[j].C = chord2_threshold(p[j].radius_arcsec);
+    f2_sep_window(p[j].radius_arcsec, &J[j].r_lo, &J[j].r_hi);
     double G = fp32_guard_band(J[j].C, kUnitVecErr);
     float lo = (float)(J[j].C - G), hi = (float)(J[j].C + G);
     if ((double)lo > J[j].C - G) lo = nextafterf(lo, 0.0f);
@@ -1849,7 +1856,7 @@ static int match_batched(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   if (fp32 && h[C_BAND]) {
     k_brecheck<<<grid_for(h[C_BAND], kThreads, 148u * 16u), kThreads, 0, st>>>(
         band, P->ctr + C_BAND, bcap, P->keyA64, P->cell_bits, P->jobs_d, A.rd, B.rd, rows,
-        P->ctr + C_ROWS, cap, P->dev_err);
+        P->ctr + C_ROWS, cap, P->ctr + C_BAND64, P->dev_err);
     HLC_LAUNCH_CHECK();
   }
   ev_record(P, 5);
@@ -1898,6 +1905,8 @@ static int match_batched(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   ar.drop(bhist);
   ar.drop(boff);
   ev_record(P, 6);
+  unsigned long long band64 = 0;
+  HLC_CUDA(cudaMemcpyAsync(&band64, P->ctr + C_BAND64, 8, cudaMemcpyDeviceToHost, st));
   HLC_CUDA(cudaStreamSynchronize(st));
   HLC_TRY(check_dev_err(P->dev_err, st, "hlc_match"));
   res->n = M;
@@ -1908,6 +1917,7 @@ static int match_batched(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   res->on_device = 1;
   P->stats.pair_tests = h[C_TESTS];
   P->stats.band_candidates = fp32 ? h[C_BAND] : 0;
+  P->stats.band_fp64 = fp32 ? band64 : 0;
   P->stats.matches = M;
   P->stats.ms_candidates = 0;
   P->stats.ms_pair = ev_ms(P, 3, 4);
@@ -2481,6 +2491,7 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
     if (G) {
       agg.pair_tests += gs.pair_tests;
       agg.band_candidates += gs.band_candidates;
+      agg.band_fp64 += gs.band_fp64;
       agg.entries_b += gs.entries_b;
       agg.ms_prep += gs.ms_prep;
       agg.ms_sort += gs.ms_sort;

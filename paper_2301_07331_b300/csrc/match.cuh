@@ -567,15 +567,19 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
   }
 }
 
-// Binary64 decision for guard-band candidates (both vectors recomputed in
-// the canonical arithmetic from the original coordinates).
+// Decision for guard-band candidates: the float-float separation decides
+// where it is certain (f2_sep_decide); the rest take the binary64 test with
+// both vectors recomputed in the canonical arithmetic from the original
+// coordinates (counted in n64).
 __global__ void __launch_bounds__(kThreads) k_recheck(
     const uint2* __restrict__ band, const unsigned long long* __restrict__ nband_dev,
     uint64_t band_cap, const uint32_t* __restrict__ idxA, const uint32_t* __restrict__ idxB,
-    const SrcRec* __restrict__ recA, const SrcRec* __restrict__ recB, double C, uint2* rows,
-    unsigned long long* count, uint64_t cap, int* err) {
+    const SrcRec* __restrict__ recA, const SrcRec* __restrict__ recB, double C, double r_lo,
+    double r_hi, uint2* rows, unsigned long long* count, uint64_t cap,
+    unsigned long long* __restrict__ n64, int* err) {
   uint64_t nb = *nband_dev;
   if (nb > band_cap) nb = band_cap;
+  unsigned long long slow = 0;
   for (uint64_t b0 = (uint64_t)blockIdx.x * kThreads; b0 < nb; b0 += (uint64_t)gridDim.x * kThreads) {
     uint64_t q = b0 + threadIdx.x;
     bool hit = false;
@@ -583,13 +587,21 @@ __global__ void __launch_bounds__(kThreads) k_recheck(
     if (q < nb) {
       p = band[q];  // entry indices, or source indices when idxA/idxB are null
       SrcRec a = recA[idxA ? idxA[p.x] : p.x], b = recB[idxB ? idxB[p.y] : p.y];
-      double ax, ay, az, bx, by, bz;
-      c_unitvec(a.ra, a.dec, &ax, &ay, &az);
-      c_unitvec(b.ra, b.dec, &bx, &by, &bz);
-      hit = c_chord2(ax, ay, az, bx, by, bz) <= C;
+      const int d = f2_sep_decide(a.ra, a.dec, b.ra, b.dec, r_lo, r_hi);
+      if (d != 0) {
+        hit = d > 0;
+      } else {
+        ++slow;
+        double ax, ay, az, bx, by, bz;
+        c_unitvec(a.ra, a.dec, &ax, &ay, &az);
+        c_unitvec(b.ra, b.dec, &bx, &by, &bz);
+        hit = c_chord2(ax, ay, az, bx, by, bz) <= C;
+      }
     }
     warp_emit(hit, p.x, p.y, rows, count, cap, err);
   }
+  for (int o = 16; o > 0; o >>= 1) slow += __shfl_down_sync(0xffffffffu, slow, o);
+  if ((threadIdx.x & 31) == 0 && slow && n64) atomicAdd(n64, slow);
 }
 
 // Highest differing bit of the source ids (OR of id ^ id[0]).

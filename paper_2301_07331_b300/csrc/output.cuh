@@ -58,43 +58,6 @@ __device__ __forceinline__ double sep_arcsec_haversine(double ra1, double dec1, 
   return 2.0 * as * (648000.0 / 3.141592653589793238462643);
 }
 
-// Separation of two nearby sources (ra in [0, 360)) in float-float arithmetic
-// on the FP32 pipe: haversine form with the angle differences formed exactly
-// from the split binary64 inputs and cos(Dec) to ~3e-8 relative, so the
-// relative error of the result is below 1e-7 (5e-7 arcsec at 5 arcsec).
-// Returns a negative value when the pair is not "nearby" (differences above
-// 20 arcsec), in which case the caller uses the binary64 unit vectors.
-__device__ __forceinline__ double sep_arcsec_f2(double ra1, double dec1, double ra2,
-                                                double dec2) {
-  f2 a1 = split_f64(ra1), d1 = split_f64(dec1), a2 = split_f64(ra2), d2 = split_f64(dec2);
-  f2 dd = f2_add(d2, f2{-d1.hi, -d1.lo});
-  f2 da = f2_add(a2, f2{-a1.hi, -a1.lo});
-  if (da.hi > 180.f) da = f2_add(da, f2{-360.f, 0.f});
-  if (da.hi < -180.f) da = f2_add(da, f2{360.f, 0.f});
-  const float lim = 20.0f / 3600.0f;
-  if (fabsf(dd.hi) > lim || fabsf(da.hi) > lim) return -1.0;
-  f2 c1 = f2_cos_deg(d1), c2 = f2_cos_deg(d2);
-  f2 K = f2_mul(c1, c2);
-  const f2 HR = {8.726646192e-3f, 6.759980075e-11f};  // pi/360 as a float pair
-  f2 x = f2_mul(dd, HR), y = f2_mul(da, HR);         // half differences, radians
-  // sin of the half differences: x - x^3/6 (x <= 5e-5 rad: next term < 1e-19)
-  f2 sx = f2_add(x, f2{-x.hi * x.hi * x.hi * (1.0f / 6.0f), 0.f});
-  f2 sy = f2_add(y, f2{-y.hi * y.hi * y.hi * (1.0f / 6.0f), 0.f});
-  f2 hav = f2_add(f2_mul(sx, sx), f2_mul(K, f2_mul(sy, sy)));
-  // v = sqrt(hav) with one float-float Newton correction
-  float v0 = sqrtf(hav.hi);
-  f2 v = {v0, 0.f};
-  if (v0 > 0.f) {
-    f2 sq = f2_mul(v, v);
-    f2 rem = f2_add(hav, f2{-sq.hi, -sq.lo});
-    v = fast_two_sum(v0, rem.hi / (2.0f * v0));
-  }
-  // asin(v) = v + v^3/6 (+ 3v^5/40 < 1e-22 relative here)
-  f2 as = f2_add(v, f2{v.hi * v.hi * v.hi * (1.0f / 6.0f), 0.f});
-  const f2 SC = {412529.625f, -1.2505806983e-2f};  // 2 * 648000 / pi as a float pair
-  f2 r = f2_mul(as, SC);
-  return (double)r.hi + (double)r.lo;
-}
 
 // One output row in 32 bytes (one sector), used while the rows are ordered.
 struct __align__(32) OutRow {

@@ -115,6 +115,45 @@ def test_pairs_a_hair_from_the_radius(prec):
     assert 0.3 * n < want["id_a"].size < n
 
 
+@pytest.mark.parametrize("r", [0.1, 1.5, 5.0, 15.0])
+def test_guard_band_decisions_near_the_radius(r):
+    """Pairs at r (1 + eps), |eps| log-uniform in [1e-8, 1e-3] (a fifth of
+    them within a decade above the float-float window, 1e-6 r + 1e-7 arcsec),
+    a tenth of them within 0.15 deg of a pole: the FP32 form (FP32 test,
+    float-float recheck, binary64 for the undecided) must give the oracle's
+    rows, and the float-float step must decide most candidates."""
+    rng = np.random.default_rng(int(r * 100) + 5)
+    n = 200_000
+    ra = rng.uniform(0, 360, n)
+    dec = np.degrees(np.arcsin(rng.uniform(-0.999, 0.999, n)))
+    polar = rng.random(n) < 0.1
+    dec[polar] = rng.choice([-1.0, 1.0], polar.sum()) * rng.uniform(89.85, 89.95, polar.sum())
+    eps = np.exp(rng.uniform(np.log(1e-8), np.log(1e-3), n)) * rng.choice([-1.0, 1.0], n)
+    pa = rng.uniform(0, 2 * math.pi, n)
+    dist = np.radians(r * (1 + eps) / 3600)
+    d0 = np.radians(dec)
+    d1 = np.arcsin(np.sin(d0) * np.cos(dist) + np.cos(d0) * np.sin(dist) * np.cos(pa))
+    a1 = np.radians(ra) + np.arctan2(np.sin(pa) * np.sin(dist) * np.cos(d0),
+                                     np.cos(dist) - np.sin(d0) * np.sin(d1))
+    ra_b, dec_b = np.mod(np.degrees(a1), 360), np.degrees(d1)
+    ids = np.arange(n, dtype=np.uint64)
+    L = 12 if r < 10 else 10
+    want, st = _check((ra, dec, ids), (ra_b, dec_b, ids), r, L, hlc.HLC_COMPLETE8,
+                      hlc.HLC_FP32_GUARD)
+    # (half the placed pairs match; the crowded polar rings add neighbours)
+    assert want["id_a"].size > 0.4 * n
+    assert st["band_candidates"] > 0.5 * n
+    # binary64 is left with the pairs inside the window (here counted with
+    # twice its width), near a pole, or not "nearby" (RA or Dec difference
+    # above 20 arcsec), and with no others
+    m = 1e-6 * r + 1e-7
+    dra = np.abs(np.mod(ra_b - ra + 180.0, 360.0) - 180.0)
+    undecidable = ((np.abs(eps) * r <= 2 * m) | (np.abs(dec) > 89.9) | (np.abs(dec_b) > 89.9)
+                   | (dra > 20 / 3600) | (np.abs(dec_b - dec) > 20 / 3600))
+    # (slack: the polar rings' own neighbour pairs inside the FP32 band)
+    assert st["band_fp64"] <= undecidable.sum() + 0.05 * n
+
+
 @pytest.mark.parametrize("prec", [hlc.HLC_FP64, hlc.HLC_FP32_GUARD])
 def test_torch_allocator_callback(prec):
     A, B = synth.patch_pair(na=8000, nb=8000)
