@@ -499,7 +499,22 @@ __global__ void __launch_bounds__(kThreads) k_brecheck(
   if ((threadIdx.x & 31) == 0 && slow && n64) atomicAdd(n64, slow);
 }
 
-// Rows of a batched match: ids, separation, job; bucket = (job, id_a bits).
+// Rows per job (lanes of a warp that share a job add once).
+__global__ void k_job_rows(const uint2* __restrict__ rows, uint64_t M,
+                           const uint64_t* __restrict__ keyA, int cell_bits,
+                           uint32_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  for (uint64_t m0 = (uint64_t)blockIdx.x * blockDim.x; m0 < M;
+       m0 += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t m = m0 + threadIdx.x;
+    const bool live = m < M;
+    const uint32_t j = live ? (uint32_t)(keyA[rows[m].x] >> cell_bits) : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xffffffffu, j);
+    if (live && lane == __ffs(peers) - 1) atomicAdd(&cnt[j], (uint32_t)__popc(peers));
+  }
+}
+
+// Rows of a batched match: ids, separation, job; bucket from the job table.
 template <bool FP32>
 __global__ void k_brows(const uint2* __restrict__ rows, uint64_t M,
                         const uint64_t* __restrict__ keyA, int cell_bits,
@@ -508,8 +523,8 @@ __global__ void k_brows(const uint2* __restrict__ rows, uint64_t M,
                         const double* __restrict__ azv, const double* __restrict__ bxv,
                         const double* __restrict__ byv, const double* __restrict__ bzv,
                         const double2* __restrict__ rdA, const double2* __restrict__ rdB,
-                        int want_sep, OutRow* __restrict__ out, int nb, int bshift,
-                        uint32_t bmask, uint32_t* __restrict__ bhist) {
+                        int want_sep, OutRow* __restrict__ out, const uint4* __restrict__ jb,
+                        uint32_t* __restrict__ bhist) {
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
        m += (uint64_t)gridDim.x * blockDim.x) {
     uint2 p = rows[m];
@@ -520,7 +535,7 @@ __global__ void k_brows(const uint2* __restrict__ rows, uint64_t M,
     o.pad = 0;
     o.s = 0.0;
     if (bhist)  // the row's rank in its bucket, for the scatter
-      o.pad = atomicAdd(&bhist[((uint64_t)o.job << nb) | ((uint32_t)(o.a >> bshift) & bmask)], 1u);
+      o.pad = atomicAdd(&bhist[row_bucket(o, 0, 0u, jb)], 1u);
     if (want_sep) {
       double sv;
       if (FP32) {

@@ -1011,14 +1011,15 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
 
 // Orders M packed rows by (job, id_a, id_b, sep) into result columns: the
 // bucket scatter + per-bucket sorts, or two or three stable radix sorts when
-// a bucket would not fit in shared memory.  nb_job < 0: single job.
+// a bucket would not fit in shared memory.  jbk null: single job; else the
+// batched plan's per-job bucket table (row_bucket).
 static int order_rows(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_t* bhist,
-                      uint32_t* boff, uint64_t nbk, int nb_job, int bshift, uint32_t bmask,
+                      uint32_t* boff, uint64_t nbk, const uint4* jbk, int bshift, uint32_t bmask,
                       bool bucketed, bool want_sep, uint64_t** oa, uint64_t** ob, double** os,
                       uint32_t** oj) {
   Arena& ar = *P->out;
   cudaStream_t st = plan_stream(P);
-  const bool batched = nb_job >= 0;
+  const bool batched = jbk != nullptr;
   uint64_t* a = ar.get_n<uint64_t>(M + 1);
   uint64_t* b = ar.get_n<uint64_t>(M + 1);
   double* sp = want_sep ? ar.get_n<double>(M + 1) : nullptr;
@@ -1045,9 +1046,9 @@ static int order_rows(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_t* bhist
     if (!scr || !t || !big) return HLC_ENOMEM;
     HLC_TRY(scan_exclusive<uint32_t>(bhist, boff, nbk + 1, P->ctr + C_TOTAL, scr, P->dev_err, st));
     HLC_CUDA(cudaMemsetAsync(P->ctr + C_MAXB, 0, 8, st));
-    k_bucket_scatter<<<g, kThreads, 0, st>>>(rows32, M, bshift, bmask, nb_job, boff, t);
+    k_bucket_scatter<<<g, kThreads, 0, st>>>(rows32, M, bshift, bmask, jbk, boff, t);
     HLC_LAUNCH_CHECK();
-    k_bucket_small<<<g, kThreads, 0, st>>>(t, M, bshift, bmask, nb_job, boff, a, b, sp, jb, big,
+    k_bucket_small<<<g, kThreads, 0, st>>>(t, M, bshift, bmask, jbk, boff, a, b, sp, jb, big,
                                            (uint32_t*)(P->ctr + C_MAXB), P->dev_err);
     HLC_LAUNCH_CHECK();
     k_bucket_sort<<<148u * 8u, kBucketThreads, 0, st>>>(t, boff, big,
@@ -1095,11 +1096,11 @@ static int order_rows(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_t* bhist
 // order_rows, then (after the stream has drained) a repeat with the radix
 // sorts when a bucket was too large for the in-block sort.
 static int order_rows_checked(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_t* bhist,
-                              uint32_t* boff, uint64_t nbk, int nb_job, int bshift,
+                              uint32_t* boff, uint64_t nbk, const uint4* jbk, int bshift,
                               uint32_t bmask, bool bucketed, bool want_sep, uint64_t** oa,
                               uint64_t** ob, double** os, uint32_t** oj) {
   cudaStream_t st = plan_stream(P);
-  HLC_TRY(order_rows(P, rows32, M, bhist, boff, nbk, nb_job, bshift, bmask, bucketed, want_sep,
+  HLC_TRY(order_rows(P, rows32, M, bhist, boff, nbk, jbk, bshift, bmask, bucketed, want_sep,
                      oa, ob, os, oj));
   int h = 0;
   HLC_CUDA(cudaMemcpyAsync(&h, P->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1110,7 +1111,7 @@ static int order_rows_checked(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_
     if (q) ar.drop(q);
   h &= ~DERR_BUCKET;
   HLC_CUDA(cudaMemcpyAsync(P->dev_err, &h, sizeof(int), cudaMemcpyHostToDevice, st));
-  HLC_TRY(order_rows(P, rows32, M, bhist, boff, nbk, nb_job, bshift, bmask, false, want_sep, oa,
+  HLC_TRY(order_rows(P, rows32, M, bhist, boff, nbk, jbk, bshift, bmask, false, want_sep, oa,
                      ob, os, oj));
   HLC_CUDA(cudaStreamSynchronize(st));
   return HLC_OK;
@@ -1277,7 +1278,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   uint64_t *oa = nullptr, *ob = nullptr;
   double* os = nullptr;
   uint32_t* oj = nullptr;
-  HLC_TRY(order_rows_checked(P, rows32, M, bhist, boff, nbk, -1, bshift, bmask, bucketed,
+  HLC_TRY(order_rows_checked(P, rows32, M, bhist, boff, nbk, nullptr, bshift, bmask, bucketed,
                              want_sep, &oa, &ob, &os, &oj));
   ar.drop(rows32);
   if (bhist) {
@@ -1869,29 +1870,52 @@ static int match_batched(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   const bool want_sep = P->p.want_sep != 0;
   OutRow* rows32 = ar.get_n<OutRow>(M + 1);
   if (!rows32) return HLC_ENOMEM;
-  // buckets: (job, bits of id_a), about four rows per bucket
-  int hb = P->id_high_bit;
-  int nb = 0;
-  while (nb < 20 && ((uint64_t)P->njobs << (nb + 2)) < M) ++nb;
-  if (nb > hb + 1) nb = std::max(hb + 1, 0);
-  const int bshift = hb >= 0 ? hb + 1 - nb : 0;
-  const uint64_t nbk = (uint64_t)P->njobs << nb;
-  const uint32_t bmask = nb ? ((1u << nb) - 1) : 0u;
+  // buckets: per job, bits of id_a enough for about four rows per bucket
+  // (the jobs' row counts differ by orders of magnitude)
+  const int hb = P->id_high_bit;
+  const uint32_t nj = P->njobs;
+  std::vector<uint32_t> jrows(nj, 0u);
+  if (M) {
+    uint32_t* jcnt = ar.get_n<uint32_t>(nj);
+    if (!jcnt) return HLC_ENOMEM;
+    HLC_CUDA(cudaMemsetAsync(jcnt, 0, nj * 4ull, st));
+    k_job_rows<<<grid_for(M, kThreads), kThreads, 0, st>>>(rows, M, P->keyA64, P->cell_bits,
+                                                           jcnt);
+    HLC_LAUNCH_CHECK();
+    HLC_CUDA(cudaMemcpyAsync(jrows.data(), jcnt, nj * 4ull, cudaMemcpyDeviceToHost, st));
+    HLC_CUDA(cudaStreamSynchronize(st));
+    ar.drop(jcnt);
+  }
+  std::vector<uint4> hjb(nj);
+  uint64_t nbk = 0;
+  for (uint32_t j = 0; j < nj; ++j) {
+    int nb = 0;
+    while (nb < 24 && (jrows[j] >> (nb + 2)) > 0) ++nb;
+    if (nb > hb + 1) nb = std::max(hb + 1, 0);
+    hjb[j] = make_uint4((uint32_t)nbk, hb >= 0 ? (uint32_t)(hb + 1 - nb) : 0u,
+                        nb ? (uint32_t)((1ull << nb) - 1) : 0u, 0u);
+    nbk += 1ull << nb;
+  }
+  if (nbk >= (1ull << 31)) {
+    set_error("batched output: %llu row buckets", (unsigned long long)nbk);
+    return HLC_EINVAL;
+  }
+  uint4* jb = ar.get_n<uint4>(nj);
   uint32_t* bhist = ar.get_n<uint32_t>(nbk + 1);
   uint32_t* boff = ar.get_n<uint32_t>(nbk + 1);
-  if (!bhist || !boff) return HLC_ENOMEM;
+  if (!jb || !bhist || !boff) return HLC_ENOMEM;
+  HLC_CUDA(cudaMemcpyAsync(jb, hjb.data(), nj * sizeof(uint4), cudaMemcpyHostToDevice, st));
   HLC_CUDA(cudaMemsetAsync(bhist, 0, (nbk + 1) * 4, st));
   if (M) {
     unsigned g = grid_for(M, kThreads);
     if (fp32)
       k_brows<true><<<g, kThreads, 0, st>>>(rows, M, P->keyA64, P->cell_bits, A.id_s, B.id_s,
                                              nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                             A.rd, B.rd, want_sep, rows32, nb, bshift, bmask,
-                                             bhist);
+                                             A.rd, B.rd, want_sep, rows32, jb, bhist);
     else
       k_brows<false><<<g, kThreads, 0, st>>>(rows, M, P->keyA64, P->cell_bits, A.id_s, B.id_s,
                                               A.vx, A.vy, A.vz, B.vx, B.vy, B.vz, nullptr,
-                                              nullptr, want_sep, rows32, nb, bshift, bmask, bhist);
+                                              nullptr, want_sep, rows32, jb, bhist);
     HLC_LAUNCH_CHECK();
   }
   ar.drop(rows);
@@ -1899,9 +1923,10 @@ static int match_batched(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   uint64_t *oa = nullptr, *ob = nullptr;
   double* os = nullptr;
   uint32_t* oj = nullptr;
-  HLC_TRY(order_rows_checked(P, rows32, M, bhist, boff, nbk, nb, bshift, bmask, true, want_sep,
-                             &oa, &ob, &os, &oj));
+  HLC_TRY(order_rows_checked(P, rows32, M, bhist, boff, nbk, jb, 0, 0u, true, want_sep, &oa,
+                             &ob, &os, &oj));
   ar.drop(rows32);
+  ar.drop(jb);
   ar.drop(bhist);
   ar.drop(boff);
   ev_record(P, 6);

@@ -126,20 +126,27 @@ __global__ void k_max_u32(const uint32_t* __restrict__ v, uint64_t n, uint32_t* 
 }
 
 // Rows to their buckets: offset of the bucket plus the rank the row drew
-// there (in OutRow.pad) when the histogram was built.
+// there (in OutRow.pad) when the histogram was built.  A single plan's
+// bucket is the bmask bits of id_a above bshift; a batched plan's is
+// jb[job].x (the job's first bucket) plus the bits jb[job].z of id_a above
+// jb[job].y, each job with as many bits as its own row count needs.
 __device__ __forceinline__ uint64_t row_bucket(const OutRow& o, int bshift, uint32_t bmask,
-                                               int nb_job) {
-  return (nb_job >= 0 ? ((uint64_t)o.job << nb_job) : 0ull) |
-         ((uint32_t)(o.a >> bshift) & bmask);
+                                               const uint4* __restrict__ jb) {
+  if (jb) {
+    const uint4 J = __ldg(jb + o.job);
+    return (uint64_t)J.x + ((uint32_t)(o.a >> J.y) & J.z);
+  }
+  return (uint32_t)(o.a >> bshift) & bmask;
 }
 
 __global__ void k_bucket_scatter(const OutRow* __restrict__ in, uint64_t M, int bshift,
-                                 uint32_t bmask, int nb_job, const uint32_t* __restrict__ boff,
+                                 uint32_t bmask, const uint4* __restrict__ jb,
+                                 const uint32_t* __restrict__ boff,
                                  OutRow* __restrict__ out) {
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
        m += (uint64_t)gridDim.x * blockDim.x) {
     OutRow o = in[m];
-    out[__ldg(boff + row_bucket(o, bshift, bmask, nb_job)) + o.pad] = o;
+    out[__ldg(boff + row_bucket(o, bshift, bmask, jb)) + o.pad] = o;
   }
 }
 
@@ -160,7 +167,8 @@ constexpr uint32_t kSmallBucket = 32;
 // k_bucket_sort; one above kBucketCap sets DERR_BUCKET and the host orders
 // the rows another way.)
 __global__ void k_bucket_small(const OutRow* __restrict__ t, uint64_t M, int bshift,
-                               uint32_t bmask, int nb_job, const uint32_t* __restrict__ boff,
+                               uint32_t bmask, const uint4* __restrict__ jb,
+                               const uint32_t* __restrict__ boff,
                                uint64_t* __restrict__ oa, uint64_t* __restrict__ ob,
                                double* __restrict__ os, uint32_t* __restrict__ oj,
                                uint32_t* __restrict__ big, uint32_t* __restrict__ nbig,
@@ -168,7 +176,7 @@ __global__ void k_bucket_small(const OutRow* __restrict__ t, uint64_t M, int bsh
   for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < M;
        p += (uint64_t)gridDim.x * blockDim.x) {
     const OutRow r = t[p];
-    const uint64_t bk = row_bucket(r, bshift, bmask, nb_job);
+    const uint64_t bk = row_bucket(r, bshift, bmask, jb);
     const uint32_t lo = __ldg(boff + bk), hi = __ldg(boff + bk + 1);
     const uint32_t n = hi - lo;
     if (n > kSmallBucket) {
