@@ -141,80 +141,66 @@ __global__ void k_bpayload(const JobDev* __restrict__ jobs, const uint64_t* __re
 
 // Autotuner inputs, per job: the sum of the B unit vectors (FP32) and, in a
 // second pass, the smallest cosine between a B source and the job's mean
-// direction -- the spherical cap the job's B catalogue occupies.
-// Sum (or maximum) over the lanes of a warp that share a job, entries of a
-// job being contiguous: after the loop the first lane of each run of equal
-// jobs holds the run's total, so a warp issues one atomic per job it touches.
-template <bool MAX>
-__device__ __forceinline__ float seg_reduce(float v, uint32_t j, int lane) {
+// direction -- the spherical cap the job's B catalogue occupies.  One warp
+// per job reads an evenly spaced sample of at most about kCapSamples of its
+// B sources (the estimate only picks the job's order).
+constexpr uint64_t kCapSamples = 1024;
+
+__device__ __forceinline__ float4 job_b_vec(const JobDev& J, uint64_t l) {
+  double a = J.ra[1][l], d = J.dec[1][l];
+  if (!(bits_finite(a) && bits_abs_le(d, 90.0))) return make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!bits_in_ra_range(a)) a = c_norm_ra(a);
+  return fp32_unitvec(a, d);
+}
+
+__global__ void k_bjob_mean(const JobDev* __restrict__ jobs, uint32_t njobs,
+                            float* __restrict__ acc) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t j = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < njobs; j += nw) {
+    const JobDev& J = jobs[j];
+    const uint64_t n = J.n[1];
+    const uint64_t step = n > kCapSamples ? n / kCapSamples : 1;
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    for (uint64_t l = lane * step; l < n; l += 32 * step) {
+      const float4 u = job_b_vec(J, l);
+      sx += u.x;
+      sy += u.y;
+      sz += u.z;
+    }
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const float y = __shfl_down_sync(0xffffffffu, v, o);
-    const uint32_t jo = __shfl_down_sync(0xffffffffu, j, o);
-    if (lane + o < 32 && jo == j) v = MAX ? fmaxf(v, y) : v + y;
-  }
-  return v;
-}
-
-__device__ __forceinline__ bool seg_head(uint32_t j, int lane) {
-  const uint32_t jp = __shfl_up_sync(0xffffffffu, j, 1);
-  return lane == 0 || jp != j;
-}
-
-__global__ void k_bjob_mean(const JobDev* __restrict__ jobs, const uint64_t* __restrict__ off,
-                            uint32_t njobs, uint64_t total, float* __restrict__ acc) {
-  const int lane = threadIdx.x & 31;
-  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < total;
-       i0 += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t i = i0 + threadIdx.x;
-    uint32_t j = 0xFFFFFFFFu;
-    float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (i < total) {
-      j = job_of(off, njobs, i);
-      const JobDev& J = jobs[j];
-      uint64_t l = i - J.off[1];
-      double a = J.ra[1][l], d = J.dec[1][l];
-      if (bits_finite(a) && bits_abs_le(d, 90.0)) {
-        if (!bits_in_ra_range(a)) a = c_norm_ra(a);
-        u = fp32_unitvec(a, d);
-      }
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      sz += __shfl_xor_sync(0xffffffffu, sz, o);
     }
-    const float sx = seg_reduce<false>(u.x, j, lane);
-    const float sy = seg_reduce<false>(u.y, j, lane);
-    const float sz = seg_reduce<false>(u.z, j, lane);
-    if (j != 0xFFFFFFFFu && seg_head(j, lane)) {
-      atomicAdd(acc + 3 * j, sx);
-      atomicAdd(acc + 3 * j + 1, sy);
-      atomicAdd(acc + 3 * j + 2, sz);
+    if (lane == 0) {
+      acc[3 * j] = sx;
+      acc[3 * j + 1] = sy;
+      acc[3 * j + 2] = sz;
     }
   }
 }
 
-// (mind: a float's bit pattern orders like the value for non-negative
-// floats; 1 - cos is stored, so the maximum is taken with integer atomics)
-__global__ void k_bjob_cap(const JobDev* __restrict__ jobs, const uint64_t* __restrict__ off,
-                           uint32_t njobs, uint64_t total, const float* __restrict__ dir,
-                           unsigned int* __restrict__ cap) {
+// (1 - cos, the largest over the sample, as float bits)
+__global__ void k_bjob_cap(const JobDev* __restrict__ jobs, uint32_t njobs,
+                           const float* __restrict__ dir, unsigned int* __restrict__ cap) {
   const int lane = threadIdx.x & 31;
-  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < total;
-       i0 += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t i = i0 + threadIdx.x;
-    uint32_t j = 0xFFFFFFFFu;
-    float om = 0.0f;
-    if (i < total) {
-      j = job_of(off, njobs, i);
-      const JobDev& J = jobs[j];
-      uint64_t l = i - J.off[1];
-      double a = J.ra[1][l], d = J.dec[1][l];
-      if (bits_finite(a) && bits_abs_le(d, 90.0)) {
-        if (!bits_in_ra_range(a)) a = c_norm_ra(a);
-        float4 u = fp32_unitvec(a, d);
-        float c = u.x * dir[3 * j] + u.y * dir[3 * j + 1] + u.z * dir[3 * j + 2];
-        om = fmaxf(1.0f - c, 0.0f);
-      }
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t j = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < njobs; j += nw) {
+    const JobDev& J = jobs[j];
+    const uint64_t n = J.n[1];
+    const uint64_t step = n > kCapSamples ? n / kCapSamples : 1;
+    const float dx = dir[3 * j], dy = dir[3 * j + 1], dz = dir[3 * j + 2];
+    float om = 0.f;
+    for (uint64_t l = lane * step; l < n; l += 32 * step) {
+      const float4 u = job_b_vec(J, l);
+      if (u.x == 0.f && u.y == 0.f && u.z == 0.f) continue;  // invalid input
+      om = fmaxf(om, fmaxf(1.0f - (u.x * dx + u.y * dy + u.z * dz), 0.0f));
     }
-    const float m = seg_reduce<true>(om, j, lane);
-    if (j != 0xFFFFFFFFu && seg_head(j, lane)) atomicMax(cap + j, __float_as_uint(m));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) om = fmaxf(om, __shfl_xor_sync(0xffffffffu, om, o));
+    if (lane == 0) cap[j] = __float_as_uint(om);
   }
 }
 

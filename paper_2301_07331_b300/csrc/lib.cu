@@ -1467,7 +1467,7 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
     if (!acc || !cap) return fail(HLC_ENOMEM);
     cudaMemsetAsync(acc, 0, (3 * njobs + 3) * 4, st);
     cudaMemsetAsync(cap, 0, (njobs + 1) * 4, st);
-    k_bjob_mean<<<grid_for(NB, kThreads), kThreads, 0, st>>>(P->jobs_d, P->offB_d, njobs, NB, acc);
+    k_bjob_mean<<<grid_for(32ull * njobs, kThreads), kThreads, 0, st>>>(P->jobs_d, njobs, acc);
     std::vector<float> h(3 * njobs);
     if (cudaMemcpyAsync(h.data(), acc, 3 * njobs * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
@@ -1482,8 +1482,8 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
       }
     }
     cudaMemcpyAsync(acc, h.data(), 3 * njobs * 4, cudaMemcpyHostToDevice, st);
-    k_bjob_cap<<<grid_for(NB, kThreads), kThreads, 0, st>>>(P->jobs_d, P->offB_d, njobs, NB, acc,
-                                                             cap);
+    k_bjob_cap<<<grid_for(32ull * njobs, kThreads), kThreads, 0, st>>>(P->jobs_d, njobs, acc,
+                                                                        cap);
     std::vector<unsigned> hc(njobs);
     if (cudaMemcpyAsync(hc.data(), cap, njobs * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
