@@ -211,10 +211,13 @@ int hlc_neighbours(const uint32_t* pix, uint64_t n, int order, int64_t* out,
 /* Quad-direction cell set of each source (Algorithm 1): the distinct pixels
  * of (ra, dec), (ra +- R, dec), (ra, dec -+ R), R = r/3600 deg, RA wrapped,
  * Dec clamped, ascending.  out: 5n device uint32 padded with 0xFFFFFFFF;
- * count: n device int32. */
+ * count: n device int32.  precision HLC_FP32_GUARD computes the same sets
+ * through the FP32 pixel estimate (the shifted coordinates in float-float),
+ * each undecided position in binary64.  Returns HLC_EINVAL for a bad order,
+ * radius or precision, or for non-finite RA/Dec or |Dec| > 90. */
 int hlc_quad_cells(const double* ra, const double* dec, uint64_t n,
-                   double radius_arcsec, int order, uint32_t* out,
-                   int32_t* count, void* stream);
+                   double radius_arcsec, int order, int precision,
+                   uint32_t* out, int32_t* count, void* stream);
 
 /* Unit vectors (3n device doubles, interleaved x,y,z) in the binary64
  * arithmetic stated above. */

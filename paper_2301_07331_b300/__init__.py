@@ -111,7 +111,7 @@ def lib():
     L.hlc_canonical_coefficients.argtypes = [P, P]
     L.hlc_ang2pix.argtypes = [P, P, u64, i32, i32, P, P]
     L.hlc_neighbours.argtypes = [P, u64, i32, P, P]
-    L.hlc_quad_cells.argtypes = [P, P, u64, d, i32, P, P, P]
+    L.hlc_quad_cells.argtypes = [P, P, u64, d, i32, i32, P, P, P]
     L.hlc_unitvec.argtypes = [P, P, u64, P, P]
     L.hlc_sort_pairs.argtypes = [P, P, u64, i32, i32, P]
     L.hlc_sort_pairs_noalloc.argtypes = [P, P, u64, i32, i32, P]
@@ -379,12 +379,13 @@ def hlc_neighbours(pix: torch.Tensor, order: int, stream=None) -> torch.Tensor:
     return out
 
 
-def hlc_quad_cells(ra, dec, radius_arcsec: float, order: int, stream=None):
+def hlc_quad_cells(ra, dec, radius_arcsec: float, order: int, precision: int = HLC_FP64,
+                   stream=None):
     _require_cuda()
     out = torch.empty((ra.numel(), 5), dtype=torch.int32, device=ra.device)
     cnt = torch.empty(ra.numel(), dtype=torch.int32, device=ra.device)
     _check(lib().hlc_quad_cells(_dptr(ra), _dptr(dec), ra.numel(), float(radius_arcsec),
-                                int(order), _dptr(out) if out.numel() else None,
+                                int(order), int(precision), _dptr(out) if out.numel() else None,
                                 _dptr(cnt) if cnt.numel() else None, _stream_ptr(stream)))
     return out, cnt
 

@@ -134,26 +134,38 @@ __device__ __forceinline__ uint32_t g_ang2pix(double ra, double dec, int order,
   return c_ang2pix(ra, dec, order);
 }
 
-// Quad-direction cells (Algorithm 1) through the guarded pixel function.  The
-// shifted coordinates are formed exactly as in the binary64 statement.
-// Returns the number of cells, or 0 when some pixel needs the binary64 path.
-__device__ __forceinline__ int g_quad_cells(double ra, double dec, double R, int order,
-                                            const PixConst& K, uint32_t out[5]) {
-  double dp_ = __dadd_rn(dec, R);
-  if (dp_ > 90.0) dp_ = 90.0;
-  double dm_ = __dsub_rn(dec, R);
-  if (dm_ < -90.0) dm_ = -90.0;
-  FastDec f0 = f_dec_part(split_f64(dec));
-  FastDec fm = f_dec_part(split_f64(dm_));
-  FastDec fp = f_dec_part(split_f64(dp_));
-  uint32_t p[5];
-  f2 r0 = split_f64(ra);
-  bool ok = f_pix(r0, f0, order, K, &p[0]);
-  ok = ok && f_pix(split_f64(wrap_ra(__dadd_rn(ra, R))), f0, order, K, &p[1]);
-  ok = ok && f_pix(split_f64(wrap_ra(__dsub_rn(ra, R))), f0, order, K, &p[2]);
-  ok = ok && f_pix(r0, fm, order, K, &p[3]);
-  ok = ok && f_pix(r0, fp, order, K, &p[4]);
-  if (!ok) return 0;
+// Quad-direction positions (Algorithm 1) through the guarded pixel function:
+// the source and its copies at ra + R, ra - R (wrapped), dec - R, dec + R
+// (clamped to the poles), in that order.  The shifted coordinates are formed
+// in float-float: within about 2e-11 deg of the binary64 statement's values,
+// far inside the guard margins, so a decided pixel is the canonical one;
+// a shifted RA whose leading float is not in [0, 360) (a wrap at the RA = 0
+// face boundary) is left undecided.  Writes the pixel of every decided
+// position to p[0..4] and returns the mask of the undecided ones.
+__device__ __forceinline__ unsigned g_quad_pos(double ra, double dec, f2 Rd, int order,
+                                               const PixConst& K, uint32_t p[5]) {
+  const f2 r0 = split_f64(ra), d0 = split_f64(dec);
+  const f2 Rn = {-Rd.hi, -Rd.lo};
+  f2 dp = f2_add(d0, Rd);
+  if (dp.hi > 90.f || (dp.hi == 90.f && dp.lo > 0.f)) dp = f2{90.f, 0.f};
+  f2 dm = f2_add(d0, Rn);
+  if (dm.hi < -90.f || (dm.hi == -90.f && dm.lo < 0.f)) dm = f2{-90.f, 0.f};
+  f2 rp = f2_add(r0, Rd);
+  if (rp.hi > 360.f || (rp.hi == 360.f && rp.lo >= 0.f)) rp = f2_add(rp, f2{-360.f, 0.f});
+  f2 rm = f2_add(r0, Rn);
+  if (rm.hi < 0.f || (rm.hi == 0.f && rm.lo < 0.f)) rm = f2_add(rm, f2{360.f, 0.f});
+  const FastDec f0 = f_dec_part(d0), fm = f_dec_part(dm), fp = f_dec_part(dp);
+  unsigned und = 0;
+  if (!f_pix(r0, f0, order, K, &p[0])) und |= 1u;
+  if (!(rp.hi >= 0.f && rp.hi < 360.f) || !f_pix(rp, f0, order, K, &p[1])) und |= 2u;
+  if (!(rm.hi >= 0.f && rm.hi < 360.f) || !f_pix(rm, f0, order, K, &p[2])) und |= 4u;
+  if (!f_pix(r0, fm, order, K, &p[3])) und |= 8u;
+  if (!f_pix(r0, fp, order, K, &p[4])) und |= 16u;
+  return und;
+}
+
+// Distinct values of p[0..4], ascending, into out; returns their number.
+__device__ __forceinline__ int quad_sort_unique(uint32_t p[5], uint32_t out[5]) {
 #pragma unroll
   for (int i = 1; i < 5; ++i) {
     uint32_t v = p[i];

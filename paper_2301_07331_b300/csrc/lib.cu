@@ -2784,10 +2784,12 @@ int hlc_neighbours(const uint32_t* pix, uint64_t n, int order, int64_t* out, voi
 }
 
 int hlc_quad_cells(const double* ra, const double* dec, uint64_t n, double radius_arcsec,
-                   int order, uint32_t* out, int32_t* count, void* stream) {
+                   int order, int precision, uint32_t* out, int32_t* count, void* stream) {
   clear_error();
-  if (order < 0 || order > 14 || !(radius_arcsec > 0.0) || !(radius_arcsec <= 648000.0)) {
-    set_error("order must be in [0, 14] and radius in (0, 648000]");
+  if (order < 0 || order > 14 || !(radius_arcsec > 0.0) || !(radius_arcsec <= 648000.0) ||
+      (precision != HLC_FP64 && precision != HLC_FP32_GUARD)) {
+    set_error("order must be in [0, 14], radius in (0, 648000] and precision HLC_FP64 or "
+              "HLC_FP32_GUARD");
     return HLC_EINVAL;
   }
   if (n == 0) return HLC_OK;
@@ -2797,13 +2799,32 @@ int hlc_quad_cells(const double* ra, const double* dec, uint64_t n, double radiu
   }
   HLC_TRY(ensure_device_tables());
   cudaStream_t st = (cudaStream_t)stream;
+  const double R = radius_arcsec / 3600.0;
   int* err = nullptr;
-  HLC_CUDA(cudaMallocAsync(&err, sizeof(int), st));
-  cudaMemsetAsync(err, 0, sizeof(int), st);
-  k_quad_cells<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-      ra, dec, nullptr, n, radius_arcsec / 3600.0, order, pix_const(order), out,
-      (uint32_t*)count, nullptr, nullptr, nullptr, err);
-  int rc = cudaGetLastError() == cudaSuccess ? HLC_OK : HLC_ECUDA;
+  HLC_CUDA(cudaMallocAsync(&err, 16, st));
+  cudaMemsetAsync(err, 0, 16, st);
+  int rc = HLC_OK;
+  if (precision == HLC_FP32_GUARD) {
+    uint32_t* slow = nullptr;
+    unsigned long long* nslow = (unsigned long long*)(err + 2);
+    if (cudaMallocAsync(&slow, n * 4, st) != cudaSuccess) {
+      cudaFreeAsync(err, st);
+      set_error("cudaMallocAsync(%llu bytes) failed", (unsigned long long)(n * 4));
+      return HLC_ENOMEM;
+    }
+    k_quad_cells<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+        ra, dec, nullptr, n, R, order, pix_const(order), out, (uint32_t*)count, nullptr, slow,
+        nslow, err);
+    k_quad_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, R, order, slow, nslow, out,
+                                                  (uint32_t*)count);
+    rc = cudaGetLastError() == cudaSuccess ? HLC_OK : HLC_ECUDA;
+    cudaFreeAsync(slow, st);
+  } else {
+    k_quad_cells<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+        ra, dec, nullptr, n, R, order, pix_const(order), out, (uint32_t*)count, nullptr, nullptr,
+        nullptr, err);
+    rc = cudaGetLastError() == cudaSuccess ? HLC_OK : HLC_ECUDA;
+  }
   if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_quad_cells");
   cudaFreeAsync(err, st);
   return rc;

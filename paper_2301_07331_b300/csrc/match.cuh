@@ -107,7 +107,9 @@ __global__ void k_prep_fallback(const double* __restrict__ ra, const double* __r
 }
 
 // Quad-direction cells of each source (Algorithm 1): 5 slots + count.
-// (FAST: sources with an undecided pixel are queued for k_quad_fallback.)
+// (FAST: no FP64 instruction on the way; a source with an undecided position
+// keeps its decided pixels in its cells row, the mask of the undecided ones
+// in count, and is queued for k_quad_fallback.)
 template <bool FAST>
 __global__ void k_quad_cells(const double* __restrict__ ra, const double* __restrict__ dec,
                              const uint64_t* __restrict__ id, uint64_t n, double R, int order,
@@ -115,6 +117,7 @@ __global__ void k_quad_cells(const double* __restrict__ ra, const double* __rest
                              uint32_t* __restrict__ count, SrcRec* __restrict__ rec,
                              uint32_t* __restrict__ slow, unsigned long long* __restrict__ nslow,
                              int* __restrict__ err) {
+  const f2 Rd = split_f64(R);
   for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n;
        i0 += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t i = i0 + threadIdx.x;
@@ -123,24 +126,32 @@ __global__ void k_quad_cells(const double* __restrict__ ra, const double* __rest
       double a = ra[i], d = dec[i];
       uint32_t c[5] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
       int m = 1;
-      if (!c_valid(a, d)) {
+      const bool valid = FAST ? (bits_finite(a) && bits_abs_le(d, 90.0)) : c_valid(a, d);
+      if (!valid) {
         atomicOr(err, DERR_INPUT);
         c[0] = 0;
       } else if (FAST) {
-        m = g_quad_cells(c_norm_ra(a), d, R, order, K, c);
-        if (m == 0) {
+        if (!bits_in_ra_range(a)) a = c_norm_ra(a);
+        uint32_t p[5];
+        const unsigned und = g_quad_pos(a, d, Rd, order, K, p);
+        if (und) {
           defer = true;
-          m = 1;
+#pragma unroll
+          for (int e = 0; e < 5; ++e) c[e] = p[e];
+          m = (int)und;  // (the mask, until k_quad_fallback)
+        } else {
+          m = quad_sort_unique(p, c);
         }
       } else {
-        m = c_quad_cells(c_norm_ra(a), d, R, order, c);
+        a = c_norm_ra(a);
+        m = c_quad_cells(a, d, R, order, c);
       }
 #pragma unroll
-      for (int e = 0; e < 5; ++e) cells[5 * i + e] = e < m ? c[e] : 0xFFFFFFFFu;
+      for (int e = 0; e < 5; ++e) cells[5 * i + e] = (defer || e < m) ? c[e] : 0xFFFFFFFFu;
       count[i] = (uint32_t)m;
       if (rec) {
         SrcRec r;
-        r.ra = c_valid(a, d) ? c_norm_ra(a) : a;
+        r.ra = a;  // normalised when valid
         r.dec = d;
         r.id = id[i];
         r.pad = 0;
@@ -160,6 +171,8 @@ __global__ void k_quad_cells(const double* __restrict__ ra, const double* __rest
   }
 }
 
+// The queued sources of k_quad_cells<true>: their undecided positions in the
+// binary64 arithmetic, then the sort and the repeats dropped.
 __global__ void k_quad_fallback(const double* __restrict__ ra, const double* __restrict__ dec,
                                 double R, int order, const uint32_t* __restrict__ slow,
                                 const unsigned long long* __restrict__ nslow,
@@ -168,8 +181,29 @@ __global__ void k_quad_fallback(const double* __restrict__ ra, const double* __r
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns;
        q += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t i = slow[q];
-    uint32_t c[5] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-    int m = c_quad_cells(c_norm_ra(ra[i]), dec[i], R, order, c);
+    const unsigned und = count[i];
+    const double a = c_norm_ra(ra[i]), d = dec[i];
+    uint32_t p[5], c[5] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+#pragma unroll
+    for (int e = 0; e < 5; ++e) p[e] = cells[5ull * i + e];
+    // the undecided positions exactly as c_quad_cells states them
+    if (und & 7u) {
+      const DecPart d0 = c_dec_part(d);
+      if (und & 1u) p[0] = c_pix(a, d0, order);
+      if (und & 2u) p[1] = c_pix(wrap_ra(__dadd_rn(a, R)), d0, order);
+      if (und & 4u) p[2] = c_pix(wrap_ra(__dsub_rn(a, R)), d0, order);
+    }
+    if (und & 8u) {
+      double dm_ = __dsub_rn(d, R);
+      if (dm_ < -90.0) dm_ = -90.0;
+      p[3] = c_ang2pix(a, dm_, order);
+    }
+    if (und & 16u) {
+      double dp_ = __dadd_rn(d, R);
+      if (dp_ > 90.0) dp_ = 90.0;
+      p[4] = c_ang2pix(a, dp_, order);
+    }
+    const int m = quad_sort_unique(p, c);
 #pragma unroll
     for (int e = 0; e < 5; ++e) cells[5ull * i + e] = e < m ? c[e] : 0xFFFFFFFFu;
     count[i] = (uint32_t)m;

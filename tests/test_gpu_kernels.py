@@ -92,14 +92,21 @@ def test_neighbours_sampled(order):
 @pytest.mark.parametrize("order,r", [(8, 30.0), (12, 1.5), (14, 1.0)])
 def test_quad_cells_equal_oracle(order, r):
     ra, dec = _points(200_000, order)
+    # and sources whose shifted copies land on the RA = 0 line, the poles
+    # and the zone boundary
+    vz = math.degrees(math.asin(2.0 / 3.0))
+    R = r / 3600.0
+    ra = np.concatenate([ra, [R, 360.0 - R, 0.0, R * 0.5, 180.0, 45.0, 45.0]])
+    dec = np.concatenate([dec, [10.0, -10.0, 90.0 - R, -90.0 + R * 0.5, vz - R, vz + R, 0.0]])
     rr, dd = _cuda(ra, dec)
-    got, cnt = hlc.hlc_quad_cells(rr, dd, r, order)
     want, wcnt = O.quad_cells(ra, dec, r, order)
-    np.testing.assert_array_equal(cnt.cpu().numpy(), wcnt)
-    g = got.cpu().numpy().view(np.uint32).astype(np.uint64)
     w = want.copy()
     w[w == np.uint64(2 ** 64 - 1)] = 0xFFFFFFFF
-    np.testing.assert_array_equal(g, w)
+    for prec in (hlc.HLC_FP64, hlc.HLC_FP32_GUARD):
+        got, cnt = hlc.hlc_quad_cells(rr, dd, r, order, prec)
+        np.testing.assert_array_equal(cnt.cpu().numpy(), wcnt)
+        g = got.cpu().numpy().view(np.uint32).astype(np.uint64)
+        np.testing.assert_array_equal(g, w)
 
 
 @pytest.mark.parametrize("n", [0, 1, 2, 1000, 3839, 3840, 3841, 3840 * 7 + 5, 1_000_003])
