@@ -132,7 +132,7 @@ __global__ void k_quad_cells(const double* __restrict__ ra, const double* __rest
         c[0] = 0;
       } else if (FAST) {
         if (!bits_in_ra_range(a)) a = c_norm_ra(a);
-        uint32_t p[5];
+        uint32_t p[5] = {0u, 0u, 0u, 0u, 0u};
         const unsigned und = g_quad_pos(a, d, Rd, order, K, p);
         if (und) {
           defer = true;
@@ -171,42 +171,73 @@ __global__ void k_quad_cells(const double* __restrict__ ra, const double* __rest
   }
 }
 
-// The queued sources of k_quad_cells<true>: their undecided positions in the
-// binary64 arithmetic, then the sort and the repeats dropped.
-__global__ void k_quad_fallback(const double* __restrict__ ra, const double* __restrict__ dec,
-                                double R, int order, const uint32_t* __restrict__ slow,
-                                const unsigned long long* __restrict__ nslow,
-                                uint32_t* __restrict__ cells, uint32_t* __restrict__ count) {
-  uint64_t ns = *nslow;
-  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns;
-       q += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t i = slow[q];
-    const unsigned und = count[i];
-    const double a = c_norm_ra(ra[i]), d = dec[i];
-    uint32_t p[5], c[5] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+// The queued sources of k_quad_cells<true>.  Each warp takes 32 of them,
+// lists their undecided (source, position) pairs in shared memory and
+// computes the pairs 32 at a time, every lane running the same binary64 pixel
+// function on the position's coordinates (formed exactly as c_quad_cells
+// states them); each lane then sorts its source's five pixels and drops the
+// repeats.
+__global__ void __launch_bounds__(kThreads) k_quad_fallback(
+    const double* __restrict__ ra, const double* __restrict__ dec, double R, int order,
+    const uint32_t* __restrict__ slow, const unsigned long long* __restrict__ nslow,
+    uint32_t* __restrict__ cells, uint32_t* __restrict__ count) {
+  __shared__ uint8_t s_pair[kThreads / 32][160];   // (lane << 3) | position
+  __shared__ uint32_t s_pix[kThreads / 32][160];   // [lane * 5 + position]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = lanemask_lt();
+  const uint64_t ns = *nslow;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t q0 = (uint64_t)blockIdx.x * blockDim.x + (uint64_t)(w * 32); q0 < ns;
+       q0 += stride) {
+    const uint64_t q = q0 + lane;
+    const bool live = q < ns;
+    const uint32_t i = live ? slow[q] : 0u;
+    const unsigned und = live ? count[i] : 0u;
+    const double a = live ? c_norm_ra(ra[i]) : 0.0, d = live ? dec[i] : 0.0;
+    int npairs = 0;
 #pragma unroll
-    for (int e = 0; e < 5; ++e) p[e] = cells[5ull * i + e];
-    // the undecided positions exactly as c_quad_cells states them
-    if (und & 7u) {
-      const DecPart d0 = c_dec_part(d);
-      if (und & 1u) p[0] = c_pix(a, d0, order);
-      if (und & 2u) p[1] = c_pix(wrap_ra(__dadd_rn(a, R)), d0, order);
-      if (und & 4u) p[2] = c_pix(wrap_ra(__dsub_rn(a, R)), d0, order);
+    for (int e = 0; e < 5; ++e) {
+      const bool mine = (und >> e) & 1u;
+      const unsigned bal = __ballot_sync(0xffffffffu, mine);
+      if (mine) s_pair[w][npairs + __popc(bal & lt)] = (uint8_t)((lane << 3) | e);
+      npairs += __popc(bal);
     }
-    if (und & 8u) {
-      double dm_ = __dsub_rn(d, R);
-      if (dm_ < -90.0) dm_ = -90.0;
-      p[3] = c_ang2pix(a, dm_, order);
+    __syncwarp();
+    for (int k0 = 0; k0 < npairs; k0 += 32) {
+      const int k = k0 + lane;
+      const bool act = k < npairs;
+      const unsigned v = act ? s_pair[w][k] : (unsigned)(lane << 3);
+      const int src = (int)(v >> 3), e = (int)(v & 7u);
+      const double sa = __shfl_sync(0xffffffffu, a, src);
+      const double sd = __shfl_sync(0xffffffffu, d, src);
+      if (act) {
+        double pa = sa, pd = sd;
+        if (e == 1) {
+          pa = wrap_ra(__dadd_rn(sa, R));
+        } else if (e == 2) {
+          pa = wrap_ra(__dsub_rn(sa, R));
+        } else if (e == 3) {
+          pd = __dsub_rn(sd, R);
+          if (pd < -90.0) pd = -90.0;
+        } else if (e == 4) {
+          pd = __dadd_rn(sd, R);
+          if (pd > 90.0) pd = 90.0;
+        }
+        s_pix[w][src * 5 + e] = c_ang2pix(pa, pd, order);
+      }
     }
-    if (und & 16u) {
-      double dp_ = __dadd_rn(d, R);
-      if (dp_ > 90.0) dp_ = 90.0;
-      p[4] = c_ang2pix(a, dp_, order);
-    }
-    const int m = quad_sort_unique(p, c);
+    __syncwarp();
+    if (live) {
+      uint32_t p[5], c[5] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
 #pragma unroll
-    for (int e = 0; e < 5; ++e) cells[5ull * i + e] = e < m ? c[e] : 0xFFFFFFFFu;
-    count[i] = (uint32_t)m;
+      for (int e = 0; e < 5; ++e)
+        p[e] = ((und >> e) & 1u) ? s_pix[w][lane * 5 + e] : cells[5ull * i + e];
+      const int m = quad_sort_unique(p, c);
+#pragma unroll
+      for (int e = 0; e < 5; ++e) cells[5ull * i + e] = e < m ? c[e] : 0xFFFFFFFFu;
+      count[i] = (uint32_t)m;
+    }
+    __syncwarp();  // s_pair and s_pix are reused by the next round
   }
 }
 
