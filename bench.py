@@ -119,6 +119,8 @@ def run_hlc(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
     A, B, r, L, Lc, wname = make_workload(args, rank, dev)
+    # (captured DRAM traffic applies to the workload it was taken on)
+    wkey = (args.workload, int(A.ra.numel()) if A.ra.numel() == B.ra.numel() else -1, args.mode)
     na, nb = A.ra.numel(), B.ra.numel()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -195,7 +197,7 @@ def run_hlc(args):
         # each pass reads and writes a 4-byte key and a 4-byte value per entry
         per_pass = 16 * (mA + mB) / 2
         gbs = per_pass * npass / (ms_passes / 1e3) / 1e9
-        tr = _traffic("k_onesweep")
+        tr = _traffic("k_onesweep", wkey)
         roofline = {"kernel": "k_onesweep (cell-key radix sort digit pass)", "bound": "hbm",
                     "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(gbs / peak, 4), "traffic": tr, "peak_source": peak_src,
@@ -216,7 +218,7 @@ def run_hlc(args):
                      + ": candidates + pair test)",
                      "bound": "hbm", "achieved": round(pair_gbs, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(pair_gbs / peak, 4),
-                     "traffic": _traffic(kname) if prec == hlc.HLC_FP32_GUARD else None,
+                     "traffic": _traffic(kname, wkey) if prec == hlc.HLC_FP32_GUARD else None,
                      "peak_source": peak_src, "bytes_per_launch": int(pair_bytes),
                      "bytes_basis": ("20" if quad else "24") + " B per A entry (key + FP32 vector"
                                     + ("" if quad else " + source index") + "), 16 B per B entry, "
@@ -297,16 +299,18 @@ def run_hlc(args):
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture, with
 # the digest of the kernel sources it was taken on; a changed source voids it.
 TRAFFIC = {
-    # ncu --set full of one sort pass in the full-sky 10M x 10M step:
-    # 81,022,976 B read + 35,151,104 B written
-    "k_onesweep": {"bytes_per_launch": 116174080, "sources": "5f96d74c07f657ea",
+    # one launch each, captured on the default line's workload (full sky
+    # 10M x 10M, complete mode, FP32 form) with
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum:
+    # a sort pass: 80,441,600 B read + 33,983,232 B written
+    "k_onesweep": {"bytes_per_launch": 114424832, "sources": "5f96d74c07f657ea",
                    "files": ("sort.cuh", "common.cuh")},
-    # ncu --set full of the pair test in the full-sky 10M x 10M step:
-    # 495,411,712 B read + 41,638,144 B written
-    "k_pair<1,0,0,1>": {"bytes_per_launch": 537049856, "sources": "d0fe5925b28a6acd",
+    # the pair test: 495,344,128 B read + 41,401,600 B written
+    "k_pair<1,0,0,1>": {"bytes_per_launch": 536745728, "sources": "ab18d71678b9633c",
                         "files": ("match.cuh", "canon.cuh", "index.cuh", "learned.cuh",
                                   "common.cuh", "fp32.cuh", "fastpix.cuh")},
 }
+TRAFFIC_WORKLOAD = ("fullsky", 10_000_000, "complete")
 
 
 def _sources_sha(files) -> str:
@@ -318,9 +322,13 @@ def _sources_sha(files) -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic(name):
+def _traffic(name, workload):
+    """Captured DRAM bytes per launch of `name`, or None when the bench runs
+    another workload or the kernel's sources changed since the capture."""
     tr = TRAFFIC.get(name)
-    return tr["bytes_per_launch"] if tr and tr["sources"] == _sources_sha(tr["files"]) else None
+    if not tr or workload != TRAFFIC_WORKLOAD:
+        return None
+    return tr["bytes_per_launch"] if tr["sources"] == _sources_sha(tr["files"]) else None
 
 
 def alg_pair_tests(hlc, A, B, L):
