@@ -203,7 +203,10 @@ def run_hlc(args):
                     "frac": round(gbs / peak, 4), "traffic": tr, "peak_source": peak_src,
                     "bytes_per_launch": int(per_pass),
                     "bytes_basis": "16 B per entry per pass (key and value read and written)",
-                    "launches_per_step": npass, "ms_per_launch": ms_passes / npass}
+                    "launches_per_step": npass, "ms_per_launch": ms_passes / npass,
+                    "timing": "CUDA events around each catalogue's digit passes; in the FP32 "
+                              "complete form A is built on a second stream beside B, so the "
+                              "passes share the GPU with the other catalogue's kernels"}
     lt = 0
     while lt < L and 12 * 4 ** lt < mB:
         lt += 1

@@ -291,7 +291,7 @@ struct PinnedBuf {
 
 enum Ctr { C_ROWS = 0, C_BAND, C_TESTS, C_DUPS, C_M, C_TOTAL, C_HEADS_A, C_HEADS_B, C_DENSE,
            C_WORK, C_IDDIFF, C_MAXB, C_SLOW, C_LHITS, C_LLOOK, C_LMAXERR, C_SCRATCH, C_BAND64,
-           C_N };
+           C_SLOW_A, C_N };
 
 }  // namespace hlc
 
@@ -667,6 +667,77 @@ static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
   return HLC_OK;
 }
 
+// The FP32 complete form builds A beside B: A's prep, sort and payload need
+// only B's table order (a function of B's size), so they run on the side
+// stream ks while B is built on the plan stream.  Every buffer is allocated
+// first, on the plan stream, and handed to ks through the event ev[0]; the
+// temporaries are returned in tmp for the caller to free once the plan
+// stream has waited for ev[2] (A's payload done).  A's dense cells, which
+// need B's table, are ordered by the caller after that join.
+static int bucket_a_side(hlc_plan_t* P, const hlc_catalog* in, uint64_t nb, cudaStream_t ks,
+                         cudaEvent_t ev[4], std::vector<void*>& tmp) {
+  Arena& ar = *P->arena;
+  cudaStream_t st = plan_stream(P);
+  CatDev& X = P->A;
+  const int L = P->p.fine_level;
+  const uint64_t n = in->n;
+  X.n = n;
+  X.m = n;
+  X.table_order = coarse_table_order(nb, L);
+  X.table_shift = 2 * (L - X.table_order);
+  const int shift = X.table_shift;
+  const int bits = 2 * L + 4;
+  HLC_ALLOC(ar, X.rec, SrcRec, n + 1);
+  HLC_ALLOC(ar, X.key, uint32_t, n + 1);
+  HLC_ALLOC(ar, X.idx, uint32_t, n + 1);
+  HLC_ALLOC(ar, X.v32, float4, n + 1);
+  uint32_t *slow = nullptr, *tk = nullptr, *tv = nullptr;
+  HLC_ALLOC(ar, slow, uint32_t, n + 1);
+  tmp.push_back(slow);
+  if (n > 1) {
+    HLC_ALLOC(ar, tk, uint32_t, n);
+    HLC_ALLOC(ar, tv, uint32_t, n);
+    void* scr = ar.get(sort_scratch_bytes(n, (bits - shift + 7) / 8));
+    if (!scr) return HLC_ENOMEM;
+    tmp.push_back(scr);
+  }
+  HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW_A, 0, 8, st));
+  HLC_CUDA(cudaEventRecord(ev[0], st));
+  HLC_CUDA(cudaStreamWaitEvent(ks, ev[0], 0));
+  if (n) {
+    k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, ks>>>(
+        in->ra_deg, in->dec_deg, in->id, n, L, pix_const(L), X.key, X.idx, X.rec, slow,
+        P->ctr + C_SLOW_A, P->dev_err);
+    HLC_LAUNCH_CHECK();
+    k_prep_fallback<<<148 * 4, kThreads, 0, ks>>>(in->ra_deg, in->dec_deg, L, slow,
+                                                  P->ctr + C_SLOW_A, X.key);
+    HLC_LAUNCH_CHECK();
+  }
+  HLC_CUDA(cudaEventRecord(ev[1], ks));
+  if (n > 1) {
+    bool in_tmp = false;
+    int np = 0;
+    cudaEvent_t* pev = P->events ? P->ev + 9 : nullptr;
+    HLC_TRY(radix_sort_pairs<uint32_t>(X.key, X.idx, tk, tv, n, bits, tmp.back(), P->dev_err,
+                                       ks, shift, &in_tmp, pev, &np));
+    P->sort_passes += np;
+    if (pev) P->sort_timed[1] = true;
+    if (in_tmp) {
+      std::swap(X.key, tk);
+      std::swap(X.idx, tv);
+    }
+    tmp.push_back(tk);  // the pair not holding the result
+    tmp.push_back(tv);
+  }
+  if (n) {
+    k_payload32<<<grid_for(n, kThreads), kThreads, 0, ks>>>(X.rec, X.idx, n, X.v32,
+                                                            P->ctr + C_IDDIFF);
+    HLC_LAUNCH_CHECK();
+  }
+  HLC_CUDA(cudaEventRecord(ev[2], ks));
+  return HLC_OK;
+}
+
 // Copy one catalogue in, build its sorted entries, payload and (for B) the
 // coarse offset table.  No host synchronisation in complete mode.
 static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool is_b,
@@ -938,11 +1009,42 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
       }
     }
   }
-  for (int i = 0; i < 2 && rc == HLC_OK; ++i) {
+  // FP32 complete form: A's prep, sort and payload on a side stream beside
+  // B's build (bucket_a_side), joined before A's dense cells are ordered
+  const bool side = P->table_buckets;
+  cudaStream_t ks = nullptr;
+  std::vector<void*> atmp;
+  if (side && rc == HLC_OK) {
+    if (cudaStreamCreateWithFlags(&ks, cudaStreamNonBlocking) != cudaSuccess) {
+      ks = nullptr;
+      rc = HLC_ECUDA;
+    } else if (cs && cudaStreamWaitEvent(ks, cev[1], 0) != cudaSuccess) {
+      rc = HLC_ECUDA;
+    } else {
+      rc = bucket_a_side(P, &dv[1], dv[0].n, ks, ea, atmp);
+    }
+  }
+  for (int i = 0; i < (side ? 1 : 2) && rc == HLC_OK; ++i) {
     if (cs && cudaStreamWaitEvent(st, cev[i], 0) != cudaSuccess) rc = HLC_ECUDA;
     const bool is_b = (i == 0) == P->table_buckets;
     if (rc == HLC_OK)
       rc = build_catalog(P, &dv[i], is_b ? P->B : P->A, is_b, is_b ? eb : ea);
+  }
+  cudaEvent_t ej = nullptr;  // (side form) the join: A's index stage starts here
+  if (side) {
+    if (rc == HLC_OK && (cudaStreamWaitEvent(st, ea[2], 0) != cudaSuccess ||
+                         cudaEventCreate(&ej) != cudaSuccess || cudaEventRecord(ej, st) != cudaSuccess))
+      rc = HLC_ECUDA;
+    if (rc == HLC_OK) {
+      for (void* q : atmp) P->arena->drop(q);
+      if (P->A.n > 1 && P->B.ndense > 0)
+        rc = dense_fixup(P, P->A, P->B.table, P->A.table_shift, true);
+      if (rc == HLC_OK && cudaEventRecord(ea[3], st) != cudaSuccess) rc = HLC_ECUDA;
+    }
+    if (ks) {
+      if (rc != HLC_OK) cudaStreamSynchronize(ks);  // nothing of A's still runs when freed
+      cudaStreamDestroy(ks);
+    }
   }
   if (cs) {
     cudaStreamSynchronize(cs);
@@ -969,13 +1071,14 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
     cudaEventElapsedTime(&t[1], eb[0], eb[1]);
     cudaEventElapsedTime(&t[2], ea[1], ea[2]);
     cudaEventElapsedTime(&t[3], eb[1], eb[2]);
-    cudaEventElapsedTime(&t[4], ea[2], ea[3]);
+    cudaEventElapsedTime(&t[4], ej ? ej : ea[2], ea[3]);
     cudaEventElapsedTime(&t[5], eb[2], eb[3]);
   }
   for (int i = 0; i < 4; ++i) {
     cudaEventDestroy(ea[i]);
     cudaEventDestroy(eb[i]);
   }
+  if (ej) cudaEventDestroy(ej);
   if (rc != HLC_OK) return fail(rc);
   ev_record(P, 1);
   unsigned long long diff = hc[C_IDDIFF];
