@@ -40,6 +40,8 @@ class HLCError(RuntimeError):
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 _DEALLOC_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+_NO_ALLOC = _ALLOC_FN()      # NULL callbacks: the library's stream-ordered pool
+_NO_DEALLOC = _DEALLOC_FN()
 
 
 class Catalog(C.Structure):
@@ -126,9 +128,16 @@ def _check(rc: int):
         raise HLCError(rc, lib().hlc_last_error().decode(errors="replace"))
 
 
+_cuda_seen = False
+
+
 def _require_cuda():
+    global _cuda_seen
+    if _cuda_seen:
+        return
     if not torch.cuda.is_available():
         raise RuntimeError("the cross-match library needs a CUDA device (none visible)")
+    _cuda_seen = True
 
 
 def _stream_ptr(stream) -> int:
@@ -232,12 +241,11 @@ def hlc_plan(A, B, radius_arcsec: float, fine_level: int, coarse_level: int | No
     cA, keepA = _catalog(*(_triple(A)))
     cB, keepB = _catalog(*(_triple(B)))
     st = _stream_ptr(stream)
-    dev = torch.cuda.current_device()
-    alloc = _TorchAllocator(dev, st) if torch_alloc else None
+    alloc = _TorchAllocator(torch.cuda.current_device(), st) if torch_alloc else None
     p = Params(float(radius_arcsec), int(fine_level if coarse_level is None else coarse_level),
                int(fine_level), int(boundary), int(precision), int(index), int(model),
                int(bool(want_sep)), int(device_mem_budget), st,
-               alloc.alloc if alloc else _ALLOC_FN(), alloc.dealloc if alloc else _DEALLOC_FN(),
+               alloc.alloc if alloc else _NO_ALLOC, alloc.dealloc if alloc else _NO_DEALLOC,
                None)
     if coarse_level is None:
         p.coarse_level = min(4, int(fine_level))
@@ -270,8 +278,8 @@ def hlc_plan_batched(jobs, precision: int = HLC_FP32_GUARD, want_sep: bool = Tru
         fl = int(jb.get("fine_level", -1))
         params[i] = Params(float(jb["radius_arcsec"]), 0, fl, HLC_COMPLETE8, int(precision),
                            HLC_INDEX_BSEARCH, HLC_MODEL_PLA, int(bool(want_sep)), 0, st,
-                           alloc.alloc if alloc else _ALLOC_FN(),
-                           alloc.dealloc if alloc else _DEALLOC_FN(), None)
+                           alloc.alloc if alloc else _NO_ALLOC,
+                           alloc.dealloc if alloc else _NO_DEALLOC, None)
     h = C.c_void_p()
     _check(L.hlc_plan(cats_a, cats_b, params, n, C.byref(h)))
     return Plan(h, params[0], alloc, (keep, cats_a, cats_b, params))
