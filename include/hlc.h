@@ -135,6 +135,11 @@ typedef struct {
   int join_level;                  /* HEALPix order used for the join */
   float ms_prep, ms_sort, ms_index, ms_candidates, ms_pair, ms_recheck,
       ms_output, ms_h2d, ms_d2h, ms_total;
+                                   /* stage times, summed over both catalogues
+                                      (in the FP32 complete form A is built on
+                                      a second stream beside B, so its prep and
+                                      sort times overlap B's); ms_total is the
+                                      plan's and the match's own span */
   uint64_t kernel_launches;        /* library kernels launched by the plan and
                                       the match */
   uint64_t dense_entries_b;        /* FP32 complete form: B entries in dense
@@ -146,7 +151,8 @@ typedef struct {
   float ms_stream_groups;          /*   the groups' copies in, matches and rows out, */
   float ms_stream_merge;           /*   merge of the groups' sorted rows */
   float ms_sort_passes;            /* FP32 complete form: the radix sort's digit
-                                      passes alone (both catalogues) */
+                                      passes alone, summed over both catalogues
+                                      (whose passes may run at the same time) */
   uint32_t sort_passes;            /*   and how many passes that was */
   uint64_t band_fp64;              /* FP32 forms: guard-band candidates the
                                       float-float separation left undecided,
