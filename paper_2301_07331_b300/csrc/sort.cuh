@@ -124,21 +124,24 @@ __global__ void __launch_bounds__(kBlock, sizeof(K) == 8 ? 3 : 4) k_onesweep(
   __syncthreads();
   const uint32_t tile = S.tile;
   const uint64_t base = (uint64_t)tile * kTile;
-  const uint64_t wbase = base + (uint64_t)warp * (kIpt * 32);
+  // tile-local 32-bit offsets: entry base + o is valid when o < rem
+  const uint32_t rem = (uint32_t)(n - base < (uint64_t)kTile ? n - base : (uint64_t)kTile);
+  const uint32_t wo = (uint32_t)warp * (kIpt * 32) + (uint32_t)lane;
+  const K* __restrict__ kt = kin + base;
+  const uint32_t* __restrict__ vt = vin + base;
 
   K k[kIpt];
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
-    uint64_t e = wbase + (uint64_t)i * 32 + lane;
-    k[i] = e < n ? kin[e] : K(0);
+    const uint32_t o = wo + (uint32_t)i * 32;
+    k[i] = o < rem ? kt[o] : K(0);
   }
   // publish this tile's digit counts before ranking, so that later tiles'
   // look-backs do not wait for it; the look-back of its own prefix follows
   // the ranking and finds earlier tiles published the same way
 #pragma unroll
   for (int i = 0; i < kIpt; ++i)
-    if (wbase + (uint64_t)i * 32 + lane < n)
-      atomicAdd(&S.dstart[(uint32_t)(k[i] >> shift) & 255u], 1u);
+    if (wo + (uint32_t)i * 32 < rem) atomicAdd(&S.dstart[(uint32_t)(k[i] >> shift) & 255u], 1u);
   __syncthreads();
   const uint32_t cnt = S.dstart[t];
   unsigned long long* slot = lookback + (uint64_t)tile * kRadix + t;
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(K) == 8 ? 3 : 4) k_onesweep(
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
     // lanes holding the same digit: intersect the 8 bit-plane ballots
-    bool valid = wbase + (uint64_t)i * 32 + lane < n;
+    const bool valid = wo + (uint32_t)i * 32 < rem;
     uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
     unsigned peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
@@ -199,17 +202,16 @@ __global__ void __launch_bounds__(kBlock, sizeof(K) == 8 ? 3 : 4) k_onesweep(
 
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
-    uint64_t e = wbase + (uint64_t)i * 32 + lane;
-    if (e < n) {
+    const uint32_t o = wo + (uint32_t)i * 32;
+    if (o < rem) {
       uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
       uint32_t pos = S.dstart[d] + S.whist[warp][d] + r[i];
       S.keys[pos] = k[i];
-      S.vals[pos] = vin[e];
+      S.vals[pos] = vt[o];
     }
   }
   __syncthreads();
-  uint32_t cnt_tile = (uint32_t)(n - base < (uint64_t)kTile ? n - base : (uint64_t)kTile);
-  for (uint32_t p = t; p < cnt_tile; p += kBlock) {
+  for (uint32_t p = t; p < rem; p += kBlock) {
     K kk = S.keys[p];
     int dd = (int)((uint32_t)(kk >> shift) & 255u);
     unsigned long long g = S.gbase[dd] + (p - S.dstart[dd]);
