@@ -85,3 +85,47 @@ def test_sampled_boxes_equal_oracle(sky, box):
     np.testing.assert_array_equal(ia[sel], want["id_a"])
     np.testing.assert_array_equal(ib[sel], want["id_b"])
     assert np.max(np.abs(sp[sel] - want["sep"]), initial=0.0) <= SEP_TOL
+
+
+# Order 14 (32-bit keys, every key bit in use) on the dense bulge recipe:
+# A = B = 8M, r = 1 arcsec, coarse order 4.
+RB, LB, LCB = 1.0, 14, 4
+
+
+@pytest.fixture(scope="module")
+def bulge():
+    return synth.bulge_pair(na=8_000_000, nb=8_000_000, device="cuda")
+
+
+def _run_bulge(A, B, prec):
+    plan = hlc.hlc_plan(A, B, RB, LB, coarse_level=LCB, precision=prec)
+    try:
+        res = hlc.hlc_match(plan)
+    finally:
+        hlc.hlc_free(plan)
+    return (res["id_a"].cpu().numpy().view(np.uint64), res["id_b"].cpu().numpy().view(np.uint64),
+            res["sep"].cpu().numpy())
+
+
+def test_bulge_order14_fp32_equals_fp64_and_oracle_boxes(bulge):
+    A, B = bulge
+    a32, b32, s32 = _run_bulge(A, B, hlc.HLC_FP32_GUARD)
+    a64, b64, s64 = _run_bulge(A, B, hlc.HLC_FP64)
+    np.testing.assert_array_equal(a32, a64)
+    np.testing.assert_array_equal(b32, b64)
+    assert np.max(np.abs(s32 - s64)) <= SEP_TOL
+    assert a32.size > 2_000_000
+    ra_a, dec_a, id_a = A.numpy()
+    ra_b, dec_b, id_b = B.numpy()
+    # the galactic centre (densest) and a box on the disk away from it
+    for lo, hi, d0, d1 in [(266.30, 266.50, -29.10, -28.90), (100.0, 100.5, 10.0, 10.5)]:
+        sa = (ra_a >= lo) & (ra_a < hi) & (dec_a >= d0) & (dec_a < d1)
+        m = 0.01
+        sb = (ra_b >= lo - m) & (ra_b < hi + m) & (dec_b >= d0 - m) & (dec_b < d1 + m)
+        assert sa.sum() > 20
+        want = O.match(ra_a[sa], dec_a[sa], id_a[sa], ra_b[sb], dec_b[sb], id_b[sb], RB, LB,
+                       O.COMPLETE)
+        sel = np.isin(a32, id_a[sa])
+        np.testing.assert_array_equal(a32[sel], want["id_a"])
+        np.testing.assert_array_equal(b32[sel], want["id_b"])
+        assert np.max(np.abs(s32[sel] - want["sep"]), initial=0.0) <= SEP_TOL
