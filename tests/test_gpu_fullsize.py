@@ -4,7 +4,8 @@ oracle cannot run all of it in seconds, so (1) the FP32 guard form must give
 exactly the binary64 form's rows (two independent GPU paths), and (2) for
 the A sources inside sampled sky boxes (equator, galactic centre, the RA
 0/360 wrap, the north polar cap) the rows must equal the oracle's, run on
-those A sources and every B source near the box."""
+those A sources and every B source near the box, in both boundary modes.
+The bulge recipe at order 14 gets the same two checks."""
 import numpy as np
 import pytest
 import torch
@@ -63,10 +64,11 @@ BOXES = [  # (ra_lo, ra_hi, dec_lo, dec_hi); ra_lo > ra_hi wraps through 0
 ]
 
 
+@pytest.mark.parametrize("mode", [hlc.HLC_COMPLETE8, hlc.HLC_QUAD])
 @pytest.mark.parametrize("box", BOXES)
-def test_sampled_boxes_equal_oracle(sky, box):
+def test_sampled_boxes_equal_oracle(sky, box, mode):
     A, B = sky
-    ia, ib, sp, _ = _run(A, B, hlc.HLC_FP32_GUARD)
+    ia, ib, sp, _ = _run(A, B, hlc.HLC_FP32_GUARD, mode)
     ra_a, dec_a, id_a = A.numpy()
     ra_b, dec_b, id_b = B.numpy()
     lo, hi, d0, d1 = box
@@ -80,7 +82,7 @@ def test_sampled_boxes_equal_oracle(sky, box):
               & (dec_b >= d0 - m) & (dec_b < d1 + m))
     assert sa.sum() > 20
     want = O.match(ra_a[sa], dec_a[sa], id_a[sa], ra_b[sb], dec_b[sb], id_b[sb], R, L,
-                   O.COMPLETE)
+                   O.COMPLETE if mode == hlc.HLC_COMPLETE8 else O.QUAD)
     sel = np.isin(ia, id_a[sa])
     np.testing.assert_array_equal(ia[sel], want["id_a"])
     np.testing.assert_array_equal(ib[sel], want["id_b"])
