@@ -45,6 +45,24 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(ms: float, device) -> float:
+    """The job's step time: the largest per-step time over the ranks (each
+    rank runs its own independent instance; this is the only exchange)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the job's
+    step time (ms)."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -160,9 +178,7 @@ def run_hlc(args):
             dist.barrier()
         ms = e0.elapsed_time(e1) / K
         if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+            ms = max_over_ranks(ms, dev)
         return ms, stats, n
 
     clocks = Clocks(local)
@@ -176,7 +192,7 @@ def run_hlc(args):
         return sum(s[key] for s in S) / len(S)
 
     sources = (na + nb) * world
-    value = sources / (ms / 1e3)
+    value = job_value(na + nb, world, ms)
     tests = stats[-1]["pair_tests"]
 
     # roofline of the dominant kernel: the radix sort's digit passes

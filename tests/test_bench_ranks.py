@@ -1,0 +1,49 @@
+"""The bench's multi-rank bookkeeping on CPU: two ranks joined over gloo
+(127.0.0.1) read their rank from the environment, take the slowest rank's
+step time as the job's, and report the units of both ranks over it."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+WORKER = r"""
+import json, os, sys
+sys.path.insert(0, sys.argv[1])
+import torch.distributed as dist
+import bench
+world, rank, local = bench._dist()
+dist.init_process_group("gloo", rank=rank, world_size=world)
+ms = bench.max_over_ranks(1.0 + 2.0 * rank, "cpu")
+print(json.dumps({"world": world, "rank": rank, "local": local, "ms": ms,
+                  "value": bench.job_value(1000, world, ms)}))
+dist.destroy_process_group()
+"""
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_two_ranks_take_the_slowest_step():
+    port = _free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                   LOCAL_RANK=str(rank), WORLD_SIZE="2")
+        procs.append(subprocess.Popen([sys.executable, "-c", WORKER, ROOT], env=env,
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    outs = []
+    for p in procs:
+        out, err = p.communicate(timeout=120)
+        assert p.returncode == 0, err
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    assert sorted(o["rank"] for o in outs) == [0, 1]
+    for o in outs:
+        assert o["world"] == 2 and o["local"] == o["rank"]
+        assert o["ms"] == 3.0                       # the slower rank's 3 ms
+        assert abs(o["value"] - 2 * 1000 / 3e-3) < 1e-6
