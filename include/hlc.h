@@ -136,10 +136,11 @@ typedef struct {
   float ms_prep, ms_sort, ms_index, ms_candidates, ms_pair, ms_recheck,
       ms_output, ms_h2d, ms_d2h, ms_total;
                                    /* stage times, summed over both catalogues
-                                      (in the FP32 complete form A is built on
-                                      a second stream beside B, so its prep and
-                                      sort times overlap B's); ms_total is the
-                                      plan's and the match's own span */
+                                      (in the FP32 complete form with device
+                                      inputs A is built on a second stream
+                                      beside B, so its prep and sort times
+                                      overlap B's); ms_total is the plan's and
+                                      the match's own span */
   uint64_t kernel_launches;        /* library kernels launched by the plan and
                                       the match */
   uint64_t dense_entries_b;        /* FP32 complete form: B entries in dense

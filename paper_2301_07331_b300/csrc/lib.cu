@@ -1010,8 +1010,10 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
     }
   }
   // FP32 complete form: A's prep, sort and payload on a side stream beside
-  // B's build (bucket_a_side), joined before A's dense cells are ordered
-  const bool side = P->table_buckets;
+  // B's build (bucket_a_side), joined before A's dense cells are ordered.
+  // (With host inputs A's build waits for its copy, which ends after B's
+  // build anyway, so it stays on the plan stream.)
+  const bool side = P->table_buckets && !cs;
   cudaStream_t ks = nullptr;
   std::vector<void*> atmp;
   if (side && rc == HLC_OK) {
