@@ -211,7 +211,8 @@ def run_hlc(args):
     ms_passes = mean("ms_sort_passes", stats)
     if npass and ms_passes > 0:
         # each pass reads and writes a 4-byte key and a 4-byte value per entry
-        per_pass = 16 * (mA + mB) / 2
+        # (a launch may cover both catalogues: sort_entries counts per launch)
+        per_pass = 16 * last["sort_entries"] / npass
         gbs = per_pass * npass / (ms_passes / 1e3) / 1e9
         tr = _traffic("k_onesweep", wkey)
         roofline = {"kernel": "k_onesweep (cell-key radix sort digit pass)", "bound": "hbm",
@@ -220,9 +221,8 @@ def run_hlc(args):
                     "bytes_per_launch": int(per_pass),
                     "bytes_basis": "16 B per entry per pass (key and value read and written)",
                     "launches_per_step": npass, "ms_per_launch": ms_passes / npass,
-                    "timing": "CUDA events around each catalogue's digit passes; in the FP32 "
-                              "complete form A is built on a second stream beside B, so the "
-                              "passes share the GPU with the other catalogue's kernels"}
+                    "timing": "CUDA events around the digit passes; with device inputs "
+                              "one launch per pass sorts both catalogues"}
     lt = 0
     while lt < L and 12 * 4 ** lt < mB:
         lt += 1

@@ -137,10 +137,10 @@ typedef struct {
       ms_output, ms_h2d, ms_d2h, ms_total;
                                    /* stage times, summed over both catalogues
                                       (in the FP32 complete form with device
-                                      inputs A is built on a second stream
-                                      beside B, so its prep and sort times
-                                      overlap B's); ms_total is the plan's and
-                                      the match's own span */
+                                      inputs the two catalogues are built at
+                                      once, so their stage times overlap);
+                                      ms_total is the plan's and the match's
+                                      own span */
   uint64_t kernel_launches;        /* library kernels launched by the plan and
                                       the match */
   uint64_t dense_entries_b;        /* FP32 complete form: B entries in dense
@@ -152,12 +152,15 @@ typedef struct {
   float ms_stream_groups;          /*   the groups' copies in, matches and rows out, */
   float ms_stream_merge;           /*   merge of the groups' sorted rows */
   float ms_sort_passes;            /* FP32 complete form: the radix sort's digit
-                                      passes alone, summed over both catalogues
-                                      (whose passes may run at the same time) */
+                                      passes alone (both catalogues) */
   uint32_t sort_passes;            /*   and how many passes that was */
   uint64_t band_fp64;              /* FP32 forms: guard-band candidates the
                                       float-float separation left undecided,
                                       finished by the binary64 test */
+  uint64_t sort_entries;           /* FP32 complete form: entries moved by the
+                                      timed digit passes, summed over the
+                                      launches (with device inputs one launch
+                                      per pass sorts both catalogues) */
 } hlc_stats;
 
 typedef struct hlc_plan_s hlc_plan_t;

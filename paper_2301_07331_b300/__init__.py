@@ -78,7 +78,8 @@ class Stats(C.Structure):
                 (f, C.c_float) for f in ("ms_stream_count", "ms_stream_bucket",
                                           "ms_stream_groups", "ms_stream_merge",
                                           "ms_sort_passes")] + [("sort_passes", C.c_uint32),
-                                                                ("band_fp64", C.c_uint64)]
+                                                                ("band_fp64", C.c_uint64),
+                                                                ("sort_entries", C.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -335,6 +335,7 @@ struct hlc_plan_s {
   uint32_t sparse_cell = hlc::kSparseCell;
   bool table_buckets = false;  // FP32 complete mode: entries bucketed by table cell
   uint32_t sort_passes = 0;    // radix passes of the table-cell sorts (ev 7-8: B, 9-10: A)
+  uint64_t sort_entries = 0;   // entries those passes moved, summed over the launches
   bool sort_timed[2] = {false, false};
   unsigned long long plan_launches = 0;
   cudaEvent_t ev[12] = {};
@@ -635,6 +636,7 @@ static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
                                        &in_tmp, pev, &np));
     P->sort_passes += np;
     if (pev) P->sort_timed[is_b ? 0 : 1] = true;
+    P->sort_entries += (uint64_t)np * n;
     ar.drop(scr);
     if (in_tmp) {
       std::swap(X.key, tk);
@@ -667,74 +669,133 @@ static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
   return HLC_OK;
 }
 
-// The FP32 complete form builds A beside B: A's prep, sort and payload need
-// only B's table order (a function of B's size), so they run on the side
-// stream ks while B is built on the plan stream.  Every buffer is allocated
-// first, on the plan stream, and handed to ks through the event ev[0]; the
-// temporaries are returned in tmp for the caller to free once the plan
-// stream has waited for ev[2] (A's payload done).  A's dense cells, which
-// need B's table, are ordered by the caller after that join.
-static int bucket_a_side(hlc_plan_t* P, const hlc_catalog* in, uint64_t nb, cudaStream_t ks,
-                         cudaEvent_t ev[4], std::vector<void*>& tmp) {
+// The FP32 complete form with device inputs builds both catalogues at once
+// (A needs only B's table order, a function of B's size): the two preps run
+// side by side, A's on the side stream ks; the two radix sorts then run as
+// one sort of both arrays on the plan stream (a launch per digit pass covers
+// the tiles of both); the two payloads and B's offset table overlap again.
+// Every buffer A uses on ks is allocated first, on the plan stream, and
+// handed over through ea[0] and e_sorted; the caller joins by making the
+// plan stream wait for ea[2] (A's payload done) before A's dense cells are
+// ordered against B's table.
+static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog* inA,
+                       cudaStream_t ks, cudaEvent_t eb[4], cudaEvent_t ea[4],
+                       cudaEvent_t e_sorted) {
   Arena& ar = *P->arena;
   cudaStream_t st = plan_stream(P);
-  CatDev& X = P->A;
   const int L = P->p.fine_level;
-  const uint64_t n = in->n;
-  X.n = n;
-  X.m = n;
-  X.table_order = coarse_table_order(nb, L);
-  X.table_shift = 2 * (L - X.table_order);
-  const int shift = X.table_shift;
   const int bits = 2 * L + 4;
-  HLC_ALLOC(ar, X.rec, SrcRec, n + 1);
-  HLC_ALLOC(ar, X.key, uint32_t, n + 1);
-  HLC_ALLOC(ar, X.idx, uint32_t, n + 1);
-  HLC_ALLOC(ar, X.v32, float4, n + 1);
-  uint32_t *slow = nullptr, *tk = nullptr, *tv = nullptr;
-  HLC_ALLOC(ar, slow, uint32_t, n + 1);
-  tmp.push_back(slow);
-  if (n > 1) {
-    HLC_ALLOC(ar, tk, uint32_t, n);
-    HLC_ALLOC(ar, tv, uint32_t, n);
-    void* scr = ar.get(sort_scratch_bytes(n, (bits - shift + 7) / 8));
-    if (!scr) return HLC_ENOMEM;
-    tmp.push_back(scr);
-  }
+  CatDev& XB = P->B;
+  CatDev& XA = P->A;
+  const uint64_t nb = inB->n, na = inA->n;
+  XB.n = XB.m = nb;
+  XA.n = XA.m = na;
+  XB.table_order = XA.table_order = coarse_table_order(nb, L);
+  XB.table_shift = XA.table_shift = 2 * (L - XB.table_order);
+  const int shift = XB.table_shift;
+  const int npass = (bits - shift + 7) / 8;
+  const uint64_t tsize = 12ull << (2 * XB.table_order);
+  // the preps' buffers of both, and A's payload
+  HLC_ALLOC(ar, XB.rec, SrcRec, nb + 1);
+  HLC_ALLOC(ar, XB.key, uint32_t, nb + 1);
+  HLC_ALLOC(ar, XB.idx, uint32_t, nb + 1);
+  HLC_ALLOC(ar, XA.rec, SrcRec, na + 1);
+  HLC_ALLOC(ar, XA.key, uint32_t, na + 1);
+  HLC_ALLOC(ar, XA.idx, uint32_t, na + 1);
+  HLC_ALLOC(ar, XA.v32, float4, na + 1);
+  uint32_t *slow_b = nullptr, *slow_a = nullptr;
+  HLC_ALLOC(ar, slow_b, uint32_t, nb + 1);
+  HLC_ALLOC(ar, slow_a, uint32_t, na + 1);
+  HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st));
   HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW_A, 0, 8, st));
-  HLC_CUDA(cudaEventRecord(ev[0], st));
-  HLC_CUDA(cudaStreamWaitEvent(ks, ev[0], 0));
-  if (n) {
-    k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, ks>>>(
-        in->ra_deg, in->dec_deg, in->id, n, L, pix_const(L), X.key, X.idx, X.rec, slow,
+  HLC_CUDA(cudaEventRecord(eb[0], st));
+  HLC_CUDA(cudaEventRecord(ea[0], st));
+  HLC_CUDA(cudaStreamWaitEvent(ks, ea[0], 0));
+  // 1. the two preps, side by side
+  if (na) {
+    k_prep_keys<true><<<grid_for(na, kThreads), kThreads, 0, ks>>>(
+        inA->ra_deg, inA->dec_deg, inA->id, na, L, pix_const(L), XA.key, XA.idx, XA.rec, slow_a,
         P->ctr + C_SLOW_A, P->dev_err);
     HLC_LAUNCH_CHECK();
-    k_prep_fallback<<<148 * 4, kThreads, 0, ks>>>(in->ra_deg, in->dec_deg, L, slow,
-                                                  P->ctr + C_SLOW_A, X.key);
+    k_prep_fallback<<<148 * 4, kThreads, 0, ks>>>(inA->ra_deg, inA->dec_deg, L, slow_a,
+                                                  P->ctr + C_SLOW_A, XA.key);
     HLC_LAUNCH_CHECK();
   }
-  HLC_CUDA(cudaEventRecord(ev[1], ks));
-  if (n > 1) {
+  HLC_CUDA(cudaEventRecord(ea[1], ks));
+  if (nb) {
+    k_prep_keys<true><<<grid_for(nb, kThreads), kThreads, 0, st>>>(
+        inB->ra_deg, inB->dec_deg, inB->id, nb, L, pix_const(L), XB.key, XB.idx, XB.rec, slow_b,
+        P->ctr + C_SLOW, P->dev_err);
+    HLC_LAUNCH_CHECK();
+    k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(inB->ra_deg, inB->dec_deg, L, slow_b,
+                                                  P->ctr + C_SLOW, XB.key);
+    HLC_LAUNCH_CHECK();
+  }
+  HLC_CUDA(cudaEventRecord(eb[1], st));
+  // 2. one sort of both arrays, after both preps
+  HLC_CUDA(cudaStreamWaitEvent(st, ea[1], 0));
+  ar.drop(slow_b);
+  ar.drop(slow_a);
+  uint32_t *tkb = nullptr, *tvb = nullptr, *tka = nullptr, *tva = nullptr;
+  void *scrb = nullptr, *scra = nullptr;
+  if (nb > 1) {
+    HLC_ALLOC(ar, tkb, uint32_t, nb);
+    HLC_ALLOC(ar, tvb, uint32_t, nb);
+    scrb = ar.get(sort_scratch_bytes(nb, npass));
+    if (!scrb) return HLC_ENOMEM;
+  }
+  if (na > 1) {
+    HLC_ALLOC(ar, tka, uint32_t, na);
+    HLC_ALLOC(ar, tva, uint32_t, na);
+    scra = ar.get(sort_scratch_bytes(na, npass));
+    if (!scra) return HLC_ENOMEM;
+  }
+  {
     bool in_tmp = false;
     int np = 0;
-    cudaEvent_t* pev = P->events ? P->ev + 9 : nullptr;
-    HLC_TRY(radix_sort_pairs<uint32_t>(X.key, X.idx, tk, tv, n, bits, tmp.back(), P->dev_err,
-                                       ks, shift, &in_tmp, pev, &np));
+    cudaEvent_t* pev = P->events ? P->ev + 7 : nullptr;
+    HLC_TRY(radix_sort_pairs2<uint32_t>(XB.key, XB.idx, tkb, tvb, nb, scrb, XA.key, XA.idx, tka,
+                                        tva, na, scra, bits, P->dev_err, st, shift, &in_tmp, pev,
+                                        &np));
     P->sort_passes += np;
-    if (pev) P->sort_timed[1] = true;
+    P->sort_entries += (uint64_t)np * ((nb > 1 && na > 1) ? nb + na : (nb > 1 ? nb : na));
+    if (pev && np) P->sort_timed[0] = true;
     if (in_tmp) {
-      std::swap(X.key, tk);
-      std::swap(X.idx, tv);
+      std::swap(XB.key, tkb);
+      std::swap(XB.idx, tvb);
+      std::swap(XA.key, tka);
+      std::swap(XA.idx, tva);
     }
-    tmp.push_back(tk);  // the pair not holding the result
-    tmp.push_back(tv);
+    for (void* q : {(void*)tkb, (void*)tvb, scrb, (void*)tka, (void*)tva, scra})
+      if (q) ar.drop(q);
   }
-  if (n) {
-    k_payload32<<<grid_for(n, kThreads), kThreads, 0, ks>>>(X.rec, X.idx, n, X.v32,
-                                                            P->ctr + C_IDDIFF);
+  HLC_CUDA(cudaEventRecord(e_sorted, st));
+  // 3. the payloads side by side (A's on ks), then B's offset table and dense cells
+  HLC_CUDA(cudaStreamWaitEvent(ks, e_sorted, 0));
+  if (na) {
+    k_payload32<<<grid_for(na, kThreads), kThreads, 0, ks>>>(XA.rec, XA.idx, na, XA.v32,
+                                                             P->ctr + C_IDDIFF);
     HLC_LAUNCH_CHECK();
   }
-  HLC_CUDA(cudaEventRecord(ev[2], ks));
+  HLC_CUDA(cudaEventRecord(ea[2], ks));
+  HLC_ALLOC(ar, XB.v32, float4, nb + 1);
+  if (nb) {
+    k_payload32<<<grid_for(nb, kThreads), kThreads, 0, st>>>(XB.rec, XB.idx, nb, XB.v32,
+                                                             nullptr);
+    HLC_LAUNCH_CHECK();
+  }
+  HLC_CUDA(cudaEventRecord(eb[2], st));
+  HLC_ALLOC(ar, XB.table, uint32_t, tsize + 1);
+  HLC_TRY(offset_table(P, XB.key, nb, shift, tsize, XB.table, P->ctr + C_HEADS_B, P->sparse_cell,
+                       P->ctr + C_DENSE));
+  if (nb > 1) {
+    unsigned long long nd = 0;
+    HLC_CUDA(cudaMemcpyAsync(&nd, P->ctr + C_DENSE, 8, cudaMemcpyDeviceToHost, st));
+    HLC_CUDA(cudaStreamSynchronize(st));
+    XB.ndense = nd;
+    if (nd > 0) HLC_TRY(dense_fixup(P, XB, XB.table, shift, false));
+  }
+  HLC_CUDA(cudaEventRecord(eb[3], st));
   return HLC_OK;
 }
 
@@ -1009,24 +1070,24 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
       }
     }
   }
-  // FP32 complete form: A's prep, sort and payload on a side stream beside
-  // B's build (bucket_a_side), joined before A's dense cells are ordered.
+  // FP32 complete form: both catalogues built at once, A's kernels on a side
+  // stream (bucket_pair), joined before A's dense cells are ordered.
   // (With host inputs A's build waits for its copy, which ends after B's
   // build anyway, so it stays on the plan stream.)
   const bool side = P->table_buckets && !cs;
   cudaStream_t ks = nullptr;
-  std::vector<void*> atmp;
+  cudaEvent_t esorted = nullptr;  // both sorts done
   if (side && rc == HLC_OK) {
     if (cudaStreamCreateWithFlags(&ks, cudaStreamNonBlocking) != cudaSuccess) {
       ks = nullptr;
       rc = HLC_ECUDA;
-    } else if (cs && cudaStreamWaitEvent(ks, cev[1], 0) != cudaSuccess) {
+    } else if (cudaEventCreateWithFlags(&esorted, cudaEventDisableTiming) != cudaSuccess) {
       rc = HLC_ECUDA;
     } else {
-      rc = bucket_a_side(P, &dv[1], dv[0].n, ks, ea, atmp);
+      rc = bucket_pair(P, &dv[0], &dv[1], ks, eb, ea, esorted);
     }
   }
-  for (int i = 0; i < (side ? 1 : 2) && rc == HLC_OK; ++i) {
+  for (int i = 0; i < (side ? 0 : 2) && rc == HLC_OK; ++i) {
     if (cs && cudaStreamWaitEvent(st, cev[i], 0) != cudaSuccess) rc = HLC_ECUDA;
     const bool is_b = (i == 0) == P->table_buckets;
     if (rc == HLC_OK)
@@ -1038,7 +1099,6 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
                          cudaEventCreate(&ej) != cudaSuccess || cudaEventRecord(ej, st) != cudaSuccess))
       rc = HLC_ECUDA;
     if (rc == HLC_OK) {
-      for (void* q : atmp) P->arena->drop(q);
       if (P->A.n > 1 && P->B.ndense > 0)
         rc = dense_fixup(P, P->A, P->B.table, P->A.table_shift, true);
       if (rc == HLC_OK && cudaEventRecord(ea[3], st) != cudaSuccess) rc = HLC_ECUDA;
@@ -1047,6 +1107,7 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
       if (rc != HLC_OK) cudaStreamSynchronize(ks);  // nothing of A's still runs when freed
       cudaStreamDestroy(ks);
     }
+    if (esorted) cudaEventDestroy(esorted);
   }
   if (cs) {
     cudaStreamSynchronize(cs);
@@ -1107,6 +1168,7 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   P->stats.ms_sort = t[2] + t[3];
   P->stats.ms_index = t[4] + t[5];
   P->stats.sort_passes = P->sort_passes;
+  P->stats.sort_entries = P->sort_entries;
   for (int i = 0; i < 2; ++i)
     if (P->sort_timed[i]) P->stats.ms_sort_passes += ev_ms(P, 7 + 2 * i, 8 + 2 * i);
   P->plan_launches = g_launches.load() - P->launches0;

@@ -7,6 +7,8 @@
 // contiguous, so a cell is a range [start, end) of the sorted arrays.
 #pragma once
 
+#include <utility>
+
 #include "common.cuh"
 
 namespace hlc {
@@ -109,11 +111,25 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
 
 // (The look-back words carry their value and flag in one 64-bit word, so
 // relaxed accesses suffice: no other data is published through them.)
+// One array of a digit pass.  A launch may sort two arrays at once (the same
+// digit of each): its tiles are numbered across both, the first ntiles
+// belonging to d0, and each array keeps its own histogram offsets and
+// look-back chain.
+template <typename K>
+struct SweepDesc {
+  const K* kin;
+  const uint32_t* vin;
+  K* kout;
+  uint32_t* vout;
+  uint64_t n;
+  const uint32_t* goff;          // this pass's global digit offsets
+  unsigned long long* lookback;  // this pass's look-back words
+  uint32_t ntiles;
+};
+
 template <typename K>
 __global__ void __launch_bounds__(kBlock, sizeof(K) == 8 ? 3 : 4) k_onesweep(
-    const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
-    uint32_t* __restrict__ vout, uint64_t n, int shift, const uint32_t* __restrict__ goff,
-    unsigned long long* __restrict__ lookback, uint32_t* __restrict__ tile_ctr,
+    const SweepDesc<K> d0, const SweepDesc<K> d1, int shift, uint32_t* __restrict__ tile_ctr,
     int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SweepSmem<K>& S = *reinterpret_cast<SweepSmem<K>*>(smem_raw);
@@ -122,7 +138,17 @@ __global__ void __launch_bounds__(kBlock, sizeof(K) == 8 ? 3 : 4) k_onesweep(
   for (int i = t; i < kWarps * kRadix; i += kBlock) (&S.whist[0][0])[i] = 0;
   S.dstart[t] = 0;  // (kBlock == kRadix) the tile's digit counts first
   __syncthreads();
-  const uint32_t tile = S.tile;
+  // (tiles are taken in order, so every earlier tile of either array has
+  // started: the look-back below never waits on a tile not yet running)
+  const bool second = S.tile >= d0.ntiles;
+  const uint32_t tile = second ? S.tile - d0.ntiles : S.tile;
+  const K* __restrict__ kin = second ? d1.kin : d0.kin;
+  const uint32_t* __restrict__ vin = second ? d1.vin : d0.vin;
+  K* __restrict__ kout = second ? d1.kout : d0.kout;
+  uint32_t* __restrict__ vout = second ? d1.vout : d0.vout;
+  const uint64_t n = second ? d1.n : d0.n;
+  const uint32_t* __restrict__ goff = second ? d1.goff : d0.goff;
+  unsigned long long* __restrict__ lookback = second ? d1.lookback : d0.lookback;
   const uint64_t base = (uint64_t)tile * kTile;
   // tile-local 32-bit offsets: entry base + o is valid when o < rem
   const uint32_t rem = (uint32_t)(n - base < (uint64_t)kTile ? n - base : (uint64_t)kTile);
@@ -278,10 +304,10 @@ int radix_sort_pairs(K* keys, uint32_t* vals, K* tmp_keys, uint32_t* tmp_vals, u
   if (npass_out) *npass_out = npass;
   if (pass_ev) cudaEventRecord(pass_ev[0], st);
   for (int p = 0; p < npass; ++p) {
-    rs::k_onesweep<K><<<(unsigned)tiles, rs::kBlock, smem, st>>>(
-        ka, va, kb, vb, n, bit_lo + 8 * p, offs + p * rs::kRadix,
-        lb + (size_t)p * tiles * rs::kRadix,
-        ctr + p, dev_err);
+    rs::SweepDesc<K> d{ka, va, kb, vb, n, offs + p * rs::kRadix,
+                       lb + (size_t)p * tiles * rs::kRadix, (uint32_t)tiles};
+    rs::k_onesweep<K><<<(unsigned)tiles, rs::kBlock, smem, st>>>(d, d, bit_lo + 8 * p, ctr + p,
+                                                                 dev_err);
     HLC_LAUNCH_CHECK();
     K* tk = ka; ka = kb; kb = tk;
     uint32_t* tv = va; va = vb; vb = tv;
@@ -292,6 +318,101 @@ int radix_sort_pairs(K* keys, uint32_t* vals, K* tmp_keys, uint32_t* tmp_vals, u
   } else if (ka != keys) {
     HLC_CUDA(cudaMemcpyAsync(keys, ka, n * sizeof(K), cudaMemcpyDeviceToDevice, st));
     HLC_CUDA(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+  }
+  return HLC_OK;
+}
+
+// Two arrays sorted by the same key bits [bit_lo, key_bits) at once: one
+// launch per digit pass covers the tiles of both (more tiles in flight than
+// either alone).  Each array has its own temporaries and scratch (from
+// sort_scratch_bytes for its own n); the pass counters live in scr0.  With
+// in_tmp set, an odd number of passes leaves both results in the temporary
+// buffers and *in_tmp says so (never when only one array needs sorting).
+// Either array may be empty.
+template <typename K>
+int radix_sort_pairs2(K* keys0, uint32_t* vals0, K* tk0, uint32_t* tv0, uint64_t n0, void* scr0,
+                      K* keys1, uint32_t* vals1, K* tk1, uint32_t* tv1, uint64_t n1, void* scr1,
+                      int key_bits, int* dev_err, cudaStream_t st, int bit_lo, bool* in_tmp,
+                      cudaEvent_t* pass_ev = nullptr, int* npass_out = nullptr) {
+  if (in_tmp) *in_tmp = false;
+  if (n0 <= 1 || n1 <= 1) {  // one array (or none) needs sorting: the single form,
+    if (npass_out) *npass_out = 0;  // its result copied back in place
+    if (n0 > 1)
+      return radix_sort_pairs<K>(keys0, vals0, tk0, tv0, n0, key_bits, scr0, dev_err, st, bit_lo,
+                                 nullptr, pass_ev, npass_out);
+    if (n1 > 1)
+      return radix_sort_pairs<K>(keys1, vals1, tk1, tv1, n1, key_bits, scr1, dev_err, st, bit_lo,
+                                 nullptr, pass_ev, npass_out);
+    return HLC_OK;
+  }
+  if (bit_lo < 0 || bit_lo >= key_bits) bit_lo = 0;
+  int npass = (key_bits - bit_lo + 7) / 8;
+  if (npass < 1) npass = 1;
+  if (npass > (int)sizeof(K)) npass = (int)sizeof(K);
+  const uint64_t t0 = (n0 + rs::kTile - 1) / rs::kTile, t1 = (n1 + rs::kTile - 1) / rs::kTile;
+  if (t0 + t1 > 0xFFFFFFFFull) {
+    set_error("radix sort: too many elements");
+    return HLC_EINVAL;
+  }
+  char* s0 = (char*)scr0;
+  char* s1 = (char*)scr1;
+  uint32_t* ctr = (uint32_t*)(s0 + 16384);
+  HLC_CUDA(cudaMemsetAsync(ctr, 0, 64, st));
+  struct Side {
+    K* keys;
+    uint32_t* vals;
+    K* tk;
+    uint32_t* tv;
+    uint64_t n, tiles;
+    char* sp;
+  } sd[2] = {{keys0, vals0, tk0, tv0, n0, t0, s0}, {keys1, vals1, tk1, tv1, n1, t1, s1}};
+  for (const Side& q : sd) {
+    uint32_t* hist = (uint32_t*)q.sp;
+    uint32_t* offs = (uint32_t*)(q.sp + 8192);
+    unsigned long long* lb = (unsigned long long*)(q.sp + kSortLookbackOffset);
+    HLC_CUDA(cudaMemsetAsync(hist, 0, (size_t)npass * rs::kRadix * 4, st));
+    HLC_CUDA(cudaMemsetAsync(lb, 0, (size_t)npass * q.tiles * rs::kRadix * 8, st));
+    rs::k_digit_hist<K><<<grid_for(q.n, rs::kBlock, 148 * 8), rs::kBlock, 0, st>>>(
+        q.keys, q.n, npass, bit_lo, hist);
+    HLC_LAUNCH_CHECK();
+    rs::k_hist_scan<<<npass, rs::kBlock, 0, st>>>(hist, offs);
+    HLC_LAUNCH_CHECK();
+  }
+  size_t smem = sizeof(rs::SweepSmem<K>);
+  HLC_CUDA(cudaFuncSetAttribute(rs::k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  K* ka[2] = {keys0, keys1};
+  uint32_t* va[2] = {vals0, vals1};
+  K* kb[2] = {tk0, tk1};
+  uint32_t* vb[2] = {tv0, tv1};
+  if (npass_out) *npass_out = npass;
+  if (pass_ev) cudaEventRecord(pass_ev[0], st);
+  for (int p = 0; p < npass; ++p) {
+    rs::SweepDesc<K> d[2];
+    for (int i = 0; i < 2; ++i)
+      d[i] = rs::SweepDesc<K>{ka[i], va[i], kb[i], vb[i], sd[i].n,
+                              (uint32_t*)(sd[i].sp + 8192) + p * rs::kRadix,
+                              (unsigned long long*)(sd[i].sp + kSortLookbackOffset) +
+                                  (size_t)p * sd[i].tiles * rs::kRadix,
+                              (uint32_t)sd[i].tiles};
+    rs::k_onesweep<K><<<(unsigned)(t0 + t1), rs::kBlock, smem, st>>>(d[0], d[1], bit_lo + 8 * p,
+                                                                     ctr + p, dev_err);
+    HLC_LAUNCH_CHECK();
+    for (int i = 0; i < 2; ++i) {
+      std::swap(ka[i], kb[i]);
+      std::swap(va[i], vb[i]);
+    }
+  }
+  if (pass_ev) cudaEventRecord(pass_ev[1], st);
+  if (ka[0] != keys0 && in_tmp) {
+    *in_tmp = true;
+  } else if (ka[0] != keys0) {
+    for (int i = 0; i < 2; ++i) {
+      HLC_CUDA(cudaMemcpyAsync(sd[i].keys, ka[i], sd[i].n * sizeof(K), cudaMemcpyDeviceToDevice,
+                               st));
+      HLC_CUDA(cudaMemcpyAsync(sd[i].vals, va[i], sd[i].n * sizeof(uint32_t),
+                               cudaMemcpyDeviceToDevice, st));
+    }
   }
   return HLC_OK;
 }
