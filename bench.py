@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -70,10 +71,10 @@ class Clocks:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, path: str = ""):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), "hlc_bench_clocks.csv")
 
     def start(self):
         try:
@@ -181,7 +182,7 @@ def run_hlc(args):
             ms = max_over_ranks(ms, dev)
         return ms, stats, n
 
-    clocks = Clocks(local)
+    clocks = Clocks(local, args.clocks_out)
     clocks.start()
     ms, stats, nmatch = timed(prec, args.steps, args.warmup, clocks)
     clk = clocks.stop()
@@ -326,7 +327,7 @@ TRAFFIC = {
     "k_onesweep": {"bytes_per_launch": 282261248, "sources": "9122f1f3b1a09b49",
                    "files": ("sort.cuh", "common.cuh")},
     # the pair test: 495,344,128 B read + 41,401,600 B written
-    "k_pair<1,0,0,1>": {"bytes_per_launch": 536745728, "sources": "ab18d71678b9633c",
+    "k_pair<1,0,0,1>": {"bytes_per_launch": 536745728, "sources": "34476020625ecb83",
                         "files": ("match.cuh", "canon.cuh", "index.cuh", "learned.cuh",
                                   "common.cuh", "fp32.cuh", "fastpix.cuh")},
 }
@@ -690,6 +691,9 @@ def main():
     ap.add_argument("--mode", default="complete", choices=["complete", "quad"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--clocks-out", default="",
+                    help="file for the nvidia-smi samples of the timed region "
+                         "(default: one in the temporary directory)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -51,7 +51,7 @@ extern "C" {
 #define HLC_ENOMEM 2       /* device or pinned host allocation failed */
 #define HLC_ECUDA 3        /* a CUDA runtime call or kernel failed */
 #define HLC_ETIMEOUT 4     /* a bounded device-side wait gave up */
-#define HLC_EUNSUPPORTED 5 /* valid request outside what this build does */
+#define HLC_EUNSUPPORTED 5 /* valid request the library does not implement */
 
 /* ---- enums -------------------------------------------------------------- */
 #define HLC_COMPLETE8 0

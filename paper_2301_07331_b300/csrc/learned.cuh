@@ -17,7 +17,7 @@
 //     answer is checked against its bracket U[lb-1] < q <= U[lb] and falls
 //     back to binary search over the partition when the check fails.
 // The plain binary search over the partition is both the fallback and the
-// judge (tests compare every lookup with it).
+// reference every lookup is tested against.
 #pragma once
 
 #include "common.cuh"
