@@ -127,47 +127,33 @@ struct SweepDesc {
   uint32_t ntiles;
 };
 
-template <typename K>
-__global__ void __launch_bounds__(kBlock, sizeof(K) == 8 ? 3 : 4) k_onesweep(
-    const SweepDesc<K> d0, const SweepDesc<K> d1, int shift, uint32_t* __restrict__ tile_ctr,
-    int* __restrict__ err) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SweepSmem<K>& S = *reinterpret_cast<SweepSmem<K>*>(smem_raw);
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  if (t == 0) S.tile = atomicAdd(tile_ctr, 1u);
-  for (int i = t; i < kWarps * kRadix; i += kBlock) (&S.whist[0][0])[i] = 0;
-  S.dstart[t] = 0;  // (kBlock == kRadix) the tile's digit counts first
-  __syncthreads();
-  // (tiles are taken in order, so every earlier tile of either array has
-  // started: the look-back below never waits on a tile not yet running)
-  const bool second = S.tile >= d0.ntiles;
-  const uint32_t tile = second ? S.tile - d0.ntiles : S.tile;
-  const K* __restrict__ kin = second ? d1.kin : d0.kin;
-  const uint32_t* __restrict__ vin = second ? d1.vin : d0.vin;
-  K* __restrict__ kout = second ? d1.kout : d0.kout;
-  uint32_t* __restrict__ vout = second ? d1.vout : d0.vout;
-  const uint64_t n = second ? d1.n : d0.n;
-  const uint32_t* __restrict__ goff = second ? d1.goff : d0.goff;
-  unsigned long long* __restrict__ lookback = second ? d1.lookback : d0.lookback;
-  const uint64_t base = (uint64_t)tile * kTile;
-  // tile-local 32-bit offsets: entry base + o is valid when o < rem
-  const uint32_t rem = (uint32_t)(n - base < (uint64_t)kTile ? n - base : (uint64_t)kTile);
-  const uint32_t wo = (uint32_t)warp * (kIpt * 32) + (uint32_t)lane;
-  const K* __restrict__ kt = kin + base;
-  const uint32_t* __restrict__ vt = vin + base;
-
+// The pass over one tile.  FULL: the tile holds kTile entries (every tile
+// but an array's last), so no entry needs a bound check and every lane of
+// the ranking ballots is live.
+template <typename K, bool FULL>
+__device__ __forceinline__ void sweep_tile(SweepSmem<K>& S, const int t, const int lane,
+                                           const int warp, const uint32_t tile,
+                                           const K* __restrict__ kt,
+                                           const uint32_t* __restrict__ vt, K* __restrict__ kout,
+                                           uint32_t* __restrict__ vout,
+                                           const uint32_t* __restrict__ goff,
+                                           unsigned long long* __restrict__ lookback,
+                                           const uint32_t rem, const uint32_t wo, int shift,
+                                           int* __restrict__ err) {
+#define HLC_IN_TILE(o) (FULL || (o) < rem)
   K k[kIpt];
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
     const uint32_t o = wo + (uint32_t)i * 32;
-    k[i] = o < rem ? kt[o] : K(0);
+    k[i] = HLC_IN_TILE(o) ? kt[o] : K(0);
   }
   // publish this tile's digit counts before ranking, so that later tiles'
   // look-backs do not wait for it; the look-back of its own prefix follows
   // the ranking and finds earlier tiles published the same way
 #pragma unroll
   for (int i = 0; i < kIpt; ++i)
-    if (wo + (uint32_t)i * 32 < rem) atomicAdd(&S.dstart[(uint32_t)(k[i] >> shift) & 255u], 1u);
+    if (HLC_IN_TILE(wo + (uint32_t)i * 32))
+      atomicAdd(&S.dstart[(uint32_t)(k[i] >> shift) & 255u], 1u);
   __syncthreads();
   const uint32_t cnt = S.dstart[t];
   unsigned long long* slot = lookback + (uint64_t)tile * kRadix + t;
@@ -177,9 +163,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(K) == 8 ? 3 : 4) k_onesweep(
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
     // lanes holding the same digit: intersect the 8 bit-plane ballots
-    const bool valid = wo + (uint32_t)i * 32 < rem;
+    const bool valid = HLC_IN_TILE(wo + (uint32_t)i * 32);
     uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
-    unsigned peers = __ballot_sync(0xffffffffu, valid);
+    unsigned peers = FULL ? 0xffffffffu : __ballot_sync(0xffffffffu, valid);
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
       bool bit = (d >> b) & 1;
@@ -229,7 +215,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(K) == 8 ? 3 : 4) k_onesweep(
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
     const uint32_t o = wo + (uint32_t)i * 32;
-    if (o < rem) {
+    if (HLC_IN_TILE(o)) {
       uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
       uint32_t pos = S.dstart[d] + S.whist[warp][d] + r[i];
       S.keys[pos] = k[i];
@@ -237,13 +223,51 @@ __global__ void __launch_bounds__(kBlock, sizeof(K) == 8 ? 3 : 4) k_onesweep(
     }
   }
   __syncthreads();
-  for (uint32_t p = t; p < rem; p += kBlock) {
+  for (uint32_t p = t; p < (FULL ? (uint32_t)kTile : rem); p += kBlock) {
     K kk = S.keys[p];
     int dd = (int)((uint32_t)(kk >> shift) & 255u);
     unsigned long long g = S.gbase[dd] + (p - S.dstart[dd]);
     kout[g] = kk;
     vout[g] = S.vals[p];
   }
+#undef HLC_IN_TILE
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kBlock, sizeof(K) == 8 ? 3 : 4) k_onesweep(
+    const SweepDesc<K> d0, const SweepDesc<K> d1, int shift, uint32_t* __restrict__ tile_ctr,
+    int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SweepSmem<K>& S = *reinterpret_cast<SweepSmem<K>*>(smem_raw);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (t == 0) S.tile = atomicAdd(tile_ctr, 1u);
+  for (int i = t; i < kWarps * kRadix; i += kBlock) (&S.whist[0][0])[i] = 0;
+  S.dstart[t] = 0;  // (kBlock == kRadix) the tile's digit counts first
+  __syncthreads();
+  // (tiles are taken in order, so every earlier tile of either array has
+  // started: the look-back below never waits on a tile not yet running)
+  const bool second = S.tile >= d0.ntiles;
+  const uint32_t tile = second ? S.tile - d0.ntiles : S.tile;
+  const K* __restrict__ kin = second ? d1.kin : d0.kin;
+  const uint32_t* __restrict__ vin = second ? d1.vin : d0.vin;
+  K* __restrict__ kout = second ? d1.kout : d0.kout;
+  uint32_t* __restrict__ vout = second ? d1.vout : d0.vout;
+  const uint64_t n = second ? d1.n : d0.n;
+  const uint32_t* __restrict__ goff = second ? d1.goff : d0.goff;
+  unsigned long long* __restrict__ lookback = second ? d1.lookback : d0.lookback;
+  const uint64_t base = (uint64_t)tile * kTile;
+  // tile-local 32-bit offsets: entry base + o is valid when o < rem
+  const uint32_t rem = (uint32_t)(n - base < (uint64_t)kTile ? n - base : (uint64_t)kTile);
+  const uint32_t wo = (uint32_t)warp * (kIpt * 32) + (uint32_t)lane;
+  const K* __restrict__ kt = kin + base;
+  const uint32_t* __restrict__ vt = vin + base;
+
+  if (rem == (uint32_t)kTile)
+    sweep_tile<K, true>(S, t, lane, warp, tile, kt, vt, kout, vout, goff, lookback, rem, wo, shift,
+                        err);
+  else
+    sweep_tile<K, false>(S, t, lane, warp, tile, kt, vt, kout, vout, goff, lookback, rem, wo,
+                         shift, err);
 }
 
 }  // namespace rs
