@@ -47,3 +47,19 @@ def test_two_ranks_take_the_slowest_step():
         assert o["world"] == 2 and o["local"] == o["rank"]
         assert o["ms"] == 3.0                       # the slower rank's 3 ms
         assert abs(o["value"] - 2 * 1000 / 3e-3) < 1e-6
+
+
+def test_captured_traffic_is_tied_to_workload_and_sources(monkeypatch):
+    """A DRAM-traffic figure is reported only for the workload it was captured
+    on and only while the digest of its kernel sources still matches."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for name, tr in list(bench.TRAFFIC.items()):
+        current = dict(tr, sources=bench._sources_sha(tr["files"]))
+        monkeypatch.setitem(bench.TRAFFIC, name, current)
+        assert bench._traffic(name, bench.TRAFFIC_WORKLOAD) == tr["bytes_per_launch"], name
+        other = ("clusters",) + tuple(bench.TRAFFIC_WORKLOAD[1:])
+        assert bench._traffic(name, other) is None
+        monkeypatch.setitem(bench.TRAFFIC, name, dict(tr, sources="0" * 16))
+        assert bench._traffic(name, bench.TRAFFIC_WORKLOAD) is None
+    assert bench._traffic("no_such_kernel", bench.TRAFFIC_WORKLOAD) is None
