@@ -117,3 +117,77 @@ def test_each_invalid_argument_is_named_before_any_device_work():
     assert rc == hlc.HLC_EINVAL and "B has NULL arrays" in msg
     rc, msg, _ = plan(_valid_params(), n_jobs=0)
     assert rc == hlc.HLC_EINVAL and "n_jobs" in msg
+
+
+def test_batched_plan_and_kernel_entry_points_reject_bad_arguments_on_the_host():
+    """Batched-plan consistency rules and the kernel-level entry points'
+    argument checks all return before the first device call."""
+    L = hlc.lib()
+    ra = np.array([10.0, 20.0])
+    dec = np.array([-5.0, 5.0])
+    ids = np.array([1, 2], dtype=np.uint64)
+
+    def cats(on_device=(0, 0)):
+        arr = (hlc.Catalog * 2)()
+        for j in range(2):
+            arr[j].ra_deg, arr[j].dec_deg = ra.ctypes.data, dec.ctypes.data
+            arr[j].id = ids.ctypes.data
+            arr[j].n, arr[j].on_device = 2, on_device[j]
+        return arr
+
+    def batched(mod, A=None, B=None):
+        ps = (hlc.Params * 2)(_valid_params(), _valid_params())
+        mod(ps)
+        out = ctypes.c_void_p()
+        rc = L.hlc_plan(A or cats(), B or cats(), ps, 2, ctypes.byref(out))
+        return rc, L.hlc_last_error().decode(), out.value
+
+    def quad(ps):
+        ps[1].boundary = hlc.HLC_QUAD
+
+    def mixed_precision(ps):
+        ps[1].precision = hlc.HLC_FP64
+
+    def bad_radius(ps):
+        ps[1].radius_arcsec = -2.0
+
+    rc, msg, out = batched(quad)
+    assert rc == hlc.HLC_EUNSUPPORTED and "complete boundary" in msg and not out
+    rc, msg, out = batched(mixed_precision)
+    assert rc == hlc.HLC_EINVAL and "share precision" in msg and not out
+    rc, msg, out = batched(bad_radius)
+    assert rc == hlc.HLC_EINVAL and "radius_arcsec" in msg and not out
+    rc, msg, out = batched(lambda ps: None, A=cats((0, 1)))
+    assert rc == hlc.HLC_EINVAL and "all on the host" in msg and not out
+
+    buf = np.zeros(64, dtype=np.float64)
+    p = buf.ctypes.data
+    assert L.hlc_ang2pix(p, p, 4, 15, hlc.HLC_FP64, p, None) == hlc.HLC_EINVAL
+    assert L.hlc_ang2pix(p, p, 4, 12, 9, p, None) == hlc.HLC_EINVAL
+    assert L.hlc_ang2pix(None, p, 4, 12, hlc.HLC_FP64, p, None) == hlc.HLC_EINVAL
+    assert b"NULL" in L.hlc_last_error()
+    assert L.hlc_neighbours(p, 4, -1, p, None) == hlc.HLC_EINVAL
+    assert L.hlc_neighbours(None, 4, 3, p, None) == hlc.HLC_EINVAL
+    assert L.hlc_quad_cells(p, p, 4, 0.0, 12, hlc.HLC_FP64, p, p, None) == hlc.HLC_EINVAL
+    assert L.hlc_quad_cells(p, p, 4, 1.0, 15, hlc.HLC_FP64, p, p, None) == hlc.HLC_EINVAL
+    assert L.hlc_quad_cells(p, p, 4, 1.0, 12, 7, p, p, None) == hlc.HLC_EINVAL
+    assert L.hlc_unitvec(p, None, 4, p, None) == hlc.HLC_EINVAL
+    for ks, kb in ((2, 8), (4, 0), (4, 33), (8, 65)):
+        assert L.hlc_sort_pairs(p, p, 4, ks, kb, None) == hlc.HLC_EINVAL, (ks, kb)
+        assert L.hlc_sort_pairs_noalloc(p, p, 4, ks, kb, None) == hlc.HLC_EINVAL, (ks, kb)
+    assert L.hlc_sort_pairs(None, p, 4, 4, 32, None) == hlc.HLC_EINVAL
+    assert L.hlc_sort_pairs_noalloc(p, p, 1 << 40, 4, 32, None) == hlc.HLC_EINVAL
+    assert b"use hlc_sort_pairs" in L.hlc_last_error()
+    m = ctypes.c_uint64()
+    assert L.hlc_cell_table(None, 4, p, p, ctypes.byref(m), None) == hlc.HLC_EINVAL
+    assert L.hlc_cell_table(p, 4, p, p, None, None) == hlc.HLC_EINVAL
+    assert L.hlc_learned_lookup(p, 4, 25, hlc.HLC_MODEL_PLA, p, 4, p, None, None) == \
+        hlc.HLC_EINVAL
+    assert L.hlc_learned_lookup(p, 4, 8, 7, p, 4, p, None, None) == hlc.HLC_EINVAL
+    assert L.hlc_learned_lookup(None, 4, 8, hlc.HLC_MODEL_PLA, p, 4, p, None, None) == \
+        hlc.HLC_EINVAL
+    res = hlc.Result()
+    assert L.hlc_match(None, ctypes.byref(res), None) == hlc.HLC_EINVAL
+    assert L.hlc_result_to_host(None, p, p, p, None) == hlc.HLC_EINVAL
+    assert L.hlc_canonical_coefficients(None, None) == hlc.HLC_EINVAL
+    L.hlc_free(None)  # a NULL plan is a no-op
