@@ -250,7 +250,7 @@ int hlc_sort_pairs(void* keys, uint32_t* vals, uint64_t n, int key_size,
  * a cudaMalloc/cudaFree (which can synchronise the device) is not acceptable.
  * This entry point performs the same stable sort, with the same arguments
  * and results, but takes every temporary buffer from one fixed device array
- * built into the library (about 17 MB, present on every device that loads
+ * built into the library (about 16 MB, present on every device that loads
  * the library until the process exits) and never allocates or frees memory.
  *   - n is limited to 1,048,576 elements; larger n returns HLC_EINVAL with a
  *     message naming the limit (use hlc_sort_pairs instead);
