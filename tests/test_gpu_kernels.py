@@ -109,7 +109,11 @@ def test_quad_cells_equal_oracle(order, r):
         np.testing.assert_array_equal(g, w)
 
 
-@pytest.mark.parametrize("n", [0, 1, 2, 1000, 3839, 3840, 3841, 3840 * 7 + 5, 1_000_003])
+# around the sort's tile of 4,608 keys (18 per thread x 256 threads): one
+# ragged tile, exactly one full tile, a full tile plus one key, whole full
+# tiles with no ragged tail, and many tiles with a ragged tail
+@pytest.mark.parametrize("n", [0, 1, 2, 1000, 3840, 4607, 4608, 4609, 4608 * 3, 4608 * 7 + 5,
+                               1_000_003])
 @pytest.mark.parametrize("ksize,bits", [(4, 28), (4, 9), (8, 64), (8, 40)])
 def test_sort_pairs_is_stable_sort(n, ksize, bits):
     rng = np.random.default_rng(n + bits)
