@@ -63,3 +63,49 @@ def test_captured_traffic_is_tied_to_workload_and_sources(monkeypatch):
         monkeypatch.setitem(bench.TRAFFIC, name, dict(tr, sources="0" * 16))
         assert bench._traffic(name, bench.TRAFFIC_WORKLOAD) is None
     assert bench._traffic("no_such_kernel", bench.TRAFFIC_WORKLOAD) is None
+
+
+def test_clock_record_rejects_slowdowns_and_unexplained_low_clocks(tmp_path):
+    """The bench's clock check: slowdown reasons or an SM clock stuck well
+    below its maximum with no reason reject a timed window; a power cap
+    alone does not.  The nvidia-smi CSV is parsed within the window only."""
+    sys.path.insert(0, ROOT)
+    import bench
+    ok = {"sm_mhz": 2032.0, "sm_max_mhz": 2032.0, "reasons": []}
+    assert bench.clocks_rejected(ok) == ""
+    assert bench.clocks_rejected(dict(ok, reasons=["sw_power_cap"])) == ""
+    assert bench.clocks_rejected(dict(ok, sm_mhz=1500.0, reasons=["sw_power_cap"])) == ""
+    assert "hw_slowdown" in bench.clocks_rejected(dict(ok, reasons=["hw_slowdown"]))
+    assert "sw_thermal_slowdown" in bench.clocks_rejected(
+        dict(ok, reasons=["sw_power_cap", "sw_thermal_slowdown"]))
+    assert "no reason" in bench.clocks_rejected(dict(ok, sm_mhz=1200.0))
+    assert bench.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None,
+                                  "reasons": ["nvidia-smi unavailable"]}) == ""
+
+    class _Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    path = tmp_path / "clocks.csv"
+    c = bench.Clocks(0, str(path))
+    c.f = open(path, "w")
+    rows = [  # before, inside (two samples), after the window
+        ("2026/01/01 00:00:00.000", 1000, "Not Active", "Not Active"),
+        ("2026/01/01 00:00:10.100", 2032, "Not Active", "Active"),
+        ("2026/01/01 00:00:10.300", 2010, "Not Active", "Not Active"),
+        ("2026/01/01 00:00:20.000", 900, "Active", "Not Active"),
+    ]
+    for ts, mhz, hw, cap in rows:
+        c.f.write(f"{ts}, 0, {mhz}, 2032, 700.0, 0x0, {hw}, Not Active, Not Active, {cap}\n")
+    c.f.flush()
+    c.proc = _Done()
+    import time as _t
+    c.t0 = _t.mktime(_t.strptime("2026/01/01 00:00:10", "%Y/%m/%d %H:%M:%S"))
+    c.t1 = c.t0 + 0.5
+    rec = c.stop()
+    assert rec["samples"] == 2 and rec["sm_max_mhz"] == 2032.0
+    assert rec["sm_mhz"] == 2021.0 and rec["reasons"] == ["sw_power_cap"]
+    assert bench.clocks_rejected(rec) == ""
