@@ -173,6 +173,34 @@ def run_hlc(args):
         hlc.hlc_free(plan)
         return st, n
 
+    def step_mode(precision, mode_):
+        plan = hlc.hlc_plan(A, B, r, L, coarse_level=Lc, boundary=mode_, precision=precision,
+                            stream=stream)
+        res = hlc.hlc_match(plan, copy=False)
+        st, n = res["stats"], res["n"]
+        hlc.hlc_free(plan)
+        return st, n
+
+    def timed_mode(fn, precision, mode_, K, W):
+        for _ in range(W):
+            fn(precision, mode_)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        sts = []
+        e0.record(stream)
+        for _ in range(K):
+            st, n = fn(precision, mode_)
+            sts.append(st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_ = e0.elapsed_time(e1) / K
+        if world > 1:
+            ms_ = max_over_ranks(ms_, dev)
+        return ms_, sts, n
+
     def timed(precision, K, W, clk=None):
         for _ in range(W):
             step(precision, A, B)
@@ -212,8 +240,26 @@ def run_hlc(args):
         ms, stats, nmatch = timed(prec, args.steps, args.warmup, clocks)
         clk = clocks.stop()
         clk["remeasured_after"] = why or "another rank's clock record"
+        # the second window is judged too: a throttled number is never
+        # reported unflagged
+        clk["still_rejected"] = clocks_rejected(clk)
     other = hlc.HLC_FP64 if prec == hlc.HLC_FP32_GUARD else hlc.HLC_FP32_GUARD
     ms_other, stats_other, _ = timed(other, max(2, args.steps // 2), 1)
+
+    def rows_of(precision, mode_):
+        """One untimed plan + match; the sorted rows on the host."""
+        plan = hlc.hlc_plan(A, B, r, L, coarse_level=Lc, boundary=mode_, precision=precision,
+                            stream=stream)
+        res = hlc.hlc_match(plan, copy=False)
+        out = (res["id_a"].cpu().numpy().view("u8"), res["id_b"].cpu().numpy().view("u8"),
+               res["sep"].cpu().numpy())
+        hlc.hlc_free(plan)
+        return out
+
+    # this run's rows in both forms: the plain form must return the same set
+    rows = rows_of(prec, mode)
+    rows_other = rows_of(other, mode)
+    plain_equal = rows_equal(rows, rows_other)
 
     def mean(key, S):
         return sum(s[key] for s in S) / len(S)
@@ -302,10 +348,38 @@ def run_hlc(args):
         e2e = {"value": sources / t, "unit": "sources/s", "ms_per_step": t * 1e3, "steps": ke,
                "h2d_bytes_per_step": (na + nb) * 24, "d2h_bytes_per_step": int(ia.size) * 24}
 
-    # CPU oracle on a bounded sample of the same workload (rank 0 only)
-    cpu = None
+    # CPU oracle on a bounded sample of the same workload (rank 0 only), and
+    # this run's rows against it
+    cpu = parity = None
     if rank == 0 and not args.no_cpu and args.workload == "fullsky":
-        cpu = cpu_baseline(A, B, r, L)
+        cpu, ores = cpu_baseline(A, B, r, L, mode == hlc.HLC_QUAD)
+        parity = oracle_parity(A, r, ores, rows, 0.0, 180.0)
+
+    # the other boundary mode of the same workload (BASELINE config 2 names
+    # both), timed and checked the same way on a narrower oracle sample
+    other_mode = None
+    if args.workload == "fullsky" and not args.no_other_mode:
+        omode = hlc.HLC_COMPLETE8 if mode == hlc.HLC_QUAD else hlc.HLC_QUAD
+        ko = max(3, args.steps // 4)
+        ms_q, st_q, n_q = timed_mode(step_mode, prec, omode, ko, 2)
+        ms_q64, _, _ = timed_mode(step_mode, other, omode, max(2, ko // 2), 1)
+        rq, rq64 = rows_of(prec, omode), rows_of(other, omode)
+        oq = None
+        if rank == 0 and not args.no_cpu:
+            _, oresq = cpu_baseline(A, B, r, L, omode == hlc.HLC_QUAD, 0.0, 30.0)
+            oq = oracle_parity(A, r, oresq, rq, 0.0, 30.0)
+        other_mode = {"boundary": "quad" if omode == hlc.HLC_QUAD else "complete",
+                      "ms_per_step": ms_q, "value": sources / (ms_q / 1e3), "unit": "sources/s",
+                      "steps": ko, "matches": n_q,
+                      "quad_duplicates": st_q[-1]["quad_duplicates"],
+                      "plain_form": {"ms_per_step": ms_q64, "value": sources / (ms_q64 / 1e3),
+                                     **rows_equal(rq, rq64)},
+                      "parity": oq}
+
+    # dense cells: the pair test where it is bound by the FP32 pipe
+    dense = None
+    if args.workload == "fullsky" and not args.no_dense:
+        dense = dense_line(args, hlc, synth, dev, stream, rank, world)
 
     if rank == 0:
         line = {
@@ -328,8 +402,16 @@ def run_hlc(args):
             "tile_items": stats[-1]["tile_items"], "tile_entries_a": stats[-1]["tile_entries_a"],
             "plain_form": {"precision": "fp64" if other == hlc.HLC_FP64 else "fp32",
                            "ms_per_step": ms_other, "value": sources / (ms_other / 1e3),
-                           "stages_ms": {k: mean(k, stats_other) for k in stage_ms}},
+                           "stages_ms": {k: mean(k, stats_other) for k in stage_ms},
+                           "equal_to_chosen": plain_equal["equal"],
+                           "rows": plain_equal["rows"],
+                           "max_sep_diff_arcsec": plain_equal["max_sep_diff_arcsec"]},
+            "parity": parity,
+            "critical_path_ms": critical_path(stats, ms),
             "stages_ms": stage_ms,
+            "stages_note": "busy time per stage summed over both catalogues; stages of the "
+                           "two catalogues overlap on two streams, so they do not add up to "
+                           "ms_per_step (critical_path_ms does)",
             "roofline": roofline,
             "roofline_pair": roofline_pair,
             "cpu_baseline": cpu,
@@ -337,6 +419,10 @@ def run_hlc(args):
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
             "clocks": clk,
         }
+        if other_mode is not None:
+            line["other_mode"] = other_mode
+        if dense is not None:
+            line["dense"] = dense
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -426,27 +512,134 @@ def _mega(n):
     return "%gM" % (n / 1e6) if n >= 1_000_000 else str(n)
 
 
-def cpu_baseline(A, B, r, L):
+def cpu_baseline(A, B, r, L, quad=False, lo=0.0, hi=180.0):
     """The oracle, as it stands, on the sources of both catalogues with RA in
-    [0, 180) deg (half of the same synthetic sky), single-threaded."""
+    [lo, hi) deg (by default half of the same synthetic sky), single-threaded.
+    Returns the baseline record and the oracle's rows."""
     import numpy as np
 
     import oracle as O
     ra_a, dec_a, id_a = (x.cpu().numpy() for x in (A.ra, A.dec, A.id))
     ra_b, dec_b, id_b = (x.cpu().numpy() for x in (B.ra, B.dec, B.id))
-    sa = ra_a < 180.0
-    sb = ra_b < 180.0
+    sa = (ra_a >= lo) & (ra_a < hi)
+    sb = (ra_b >= lo) & (ra_b < hi)
     t0 = time.perf_counter()
     res = O.match(ra_a[sa], dec_a[sa], id_a[sa].view(np.uint64), ra_b[sb], dec_b[sb],
-                  id_b[sb].view(np.uint64), r, L, O.COMPLETE)
+                  id_b[sb].view(np.uint64), r, L, O.QUAD if quad else O.COMPLETE)
     t = time.perf_counter() - t0
     n = int(sa.sum() + sb.sum())
-    return {"value": n / t, "unit": "sources/s", "cores": 1, "kind": "oracle",
-            "sample": "sources with RA in [0,180) of both catalogues (%d sources, %d matches)"
-                      % (n, res["id_a"].size), "seconds": t}
+    rec = {"value": n / t, "unit": "sources/s", "cores": 1, "kind": "oracle",
+           "sample": "sources with RA in [%g,%g) of both catalogues (%d sources, %d matches, "
+                     "%s mode)" % (lo, hi, n, res["id_a"].size, "quad" if quad else "complete"),
+           "seconds": t}
+    return rec, res
 
 
-def _timed_loop(fn, K, W, stream):
+def rows_equal(x, y) -> dict:
+    """Equality of two sorted row sets (id_a, id_b, sep) from two forms of the
+    library, and the largest separation difference."""
+    import numpy as np
+    eq = (x[0].size == y[0].size and bool(np.array_equal(x[0], y[0]))
+          and bool(np.array_equal(x[1], y[1])))
+    d = float(np.max(np.abs(x[2] - y[2]))) if eq and x[2].size else (0.0 if eq else None)
+    return {"equal": eq, "rows": int(x[0].size), "max_sep_diff_arcsec": d}
+
+
+def oracle_parity(A, r, ores, rows, lo, hi) -> dict:
+    """This run's rows against the oracle's on its RA band [lo, hi): the A
+    sources whose whole r-disc lies inside the band (RA at least twice the
+    disc's RA half-width r / cos(dec) from either edge, |dec| < 89.9) have
+    every partner in the oracle's sample, so their rows must be equal bit for
+    bit and their separations within 1e-6 arcsec."""
+    import numpy as np
+    ra, dec, ida = (x.cpu().numpy() for x in (A.ra, A.dec, A.id))
+    ida = ida.view(np.uint64)
+    cosd = np.cos(np.radians(dec))
+    w = 2.0 * (r / 3600.0) / np.maximum(cosd, 1e-12) + 1e-6
+    inside = (ra >= lo + w) & (ra < hi - w) & (np.abs(dec) < 89.9)
+    keep = np.sort(ida[inside])
+    g = np.isin(rows[0], keep)
+    o = np.isin(ores["id_a"], keep)
+    ga, gb, gs = rows[0][g], rows[1][g], rows[2][g]
+    oa, ob, os_ = ores["id_a"][o], ores["id_b"][o], ores["sep"][o]
+    eq = ga.size == oa.size and bool(np.array_equal(ga, oa)) and bool(np.array_equal(gb, ob))
+    err = float(np.max(np.abs(gs - os_))) if eq and ga.size else (0.0 if eq else None)
+    return {"equal": eq, "rows": int(ga.size), "oracle_rows": int(oa.size),
+            "a_sources": int(inside.sum()), "max_sep_err_arcsec": err,
+            "sep_tolerance_arcsec": 1e-6, "sep_within_tolerance": bool(eq and err <= 1e-6),
+            "sample": "A sources with RA in [%g,%g) deg whose r-disc lies inside the band" % (lo, hi)}
+
+
+def critical_path(stats, ms_step) -> dict:
+    """Consecutive intervals on the plan stream that add up to the step: the
+    plan (its sort passes and, in the two-stream build, the part before them),
+    the match's stages, and the rest of the step (host gaps, hlc_free)."""
+    n = len(stats)
+
+    def mean(k):
+        return sum(s[k] for s in stats) / n
+    plan = mean("ms_plan_span")
+    pre = mean("ms_plan_presort")
+    passes = mean("ms_sort_passes") if pre > 0 else 0.0
+    out = {}
+    if pre > 0:
+        out["plan_preps_and_histograms"] = pre
+        out["plan_sort_passes"] = passes
+        out["plan_payloads_table_dense_cells"] = plan - pre - passes
+    else:
+        out["plan"] = plan
+    for k in ("ms_candidates", "ms_pair", "ms_recheck", "ms_output"):
+        out["match_" + k[3:]] = mean(k)
+    out["host_gaps_and_free"] = ms_step - sum(out.values())
+    return out
+
+
+def dense_line(args, hlc, synth, dev, stream, rank, world):
+    """Dense cells, where the pair test is bound by the FP32 pipe: the
+    clustered workload at a reduced size (galactic mixture + Plummer clusters
+    of 50k members, a = 2 arcmin, r = 1 arcsec, fine order 13).  Pair tests/s
+    = algorithmic tests / pair-stage time, against SMs x 128 x f / 6 (six
+    FP32 FMA-pipe instructions per test) at the median SM clock sampled in
+    the timed window."""
+    import torch
+    n = args.dense_n
+    ncl = max(1, n // 2_000_000)
+    A, B = synth.clustered_pair(seed=2301073312 + rank, na=n, nb=n * 3 // 4, n_clusters=ncl,
+                                device=dev)
+    r, L, Lc = 1.0, 13, 3
+
+    def step():
+        plan = hlc.hlc_plan(A, B, r, L, coarse_level=Lc, stream=stream)
+        res = hlc.hlc_match(plan, copy=False)
+        st_ = res["stats"]
+        hlc.hlc_free(plan)
+        return st_
+    K = max(3, args.steps // 10)
+    clocks = Clocks(torch.cuda.current_device(), args.clocks_out + ".dense" if args.clocks_out
+                    else "")
+    clocks.start()
+    ms, sts = _timed_loop(lambda: step(), K, 2, stream, collect=True)
+    clk = clocks.stop()
+    alg = alg_pair_tests(hlc, A, B, L)
+    ms_pair = sum(s["ms_pair"] for s in sts) / len(sts)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_mhz = clk.get("sm_mhz") or 2032.0
+    peak = sms * 128 * f_mhz * 1e6 / 6
+    tps = alg / (ms_pair / 1e3)
+    last = sts[-1]
+    return {"workload": "clusters %s x %s (%d Plummer clusters), r=1 arcsec, fine order 13"
+                        % (_mega(n), _mega(n * 3 // 4), ncl),
+            "ms_per_step": ms, "value": (n + n * 3 // 4) / (ms / 1e3), "unit": "sources/s",
+            "steps": K, "pair_tests_alg": alg, "pair_tests_executed": last["pair_tests"],
+            "ms_pair": ms_pair, "pair_tests_per_s": tps,
+            "fp32_bound": {"peak_tests_per_s": peak, "frac": tps / peak, "sms": sms,
+                           "sm_mhz": f_mhz,
+                           "basis": "SMs x 128 FP32 lanes x SM clock / 6 instructions per test"},
+            "tile_items": last["tile_items"], "tile_entries_a": last["tile_entries_a"],
+            "matches": last["matches"], "clocks": clk}
+
+
+def _timed_loop(fn, K, W, stream, collect=False):
     import torch
     for _ in range(W):
         fn()
@@ -455,11 +648,14 @@ def _timed_loop(fn, K, W, stream):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     out = None
+    outs = []
     for _ in range(K):
         out = fn()
+        if collect:
+            outs.append(out)
     e1.record(stream)
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / K, out
+    return e0.elapsed_time(e1) / K, (outs if collect else out)
 
 
 def _line(args, metric, value, unit, ms, config, **extra):
@@ -717,6 +913,11 @@ def main():
     ap.add_argument("--mode", default="complete", choices=["complete", "quad"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-other-mode", action="store_true",
+                    help="skip the other boundary mode's sub-line")
+    ap.add_argument("--no-dense", action="store_true", help="skip the dense-cell sub-line")
+    ap.add_argument("--dense-n", type=int, default=20_000_000,
+                    help="A sources of the dense-cell sub-line (B = 3/4 of it)")
     ap.add_argument("--clocks-out", default="",
                     help="file for the nvidia-smi samples of the timed region "
                          "(default: one in the temporary directory)")

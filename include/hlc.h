@@ -161,6 +161,14 @@ typedef struct {
                                       timed digit passes, summed over the
                                       launches (with device inputs one launch
                                       per pass sorts both catalogues) */
+  float ms_plan_span;              /* hlc_plan's own span on the plan stream
+                                      (ms_total = ms_plan_span + ms_candidates
+                                      + ms_pair + ms_recheck + ms_output for
+                                      single plans: consecutive intervals) */
+  float ms_plan_presort;           /* FP32 complete form with device inputs:
+                                      from the plan's start to the first digit
+                                      pass (both preps, side by side, and the
+                                      digit histograms); else 0 */
 } hlc_stats;
 
 typedef struct hlc_plan_s hlc_plan_t;
@@ -254,16 +262,36 @@ int hlc_sort_pairs(void* keys, uint32_t* vals, uint64_t n, int key_size,
  * the library until the process exits) and never allocates or frees memory.
  *   - n is limited to 1,048,576 elements; larger n returns HLC_EINVAL with a
  *     message naming the limit (use hlc_sort_pairs instead);
- *   - the first call on a device looks up the array's device address (with
- *     that device current), so make the first call on each device before any
- *     stream capture;
+ *   - every call looks up the array's address on the current device (no
+ *     address is cached, so a device reset that reloads the library's module
+ *     is handled); the first call on a device may load that module, so make
+ *     the first call on each device before any stream capture;
  *   - all calls share the one array: calls that overlap on the GPU (other
  *     streams, other host threads) race and corrupt each other's results;
  *     the array keeps the last call's contents, and each call clears what
  *     must start at zero;
- *   - synchronises the stream before returning. */
+ *   - synchronises the stream before returning, on success and on every
+ *     error after the array's address was taken. */
 int hlc_sort_pairs_noalloc(void* keys, uint32_t* vals, uint64_t n, int key_size,
                            int key_bits, void* stream);
+
+/* ---- test hooks (no counterpart in the paper) -----------------------------
+ * Every device-side wait of the library (the radix sort's and the scans'
+ * look-back on a predecessor tile, the tile kernel's mbarrier waits) polls at
+ * most a fixed number of times, then records HLC_ETIMEOUT and returns.  These
+ * two calls let a test watch that happen without hanging or faulting a GPU. */
+
+/* Shift every wait's poll limit right by `shift` (0..24) on the current
+ * device; 0 restores the production limits.  Affects every later launch on
+ * that device until changed again.  HLC_EINVAL outside 0..24. */
+int hlc_test_spin_shift(int shift);
+
+/* Run one of the library's bounded waits against a flag that nothing sets:
+ * which = 0 the radix sort's look-back, 1 the scans' look-back, 2 the tile
+ * kernel's mbarrier wait.  The kernel gives up after its (shifted) limit and
+ * the call returns HLC_ETIMEOUT; the context stays usable.  Allocates a few
+ * KB with cudaMallocAsync on the stream and synchronises it. */
+int hlc_test_unset_wait(int which, void* stream);
 
 /* Run-length table of sorted uint32 keys: unique keys uniq[0..m) and
  * start[0..m] (start[m] = n); *m_out receives m (host).  uniq and start must

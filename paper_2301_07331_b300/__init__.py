@@ -79,7 +79,9 @@ class Stats(C.Structure):
                                           "ms_stream_groups", "ms_stream_merge",
                                           "ms_sort_passes")] + [("sort_passes", C.c_uint32),
                                                                 ("band_fp64", C.c_uint64),
-                                                                ("sort_entries", C.c_uint64)]
+                                                                ("sort_entries", C.c_uint64),
+                                                                ("ms_plan_span", C.c_float),
+                                                                ("ms_plan_presort", C.c_float)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -120,6 +122,8 @@ def lib():
     L.hlc_sort_pairs_noalloc.argtypes = [P, P, u64, i32, i32, P]
     L.hlc_cell_table.argtypes = [P, u64, P, P, C.POINTER(C.c_uint64), P]
     L.hlc_learned_lookup.argtypes = [P, u64, i32, i32, P, u64, P, P, P]
+    L.hlc_test_spin_shift.argtypes = [i32]
+    L.hlc_test_unset_wait.argtypes = [i32, P]
     _lib = L
     return L
 

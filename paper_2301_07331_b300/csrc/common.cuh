@@ -174,7 +174,37 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-inline unsigned grid_for(uint64_t n, int block, unsigned cap = 148u * 64u) {
+// Test hook: every bounded device wait gives up after its spin limit shifted
+// right by d_spin_shift (0, the default, keeps the production limits; set
+// through hlc_test_spin_shift).
+__device__ int d_spin_shift = 0;
+__device__ __forceinline__ long long spin_limit(long long base) { return base >> d_spin_shift; }
+
+// Streaming multiprocessors of the current device (queried once per device;
+// grids are sized in multiples of it).
+inline unsigned num_sms() {
+  static std::atomic<unsigned> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 148u;
+  }
+  unsigned v = cache[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 148;
+    }
+    v = (unsigned)n;
+    cache[dev].store(v, std::memory_order_relaxed);
+  }
+  return v;
+}
+
+// Blocks for n items of `block` threads, at most `cap` (0: 64 per SM).
+inline unsigned grid_for(uint64_t n, int block, unsigned cap = 0) {
+  if (cap == 0) cap = num_sms() * 64u;
   uint64_t g = (n + block - 1) / block;
   if (g == 0) g = 1;
   if (g > cap) g = cap;

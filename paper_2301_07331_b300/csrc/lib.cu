@@ -462,7 +462,7 @@ static int build_learned(Arena& ar, const uint32_t* uniq, uint64_t m, int shift,
   } else {
     float* w3 = ar.get_n<float>(P * (kMlpH + 1) + 1);
     if (!w3) return HLC_ENOMEM;
-    k_mlp_fit<<<(unsigned)std::min<uint64_t>(P, 148u * 8u), 256, 0, st>>>(uniq, part, P, shift,
+    k_mlp_fit<<<(unsigned)std::min<uint64_t>(P, num_sms() * 8u), 256, 0, st>>>(uniq, part, P, shift,
                                                                           w3);
     HLC_LAUNCH_CHECK();
     L.w3 = w3;
@@ -492,7 +492,7 @@ static int offset_table(hlc_plan_t* P, const uint32_t* keys, uint64_t m, int shi
   k_table_bounds<<<grid_for(32 * (nt + 1), kThreads), kThreads, 0, st>>>(keys, m, shift, S, nt,
                                                                          bnd);
   HLC_LAUNCH_CHECK();
-  k_table_tiles<<<(unsigned)std::min<uint64_t>(nt, 148u * 64u), kTabThreads, 0, st>>>(
+  k_table_tiles<<<(unsigned)std::min<uint64_t>(nt, num_sms() * 64u), kTabThreads, 0, st>>>(
       keys, m, shift, S, nt, bnd, T, heads, dense_above, ndense);
   HLC_LAUNCH_CHECK();
   ar.drop(bnd);
@@ -561,7 +561,7 @@ static int dense_fixup(hlc_plan_t* P, CatDev& X, const uint32_t* T, int shift, b
   HLC_TRY(cell_table(dkey, nd, 0, cell_of, X.tile_cell, X.tile_start, X.tile_n, rscr, P->dev_err,
                      st));
   HLC_CUDA(cudaMemsetAsync(X.tiled, 0, n + 1, st));
-  k_mark_tiled<<<grid_for(nd, kThreads, 148u * 8u), kThreads, 0, st>>>(X.tile_start, dpos,
+  k_mark_tiled<<<grid_for(nd, kThreads, num_sms() * 8u), kThreads, 0, st>>>(X.tile_start, dpos,
                                                                        X.tile_n, X.tiled);
   HLC_LAUNCH_CHECK();
   X.tile_dpos = dpos;
@@ -582,7 +582,7 @@ static int dense_fixup(hlc_plan_t* P, CatDev& X, const uint32_t* T, int shift, b
     ta.bix.table = P->B.table;
     ta.bix.shift = P->B.table_shift;
     ta.order = P->join_level;
-    k_tile_items<false><<<148u * 16u, 256, 0, st>>>(ta, X.tile_items, X.tile_nprep, cap);
+    k_tile_items<false><<<num_sms() * 16u, 256, 0, st>>>(ta, X.tile_items, X.tile_nprep, cap);
     HLC_LAUNCH_CHECK();
   }
   ar.drop(cell_of);
@@ -619,7 +619,7 @@ static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
     k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
         ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, slow, P->ctr + C_SLOW, P->dev_err);
     HLC_LAUNCH_CHECK();
-    k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key);
+    k_prep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key);
     HLC_LAUNCH_CHECK();
     ar.drop(slow);
   }
@@ -717,7 +717,7 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
         inA->ra_deg, inA->dec_deg, inA->id, na, L, pix_const(L), XA.key, XA.idx, XA.rec, slow_a,
         P->ctr + C_SLOW_A, P->dev_err);
     HLC_LAUNCH_CHECK();
-    k_prep_fallback<<<148 * 4, kThreads, 0, ks>>>(inA->ra_deg, inA->dec_deg, L, slow_a,
+    k_prep_fallback<<<num_sms() * 4u, kThreads, 0, ks>>>(inA->ra_deg, inA->dec_deg, L, slow_a,
                                                   P->ctr + C_SLOW_A, XA.key);
     HLC_LAUNCH_CHECK();
   }
@@ -727,7 +727,7 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
         inB->ra_deg, inB->dec_deg, inB->id, nb, L, pix_const(L), XB.key, XB.idx, XB.rec, slow_b,
         P->ctr + C_SLOW, P->dev_err);
     HLC_LAUNCH_CHECK();
-    k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(inB->ra_deg, inB->dec_deg, L, slow_b,
+    k_prep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(inB->ra_deg, inB->dec_deg, L, slow_b,
                                                   P->ctr + C_SLOW, XB.key);
     HLC_LAUNCH_CHECK();
   }
@@ -855,7 +855,7 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
             ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, slow, P->ctr + C_SLOW,
             P->dev_err);
         HLC_LAUNCH_CHECK();
-        k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key);
+        k_prep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key);
         HLC_LAUNCH_CHECK();
         ar.drop(slow);
       } else {
@@ -880,7 +880,7 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
             ra, dec, id, n, R, L, pix_const(L), X.cells5, cnt, X.rec, slow, P->ctr + C_SLOW,
             P->dev_err);
         HLC_LAUNCH_CHECK();
-        k_quad_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, R, L, slow, P->ctr + C_SLOW,
+        k_quad_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(ra, dec, R, L, slow, P->ctr + C_SLOW,
                                                       X.cells5, cnt);
         HLC_LAUNCH_CHECK();
         ar.drop(slow);
@@ -1119,7 +1119,7 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
         if (stage[i][k]) P->arena->drop(stage[i][k]);
   }
   if (rc == HLC_OK && P->A.n && !P->table_buckets) {
-    k_id_diff_rec<<<grid_for(P->A.n, kThreads, 148u * 8u), kThreads, 0, st>>>(P->A.rec, P->A.n,
+    k_id_diff_rec<<<grid_for(P->A.n, kThreads, num_sms() * 8u), kThreads, 0, st>>>(P->A.rec, P->A.n,
                                                                               P->ctr + C_IDDIFF);
     if (cudaGetLastError() != cudaSuccess) rc = HLC_ECUDA;
   }
@@ -1171,6 +1171,7 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   P->stats.sort_entries = P->sort_entries;
   for (int i = 0; i < 2; ++i)
     if (P->sort_timed[i]) P->stats.ms_sort_passes += ev_ms(P, 7 + 2 * i, 8 + 2 * i);
+  if (side && P->sort_timed[0]) P->stats.ms_plan_presort = ev_ms(P, 0, 7);
   P->plan_launches = g_launches.load() - P->launches0;
   *out = P;
   return HLC_OK;
@@ -1218,7 +1219,7 @@ static int order_rows(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_t* bhist
     k_bucket_small<<<g, kThreads, 0, st>>>(t, M, bshift, bmask, jbk, boff, a, b, sp, jb, big,
                                            (uint32_t*)(P->ctr + C_MAXB), P->dev_err);
     HLC_LAUNCH_CHECK();
-    k_bucket_sort<<<148u * 8u, kBucketThreads, 0, st>>>(t, boff, big,
+    k_bucket_sort<<<num_sms() * 8u, kBucketThreads, 0, st>>>(t, boff, big,
                                                          (uint32_t*)(P->ctr + C_MAXB),
                                                          want_sep ? 1 : 0, a, b, sp, jb);
     HLC_LAUNCH_CHECK();
@@ -1314,7 +1315,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
                   P->ctr + C_TESTS, P->ctr + C_DUPS,
                   P->table_buckets ? nullptr : P->ctr + C_HEADS_A, P->dev_err};
     if (A.m && B.m) {
-      unsigned grid = grid_for(A.m, kThreads, 148u * 16u);
+      unsigned grid = grid_for(A.m, kThreads, num_sms() * 16u);
       PairArgs pa;
       pa.mA = A.m;
       pa.keyA = A.key;
@@ -1371,7 +1372,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
         const int smem = 2 * kTileCap * 16;
         HLC_CUDA(cudaFuncSetAttribute(k_pair_tile,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        k_pair_tile<<<148 * 3, kTileThreads + 32, smem, st>>>(ta, sink);
+        k_pair_tile<<<num_sms() * 3u, kTileThreads + 32, smem, st>>>(ta, sink);
         HLC_LAUNCH_CHECK();
       }
     }
@@ -1393,7 +1394,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   ev_record(P, 4);
   if (fp32 && h[C_BAND]) {
     // (the table-cell form's rows already hold source indices)
-    k_recheck<<<grid_for(h[C_BAND], kThreads, 148u * 16u), kThreads, 0, st>>>(
+    k_recheck<<<grid_for(h[C_BAND], kThreads, num_sms() * 16u), kThreads, 0, st>>>(
         band, P->ctr + C_BAND, bcap, P->table_buckets ? nullptr : A.idx,
         P->table_buckets ? nullptr : B.idx, A.rec, B.rec, P->C, P->r_lo, P->r_hi, rows,
         P->ctr + C_ROWS, cap, P->ctr + C_BAND64, P->dev_err);
@@ -1474,6 +1475,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   P->stats.ms_pair = ev_ms(P, 3, 4);
   P->stats.ms_recheck = ev_ms(P, 4, 5);
   P->stats.ms_output = ev_ms(P, 5, 6);
+  P->stats.ms_plan_span = ev_ms(P, 0, 1);
   P->stats.ms_total = ev_ms(P, 0, 1) + ev_ms(P, 2, 6);
   P->stats.kernel_launches = (g_launches.load() - launches_match0) + P->plan_launches;
   if (stats) *stats = P->stats;
@@ -1713,7 +1715,7 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
         k_bprep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
             P->jobs_d, offd[s], njobs, s, n, P->cell_bits, keys[s], X.idx, slow, P->ctr + C_SLOW,
             P->dev_err);
-        k_bprep_fallback<<<148 * 4, kThreads, 0, st>>>(P->jobs_d, offd[s], njobs, s, P->cell_bits,
+        k_bprep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(P->jobs_d, offd[s], njobs, s, P->cell_bits,
                                                        slow, P->ctr + C_SLOW, keys[s]);
       } else {
         k_bprep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
@@ -1802,7 +1804,7 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
     ar.drop(scr);
   }
   if (rc == HLC_OK && NA) {
-    k_id_diff<<<grid_for(NA, kThreads, 148u * 8u), kThreads, 0, st>>>(P->A.id_s, NA,
+    k_id_diff<<<grid_for(NA, kThreads, num_sms() * 8u), kThreads, 0, st>>>(P->A.id_s, NA,
                                                                       P->ctr + C_IDDIFF);
     ++g_launches;
   }
@@ -1825,7 +1827,7 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
     if (rc) return fail(rc);
     k_run_starts<<<grid_for(NA, kThreads), kThreads, 0, st>>>(flag, off, NA, P->A.tile_n,
                                                                P->A.tile_start);
-    k_mark_tiled<<<grid_for(NA, kThreads, 148u * 8u), kThreads, 0, st>>>(
+    k_mark_tiled<<<grid_for(NA, kThreads, num_sms() * 8u), kThreads, 0, st>>>(
         P->A.tile_start, nullptr, P->A.tile_n, P->A.tiled);
     g_launches += 2;
     const uint64_t cap = NA / kTileMinA + 1;
@@ -1841,7 +1843,7 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
     tp.btable = P->btable;
     tp.jobs = P->jobs_d;
     tp.cell_bits = P->cell_bits;
-    k_tile_items<true><<<148u * 16u, 256, 0, st>>>(tp, P->A.tile_items, P->A.tile_nprep, cap);
+    k_tile_items<true><<<num_sms() * 16u, 256, 0, st>>>(tp, P->A.tile_items, P->A.tile_nprep, cap);
     ++g_launches;
     ar.drop(flag);
     ar.drop(off);
@@ -1939,9 +1941,9 @@ static int batched_pair_graph(hlc_plan_t* P, uint2* rows, uint64_t cap, uint2* b
     pa.tiled = P->A.tiled;
     if (P->A.m && P->B.m) {
       if (fp32)
-        k_bpair<true><<<148 * 8, kThreads, 0, cs>>>(pa, sink);
+        k_bpair<true><<<num_sms() * 8u, kThreads, 0, cs>>>(pa, sink);
       else
-        k_bpair<false><<<148 * 8, kThreads, 0, cs>>>(pa, sink);
+        k_bpair<false><<<num_sms() * 8u, kThreads, 0, cs>>>(pa, sink);
       if (fp32 && P->A.tiled) {
         TileArgs ta{};
         ta.items = P->A.tile_items;
@@ -1955,7 +1957,7 @@ static int batched_pair_graph(hlc_plan_t* P, uint2* rows, uint64_t cap, uint2* b
         ta.btable = P->btable;
         ta.jobs = P->jobs_d;
         ta.cell_bits = P->cell_bits;
-        k_pair_tile<<<148 * 3, kTileThreads + 32, tile_smem, cs>>>(ta, sink);
+        k_pair_tile<<<num_sms() * 3u, kTileThreads + 32, tile_smem, cs>>>(ta, sink);
       }
     }
     e = cudaStreamEndCapture(cs, &g);
@@ -2022,7 +2024,7 @@ static int match_batched(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   P->row_cap = std::max<uint64_t>(P->row_cap, cap);
   ev_record(P, 4);
   if (fp32 && h[C_BAND]) {
-    k_brecheck<<<grid_for(h[C_BAND], kThreads, 148u * 16u), kThreads, 0, st>>>(
+    k_brecheck<<<grid_for(h[C_BAND], kThreads, num_sms() * 16u), kThreads, 0, st>>>(
         band, P->ctr + C_BAND, bcap, P->keyA64, P->cell_bits, P->jobs_d, A.rd, B.rd, rows,
         P->ctr + C_ROWS, cap, P->ctr + C_BAND64, P->dev_err);
     HLC_LAUNCH_CHECK();
@@ -2115,6 +2117,7 @@ static int match_batched(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   P->stats.ms_pair = ev_ms(P, 3, 4);
   P->stats.ms_recheck = ev_ms(P, 4, 5);
   P->stats.ms_output = ev_ms(P, 5, 6);
+  P->stats.ms_plan_span = ev_ms(P, 0, 1);
   P->stats.ms_total = ev_ms(P, 0, 1) + ev_ms(P, 2, 6);
   P->stats.kernel_launches = (g_launches.load() - launches_match0) + P->plan_launches;
   if (stats) *stats = P->stats;
@@ -2543,7 +2546,7 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
             int b) {
           HLC_CUDA(cudaMemsetAsync(gcnt[b], 0, (ngroups + 1) * 4, s));
           HLC_CUDA(cudaMemsetAsync(gcur[b], 0, (ngroups + 1) * 4, s));
-          k_group_hist<<<grid_for(n, kThreads, 148u * 4u), kThreads, gsmem / 2, s>>>(
+          k_group_hist<<<grid_for(n, kThreads, num_sms() * 4u), kThreads, gsmem / 2, s>>>(
               r, d, n, Lf, Lc, side, K, cell2group, ngroups, gcnt[b]);
           HLC_LAUNCH_CHECK();
           k_small_excl_scan<<<1, 1024, 0, s>>>(gcnt[b], ngroups, goff[b]);
@@ -2567,7 +2570,7 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
             if (!bra[b] || !bdec[b] || !bid[b]) return HLC_ENOMEM;
             HLC_CUDA(cudaStreamSynchronize(st));  // allocations are ordered on the plan stream
           }
-          k_group_scatter<<<grid_for(n, kThreads, 148u * 4u), kThreads, gsmem, s>>>(
+          k_group_scatter<<<grid_for(n, kThreads, num_sms() * 4u), kThreads, gsmem, s>>>(
               r, d, id, n, Lf, Lc, side, K, cell2group, ngroups, goff[b], gcur[b], bra[b],
               bdec[b], bid[b], err);
           HLC_LAUNCH_CHECK();
@@ -2887,7 +2890,7 @@ int hlc_ang2pix(const double* ra, const double* dec, uint64_t n, int order, int 
     cudaMemsetAsync(nslow, 0, 8, st);
     k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
         ra, dec, nullptr, n, order, pix_const(order), pix, idx, nullptr, slow, nslow, err);
-    k_prep_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, order, slow, nslow, pix);
+    k_prep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(ra, dec, order, slow, nslow, pix);
   } else {
     k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
         ra, dec, nullptr, n, order, pix_const(order), pix, idx, nullptr, nullptr, nullptr, err);
@@ -2982,7 +2985,7 @@ int hlc_quad_cells(const double* ra, const double* dec, uint64_t n, double radiu
     k_quad_cells<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
         ra, dec, nullptr, n, R, order, pix_const(order), out, (uint32_t*)count, nullptr, slow,
         nslow, err);
-    k_quad_fallback<<<148 * 4, kThreads, 0, st>>>(ra, dec, R, order, slow, nslow, out,
+    k_quad_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(ra, dec, R, order, slow, nslow, out,
                                                   (uint32_t*)count);
     rc = cudaGetLastError() == cudaSuccess ? HLC_OK : HLC_ECUDA;
     cudaFreeAsync(slow, st);
@@ -3169,6 +3172,83 @@ int hlc_learned_lookup(const uint32_t* uniq, uint64_t m, int shift, int model,
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Test hooks: shortened spin limits, and each kind of bounded device wait run
+// against a flag that nothing sets, so that tests can watch a wait give up
+// and the error reach the caller without faulting or hanging the GPU.
+// ---------------------------------------------------------------------------
+namespace hlc {
+
+constexpr int kTestWords = 2 * rs::kRadix;  // look-back words of tiles 0 and 1
+
+__global__ void k_test_unset_wait(int which, unsigned long long* words, int* err) {
+  if (which == 0) {
+    // the radix sort's look-back: tile 1 waits for tile 0's digit counts
+    (void)rs::lookback_excl(words, 1, (int)threadIdx.x, err);
+  } else if (which == 1) {
+    // the scan's look-back (one warp): tile 1 waits for tile 0's prefix
+    if (threadIdx.x < 32) (void)sc::lookback_prefix(1, 5, words, err);
+  } else {
+    // the tile kernel's stage wait: an mbarrier expecting one arrival
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (!mbar_wait(&bar, 0) && (threadIdx.x & 31) == 0) atomicOr(err, DERR_TIMEOUT);
+  }
+}
+
+}  // namespace hlc
+
+extern "C" int hlc_test_spin_shift(int shift) {
+  clear_error();
+  if (shift < 0 || shift > 24) {
+    set_error("hlc_test_spin_shift: shift must lie in [0, 24]");
+    return HLC_EINVAL;
+  }
+  HLC_CUDA(cudaMemcpyToSymbol(d_spin_shift, &shift, sizeof(int)));
+  return HLC_OK;
+}
+
+extern "C" int hlc_test_unset_wait(int which, void* stream) {
+  clear_error();
+  if (which < 0 || which > 2) {
+    set_error("hlc_test_unset_wait: which must be 0, 1 or 2");
+    return HLC_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long* words = nullptr;
+  int* err = nullptr;
+  if (cudaMallocAsync(&words, kTestWords * 8, st) != cudaSuccess ||
+      cudaMallocAsync(&err, 64, st) != cudaSuccess) {
+    cudaGetLastError();
+    if (words) cudaFreeAsync(words, st);
+    set_error("hlc_test_unset_wait: cudaMallocAsync failed");
+    return HLC_ENOMEM;
+  }
+  int rc = HLC_OK;
+  if (cudaMemsetAsync(words, 0, kTestWords * 8, st) != cudaSuccess ||
+      cudaMemsetAsync(err, 0, 64, st) != cudaSuccess) {
+    set_error("hlc_test_unset_wait: %s", cudaGetErrorString(cudaGetLastError()));
+    rc = HLC_ECUDA;
+  }
+  if (rc == HLC_OK) {
+    k_test_unset_wait<<<1, rs::kRadix, 0, st>>>(which, words, err);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (cudaGetLastError() != cudaSuccess) {
+      set_error("hlc_test_unset_wait: launch failed");
+      rc = HLC_ECUDA;
+    }
+  }
+  if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_test_unset_wait");
+  cudaFreeAsync(words, st);
+  cudaFreeAsync(err, st);
+  cudaStreamSynchronize(st);
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free radix sort: the same sort as hlc_sort_pairs, with every
 // temporary (alternate key/value buffers, histograms, look-back words and the
 // error word) carved out of one fixed device array compiled into the library.
@@ -3186,29 +3266,18 @@ constexpr size_t kNoAllocBytes = 256 + kNoAllocKeyBytes + kNoAllocValBytes + kNo
 // Lives on every device that loads the library, until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_ptr[64] = {nullptr};
-
-// Device address of the scratch array on the current device (looked up once
-// per device, with that device current).
+// Device address of the scratch array on the current device.  Looked up on
+// every call (the lookup allocates nothing): after a device reset the module
+// is loaded again and the array may sit at another address.
 static int noalloc_scratch(void** out) {
-  int dev = 0;
-  HLC_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) {
-    set_error("device ordinal %d out of range", dev);
-    return HLC_EUNSUPPORTED;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    set_error("cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+    return HLC_ECUDA;
   }
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      set_error("cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
-      return HLC_ECUDA;
-    }
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+  *out = p;
   return HLC_OK;
 }
 
@@ -3240,14 +3309,20 @@ extern "C" int hlc_sort_pairs_noalloc(void* keys, uint32_t* vals, uint64_t n, in
   void* tk = b + 256;
   uint32_t* tv = (uint32_t*)(b + 256 + kNoAllocKeyBytes);
   void* scr = b + 256 + kNoAllocKeyBytes + kNoAllocValBytes;
-  HLC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
-  int rc;
-  if (key_size == 4)
+  int rc = HLC_OK;
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) {
+    set_error("hlc_sort_pairs_noalloc: %s", cudaGetErrorString(cudaGetLastError()));
+    rc = HLC_ECUDA;
+  }
+  if (rc == HLC_OK && key_size == 4)
     rc = radix_sort_pairs<uint32_t>((uint32_t*)keys, vals, (uint32_t*)tk, tv, n, key_bits, scr,
                                     err, st);
-  else
+  else if (rc == HLC_OK)
     rc = radix_sort_pairs<uint64_t>((uint64_t*)keys, vals, (uint64_t*)tk, tv, n, key_bits, scr,
                                     err, st);
   if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_sort_pairs_noalloc");
+  // On every path, success or not, no queued kernel may still be using the
+  // shared array when the call returns.
+  cudaStreamSynchronize(st);
   return rc;
 }

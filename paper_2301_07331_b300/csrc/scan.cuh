@@ -45,7 +45,7 @@ __device__ __forceinline__ unsigned long long lookback_prefix(uint32_t tile,
     const int last = inc ? __ffs(inc) - 1 : 31;  // lanes 0..last are needed
     const unsigned need = last == 31 ? 0xffffffffu : (2u << last) - 1u;
     if (wait & need) {
-      if (++spins > kSpinLimit) {
+      if (++spins > spin_limit(kSpinLimit)) {
         if (lane == 0) atomicOr(err, DERR_TIMEOUT);
         break;
       }

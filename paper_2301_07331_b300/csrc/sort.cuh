@@ -111,6 +111,36 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
 
 // (The look-back words carry their value and flag in one 64-bit word, so
 // relaxed accesses suffice: no other data is published through them.)
+
+// Exclusive prefix of digit t over the tiles before `tile`: walk back from
+// the predecessor adding published counts until an inclusive prefix is met.
+// A predecessor that has published nothing yet is waited for, at most
+// spin_limit(kSpinLimit) polls; then DERR_TIMEOUT is flagged and the partial
+// prefix returned (every later position stays below the true one, so the
+// scatter stays in bounds).
+__device__ __forceinline__ unsigned long long lookback_excl(
+    const unsigned long long* lookback, uint32_t tile, int t, int* err) {
+  unsigned long long excl = 0;
+  long long spins = 0;
+  const long long lim = spin_limit(kSpinLimit);
+  int64_t j = (int64_t)tile - 1;
+  while (j >= 0) {
+    unsigned long long w = ld_relaxed_u64(lookback + (uint64_t)j * kRadix + t);
+    unsigned long long flag = w & ~kValMask;
+    if (flag == 0) {
+      if (++spins > lim) {
+        atomicOr(err, DERR_TIMEOUT);
+        break;
+      }
+      continue;
+    }
+    excl += w & kValMask;
+    if (flag == kFlagInc) break;
+    --j;
+  }
+  return excl;
+}
+
 // One array of a digit pass.  A launch may sort two arrays at once (the same
 // digit of each): its tiles are numbered across both, the first ntiles
 // belonging to d0, and each array keeps its own histogram offsets and
@@ -189,22 +219,7 @@ __device__ __forceinline__ void sweep_tile(SweepSmem<K>& S, const int t, const i
   }
   unsigned long long excl = 0;
   if (tile != 0) {
-    long long spins = 0;
-    int64_t j = (int64_t)tile - 1;
-    while (j >= 0) {
-      unsigned long long w = ld_relaxed_u64(lookback + (uint64_t)j * kRadix + t);
-      unsigned long long flag = w & ~kValMask;
-      if (flag == 0) {
-        if (++spins > kSpinLimit) {
-          atomicOr(err, DERR_TIMEOUT);
-          break;
-        }
-        continue;
-      }
-      excl += w & kValMask;
-      if (flag == kFlagInc) break;
-      --j;
-    }
+    excl = lookback_excl(lookback, tile, t, err);
     st_relaxed_u64(slot, kFlagInc | (excl + cnt));
   }
   S.gbase[t] = (unsigned long long)goff[t] + excl;
@@ -313,7 +328,7 @@ int radix_sort_pairs(K* keys, uint32_t* vals, K* tmp_keys, uint32_t* tmp_vals, u
   HLC_CUDA(cudaMemsetAsync(hist, 0, (size_t)npass * rs::kRadix * 4, st));
   HLC_CUDA(cudaMemsetAsync(ctr, 0, 64, st));
   HLC_CUDA(cudaMemsetAsync(lb, 0, lb_bytes, st));
-  rs::k_digit_hist<K><<<grid_for(n, rs::kBlock, 148 * 8), rs::kBlock, 0, st>>>(keys, n, npass,
+  rs::k_digit_hist<K><<<grid_for(n, rs::kBlock, num_sms() * 8u), rs::kBlock, 0, st>>>(keys, n, npass,
                                                                                bit_lo, hist);
   HLC_LAUNCH_CHECK();
   rs::k_hist_scan<<<npass, rs::kBlock, 0, st>>>(hist, offs);
@@ -396,7 +411,7 @@ int radix_sort_pairs2(K* keys0, uint32_t* vals0, K* tk0, uint32_t* tv0, uint64_t
     unsigned long long* lb = (unsigned long long*)(q.sp + kSortLookbackOffset);
     HLC_CUDA(cudaMemsetAsync(hist, 0, (size_t)npass * rs::kRadix * 4, st));
     HLC_CUDA(cudaMemsetAsync(lb, 0, (size_t)npass * q.tiles * rs::kRadix * 8, st));
-    rs::k_digit_hist<K><<<grid_for(q.n, rs::kBlock, 148 * 8), rs::kBlock, 0, st>>>(
+    rs::k_digit_hist<K><<<grid_for(q.n, rs::kBlock, num_sms() * 8u), rs::kBlock, 0, st>>>(
         q.keys, q.n, npass, bit_lo, hist);
     HLC_LAUNCH_CHECK();
     rs::k_hist_scan<<<npass, rs::kBlock, 0, st>>>(hist, offs);

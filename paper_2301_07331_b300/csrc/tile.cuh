@@ -83,7 +83,8 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
   const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < kTileSpin; ++it) {
+  const long long lim = spin_limit(kTileSpin);
+  for (long long it = 0; it < lim; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"

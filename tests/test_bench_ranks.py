@@ -109,3 +109,59 @@ def test_clock_record_rejects_slowdowns_and_unexplained_low_clocks(tmp_path):
     assert rec["samples"] == 2 and rec["sm_max_mhz"] == 2032.0
     assert rec["sm_mhz"] == 2021.0 and rec["reasons"] == ["sw_power_cap"]
     assert bench.clocks_rejected(rec) == ""
+
+
+def test_parity_check_selects_only_fully_sampled_sources():
+    """The bench's per-run parity check: rows of A sources whose r-disc lies
+    inside the oracle's RA band are compared.  With the full-sky oracle
+    standing in for the library's rows, the band comparison must be equal
+    (no selected source has a partner outside the band, also near the poles
+    and the band's edges) and a single dropped or altered row must show."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch
+
+    import bench
+    import oracle as O
+    from paper_2301_07331_b300 import synth
+    A, B = synth.fullsky_pair(seed=5, na=30000, nb=30000, device="cpu")
+    # crowd the band's edges and the poles with close pairs
+    ra_a, dec_a = A.ra.numpy().copy(), A.dec.numpy().copy()
+    ra_a[:400] = np.linspace(-0.001, 0.001, 400) % 360.0
+    ra_a[400:800] = 30.0 + np.linspace(-0.001, 0.001, 400)
+    dec_a[800:1200] = np.linspace(89.95, 89.9999, 400)
+    A = synth.Catalogue(torch.from_numpy(ra_a), torch.from_numpy(dec_a), A.id)
+    ra_b, dec_b = B.ra.numpy().copy(), B.dec.numpy().copy()
+    ra_b[:1200] = (ra_a[:1200] + 0.3 / 3600) % 360.0
+    dec_b[:1200] = dec_a[:1200]
+    B = synth.Catalogue(torch.from_numpy(ra_b), torch.from_numpy(dec_b), B.id)
+    r, L = 50.0, 9
+    full = O.match(*A.numpy(), *B.numpy(), r, L, O.COMPLETE)
+    rows = (full["id_a"], full["id_b"], full["sep"])
+    _, band = bench.cpu_baseline(A, B, r, L, False, 0.0, 30.0)
+    rec = bench.oracle_parity(A, r, band, rows, 0.0, 30.0)
+    assert rec["equal"] and rec["rows"] > 0 and rec["max_sep_err_arcsec"] == 0.0
+    # one selected row dropped from the library's side
+    sel = np.isin(rows[0], band["id_a"])
+    k = int(np.flatnonzero(sel)[0])
+    dropped = tuple(np.delete(x, k) for x in rows)
+    assert not bench.oracle_parity(A, r, band, dropped, 0.0, 30.0)["equal"]
+    # a separation off by more than the tolerance
+    bad = (rows[0], rows[1], rows[2].copy())
+    bad[2][k] += 2e-6
+    rec = bench.oracle_parity(A, r, band, bad, 0.0, 30.0)
+    assert rec["equal"] and not rec["sep_within_tolerance"]
+    assert bench.rows_equal(rows, rows)["equal"]
+    assert not bench.rows_equal(rows, dropped)["equal"]
+
+
+def test_critical_path_adds_up_to_the_step():
+    sys.path.insert(0, ROOT)
+    import bench
+    st = {"ms_plan_span": 1.5, "ms_plan_presort": 0.4, "ms_sort_passes": 0.45,
+          "ms_candidates": 0.0, "ms_pair": 0.5, "ms_recheck": 0.05, "ms_output": 0.5}
+    cp = bench.critical_path([st, st], 2.8)
+    assert abs(sum(cp.values()) - 2.8) < 1e-9
+    assert abs(cp["plan_payloads_table_dense_cells"] - 0.65) < 1e-9
+    cp = bench.critical_path([dict(st, ms_plan_presort=0.0)], 2.8)
+    assert "plan" in cp and abs(sum(cp.values()) - 2.8) < 1e-9
