@@ -78,6 +78,14 @@ def lib():
                                       C.POINTER(_Result)]
         L.orc_match_brute.restype = i32
         L.orc_result_free.argtypes = [C.POINTER(_Result)]
+        L.orc_match_eq4.argtypes = [P, P, P, P, u64, P, P, P, P, u64, i32, C.POINTER(_Result)]
+        L.orc_match_eq4.restype = i32
+        L.orc_match_brute_eq4.argtypes = [P, P, P, P, u64, P, P, P, P, u64,
+                                          C.POINTER(_Result)]
+        L.orc_match_brute_eq4.restype = i32
+        L.orc_pair_radius.argtypes = [d, d]
+        L.orc_pair_radius.restype = d
+        L.orc_pair_radius_n.argtypes = [P, P, u64, P]
         _lib = L
     return _lib
 
@@ -215,4 +223,39 @@ def match_brute(ra_a, dec_a, id_a, ra_b, dec_b, id_b, r_arcsec: float) -> dict:
                                float(r_arcsec), C.byref(res))
     if rc != 0:
         raise OracleError("orc_match_brute failed with code %d" % rc)
+    return _collect(res)
+
+
+def pair_radius(e1, e2):
+    """Eq. 4 pair radius 3 sqrt(e1^2 + e2^2) (arcsec), element-wise."""
+    e1, e2 = np.broadcast_arrays(_f64(e1), _f64(e2))
+    e1, e2 = _f64(e1), _f64(e2)
+    out = np.empty(e1.shape)
+    lib().orc_pair_radius_n(_p(e1), _p(e2), e1.size, _p(out))
+    return out
+
+
+def match_eq4(ra_a, dec_a, id_a, err_a, ra_b, dec_b, id_b, err_b, order: int) -> dict:
+    """Complete-mode match with per-source error radii (Eq. 4): every
+    (A_i, B_j) with separation <= 3 sqrt(err_a[i]^2 + err_b[j]^2) arcsec."""
+    ra_a, dec_a, id_a, err_a = _f64(ra_a), _f64(dec_a), _u64(id_a), _f64(err_a)
+    ra_b, dec_b, id_b, err_b = _f64(ra_b), _f64(dec_b), _u64(id_b), _f64(err_b)
+    res = _Result()
+    rc = lib().orc_match_eq4(_p(ra_a), _p(dec_a), _p(id_a), _p(err_a), ra_a.size, _p(ra_b),
+                             _p(dec_b), _p(id_b), _p(err_b), ra_b.size, int(order),
+                             C.byref(res))
+    if rc != 0:
+        raise OracleError("orc_match_eq4 failed with code %d" % rc)
+    return _collect(res)
+
+
+def match_brute_eq4(ra_a, dec_a, id_a, err_a, ra_b, dec_b, id_b, err_b) -> dict:
+    ra_a, dec_a, id_a, err_a = _f64(ra_a), _f64(dec_a), _u64(id_a), _f64(err_a)
+    ra_b, dec_b, id_b, err_b = _f64(ra_b), _f64(dec_b), _u64(id_b), _f64(err_b)
+    res = _Result()
+    rc = lib().orc_match_brute_eq4(_p(ra_a), _p(dec_a), _p(id_a), _p(err_a), ra_a.size,
+                                   _p(ra_b), _p(dec_b), _p(id_b), _p(err_b), ra_b.size,
+                                   C.byref(res))
+    if rc != 0:
+        raise OracleError("orc_match_brute_eq4 failed with code %d" % rc)
     return _collect(res)

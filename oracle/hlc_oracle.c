@@ -10,7 +10,8 @@
  *   - Sec. 4.2 ("hp_nestid"): HEALPix nested ang2pix (Gorski et al. 2005);
  *   - Sec. 3.2 and Algorithm 1: the quad-direction boundary strategy;
  *   - complete mode: the exact set of Eq. 1 reached through the cell of each
- *     A source and its 8 HEALPix neighbours.
+ *     A source and its 8 HEALPix neighbours;
+ *   - Eq. 4: per-source error radii, each pair's radius 3 sqrt(e1^2 + e2^2).
  *
  * Compiled with -O2 -ffp-contract=off: every floating-point expression below
  * is evaluated exactly as written, one correctly rounded IEEE binary64
@@ -143,6 +144,18 @@ double orc_sep_arcsec(double chord2) {
 double orc_complete_max_radius(int order) {
   double side_rad = sqrt(M_PI / 3.0) / ldexp(1.0, order);
   return side_rad * (648000.0 / M_PI) / 8.0;
+}
+
+/* Eq. 4 (Sec. 2.1): two sources with error radii e1, e2 match when their
+ * distance is at most 3 sqrt(e1^2 + e2^2).  The pair radius in arcsec, in a
+ * fixed operation order that is symmetric in the two errors (so swapping the
+ * catalogues cannot change a decision): a = e1 e1, b = e2 e2, t = a + b,
+ * r = 3 sqrt(t), each step correctly rounded. */
+double orc_pair_radius(double e1, double e2) {
+  double a = e1 * e1;
+  double b = e2 * e2;
+  double t = a + b;
+  return 3.0 * sqrt(t);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -501,11 +514,14 @@ static uint64_t lower_bound_kv(const kv_t* a, uint64_t n, uint64_t q) {
   return lo;
 }
 
+/* err_a/err_b: NULL for one radius (threshold C for every pair); else the
+ * per-source error radii of Eq. 4 and each pair's own threshold
+ * 4 sin^2(r_ij / 2), r_ij = orc_pair_radius(err_a[i], err_b[j]). */
 static int match_complete(const double* ra_a, const double* dec_a,
-                          const uint64_t* id_a, uint64_t na,
+                          const uint64_t* id_a, const double* err_a, uint64_t na,
                           const double* ra_b, const double* dec_b,
-                          const uint64_t* id_b, uint64_t nb, double C,
-                          int order, orc_result* out) {
+                          const uint64_t* id_b, const double* err_b, uint64_t nb,
+                          double C, int order, orc_result* out) {
   double* va = unit_vectors(ra_a, dec_a, na);
   double* vb = unit_vectors(ra_b, dec_b, nb);
   kv_t* kb = (kv_t*)malloc((nb ? nb : 1) * sizeof(kv_t));
@@ -541,7 +557,8 @@ static int match_complete(const double* ra_a, const double* dec_a,
         uint32_t j = kb[t].idx;
         double c2 = orc_chord2(va + 3 * i, vb + 3 * (uint64_t)j);
         ++tests;
-        if (c2 <= C) {
+        double Cij = err_a ? orc_threshold(orc_pair_radius(err_a[i], err_b[j])) : C;
+        if (c2 <= Cij) {
           pair_t pr = {id_a[i], id_b[j], (uint32_t)i, j, c2};
           rc = push_pair(&pv, pr);
           if (rc) break;
@@ -649,8 +666,8 @@ int orc_match(const double* ra_a, const double* dec_a, const uint64_t* id_a,
     return ORC_EINVAL;
   double C = orc_threshold(r_arcsec);
   if (mode == 0)
-    return match_complete(ra_a, dec_a, id_a, na, ra_b, dec_b, id_b, nb, C,
-                          order, out);
+    return match_complete(ra_a, dec_a, id_a, NULL, na, ra_b, dec_b, id_b, NULL, nb,
+                          C, order, out);
   return match_quad(ra_a, dec_a, id_a, na, ra_b, dec_b, id_b, nb, r_arcsec, C,
                     order, out);
 }
@@ -676,6 +693,72 @@ int orc_match_brute(const double* ra_a, const double* dec_a,
     for (uint64_t j = 0; j < nb; ++j) {
       double c2 = orc_chord2(va + 3 * i, vb + 3 * j);
       if (c2 <= C) {
+        pair_t pr = {id_a[i], id_b[j], (uint32_t)i, (uint32_t)j, c2};
+        rc = push_pair(&pv, pr);
+        if (rc) break;
+      }
+    }
+  free(va); free(vb);
+  if (rc) {
+    free(pv.v);
+    return rc;
+  }
+  return finish(&pv, na * nb, out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-source error radii (Eq. 4).                                           */
+/* ------------------------------------------------------------------------ */
+
+static int valid_errors(const double* e, uint64_t n, double* emax) {
+  *emax = 0.0;
+  for (uint64_t i = 0; i < n; ++i) {
+    if (!isfinite(e[i]) || e[i] < 0.0) return 0;
+    if (e[i] > *emax) *emax = e[i];
+  }
+  return 1;
+}
+
+int orc_match_eq4(const double* ra_a, const double* dec_a, const uint64_t* id_a,
+                  const double* err_a, uint64_t na, const double* ra_b,
+                  const double* dec_b, const uint64_t* id_b, const double* err_b,
+                  uint64_t nb, int order, orc_result* out) {
+  memset(out, 0, sizeof(*out));
+  if (order < 0 || order > 29) return ORC_EINVAL;
+  if (na > 0xFFFFFFFFull || nb > 0xFFFFFFFFull) return ORC_EINVAL;
+  if (!valid_inputs(ra_a, dec_a, na) || !valid_inputs(ra_b, dec_b, nb))
+    return ORC_EINVAL;
+  double ma, mb;
+  if (!valid_errors(err_a, na, &ma) || !valid_errors(err_b, nb, &mb))
+    return ORC_EINVAL;
+  /* complete mode is exact only while every pair radius is <= theta_L/8 */
+  if (orc_pair_radius(ma, mb) > orc_complete_max_radius(order)) return ORC_EINVAL;
+  return match_complete(ra_a, dec_a, id_a, err_a, na, ra_b, dec_b, id_b, err_b,
+                        nb, 0.0, order, out);
+}
+
+int orc_match_brute_eq4(const double* ra_a, const double* dec_a,
+                        const uint64_t* id_a, const double* err_a, uint64_t na,
+                        const double* ra_b, const double* dec_b,
+                        const uint64_t* id_b, const double* err_b, uint64_t nb,
+                        orc_result* out) {
+  memset(out, 0, sizeof(*out));
+  double ma, mb;
+  if (!valid_inputs(ra_a, dec_a, na) || !valid_inputs(ra_b, dec_b, nb) ||
+      !valid_errors(err_a, na, &ma) || !valid_errors(err_b, nb, &mb))
+    return ORC_EINVAL;
+  double* va = unit_vectors(ra_a, dec_a, na);
+  double* vb = unit_vectors(ra_b, dec_b, nb);
+  if (!va || !vb) {
+    free(va); free(vb);
+    return ORC_ENOMEM;
+  }
+  pairvec pv = {0};
+  int rc = ORC_OK;
+  for (uint64_t i = 0; i < na && rc == ORC_OK; ++i)
+    for (uint64_t j = 0; j < nb; ++j) {
+      double c2 = orc_chord2(va + 3 * i, vb + 3 * j);
+      if (c2 <= orc_threshold(orc_pair_radius(err_a[i], err_b[j]))) {
         pair_t pr = {id_a[i], id_b[j], (uint32_t)i, (uint32_t)j, c2};
         rc = push_pair(&pv, pr);
         if (rc) break;
@@ -731,6 +814,10 @@ void orc_quad_cells_n(const double* ra, const double* dec, uint64_t n,
     for (int e = 0; e < 5; ++e) out[5 * i + e] = e < m ? c[e] : UINT64_MAX;
     cnt[i] = m;
   }
+}
+
+void orc_pair_radius_n(const double* e1, const double* e2, uint64_t n, double* out) {
+  for (uint64_t i = 0; i < n; ++i) out[i] = orc_pair_radius(e1[i], e2[i]);
 }
 
 void orc_chord2_n(const double* va, const double* vb, uint64_t n, double* out) {

@@ -102,6 +102,25 @@ int orc_match_brute(const double* ra_a, const double* dec_a,
 
 void orc_result_free(orc_result* r);
 
+/* Eq. 4 pair radius 3 sqrt(e1^2 + e2^2) arcsec (fixed operation order). */
+double orc_pair_radius(double e1, double e2);
+
+/* Complete mode with per-source error radii err_a, err_b (arcsec, finite,
+ * >= 0): every (A_i, B_j) with separation <= orc_pair_radius(err_a[i],
+ * err_b[j]).  ORC_EINVAL when the largest pair radius exceeds
+ * orc_complete_max_radius(order). */
+int orc_match_eq4(const double* ra_a, const double* dec_a, const uint64_t* id_a,
+                  const double* err_a, uint64_t na, const double* ra_b,
+                  const double* dec_b, const uint64_t* id_b, const double* err_b,
+                  uint64_t nb, int order, orc_result* out);
+
+/* All-pairs form of the same (tiny inputs only). */
+int orc_match_brute_eq4(const double* ra_a, const double* dec_a,
+                        const uint64_t* id_a, const double* err_a, uint64_t na,
+                        const double* ra_b, const double* dec_b,
+                        const uint64_t* id_b, const double* err_b, uint64_t nb,
+                        orc_result* out);
+
 /* Largest radius (arcsec) for which complete mode is exact at this order:
  * one eighth of the mean pixel side sqrt(pi/3)/2^order. */
 double orc_complete_max_radius(int order);
@@ -120,6 +139,7 @@ void orc_pix2ang_n(const uint64_t* pix, uint64_t n, int order, double* ra,
 void orc_quad_cells_n(const double* ra, const double* dec, uint64_t n,
                       double r_arcsec, int order, uint64_t* out, int* cnt);
 void orc_chord2_n(const double* va, const double* vb, uint64_t n, double* out);
+void orc_pair_radius_n(const double* e1, const double* e2, uint64_t n, double* out);
 
 #ifdef __cplusplus
 }

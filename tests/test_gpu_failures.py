@@ -124,10 +124,11 @@ def test_unset_flag_wait_times_out_and_returns(which):
         t0 = time.perf_counter()
         rc = L.hlc_test_unset_wait(which, stream)
         dt = time.perf_counter() - t0
+        msg = L.hlc_last_error()  # (read before the next call clears it)
     finally:
         assert L.hlc_test_spin_shift(0) == 0
-    assert rc == hlc.HLC_ETIMEOUT, (rc, L.hlc_last_error())
-    assert b"bounded device wait" in L.hlc_last_error()
+    assert rc == hlc.HLC_ETIMEOUT, (rc, msg)
+    assert b"bounded device wait" in msg
     print("wait %d gave up after %.1f ms with the limit shifted by 16" % (which, dt * 1e3))
     # the context is usable: a match right after equals the oracle
     A, B = synth.patch_pair(na=3000, nb=3000)
