@@ -27,6 +27,7 @@ _lib = None
 
 COMPLETE = 0
 QUAD = 1
+QUAD_COS = 2
 
 
 def build(force: bool = False) -> str:
@@ -63,6 +64,7 @@ def lib():
         L.orc_neighbours_n.argtypes = [P, u64, i32, P]
         L.orc_pix2ang_n.argtypes = [P, u64, i32, P, P]
         L.orc_quad_cells_n.argtypes = [P, P, u64, d, i32, P, P]
+        L.orc_quad_cells_mode_n.argtypes = [P, P, u64, d, i32, i32, P, P]
         L.orc_chord2_n.argtypes = [P, P, u64, P]
         L.orc_threshold.argtypes = [d]
         L.orc_threshold.restype = d
@@ -172,12 +174,13 @@ def pix2ang(pix, order: int):
     return ra, dec
 
 
-def quad_cells(ra, dec, r_arcsec: float, order: int):
+def quad_cells(ra, dec, r_arcsec: float, order: int, cosdec: bool = False):
+    """Quad-direction cells (Algorithm 1); cosdec: the RA shift R / cos(dec)."""
     ra, dec = _f64(ra), _f64(dec)
     out = np.empty((ra.size, 5), dtype=np.uint64)
     cnt = np.empty(ra.size, dtype=np.int32)
-    lib().orc_quad_cells_n(_p(ra), _p(dec), ra.size, float(r_arcsec), int(order),
-                           _p(out), _p(cnt))
+    lib().orc_quad_cells_mode_n(_p(ra), _p(dec), ra.size, float(r_arcsec), int(order),
+                                int(bool(cosdec)), _p(out), _p(cnt))
     return out, cnt
 
 

@@ -8,7 +8,9 @@
  *     |u1 - u2|^2 <= 4 sin^2(r/2), which is Eq. 1 rewritten without the
  *     catastrophic cancellation of arccos near 0;
  *   - Sec. 4.2 ("hp_nestid"): HEALPix nested ang2pix (Gorski et al. 2005);
- *   - Sec. 3.2 and Algorithm 1: the quad-direction boundary strategy;
+ *   - Sec. 3.2 and Algorithm 1: the quad-direction boundary strategy, read
+ *     literally (R_A = R_B = r) and in a variant whose RA shift is the RA
+ *     extent r / cos(dec) of the radius at the source's declination;
  *   - complete mode: the exact set of Eq. 1 reached through the cell of each
  *     A source and its 8 HEALPix neighbours;
  *   - Eq. 4: per-source error radii, each pair's radius 3 sqrt(e1^2 + e2^2).
@@ -380,17 +382,32 @@ static int cmp_u64(const void* a, const void* b) {
   return (x > y) - (x < y);
 }
 
-int orc_quad_cells(double ra, double dec, double r_arcsec, int order,
-                   uint64_t out[5]) {
-  double R = r_arcsec / 3600.0; /* R_A = R_B = r in degrees */
+/* The RA shift of the cos(Dec) variant: the RA extent R / cos(dec) of an
+ * angle R at declination dec (canonical cosine), 180 deg at most (and where
+ * cos(dec) is 0). */
+static double ra_shift_cos(double R, double dec) {
+  double sd, cd;
+  orc_sincos_deg(dec, &sd, &cd);
+  double c = fabs(cd);
+  double RA = c > 0.0 ? R / c : 180.0;
+  if (RA > 180.0) RA = 180.0;
+  return RA;
+}
+
+/* cosdec = 0: Algorithm 1 read literally (R_A = R_B = r in degrees);
+ * cosdec = 1: the variant with R_A = R / cos(dec), R_B = R. */
+static int quad_cells_impl(double ra, double dec, double r_arcsec, int order, int cosdec,
+                           uint64_t out[5]) {
+  double R = r_arcsec / 3600.0; /* R_B = r in degrees */
+  double RA = cosdec ? ra_shift_cos(R, dec) : R;
   double dec_plus = dec + R;
   if (dec_plus > 90.0) dec_plus = 90.0;
   double dec_minus = dec - R;
   if (dec_minus < -90.0) dec_minus = -90.0;
   uint64_t p[5];
   p[0] = orc_ang2pix(ra, dec, order);
-  p[1] = orc_ang2pix(wrap_ra(ra + R), dec, order);
-  p[2] = orc_ang2pix(wrap_ra(ra - R), dec, order);
+  p[1] = orc_ang2pix(wrap_ra(ra + RA), dec, order);
+  p[2] = orc_ang2pix(wrap_ra(ra - RA), dec, order);
   p[3] = orc_ang2pix(ra, dec_minus, order);
   p[4] = orc_ang2pix(ra, dec_plus, order);
   qsort(p, 5, sizeof(uint64_t), cmp_u64);
@@ -398,6 +415,14 @@ int orc_quad_cells(double ra, double dec, double r_arcsec, int order,
   for (int i = 0; i < 5; ++i)
     if (m == 0 || p[i] != out[m - 1]) out[m++] = p[i];
   return m;
+}
+
+int orc_quad_cells(double ra, double dec, double r_arcsec, int order, uint64_t out[5]) {
+  return quad_cells_impl(ra, dec, r_arcsec, order, 0, out);
+}
+
+int orc_quad_cells_cos(double ra, double dec, double r_arcsec, int order, uint64_t out[5]) {
+  return quad_cells_impl(ra, dec, r_arcsec, order, 1, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -577,7 +602,8 @@ static int match_complete(const double* ra_a, const double* dec_a,
 static int match_quad(const double* ra_a, const double* dec_a,
                       const uint64_t* id_a, uint64_t na, const double* ra_b,
                       const double* dec_b, const uint64_t* id_b, uint64_t nb,
-                      double r_arcsec, double C, int order, orc_result* out) {
+                      double r_arcsec, double C, int order, int cosdec,
+                      orc_result* out) {
   double* va = unit_vectors(ra_a, dec_a, na);
   double* vb = unit_vectors(ra_b, dec_b, nb);
   uint64_t* ca = (uint64_t*)malloc((na ? na : 1) * 5 * sizeof(uint64_t));
@@ -591,8 +617,8 @@ static int match_quad(const double* ra_a, const double* dec_a,
   uint64_t nea = 0, neb = 0;
   if (rc == ORC_OK) {
     for (uint64_t i = 0; i < na; ++i) {
-      nca[i] = orc_quad_cells(orc_norm_ra(ra_a[i]), dec_a[i], r_arcsec, order,
-                              ca + 5 * i);
+      nca[i] = quad_cells_impl(orc_norm_ra(ra_a[i]), dec_a[i], r_arcsec, order, cosdec,
+                               ca + 5 * i);
       for (int e = 0; e < nca[i]; ++e) {
         ea[nea].key = ca[5 * i + e];
         ea[nea].idx = (uint32_t)i;
@@ -600,8 +626,8 @@ static int match_quad(const double* ra_a, const double* dec_a,
       }
     }
     for (uint64_t j = 0; j < nb; ++j) {
-      ncb[j] = orc_quad_cells(orc_norm_ra(ra_b[j]), dec_b[j], r_arcsec, order,
-                              cb + 5 * j);
+      ncb[j] = quad_cells_impl(orc_norm_ra(ra_b[j]), dec_b[j], r_arcsec, order, cosdec,
+                               cb + 5 * j);
       for (int e = 0; e < ncb[j]; ++e) {
         eb[neb].key = cb[5 * j + e];
         eb[neb].idx = (uint32_t)j;
@@ -659,7 +685,7 @@ int orc_match(const double* ra_a, const double* dec_a, const uint64_t* id_a,
   memset(out, 0, sizeof(*out));
   if (!(r_arcsec > 0.0) || !(r_arcsec <= 648000.0)) return ORC_EINVAL;
   if (order < 0 || order > 29) return ORC_EINVAL;
-  if (mode != 0 && mode != 1) return ORC_EINVAL;
+  if (mode != 0 && mode != 1 && mode != 2) return ORC_EINVAL;
   if (mode == 0 && r_arcsec > orc_complete_max_radius(order)) return ORC_EINVAL;
   if (na > 0xFFFFFFFFull || nb > 0xFFFFFFFFull) return ORC_EINVAL;
   if (!valid_inputs(ra_a, dec_a, na) || !valid_inputs(ra_b, dec_b, nb))
@@ -669,7 +695,7 @@ int orc_match(const double* ra_a, const double* dec_a, const uint64_t* id_a,
     return match_complete(ra_a, dec_a, id_a, NULL, na, ra_b, dec_b, id_b, NULL, nb,
                           C, order, out);
   return match_quad(ra_a, dec_a, id_a, na, ra_b, dec_b, id_b, nb, r_arcsec, C,
-                    order, out);
+                    order, mode == 2, out);
 }
 
 int orc_match_brute(const double* ra_a, const double* dec_a,
@@ -808,9 +834,14 @@ void orc_pix2ang_n(const uint64_t* pix, uint64_t n, int order, double* ra,
 
 void orc_quad_cells_n(const double* ra, const double* dec, uint64_t n,
                       double r_arcsec, int order, uint64_t* out, int* cnt) {
+  orc_quad_cells_mode_n(ra, dec, n, r_arcsec, order, 0, out, cnt);
+}
+
+void orc_quad_cells_mode_n(const double* ra, const double* dec, uint64_t n,
+                           double r_arcsec, int order, int cosdec, uint64_t* out, int* cnt) {
   for (uint64_t i = 0; i < n; ++i) {
     uint64_t c[5];
-    int m = orc_quad_cells(orc_norm_ra(ra[i]), dec[i], r_arcsec, order, c);
+    int m = quad_cells_impl(orc_norm_ra(ra[i]), dec[i], r_arcsec, order, cosdec, c);
     for (int e = 0; e < 5; ++e) out[5 * i + e] = e < m ? c[e] : UINT64_MAX;
     cnt[i] = m;
   }

@@ -71,6 +71,11 @@ void orc_pix2ang(uint64_t pix, int order, double* ra, double* dec);
 int orc_quad_cells(double ra, double dec, double r_arcsec, int order,
                    uint64_t out[5]);
 
+/* The same with the RA copies shifted by R / cos(dec) (at most 180 deg)
+ * instead of R: the RA extent of the radius at the source's declination. */
+int orc_quad_cells_cos(double ra, double dec, double r_arcsec, int order,
+                       uint64_t out[5]);
+
 /* Match result: pairs sorted by (id_a, id_b) unsigned, ties by (ia, ib). */
 typedef struct {
   uint64_t n;
@@ -88,7 +93,8 @@ typedef struct {
 #define ORC_EINVAL 1
 #define ORC_ENOMEM 2
 
-/* mode: 0 = complete 8-neighbour, 1 = quad-direction. */
+/* mode: 0 = complete 8-neighbour, 1 = quad-direction, 2 = quad-direction
+ * with the RA shift R / cos(dec). */
 int orc_match(const double* ra_a, const double* dec_a, const uint64_t* id_a,
               uint64_t na, const double* ra_b, const double* dec_b,
               const uint64_t* id_b, uint64_t nb, double r_arcsec, int order,
@@ -138,6 +144,8 @@ void orc_pix2ang_n(const uint64_t* pix, uint64_t n, int order, double* ra,
                    double* dec);
 void orc_quad_cells_n(const double* ra, const double* dec, uint64_t n,
                       double r_arcsec, int order, uint64_t* out, int* cnt);
+void orc_quad_cells_mode_n(const double* ra, const double* dec, uint64_t n,
+                           double r_arcsec, int order, int cosdec, uint64_t* out, int* cnt);
 void orc_chord2_n(const double* va, const double* vb, uint64_t n, double* out);
 void orc_pair_radius_n(const double* e1, const double* e2, uint64_t n, double* out);
 

@@ -108,11 +108,11 @@ def test_invalid_inputs_rejected():
         O.match(one, one, ids, one, one, ids, 10.0, 14)
 
 
-def _quad_brute(ra_a, dec_a, ra_b, dec_b, r, L):
+def _quad_brute(ra_a, dec_a, ra_b, dec_b, r, L, cosdec=False):
     """All-pairs statement of the quad-direction set: a pair is reported when
     the two cell sets intersect and Eq. 1 holds."""
-    ca, na = O.quad_cells(ra_a, dec_a, r, L)
-    cb, nb = O.quad_cells(ra_b, dec_b, r, L)
+    ca, na = O.quad_cells(ra_a, dec_a, r, L, cosdec)
+    cb, nb = O.quad_cells(ra_b, dec_b, r, L, cosdec)
     ref = O.match_brute(ra_a, dec_a, np.arange(ra_a.size, dtype=np.uint64),
                         ra_b, dec_b, np.arange(ra_b.size, dtype=np.uint64), r)
     out = set()
@@ -122,16 +122,17 @@ def _quad_brute(ra_a, dec_a, ra_b, dec_b, r, L):
     return out, _pairs(ref)
 
 
+@pytest.mark.parametrize("mode", [O.QUAD, O.QUAD_COS], ids=["literal", "cosdec"])
 @pytest.mark.parametrize("L,seed", [(6, 0), (9, 1), (12, 2)])
-def test_quad_equals_its_all_pairs_definition(L, seed):
+def test_quad_equals_its_all_pairs_definition(L, seed, mode):
     rng = np.random.default_rng(seed)
     r = O.complete_max_radius(L) * 2.5  # quad mode has no radius limit
     cen = _centres(rng, L)
     ra_a, dec_a = _clumpy(rng, 1200, r, cen)
     ra_b, dec_b = _clumpy(rng, 1200, r, cen)
     ids = np.arange(1200, dtype=np.uint64)
-    got = O.match(ra_a, dec_a, ids, ra_b, dec_b, ids, r, L, O.QUAD)
-    want, full = _quad_brute(ra_a, dec_a, ra_b, dec_b, r, L)
+    got = O.match(ra_a, dec_a, ids, ra_b, dec_b, ids, r, L, mode)
+    want, full = _quad_brute(ra_a, dec_a, ra_b, dec_b, r, L, mode == O.QUAD_COS)
     gp = list(zip(got["ia"].tolist(), got["ib"].tolist()))
     assert len(gp) == len(set(gp))  # each pair once
     assert set(gp) == want
@@ -151,6 +152,9 @@ def test_quad_loses_no_more_than_same_cell_join():
     assert _pairs(quad) <= _pairs(comp)
     assert same_cell <= quad["id_a"].size <= comp["id_a"].size
     assert comp["id_a"].size - quad["id_a"].size < 0.01 * comp["id_a"].size
+    qcos = O.match(ra_a, dec_a, ida, ra_b, dec_b, idb, r, L, O.QUAD_COS)
+    assert _pairs(qcos) <= _pairs(comp)
+    assert same_cell <= qcos["id_a"].size
 
 
 def test_jittered_recovery_rate_c1():

@@ -15,12 +15,13 @@ import oracle as O
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 GOLDEN = os.path.join(HERE, "golden", "quad_cells.txt")
+GOLDEN_COS = os.path.join(HERE, "golden", "quad_cells_cos.txt")
 ORACLE_SRC = os.path.join(os.path.dirname(HERE), "oracle", "hlc_oracle.c")
 
 
-def _cases():
+def _cases(path=GOLDEN):
     out = []
-    for ln in open(GOLDEN):
+    for ln in open(path):
         if ln.startswith("#") or not ln.strip():
             continue
         lhs, rhs = ln.split(":")
@@ -30,6 +31,7 @@ def _cases():
 
 
 CASES = _cases()
+CASES_COS = _cases(GOLDEN_COS)
 
 
 def test_golden_file_covers_the_rule():
@@ -46,6 +48,23 @@ def test_quad_cells_equal_hand_placed_sets(case):
     cells, cnt = O.quad_cells([ra], [dec], r, L)
     assert cells[0, :cnt[0]].tolist() == want
     assert np.all(cells[0, cnt[0]:] == np.iinfo(np.uint64).max)
+
+
+@pytest.mark.parametrize("case", CASES_COS,
+                         ids=[f"{c[0]}_{c[1]}_{c[2]}_L{c[3]}" for c in CASES_COS])
+def test_cos_variant_cells_equal_hand_placed_sets(case):
+    """The variant with R_A = R / cos(dec), beside the literal reading."""
+    ra, dec, r, L, want = case
+    cells, cnt = O.quad_cells([ra], [dec], r, L, cosdec=True)
+    assert cells[0, :cnt[0]].tolist() == want
+
+
+def test_the_two_readings_differ_where_cos_dec_matters():
+    lit = {c[:4]: c[4] for c in CASES}
+    cos = {c[:4]: c[4] for c in CASES_COS}
+    common = set(lit) & set(cos)
+    assert any(lit[k] != cos[k] for k in common)           # Dec 60 and the pole
+    assert all(lit[k] == cos[k] for k in common if k[1] == 0.0)  # equator: equal
 
 
 # Each misreading as a textual change of the oracle source: (old, new).  Every
@@ -70,10 +89,7 @@ MUTANTS = {
          "p[3] = dec - R < -90.0 ? orc_ang2pix(wrap_ra(ra + 180.0), -180.0 - (dec - R), order)"
          " : orc_ang2pix(ra, dec_minus, order);")],
     "ra_shift_over_cos_dec": [
-        ("p[1] = orc_ang2pix(wrap_ra(ra + R), dec, order);",
-         "p[1] = orc_ang2pix(wrap_ra(ra + R / cos(dec * (M_PI / 180.0))), dec, order);"),
-        ("p[2] = orc_ang2pix(wrap_ra(ra - R), dec, order);",
-         "p[2] = orc_ang2pix(wrap_ra(ra - R / cos(dec * (M_PI / 180.0))), dec, order);")],
+        ("double RA = cosdec ? ra_shift_cos(R, dec) : R;", "double RA = ra_shift_cos(R, dec);")],
     "no_dedup": [("if (m == 0 || p[i] != out[m - 1]) out[m++] = p[i];", "out[m++] = p[i];")],
 }
 
@@ -95,6 +111,8 @@ def _build_mutant(tmp_path, name, edits):
     lib.orc_quad_cells.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int,
                                    C.POINTER(C.c_uint64)]
     lib.orc_quad_cells.restype = C.c_int
+    lib.orc_quad_cells_cos.argtypes = lib.orc_quad_cells.argtypes
+    lib.orc_quad_cells_cos.restype = C.c_int
     return lib
 
 
@@ -115,3 +133,25 @@ def test_each_misreading_fails_a_hand_placed_case(tmp_path, name):
     lib = _build_mutant(tmp_path, name, MUTANTS[name])
     wrong = [c[:4] for c in CASES if _cells(lib, *c[:4]) != c[4]]
     assert wrong, f"misreading {name} passes every hand-placed case"
+
+
+# Misreadings of the variant's RA shift, checked against its own cases.
+MUTANTS_COS = {
+    "times_cos_not_over": [("double RA = c > 0.0 ? R / c : 180.0;",
+                            "double RA = c > 0.0 ? R * c : 180.0;")],
+    "no_cap_at_180": [("  if (RA > 180.0) RA = 180.0;\n  return RA;", "  return RA;")],
+    "cos_of_radians": [("  orc_sincos_deg(dec, &sd, &cd);\n  double c = fabs(cd);",
+                        "  orc_sincos_deg(dec, &sd, &cd);\n  double c = fabs(cos(dec));")],
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_COS))
+def test_each_misreading_of_the_variant_fails_a_case(tmp_path, name):
+    lib = _build_mutant(tmp_path, name, MUTANTS_COS[name])
+    buf = (C.c_uint64 * 5)()
+    wrong = []
+    for ra, dec, r, L, want in CASES_COS:
+        m = lib.orc_quad_cells_cos(ra, dec, r, L, buf)
+        if [int(buf[i]) for i in range(m)] != want:
+            wrong.append((ra, dec))
+    assert wrong, f"misreading {name} passes every hand-placed case of the variant"
