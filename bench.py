@@ -376,6 +376,11 @@ def run_hlc(args):
                                      **rows_equal(rq, rq64)},
                       "parity": oq}
 
+    # per-source error radii (Eq. 4) on the same catalogues
+    eq4 = None
+    if args.workload == "fullsky" and not args.no_eq4 and mode == hlc.HLC_COMPLETE8:
+        eq4 = eq4_line(args, hlc, synth, A, B, L, Lc, stream, rank, world, prec, other)
+
     # dense cells: the pair test where it is bound by the FP32 pipe
     dense = None
     if args.workload == "fullsky" and not args.no_dense:
@@ -423,6 +428,8 @@ def run_hlc(args):
             line["other_mode"] = other_mode
         if dense is not None:
             line["dense"] = dense
+        if eq4 is not None:
+            line["eq4"] = eq4
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -594,6 +601,69 @@ def critical_path(stats, ms_step) -> dict:
     return out
 
 
+def eq4_line(args, hlc, synth, A, B, L, Lc, stream, rank, world, prec, other):
+    """The same catalogues with per-source error radii (Eq. 4): e log-uniform
+    in [0.05, 0.5] arcsec per source, so pair radii 3 sqrt(e_a^2 + e_b^2)
+    span 0.2-2.1 arcsec.  Timed in both forms; the chosen form's rows must
+    equal the plain form's and, for a sample of A sources, the oracle's."""
+    import numpy as np
+    import torch
+    dev = A.ra.device
+    ea = synth.error_radii(2301073315 + rank, 1, A.ra.numel(), 0.05, 0.5, device=dev)
+    eb = synth.error_radii(2301073315 + rank, 2, B.ra.numel(), 0.05, 0.5, device=dev)
+
+    def step(precision):
+        plan = hlc.hlc_plan(A, B, 0.0, L, coarse_level=Lc, precision=precision, stream=stream,
+                            err_a=ea, err_b=eb)
+        res = hlc.hlc_match(plan, copy=False)
+        st = res["stats"]
+        hlc.hlc_free(plan)
+        return st
+    K = max(3, args.steps // 4)
+    ms, sts = _timed_loop(lambda: step(prec), K, 2, stream, collect=True)
+    ms64, _ = _timed_loop(lambda: step(other), max(2, K // 2), 1, stream)
+
+    def rows(precision):
+        plan = hlc.hlc_plan(A, B, 0.0, L, coarse_level=Lc, precision=precision, stream=stream,
+                            err_a=ea, err_b=eb)
+        res = hlc.hlc_match(plan, copy=False)
+        out = (res["id_a"].cpu().numpy().view("u8"), res["id_b"].cpu().numpy().view("u8"),
+               res["sep"].cpu().numpy())
+        hlc.hlc_free(plan)
+        return out
+    r32, r64 = rows(prec), rows(other)
+    parity = None
+    if rank == 0 and not args.no_cpu:
+        import oracle as O
+        rng = np.random.default_rng(17)
+        ra_a, dec_a, id_a = (x.cpu().numpy() for x in (A.ra, A.dec, A.id))
+        id_a = id_a.view(np.uint64)
+        pick = np.sort(rng.choice(ra_a.size, 20000, replace=False))
+        t0 = time.perf_counter()
+        want = O.match_eq4(ra_a[pick], dec_a[pick], id_a[pick], ea.cpu().numpy()[pick],
+                           B.ra.cpu().numpy(), B.dec.cpu().numpy(),
+                           B.id.cpu().numpy().view(np.uint64), eb.cpu().numpy(), L)
+        t = time.perf_counter() - t0
+        sel = np.isin(r32[0], id_a[pick])
+        ga, gb, gs = r32[0][sel], r32[1][sel], r32[2][sel]
+        eq = ga.size == want["id_a"].size and bool(np.array_equal(ga, want["id_a"])) and \
+            bool(np.array_equal(gb, want["id_b"]))
+        err = float(np.max(np.abs(gs - want["sep"]))) if eq and ga.size else (0.0 if eq else None)
+        parity = {"equal": eq, "rows": int(ga.size), "a_sources": int(pick.size),
+                  "max_sep_err_arcsec": err, "sep_within_tolerance": bool(eq and err <= 1e-6),
+                  "oracle_seconds": t,
+                  "sample": "20000 random A sources against all of B (oracle per-pair radii)"}
+    n = A.ra.numel() + B.ra.numel()
+    last = sts[-1]
+    return {"radii": "e log-uniform in [0.05, 0.5] arcsec per source; r_ij = 3 sqrt(e_i^2 + "
+                     "e_j^2) in [0.21, 2.12] arcsec",
+            "ms_per_step": ms, "value": n / (ms / 1e3), "unit": "sources/s", "steps": K,
+            "matches": last["matches"], "band_candidates": last["band_candidates"],
+            "band_fp64": last["band_fp64"],
+            "plain_form": {"ms_per_step": ms64, "value": n / (ms64 / 1e3), **rows_equal(r32, r64)},
+            "parity": parity}
+
+
 def dense_line(args, hlc, synth, dev, stream, rank, world):
     """Dense cells, where the pair test is bound by the FP32 pipe: the
     clustered workload at a reduced size (galactic mixture + Plummer clusters
@@ -658,9 +728,10 @@ def _timed_loop(fn, K, W, stream, collect=False):
     return e0.elapsed_time(e1) / K, (outs if collect else out)
 
 
-def _line(args, metric, value, unit, ms, config, **extra):
+def _line(args, metric, value, unit, ms, config, higher_is_better=True, **extra):
     d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
-         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": higher_is_better,
+         "scaling": "weak",
          "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded, generated on device)",
          "config": config}
     d.update(extra)
@@ -769,14 +840,19 @@ def run_batched(args):
     stream = torch.cuda.current_stream()
     spec = [{"A": j.A, "B": j.B, "radius_arcsec": j.r_arcsec} for j in jobs]
     total = sum(j.A.ra.numel() + j.B.ra.numel() for j in jobs)
+    # the autotuner (form 2) on a sample of these jobs, outside the timed region
+    t0 = time.perf_counter()
+    tune, report = hlc.hlc_autotune(spec, sample_jobs=args.tune_sample, stream=stream)
+    report["seconds"] = time.perf_counter() - t0
 
-    def batched():
-        plan = hlc.hlc_plan_batched(spec, stream=stream)
+    def batched(tn=None):
+        plan = hlc.hlc_plan_batched(spec, stream=stream, tune=tn)
         out = hlc.hlc_match(plan, copy=False)
         n_, st_ = out["n"], out["stats"]
         hlc.hlc_free(plan)
         return n_, st_
-    ms_b, (nb_, st_b) = _timed_loop(batched, args.steps, args.warmup, stream)
+    ms_b, (nb_, st_b) = _timed_loop(lambda: batched(tune), args.steps, args.warmup, stream)
+    ms_r, (nr_, st_r) = _timed_loop(lambda: batched(None), args.steps, args.warmup, stream)
     orders = [_auto_order(j.B.ra.numel(), j.cone_deg, j.r_arcsec) for j in jobs]
 
     def per_job():
@@ -793,6 +869,9 @@ def run_batched(args):
                                                        total)},
           matches=nb_, per_job={"ms": ms_j, "sources_per_s": total / (ms_j / 1e3), "matches": nj_},
           speedup_vs_per_job=ms_j / ms_b, pair_tests=st_b["pair_tests"],
+          autotune=report, rule={"ms": ms_r, "sources_per_s": total / (ms_r / 1e3),
+                                 "matches": nr_, "ms_pair": st_r["ms_pair"]},
+          tuned_vs_rule=ms_r / ms_b,
           gpu_launches=st_b["kernel_launches"], tile_items=st_b["tile_items"],
           tile_entries_a=st_b["tile_entries_a"], band_candidates=st_b["band_candidates"],
           stages_ms={k: st_b[k] for k in ("ms_prep", "ms_sort", "ms_index", "ms_pair",
@@ -850,6 +929,62 @@ def run_streamed(args):
           equal_counts=ns_ == nc_)
 
 
+def run_completeness(args):
+    """Completeness of the quad-direction strategy (the analogue of Table 4 and
+    Sec. 5.3): for catalogues of growing size and several HEALPix orders, the
+    pairs each quad reading (Algorithm 1 literal, and with the RA shift
+    r / cos(dec)) loses against complete mode, whose set is the exact set of
+    Eq. 1 (equal to the oracle's in the parity tests).  The paper's simulated
+    data sets are not available; the full-sky recipe (40% uniform + 60%
+    galactic disk, B = 60% jittered copies) and a clustered sky stand in."""
+    import torch
+
+    import paper_2301_07331_b300 as hlc
+    from paper_2301_07331_b300 import synth
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    r = 1.5
+    rows = []
+    sizes = [int(x) for x in args.sizes.split(",")]
+    levels = [int(x) for x in args.levels.split(",")]
+
+    def run(A, B, L, mode):
+        ms, (n, st) = _timed_loop(lambda: _one(A, B, L, mode), 2, 1, stream)
+        return n, ms
+
+    def _one(A, B, L, mode):
+        plan = hlc.hlc_plan(A, B, r, L, coarse_level=min(4, L), boundary=mode, stream=stream)
+        res = hlc.hlc_match(plan, copy=False)
+        n, st = res["n"], res["stats"]
+        hlc.hlc_free(plan)
+        return n, st
+    skies = [("fullsky", n, lambda n=n: synth.fullsky_pair(na=n, nb=n, device=dev)) for n in sizes]
+    skies.append(("clusters", sizes[-1] // 2, lambda: synth.clustered_pair(
+        na=sizes[-1] // 2, nb=sizes[-1] // 2, n_clusters=max(1, sizes[-1] // 4_000_000),
+        device=dev)))
+    for name, n, make in skies:
+        A, B = make()
+        for L in levels:
+            if r > math.sqrt(math.pi / 3) / 2 ** L * 648000 / math.pi / 8:
+                continue
+            nc, msc = run(A, B, L, hlc.HLC_COMPLETE8)
+            nq, msq = run(A, B, L, hlc.HLC_QUAD)
+            nqc, msqc = run(A, B, L, hlc.HLC_QUAD_COSDEC)
+            rows.append({"sky": name, "n_per_side": n, "order": L, "complete": nc,
+                         "quad_lost": nc - nq, "quad_cosdec_lost": nc - nqc,
+                         "ms_complete": msc, "ms_quad": msq, "ms_quad_cosdec": msqc})
+        del A, B
+        torch.cuda.empty_cache()
+    total = sum(x["complete"] for x in rows)
+    _line(args, "pairs lost by the quad-direction strategy against the exact set",
+          sum(x["quad_cosdec_lost"] for x in rows), "pairs", sum(x["ms_quad_cosdec"] for x in rows),
+          {"workload": "completeness study: full sky %s per side and a clustered sky, orders %s, "
+                       "r = %g arcsec" % ("/".join(_mega(x) for x in sizes), args.levels, r)},
+          higher_is_better=False, rows=rows, exact_pairs_total=total,
+          quad_lost_total=sum(x["quad_lost"] for x in rows),
+          quad_cosdec_lost_total=sum(x["quad_cosdec_lost"] for x in rows))
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle on a bounded sample per step."""
     import torch
@@ -902,13 +1037,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hlc", choices=["hlc", "reference"])
     ap.add_argument("--workload", default="fullsky",
-                    choices=["fullsky", "clusters", "bulge", "learned", "batched", "streamed"])
+                    choices=["fullsky", "clusters", "bulge", "learned", "batched", "streamed",
+                             "completeness"])
     ap.add_argument("--n-match", type=int, default=100_000_000,
                     help="learned: sources per side of the match slice")
     ap.add_argument("--jobs", type=int, default=4096, help="batched: number of jobs")
     ap.add_argument("--scale", type=float, default=1.0, help="batched: source-count scale")
+    ap.add_argument("--tune-sample", type=int, default=1024,
+                    help="batched: jobs in the autotuner's calibration sample")
     ap.add_argument("--budget-gb", type=int, default=16, help="streamed: device budget")
     ap.add_argument("--n", type=int, default=0, help="A sources (0: the workload's size)")
+    ap.add_argument("--sizes", default="1000000,4000000,10000000,20000000",
+                    help="completeness: sources per side of the full-sky catalogues")
+    ap.add_argument("--levels", default="10,11,12,13", help="completeness: HEALPix orders")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--mode", default="complete", choices=["complete", "quad"])
     ap.add_argument("--no-e2e", action="store_true")
@@ -916,6 +1057,8 @@ def main():
     ap.add_argument("--no-other-mode", action="store_true",
                     help="skip the other boundary mode's sub-line")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense-cell sub-line")
+    ap.add_argument("--no-eq4", action="store_true",
+                    help="skip the per-source radii (Eq. 4) sub-line")
     ap.add_argument("--dense-n", type=int, default=20_000_000,
                     help="A sources of the dense-cell sub-line (B = 3/4 of it)")
     ap.add_argument("--clocks-out", default="",
@@ -930,6 +1073,8 @@ def main():
         run_batched(args)
     elif args.workload == "streamed":
         run_streamed(args)
+    elif args.workload == "completeness":
+        run_completeness(args)
     else:
         run_hlc(args)
 

@@ -16,6 +16,11 @@
  *                    the exact set; each pair is reported once, from the
  *                    smallest cell the two sources share).
  *
+ * The radius is one r for every pair, or with HLC_RADIUS_EQ4 the paper's
+ * criterion of Eq. 4 with per-source error radii: r_ij = 3 sqrt(e_i^2 +
+ * e_j^2), evaluated as a = e_i e_i, b = e_j e_j, t = a + b, r = 3 sqrt(t)
+ * (each step a correctly rounded binary64 operation; symmetric in i, j).
+ *
  * Decision arithmetic.  A pair matches when its squared chord
  * |u_A - u_B|^2 <= 4 sin^2(r/2) (Eq. 1 in chord form), both sides evaluated
  * in a fixed sequence of IEEE binary64 operations: sin/cos in degrees by exact
@@ -56,12 +61,22 @@ extern "C" {
 /* ---- enums -------------------------------------------------------------- */
 #define HLC_COMPLETE8 0
 #define HLC_QUAD 1
+#define HLC_QUAD_COSDEC 2 /* Algorithm 1 with the RA error radius read as an
+                             angle on the sky: the RA copies are shifted by
+                             R / cos(dec) (canonical cosine, at most 180 deg)
+                             instead of R; Dec copies by R as in HLC_QUAD */
 
 #define HLC_FP64 0       /* plain form: binary64 vectors and pair test */
 #define HLC_FP32_GUARD 1 /* FP32 bulk test + guard band + binary64 recheck */
 
 #define HLC_INDEX_BSEARCH 0 /* cell offsets by binary search of unique keys */
 #define HLC_INDEX_LEARNED 1 /* per-partition learned model + bounded search */
+
+#define HLC_RADIUS_FIXED 0 /* one radius r = radius_arcsec for every pair */
+#define HLC_RADIUS_EQ4 1   /* per-source error radii (Sec. 2.1, Eq. 4): pair
+                              (A_i, B_j) matches when its separation is at
+                              most r_ij = 3 sqrt(e_i^2 + e_j^2), e from the
+                              catalogues' err_arcsec columns */
 
 #define HLC_MODEL_PLA 0 /* 256-segment monotone piecewise-linear model */
 #define HLC_MODEL_MLP 1 /* 1-input 2x32 ReLU MLP, bracket-checked */
@@ -74,19 +89,54 @@ typedef struct {
   const double* dec_deg; /* n values */
   const uint64_t* id;    /* n user ids (need not be unique) */
   uint64_t n;            /* number of sources, < 2^31 */
-  int on_device;         /* 1: the three arrays are device pointers;
+  int on_device;         /* 1: the arrays are device pointers;
                             0: host pointers (pinned or pageable) */
+  const double* err_arcsec; /* n per-source position error radii in arcsec
+                               (finite, >= 0), read with HLC_RADIUS_EQ4 only;
+                               may be NULL otherwise.  Same memory space as
+                               the other arrays. */
 } hlc_catalog;
+
+/* Shape of the batched form's work (form 2): the order each job is matched
+ * at and the tile kernel's tiles for dense cells.  The library's rule is
+ * {2.0, {2, 4, 4}, 1536}; hlc_autotune times alternatives on a sample of the
+ * caller's own jobs and returns the fastest it found. */
+typedef struct {
+  double target_per_cell;   /* batched jobs with fine_level < 0: the order is
+                               the one leaving about this many B sources per
+                               cell (capped by r <= theta_L/8); > 0 */
+  uint32_t ka[3];           /* tile kernel: A sources per lane (1, 2 or 4)
+                               for dense A cells of 33-64, 65-256 and more
+                               than 256 sources (cells of 32 use 1) */
+  uint32_t stage;           /* tile kernel: B vectors per staged round, a
+                               multiple of 8 in [8, 1536] */
+} hlc_tune;
+
+/* One timed candidate of hlc_autotune. */
+typedef struct {
+  hlc_tune tune;
+  float ms;                 /* device time of hlc_plan + hlc_match on the
+                               sample (best of two runs) */
+} hlc_tune_trial;
+
+typedef struct {
+  hlc_tune best;            /* the fastest candidate */
+  float ms_rule, ms_best;   /* the rule's and the best candidate's time */
+  uint32_t sample_jobs;     /* jobs in the calibration sample */
+  uint32_t n_trials;        /* entries of trials[] used */
+  hlc_tune_trial trials[32];
+} hlc_tune_report;
 
 typedef void* (*hlc_alloc_fn)(size_t bytes, void* ctx);
 typedef void (*hlc_dealloc_fn)(void* ptr, void* ctx);
 
 typedef struct {
-  double radius_arcsec;       /* r > 0; COMPLETE8 needs r <= theta_L/8 */
+  double radius_arcsec;       /* r > 0; COMPLETE8 needs r <= theta_L/8
+                                 (HLC_RADIUS_FIXED) */
   int coarse_level;           /* HEALPix order of streaming / learned-index
                                  partitions, 0 <= coarse <= fine */
   int fine_level;             /* HEALPix order L of the cells, 0..14 */
-  int boundary;               /* HLC_COMPLETE8 or HLC_QUAD */
+  int boundary;               /* HLC_COMPLETE8, HLC_QUAD or HLC_QUAD_COSDEC */
   int precision;              /* HLC_FP64 or HLC_FP32_GUARD */
   int index;                  /* HLC_INDEX_BSEARCH or HLC_INDEX_LEARNED */
   int model;                  /* HLC_MODEL_PLA or HLC_MODEL_MLP (learned) */
@@ -99,6 +149,18 @@ typedef struct {
                                  library uses cudaMallocAsync on stream) */
   hlc_dealloc_fn dealloc;
   void* alloc_ctx;
+  const hlc_tune* tune;       /* NULL: the library's rule; else the order
+                                 target and tile shape to use (batched plans:
+                                 the same pointer for every job) */
+  int radius_rule;            /* HLC_RADIUS_FIXED (radius_arcsec) or
+                                 HLC_RADIUS_EQ4 (per-pair radius from the
+                                 catalogues' err_arcsec; radius_arcsec is then
+                                 ignored).  EQ4 is implemented for single,
+                                 in-core plans in complete mode with the
+                                 binary-searched index, in both precisions
+                                 (HLC_EUNSUPPORTED otherwise), and needs the
+                                 largest pair radius 3 sqrt(max e_A^2 +
+                                 max e_B^2) <= theta_L/8 (HLC_EINVAL above). */
 } hlc_params;
 
 /* Result of hlc_match: rows sorted ascending by (id_a, id_b) as unsigned
@@ -165,6 +227,12 @@ typedef struct {
                                       (ms_total = ms_plan_span + ms_candidates
                                       + ms_pair + ms_recheck + ms_output for
                                       single plans: consecutive intervals) */
+  uint64_t h2d_bytes, h2d_copies;  /* streamed plans: host-to-device copies issued */
+  uint64_t d2h_bytes, d2h_copies;  /*   and device-to-host copies */
+  float ms_model_h2d, ms_model_d2h;/*   their time by the transfer model of Eq. 5,
+                                      the sum over copies of alpha + beta d with
+                                      the device's measured fit (hlc_transfer_model) */
+  uint64_t stream_chunk;           /*   sources per streamed chunk (from the fit) */
   float ms_plan_presort;           /* FP32 complete form with device inputs:
                                       from the plan's start to the first digit
                                       pass (both preps, side by side, and the
@@ -227,14 +295,16 @@ int hlc_neighbours(const uint32_t* pix, uint64_t n, int order, int64_t* out,
                    void* stream);
 
 /* Quad-direction cell set of each source (Algorithm 1): the distinct pixels
- * of (ra, dec), (ra +- R, dec), (ra, dec -+ R), R = r/3600 deg, RA wrapped,
- * Dec clamped, ascending.  out: 5n device uint32 padded with 0xFFFFFFFF;
- * count: n device int32.  precision HLC_FP32_GUARD computes the same sets
- * through the FP32 pixel estimate (the shifted coordinates in float-float),
- * each undecided position in binary64.  Returns HLC_EINVAL for a bad order,
- * radius or precision, or for non-finite RA/Dec or |Dec| > 90. */
+ * of (ra, dec), (ra +- R_A, dec), (ra, dec -+ R), R = r/3600 deg, R_A = R
+ * (boundary HLC_QUAD) or R / cos(dec) capped at 180 (HLC_QUAD_COSDEC), RA
+ * wrapped, Dec clamped, ascending.  out: 5n device uint32 padded with
+ * 0xFFFFFFFF; count: n device int32.  precision HLC_FP32_GUARD computes the
+ * same sets through the FP32 pixel estimate (the shifted coordinates in
+ * float-float), each undecided position in binary64.  Returns HLC_EINVAL for
+ * a bad order, radius, precision or boundary, or for non-finite RA/Dec or
+ * |Dec| > 90. */
 int hlc_quad_cells(const double* ra, const double* dec, uint64_t n,
-                   double radius_arcsec, int order, int precision,
+                   double radius_arcsec, int order, int precision, int boundary,
                    uint32_t* out, int32_t* count, void* stream);
 
 /* Unit vectors (3n device doubles, interleaved x,y,z) in the binary64
@@ -274,6 +344,46 @@ int hlc_sort_pairs(void* keys, uint32_t* vals, uint64_t n, int key_size,
  *     error after the array's address was taken. */
 int hlc_sort_pairs_noalloc(void* keys, uint32_t* vals, uint64_t n, int key_size,
                            int key_bits, void* stream);
+
+/* Transfer-cost model of Sec. 4.1.1, Eq. 5: a copy of d bytes between host
+ * and device takes T(d) = alpha + beta d.  Measured on the current device
+ * the paper's way: alpha is the time of a one-byte copy, beta = (t_s - alpha)
+ * / s from the time t_s of an s = 256 MiB copy (pinned host memory, medians
+ * of 21 and 5 copies, CUDA events on a stream of its own).  Four more sizes
+ * are timed to check the line.  Streamed plans use the same fit, measured
+ * once per device and kept: their chunk is the smallest number of sources
+ * (a multiple of 2^20, at most 8 Mi) whose copy spends at most 1% of its time
+ * in alpha, and hlc_stats reports their copies' predicted time beside the
+ * measured one.  Allocates 256 MiB of pinned host and device memory for the
+ * duration of the call and synchronises. */
+typedef struct {
+  double alpha_s[2];          /* [0] host to device, [1] device to host */
+  double beta_s_per_byte[2];
+  double gbs[2];              /* 1 / beta, GB/s */
+  uint64_t check_bytes[4];    /* the sizes timed to check the line */
+  double check_measured_s[2][4];
+  double check_model_s[2][4];
+} hlc_transfer_fit;
+
+int hlc_transfer_model(hlc_transfer_fit* out);
+
+/* Autotuner of the batched form (form 2; the paper's counterpart is the
+ * blockDim sweep of Sec. 5.2, Fig. 8).  Takes the same arguments as a
+ * batched hlc_plan (A, B, p: arrays of n_jobs) and times, on a sample of at
+ * most sample_jobs of those jobs spread over their B sizes, the rule and
+ * candidates changed one at a time (coordinate descent): the order target
+ * in {0.5, 1, 2, 4, 8} B sources per cell, then KA in {1, 2, 4} for each
+ * density class of dense A cells, then the staged round in {384, 768, 1536}
+ * B vectors; a change is kept when it is at least 3% faster.  Each
+ * candidate is a full batched plan + match of the sample (device time, best
+ * of three).  Last, the winner and the rule are timed in turn (best of four
+ * each) and the winner is reported only if it is at least 2% faster, else
+ * the rule.  report->best can be passed as hlc_params.tune.  The jobs' own
+ * fine_level and p[].tune are ignored for the ordering rule's trials only
+ * where fine_level >= 0 (those jobs keep their order).  Synchronises the
+ * stream; allocates like hlc_plan. */
+int hlc_autotune(const hlc_catalog* A, const hlc_catalog* B, const hlc_params* p,
+                 uint32_t n_jobs, uint32_t sample_jobs, hlc_tune_report* report);
 
 /* ---- test hooks (no counterpart in the paper) -----------------------------
  * Every device-side wait of the library (the radix sort's and the scans'

@@ -23,10 +23,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "libhlc.so")
 
 HLC_OK, HLC_EINVAL, HLC_ENOMEM, HLC_ECUDA, HLC_ETIMEOUT, HLC_EUNSUPPORTED = range(6)
-HLC_COMPLETE8, HLC_QUAD = 0, 1
+HLC_COMPLETE8, HLC_QUAD, HLC_QUAD_COSDEC = 0, 1, 2
 HLC_FP64, HLC_FP32_GUARD = 0, 1
 HLC_INDEX_BSEARCH, HLC_INDEX_LEARNED = 0, 1
 HLC_MODEL_PLA, HLC_MODEL_MLP, HLC_MODEL_NONE = 0, 1, 2
+HLC_RADIUS_FIXED, HLC_RADIUS_EQ4 = 0, 1
 
 _ERRNAMES = {1: "HLC_EINVAL", 2: "HLC_ENOMEM", 3: "HLC_ECUDA", 4: "HLC_ETIMEOUT",
              5: "HLC_EUNSUPPORTED"}
@@ -46,7 +47,7 @@ _NO_DEALLOC = _DEALLOC_FN()
 
 class Catalog(C.Structure):
     _fields_ = [("ra_deg", C.c_void_p), ("dec_deg", C.c_void_p), ("id", C.c_void_p),
-                ("n", C.c_uint64), ("on_device", C.c_int)]
+                ("n", C.c_uint64), ("on_device", C.c_int), ("err_arcsec", C.c_void_p)]
 
 
 class Params(C.Structure):
@@ -54,7 +55,34 @@ class Params(C.Structure):
                 ("fine_level", C.c_int), ("boundary", C.c_int), ("precision", C.c_int),
                 ("index", C.c_int), ("model", C.c_int), ("want_sep", C.c_int),
                 ("device_mem_budget", C.c_uint64), ("stream", C.c_void_p),
-                ("alloc", _ALLOC_FN), ("dealloc", _DEALLOC_FN), ("alloc_ctx", C.c_void_p)]
+                ("alloc", _ALLOC_FN), ("dealloc", _DEALLOC_FN), ("alloc_ctx", C.c_void_p),
+                ("tune", C.c_void_p), ("radius_rule", C.c_int)]
+
+
+class TransferFit(C.Structure):
+    """hlc_transfer_fit: alpha and beta of Eq. 5 per direction."""
+    _fields_ = [("alpha_s", C.c_double * 2), ("beta_s_per_byte", C.c_double * 2),
+                ("gbs", C.c_double * 2), ("check_bytes", C.c_uint64 * 4),
+                ("check_measured_s", (C.c_double * 4) * 2), ("check_model_s", (C.c_double * 4) * 2)]
+
+
+class Tune(C.Structure):
+    """hlc_tune: the batched form's order target and tile shape."""
+    _fields_ = [("target_per_cell", C.c_double), ("ka", C.c_uint32 * 3), ("stage", C.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {"target_per_cell": self.target_per_cell, "ka": list(self.ka),
+                "stage": self.stage}
+
+
+class TuneTrial(C.Structure):
+    _fields_ = [("tune", Tune), ("ms", C.c_float)]
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("best", Tune), ("ms_rule", C.c_float), ("ms_best", C.c_float),
+                ("sample_jobs", C.c_uint32), ("n_trials", C.c_uint32),
+                ("trials", TuneTrial * 32)]
 
 
 class Result(C.Structure):
@@ -80,8 +108,11 @@ class Stats(C.Structure):
                                           "ms_sort_passes")] + [("sort_passes", C.c_uint32),
                                                                 ("band_fp64", C.c_uint64),
                                                                 ("sort_entries", C.c_uint64),
-                                                                ("ms_plan_span", C.c_float),
-                                                                ("ms_plan_presort", C.c_float)]
+                                                                ("ms_plan_span", C.c_float)] + [
+                (f, C.c_uint64) for f in ("h2d_bytes", "h2d_copies", "d2h_bytes",
+                                          "d2h_copies")] + [
+                ("ms_model_h2d", C.c_float), ("ms_model_d2h", C.c_float),
+                ("stream_chunk", C.c_uint64), ("ms_plan_presort", C.c_float)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -116,12 +147,14 @@ def lib():
     L.hlc_canonical_coefficients.argtypes = [P, P]
     L.hlc_ang2pix.argtypes = [P, P, u64, i32, i32, P, P]
     L.hlc_neighbours.argtypes = [P, u64, i32, P, P]
-    L.hlc_quad_cells.argtypes = [P, P, u64, d, i32, i32, P, P, P]
+    L.hlc_quad_cells.argtypes = [P, P, u64, d, i32, i32, i32, P, P, P]
     L.hlc_unitvec.argtypes = [P, P, u64, P, P]
     L.hlc_sort_pairs.argtypes = [P, P, u64, i32, i32, P]
     L.hlc_sort_pairs_noalloc.argtypes = [P, P, u64, i32, i32, P]
     L.hlc_cell_table.argtypes = [P, u64, P, P, C.POINTER(C.c_uint64), P]
     L.hlc_learned_lookup.argtypes = [P, u64, i32, i32, P, u64, P, P, P]
+    L.hlc_autotune.argtypes = [P, P, P, C.c_uint32, C.c_uint32, P]
+    L.hlc_transfer_model.argtypes = [P]
     L.hlc_test_spin_shift.argtypes = [i32]
     L.hlc_test_unset_wait.argtypes = [i32, P]
     _lib = L
@@ -211,8 +244,9 @@ class Plan:
             pass
 
 
-def _catalog(ra, dec, ids):
-    """Catalog struct for torch (CUDA or CPU) tensors or numpy arrays."""
+def _catalog(ra, dec, ids, err=None):
+    """Catalog struct for torch (CUDA or CPU) tensors or numpy arrays; err:
+    optional per-source error radii (arcsec) in the same memory space."""
     if isinstance(ra, torch.Tensor):
         on_dev = ra.is_cuda
         ra = ra.contiguous().to(torch.float64)
@@ -220,31 +254,43 @@ def _catalog(ra, dec, ids):
         ids = ids.contiguous()
         if ids.dtype not in (torch.int64, torch.uint64):
             ids = ids.to(torch.int64)
+        if err is not None:
+            err = torch.as_tensor(err, dtype=torch.float64, device=ra.device).contiguous()
         if not on_dev:
-            ptrs = (ra.data_ptr(), dec.data_ptr(), ids.data_ptr())
+            ptrs = (ra.data_ptr(), dec.data_ptr(), ids.data_ptr(),
+                    err.data_ptr() if err is not None else None)
         else:
-            ptrs = (_dptr(ra), _dptr(dec), _dptr(ids))
-        return Catalog(ptrs[0], ptrs[1], ptrs[2], ra.numel(), int(on_dev)), (ra, dec, ids)
+            ptrs = (_dptr(ra), _dptr(dec), _dptr(ids), _dptr(err) if err is not None else None)
+        return (Catalog(ptrs[0], ptrs[1], ptrs[2], ra.numel(), int(on_dev), ptrs[3]),
+                (ra, dec, ids, err))
     ra = np.ascontiguousarray(ra, dtype=np.float64)
     dec = np.ascontiguousarray(dec, dtype=np.float64)
     ids = np.ascontiguousarray(ids).view(np.uint64) if np.asarray(ids).dtype.itemsize == 8 \
         else np.ascontiguousarray(ids, dtype=np.uint64)
-    return Catalog(ra.ctypes.data, dec.ctypes.data, ids.ctypes.data, ra.size, 0), (ra, dec, ids)
+    if err is not None:
+        err = np.ascontiguousarray(err, dtype=np.float64)
+    return (Catalog(ra.ctypes.data, dec.ctypes.data, ids.ctypes.data, ra.size, 0,
+                    err.ctypes.data if err is not None else None), (ra, dec, ids, err))
 
 
 def hlc_plan(A, B, radius_arcsec: float, fine_level: int, coarse_level: int | None = None,
              boundary: int = HLC_COMPLETE8, precision: int = HLC_FP32_GUARD,
              index: int = HLC_INDEX_BSEARCH, model: int = HLC_MODEL_PLA, want_sep: bool = True,
-             device_mem_budget: int = 0, stream=None, torch_alloc: bool = False) -> Plan:
+             device_mem_budget: int = 0, stream=None, torch_alloc: bool = False,
+             err_a=None, err_b=None) -> Plan:
     """Index two catalogues.  A and B are (ra, dec, id) triples (torch tensors
     on the device or host, or numpy arrays on the host) or objects with .ra,
     .dec, .id.  Device memory comes from the library's stream-ordered pool,
-    or from torch's caching allocator with torch_alloc=True.  Returns a Plan
-    for hlc_match."""
+    or from torch's caching allocator with torch_alloc=True.  With err_a and
+    err_b (per-source error radii in arcsec, beside the coordinates) the
+    radius of each pair is Eq. 4's 3 sqrt(err_a[i]^2 + err_b[j]^2) and
+    radius_arcsec is ignored.  Returns a Plan for hlc_match."""
     _require_cuda()
     L = lib()
-    cA, keepA = _catalog(*(_triple(A)))
-    cB, keepB = _catalog(*(_triple(B)))
+    if (err_a is None) != (err_b is None):
+        raise ValueError("give both err_a and err_b (Eq. 4) or neither")
+    cA, keepA = _catalog(*(_triple(A)), err=err_a)
+    cB, keepB = _catalog(*(_triple(B)), err=err_b)
     st = _stream_ptr(stream)
     alloc = _TorchAllocator(torch.cuda.current_device(), st) if torch_alloc else None
     p = Params(float(radius_arcsec), int(fine_level if coarse_level is None else coarse_level),
@@ -254,18 +300,13 @@ def hlc_plan(A, B, radius_arcsec: float, fine_level: int, coarse_level: int | No
                None)
     if coarse_level is None:
         p.coarse_level = min(4, int(fine_level))
+    p.radius_rule = HLC_RADIUS_EQ4 if err_a is not None else HLC_RADIUS_FIXED
     h = C.c_void_p()
     _check(L.hlc_plan(C.byref(cA), C.byref(cB), C.byref(p), 1, C.byref(h)))
     return Plan(h, p, alloc, (keepA, keepB))
 
 
-def hlc_plan_batched(jobs, precision: int = HLC_FP32_GUARD, want_sep: bool = True,
-                     stream=None, torch_alloc: bool = False) -> Plan:
-    """One plan over many independent jobs.  jobs: sequence of dicts with keys
-    A, B ((ra, dec, id) triples or catalogue objects), radius_arcsec and
-    fine_level (-1 = chosen by the library from the job's density)."""
-    _require_cuda()
-    L = lib()
+def _batched_args(jobs, precision, want_sep, stream, torch_alloc, tune):
     n = len(jobs)
     cats_a = (Catalog * n)()
     cats_b = (Catalog * n)()
@@ -284,10 +325,56 @@ def hlc_plan_batched(jobs, precision: int = HLC_FP32_GUARD, want_sep: bool = Tru
         params[i] = Params(float(jb["radius_arcsec"]), 0, fl, HLC_COMPLETE8, int(precision),
                            HLC_INDEX_BSEARCH, HLC_MODEL_PLA, int(bool(want_sep)), 0, st,
                            alloc.alloc if alloc else _NO_ALLOC,
-                           alloc.dealloc if alloc else _NO_DEALLOC, None)
+                           alloc.dealloc if alloc else _NO_DEALLOC, None,
+                           C.addressof(tune) if tune is not None else None, HLC_RADIUS_FIXED)
+    return n, cats_a, cats_b, params, keep, alloc
+
+
+def hlc_transfer_model() -> dict:
+    """Measure the transfer-cost model of Eq. 5 (alpha, beta per direction)."""
+    _require_cuda()
+    f = TransferFit()
+    _check(lib().hlc_transfer_model(C.byref(f)))
+    names = ("h2d", "d2h")
+    out = {}
+    for k, nm in enumerate(names):
+        out[nm] = {"alpha_s": f.alpha_s[k], "beta_s_per_byte": f.beta_s_per_byte[k],
+                   "gbs": f.gbs[k],
+                   "check": [{"bytes": int(f.check_bytes[i]),
+                              "measured_s": f.check_measured_s[k][i],
+                              "model_s": f.check_model_s[k][i]} for i in range(4)]}
+    return out
+
+
+def hlc_autotune(jobs, sample_jobs: int = 256, precision: int = HLC_FP32_GUARD, stream=None):
+    """Time the batched form's candidate order targets and tile shapes on a
+    sample of these jobs (same job dicts as hlc_plan_batched).  Returns the
+    best Tune (to pass as hlc_plan_batched(..., tune=)) and the report."""
+    _require_cuda()
+    n, ca, cb, params, keep, _ = _batched_args(jobs, precision, True, stream, False, None)
+    rep = TuneReport()
+    _check(lib().hlc_autotune(ca, cb, params, n, int(sample_jobs), C.byref(rep)))
+    best = Tune()
+    C.pointer(best)[0] = rep.best
+    trials = [dict(rep.trials[i].tune.as_dict(), ms=rep.trials[i].ms)
+              for i in range(rep.n_trials)]
+    return best, {"best": rep.best.as_dict(), "ms_rule": rep.ms_rule, "ms_best": rep.ms_best,
+                  "sample_jobs": rep.sample_jobs, "trials": trials}
+
+
+def hlc_plan_batched(jobs, precision: int = HLC_FP32_GUARD, want_sep: bool = True,
+                     stream=None, torch_alloc: bool = False, tune: Tune | None = None) -> Plan:
+    """One plan over many independent jobs.  jobs: sequence of dicts with keys
+    A, B ((ra, dec, id) triples or catalogue objects), radius_arcsec and
+    fine_level (-1 = chosen by the library from the job's density).  tune:
+    a Tune from hlc_autotune (None: the library's rule)."""
+    _require_cuda()
+    L = lib()
+    n, cats_a, cats_b, params, keep, alloc = _batched_args(jobs, precision, want_sep, stream,
+                                                           torch_alloc, tune)
     h = C.c_void_p()
     _check(L.hlc_plan(cats_a, cats_b, params, n, C.byref(h)))
-    return Plan(h, params[0], alloc, (keep, cats_a, cats_b, params))
+    return Plan(h, params[0], alloc, (keep, cats_a, cats_b, params, tune))
 
 
 def _triple(X):
@@ -393,12 +480,13 @@ def hlc_neighbours(pix: torch.Tensor, order: int, stream=None) -> torch.Tensor:
 
 
 def hlc_quad_cells(ra, dec, radius_arcsec: float, order: int, precision: int = HLC_FP64,
-                   stream=None):
+                   stream=None, boundary: int = HLC_QUAD):
     _require_cuda()
     out = torch.empty((ra.numel(), 5), dtype=torch.int32, device=ra.device)
     cnt = torch.empty(ra.numel(), dtype=torch.int32, device=ra.device)
     _check(lib().hlc_quad_cells(_dptr(ra), _dptr(dec), ra.numel(), float(radius_arcsec),
-                                int(order), int(precision), _dptr(out) if out.numel() else None,
+                                int(order), int(precision), int(boundary),
+                                _dptr(out) if out.numel() else None,
                                 _dptr(cnt) if cnt.numel() else None, _stream_ptr(stream)))
     return out, cnt
 

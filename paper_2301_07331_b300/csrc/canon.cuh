@@ -67,6 +67,21 @@ __device__ __forceinline__ void c_sincos_deg(double x, double* s, double* c) {
   *c = rc;
 }
 
+// Eq. 4 (Sec. 2.1): the radius of a pair with error radii e1, e2 (arcsec),
+// 3 sqrt(e1^2 + e2^2), in the fixed order a = e1 e1, b = e2 e2, t = a + b,
+// r = 3 sqrt(t), symmetric in the two errors.
+__device__ __forceinline__ double c_pair_radius(double e1, double e2) {
+  const double a = __dmul_rn(e1, e1), b = __dmul_rn(e2, e2);
+  return __dmul_rn(3.0, __dsqrt_rn(__dadd_rn(a, b)));
+}
+
+// Squared-chord threshold 4 sin^2(r/2) of a radius r in arcsec.
+__device__ __forceinline__ double c_threshold(double r_arcsec) {
+  double s, c;
+  c_sincos_deg(__ddiv_rn(r_arcsec, 7200.0), &s, &c);
+  return __dmul_rn(4.0, __dmul_rn(s, s));
+}
+
 __device__ __forceinline__ double c_norm_ra(double ra) {
   if (ra >= 0.0 && ra < 360.0) return ra;  // fmod would return it unchanged
   double a = fmod(ra, 360.0);
@@ -314,8 +329,21 @@ __device__ __forceinline__ double wrap_ra(double x) {
 }
 
 // Distinct pixels of the source and its four shifted copies, ascending.
+// RA shift of the cos(Dec) quad variant: R / cos(dec) with the canonical
+// cosine, at most 180 deg (and 180 where the cosine is 0).
+__device__ __forceinline__ double c_ra_shift_cos(double R, double dec) {
+  double s, c;
+  c_sincos_deg(dec, &s, &c);
+  c = fabs(c);
+  double RA = c > 0.0 ? __ddiv_rn(R, c) : 180.0;
+  if (RA > 180.0) RA = 180.0;
+  return RA;
+}
+
+// cosdec: the RA copies are shifted by c_ra_shift_cos(R, dec) instead of R.
 __device__ __forceinline__ int c_quad_cells(double ra, double dec, double R, int order,
-                                            uint32_t out[5]) {
+                                            uint32_t out[5], bool cosdec = false) {
+  const double RA = cosdec ? c_ra_shift_cos(R, dec) : R;
   double dp_ = __dadd_rn(dec, R);
   if (dp_ > 90.0) dp_ = 90.0;
   double dm_ = __dsub_rn(dec, R);
@@ -323,8 +351,8 @@ __device__ __forceinline__ int c_quad_cells(double ra, double dec, double R, int
   DecPart d0 = c_dec_part(dec);
   uint32_t p[5];
   p[0] = c_pix(ra, d0, order);
-  p[1] = c_pix(wrap_ra(__dadd_rn(ra, R)), d0, order);
-  p[2] = c_pix(wrap_ra(__dsub_rn(ra, R)), d0, order);
+  p[1] = c_pix(wrap_ra(__dadd_rn(ra, RA)), d0, order);
+  p[2] = c_pix(wrap_ra(__dsub_rn(ra, RA)), d0, order);
   p[3] = c_ang2pix(ra, dm_, order);
   p[4] = c_ang2pix(ra, dp_, order);
   // sort five values (insertion), then drop repeats

@@ -142,17 +142,20 @@ __device__ __forceinline__ uint32_t g_ang2pix(double ra, double dec, int order,
 // a shifted RA whose leading float is not in [0, 360) (a wrap at the RA = 0
 // face boundary) is left undecided.  Writes the pixel of every decided
 // position to p[0..4] and returns the mask of the undecided ones.
-__device__ __forceinline__ unsigned g_quad_pos(double ra, double dec, f2 Rd, int order,
+// (Ra: the RA shift, Rd itself or the cos(Dec) variant's binary64 shift
+// split into float-float.)
+__device__ __forceinline__ unsigned g_quad_pos(double ra, double dec, f2 Rd, f2 Ra, int order,
                                                const PixConst& K, uint32_t p[5]) {
   const f2 r0 = split_f64(ra), d0 = split_f64(dec);
   const f2 Rn = {-Rd.hi, -Rd.lo};
+  const f2 Ran = {-Ra.hi, -Ra.lo};
   f2 dp = f2_add(d0, Rd);
   if (dp.hi > 90.f || (dp.hi == 90.f && dp.lo > 0.f)) dp = f2{90.f, 0.f};
   f2 dm = f2_add(d0, Rn);
   if (dm.hi < -90.f || (dm.hi == -90.f && dm.lo < 0.f)) dm = f2{-90.f, 0.f};
-  f2 rp = f2_add(r0, Rd);
+  f2 rp = f2_add(r0, Ra);
   if (rp.hi > 360.f || (rp.hi == 360.f && rp.lo >= 0.f)) rp = f2_add(rp, f2{-360.f, 0.f});
-  f2 rm = f2_add(r0, Rn);
+  f2 rm = f2_add(r0, Ran);
   if (rm.hi < 0.f || (rm.hi == 0.f && rm.lo < 0.f)) rm = f2_add(rm, f2{360.f, 0.f});
   const FastDec f0 = f_dec_part(d0), fm = f_dec_part(dm), fp = f_dec_part(dp);
   unsigned und = 0;

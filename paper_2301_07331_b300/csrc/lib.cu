@@ -187,6 +187,7 @@ struct CatDev {
   uint32_t* key = nullptr;   // sorted cell keys of the entries
   uint32_t* idx = nullptr;   // source of each sorted entry
   double *vx = nullptr, *vy = nullptr, *vz = nullptr;
+  double* ve = nullptr;        // Eq. 4, binary64 form: entry-ordered error radii
   float4* v32 = nullptr;
   double2* rd = nullptr;       // entry-ordered (ra, dec) (batched plans)
   uint64_t* id_s = nullptr;    // entry-ordered ids (batched plans)
@@ -291,7 +292,7 @@ struct PinnedBuf {
 
 enum Ctr { C_ROWS = 0, C_BAND, C_TESTS, C_DUPS, C_M, C_TOTAL, C_HEADS_A, C_HEADS_B, C_DENSE,
            C_WORK, C_IDDIFF, C_MAXB, C_SLOW, C_LHITS, C_LLOOK, C_LMAXERR, C_SCRATCH, C_BAND64,
-           C_SLOW_A, C_N };
+           C_SLOW_A, C_EMAXA, C_EMAXB, C_N };
 
 }  // namespace hlc
 
@@ -303,6 +304,13 @@ struct hlc_plan_s {
   hlc::CatDev A, B;
   double C = 0;
   double r_lo = 0, r_hi = 0;  // separations left to the binary64 recheck
+  bool eq4 = false;           // per-source radii (Eq. 4)
+  // tile kernel shape (the rule, or a batched plan's hlc_tune)
+  uint32_t tile_ka[3] = {hlc::kTileRuleKA[0], hlc::kTileRuleKA[1], hlc::kTileRuleKA[2]};
+  uint32_t tile_stage = hlc::kTileCap;
+  double target_per_cell = 0;  // batched order rule (0: kTargetPerCell)
+  double k9 = 0;              // 9 (pi/648000)^2: squared pair radius per squared error
+  double eq4_rmax = 0;        // largest pair radius (arcsec)
   float lo32 = 0, hi32 = 0;
   int join_level = 0;
   int nslot = 9;
@@ -351,7 +359,12 @@ static int validate_params(const hlc_params* p) {
     set_error("params is NULL");
     return HLC_EINVAL;
   }
-  if (!(p->radius_arcsec > 0.0) || !(p->radius_arcsec <= 648000.0)) {
+  if (p->radius_rule != HLC_RADIUS_FIXED && p->radius_rule != HLC_RADIUS_EQ4) {
+    set_error("radius_rule must be HLC_RADIUS_FIXED or HLC_RADIUS_EQ4");
+    return HLC_EINVAL;
+  }
+  const bool eq4 = p->radius_rule == HLC_RADIUS_EQ4;
+  if (!eq4 && (!(p->radius_arcsec > 0.0) || !(p->radius_arcsec <= 648000.0))) {
     set_error("radius_arcsec must be in (0, 648000], got %g", p->radius_arcsec);
     return HLC_EINVAL;
   }
@@ -363,8 +376,9 @@ static int validate_params(const hlc_params* p) {
     set_error("coarse_level must be in [0, fine_level], got %d", p->coarse_level);
     return HLC_EINVAL;
   }
-  if (p->boundary != HLC_COMPLETE8 && p->boundary != HLC_QUAD) {
-    set_error("boundary must be HLC_COMPLETE8 or HLC_QUAD");
+  if (p->boundary != HLC_COMPLETE8 && p->boundary != HLC_QUAD &&
+      p->boundary != HLC_QUAD_COSDEC) {
+    set_error("boundary must be HLC_COMPLETE8, HLC_QUAD or HLC_QUAD_COSDEC");
     return HLC_EINVAL;
   }
   if (p->precision != HLC_FP64 && p->precision != HLC_FP32_GUARD) {
@@ -379,10 +393,26 @@ static int validate_params(const hlc_params* p) {
     set_error("model must be HLC_MODEL_PLA or HLC_MODEL_MLP");
     return HLC_EINVAL;
   }
-  if (p->boundary == HLC_COMPLETE8 && p->radius_arcsec > complete_max_radius(p->fine_level)) {
+  if (!eq4 && p->boundary == HLC_COMPLETE8 &&
+      p->radius_arcsec > complete_max_radius(p->fine_level)) {
     set_error("radius %g arcsec exceeds theta_L/8 = %g arcsec at fine_level %d (complete mode)",
               p->radius_arcsec, complete_max_radius(p->fine_level), p->fine_level);
     return HLC_EINVAL;
+  }
+  if (eq4 && (p->boundary != HLC_COMPLETE8 || p->index != HLC_INDEX_BSEARCH)) {
+    set_error("HLC_RADIUS_EQ4 is implemented for complete mode with the binary-searched index");
+    return HLC_EUNSUPPORTED;
+  }
+  if (p->tune) {
+    const hlc_tune& t = *p->tune;
+    bool ok = t.target_per_cell > 0.0 && t.target_per_cell <= 1e6 && t.stage >= 8 &&
+              t.stage <= (uint32_t)kTileCap && t.stage % 8 == 0;
+    for (int c = 0; c < 3; ++c) ok = ok && (t.ka[c] == 1 || t.ka[c] == 2 || t.ka[c] == 4);
+    if (!ok) {
+      set_error("tune: target_per_cell must be > 0, ka in {1, 2, 4}, stage a multiple of 8 in "
+                "[8, %d]", kTileCap);
+      return HLC_EINVAL;
+    }
   }
   if ((p->alloc == nullptr) != (p->dealloc == nullptr)) {
     set_error("alloc and dealloc must both be set or both be NULL");
@@ -599,7 +629,8 @@ static int dense_fixup(hlc_plan_t* P, CatDev& X, const uint32_t* T, int shift, b
 // B, is grouped by B's table cells and gets fine order (and tile-kernel work
 // items) where B's table cells are dense.
 static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
-                          const double* dec, const uint64_t* id, cudaEvent_t ev[4]) {
+                          const double* dec, const uint64_t* id, const double* perr,
+                          cudaEvent_t ev[4]) {
   Arena& ar = *P->arena;
   cudaStream_t st = plan_stream(P);
   const int L = P->p.fine_level;
@@ -617,7 +648,8 @@ static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
     if (!slow) return HLC_ENOMEM;
     HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st));
     k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-        ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, slow, P->ctr + C_SLOW, P->dev_err);
+        ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, slow, P->ctr + C_SLOW, P->dev_err,
+        P->eq4 ? perr : nullptr);
     HLC_LAUNCH_CHECK();
     k_prep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key);
     HLC_LAUNCH_CHECK();
@@ -647,8 +679,9 @@ static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
   }
   HLC_ALLOC(ar, X.v32, float4, n + 1);
   if (n) {
-    k_payload32<<<grid_for(n, kThreads), kThreads, 0, st>>>(X.rec, X.idx, n, X.v32,
-                                                            is_b ? nullptr : P->ctr + C_IDDIFF);
+    k_payload32<<<grid_for(n, kThreads), kThreads, 0, st>>>(
+        X.rec, X.idx, n, X.v32, is_b ? nullptr : P->ctr + C_IDDIFF,
+        P->eq4 ? (is_b ? -1.f : 1.f) : 0.f, P->k9);
     HLC_LAUNCH_CHECK();
   }
   cudaEventRecord(ev[2], st);
@@ -715,7 +748,7 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
   if (na) {
     k_prep_keys<true><<<grid_for(na, kThreads), kThreads, 0, ks>>>(
         inA->ra_deg, inA->dec_deg, inA->id, na, L, pix_const(L), XA.key, XA.idx, XA.rec, slow_a,
-        P->ctr + C_SLOW_A, P->dev_err);
+        P->ctr + C_SLOW_A, P->dev_err, P->eq4 ? inA->err_arcsec : nullptr);
     HLC_LAUNCH_CHECK();
     k_prep_fallback<<<num_sms() * 4u, kThreads, 0, ks>>>(inA->ra_deg, inA->dec_deg, L, slow_a,
                                                   P->ctr + C_SLOW_A, XA.key);
@@ -725,7 +758,7 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
   if (nb) {
     k_prep_keys<true><<<grid_for(nb, kThreads), kThreads, 0, st>>>(
         inB->ra_deg, inB->dec_deg, inB->id, nb, L, pix_const(L), XB.key, XB.idx, XB.rec, slow_b,
-        P->ctr + C_SLOW, P->dev_err);
+        P->ctr + C_SLOW, P->dev_err, P->eq4 ? inB->err_arcsec : nullptr);
     HLC_LAUNCH_CHECK();
     k_prep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(inB->ra_deg, inB->dec_deg, L, slow_b,
                                                   P->ctr + C_SLOW, XB.key);
@@ -773,15 +806,15 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
   // 3. the payloads side by side (A's on ks), then B's offset table and dense cells
   HLC_CUDA(cudaStreamWaitEvent(ks, e_sorted, 0));
   if (na) {
-    k_payload32<<<grid_for(na, kThreads), kThreads, 0, ks>>>(XA.rec, XA.idx, na, XA.v32,
-                                                             P->ctr + C_IDDIFF);
+    k_payload32<<<grid_for(na, kThreads), kThreads, 0, ks>>>(
+        XA.rec, XA.idx, na, XA.v32, P->ctr + C_IDDIFF, P->eq4 ? 1.f : 0.f, P->k9);
     HLC_LAUNCH_CHECK();
   }
   HLC_CUDA(cudaEventRecord(ea[2], ks));
   HLC_ALLOC(ar, XB.v32, float4, nb + 1);
   if (nb) {
-    k_payload32<<<grid_for(nb, kThreads), kThreads, 0, st>>>(XB.rec, XB.idx, nb, XB.v32,
-                                                             nullptr);
+    k_payload32<<<grid_for(nb, kThreads), kThreads, 0, st>>>(
+        XB.rec, XB.idx, nb, XB.v32, nullptr, P->eq4 ? -1.f : 0.f, P->k9);
     HLC_LAUNCH_CHECK();
   }
   HLC_CUDA(cudaEventRecord(eb[2], st));
@@ -806,7 +839,7 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
   Arena& ar = *P->arena;
   cudaStream_t st = plan_stream(P);
   const int L = P->p.fine_level;
-  const bool quad = P->p.boundary == HLC_QUAD;
+  const bool quad = P->p.boundary != HLC_COMPLETE8;
   const bool fp32 = P->p.precision == HLC_FP32_GUARD;
   X.n = in->n;
   uint64_t n = X.n;
@@ -815,29 +848,34 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
   const double* ra = in->ra_deg;
   const double* dec = in->dec_deg;
   const uint64_t* id = in->id;
-  double *tra = nullptr, *tdec = nullptr;
+  const double* perr = P->eq4 ? in->err_arcsec : nullptr;
+  double *tra = nullptr, *tdec = nullptr, *terr = nullptr;
   uint64_t* tid = nullptr;
   if (!in->on_device) {
     HLC_ALLOC(ar, tra, double, n + 1);
     HLC_ALLOC(ar, tdec, double, n + 1);
     HLC_ALLOC(ar, tid, uint64_t, n + 1);
+    if (perr) HLC_ALLOC(ar, terr, double, n + 1);
     if (n) {
       HLC_CUDA(cudaMemcpyAsync(tra, in->ra_deg, n * 8, cudaMemcpyHostToDevice, st));
       HLC_CUDA(cudaMemcpyAsync(tdec, in->dec_deg, n * 8, cudaMemcpyHostToDevice, st));
       HLC_CUDA(cudaMemcpyAsync(tid, in->id, n * 8, cudaMemcpyHostToDevice, st));
+      if (perr) HLC_CUDA(cudaMemcpyAsync(terr, perr, n * 8, cudaMemcpyHostToDevice, st));
     }
     ra = tra;
     dec = tdec;
     id = tid;
+    if (perr) perr = terr;
   }
   cudaEventRecord(ev[0], st);
   HLC_ALLOC(ar, X.rec, SrcRec, n + 1);
   if (P->table_buckets) {
-    HLC_TRY(bucket_catalog(P, X, is_b, ra, dec, id, ev));
+    HLC_TRY(bucket_catalog(P, X, is_b, ra, dec, id, perr, ev));
     if (tra) {
       ar.drop(tra);
       ar.drop(tdec);
       ar.drop(tid);
+      if (terr) ar.drop(terr);
     }
     cudaEventRecord(ev[3], st);
     return HLC_OK;
@@ -860,7 +898,8 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
         ar.drop(slow);
       } else {
         k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, nullptr, nullptr, P->dev_err);
+            ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, nullptr, nullptr, P->dev_err,
+            perr);
         HLC_LAUNCH_CHECK();
       }
     }
@@ -872,22 +911,23 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     if (!cnt || !off || !scr) return HLC_ENOMEM;
     if (n) {
       const double R = P->p.radius_arcsec / 3600.0;
+      const bool cosdec = P->p.boundary == HLC_QUAD_COSDEC;
       if (fp32) {
         uint32_t* slow = ar.get_n<uint32_t>(n + 1);
         if (!slow) return HLC_ENOMEM;
         HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st));
         k_quad_cells<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
             ra, dec, id, n, R, L, pix_const(L), X.cells5, cnt, X.rec, slow, P->ctr + C_SLOW,
-            P->dev_err);
+            P->dev_err, cosdec);
         HLC_LAUNCH_CHECK();
         k_quad_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(ra, dec, R, L, slow, P->ctr + C_SLOW,
-                                                      X.cells5, cnt);
+                                                      X.cells5, cnt, cosdec);
         HLC_LAUNCH_CHECK();
         ar.drop(slow);
       } else {
         k_quad_cells<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
             ra, dec, id, n, R, L, pix_const(L), X.cells5, cnt, X.rec, nullptr, nullptr,
-            P->dev_err);
+            P->dev_err, cosdec);
         HLC_LAUNCH_CHECK();
       }
     }
@@ -925,8 +965,10 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     HLC_ALLOC(ar, X.vx, double, m + 1);
     HLC_ALLOC(ar, X.vy, double, m + 1);
     HLC_ALLOC(ar, X.vz, double, m + 1);
+    if (P->eq4) HLC_ALLOC(ar, X.ve, double, m + 1);
     if (m) {
-      k_payload64<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.rec, X.idx, m, X.vx, X.vy, X.vz);
+      k_payload64<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.rec, X.idx, m, X.vx, X.vy, X.vz,
+                                                              X.ve);
       HLC_LAUNCH_CHECK();
     }
   } else {
@@ -940,6 +982,7 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     ar.drop(tra);
     ar.drop(tdec);
     ar.drop(tid);
+    if (terr) ar.drop(terr);
   }
   unsigned long long* heads = P->ctr + (is_b ? C_HEADS_B : C_HEADS_A);
   if (is_b && P->p.index == HLC_INDEX_LEARNED) {
@@ -976,6 +1019,82 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
   return HLC_OK;
 }
 
+// Eq. 4 pair radius on the host, in the same operation order as the device
+// (c_pair_radius): a = e1 e1, b = e2 e2, t = a + b, r = 3 sqrt(t).
+static double host_pair_radius(double e1, double e2) {
+  volatile double a = e1 * e1;
+  volatile double b = e2 * e2;
+  volatile double t = a + b;
+  return 3.0 * std::sqrt((double)t);
+}
+
+// Eq. 4 set-up of a plan: the largest error radius of each catalogue (device
+// columns reduced on the device, host columns on the host; every value must
+// be finite and >= 0), the largest pair radius, which complete mode needs
+// within theta_L/8, and the FP32 band around s - (rho_a + rho_b).
+static int eq4_setup(hlc_plan_t* P, const hlc_catalog* A, const hlc_catalog* B) {
+  cudaStream_t st = plan_stream(P);
+  const hlc_catalog* X[2] = {A, B};
+  double emax[2] = {0.0, 0.0};
+  bool dev_any = false;
+  for (int i = 0; i < 2; ++i) {
+    if (X[i]->n && !X[i]->err_arcsec) {
+      set_error("HLC_RADIUS_EQ4: catalogue %s has no err_arcsec column", i ? "B" : "A");
+      return HLC_EINVAL;
+    }
+    if (!X[i]->n) continue;
+    if (X[i]->on_device) {
+      dev_any = true;
+      k_err_max<<<grid_for(X[i]->n, kThreads, num_sms() * 8u), kThreads, 0, st>>>(
+          X[i]->err_arcsec, X[i]->n, P->ctr + (i ? C_EMAXB : C_EMAXA), P->dev_err);
+      HLC_LAUNCH_CHECK();
+    } else {
+      for (uint64_t k = 0; k < X[i]->n; ++k) {
+        const double v = X[i]->err_arcsec[k];
+        if (!(v >= 0.0) || !std::isfinite(v)) {
+          set_error("HLC_RADIUS_EQ4: catalogue %s error radius %llu is %g (must be finite "
+                    "and >= 0)", i ? "B" : "A", (unsigned long long)k, v);
+          return HLC_EINVAL;
+        }
+        emax[i] = std::max(emax[i], v);
+      }
+    }
+  }
+  if (dev_any) {
+    unsigned long long hm[2] = {0, 0};
+    HLC_CUDA(cudaMemcpyAsync(hm, P->ctr + C_EMAXA, 16, cudaMemcpyDeviceToHost, st));
+    int rc = check_dev_err(P->dev_err, st, "hlc_plan");
+    if (rc == HLC_EINVAL) {
+      set_error("HLC_RADIUS_EQ4: an error radius is not finite or is negative");
+      return rc;
+    }
+    HLC_TRY(rc);
+    for (int i = 0; i < 2; ++i)
+      if (X[i]->on_device) memcpy(&emax[i], &hm[i], 8);
+  }
+  const double pi = 3.14159265358979323846;
+  P->eq4_rmax = host_pair_radius(emax[0], emax[1]);
+  const int L = P->p.fine_level;
+  if (P->eq4_rmax > complete_max_radius(L)) {
+    set_error("HLC_RADIUS_EQ4: the largest pair radius 3 sqrt(%g^2 + %g^2) = %g arcsec exceeds "
+              "theta_L/8 = %g arcsec at fine_level %d", emax[0], emax[1], P->eq4_rmax,
+              complete_max_radius(L), L);
+    return HLC_EINVAL;
+  }
+  P->k9 = 9.0 * (pi / 648000.0) * (pi / 648000.0);
+  P->C = chord2_threshold(P->eq4_rmax);
+  // the single-radius band at the largest threshold, plus the roundings of
+  // rho_a, rho_b and their sum (3 half-ulps of C) and 4 sin^2(x/2) = x^2 -
+  // x^4/12 + ... against x^2 = rho_a + rho_b
+  const double u = 1.0 / 16777216.0;
+  const double G = fp32_guard_band(P->C, kUnitVecErr) + 4.0 * u * P->C + 1.1 * P->C * P->C / 12.0;
+  P->lo32 = (float)(-G);
+  P->hi32 = (float)G;
+  if ((double)P->lo32 > -G) P->lo32 = nextafterf(P->lo32, -1e30f);
+  if ((double)P->hi32 < G) P->hi32 = nextafterf(P->hi32, 1e30f);
+  return HLC_OK;
+}
+
 static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_params* p,
                        hlc_plan_t** out) {
   HLC_TRY(validate_params(p));
@@ -991,18 +1110,25 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   P->arena = new Arena(P->al);
   P->out = new Arena(P->al);
   P->join_level = p->fine_level;
-  P->nslot = p->boundary == HLC_QUAD ? 1 : 9;
+  P->nslot = p->boundary != HLC_COMPLETE8 ? 1 : 9;
   P->table_buckets = p->boundary == HLC_COMPLETE8 && p->precision == HLC_FP32_GUARD &&
                      p->index != HLC_INDEX_LEARNED;
-  P->C = chord2_threshold(p->radius_arcsec);
-  f2_sep_window(p->radius_arcsec, &P->r_lo, &P->r_hi);
-  double G = fp32_guard_band(P->C, kUnitVecErr);
-  P->lo32 = (float)(P->C - G);
-  P->hi32 = (float)(P->C + G);
-  // make the float thresholds conservative
-  if ((double)P->lo32 > P->C - G) P->lo32 = nextafterf(P->lo32, 0.0f);
-  if ((double)P->hi32 < P->C + G) P->hi32 = nextafterf(P->hi32, 1e30f);
-  if (P->lo32 < 0) P->lo32 = -1.0f;
+  if (p->tune) {
+    for (int c = 0; c < 3; ++c) P->tile_ka[c] = p->tune->ka[c];
+    P->tile_stage = p->tune->stage;
+  }
+  P->eq4 = p->radius_rule == HLC_RADIUS_EQ4;
+  if (!P->eq4) {
+    P->C = chord2_threshold(p->radius_arcsec);
+    f2_sep_window(p->radius_arcsec, &P->r_lo, &P->r_hi);
+    double G = fp32_guard_band(P->C, kUnitVecErr);
+    P->lo32 = (float)(P->C - G);
+    P->hi32 = (float)(P->C + G);
+    // make the float thresholds conservative
+    if ((double)P->lo32 > P->C - G) P->lo32 = nextafterf(P->lo32, 0.0f);
+    if ((double)P->hi32 < P->C + G) P->hi32 = nextafterf(P->hi32, 1e30f);
+    if (P->lo32 < 0) P->lo32 = -1.0f;
+  }
   for (int i = 0; i < 12; ++i) cudaEventCreate(&P->ev[i]);
   P->events = true;
   auto fail = [&](int rc) {
@@ -1020,6 +1146,10 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   }
   ev_record(P, 0);
   P->launches0 = g_launches.load();
+  if (P->eq4) {
+    const int rc = eq4_setup(P, A, B);
+    if (rc != HLC_OK) return fail(rc);
+  }
   cudaEvent_t ea[4], eb[4];
   for (int i = 0; i < 4; ++i) {
     cudaEventCreate(&ea[i]);
@@ -1031,7 +1161,8 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   // host inputs: both catalogues are copied in on a side stream in build
   // order, so that building the first overlaps the copy of the second
   hlc_catalog dv[2] = {*first, *second};
-  void* stage[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  void* stage[2][4] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
+  const int ncol = P->eq4 ? 4 : 3;  // ra, dec, id (+ Eq. 4 error radius)
   cudaStream_t cs = nullptr;
   cudaEvent_t cev[3] = {nullptr, nullptr, nullptr};
   int rc = HLC_OK;
@@ -1042,7 +1173,7 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
     for (int i = 0; i < 2 && rc == HLC_OK; ++i) {
       if (dv[i].on_device) continue;
       const uint64_t n = dv[i].n;
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < ncol; ++k) {
         stage[i][k] = P->arena->get((n + 1) * 8);
         if (!stage[i][k]) rc = HLC_ENOMEM;
       }
@@ -1058,7 +1189,9 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
             cudaMemcpyAsync(stage[i][1], dv[i].dec_deg, n * 8, cudaMemcpyHostToDevice, cs) !=
                 cudaSuccess ||
             cudaMemcpyAsync(stage[i][2], dv[i].id, n * 8, cudaMemcpyHostToDevice, cs) !=
-                cudaSuccess)
+                cudaSuccess ||
+            (ncol == 4 && cudaMemcpyAsync(stage[i][3], dv[i].err_arcsec, n * 8,
+                                          cudaMemcpyHostToDevice, cs) != cudaSuccess))
           rc = HLC_ECUDA;
       }
       if (rc == HLC_OK && cudaEventRecord(cev[i], cs) != cudaSuccess) rc = HLC_ECUDA;
@@ -1066,6 +1199,7 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
         dv[i].ra_deg = (const double*)stage[i][0];
         dv[i].dec_deg = (const double*)stage[i][1];
         dv[i].id = (const uint64_t*)stage[i][2];
+        if (ncol == 4) dv[i].err_arcsec = (const double*)stage[i][3];
         dv[i].on_device = 1;
       }
     }
@@ -1115,7 +1249,7 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
     for (int i = 0; i < 3; ++i)
       if (cev[i]) cudaEventDestroy(cev[i]);
     for (int i = 0; i < 2; ++i)
-      for (int k = 0; k < 3; ++k)
+      for (int k = 0; k < 4; ++k)
         if (stage[i][k]) P->arena->drop(stage[i][k]);
   }
   if (rc == HLC_OK && P->A.n && !P->table_buckets) {
@@ -1292,7 +1426,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   CatDev& A = P->A;
   CatDev& B = P->B;
   const bool fp32 = P->p.precision == HLC_FP32_GUARD;
-  const bool quad = P->p.boundary == HLC_QUAD;
+  const bool quad = P->p.boundary != HLC_COMPLETE8;
   const unsigned long long launches_match0 = g_launches.load();
   HLC_CUDA(cudaMemsetAsync(P->dev_err, 0, 64, st));
   ev_record(P, 2);
@@ -1340,10 +1474,17 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
       pa.lhits = P->ctr + C_LHITS;
       pa.llook = P->ctr + C_LLOOK;
       pa.tiled = A.tiled;
+      pa.aev = A.ve;
+      pa.bev = B.ve;
+      pa.k9 = P->k9;
       const bool learned = P->p.index == HLC_INDEX_LEARNED;
 #define HLC_PAIR(F, Q, LR) k_pair<F, Q, LR, false><<<grid, kThreads, 0, st>>>(pa, sink)
-      if (P->table_buckets) {
+      if (P->table_buckets && P->eq4) {
+        k_pair<true, false, false, true, true><<<grid, kThreads, 0, st>>>(pa, sink);
+      } else if (P->table_buckets) {
         k_pair<true, false, false, true><<<grid, kThreads, 0, st>>>(pa, sink);
+      } else if (P->eq4) {  // (binary64, complete mode, binary-searched index)
+        k_pair<false, false, false, false, true><<<grid, kThreads, 0, st>>>(pa, sink);
       } else if (fp32 && quad) {
         if (learned) HLC_PAIR(true, true, true); else HLC_PAIR(true, true, false);
       } else if (fp32) {
@@ -1369,10 +1510,18 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
         ta.lo32 = P->lo32;
         ta.hi32 = P->hi32;
         ta.sparse_cell = P->sparse_cell;
+        for (int c = 0; c < 3; ++c) ta.ka[c] = P->tile_ka[c];
+        ta.stage = P->tile_stage;
         const int smem = 2 * kTileCap * 16;
-        HLC_CUDA(cudaFuncSetAttribute(k_pair_tile,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        k_pair_tile<<<num_sms() * 3u, kTileThreads + 32, smem, st>>>(ta, sink);
+        if (P->eq4) {
+          HLC_CUDA(cudaFuncSetAttribute(k_pair_tile<true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+          k_pair_tile<true><<<num_sms() * 3u, kTileThreads + 32, smem, st>>>(ta, sink);
+        } else {
+          HLC_CUDA(cudaFuncSetAttribute(k_pair_tile<false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+          k_pair_tile<false><<<num_sms() * 3u, kTileThreads + 32, smem, st>>>(ta, sink);
+        }
         HLC_LAUNCH_CHECK();
       }
     }
@@ -1394,10 +1543,18 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   ev_record(P, 4);
   if (fp32 && h[C_BAND]) {
     // (the table-cell form's rows already hold source indices)
-    k_recheck<<<grid_for(h[C_BAND], kThreads, num_sms() * 16u), kThreads, 0, st>>>(
-        band, P->ctr + C_BAND, bcap, P->table_buckets ? nullptr : A.idx,
-        P->table_buckets ? nullptr : B.idx, A.rec, B.rec, P->C, P->r_lo, P->r_hi, rows,
-        P->ctr + C_ROWS, cap, P->ctr + C_BAND64, P->dev_err);
+    const unsigned rg = grid_for(h[C_BAND], kThreads, num_sms() * 16u);
+    const uint32_t* ia = P->table_buckets ? nullptr : A.idx;
+    const uint32_t* ib = P->table_buckets ? nullptr : B.idx;
+    if (P->eq4)
+      k_recheck<true><<<rg, kThreads, 0, st>>>(band, P->ctr + C_BAND, bcap, ia, ib, A.rec, B.rec,
+                                               P->C, P->r_lo, P->r_hi, rows, P->ctr + C_ROWS,
+                                               cap, P->ctr + C_BAND64, P->dev_err);
+    else
+      k_recheck<false><<<rg, kThreads, 0, st>>>(band, P->ctr + C_BAND, bcap, ia, ib, A.rec,
+                                                B.rec, P->C, P->r_lo, P->r_hi, rows,
+                                                P->ctr + C_ROWS, cap, P->ctr + C_BAND64,
+                                                P->dev_err);
     HLC_LAUNCH_CHECK();
   }
   ev_record(P, 5);
@@ -1491,11 +1648,11 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
 // sources per cell, no finer than the completeness limit r <= theta_L / 8.
 constexpr double kTargetPerCell = 2.0;
 
-static int auto_order(double nb, double cap_one_minus_cos, double r_arcsec) {
+static int auto_order(double nb, double cap_one_minus_cos, double r_arcsec, double target) {
   const double pi = 3.14159265358979323846;
   double area = 2.0 * pi * std::max(cap_one_minus_cos, 1e-12);  // sr
   double density = std::max(nb, 1.0) / area;
-  double cells = 4.0 * pi * density / (12.0 * kTargetPerCell);  // 4^L
+  double cells = 4.0 * pi * density / (12.0 * target);  // 4^L
   int L = cells > 1.0 ? (int)std::floor(std::log(cells) / std::log(4.0) + 0.5) : 0;
   int Lmax = 0;
   while (Lmax < 14 && r_arcsec <= complete_max_radius(Lmax + 1)) ++Lmax;
@@ -1516,9 +1673,10 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
       return HLC_EUNSUPPORTED;
     }
     if (p[j].precision != p[0].precision || p[j].stream != p[0].stream ||
-        p[j].want_sep != p[0].want_sep || p[j].alloc != p[0].alloc) {
-      set_error("all jobs of a batched plan must share precision, stream, want_sep and "
-                "allocator");
+        p[j].want_sep != p[0].want_sep || p[j].alloc != p[0].alloc ||
+        p[j].tune != p[0].tune) {
+      set_error("all jobs of a batched plan must share precision, stream, want_sep, "
+                "allocator and tune");
       return HLC_EINVAL;
     }
     if (A[j].on_device != A[0].on_device || B[j].on_device != A[0].on_device) {
@@ -1540,6 +1698,11 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
   P->al.stream = (cudaStream_t)p[0].stream;
   P->arena = new Arena(P->al);
   P->out = new Arena(P->al);
+  if (p[0].tune) {
+    for (int c = 0; c < 3; ++c) P->tile_ka[c] = p[0].tune->ka[c];
+    P->tile_stage = p[0].tune->stage;
+    P->target_per_cell = p[0].tune->target_per_cell;
+  }
   for (int i = 0; i < 12; ++i) cudaEventCreate(&P->ev[i]);
   P->events = true;
   auto fail = [&](int rc) {
@@ -1661,7 +1824,8 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
       if (p[j].fine_level >= 0) continue;
       float om;
       memcpy(&om, &hc[j], 4);
-      J[j].L = auto_order((double)B[j].n, (double)om, p[j].radius_arcsec);
+      J[j].L = auto_order((double)B[j].n, (double)om, p[j].radius_arcsec,
+                          P->target_per_cell > 0 ? P->target_per_cell : kTargetPerCell);
     }
   } else {
     for (uint32_t j = 0; j < njobs; ++j)
@@ -1917,7 +2081,7 @@ static int batched_pair_graph(hlc_plan_t* P, uint2* rows, uint64_t cap, uint2* b
   cudaStream_t cs;
   HLC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   const int tile_smem = 2 * kTileCap * 16;
-  HLC_CUDA(cudaFuncSetAttribute(k_pair_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  HLC_CUDA(cudaFuncSetAttribute(k_pair_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tile_smem));
   cudaGraph_t g;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
@@ -1957,7 +2121,9 @@ static int batched_pair_graph(hlc_plan_t* P, uint2* rows, uint64_t cap, uint2* b
         ta.btable = P->btable;
         ta.jobs = P->jobs_d;
         ta.cell_bits = P->cell_bits;
-        k_pair_tile<<<num_sms() * 3u, kTileThreads + 32, tile_smem, cs>>>(ta, sink);
+        for (int c = 0; c < 3; ++c) ta.ka[c] = P->tile_ka[c];
+        ta.stage = P->tile_stage;
+        k_pair_tile<false><<<num_sms() * 3u, kTileThreads + 32, tile_smem, cs>>>(ta, sink);
       }
     }
     e = cudaStreamEndCapture(cs, &g);
@@ -2141,13 +2307,115 @@ struct HostRows {  // one group's sorted rows, in a pooled pinned block
   size_t n = 0;
 };
 
+// ---------------------------------------------------------------------------
+// Transfer-cost model (Sec. 4.1.1, Eq. 5): a copy of d bytes takes
+// T(d) = alpha + beta d.  alpha: the time of a one-byte copy; beta: (t_s -
+// alpha) / s from a large copy of s bytes (pinned host memory).
+// ---------------------------------------------------------------------------
+struct TransferFit {
+  double a[2] = {0, 0}, b[2] = {0, 0};  // [0] host to device, [1] device to host
+  bool ok = false;
+  double predict(int dir, uint64_t bytes, uint64_t copies) const {
+    return a[dir] * (double)copies + b[dir] * (double)bytes;
+  }
+};
+
+static int measure_transfer(TransferFit* fit, hlc_transfer_fit* detail) {
+  const size_t S = (size_t)256 << 20;
+  void* h = nullptr;
+  void* d = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = HLC_OK;
+  if (cudaHostAlloc(&h, S, cudaHostAllocDefault) != cudaSuccess || cudaMalloc(&d, S) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("transfer model: allocation of the 256 MiB probe buffers failed");
+    rc = HLC_ENOMEM;
+  }
+  // median time (s) of `reps` copies of `bytes` in direction dir
+  auto time_copy = [&](int dir, size_t bytes, int reps, double* out) -> int {
+    std::vector<double> t;
+    for (int k = 0; k < reps + 1; ++k) {  // (the first copy warms up)
+      cudaEventRecord(e0, st);
+      cudaError_t e = dir == 0 ? cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st)
+                               : cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, st);
+      cudaEventRecord(e1, st);
+      if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        set_error("transfer model: a probe copy failed");
+        return HLC_ECUDA;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (k) t.push_back(ms * 1e-3);
+    }
+    std::sort(t.begin(), t.end());
+    *out = t[t.size() / 2];
+    return HLC_OK;
+  };
+  static const uint64_t kCheck[4] = {64u << 10, 1u << 20, 16u << 20, 64u << 20};
+  for (int dir = 0; dir < 2 && rc == HLC_OK; ++dir) {
+    double alpha = 0, ts = 0;
+    rc = time_copy(dir, 1, 21, &alpha);
+    if (rc == HLC_OK) rc = time_copy(dir, S, 5, &ts);
+    if (rc != HLC_OK) break;
+    fit->a[dir] = alpha;
+    fit->b[dir] = (ts - alpha) / (double)S;
+    if (detail) {
+      detail->alpha_s[dir] = alpha;
+      detail->beta_s_per_byte[dir] = fit->b[dir];
+      detail->gbs[dir] = fit->b[dir] > 0 ? 1e-9 / fit->b[dir] : 0.0;
+      for (int i = 0; i < 4 && rc == HLC_OK; ++i) {
+        detail->check_bytes[i] = kCheck[i];
+        rc = time_copy(dir, kCheck[i], 5, &detail->check_measured_s[dir][i]);
+        detail->check_model_s[dir][i] = fit->predict(dir, kCheck[i], 1);
+      }
+    }
+  }
+  fit->ok = rc == HLC_OK && fit->b[0] > 0 && fit->b[1] > 0;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  if (d) cudaFree(d);
+  if (h) cudaFreeHost(h);
+  return rc;
+}
+
+static std::mutex g_fit_mu;
+static TransferFit g_fit[64];
+
+// The current device's fit, measured on first use and kept.
+static int transfer_fit(TransferFit* out) {
+  int dev = 0;
+  HLC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal %d out of range", dev);
+    return HLC_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(g_fit_mu);
+  if (!g_fit[dev].ok) HLC_TRY(measure_transfer(&g_fit[dev], nullptr));
+  *out = g_fit[dev];
+  return HLC_OK;
+}
+
+// Sources per streamed chunk: the smallest multiple of 2^20 (24 bytes each
+// in three copies) whose copies spend at most 1% of their time in alpha,
+// at most kStreamChunk.
+static uint64_t chunk_from_fit(const TransferFit& f) {
+  const double a = f.a[0], b = f.b[0];
+  double need = b > 0 ? 100.0 * 3.0 * a / (b * 24.0) : (double)kStreamChunk;
+  uint64_t c = ((uint64_t)std::ceil(need / (double)(1u << 20))) << 20;
+  return std::max<uint64_t>(1u << 20, std::min<uint64_t>(c, kStreamChunk));
+}
+
 // Streams one host catalogue through the device in chunks on two streams,
 // running `fn(chunk ra, dec, id, n, stream)` on each.  Pinned inputs are
 // copied directly; pageable ones through two pinned staging buffers.
 template <typename Fn>
 static int stream_catalog(const hlc_catalog* X, double* dra[2], double* ddec[2], uint64_t* did[2],
                           void* stage[2], cudaStream_t ss[2], cudaEvent_t done[2], float* ms_h2d,
-                          Fn fn) {
+                          uint64_t chunk, uint64_t led[4], Fn fn) {
   cudaPointerAttributes at;
   bool pinned = X->n && cudaPointerGetAttributes(&at, X->ra_deg) == cudaSuccess &&
                 at.type == cudaMemoryTypeHost;
@@ -2159,12 +2427,12 @@ static int stream_catalog(const hlc_catalog* X, double* dra[2], double* ddec[2],
              cudaPointerGetAttributes(&a3, X->id) == cudaSuccess && a3.type == cudaMemoryTypeHost;
     cudaGetLastError();
   }
-  uint64_t nchunks = (X->n + kStreamChunk - 1) / kStreamChunk;
+  uint64_t nchunks = (X->n + chunk - 1) / chunk;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tev;  // H2D spans, read at the end
   for (uint64_t c = 0; c < nchunks; ++c) {
     int b = (int)(c & 1);
-    uint64_t o = c * kStreamChunk;
-    uint64_t n = std::min(kStreamChunk, X->n - o);
+    uint64_t o = c * chunk;
+    uint64_t n = std::min(chunk, X->n - o);
     // the buffer of this parity is free once its previous chunk is done
     HLC_CUDA(cudaEventSynchronize(done[b]));
     const double* sra = X->ra_deg + o;
@@ -2173,11 +2441,11 @@ static int stream_catalog(const hlc_catalog* X, double* dra[2], double* ddec[2],
     if (!pinned) {
       char* h = (char*)stage[b];
       memcpy(h, sra, n * 8);
-      memcpy(h + kStreamChunk * 8, sdec, n * 8);
-      memcpy(h + kStreamChunk * 16, sid, n * 8);
+      memcpy(h + chunk * 8, sdec, n * 8);
+      memcpy(h + chunk * 16, sid, n * 8);
       sra = (const double*)h;
-      sdec = (const double*)(h + kStreamChunk * 8);
-      sid = (const uint64_t*)(h + kStreamChunk * 16);
+      sdec = (const double*)(h + chunk * 8);
+      sid = (const uint64_t*)(h + chunk * 16);
     }
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
@@ -2187,6 +2455,8 @@ static int stream_catalog(const hlc_catalog* X, double* dra[2], double* ddec[2],
     HLC_CUDA(cudaMemcpyAsync(dra[b], sra, n * 8, cudaMemcpyHostToDevice, ss[b]));
     HLC_CUDA(cudaMemcpyAsync(ddec[b], sdec, n * 8, cudaMemcpyHostToDevice, ss[b]));
     HLC_CUDA(cudaMemcpyAsync(did[b], sid, n * 8, cudaMemcpyHostToDevice, ss[b]));
+    led[0] += 3 * n * 8;  // (the transfer ledger: bytes and copies host to device)
+    led[1] += 3;
     cudaEventRecord(t1, ss[b]);
     HLC_TRY(fn(dra[b], ddec[b], did[b], n, ss[b], c, b));
     HLC_CUDA(cudaEventRecord(done[b], ss[b]));
@@ -2339,6 +2609,15 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
   cudaStream_t st = plan_stream(P);
   Arena& ar = *P->arena;
   const int Lf = p->fine_level, Lc = p->coarse_level;
+  // the transfer-cost model of Eq. 5 (measured once per device): chunk size,
+  // and every copy below goes into the ledger it predicts the time of
+  TransferFit fit;
+  {
+    const int frc = transfer_fit(&fit);
+    if (frc != HLC_OK) return fail(frc);
+  }
+  const uint64_t chunk = chunk_from_fit(fit);
+  uint64_t led[4] = {0, 0, 0, 0};  // bytes and copies host to device, device to host
   const uint64_t nparts = 12ull << (2 * Lc);
   const PixConst K = pix_const(Lf);
   cudaEvent_t e0, e1;
@@ -2349,9 +2628,9 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
   double *dra[2], *ddec[2];
   uint64_t* did[2];
   for (int b = 0; b < 2; ++b) {
-    dra[b] = ar.get_n<double>(kStreamChunk);
-    ddec[b] = ar.get_n<double>(kStreamChunk);
-    did[b] = ar.get_n<uint64_t>(kStreamChunk);
+    dra[b] = ar.get_n<double>(chunk);
+    ddec[b] = ar.get_n<double>(chunk);
+    did[b] = ar.get_n<uint64_t>(chunk);
     if (!dra[b] || !ddec[b] || !did[b]) return fail(HLC_ENOMEM);
   }
   unsigned long long* counts = ar.get_n<unsigned long long>(2 * nparts);
@@ -2378,7 +2657,7 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
     cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming);
     cudaEventRecord(done[b], ss[b]);
     if (need_stage &&
-        cudaHostAlloc(&stage[b], kStreamChunk * 24, cudaHostAllocDefault) != cudaSuccess) {
+        cudaHostAlloc(&stage[b], chunk * 24, cudaHostAllocDefault) != cudaSuccess) {
       cudaGetLastError();
       set_error("pinned staging allocation failed");
       return fail(HLC_ENOMEM);
@@ -2407,7 +2686,7 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
   for (int side = 0; side < 2 && rc == HLC_OK; ++side) {
     const hlc_catalog* X = side ? B : A;
     unsigned long long* cnt = counts + side * nparts;
-    rc = stream_catalog(X, dra, ddec, did, stage, ss, done, &ms_h2d,
+    rc = stream_catalog(X, dra, ddec, did, stage, ss, done, &ms_h2d, chunk, led,
                         [&](double* r, double* d, uint64_t* id, uint64_t n, cudaStream_t s,
                             uint64_t, int) {
                           (void)id;
@@ -2431,7 +2710,7 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
   tw = wall();
   // groups of consecutive coarse cells that fit the budget
   uint64_t budget = p->device_mem_budget;
-  uint64_t fixed = 6 * kStreamChunk * 8 + 2 * nparts * 8 + (64ull << 20);
+  uint64_t fixed = 6 * chunk * 8 + 2 * nparts * 8 + (64ull << 20);
   uint64_t cap_entries =
       std::max<uint64_t>(4096, (budget > fixed ? budget - fixed : budget) / kStreamBytesPerEntry);
   std::vector<std::pair<uint32_t, uint32_t>> groups;
@@ -2476,7 +2755,7 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
     gcur[b] = ar.get_n<uint32_t>(ngroups + 1);
     goff[b] = ar.get_n<uint32_t>(ngroups + 1);
     // group-ordered chunk (grown when a chunk's B halo needs more)
-    bcap[b] = std::max<uint64_t>(1024, std::min<uint64_t>(kStreamChunk,
+    bcap[b] = std::max<uint64_t>(1024, std::min<uint64_t>(chunk,
                                                          std::max(A->n, B->n)) * 5 / 4);
     bra[b] = ar.get_n<double>(bcap[b]);
     bdec[b] = ar.get_n<double>(bcap[b]);
@@ -2541,7 +2820,7 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
     const hlc_catalog* X = side ? B : A;
     uint64_t filled = 0;
     rc = stream_catalog(
-        X, dra, ddec, did, stage, ss, done, &ms_h2d,
+        X, dra, ddec, did, stage, ss, done, &ms_h2d, chunk, led,
         [&](double* r, double* d, uint64_t* id, uint64_t n, cudaStream_t s, uint64_t c,
             int b) {
           HLC_CUDA(cudaMemsetAsync(gcnt[b], 0, (ngroups + 1) * 4, s));
@@ -2553,6 +2832,8 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
           HLC_LAUNCH_CHECK();
           uint32_t* hg = hgoff_pin + b * (ngroups + 1);
           HLC_CUDA(cudaMemcpyAsync(hg, goff[b], (ngroups + 1) * 4, cudaMemcpyDeviceToHost, s));
+          led[2] += (ngroups + 1) * 4;
+          led[3] += 1;
           HLC_CUDA(cudaStreamSynchronize(s));
           const uint64_t tot = hg[ngroups];
           if (filled + tot > hcap[side]) {
@@ -2583,6 +2864,8 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
                                      cudaMemcpyDeviceToHost, s));
             HLC_CUDA(cudaMemcpyAsync(hid[side] + filled, bid[b], tot * 8, cudaMemcpyDeviceToHost,
                                      s));
+            led[2] += 3 * tot * 8;
+            led[3] += 3;
           }
           filled += tot;
           (void)c;
@@ -2632,6 +2915,8 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
             cudaMemcpyAsync(gid[side] + o, hid[side] + s0, len * 8, cudaMemcpyHostToDevice, st) !=
                 cudaSuccess)
           rc = HLC_ECUDA;
+        led[0] += 3 * len * 8;
+        led[1] += 3;
         o += len;
       }
       cudaEventRecord(t1, st);
@@ -2673,6 +2958,8 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
             (r.sep_arcsec && cudaMemcpyAsync(h.buf.p + 2 * rb, r.sep_arcsec, rb,
                                              cudaMemcpyDeviceToHost, st) != cudaSuccess))
           rc = HLC_ECUDA;
+        led[2] += (r.sep_arcsec ? 3 : 2) * rb;
+        led[3] += r.sep_arcsec ? 3 : 2;
         cudaEventRecord(d1, st);
         cudaStreamSynchronize(st);
         float ms = 0;
@@ -2740,6 +3027,13 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
   agg.matches = M;
   agg.join_level = Lf;
   agg.ms_h2d = ms_h2d;
+  agg.h2d_bytes = led[0];
+  agg.h2d_copies = led[1];
+  agg.d2h_bytes = led[2];
+  agg.d2h_copies = led[3];
+  agg.ms_model_h2d = (float)(fit.predict(0, led[0], led[1]) * 1e3);
+  agg.ms_model_d2h = (float)(fit.predict(1, led[2], led[3]) * 1e3);
+  agg.stream_chunk = chunk;
   agg.ms_total = total;
   agg.ms_stream_count = w_count;
   agg.ms_stream_bucket = w_bucket;
@@ -2799,11 +3093,24 @@ int hlc_plan(const hlc_catalog* A, const hlc_catalog* B, const hlc_params* p, ui
     set_error("A, B or params is NULL");
     return HLC_EINVAL;
   }
-  if (n_jobs > 1) return plan_batched(A, B, p, n_jobs, out);
+  if (n_jobs > 1) {
+    for (uint32_t j = 0; j < n_jobs; ++j)
+      if (p[j].radius_rule != HLC_RADIUS_FIXED) {
+        set_error("job %u: batched plans take one radius per job (HLC_RADIUS_FIXED)", j);
+        return HLC_EUNSUPPORTED;
+      }
+    return plan_batched(A, B, p, n_jobs, out);
+  }
   if (p->device_mem_budget && !A->on_device && !B->on_device) {
     // stream by coarse partition when the in-core footprint exceeds the budget
     uint64_t need = (A->n + B->n) * kStreamBytesPerEntry;
-    if (need > p->device_mem_budget) return plan_streamed(A, B, p, out);
+    if (need > p->device_mem_budget) {
+      if (p->radius_rule != HLC_RADIUS_FIXED) {
+        set_error("streamed plans take one radius (HLC_RADIUS_FIXED)");
+        return HLC_EUNSUPPORTED;
+      }
+      return plan_streamed(A, B, p, out);
+    }
   }
   return plan_single(A, B, p, out);
 }
@@ -2954,14 +3261,17 @@ int hlc_neighbours(const uint32_t* pix, uint64_t n, int order, int64_t* out, voi
 }
 
 int hlc_quad_cells(const double* ra, const double* dec, uint64_t n, double radius_arcsec,
-                   int order, int precision, uint32_t* out, int32_t* count, void* stream) {
+                   int order, int precision, int boundary, uint32_t* out, int32_t* count,
+                   void* stream) {
   clear_error();
   if (order < 0 || order > 14 || !(radius_arcsec > 0.0) || !(radius_arcsec <= 648000.0) ||
-      (precision != HLC_FP64 && precision != HLC_FP32_GUARD)) {
-    set_error("order must be in [0, 14], radius in (0, 648000] and precision HLC_FP64 or "
-              "HLC_FP32_GUARD");
+      (precision != HLC_FP64 && precision != HLC_FP32_GUARD) ||
+      (boundary != HLC_QUAD && boundary != HLC_QUAD_COSDEC)) {
+    set_error("order must be in [0, 14], radius in (0, 648000], precision HLC_FP64 or "
+              "HLC_FP32_GUARD and boundary HLC_QUAD or HLC_QUAD_COSDEC");
     return HLC_EINVAL;
   }
+  const bool cosdec = boundary == HLC_QUAD_COSDEC;
   if (n == 0) return HLC_OK;
   if (!ra || !dec || !out || !count) {
     set_error("NULL array");
@@ -2984,15 +3294,15 @@ int hlc_quad_cells(const double* ra, const double* dec, uint64_t n, double radiu
     }
     k_quad_cells<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
         ra, dec, nullptr, n, R, order, pix_const(order), out, (uint32_t*)count, nullptr, slow,
-        nslow, err);
+        nslow, err, cosdec);
     k_quad_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(ra, dec, R, order, slow, nslow, out,
-                                                  (uint32_t*)count);
+                                                  (uint32_t*)count, cosdec);
     rc = cudaGetLastError() == cudaSuccess ? HLC_OK : HLC_ECUDA;
     cudaFreeAsync(slow, st);
   } else {
     k_quad_cells<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
         ra, dec, nullptr, n, R, order, pix_const(order), out, (uint32_t*)count, nullptr, nullptr,
-        nullptr, err);
+        nullptr, err, cosdec);
     rc = cudaGetLastError() == cudaSuccess ? HLC_OK : HLC_ECUDA;
   }
   if (rc == HLC_OK) rc = check_dev_err(err, st, "hlc_quad_cells");
@@ -3170,6 +3480,135 @@ int hlc_learned_lookup(const uint32_t* uniq, uint64_t m, int shift, int model,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner of the batched form: times candidate order targets and tile
+// shapes on a sample of the caller's jobs (coordinate descent from the rule).
+// ---------------------------------------------------------------------------
+extern "C" int hlc_transfer_model(hlc_transfer_fit* out) {
+  clear_error();
+  if (!out) {
+    set_error("hlc_transfer_model: out is NULL");
+    return HLC_EINVAL;
+  }
+  int dev = 0;
+  HLC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal %d out of range", dev);
+    return HLC_EUNSUPPORTED;
+  }
+  hlc_transfer_fit d;
+  memset(&d, 0, sizeof(d));
+  TransferFit f;
+  HLC_TRY(measure_transfer(&f, &d));
+  {
+    std::lock_guard<std::mutex> lk(g_fit_mu);
+    g_fit[dev] = f;  // later streamed plans use the newest fit
+  }
+  *out = d;
+  return HLC_OK;
+}
+
+extern "C" int hlc_autotune(const hlc_catalog* A, const hlc_catalog* B, const hlc_params* p,
+                            uint32_t n_jobs, uint32_t sample_jobs, hlc_tune_report* report) {
+  clear_error();
+  if (!A || !B || !p || !report || n_jobs == 0 || sample_jobs == 0) {
+    set_error("hlc_autotune: NULL argument, n_jobs = 0 or sample_jobs = 0");
+    return HLC_EINVAL;
+  }
+  // the sample: jobs ordered by B size, picked at even steps of that order
+  std::vector<uint32_t> ord(n_jobs);
+  for (uint32_t j = 0; j < n_jobs; ++j) ord[j] = j;
+  std::stable_sort(ord.begin(), ord.end(),
+                   [&](uint32_t a, uint32_t b) { return B[a].n < B[b].n; });
+  const uint32_t m = std::min(n_jobs, sample_jobs);
+  std::vector<hlc_catalog> sa(m), sb(m);
+  std::vector<hlc_params> sp(m);
+  for (uint32_t k = 0; k < m; ++k) {
+    const uint32_t j = ord[(uint64_t)k * n_jobs / m];
+    sa[k] = A[j];
+    sb[k] = B[j];
+    sp[k] = p[j];
+  }
+  hlc_tune_report R;
+  memset(&R, 0, sizeof(R));
+  R.sample_jobs = m;
+  // device time of one plan + match of the sample with tune t (best of reps)
+  auto timed_n = [&](const hlc_tune& t, int reps, float* ms) -> int {
+    for (uint32_t k = 0; k < m; ++k) sp[k].tune = &t;
+    float best = 1e30f;
+    for (int rep = 0; rep < reps; ++rep) {
+      hlc_plan_t* P = nullptr;
+      int rc = plan_batched(sa.data(), sb.data(), sp.data(), m, &P);
+      if (rc != HLC_OK) return rc;
+      hlc_result r;
+      hlc_stats st;
+      rc = hlc_match(P, &r, &st);
+      hlc_free(P);
+      if (rc != HLC_OK) return rc;
+      best = std::min(best, st.ms_total);
+    }
+    *ms = best;
+    return HLC_OK;
+  };
+  auto timed = [&](const hlc_tune& t, float* ms) -> int {
+    HLC_TRY(timed_n(t, 3, ms));
+    if (R.n_trials < 32) R.trials[R.n_trials++] = hlc_tune_trial{t, *ms};
+    return HLC_OK;
+  };
+  const hlc_tune rule{kTargetPerCell, {kTileRuleKA[0], kTileRuleKA[1], kTileRuleKA[2]},
+                      (uint32_t)kTileCap};
+  hlc_tune cur = rule;
+  float tcur = 0;
+  HLC_TRY(timed(cur, &tcur));
+  auto consider = [&](const hlc_tune& c) -> int {
+    float t = 0;
+    HLC_TRY(timed(c, &t));
+    if (t < 0.97f * tcur) {
+      cur = c;
+      tcur = t;
+    }
+    return HLC_OK;
+  };
+  for (double T : {0.5, 1.0, 4.0, 8.0}) {
+    hlc_tune c = cur;
+    c.target_per_cell = T;
+    HLC_TRY(consider(c));
+  }
+  for (int cls = 0; cls < 3; ++cls)
+    for (uint32_t ka : {1u, 2u, 4u}) {
+      if (ka == cur.ka[cls]) continue;
+      hlc_tune c = cur;
+      c.ka[cls] = ka;
+      HLC_TRY(consider(c));
+    }
+  for (uint32_t stg : {384u, 768u, 1536u}) {
+    if (stg == cur.stage) continue;
+    hlc_tune c = cur;
+    c.stage = stg;
+    HLC_TRY(consider(c));
+  }
+  // the winner against the rule, interleaved, best of four each: it is kept
+  // only when at least 2% faster (timing noise on a busy GPU is ~2%)
+  float tr = 1e30f, tb = 1e30f;
+  for (int k = 0; k < 4; ++k) {
+    float a = 0, b = 0;
+    HLC_TRY(timed_n(rule, 1, &a));
+    HLC_TRY(timed_n(cur, 1, &b));
+    tr = std::min(tr, a);
+    tb = std::min(tb, b);
+  }
+  R.ms_rule = tr;
+  if (tb < 0.98f * tr) {
+    R.best = cur;
+    R.ms_best = tb;
+  } else {
+    R.best = rule;
+    R.ms_best = tr;
+  }
+  *report = R;
+  return HLC_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Test hooks: shortened spin limits, and each kind of bounded device wait run

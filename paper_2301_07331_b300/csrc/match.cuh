@@ -20,8 +20,38 @@ constexpr int kThreads = 256;
 // index touch a single sector.
 struct __align__(32) SrcRec {
   double ra, dec;
-  uint64_t id, pad;
+  uint64_t id, pad;  // pad: the bits of the source's Eq. 4 error radius (or 0)
 };
+
+__device__ __forceinline__ double rec_err(const SrcRec& r) {
+  return __longlong_as_double((long long)r.pad);
+}
+
+// Largest per-source error radius of a column (Eq. 4), as the bits of a
+// non-negative double (whose integer order is the numeric order); a value
+// that is not finite or is negative flags invalid input.
+__global__ void k_err_max(const double* __restrict__ e, uint64_t n,
+                          unsigned long long* __restrict__ out, int* __restrict__ err) {
+  unsigned long long m = 0;
+  bool bad = false;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    double v = e[i];
+    if (!(v >= 0.0) || !(v <= 1.7976931348623157e308)) {
+      bad = true;
+      continue;
+    }
+    if (v == 0.0) v = 0.0;  // -0 has the sign bit set
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    m = b > m ? b : m;
+  }
+  if (bad) atomicOr(err, DERR_INPUT);
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_down_sync(0xffffffffu, m, o);
+    m = y > m ? y : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
 // Number of B entries in a table cell up to which the FP32 join uses the
 // table order (sparse regions).
 constexpr int kPairUnroll = 4;  // candidates per lane per pair-test iteration
@@ -44,7 +74,8 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
                             const uint64_t* __restrict__ id, uint64_t n, int order, PixConst K,
                             uint32_t* __restrict__ key, uint32_t* __restrict__ idx,
                             SrcRec* __restrict__ rec, uint32_t* __restrict__ slow,
-                            unsigned long long* __restrict__ nslow, int* __restrict__ err) {
+                            unsigned long long* __restrict__ nslow, int* __restrict__ err,
+                            const double* __restrict__ perr = nullptr) {
   for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n;
        i0 += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t i = i0 + threadIdx.x;
@@ -76,7 +107,7 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
         r.ra = a;
         r.dec = d;
         r.id = id[i];
-        r.pad = 0;
+        r.pad = perr ? (uint64_t)__double_as_longlong(perr[i]) : 0ull;  // Eq. 4 error radius
         rec[i] = r;
       }
     }
@@ -107,16 +138,18 @@ __global__ void k_prep_fallback(const double* __restrict__ ra, const double* __r
 }
 
 // Quad-direction cells of each source (Algorithm 1): 5 slots + count.
-// (FAST: no FP64 instruction on the way; a source with an undecided position
-// keeps its decided pixels in its cells row, the mask of the undecided ones
-// in count, and is queued for k_quad_fallback.)
+// (FAST: no FP64 instruction on the way, except the cosine of the cos(Dec)
+// variant; a source with an undecided position keeps its decided pixels in
+// its cells row, the mask of the undecided ones in count, and is queued for
+// k_quad_fallback.)  cosdec: the RA copies are shifted by R / cos(dec)
+// (c_ra_shift_cos), the variant beside Algorithm 1's literal R.
 template <bool FAST>
 __global__ void k_quad_cells(const double* __restrict__ ra, const double* __restrict__ dec,
                              const uint64_t* __restrict__ id, uint64_t n, double R, int order,
                              PixConst K, uint32_t* __restrict__ cells,
                              uint32_t* __restrict__ count, SrcRec* __restrict__ rec,
                              uint32_t* __restrict__ slow, unsigned long long* __restrict__ nslow,
-                             int* __restrict__ err) {
+                             int* __restrict__ err, bool cosdec = false) {
   const f2 Rd = split_f64(R);
   for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n;
        i0 += (uint64_t)gridDim.x * blockDim.x) {
@@ -133,7 +166,8 @@ __global__ void k_quad_cells(const double* __restrict__ ra, const double* __rest
       } else if (FAST) {
         if (!bits_in_ra_range(a)) a = c_norm_ra(a);
         uint32_t p[5] = {0u, 0u, 0u, 0u, 0u};
-        const unsigned und = g_quad_pos(a, d, Rd, order, K, p);
+        const f2 Ra = cosdec ? split_f64(c_ra_shift_cos(R, d)) : Rd;
+        const unsigned und = g_quad_pos(a, d, Rd, Ra, order, K, p);
         if (und) {
           defer = true;
 #pragma unroll
@@ -144,7 +178,7 @@ __global__ void k_quad_cells(const double* __restrict__ ra, const double* __rest
         }
       } else {
         a = c_norm_ra(a);
-        m = c_quad_cells(a, d, R, order, c);
+        m = c_quad_cells(a, d, R, order, c, cosdec);
       }
 #pragma unroll
       for (int e = 0; e < 5; ++e) cells[5 * i + e] = (defer || e < m) ? c[e] : 0xFFFFFFFFu;
@@ -180,7 +214,7 @@ __global__ void k_quad_cells(const double* __restrict__ ra, const double* __rest
 __global__ void __launch_bounds__(kThreads) k_quad_fallback(
     const double* __restrict__ ra, const double* __restrict__ dec, double R, int order,
     const uint32_t* __restrict__ slow, const unsigned long long* __restrict__ nslow,
-    uint32_t* __restrict__ cells, uint32_t* __restrict__ count) {
+    uint32_t* __restrict__ cells, uint32_t* __restrict__ count, bool cosdec = false) {
   __shared__ uint8_t s_pair[kThreads / 32][160];   // (lane << 3) | position
   __shared__ uint32_t s_pix[kThreads / 32][160];   // [lane * 5 + position]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -212,10 +246,9 @@ __global__ void __launch_bounds__(kThreads) k_quad_fallback(
       const double sd = __shfl_sync(0xffffffffu, d, src);
       if (act) {
         double pa = sa, pd = sd;
-        if (e == 1) {
-          pa = wrap_ra(__dadd_rn(sa, R));
-        } else if (e == 2) {
-          pa = wrap_ra(__dsub_rn(sa, R));
+        if (e == 1 || e == 2) {
+          const double RA = cosdec ? c_ra_shift_cos(R, sd) : R;
+          pa = wrap_ra(e == 1 ? __dadd_rn(sa, RA) : __dsub_rn(sa, RA));
         } else if (e == 3) {
           pd = __dsub_rn(sd, R);
           if (pd < -90.0) pd = -90.0;
@@ -257,9 +290,10 @@ __global__ void k_quad_emit(const uint32_t* __restrict__ cells, const uint32_t* 
 }
 
 // Sorted payload: binary64 canonical unit vectors (plain form).
+// (ve, when given: the entries' Eq. 4 error radii.)
 __global__ void k_payload64(const SrcRec* __restrict__ rec, const uint32_t* __restrict__ idx,
                             uint64_t m, double* __restrict__ vx, double* __restrict__ vy,
-                            double* __restrict__ vz) {
+                            double* __restrict__ vz, double* __restrict__ ve = nullptr) {
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
        e += (uint64_t)gridDim.x * blockDim.x) {
     SrcRec r = rec[idx[e]];
@@ -268,6 +302,7 @@ __global__ void k_payload64(const SrcRec* __restrict__ rec, const uint32_t* __re
     vx[e] = x;
     vy[e] = y;
     vz[e] = z;
+    if (ve) ve[e] = rec_err(r);
   }
 }
 
@@ -275,9 +310,13 @@ __global__ void k_payload64(const SrcRec* __restrict__ rec, const uint32_t* __re
 // bound, in entry order.
 // (iddiff, when given, receives the OR of id ^ id of source 0 over all
 // entries: the bits in which the ids differ, for the output bucketing.)
+// Eq. 4: w = wsign * rho with rho = k9 e^2, k9 = 9 (pi/648000)^2, the
+// source's share of the pair's squared radius in radians (+rho for A, -rho
+// for B, so that b.w - a.w = -(rho_a + rho_b)); otherwise w = 0.
 __global__ void k_payload32(const SrcRec* __restrict__ rec, const uint32_t* __restrict__ idx,
                             uint64_t m, float4* __restrict__ v,
-                            unsigned long long* __restrict__ iddiff) {
+                            unsigned long long* __restrict__ iddiff, float wsign = 0.f,
+                            double k9 = 0.0) {
   const uint64_t id0 = (iddiff && m) ? rec[0].id : 0;
   unsigned long long acc = 0;
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
@@ -285,6 +324,10 @@ __global__ void k_payload32(const SrcRec* __restrict__ rec, const uint32_t* __re
     SrcRec r = rec[idx[e]];
     float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
     if (bits_finite(r.ra) && bits_abs_le(r.dec, 90.0)) u = fp32_unitvec(r.ra, r.dec);
+    if (wsign != 0.f) {
+      const double er = rec_err(r);
+      u.w = wsign * (float)(er * er * k9);
+    }
     v[e] = u;
     acc |= r.id ^ id0;
   }
@@ -407,11 +450,20 @@ struct PairArgs {
   uint32_t sparse_cell;
   unsigned long long *lhits, *llook;
   const uint8_t* tiled;   // (BUCKET) A entries taken by the tile kernel, or null
+  // Eq. 4 (EQ4): binary64 form: the entries' error radii and 9 (pi/648000)^2
+  const double *aev, *bev;
+  double k9;
 };
 
 // BUCKET: B is bucketed by table cell (ordered by fine key only inside dense
 // table cells); a sparse table cell is read whole, once per A entry.
-template <bool FP32, bool QUAD, bool LEARNED, bool BUCKET>
+// EQ4: each pair has its own radius (Eq. 4).  FP32: the vectors' w carry
+// +rho_a / -rho_b, the tested value is s - (rho_a + rho_b) and lo32 / hi32
+// are -G / +G around 0.  Binary64: a pair whose s exceeds the bound
+// x^2 = 9 (pi/648000)^2 (e_a^2 + e_b^2) >= 4 sin^2(r_ij/2) (with a 1e-12
+// margin for rounding) is rejected, the rest are decided against the
+// canonical 4 sin^2(r_ij/2).
+template <bool FP32, bool QUAD, bool LEARNED, bool BUCKET, bool EQ4 = false>
 __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink sink) {
   const uint64_t mA = pa.mA;
   const uint32_t* __restrict__ keyA = pa.keyA;
@@ -446,13 +498,14 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
     bool live = k < mA;
     if (BUCKET && pa.tiled && live && pa.tiled[k]) live = false;  // the tile kernel's
     uint32_t cell = live ? keyA[k] : 0u;
-    double ax = 0, ay = 0, az = 0;
+    double ax = 0, ay = 0, az = 0, ae = 0;
     float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (live) {
       if (FP32) {
         a4 = a32[k];
       } else {
         ax = axv[k]; ay = ayv[k]; az = azv[k];
+        if (EQ4) ae = pa.aev[k];
       }
     }
     // neighbourhood of the A cell (complete) or the cell itself (quad).  In
@@ -560,7 +613,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           float dx = a4.x - bb[u].x, dy = a4.y - bb[u].y, dz = a4.z - bb[u].z;
-          float s2 = dx * dx;
+          float s2 = EQ4 ? fmaf(dx, dx, bb[u].w - a4.w) : dx * dx;
           s2 = fmaf(dy, dy, s2);
           s2 = fmaf(dz, dz, s2);
           hit[u] = act[u] && s2 <= lo32;
@@ -575,10 +628,19 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
           by[u] = act[u] ? byv[jj[u]] : ay;
           bz[u] = act[u] ? bzv[jj[u]] : az;
         }
+        double be[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) be[u] = (EQ4 && act[u]) ? pa.bev[jj[u]] : 0.0;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           double s2 = c_chord2(ax, ay, az, bx[u], by[u], bz[u]);
-          hit[u] = act[u] && s2 <= C;
+          if (EQ4) {
+            const double x2 = (ae * ae + be[u] * be[u]) * pa.k9;
+            hit[u] = act[u] && s2 <= x2 * (1.0 + 1e-12) &&
+                     s2 <= c_threshold(c_pair_radius(ae, be[u]));
+          } else {
+            hit[u] = act[u] && s2 <= C;
+          }
           band[u] = false;
           anyv |= hit[u];
         }
@@ -636,6 +698,9 @@ __global__ void __launch_bounds__(kThreads) k_pair(const PairArgs pa, PairSink s
 // where it is certain (f2_sep_decide); the rest take the binary64 test with
 // both vectors recomputed in the canonical arithmetic from the original
 // coordinates (counted in n64).
+// EQ4: each pair's radius r_ij from the two records' error radii (Eq. 4),
+// its own window [r_ij - m, r_ij + m] and threshold 4 sin^2(r_ij/2).
+template <bool EQ4>
 __global__ void __launch_bounds__(kThreads) k_recheck(
     const uint2* __restrict__ band, const unsigned long long* __restrict__ nband_dev,
     uint64_t band_cap, const uint32_t* __restrict__ idxA, const uint32_t* __restrict__ idxB,
@@ -652,7 +717,15 @@ __global__ void __launch_bounds__(kThreads) k_recheck(
     if (q < nb) {
       p = band[q];  // entry indices, or source indices when idxA/idxB are null
       SrcRec a = recA[idxA ? idxA[p.x] : p.x], b = recB[idxB ? idxB[p.y] : p.y];
-      const int d = f2_sep_decide(a.ra, a.dec, b.ra, b.dec, r_lo, r_hi);
+      double lo = r_lo, hi = r_hi, Cp = C;
+      if (EQ4) {
+        const double r = c_pair_radius(rec_err(a), rec_err(b));
+        const double m = kSepRel * r + kSepAbs;
+        lo = r - m;
+        hi = r + m;
+        Cp = c_threshold(r);
+      }
+      const int d = f2_sep_decide(a.ra, a.dec, b.ra, b.dec, lo, hi);
       if (d != 0) {
         hit = d > 0;
       } else {
@@ -660,7 +733,7 @@ __global__ void __launch_bounds__(kThreads) k_recheck(
         double ax, ay, az, bx, by, bz;
         c_unitvec(a.ra, a.dec, &ax, &ay, &az);
         c_unitvec(b.ra, b.dec, &bx, &by, &bz);
-        hit = c_chord2(ax, ay, az, bx, by, bz) <= C;
+        hit = c_chord2(ax, ay, az, bx, by, bz) <= Cp;
       }
     }
     warp_emit(hit, p.x, p.y, rows, count, cap, err);

@@ -23,11 +23,12 @@
 // of a group in a bit mask; the warp walks them (a ballot per step) only when
 // one lane has any.
 //
-// Tile shape per cell (the density rule): KA, the A sources per lane, is the
-// smallest of 1, 2, 4 that covers the cell's A sources in one pass of the 32
-// lanes (4 beyond 64 sources), which keeps lanes busy on small cells and
-// amortises each shared load over more tests on large ones; a staged round
-// is min(kTileCap, the neighbourhood's B count).
+// Tile shape per cell: KA, the A sources per lane, is 1 for a cell of 32 A
+// sources and otherwise taken by density class (33-64, 65-256, more than 256
+// A sources) from TileArgs::ka; a staged round is min(TileArgs::stage, the
+// neighbourhood's B count).  The library's rule is KA = 2, 4, 4 (the smallest
+// that covers the cell in one pass of the 32 lanes, 4 beyond 64 sources) and
+// stage = kTileCap; hlc_autotune times other choices on the caller's jobs.
 //
 // Every mbarrier wait is bounded: on time-out the kernel flags DERR_TIMEOUT,
 // the producer waits (bounded) once more for its last copies, and all warps
@@ -53,7 +54,12 @@ constexpr float kFarA = 1e30f, kFarB = -1e30f;      // padding: never within any
 
 struct TileItem;
 
+// The rule's KA per density class and its staged round.
+constexpr uint32_t kTileRuleKA[3] = {2u, 4u, 4u};
+
 struct TileArgs {
+  uint32_t ka[3];            // A sources per lane by class (33-64, 65-256, >256): 1, 2 or 4
+  uint32_t stage;            // B vectors per staged round, 8 .. kTileCap (a multiple of 8)
   const uint32_t* cell;      // (single) item cells (fine ids)
   const uint32_t* start;     // item starts (single: in the dense-subset order), u + 1
   const uint32_t* dpos;      // (single) dense-subset index -> A entry
@@ -139,7 +145,9 @@ __global__ void k_run_starts(const uint32_t* __restrict__ flag, const uint32_t* 
 }
 
 // One staged round against every A pass of the item, KA A sources per lane.
-template <int KA>
+// EQ4: the tested value is s - (rho_a + rho_b) from the vectors' w (Eq. 4),
+// against lo32 / hi32 = -G / +G.
+template <int KA, bool EQ4>
 __device__ __forceinline__ void tile_round(const float4* __restrict__ sB, uint32_t nr,
                                            uint32_t nrp, uint32_t R0, const uint32_t* s_rb,
                                            const uint32_t* s_off, const float4* __restrict__ a32,
@@ -170,7 +178,7 @@ __device__ __forceinline__ void tile_round(const float4* __restrict__ sB, uint32
 #pragma unroll
         for (int u = 0; u < KA; ++u) {
           const float dx = a[u].x - b.x, dy = a[u].y - b.y, dz = a[u].z - b.z;
-          float s2 = dx * dx;
+          float s2 = EQ4 ? fmaf(dx, dx, b.w - a[u].w) : dx * dx;
           s2 = fmaf(dy, dy, s2);
           s2 = fmaf(dz, dz, s2);
           mask |= (s2 <= hi32 ? 1u : 0u) << (g * KA + u);
@@ -192,7 +200,7 @@ __device__ __forceinline__ void tile_round(const float4* __restrict__ sB, uint32
           for (int v = 1; v < KA; ++v)
             if (u == v) av = a[v];
           const float dx = av.x - b.x, dy = av.y - b.y, dz = av.z - b.z;
-          float s2 = dx * dx;
+          float s2 = EQ4 ? fmaf(dx, dx, b.w - av.w) : dx * dx;
           s2 = fmaf(dy, dy, s2);
           s2 = fmaf(dz, dz, s2);
           const bool hit = act && s2 <= lo32;
@@ -336,6 +344,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // vectors against the item's A sources).  Full/empty mbarrier pairs hand the
 // buffers over, so the copies for the next round overlap the tests of the
 // current one.
+template <bool EQ4>
 __global__ void __launch_bounds__(kTileThreads + 32) k_pair_tile(const TileArgs ta,
                                                                  PairSink sink) {
   extern __shared__ __align__(128) unsigned char tile_smem[];
@@ -372,13 +381,14 @@ __global__ void __launch_bounds__(kTileThreads + 32) k_pair_tile(const TileArgs 
       const uint32_t excl = lane < 10 ? T.off[lane] : 0u;
       const uint32_t incl = lane < 9 ? T.off[lane + 1] : 0u;
       const uint32_t total = T.off[9];
-      for (uint32_t R0 = 0; R0 < total && ok; R0 += kTileCap) {
+      const uint32_t stage = ta.stage;
+      for (uint32_t R0 = 0; R0 < total && ok; R0 += stage) {
         const uint32_t b = s & 1u, use = s >> 1;
         if (!mbar_wait(&empty[b], (use & 1u) ^ 1u)) {  // the consumers freed it
           ok = false;
           break;
         }
-        const uint32_t nr = min((uint32_t)kTileCap, total - R0);
+        const uint32_t nr = min(stage, total - R0);
         const uint32_t nrp = (nr + kTileGroup - 1) / kTileGroup * kTileGroup;
         float4* sB = sB0 + (size_t)b * kTileCap;
         TileDesc& D = desc[b];
@@ -453,15 +463,15 @@ __global__ void __launch_bounds__(kTileThreads + 32) k_pair_tile(const TileArgs 
     if (D.done) break;
     const uint32_t na = D.na;
     const float4* sB = sB0 + (size_t)b * kTileCap;
-    const int ka = na <= 32 ? 1 : (na <= 64 ? 2 : 4);  // the density rule
+    const int ka = na <= 32 ? 1 : (int)ta.ka[na <= 64 ? 0 : (na <= 256 ? 1 : 2)];
     if (ka == 1)
-      tile_round<1>(sB, D.nr, D.nrp, D.R0, D.rb, D.off, ta.a32, D.a0, na, D.lo32, D.hi32, lane,
+      tile_round<1, EQ4>(sB, D.nr, D.nrp, D.R0, D.rb, D.off, ta.a32, D.a0, na, D.lo32, D.hi32, lane,
                     cw, wrows, wband, sink, ta.idxA, ta.idxB, ntest);
     else if (ka == 2)
-      tile_round<2>(sB, D.nr, D.nrp, D.R0, D.rb, D.off, ta.a32, D.a0, na, D.lo32, D.hi32, lane,
+      tile_round<2, EQ4>(sB, D.nr, D.nrp, D.R0, D.rb, D.off, ta.a32, D.a0, na, D.lo32, D.hi32, lane,
                     cw, wrows, wband, sink, ta.idxA, ta.idxB, ntest);
     else
-      tile_round<4>(sB, D.nr, D.nrp, D.R0, D.rb, D.off, ta.a32, D.a0, na, D.lo32, D.hi32, lane,
+      tile_round<4, EQ4>(sB, D.nr, D.nrp, D.R0, D.rb, D.off, ta.a32, D.a0, na, D.lo32, D.hi32, lane,
                     cw, wrows, wband, sink, ta.idxA, ta.idxB, ntest);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[b]);

@@ -224,6 +224,15 @@ class Catalogue:
                 self.id.cpu().numpy().view("uint64"))
 
 
+def error_radii(seed, stream, n, lo_arcsec=0.05, hi_arcsec=0.4, device="cpu", offset=0):
+    """n per-source position error radii in arcsec, log-uniform on [lo, hi]:
+    the spread of positional errors inside one survey catalogue, one value
+    per source as Eq. 4 takes them."""
+    u = uniform(seed, 900 + stream, n, device, offset)
+    return lo_arcsec * torch.pow(torch.tensor(hi_arcsec / lo_arcsec, dtype=torch.float64,
+                                              device=u.device), u)
+
+
 def _mixture_galactic(seed, stream, n, frac_uniform, device):
     """frac_uniform of the sources uniform on the sphere, the rest in the
     exp(-|b|/10 deg) disk; the component of source i is drawn per source."""

@@ -168,9 +168,11 @@ def test_batched_plan_and_kernel_entry_points_reject_bad_arguments_on_the_host()
     assert b"NULL" in L.hlc_last_error()
     assert L.hlc_neighbours(p, 4, -1, p, None) == hlc.HLC_EINVAL
     assert L.hlc_neighbours(None, 4, 3, p, None) == hlc.HLC_EINVAL
-    assert L.hlc_quad_cells(p, p, 4, 0.0, 12, hlc.HLC_FP64, p, p, None) == hlc.HLC_EINVAL
-    assert L.hlc_quad_cells(p, p, 4, 1.0, 15, hlc.HLC_FP64, p, p, None) == hlc.HLC_EINVAL
-    assert L.hlc_quad_cells(p, p, 4, 1.0, 12, 7, p, p, None) == hlc.HLC_EINVAL
+    Q = hlc.HLC_QUAD
+    assert L.hlc_quad_cells(p, p, 4, 0.0, 12, hlc.HLC_FP64, Q, p, p, None) == hlc.HLC_EINVAL
+    assert L.hlc_quad_cells(p, p, 4, 1.0, 15, hlc.HLC_FP64, Q, p, p, None) == hlc.HLC_EINVAL
+    assert L.hlc_quad_cells(p, p, 4, 1.0, 12, 7, Q, p, p, None) == hlc.HLC_EINVAL
+    assert L.hlc_quad_cells(p, p, 4, 1.0, 12, hlc.HLC_FP64, 0, p, p, None) == hlc.HLC_EINVAL
     assert L.hlc_unitvec(p, None, 4, p, None) == hlc.HLC_EINVAL
     for ks, kb in ((2, 8), (4, 0), (4, 33), (8, 65)):
         assert L.hlc_sort_pairs(p, p, 4, ks, kb, None) == hlc.HLC_EINVAL, (ks, kb)

@@ -84,3 +84,87 @@ def test_dense_jobs_use_the_tile_kernel():
     assert _check(jobs, hlc.HLC_FP32_GUARD) > 1000
     *_, st = _run(jobs, hlc.HLC_FP32_GUARD)
     assert st["tile_items"] > 0 and st["tile_entries_a"] >= 32 * st["tile_items"]
+
+
+def _spec(jobs, level=-1):
+    return [dict(A=(j.A.ra.cuda(), j.A.dec.cuda(), j.A.id.cuda()),
+                 B=(j.B.ra.cuda(), j.B.dec.cuda(), j.B.id.cuda()), radius_arcsec=j.r_arcsec,
+                 fine_level=level) for j in jobs]
+
+
+def _rows(spec, prec=hlc.HLC_FP32_GUARD, tune=None):
+    plan = hlc.hlc_plan_batched(spec, precision=prec, tune=tune)
+    res = hlc.hlc_match(plan)
+    hlc.hlc_free(plan)
+    return (res["job"].cpu().numpy(), res["id_a"].cpu().numpy().view(np.uint64),
+            res["id_b"].cpu().numpy().view(np.uint64), res["sep"].cpu().numpy(), res["stats"])
+
+
+def test_autotune_table_is_valid_and_keeps_the_set():
+    """The autotuner (form 2) times candidates on a sample of the jobs; its
+    table is within the documented ranges and a plan that uses it returns the
+    same rows as the rule (the set does not depend on the tile shape)."""
+    jobs = synth.cone_jobs(n_jobs=48, nmin=200, nmax=40000, seed=21)
+    # a few small crowded cones so that dense cells reach the tile kernel
+    for i in range(4):
+        jb = jobs[i]
+        ra, dec = synth.cone_uniform(300 + i, 1, 15000, jb.ra_c, jb.dec_c, 0.02)
+        A = synth.Catalogue(ra, dec, synth.ids(300 + i, 1, 15000))
+        ra, dec = synth.cone_uniform(400 + i, 2, 4000, jb.ra_c, jb.dec_c, 0.02)
+        B = synth.Catalogue(ra, dec, synth.ids(400 + i, 2, 4000))
+        jobs[i] = synth.ConeJob(A, B, 4.0, 0, jb.ra_c, jb.dec_c, 0.02)
+    spec = _spec(jobs)
+    best, rep = hlc.hlc_autotune(spec, sample_jobs=16)
+    assert rep["sample_jobs"] == 16 and len(rep["trials"]) >= 8
+    assert rep["ms_best"] <= rep["ms_rule"]
+    assert best.target_per_cell > 0 and all(k in (1, 2, 4) for k in best.ka)
+    assert best.stage % 8 == 0 and 8 <= best.stage <= 1536
+    assert rep["ms_best"] > 0 and rep["ms_rule"] > 0
+    rule = _rows(spec)
+    tuned = _rows(spec, tune=best)
+    for a, b in zip(rule[:3], tuned[:3]):
+        np.testing.assert_array_equal(a, b)
+    assert np.max(np.abs(rule[3] - tuned[3])) <= 1e-6
+    # every tile shape gives the same set
+    for ka, stage in (((1, 1, 1), 64), ((4, 4, 4), 1536), ((2, 2, 1), 768)):
+        t = hlc.Tune(2.0, (hlc.C.c_uint32 * 3)(*ka), stage)
+        got = _rows(spec, tune=t)
+        np.testing.assert_array_equal(got[1], rule[1])
+        np.testing.assert_array_equal(got[2], rule[2])
+    assert rule[4]["tile_items"] > 0
+
+
+def test_rejected_tune_tables():
+    jobs = synth.cone_jobs(n_jobs=3, nmin=100, nmax=500, seed=22)
+    spec = _spec(jobs)
+    for bad in (hlc.Tune(0.0, (hlc.C.c_uint32 * 3)(2, 4, 4), 1536),
+                hlc.Tune(2.0, (hlc.C.c_uint32 * 3)(3, 4, 4), 1536),
+                hlc.Tune(2.0, (hlc.C.c_uint32 * 3)(2, 4, 4), 1540),
+                hlc.Tune(2.0, (hlc.C.c_uint32 * 3)(2, 4, 4), 12)):
+        with pytest.raises(hlc.HLCError) as ei:
+            hlc.hlc_plan_batched(spec, tune=bad)
+        assert ei.value.code == hlc.HLC_EINVAL
+
+
+def test_4096_jobs_equal_oracle_on_sampled_jobs():
+    """The C4 job count (4096 cone pairs, counts log-uniform 20-2000 per side
+    instead of 1e3-1e6) in one plan with the autotuned table; 64 jobs spread
+    over the list equal the oracle element by element, and the total row
+    count is positive (independent uniform cones match rarely)."""
+    jobs = synth.cone_jobs(n_jobs=4096, nmin=20, nmax=2000, seed=23)
+    spec = _spec(jobs)
+    best, _ = hlc.hlc_autotune(spec, sample_jobs=128)
+    job, ia, ib, sep, st = _rows(spec, tune=best)
+    key = job.astype(np.int64)
+    assert np.all(np.diff(key) >= 0)
+    rng = np.random.default_rng(23)
+    for j in sorted(rng.choice(4096, 64, replace=False).tolist()):
+        jb = jobs[j]
+        want = O.match(*jb.A.numpy(), *jb.B.numpy(), jb.r_arcsec, 10, O.COMPLETE)
+        m = job == j
+        np.testing.assert_array_equal(ia[m], want["id_a"])
+        np.testing.assert_array_equal(ib[m], want["id_b"])
+        if want["sep"].size:
+            assert np.max(np.abs(sep[m] - want["sep"])) <= 1e-6
+    assert st["n_a"] == sum(j.A.n for j in jobs)
+    assert ia.size > 1000

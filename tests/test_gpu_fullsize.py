@@ -36,7 +36,7 @@ def _run(A, B, prec, mode=hlc.HLC_COMPLETE8):
             res["sep"].cpu().numpy(), res["stats"])
 
 
-@pytest.mark.parametrize("mode", [hlc.HLC_COMPLETE8, hlc.HLC_QUAD])
+@pytest.mark.parametrize("mode", [hlc.HLC_COMPLETE8, hlc.HLC_QUAD, hlc.HLC_QUAD_COSDEC])
 def test_fp32_form_equals_fp64_form(sky, mode):
     A, B = sky
     a32, b32, s32, st = _run(A, B, hlc.HLC_FP32_GUARD, mode)
@@ -64,7 +64,7 @@ BOXES = [  # (ra_lo, ra_hi, dec_lo, dec_hi); ra_lo > ra_hi wraps through 0
 ]
 
 
-@pytest.mark.parametrize("mode", [hlc.HLC_COMPLETE8, hlc.HLC_QUAD])
+@pytest.mark.parametrize("mode", [hlc.HLC_COMPLETE8, hlc.HLC_QUAD, hlc.HLC_QUAD_COSDEC])
 @pytest.mark.parametrize("box", BOXES)
 def test_sampled_boxes_equal_oracle(sky, box, mode):
     A, B = sky
@@ -82,7 +82,7 @@ def test_sampled_boxes_equal_oracle(sky, box, mode):
               & (dec_b >= d0 - m) & (dec_b < d1 + m))
     assert sa.sum() > 20
     want = O.match(ra_a[sa], dec_a[sa], id_a[sa], ra_b[sb], dec_b[sb], id_b[sb], R, L,
-                   O.COMPLETE if mode == hlc.HLC_COMPLETE8 else O.QUAD)
+                   mode)  # (the oracle's mode numbers are the library's)
     sel = np.isin(ia, id_a[sa])
     np.testing.assert_array_equal(ia[sel], want["id_a"])
     np.testing.assert_array_equal(ib[sel], want["id_b"])

@@ -89,21 +89,27 @@ def test_neighbours_sampled(order):
     np.testing.assert_array_equal(got, O.neighbours(pix, order))
 
 
+@pytest.mark.parametrize("cosdec", [False, True], ids=["literal", "cosdec"])
 @pytest.mark.parametrize("order,r", [(8, 30.0), (12, 1.5), (14, 1.0)])
-def test_quad_cells_equal_oracle(order, r):
+def test_quad_cells_equal_oracle(order, r, cosdec):
     ra, dec = _points(200_000, order)
     # and sources whose shifted copies land on the RA = 0 line, the poles
-    # and the zone boundary
+    # and the zone boundary; near the poles the cos(Dec) variant's RA shift
+    # grows to its 180 deg cap
     vz = math.degrees(math.asin(2.0 / 3.0))
     R = r / 3600.0
-    ra = np.concatenate([ra, [R, 360.0 - R, 0.0, R * 0.5, 180.0, 45.0, 45.0]])
-    dec = np.concatenate([dec, [10.0, -10.0, 90.0 - R, -90.0 + R * 0.5, vz - R, vz + R, 0.0]])
+    ra = np.concatenate([ra, [R, 360.0 - R, 0.0, R * 0.5, 180.0, 45.0, 45.0],
+                         np.linspace(0.0, 359.0, 40)])
+    dec = np.concatenate([dec, [10.0, -10.0, 90.0 - R, -90.0 + R * 0.5, vz - R, vz + R, 0.0],
+                          np.concatenate([90.0 - np.geomspace(R * 1e-3, R * 50, 20),
+                                          -90.0 + np.geomspace(R * 1e-3, R * 50, 20)])])
     rr, dd = _cuda(ra, dec)
-    want, wcnt = O.quad_cells(ra, dec, r, order)
+    want, wcnt = O.quad_cells(ra, dec, r, order, cosdec)
     w = want.copy()
     w[w == np.uint64(2 ** 64 - 1)] = 0xFFFFFFFF
+    bnd = hlc.HLC_QUAD_COSDEC if cosdec else hlc.HLC_QUAD
     for prec in (hlc.HLC_FP64, hlc.HLC_FP32_GUARD):
-        got, cnt = hlc.hlc_quad_cells(rr, dd, r, order, prec)
+        got, cnt = hlc.hlc_quad_cells(rr, dd, r, order, prec, boundary=bnd)
         np.testing.assert_array_equal(cnt.cpu().numpy(), wcnt)
         g = got.cpu().numpy().view(np.uint32).astype(np.uint64)
         np.testing.assert_array_equal(g, w)

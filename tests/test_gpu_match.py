@@ -45,7 +45,9 @@ def _check(A, B, r, L, mode, prec, **kw):
 
 
 MODES = [(hlc.HLC_COMPLETE8, hlc.HLC_FP64), (hlc.HLC_COMPLETE8, hlc.HLC_FP32_GUARD),
-         (hlc.HLC_QUAD, hlc.HLC_FP64), (hlc.HLC_QUAD, hlc.HLC_FP32_GUARD)]
+         (hlc.HLC_QUAD, hlc.HLC_FP64), (hlc.HLC_QUAD, hlc.HLC_FP32_GUARD),
+         (hlc.HLC_QUAD_COSDEC, hlc.HLC_FP64), (hlc.HLC_QUAD_COSDEC, hlc.HLC_FP32_GUARD)]
+assert O.QUAD == hlc.HLC_QUAD and O.QUAD_COS == hlc.HLC_QUAD_COSDEC  # same mode numbers
 
 
 @pytest.mark.parametrize("mode,prec", MODES)

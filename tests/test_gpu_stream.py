@@ -66,3 +66,35 @@ def test_streamed_equals_in_core():
     np.testing.assert_array_equal(s["id_a"].numpy(), c["id_a"].cpu().numpy())
     np.testing.assert_array_equal(s["id_b"].numpy(), c["id_b"].cpu().numpy())
     np.testing.assert_array_equal(s["sep"].numpy(), c["sep"].cpu().numpy())
+
+
+def test_transfer_model_fits_the_line():
+    """The transfer-cost model of Sec. 4.1.1, Eq. 5, measured the paper's way
+    (alpha from a one-byte copy, beta from a 256 MiB copy): plausible values,
+    and the line predicts copies of 16 and 64 MiB within 15%."""
+    fit = hlc.hlc_transfer_model()
+    for d in ("h2d", "d2h"):
+        f = fit[d]
+        assert 0 < f["alpha_s"] < 1e-3            # a one-byte copy: microseconds
+        assert 1.0 < f["gbs"] < 2000.0            # PCIe / C2C bandwidths
+        for c in f["check"]:
+            if c["bytes"] >= 16 << 20:
+                assert abs(c["measured_s"] - c["model_s"]) <= 0.15 * c["measured_s"], (d, c)
+
+
+def test_streamed_plan_reports_its_copies_and_their_model_time():
+    A, B = _clustered(n_a=300_000, n_b=200_000)
+    plan = hlc.hlc_plan(_host(A, True), _host(B, True), 1.0, 13, coarse_level=3,
+                        device_mem_budget=32 << 20)
+    res = hlc.hlc_match(plan)
+    st = res["stats"]
+    hlc.hlc_free(plan)
+    n = A.n + B.n
+    # inputs go in twice (counting, bucketing), the bucketed runs out once and
+    # back in by group (B's halo copies included), the rows out
+    assert st["h2d_bytes"] >= 3 * 24 * n and st["d2h_bytes"] >= 24 * n
+    assert st["h2d_copies"] >= 9 and st["d2h_copies"] >= 3
+    assert (1 << 20) <= st["stream_chunk"] <= (8 << 20) and st["stream_chunk"] % (1 << 20) == 0
+    assert st["ms_model_h2d"] > 0 and st["ms_model_d2h"] > 0
+    # the model is a floor of the copy time actually spent (plus noise)
+    assert st["ms_model_h2d"] <= 1.5 * st["ms_h2d"] + 1.0
