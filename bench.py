@@ -697,6 +697,8 @@ def dense_line(args, hlc, synth, dev, stream, rank, world):
     peak = sms * 128 * f_mhz * 1e6 / 6
     tps = alg / (ms_pair / 1e3)
     last = sts[-1]
+    ms_tile = sum(s["ms_tile"] for s in sts) / len(sts)
+    tile_tps = last["tile_tests"] / (ms_tile / 1e3) if ms_tile > 0 else None
     return {"workload": "clusters %s x %s (%d Plummer clusters), r=1 arcsec, fine order 13"
                         % (_mega(n), _mega(n * 3 // 4), ncl),
             "ms_per_step": ms, "value": (n + n * 3 // 4) / (ms / 1e3), "unit": "sources/s",
@@ -704,7 +706,13 @@ def dense_line(args, hlc, synth, dev, stream, rank, world):
             "ms_pair": ms_pair, "pair_tests_per_s": tps,
             "fp32_bound": {"peak_tests_per_s": peak, "frac": tps / peak, "sms": sms,
                            "sm_mhz": f_mhz,
-                           "basis": "SMs x 128 FP32 lanes x SM clock / 6 instructions per test"},
+                           "basis": "SMs x 128 FP32 lanes x SM clock / 6 FP32 operations per "
+                                    "test (3 differences, 1 square, 2 fused multiply-adds)"},
+            "tile_kernel": {"kernel": "k_pair_tile (dense cells, B staged in shared memory by "
+                                      "bulk copies, packed f32x2 arithmetic)",
+                            "ms": ms_tile, "tests": last["tile_tests"],
+                            "tests_per_s": tile_tps,
+                            "frac_of_fp32_bound": (tile_tps / peak) if tile_tps else None},
             "tile_items": last["tile_items"], "tile_entries_a": last["tile_entries_a"],
             "matches": last["matches"], "clocks": clk}
 

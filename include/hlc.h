@@ -233,6 +233,9 @@ typedef struct {
                                       the sum over copies of alpha + beta d with
                                       the device's measured fit (hlc_transfer_model) */
   uint64_t stream_chunk;           /*   sources per streamed chunk (from the fit) */
+  float ms_tile;                   /* FP32 complete form: the dense-cell pair
+                                      kernel alone (inside ms_pair) */
+  uint64_t tile_tests;             /*   and the pair tests it ran */
   float ms_plan_presort;           /* FP32 complete form with device inputs:
                                       from the plan's start to the first digit
                                       pass (both preps, side by side, and the

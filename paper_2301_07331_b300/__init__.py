@@ -112,7 +112,8 @@ class Stats(C.Structure):
                 (f, C.c_uint64) for f in ("h2d_bytes", "h2d_copies", "d2h_bytes",
                                           "d2h_copies")] + [
                 ("ms_model_h2d", C.c_float), ("ms_model_d2h", C.c_float),
-                ("stream_chunk", C.c_uint64), ("ms_plan_presort", C.c_float)]
+                ("stream_chunk", C.c_uint64), ("ms_tile", C.c_float), ("tile_tests", C.c_uint64),
+                ("ms_plan_presort", C.c_float)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -292,7 +292,7 @@ struct PinnedBuf {
 
 enum Ctr { C_ROWS = 0, C_BAND, C_TESTS, C_DUPS, C_M, C_TOTAL, C_HEADS_A, C_HEADS_B, C_DENSE,
            C_WORK, C_IDDIFF, C_MAXB, C_SLOW, C_LHITS, C_LLOOK, C_LMAXERR, C_SCRATCH, C_BAND64,
-           C_SLOW_A, C_EMAXA, C_EMAXB, C_N };
+           C_SLOW_A, C_EMAXA, C_EMAXB, C_TILE_TESTS, C_N };
 
 }  // namespace hlc
 
@@ -1431,6 +1431,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   HLC_CUDA(cudaMemsetAsync(P->dev_err, 0, 64, st));
   ev_record(P, 2);
   ev_record(P, 3);
+  bool tile_timed = false;  // (ev 11 .. ev 4: the tile kernel, the last pair launch)
   CellIndex bix;
   bix.keys = B.key;
   bix.table = B.table;
@@ -1513,15 +1514,19 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
         for (int c = 0; c < 3; ++c) ta.ka[c] = P->tile_ka[c];
         ta.stage = P->tile_stage;
         const int smem = 2 * kTileCap * 16;
+        PairSink tsink = sink;  // (its own test counter)
+        tsink.tests = P->ctr + C_TILE_TESTS;
+        ev_record(P, 11);
         if (P->eq4) {
           HLC_CUDA(cudaFuncSetAttribute(k_pair_tile<true>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-          k_pair_tile<true><<<num_sms() * 3u, kTileThreads + 32, smem, st>>>(ta, sink);
+          k_pair_tile<true><<<num_sms() * 3u, kTileThreads + 32, smem, st>>>(ta, tsink);
         } else {
           HLC_CUDA(cudaFuncSetAttribute(k_pair_tile<false>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-          k_pair_tile<false><<<num_sms() * 3u, kTileThreads + 32, smem, st>>>(ta, sink);
+          k_pair_tile<false><<<num_sms() * 3u, kTileThreads + 32, smem, st>>>(ta, tsink);
         }
+        tile_timed = true;
         HLC_LAUNCH_CHECK();
       }
     }
@@ -1621,7 +1626,9 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   res->sep_arcsec = want_sep ? os : nullptr;
   res->job = nullptr;
   res->on_device = 1;
-  P->stats.pair_tests = h[C_TESTS];
+  P->stats.pair_tests = h[C_TESTS] + h[C_TILE_TESTS];
+  P->stats.tile_tests = h[C_TILE_TESTS];
+  P->stats.ms_tile = tile_timed ? ev_ms(P, 11, 4) : 0.f;
   if (!P->table_buckets) P->stats.cells_a = h[C_HEADS_A];  // counted by the pair test
   P->stats.band_candidates = fp32 ? h[C_BAND] : 0;
   P->stats.band_fp64 = fp32 ? band64 : 0;

@@ -170,18 +170,53 @@ __device__ __forceinline__ void tile_round(const float4* __restrict__ sB, uint32
       a[u] = q < na ? a32[a0 + q] : make_float4(kFarA, kFarA, kFarA, 0.f);
       ntest += q < na ? jreal : 0u;
     }
+    // KA >= 2: the lane's A sources in pairs (u, u + 1) on the packed FP32
+    // instructions (FFMA2 / FMUL2: one instruction, two tests); each packed
+    // operation rounds as its scalar twin (a - b as fma(b, -1, a)), so every
+    // s2 is bit for bit the scalar one and the guard band is unchanged
+    constexpr int KP = KA >= 2 ? KA / 2 : 1;
+    float2 ax[KP], ay[KP], az[KP], aw[KP];
+#pragma unroll
+    for (int v = 0; v < KP; ++v) {
+      const int u0 = KA >= 2 ? 2 * v : 0, u1 = KA >= 2 ? 2 * v + 1 : 0;
+      ax[v] = make_float2(a[u0].x, a[u1].x);
+      ay[v] = make_float2(a[u0].y, a[u1].y);
+      az[v] = make_float2(a[u0].z, a[u1].z);
+      aw[v] = make_float2(a[u0].w, a[u1].w);
+    }
+    const float2 m1 = make_float2(-1.f, -1.f);
     for (uint32_t j0 = jbeg; j0 < jend; j0 += kTileGroup) {
       uint32_t mask = 0;
 #pragma unroll
       for (int g = 0; g < kTileGroup; ++g) {
         const float4 b = sB[j0 + g];
+        if constexpr (KA >= 2) {
+          const float2 bx = make_float2(b.x, b.x), by = make_float2(b.y, b.y),
+                       bz = make_float2(b.z, b.z);
 #pragma unroll
-        for (int u = 0; u < KA; ++u) {
-          const float dx = a[u].x - b.x, dy = a[u].y - b.y, dz = a[u].z - b.z;
-          float s2 = EQ4 ? fmaf(dx, dx, b.w - a[u].w) : dx * dx;
-          s2 = fmaf(dy, dy, s2);
-          s2 = fmaf(dz, dz, s2);
-          mask |= (s2 <= hi32 ? 1u : 0u) << (g * KA + u);
+          for (int v = 0; v < KP; ++v) {
+            const float2 dx = __ffma2_rn(bx, m1, ax[v]);
+            const float2 dy = __ffma2_rn(by, m1, ay[v]);
+            const float2 dz = __ffma2_rn(bz, m1, az[v]);
+            float2 s2;
+            if constexpr (EQ4)
+              s2 = __ffma2_rn(dx, dx, __ffma2_rn(aw[v], m1, make_float2(b.w, b.w)));
+            else
+              s2 = __fmul2_rn(dx, dx);
+            s2 = __ffma2_rn(dy, dy, s2);
+            s2 = __ffma2_rn(dz, dz, s2);
+            mask |= (s2.x <= hi32 ? 1u : 0u) << (g * KA + 2 * v);
+            mask |= (s2.y <= hi32 ? 1u : 0u) << (g * KA + 2 * v + 1);
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < KA; ++u) {
+            const float dx = a[u].x - b.x, dy = a[u].y - b.y, dz = a[u].z - b.z;
+            float s2 = EQ4 ? fmaf(dx, dx, b.w - a[u].w) : dx * dx;
+            s2 = fmaf(dy, dy, s2);
+            s2 = fmaf(dz, dz, s2);
+            mask |= (s2 <= hi32 ? 1u : 0u) << (g * KA + u);
+          }
         }
       }
       if (__any_sync(0xffffffffu, mask != 0u)) {
