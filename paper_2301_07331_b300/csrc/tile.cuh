@@ -8,7 +8,9 @@
 // were put in fine order; in the batched form: every such cell of every job,
 // A being sorted by (job, cell)).  A first pass (k_tile_items, a warp per
 // cell) finds the B ranges of each cell and its 8 neighbours (single form: a
-// sparse neighbour table cell contributes its whole range, once).  The pair
+// sparse neighbour table cell contributes its whole range, once) and cuts the
+// cell's A sources into items of at most kTileChunkA, which balances the
+// CTAs when a few cells hold far more sources than the rest.  The pair
 // kernel is warp-specialised.  Its producer warp takes prepared items from an
 // atomic counter, writes a round descriptor and copies the round's B vectors
 // into one of two stage buffers with cp.async.bulk (the TMA engine's bulk
@@ -47,6 +49,7 @@ constexpr int kTileThreads = 256;                   // consumer threads (+1 prod
 constexpr int kTileWarps = kTileThreads / 32;
 constexpr int kTileCap = 1536;                      // B vectors per stage buffer (24 KB)
 constexpr uint32_t kTileMinA = 32;                  // smaller cells stay with the lane kernels
+constexpr uint32_t kTileChunkA = 128;               // A sources per work item (a larger cell is split)
 constexpr int kTileGroup = 8;                       // B vectors per any-vote
 constexpr int kTileRowCap = 128, kTileBandCap = 64; // staged rows per warp
 constexpr long long kTileSpin = 1ll << 24;
@@ -268,10 +271,11 @@ __device__ __forceinline__ void tile_round(const float4* __restrict__ sB, uint32
 // the pair test by a warp per cell (the lookups are dependent loads; run apart
 // from the test, they overlap across the whole GPU).
 struct TileItem {
-  uint32_t a0, na;
+  uint32_t a0, na;          // this item's A entries (a chunk of its cell's)
   float lo32, hi32;
   uint32_t rb[9], off[10];  // B range start per slot; exclusive prefix of lengths
-  uint32_t pad[2];
+  uint32_t ncell;           // A sources of the whole cell (its density class)
+  uint32_t pad;
 };
 
 template <bool BATCH>
@@ -343,27 +347,34 @@ __global__ void k_tile_items(const TileArgs ta, TileItem* __restrict__ out,
     }
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 8);
     if (total == 0) continue;
+    // a cell with many A sources becomes several items of kTileChunkA A
+    // sources each, against the same B ranges, so that the densest cells do
+    // not keep one CTA busy while the others have run out of work
+    const uint32_t nch = (na + kTileChunkA - 1) / kTileChunkA;
     unsigned long long slot = 0;
-    if (lane == 0) slot = atomicAdd(nout, 1ull);
+    if (lane == 0) slot = atomicAdd(nout, (unsigned long long)nch);
     slot = __shfl_sync(0xffffffffu, slot, 0);
-    if (slot >= cap) continue;  // sized for the worst case; never taken
-    TileItem& T = out[slot];
-    if (lane < 9) {
-      T.rb[lane] = rb;
-      T.off[lane] = incl - len;
-    }
-    if (lane == 8) T.off[9] = incl;
-    if (lane == 0) {
-      T.a0 = a0;
-      T.na = na;
-      T.lo32 = lo32;
-      T.hi32 = hi32;
+    for (uint32_t c = 0; c < nch; ++c) {
+      if (slot + c >= cap) break;  // sized for the worst case (na >= 32 per cell); never taken
+      TileItem& T = out[slot + c];
+      if (lane < 9) {
+        T.rb[lane] = rb;
+        T.off[lane] = incl - len;
+      }
+      if (lane == 8) T.off[9] = incl;
+      if (lane == 0) {
+        T.a0 = a0 + c * kTileChunkA;
+        T.na = min(kTileChunkA, na - c * kTileChunkA);
+        T.ncell = na;
+        T.lo32 = lo32;
+        T.hi32 = hi32;
+      }
     }
   }
 }
 
 struct TileDesc {  // one staged round, written by the producer warp
-  uint32_t a0, na, R0, nr, nrp;
+  uint32_t a0, na, ncell, R0, nr, nrp;
   float lo32, hi32;
   uint32_t rb[9], off[10];
   int done;
@@ -410,7 +421,7 @@ __global__ void __launch_bounds__(kTileThreads + 32) k_pair_tile(const TileArgs 
       item = __shfl_sync(0xffffffffu, item, 0);
       if (item >= nitems) break;
       const TileItem& T = ta.items[item];
-      const uint32_t a0 = T.a0, na = T.na;
+      const uint32_t a0 = T.a0, na = T.na, ncell = T.ncell;
       const float lo32 = T.lo32, hi32 = T.hi32;
       const uint32_t rb = lane < 9 ? T.rb[lane] : 0u;
       const uint32_t excl = lane < 10 ? T.off[lane] : 0u;
@@ -435,6 +446,7 @@ __global__ void __launch_bounds__(kTileThreads + 32) k_pair_tile(const TileArgs 
         if (lane == 0) {
           D.a0 = a0;
           D.na = na;
+          D.ncell = ncell;
           D.R0 = R0;
           D.nr = nr;
           D.nrp = nrp;
@@ -498,7 +510,10 @@ __global__ void __launch_bounds__(kTileThreads + 32) k_pair_tile(const TileArgs 
     if (D.done) break;
     const uint32_t na = D.na;
     const float4* sB = sB0 + (size_t)b * kTileCap;
-    const int ka = na <= 32 ? 1 : (int)ta.ka[na <= 64 ? 0 : (na <= 256 ? 1 : 2)];
+    const uint32_t nc = D.ncell;  // the class is the whole cell's; KA never above the chunk's need
+    int ka = nc <= 32 ? 1 : (int)ta.ka[nc <= 64 ? 0 : (nc <= 256 ? 1 : 2)];
+    if (na <= 32) ka = 1;
+    else if (na <= 64 && ka > 2) ka = 2;
     if (ka == 1)
       tile_round<1, EQ4>(sB, D.nr, D.nrp, D.R0, D.rb, D.off, ta.a32, D.a0, na, D.lo32, D.hi32, lane,
                     cw, wrows, wband, sink, ta.idxA, ta.idxB, ntest);
