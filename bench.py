@@ -904,6 +904,7 @@ def run_streamed(args):
     Ah = synth.Catalogue(A.ra.cpu().pin_memory(), A.dec.cpu().pin_memory(), A.id.cpu().pin_memory())
     Bh = synth.Catalogue(B.ra.cpu().pin_memory(), B.dec.cpu().pin_memory(), B.id.cpu().pin_memory())
     budget = args.budget_gb << 30
+    fit = hlc.hlc_transfer_model()  # Eq. 5 on this machine (the plans reuse it)
 
     def streamed():
         plan = hlc.hlc_plan(Ah, Bh, r, L, coarse_level=Lc, device_mem_budget=budget,
@@ -922,6 +923,29 @@ def run_streamed(args):
         hlc.hlc_free(plan)
         return n_
     ms_c, nc_ = _timed_loop(in_core, args.steps, args.warmup, stream)
+    # the two row sets, compared on the device (untimed)
+    plan = hlc.hlc_plan(Ah, Bh, r, L, coarse_level=Lc, device_mem_budget=budget, stream=stream)
+    so = hlc.hlc_match(plan, copy=False)
+    sa, sb = so["id_a"].to(dev), so["id_b"].to(dev)
+    hlc.hlc_free(plan)
+    plan = hlc.hlc_plan(A, B, r, L, coarse_level=Lc, stream=stream)
+    co = hlc.hlc_match(plan, copy=False)
+    equal_rows = bool(sa.numel() == co["n"] and torch.equal(sa, co["id_a"])
+                      and torch.equal(sb, co["id_b"]))
+    hlc.hlc_free(plan)
+    del sa, sb
+    copy_ms = {"h2d": st_s["ms_h2d"], "d2h": st_s["ms_d2h"]}
+    tmodel = {"alpha_us": {k: fit[k]["alpha_s"] * 1e6 for k in ("h2d", "d2h")},
+              "beta_gbs": {k: fit[k]["gbs"] for k in ("h2d", "d2h")},
+              "chunk_sources": st_s["stream_chunk"],
+              "h2d": {"bytes": st_s["h2d_bytes"], "copies": st_s["h2d_copies"],
+                      "model_ms": st_s["ms_model_h2d"], "measured_copy_ms": copy_ms["h2d"]},
+              "d2h": {"bytes": st_s["d2h_bytes"], "copies": st_s["d2h_copies"],
+                      "model_ms": st_s["ms_model_d2h"], "measured_copy_ms": copy_ms["d2h"]},
+              "model_transfer_share_of_step": (st_s["ms_model_h2d"] + st_s["ms_model_d2h"])
+              / ms_s,
+              "basis": "Eq. 5 per copy, alpha from a one-byte copy and beta from a 256 MiB "
+                       "copy (pinned); measured_copy_ms: the copies' own CUDA-event spans"}
     _line(args, "sources matched/s, streamed from pinned host memory", (n + nb) / (ms_s / 1e3),
           "sources/s", ms_s,
           {"workload": "clusters %s x %s (%d Plummer clusters), r=1 arcsec, fine order 13, "
@@ -932,9 +956,9 @@ def run_streamed(args):
                                           "ms_stream_groups", "ms_stream_merge", "ms_d2h",
                                           "ms_prep", "ms_sort", "ms_index", "ms_pair",
                                           "ms_recheck", "ms_output")},
-          h2d_gbs=(n + nb) * 24 / (st_s["ms_h2d"] / 1e3) / 1e9 if st_s["ms_h2d"] else None,
+          h2d_gbs=st_s["h2d_bytes"] / (st_s["ms_h2d"] / 1e3) / 1e9 if st_s["ms_h2d"] else None,
           in_core={"ms": ms_c, "sources_per_s": (n + nb) / (ms_c / 1e3), "matches": nc_},
-          equal_counts=ns_ == nc_)
+          equal_counts=ns_ == nc_, equal_rows=equal_rows, transfer_model=tmodel)
 
 
 def run_completeness(args):
