@@ -212,7 +212,8 @@ struct CatDev {
   unsigned long long* tile_n = nullptr;  // device: runs, items taken, their entries
   uint8_t* tiled = nullptr;              // 1 for A entries the tile kernel takes
   TileItem* tile_items = nullptr;        // prepared items (B ranges found)
-  unsigned long long* tile_nprep = nullptr;
+  unsigned long long* tile_nprep = nullptr;  // items placed from the front, from the back
+  uint64_t tile_icap = 0;                     // capacity of tile_items
 };
 
 // Pinned host memory of streamed plans (the pass-1 runs, the groups' result
@@ -596,10 +597,11 @@ static int dense_fixup(hlc_plan_t* P, CatDev& X, const uint32_t* T, int shift, b
   HLC_LAUNCH_CHECK();
   X.tile_dpos = dpos;
   {  // the B ranges of every item, ahead of the pair test
-    const uint64_t cap = nd / kTileMinA + 1;
+    const uint64_t cap = nd / kTileItemDiv + 1;
+    X.tile_icap = cap;
     HLC_ALLOC(ar, X.tile_items, TileItem, cap);
-    HLC_ALLOC(ar, X.tile_nprep, unsigned long long, 1);
-    HLC_CUDA(cudaMemsetAsync(X.tile_nprep, 0, 8, st));
+    HLC_ALLOC(ar, X.tile_nprep, unsigned long long, 2);
+    HLC_CUDA(cudaMemsetAsync(X.tile_nprep, 0, 16, st));
     TileArgs ta{};
     ta.cell = X.tile_cell;
     ta.start = X.tile_start;
@@ -1501,6 +1503,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
         TileArgs ta{};
         ta.items = A.tile_items;
         ta.nitems = A.tile_nprep;
+        ta.icap = A.tile_icap;
         ta.idxA = A.idx;
         ta.idxB = B.idx;
         ta.work = (unsigned*)(P->ctr + C_WORK);
@@ -1513,7 +1516,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
         ta.sparse_cell = P->sparse_cell;
         for (int c = 0; c < 3; ++c) ta.ka[c] = P->tile_ka[c];
         ta.stage = P->tile_stage;
-        const int smem = 2 * kTileCap * 16;
+        const int smem = kTileSmemDyn;
         PairSink tsink = sink;  // (its own test counter)
         tsink.tests = P->ctr + C_TILE_TESTS;
         ev_record(P, 11);
@@ -2001,11 +2004,12 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
     k_mark_tiled<<<grid_for(NA, kThreads, num_sms() * 8u), kThreads, 0, st>>>(
         P->A.tile_start, nullptr, P->A.tile_n, P->A.tiled);
     g_launches += 2;
-    const uint64_t cap = NA / kTileMinA + 1;
+    const uint64_t cap = NA / kTileItemDiv + 1;
+    P->A.tile_icap = cap;
     P->A.tile_items = ar.get_n<TileItem>(cap);
-    P->A.tile_nprep = ar.get_n<unsigned long long>(1);
+    P->A.tile_nprep = ar.get_n<unsigned long long>(2);
     if (!P->A.tile_items || !P->A.tile_nprep) return fail(HLC_ENOMEM);
-    cudaMemsetAsync(P->A.tile_nprep, 0, 8, st);
+    cudaMemsetAsync(P->A.tile_nprep, 0, 16, st);
     TileArgs tp{};
     tp.start = P->A.tile_start;
     tp.nitems = P->A.tile_n;
@@ -2087,7 +2091,7 @@ static int batched_pair_graph(hlc_plan_t* P, uint2* rows, uint64_t cap, uint2* b
   }
   cudaStream_t cs;
   HLC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  const int tile_smem = 2 * kTileCap * 16;
+  const int tile_smem = kTileSmemDyn;
   HLC_CUDA(cudaFuncSetAttribute(k_pair_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tile_smem));
   cudaGraph_t g;
@@ -2119,6 +2123,7 @@ static int batched_pair_graph(hlc_plan_t* P, uint2* rows, uint64_t cap, uint2* b
         TileArgs ta{};
         ta.items = P->A.tile_items;
         ta.nitems = P->A.tile_nprep;
+        ta.icap = P->A.tile_icap;
         ta.work = (unsigned*)(P->ctr + C_WORK);
         ta.a32 = P->A.v32;
         ta.b32 = P->B.v32;

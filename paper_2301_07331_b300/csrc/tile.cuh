@@ -1,36 +1,48 @@
-// Pair test for dense cells: one CTA per A cell, B tiles staged in shared
-// memory by the TMA engine (the calculation-block kernel of Sec. 4.3 / Fig. 7
-// in B300 form: the A sources of a block against all B sources of its block
-// and the neighbouring blocks).
+// Pair test for dense cells: one CTA per work item at a time, B tiles staged
+// in shared memory by the TMA engine (the calculation-block kernel of Sec.
+// 4.3 / Fig. 7 in B300 form: the A sources of a block against all B sources
+// of its block and the neighbouring blocks).
 //
-// Work items are fine cells of A holding at least kTileMinA entries (in the
-// single form: cells that lie in a dense table cell of B, where the A entries
-// were put in fine order; in the batched form: every such cell of every job,
-// A being sorted by (job, cell)).  A first pass (k_tile_items, a warp per
-// cell) finds the B ranges of each cell and its 8 neighbours (single form: a
-// sparse neighbour table cell contributes its whole range, once) and cuts the
-// cell's A sources into items of at most kTileChunkA, which balances the
-// CTAs when a few cells hold far more sources than the rest.  The pair
-// kernel is warp-specialised.  Its producer warp takes prepared items from an
-// atomic counter, writes a round descriptor and copies the round's B vectors
-// into one of two stage buffers with cp.async.bulk (the TMA engine's bulk
-// mode: contiguous 16-byte vectors need no tensor map) on the buffer's "full"
-// mbarrier.  Eight consumer warps each take a share of a staged round
-// while their lanes hold KA A sources each: one broadcast shared load per B
-// vector and KA FP32 squared-chord tests; then they arrive on the buffer's
-// "empty" mbarrier.  The producer's copies for the next round thus overlap
-// the consumers' tests of the current one.  Rounds are padded to whole
-// groups with vectors far from everything and dead A lanes hold such a vector
-// too, so the inner loop has no bounds tests.  A lane records its candidates
-// of a group in a bit mask; the warp walks them (a ballot per step) only when
-// one lane has any.
+// Work items come from fine cells of A holding at least kTileMinA entries (in
+// the single form: cells that lie in a dense table cell of B, where the A
+// entries were put in fine order; in the batched form: every such cell of
+// every job, A being sorted by (job, cell)).  A first pass (k_tile_items, a
+// warp per cell) finds the B ranges of each cell and its 8 neighbours (single
+// form: a sparse neighbour table cell contributes its whole range, once) and
+// cuts the cell into items: its A sources in chunks of at most kTileChunkA,
+// its neighbourhood's B sources in windows of at most kTileChunkB, so that no
+// item holds a CTA much longer than the others; items of many tests are
+// handed out first.  The pair kernel is warp-specialised.  Its producer warp
+// takes items from an atomic counter, writes a round descriptor and copies
+// the round's B vectors and the item's A vectors into one of two stage
+// buffers with cp.async.bulk (the TMA engine's bulk mode: contiguous 16-byte
+// vectors need no tensor map) on the buffer's "full" mbarrier.  Eight
+// consumer warps each take a share of a staged round while their lanes hold
+// KA A sources each, then arrive on the buffer's "empty" mbarrier; the
+// producer's copies for the next round overlap the tests of the current one.
+//
+// The test runs in a local frame: with c the item's first A vector, a' = a -
+// c and b' = b - c are of the size of the neighbourhood, and
+//   |a - b|^2 = |a'|^2 + |b'|^2 - 2 a'.b'
+// keeps FP32's relative precision.  Each consumer warp writes its share of
+// the staged B vectors as (b', |b'|^2 + w_b) into slots of its own,
+// kTileConv at a time, and each lane keeps -2a' and |a'|^2 - w_a - thr for
+// its A sources, so a test is one add and three fused multiply-adds,
+// r = (|b'|^2 + w_b) + (|a'|^2 - w_a - thr) - 2a'.b', and a pair is a
+// candidate when r < 0 (its sign bit, OR-ed over a group of tests).  thr is
+// the guard band's upper edge widened by a bound on the rounding of the
+// local form (derived at tile_threshold), so every pair the global-frame
+// FP32 test would keep is a candidate.  Candidates are then decided exactly
+// as the lane kernels decide them: the squared chord of the global FP32
+// vectors (both from the staged copies) against the guard band, so the tile
+// kernel's rows equal the lane kernels' bit for bit.
 //
 // Tile shape per cell: KA, the A sources per lane, is 1 for a cell of 32 A
 // sources and otherwise taken by density class (33-64, 65-256, more than 256
 // A sources) from TileArgs::ka; a staged round is min(TileArgs::stage, the
-// neighbourhood's B count).  The library's rule is KA = 2, 4, 4 (the smallest
-// that covers the cell in one pass of the 32 lanes, 4 beyond 64 sources) and
-// stage = kTileCap; hlc_autotune times other choices on the caller's jobs.
+// item's B window).  The library's rule is KA = 2, 4, 4 (the smallest that
+// covers the cell in one pass of the 32 lanes, 4 beyond 64 sources) and stage
+// = kTileCap; hlc_autotune times other choices on the caller's jobs.
 //
 // Every mbarrier wait is bounded: on time-out the kernel flags DERR_TIMEOUT,
 // the producer waits (bounded) once more for its last copies, and all warps
@@ -50,10 +62,18 @@ constexpr int kTileWarps = kTileThreads / 32;
 constexpr int kTileCap = 1536;                      // B vectors per stage buffer (24 KB)
 constexpr uint32_t kTileMinA = 32;                  // smaller cells stay with the lane kernels
 constexpr uint32_t kTileChunkA = 128;               // A sources per work item (a larger cell is split)
+constexpr uint32_t kTileChunkB = 1024;              // B vectors per work item's window
+constexpr uint32_t kTileItemDiv = 8;                // items per cell <= its A sources / 8
+constexpr uint64_t kTileHeavy = 32768;              // tests of an item handed out first
 constexpr int kTileGroup = 8;                       // B vectors per any-vote
 constexpr int kTileRowCap = 128, kTileBandCap = 64; // staged rows per warp
 constexpr long long kTileSpin = 1ll << 24;
-constexpr float kFarA = 1e30f, kFarB = -1e30f;      // padding: never within any radius
+constexpr float kFarW = 1e30f;                      // padding: r never below zero
+constexpr uint32_t kTileConv = 64;                  // B vectors per warp in the local frame
+// dynamic shared memory of k_pair_tile: two stage buffers of B, two of A, and
+// each consumer warp's local-frame slots
+constexpr int kTileSmemDyn =
+    (2 * (kTileCap + (int)kTileChunkA) + kTileWarps * (int)kTileConv) * 16;
 
 struct TileItem;
 
@@ -66,7 +86,8 @@ struct TileArgs {
   const uint32_t* cell;      // (single) item cells (fine ids)
   const uint32_t* start;     // item starts (single: in the dense-subset order), u + 1
   const uint32_t* dpos;      // (single) dense-subset index -> A entry
-  const unsigned long long* nitems;
+  const unsigned long long* nitems;  // k_tile_items: cells; k_pair_tile: items (front, back)
+  uint64_t icap;             // k_pair_tile: capacity of items (the back ones count down from it)
   unsigned* work;            // atomic item counter (zeroed)
   const float4* a32;
   const float4* b32;
@@ -147,13 +168,67 @@ __global__ void k_run_starts(const uint32_t* __restrict__ flag, const uint32_t* 
   if (blockIdx.x == 0 && threadIdx.x == 0) start[*runs] = (uint32_t)n;
 }
 
+// Upper edge of the local-form filter for one warp's share of a round.  hi is
+// the guard band's upper edge of the global-frame test (hi > 0 in both
+// radius rules), mA and mB bound |a'|^2 (+ |w_a|) and |b'|^2 (+ |w_b|) over
+// the item's A sources and the warp's B vectors, u = 2^-24.  A pair the
+// global-frame test keeps (s2 <= hi) has D^2 = |a - b|^2 <= hi (1 + 6u) in the
+// plain rule (each of the test's five roundings is relative; with the Eq. 4
+// term, D^2 - rho <= hi + 5u (D^2 + rho)); the local vectors carry the
+// roundings of a - c and b - c, |(a' - b') - (a - b)| <= u (|a'| + |b'|), which
+// adds at most 2u (mA + mB) + u D^2; and the ten roundings of r (three for
+// |a'|^2, three for |b'|^2, one for |a'|^2 - thr, one add, three fused
+// multiply-adds) stay below 8u (|a'|^2 + |b'|^2 + 2|a'||b'| + thr) <=
+// 16u (mA + mB) + 8u thr.  With D^2 <= 2 (mA + mB) and rho <= mA + mB the sum
+// is below hi + 43u (mA + mB) + 8u thr, which the value below exceeds by more
+// than the three roundings of its own evaluation: every such pair has r < 0.
+__device__ __forceinline__ float tile_threshold(float hi, float mA, float mB) {
+  constexpr float u = 5.9604644775390625e-8f;  // 2^-24
+  return (hi + 64.0f * u * (mA + mB)) * (1.0f + 16.0f * u);
+}
+
+__device__ __forceinline__ float warp_max_nonneg(float v) {
+  // non-negative floats order as their bit patterns
+  return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(v)));
+}
+
+// A warp's staged rows out to the sink, the entry -> source translation
+// (idxA non-null) done here with a row per lane, so that the dependent index
+// loads of a whole buffer overlap instead of stalling each candidate.
+template <int CAP>
+__device__ __forceinline__ void tile_flush(WarpRows<CAP>& w, uint2* rows,
+                                           unsigned long long* count, uint64_t cap, int* err,
+                                           const uint32_t* __restrict__ idxA,
+                                           const uint32_t* __restrict__ idxB) {
+  if (w.fill == 0) return;
+  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(count, (unsigned long long)w.fill);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  for (int i = lane; i < w.fill; i += 32) {
+    uint2 r = w.buf[i];
+    if (idxA) r = make_uint2(__ldg(idxA + r.x), __ldg(idxB + r.y));
+    if (base + i < cap)
+      rows[base + i] = r;
+    else
+      atomicOr(err, DERR_OVERFLOW);
+  }
+  __syncwarp();
+  w.fill = 0;
+}
+
 // One staged round against every A pass of the item, KA A sources per lane.
-// EQ4: the tested value is s - (rho_a + rho_b) from the vectors' w (Eq. 4),
-// against lo32 / hi32 = -G / +G.
+// sB: the round's B vectors and sA: the item's A vectors, both as copied
+// (global frame, read only); sC: this warp's kTileConv slots, which receive
+// its share of sB in the local frame, kTileConv vectors at a time.
+// EQ4: w holds +rho_a (A) and -rho_b (B) and the tested value is
+// s - (rho_a + rho_b) against lo32 / hi32 = -G / +G (Eq. 4).
 template <int KA, bool EQ4>
-__device__ __forceinline__ void tile_round(const float4* __restrict__ sB, uint32_t nr,
-                                           uint32_t nrp, uint32_t R0, const uint32_t* s_rb,
-                                           const uint32_t* s_off, const float4* __restrict__ a32,
+__device__ __forceinline__ void tile_round(const float4* __restrict__ sB,
+                                           const float4* __restrict__ sA, float4* __restrict__ sC,
+                                           uint32_t nr, uint32_t nrp, uint32_t R0,
+                                           const uint32_t* s_rb, const uint32_t* s_off,
                                            uint32_t a0, uint32_t na, float lo32, float hi32,
                                            int lane, int warp, WarpRows<kTileRowCap>& wrows,
                                            WarpRows<kTileBandCap>& wband, const PairSink& sink,
@@ -164,118 +239,157 @@ __device__ __forceinline__ void tile_round(const float4* __restrict__ sB, uint32
   const uint32_t gper = (ngroups + kTileWarps - 1) / kTileWarps;
   const uint32_t jbeg = min(ngroups, warp * gper) * kTileGroup;
   const uint32_t jend = min(ngroups, (warp + 1) * gper) * kTileGroup;
-  const uint32_t jreal = jend <= nr ? jend - jbeg : (nr > jbeg ? nr - jbeg : 0u);
-  for (uint32_t p0 = 0; p0 < na && jbeg < jend; p0 += 32 * KA) {
-    float4 a[KA];
-#pragma unroll
-    for (int u = 0; u < KA; ++u) {
-      const uint32_t q = p0 + (uint32_t)u * 32 + lane;
-      a[u] = q < na ? a32[a0 + q] : make_float4(kFarA, kFarA, kFarA, 0.f);
-      ntest += q < na ? jreal : 0u;
+  const float4 c = sA[0];
+  float mA = 0.f;
+  for (uint32_t q = lane; q < na; q += 32) {
+    const float4 a = sA[q];
+    const float x = a.x - c.x, y = a.y - c.y, z = a.z - c.z;
+    const float n2 = fmaf(z, z, fmaf(y, y, x * x));
+    mA = fmaxf(mA, EQ4 ? n2 + fabsf(a.w) : n2);
+  }
+  mA = warp_max_nonneg(mA);
+  constexpr int KP = KA >= 2 ? KA / 2 : 1;
+  for (uint32_t s0 = jbeg; s0 < jend; s0 += kTileConv) {
+    const uint32_t s1 = min(jend, s0 + kTileConv);
+    const uint32_t sreal = min(s1, nr) > s0 ? min(s1, nr) - s0 : 0u;
+    // B vectors s0 .. s1 to (b', |b'|^2 + w_b) in sC; padding slots to a
+    // vector no A source comes near
+    __syncwarp();  // (the previous slice's tests are done with sC)
+    float mB = 0.f;
+    for (uint32_t j = s0 + lane; j < s1; j += 32) {
+      float4 v = make_float4(0.f, 0.f, 0.f, kFarW);
+      if (j < nr) {
+        const float4 b = sB[j];
+        const float x = b.x - c.x, y = b.y - c.y, z = b.z - c.z;
+        const float n2 = fmaf(z, z, fmaf(y, y, x * x));
+        v = make_float4(x, y, z, EQ4 ? n2 + b.w : n2);
+        mB = fmaxf(mB, EQ4 ? n2 + fabsf(b.w) : n2);
+      }
+      sC[j - s0] = v;
     }
-    // KA >= 2: the lane's A sources in pairs (u, u + 1) on the packed FP32
-    // instructions (FFMA2 / FMUL2: one instruction, two tests); each packed
-    // operation rounds as its scalar twin (a - b as fma(b, -1, a)), so every
-    // s2 is bit for bit the scalar one and the guard band is unchanged
-    constexpr int KP = KA >= 2 ? KA / 2 : 1;
-    float2 ax[KP], ay[KP], az[KP], aw[KP];
+    const float thr = tile_threshold(hi32, mA, warp_max_nonneg(mB));
+    __syncwarp();
+    for (uint32_t p0 = 0; p0 < na; p0 += 32 * KA) {
+      // -2a' and |a'|^2 - w_a - thr of the lane's A sources; dead lanes never
+      // become candidates
+      float ax[KA], ay[KA], az[KA], ac[KA];
 #pragma unroll
-    for (int v = 0; v < KP; ++v) {
-      const int u0 = KA >= 2 ? 2 * v : 0, u1 = KA >= 2 ? 2 * v + 1 : 0;
-      ax[v] = make_float2(a[u0].x, a[u1].x);
-      ay[v] = make_float2(a[u0].y, a[u1].y);
-      az[v] = make_float2(a[u0].z, a[u1].z);
-      aw[v] = make_float2(a[u0].w, a[u1].w);
-    }
-    const float2 m1 = make_float2(-1.f, -1.f);
-    for (uint32_t j0 = jbeg; j0 < jend; j0 += kTileGroup) {
-      uint32_t mask = 0;
+      for (int u = 0; u < KA; ++u) {
+        const uint32_t q = p0 + (uint32_t)u * 32 + lane;
+        ax[u] = ay[u] = az[u] = 0.f;
+        ac[u] = kFarW;
+        if (q < na) {
+          const float4 a = sA[q];
+          const float x = a.x - c.x, y = a.y - c.y, z = a.z - c.z;
+          const float n2 = fmaf(z, z, fmaf(y, y, x * x));
+          ax[u] = -2.f * x;
+          ay[u] = -2.f * y;
+          az[u] = -2.f * z;
+          ac[u] = (EQ4 ? n2 - a.w : n2) - thr;
+        }
+        ntest += q < na ? sreal : 0u;
+      }
+      // KA >= 2: pairs of A sources on the packed FP32 instructions (FADD2 /
+      // FFMA2, each half rounded as its scalar twin)
+      float2 px[KP], py[KP], pz[KP], pc[KP];
 #pragma unroll
-      for (int g = 0; g < kTileGroup; ++g) {
-        const float4 b = sB[j0 + g];
-        if constexpr (KA >= 2) {
-          const float2 bx = make_float2(b.x, b.x), by = make_float2(b.y, b.y),
-                       bz = make_float2(b.z, b.z);
+      for (int v = 0; v < KP; ++v) {
+        const int u0 = KA >= 2 ? 2 * v : 0, u1 = KA >= 2 ? 2 * v + 1 : 0;
+        px[v] = make_float2(ax[u0], ax[u1]);
+        py[v] = make_float2(ay[u0], ay[u1]);
+        pz[v] = make_float2(az[u0], az[u1]);
+        pc[v] = make_float2(ac[u0], ac[u1]);
+      }
+      for (uint32_t j0 = s0; j0 < s1; j0 += kTileGroup) {
+        const float4* cg = sC + (j0 - s0);
+        uint32_t gm = 0;  // bit g: some test of B vector j0 + g has r < 0
 #pragma unroll
-          for (int v = 0; v < KP; ++v) {
-            const float2 dx = __ffma2_rn(bx, m1, ax[v]);
-            const float2 dy = __ffma2_rn(by, m1, ay[v]);
-            const float2 dz = __ffma2_rn(bz, m1, az[v]);
-            float2 s2;
-            if constexpr (EQ4)
-              s2 = __ffma2_rn(dx, dx, __ffma2_rn(aw[v], m1, make_float2(b.w, b.w)));
-            else
-              s2 = __fmul2_rn(dx, dx);
-            s2 = __ffma2_rn(dy, dy, s2);
-            s2 = __ffma2_rn(dz, dz, s2);
-            mask |= (s2.x <= hi32 ? 1u : 0u) << (g * KA + 2 * v);
-            mask |= (s2.y <= hi32 ? 1u : 0u) << (g * KA + 2 * v + 1);
+        for (int g = 0; g < kTileGroup; ++g) {
+          const float4 b = cg[g];
+          uint32_t sg = 0;
+          if constexpr (KA >= 2) {
+            const float2 bx = make_float2(b.x, b.x), by = make_float2(b.y, b.y),
+                         bz = make_float2(b.z, b.z), bw = make_float2(b.w, b.w);
+#pragma unroll
+            for (int v = 0; v < KP; ++v) {
+              float2 r = __fadd2_rn(bw, pc[v]);
+              r = __ffma2_rn(px[v], bx, r);
+              r = __ffma2_rn(py[v], by, r);
+              r = __ffma2_rn(pz[v], bz, r);
+              sg |= __float_as_uint(r.x) | __float_as_uint(r.y);
+            }
+          } else {
+            float r = b.w + ac[0];
+            r = fmaf(ax[0], b.x, r);
+            r = fmaf(ay[0], b.y, r);
+            r = fmaf(az[0], b.z, r);
+            sg = __float_as_uint(r);
           }
-        } else {
+          gm |= (sg >> 31) << g;
+        }
+        if (__any_sync(0xffffffffu, gm != 0u)) {
+          // the flagged vectors' tests again, one bit per candidate test
+          uint32_t mask = 0;
+          for (uint32_t m = gm; m != 0u; m &= m - 1u) {
+            const int g = __ffs(m) - 1;
+            const float4 b = cg[g];
 #pragma unroll
-          for (int u = 0; u < KA; ++u) {
-            const float dx = a[u].x - b.x, dy = a[u].y - b.y, dz = a[u].z - b.z;
-            float s2 = EQ4 ? fmaf(dx, dx, b.w - a[u].w) : dx * dx;
+            for (int u = 0; u < KA; ++u) {
+              float r = b.w + ac[u];
+              r = fmaf(ax[u], b.x, r);
+              r = fmaf(ay[u], b.y, r);
+              r = fmaf(az[u], b.z, r);
+              mask |= (__float_as_uint(r) >> 31) << (g * KA + u);
+            }
+          }
+          // each lane walks its own candidates: the global-frame FP32 test
+          const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)__popc(mask));
+          for (int it = 0; it < nmax; ++it) {
+            const bool act = mask != 0u;
+            const int bit = act ? __ffs(mask) - 1 : 0;
+            mask &= mask - 1u;
+            const int g = bit / KA, u = bit % KA;
+            const uint32_t j = j0 + (uint32_t)g;
+            const uint32_t qa = p0 + (uint32_t)u * 32 + lane;
+            const float4 av = sA[act ? qa : 0u];
+            const float4 b = sB[j];
+            const float dx = av.x - b.x, dy = av.y - b.y, dz = av.z - b.z;
+            float s2 = EQ4 ? fmaf(dx, dx, b.w - av.w) : dx * dx;
             s2 = fmaf(dy, dy, s2);
             s2 = fmaf(dz, dz, s2);
-            mask |= (s2 <= hi32 ? 1u : 0u) << (g * KA + u);
-          }
-        }
-      }
-      if (__any_sync(0xffffffffu, mask != 0u)) {
-
-        // slow path: each lane walks its own candidates
-        const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)__popc(mask));
-        for (int it = 0; it < nmax; ++it) {
-          const bool act = mask != 0u;
-          const int bit = act ? __ffs(mask) - 1 : 0;
-          mask &= mask - 1u;
-          const int g = bit / KA, u = bit % KA;
-          const uint32_t j = j0 + g;
-          const float4 b = sB[j];
-          float4 av = a[0];
-#pragma unroll
-          for (int v = 1; v < KA; ++v)
-            if (u == v) av = a[v];
-          const float dx = av.x - b.x, dy = av.y - b.y, dz = av.z - b.z;
-          float s2 = EQ4 ? fmaf(dx, dx, b.w - av.w) : dx * dx;
-          s2 = fmaf(dy, dy, s2);
-          s2 = fmaf(dz, dz, s2);
-          const bool hit = act && s2 <= lo32;
-          const bool band = act && !hit && s2 <= hi32;
-          uint32_t jb = 0;
-          if (act) {  // B entry of staged slot R0 + j
-            const uint32_t o = R0 + j;
-            int sgi = 0;
+            const bool hit = act && s2 <= lo32;
+            const bool band = act && !hit && s2 <= hi32;
+            uint32_t jb = 0;
+            if (act) {  // B entry of staged slot R0 + j
+              const uint32_t o = R0 + j;
+              int sgi = 0;
 #pragma unroll 1
-            while (sgi < 8 && s_off[sgi + 1] <= o) ++sgi;
-            jb = s_rb[sgi] + (o - s_off[sgi]);
+              while (sgi < 8 && s_off[sgi + 1] <= o) ++sgi;
+              jb = s_rb[sgi] + (o - s_off[sgi]);
+            }
+            wrows.add(hit, a0 + qa, jb);  // entries; tile_flush translates them
+            wband.add(band, a0 + qa, jb);
+            if (wrows.fill > kTileRowCap - 32)
+              tile_flush(wrows, sink.rows, sink.count, sink.cap, sink.err, idxA, idxB);
+            if (wband.fill > kTileBandCap - 32)
+              tile_flush(wband, sink.band, sink.band_count, sink.band_cap, sink.err, idxA, idxB);
           }
-          uint32_t ka = a0 + p0 + (uint32_t)u * 32 + lane;
-          if (idxA && act) {  // rows of source indices
-            ka = __ldg(idxA + ka);
-            jb = __ldg(idxB + jb);
-          }
-          wrows.add(hit, ka, jb);
-          wband.add(band, ka, jb);
-          if (wrows.fill > kTileRowCap - 32) wrows.flush(sink.rows, sink.count, sink.cap, sink.err);
-          if (wband.fill > kTileBandCap - 32)
-            wband.flush(sink.band, sink.band_count, sink.band_cap, sink.err);
         }
       }
     }
   }
 }
 
-// One dense A cell with the B ranges of its neighbourhood, found ahead of
-// the pair test by a warp per cell (the lookups are dependent loads; run apart
-// from the test, they overlap across the whole GPU).
+// A chunk of a dense A cell against a window of the B ranges of its
+// neighbourhood, found ahead of the pair test by a warp per cell (the lookups
+// are dependent loads; run apart from the test, they overlap across the whole
+// GPU).
 struct TileItem {
   uint32_t a0, na;          // this item's A entries (a chunk of its cell's)
   float lo32, hi32;
   uint32_t rb[9], off[10];  // B range start per slot; exclusive prefix of lengths
   uint32_t ncell;           // A sources of the whole cell (its density class)
-  uint32_t pad;
+  uint32_t rlo, rhi;        // this item's window [rlo, rhi) of the concatenated ranges
 };
 
 template <bool BATCH>
@@ -347,27 +461,40 @@ __global__ void k_tile_items(const TileArgs ta, TileItem* __restrict__ out,
     }
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 8);
     if (total == 0) continue;
-    // a cell with many A sources becomes several items of kTileChunkA A
-    // sources each, against the same B ranges, so that the densest cells do
-    // not keep one CTA busy while the others have run out of work
-    const uint32_t nch = (na + kTileChunkA - 1) / kTileChunkA;
+    // the cell becomes items of at most kTileChunkA A sources against B
+    // windows of at most kTileChunkB vectors (a multiple of kTileGroup), and
+    // at most na / kTileItemDiv items in all, so that the items of every
+    // cell fit the array (its capacity is the A entries / kTileItemDiv + 1);
+    // items of at least kTileHeavy tests are placed from the front, the rest
+    // from the back, and the pair kernel takes the front ones first
+    const uint32_t nch_a = (na + kTileChunkA - 1) / kTileChunkA;
+    uint32_t nch_b = (total + kTileChunkB - 1) / kTileChunkB;
+    nch_b = min(nch_b, max(1u, (na / kTileItemDiv) / nch_a));
+    uint32_t wb = (total + nch_b - 1) / nch_b;
+    wb = (wb + kTileGroup - 1) / kTileGroup * kTileGroup;
+    nch_b = (total + wb - 1) / wb;
+    const uint32_t nch = nch_a * nch_b;
+    const bool heavy = (uint64_t)min(na, kTileChunkA) * wb >= kTileHeavy;
     unsigned long long slot = 0;
-    if (lane == 0) slot = atomicAdd(nout, (unsigned long long)nch);
+    if (lane == 0) slot = atomicAdd(nout + (heavy ? 0 : 1), (unsigned long long)nch);
     slot = __shfl_sync(0xffffffffu, slot, 0);
     for (uint32_t c = 0; c < nch; ++c) {
-      if (slot + c >= cap) break;  // sized for the worst case (na >= 32 per cell); never taken
-      TileItem& T = out[slot + c];
+      if (slot + c >= cap) break;  // the capacity bounds every cell's items; never taken
+      TileItem& T = out[heavy ? slot + c : cap - 1 - (slot + c)];
+      const uint32_t ca = c / nch_b, cb = c % nch_b;
       if (lane < 9) {
         T.rb[lane] = rb;
         T.off[lane] = incl - len;
       }
       if (lane == 8) T.off[9] = incl;
       if (lane == 0) {
-        T.a0 = a0 + c * kTileChunkA;
-        T.na = min(kTileChunkA, na - c * kTileChunkA);
+        T.a0 = a0 + ca * kTileChunkA;
+        T.na = min(kTileChunkA, na - ca * kTileChunkA);
         T.ncell = na;
         T.lo32 = lo32;
         T.hi32 = hi32;
+        T.rlo = cb * wb;
+        T.rhi = min(total, (cb + 1) * wb);
       }
     }
   }
@@ -385,16 +512,19 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // Warp-specialised: warp 0 produces (takes prepared items from the work
-// counter, writes a round descriptor and issues the bulk copies into one of
-// two stage buffers), warps 1..8 consume (test their share of the staged B
-// vectors against the item's A sources).  Full/empty mbarrier pairs hand the
-// buffers over, so the copies for the next round overlap the tests of the
-// current one.
+// counter, writes a round descriptor and issues the bulk copies of the
+// round's B vectors and the item's A vectors into one of two stage buffers),
+// warps 1..8 consume (move their share of the staged B vectors to the local
+// frame and test it against the item's A sources).  Full/empty mbarrier
+// pairs hand the buffers over, so the copies for the next round overlap the
+// tests of the current one; the consumers only read the stage buffers.
 template <bool EQ4>
 __global__ void __launch_bounds__(kTileThreads + 32) k_pair_tile(const TileArgs ta,
                                                                  PairSink sink) {
   extern __shared__ __align__(128) unsigned char tile_smem[];
-  float4* sB0 = reinterpret_cast<float4*>(tile_smem);
+  float4* sB0 = reinterpret_cast<float4*>(tile_smem);        // 2 x kTileCap
+  float4* sA0 = sB0 + 2 * kTileCap;                           // 2 x kTileChunkA
+  float4* sC0 = sA0 + 2 * kTileChunkA;                        // kTileWarps x kTileConv
   __shared__ uint2 s_rows[kTileWarps][kTileRowCap];
   __shared__ uint2 s_band[kTileWarps][kTileBandCap];
   __shared__ __align__(8) uint64_t full[2], empty[2];
@@ -412,31 +542,35 @@ __global__ void __launch_bounds__(kTileThreads + 32) k_pair_tile(const TileArgs 
   __syncthreads();
   if (warp == 0) {
     // ---------------- producer ----------------
-    const uint64_t nitems = *ta.nitems;  // prepared items (k_tile_items)
+    const uint64_t nfront = ta.nitems[0];                 // prepared items (k_tile_items):
+    const uint64_t nitems = nfront + ta.nitems[1];        // the front ones, then the back ones
     uint32_t s = 0;  // rounds issued
     bool ok = true;
+    unsigned nxt = 0;  // the next item's index, taken one item ahead
+    if (lane == 0) nxt = atomicAdd(ta.work, 1u);
     for (;;) {
-      unsigned item = 0;
-      if (lane == 0) item = atomicAdd(ta.work, 1u);
-      item = __shfl_sync(0xffffffffu, item, 0);
+      const unsigned item = __shfl_sync(0xffffffffu, nxt, 0);
       if (item >= nitems) break;
-      const TileItem& T = ta.items[item];
+      // (taken now, used after this item's rounds: its latency overlaps them)
+      if (lane == 0) nxt = atomicAdd(ta.work, 1u);
+      const TileItem& T = ta.items[item < nfront ? item : ta.icap - 1 - (item - nfront)];
       const uint32_t a0 = T.a0, na = T.na, ncell = T.ncell;
       const float lo32 = T.lo32, hi32 = T.hi32;
       const uint32_t rb = lane < 9 ? T.rb[lane] : 0u;
       const uint32_t excl = lane < 10 ? T.off[lane] : 0u;
       const uint32_t incl = lane < 9 ? T.off[lane + 1] : 0u;
-      const uint32_t total = T.off[9];
+      const uint32_t rlo = T.rlo, rhi = T.rhi;
       const uint32_t stage = ta.stage;
-      for (uint32_t R0 = 0; R0 < total && ok; R0 += stage) {
+      for (uint32_t R0 = rlo; R0 < rhi && ok; R0 += stage) {
         const uint32_t b = s & 1u, use = s >> 1;
         if (!mbar_wait(&empty[b], (use & 1u) ^ 1u)) {  // the consumers freed it
           ok = false;
           break;
         }
-        const uint32_t nr = min(stage, total - R0);
+        const uint32_t nr = min(stage, rhi - R0);
         const uint32_t nrp = (nr + kTileGroup - 1) / kTileGroup * kTileGroup;
         float4* sB = sB0 + (size_t)b * kTileCap;
+        float4* sA = sA0 + (size_t)b * kTileChunkA;
         TileDesc& D = desc[b];
         if (lane < 9) {
           D.rb[lane] = rb;
@@ -454,16 +588,14 @@ __global__ void __launch_bounds__(kTileThreads + 32) k_pair_tile(const TileArgs 
           D.hi32 = hi32;
           D.done = 0;
         }
-        // pad the round to whole groups with vectors far from everything
-        if ((uint32_t)lane < nrp - nr) sB[nr + lane] = make_float4(kFarB, kFarB, kFarB, 0.f);
         __syncwarp();
         if (lane == 0) {
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
                            smem_u32(&full[b])),
-                       "r"(nr * 16u)
+                       "r"((nr + na) * 16u)
                        : "memory");
         }
-        // lanes 0..8 copy their range's part of the round
+        // lanes 0..8 copy their range's part of the round, lane 9 the A chunk
         if (lane < 9) {
           const uint32_t o0 = max(excl, R0), o1 = min(incl, R0 + nr);
           if (o1 > o0) {
@@ -474,6 +606,12 @@ __global__ void __launch_bounds__(kTileThreads + 32) k_pair_tile(const TileArgs 
                 "l"(src), "r"((o1 - o0) * 16u), "r"(smem_u32(&full[b]))
                 : "memory");
           }
+        } else if (lane == 9) {
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+              "[%0], [%1], %2, [%3];" ::"r"(smem_u32(sA)),
+              "l"(ta.a32 + a0), "r"(na * 16u), "r"(smem_u32(&full[b]))
+              : "memory");
         }
         ++s;
       }
@@ -510,24 +648,26 @@ __global__ void __launch_bounds__(kTileThreads + 32) k_pair_tile(const TileArgs 
     if (D.done) break;
     const uint32_t na = D.na;
     const float4* sB = sB0 + (size_t)b * kTileCap;
+    const float4* sA = sA0 + (size_t)b * kTileChunkA;
+    float4* sC = sC0 + (size_t)cw * kTileConv;
     const uint32_t nc = D.ncell;  // the class is the whole cell's; KA never above the chunk's need
     int ka = nc <= 32 ? 1 : (int)ta.ka[nc <= 64 ? 0 : (nc <= 256 ? 1 : 2)];
     if (na <= 32) ka = 1;
     else if (na <= 64 && ka > 2) ka = 2;
     if (ka == 1)
-      tile_round<1, EQ4>(sB, D.nr, D.nrp, D.R0, D.rb, D.off, ta.a32, D.a0, na, D.lo32, D.hi32, lane,
-                    cw, wrows, wband, sink, ta.idxA, ta.idxB, ntest);
+      tile_round<1, EQ4>(sB, sA, sC, D.nr, D.nrp, D.R0, D.rb, D.off, D.a0, na, D.lo32, D.hi32,
+                         lane, cw, wrows, wband, sink, ta.idxA, ta.idxB, ntest);
     else if (ka == 2)
-      tile_round<2, EQ4>(sB, D.nr, D.nrp, D.R0, D.rb, D.off, ta.a32, D.a0, na, D.lo32, D.hi32, lane,
-                    cw, wrows, wband, sink, ta.idxA, ta.idxB, ntest);
+      tile_round<2, EQ4>(sB, sA, sC, D.nr, D.nrp, D.R0, D.rb, D.off, D.a0, na, D.lo32, D.hi32,
+                         lane, cw, wrows, wband, sink, ta.idxA, ta.idxB, ntest);
     else
-      tile_round<4, EQ4>(sB, D.nr, D.nrp, D.R0, D.rb, D.off, ta.a32, D.a0, na, D.lo32, D.hi32, lane,
-                    cw, wrows, wband, sink, ta.idxA, ta.idxB, ntest);
+      tile_round<4, EQ4>(sB, sA, sC, D.nr, D.nrp, D.R0, D.rb, D.off, D.a0, na, D.lo32, D.hi32,
+                         lane, cw, wrows, wband, sink, ta.idxA, ta.idxB, ntest);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[b]);
   }
-  wrows.flush(sink.rows, sink.count, sink.cap, sink.err);
-  wband.flush(sink.band, sink.band_count, sink.band_cap, sink.err);
+  tile_flush(wrows, sink.rows, sink.count, sink.cap, sink.err, ta.idxA, ta.idxB);
+  tile_flush(wband, sink.band, sink.band_count, sink.band_cap, sink.err, ta.idxA, ta.idxB);
   for (int o = 16; o > 0; o >>= 1) ntest += __shfl_down_sync(0xffffffffu, ntest, o);
   if (lane == 0 && ntest) atomicAdd(sink.tests, ntest);
 }
