@@ -312,6 +312,7 @@ struct hlc_plan_s {
   double target_per_cell = 0;  // batched order rule (0: kTargetPerCell)
   double k9 = 0;              // 9 (pi/648000)^2: squared pair radius per squared error
   double eq4_rmax = 0;        // largest pair radius (arcsec)
+  double eq4_rho_max = 0;     // bound on rho_a + rho_b (squared chord)
   float lo32 = 0, hi32 = 0;
   int join_level = 0;
   int nslot = 9;
@@ -1084,6 +1085,8 @@ static int eq4_setup(hlc_plan_t* P, const hlc_catalog* A, const hlc_catalog* B) 
     return HLC_EINVAL;
   }
   P->k9 = 9.0 * (pi / 648000.0) * (pi / 648000.0);
+  // bound on rho_a + rho_b as the FP32 payloads hold them (each rounded once)
+  P->eq4_rho_max = 1.01 * P->k9 * (emax[0] * emax[0] + emax[1] * emax[1]);
   P->C = chord2_threshold(P->eq4_rmax);
   // the single-radius band at the largest threshold, plus the roundings of
   // rho_a, rho_b and their sum (3 half-ulps of C) and 4 sin^2(x/2) = x^2 -
@@ -1516,6 +1519,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
         ta.sparse_cell = P->sparse_cell;
         for (int c = 0; c < 3; ++c) ta.ka[c] = P->tile_ka[c];
         ta.stage = P->tile_stage;
+        ta.rho_max = P->eq4 ? (float)P->eq4_rho_max : 0.f;
         const int smem = kTileSmemDyn;
         PairSink tsink = sink;  // (its own test counter)
         tsink.tests = P->ctr + C_TILE_TESTS;

@@ -70,10 +70,12 @@ constexpr int kTileRowCap = 128, kTileBandCap = 64; // staged rows per warp
 constexpr long long kTileSpin = 1ll << 24;
 constexpr float kFarW = 1e30f;                      // padding: r never below zero
 constexpr uint32_t kTileConv = 64;                  // B vectors per warp in the local frame
-// dynamic shared memory of k_pair_tile: two stage buffers of B, two of A, and
-// each consumer warp's local-frame slots
+constexpr uint32_t kTileQueue = 64;                 // candidates queued per warp
+// dynamic shared memory of k_pair_tile: two stage buffers of B, two of A,
+// each consumer warp's local-frame slots and its candidate queue
 constexpr int kTileSmemDyn =
-    (2 * (kTileCap + (int)kTileChunkA) + kTileWarps * (int)kTileConv) * 16;
+    (2 * (kTileCap + (int)kTileChunkA) + kTileWarps * (int)kTileConv) * 16 +
+    kTileWarps * (int)kTileQueue * 4;
 
 struct TileItem;
 
@@ -83,6 +85,7 @@ constexpr uint32_t kTileRuleKA[3] = {2u, 4u, 4u};
 struct TileArgs {
   uint32_t ka[3];            // A sources per lane by class (33-64, 65-256, >256): 1, 2 or 4
   uint32_t stage;            // B vectors per staged round, 8 .. kTileCap (a multiple of 8)
+  float rho_max;             // Eq. 4: bound on rho_a + rho_b (0 for the single radius)
   const uint32_t* cell;      // (single) item cells (fine ids)
   const uint32_t* start;     // item starts (single: in the dense-subset order), u + 1
   const uint32_t* dpos;      // (single) dense-subset index -> A entry
@@ -168,23 +171,25 @@ __global__ void k_run_starts(const uint32_t* __restrict__ flag, const uint32_t* 
   if (blockIdx.x == 0 && threadIdx.x == 0) start[*runs] = (uint32_t)n;
 }
 
-// Upper edge of the local-form filter for one warp's share of a round.  hi is
-// the guard band's upper edge of the global-frame test (hi > 0 in both
-// radius rules), mA and mB bound |a'|^2 (+ |w_a|) and |b'|^2 (+ |w_b|) over
-// the item's A sources and the warp's B vectors, u = 2^-24.  A pair the
-// global-frame test keeps (s2 <= hi) has D^2 = |a - b|^2 <= hi (1 + 6u) in the
-// plain rule (each of the test's five roundings is relative; with the Eq. 4
-// term, D^2 - rho <= hi + 5u (D^2 + rho)); the local vectors carry the
-// roundings of a - c and b - c, |(a' - b') - (a - b)| <= u (|a'| + |b'|), which
-// adds at most 2u (mA + mB) + u D^2; and the ten roundings of r (three for
-// |a'|^2, three for |b'|^2, one for |a'|^2 - thr, one add, three fused
-// multiply-adds) stay below 8u (|a'|^2 + |b'|^2 + 2|a'||b'| + thr) <=
-// 16u (mA + mB) + 8u thr.  With D^2 <= 2 (mA + mB) and rho <= mA + mB the sum
-// is below hi + 43u (mA + mB) + 8u thr, which the value below exceeds by more
-// than the three roundings of its own evaluation: every such pair has r < 0.
-__device__ __forceinline__ float tile_threshold(float hi, float mA, float mB) {
+// Upper edge of the local-form filter for one item.  hi is the guard band's
+// upper edge of the global-frame test (C + G for a single radius, G under
+// Eq. 4; hi > 0), rho the bound on rho_a + rho_b (0 for a single radius), mA
+// a bound on |a'|^2 over the item's A sources, u = 2^-24.  Only pairs the
+// global-frame test keeps (s2 <= hi) must come out with r < 0, and such a
+// pair is near its A source: each of the test's five roundings is relative,
+// so D^2 = |a - b|^2 <= (hi + rho) (1 + 6u), and |b'| <= |a'| + D + (tiny).
+// The local vectors carry the roundings of a - c and b - c, which move
+// |a' - b'|^2 by at most u (2 mA + 4 D^2); the ten roundings of r (three for
+// |a'|^2, three for |b'|^2, one for |a'|^2 - w_a - thr, one add, three fused
+// multiply-adds) stay below 8u (|a'|^2 + |b'|^2 + 2|a'||b'| + thr + rho) <=
+// 8u (8 mA + 2 D^2 + thr + rho).  Summed, r <= hi + 38u (hi + rho) + 66u mA +
+// 8u thr - thr, and the value below makes that negative with room for the
+// three roundings of its own evaluation.  (Pairs far from every A source may
+// have larger errors; they can only become false candidates, which the
+// global-frame test then rejects.)
+__device__ __forceinline__ float tile_threshold(float hi, float rho, float mA) {
   constexpr float u = 5.9604644775390625e-8f;  // 2^-24
-  return (hi + 64.0f * u * (mA + mB)) * (1.0f + 16.0f * u);
+  return (hi + 64.0f * u * (hi + rho) + 128.0f * u * mA) * (1.0f + 16.0f * u);
 }
 
 __device__ __forceinline__ float warp_max_nonneg(float v) {
@@ -218,19 +223,66 @@ __device__ __forceinline__ void tile_flush(WarpRows<CAP>& w, uint2* rows,
   w.fill = 0;
 }
 
+// A warp's candidates of the current round, decided 32 at a time: the
+// global-frame FP32 test of each (A slot qa, B slot j) against the guard band.
+template <bool EQ4>
+__device__ __forceinline__ void tile_drain(uint32_t* __restrict__ q, uint32_t& qfill,
+                                           const float4* __restrict__ sB,
+                                           const float4* __restrict__ sA, uint32_t R0,
+                                           const uint32_t* s_rb, const uint32_t* s_off,
+                                           uint32_t a0, float lo32, float hi32, int lane,
+                                           WarpRows<kTileRowCap>& wrows,
+                                           WarpRows<kTileBandCap>& wband, const PairSink& sink,
+                                           const uint32_t* __restrict__ idxA,
+                                           const uint32_t* __restrict__ idxB) {
+  __syncwarp();
+  for (uint32_t base = 0; base < qfill; base += 32) {
+    const uint32_t i = base + (uint32_t)lane;
+    const bool act = i < qfill;
+    const uint32_t e = act ? q[i] : 0u;
+    const uint32_t j = e >> 8, qa = e & 255u;
+    const float4 av = sA[qa];
+    const float4 b = sB[j];
+    const float dx = av.x - b.x, dy = av.y - b.y, dz = av.z - b.z;
+    float s2 = EQ4 ? fmaf(dx, dx, b.w - av.w) : dx * dx;
+    s2 = fmaf(dy, dy, s2);
+    s2 = fmaf(dz, dz, s2);
+    const bool hit = act && s2 <= lo32;
+    const bool band = act && !hit && s2 <= hi32;
+    uint32_t jb = 0;
+    if (hit || band) {  // B entry of staged slot R0 + j
+      const uint32_t o = R0 + j;
+      int sgi = 0;
+#pragma unroll 1
+      while (sgi < 8 && s_off[sgi + 1] <= o) ++sgi;
+      jb = s_rb[sgi] + (o - s_off[sgi]);
+    }
+    wrows.add(hit, a0 + qa, jb);  // entries; tile_flush translates them
+    wband.add(band, a0 + qa, jb);
+    if (wrows.fill > kTileRowCap - 32)
+      tile_flush(wrows, sink.rows, sink.count, sink.cap, sink.err, idxA, idxB);
+    if (wband.fill > kTileBandCap - 32)
+      tile_flush(wband, sink.band, sink.band_count, sink.band_cap, sink.err, idxA, idxB);
+  }
+  __syncwarp();
+  qfill = 0;
+}
+
 // One staged round against every A pass of the item, KA A sources per lane.
 // sB: the round's B vectors and sA: the item's A vectors, both as copied
 // (global frame, read only); sC: this warp's kTileConv slots, which receive
-// its share of sB in the local frame, kTileConv vectors at a time.
+// its share of sB in the local frame, kTileConv vectors at a time; q: its
+// candidate queue (kTileQueue slots), drained before the round ends.
 // EQ4: w holds +rho_a (A) and -rho_b (B) and the tested value is
 // s - (rho_a + rho_b) against lo32 / hi32 = -G / +G (Eq. 4).
 template <int KA, bool EQ4>
 __device__ __forceinline__ void tile_round(const float4* __restrict__ sB,
                                            const float4* __restrict__ sA, float4* __restrict__ sC,
-                                           uint32_t nr, uint32_t nrp, uint32_t R0,
-                                           const uint32_t* s_rb, const uint32_t* s_off,
-                                           uint32_t a0, uint32_t na, float lo32, float hi32,
-                                           int lane, int warp, WarpRows<kTileRowCap>& wrows,
+                                           uint32_t* __restrict__ q, uint32_t nr, uint32_t nrp,
+                                           uint32_t R0, const uint32_t* s_rb,
+                                           const uint32_t* s_off, uint32_t a0, uint32_t na,
+                                           float lo32, float hi32, float rho_max, int lane,
+                                           int warp, WarpRows<kTileRowCap>& wrows,
                                            WarpRows<kTileBandCap>& wband, const PairSink& sink,
                                            const uint32_t* __restrict__ idxA,
                                            const uint32_t* __restrict__ idxB,
@@ -239,67 +291,66 @@ __device__ __forceinline__ void tile_round(const float4* __restrict__ sB,
   const uint32_t gper = (ngroups + kTileWarps - 1) / kTileWarps;
   const uint32_t jbeg = min(ngroups, warp * gper) * kTileGroup;
   const uint32_t jend = min(ngroups, (warp + 1) * gper) * kTileGroup;
+  if (jbeg >= jend) return;
+  const uint32_t jreal = jend <= nr ? jend - jbeg : (nr > jbeg ? nr - jbeg : 0u);
   const float4 c = sA[0];
   float mA = 0.f;
-  for (uint32_t q = lane; q < na; q += 32) {
-    const float4 a = sA[q];
+  for (uint32_t k = lane; k < na; k += 32) {
+    const float4 a = sA[k];
     const float x = a.x - c.x, y = a.y - c.y, z = a.z - c.z;
-    const float n2 = fmaf(z, z, fmaf(y, y, x * x));
-    mA = fmaxf(mA, EQ4 ? n2 + fabsf(a.w) : n2);
+    mA = fmaxf(mA, fmaf(z, z, fmaf(y, y, x * x)));
   }
-  mA = warp_max_nonneg(mA);
+  const float thr = tile_threshold(hi32, rho_max, warp_max_nonneg(mA));
+  uint32_t qfill = 0;
   constexpr int KP = KA >= 2 ? KA / 2 : 1;
-  for (uint32_t s0 = jbeg; s0 < jend; s0 += kTileConv) {
-    const uint32_t s1 = min(jend, s0 + kTileConv);
-    const uint32_t sreal = min(s1, nr) > s0 ? min(s1, nr) - s0 : 0u;
-    // B vectors s0 .. s1 to (b', |b'|^2 + w_b) in sC; padding slots to a
-    // vector no A source comes near
-    __syncwarp();  // (the previous slice's tests are done with sC)
-    float mB = 0.f;
-    for (uint32_t j = s0 + lane; j < s1; j += 32) {
-      float4 v = make_float4(0.f, 0.f, 0.f, kFarW);
-      if (j < nr) {
-        const float4 b = sB[j];
-        const float x = b.x - c.x, y = b.y - c.y, z = b.z - c.z;
+  for (uint32_t p0 = 0; p0 < na; p0 += 32 * KA) {
+    // -2a' and |a'|^2 - w_a - thr of the lane's A sources, A sources u and
+    // u + 1 side by side (KA >= 2: for the packed FP32 instructions FADD2 /
+    // FFMA2, each half rounded as its scalar twin); dead lanes never become
+    // candidates
+    float2 px[KP], py[KP], pz[KP], pc[KP];
+#pragma unroll
+    for (int u = 0; u < KA; ++u) {
+      const uint32_t k = p0 + (uint32_t)u * 32 + lane;
+      float x2 = 0.f, y2 = 0.f, z2 = 0.f, w2 = kFarW;
+      if (k < na) {
+        const float4 a = sA[k];
+        const float x = a.x - c.x, y = a.y - c.y, z = a.z - c.z;
         const float n2 = fmaf(z, z, fmaf(y, y, x * x));
-        v = make_float4(x, y, z, EQ4 ? n2 + b.w : n2);
-        mB = fmaxf(mB, EQ4 ? n2 + fabsf(b.w) : n2);
+        x2 = -2.f * x;
+        y2 = -2.f * y;
+        z2 = -2.f * z;
+        w2 = (EQ4 ? n2 - a.w : n2) - thr;
       }
-      sC[j - s0] = v;
+      if (u % 2 == 0) {
+        px[u / 2] = make_float2(x2, x2);
+        py[u / 2] = make_float2(y2, y2);
+        pz[u / 2] = make_float2(z2, z2);
+        pc[u / 2] = make_float2(w2, w2);
+      } else {
+        px[u / 2].y = x2;
+        py[u / 2].y = y2;
+        pz[u / 2].y = z2;
+        pc[u / 2].y = w2;
+      }
+      ntest += k < na ? jreal : 0u;
     }
-    const float thr = tile_threshold(hi32, mA, warp_max_nonneg(mB));
-    __syncwarp();
-    for (uint32_t p0 = 0; p0 < na; p0 += 32 * KA) {
-      // -2a' and |a'|^2 - w_a - thr of the lane's A sources; dead lanes never
-      // become candidates
-      float ax[KA], ay[KA], az[KA], ac[KA];
-#pragma unroll
-      for (int u = 0; u < KA; ++u) {
-        const uint32_t q = p0 + (uint32_t)u * 32 + lane;
-        ax[u] = ay[u] = az[u] = 0.f;
-        ac[u] = kFarW;
-        if (q < na) {
-          const float4 a = sA[q];
-          const float x = a.x - c.x, y = a.y - c.y, z = a.z - c.z;
+    for (uint32_t s0 = jbeg; s0 < jend; s0 += kTileConv) {
+      const uint32_t s1 = min(jend, s0 + kTileConv);
+      // B vectors s0 .. s1 to (b', |b'|^2 + w_b) in sC; padding slots to a
+      // vector no A source comes near
+      __syncwarp();  // (the previous slice's tests are done with sC)
+      for (uint32_t j = s0 + lane; j < s1; j += 32) {
+        float4 v = make_float4(0.f, 0.f, 0.f, kFarW);
+        if (j < nr) {
+          const float4 b = sB[j];
+          const float x = b.x - c.x, y = b.y - c.y, z = b.z - c.z;
           const float n2 = fmaf(z, z, fmaf(y, y, x * x));
-          ax[u] = -2.f * x;
-          ay[u] = -2.f * y;
-          az[u] = -2.f * z;
-          ac[u] = (EQ4 ? n2 - a.w : n2) - thr;
+          v = make_float4(x, y, z, EQ4 ? n2 + b.w : n2);
         }
-        ntest += q < na ? sreal : 0u;
+        sC[j - s0] = v;
       }
-      // KA >= 2: pairs of A sources on the packed FP32 instructions (FADD2 /
-      // FFMA2, each half rounded as its scalar twin)
-      float2 px[KP], py[KP], pz[KP], pc[KP];
-#pragma unroll
-      for (int v = 0; v < KP; ++v) {
-        const int u0 = KA >= 2 ? 2 * v : 0, u1 = KA >= 2 ? 2 * v + 1 : 0;
-        px[v] = make_float2(ax[u0], ax[u1]);
-        py[v] = make_float2(ay[u0], ay[u1]);
-        pz[v] = make_float2(az[u0], az[u1]);
-        pc[v] = make_float2(ac[u0], ac[u1]);
-      }
+      __syncwarp();
       for (uint32_t j0 = s0; j0 < s1; j0 += kTileGroup) {
         const float4* cg = sC + (j0 - s0);
         uint32_t gm = 0;  // bit g: some test of B vector j0 + g has r < 0
@@ -319,65 +370,54 @@ __device__ __forceinline__ void tile_round(const float4* __restrict__ sB,
               sg |= __float_as_uint(r.x) | __float_as_uint(r.y);
             }
           } else {
-            float r = b.w + ac[0];
-            r = fmaf(ax[0], b.x, r);
-            r = fmaf(ay[0], b.y, r);
-            r = fmaf(az[0], b.z, r);
+            float r = b.w + pc[0].x;
+            r = fmaf(px[0].x, b.x, r);
+            r = fmaf(py[0].x, b.y, r);
+            r = fmaf(pz[0].x, b.z, r);
             sg = __float_as_uint(r);
           }
           gm |= (sg >> 31) << g;
         }
         if (__any_sync(0xffffffffu, gm != 0u)) {
-          // the flagged vectors' tests again, one bit per candidate test
+          // the flagged vectors' tests again, one bit per candidate test ...
           uint32_t mask = 0;
           for (uint32_t m = gm; m != 0u; m &= m - 1u) {
             const int g = __ffs(m) - 1;
             const float4 b = cg[g];
 #pragma unroll
             for (int u = 0; u < KA; ++u) {
-              float r = b.w + ac[u];
-              r = fmaf(ax[u], b.x, r);
-              r = fmaf(ay[u], b.y, r);
-              r = fmaf(az[u], b.z, r);
+              const bool hi_half = u % 2 != 0;
+              const int v = u / 2;
+              float r = b.w + (hi_half ? pc[v].y : pc[v].x);
+              r = fmaf(hi_half ? px[v].y : px[v].x, b.x, r);
+              r = fmaf(hi_half ? py[v].y : py[v].x, b.y, r);
+              r = fmaf(hi_half ? pz[v].y : pz[v].x, b.z, r);
               mask |= (__float_as_uint(r) >> 31) << (g * KA + u);
             }
           }
-          // each lane walks its own candidates: the global-frame FP32 test
-          const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)__popc(mask));
-          for (int it = 0; it < nmax; ++it) {
+          // ... appended to the warp's queue as (B slot, A slot)
+          for (;;) {
             const bool act = mask != 0u;
-            const int bit = act ? __ffs(mask) - 1 : 0;
-            mask &= mask - 1u;
-            const int g = bit / KA, u = bit % KA;
-            const uint32_t j = j0 + (uint32_t)g;
-            const uint32_t qa = p0 + (uint32_t)u * 32 + lane;
-            const float4 av = sA[act ? qa : 0u];
-            const float4 b = sB[j];
-            const float dx = av.x - b.x, dy = av.y - b.y, dz = av.z - b.z;
-            float s2 = EQ4 ? fmaf(dx, dx, b.w - av.w) : dx * dx;
-            s2 = fmaf(dy, dy, s2);
-            s2 = fmaf(dz, dz, s2);
-            const bool hit = act && s2 <= lo32;
-            const bool band = act && !hit && s2 <= hi32;
-            uint32_t jb = 0;
-            if (act) {  // B entry of staged slot R0 + j
-              const uint32_t o = R0 + j;
-              int sgi = 0;
-#pragma unroll 1
-              while (sgi < 8 && s_off[sgi + 1] <= o) ++sgi;
-              jb = s_rb[sgi] + (o - s_off[sgi]);
+            const unsigned bal = __ballot_sync(0xffffffffu, act);
+            if (bal == 0u) break;
+            if (qfill + 32 > kTileQueue)
+              tile_drain<EQ4>(q, qfill, sB, sA, R0, s_rb, s_off, a0, lo32, hi32, lane, wrows,
+                              wband, sink, idxA, idxB);
+            if (act) {
+              const int bit = __ffs(mask) - 1;
+              mask &= mask - 1u;
+              const uint32_t j = j0 + (uint32_t)(bit / KA);
+              const uint32_t k = p0 + (uint32_t)(bit % KA) * 32 + lane;
+              q[qfill + __popc(bal & lanemask_lt())] = (j << 8) | k;
             }
-            wrows.add(hit, a0 + qa, jb);  // entries; tile_flush translates them
-            wband.add(band, a0 + qa, jb);
-            if (wrows.fill > kTileRowCap - 32)
-              tile_flush(wrows, sink.rows, sink.count, sink.cap, sink.err, idxA, idxB);
-            if (wband.fill > kTileBandCap - 32)
-              tile_flush(wband, sink.band, sink.band_count, sink.band_cap, sink.err, idxA, idxB);
+            qfill += __popc(bal);
           }
         }
       }
     }
   }
+  tile_drain<EQ4>(q, qfill, sB, sA, R0, s_rb, s_off, a0, lo32, hi32, lane, wrows, wband, sink,
+                  idxA, idxB);
 }
 
 // A chunk of a dense A cell against a window of the B ranges of its
@@ -519,12 +559,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // pairs hand the buffers over, so the copies for the next round overlap the
 // tests of the current one; the consumers only read the stage buffers.
 template <bool EQ4>
-__global__ void __launch_bounds__(kTileThreads + 32) k_pair_tile(const TileArgs ta,
+__global__ void __launch_bounds__(kTileThreads + 32, 3) k_pair_tile(const TileArgs ta,
                                                                  PairSink sink) {
   extern __shared__ __align__(128) unsigned char tile_smem[];
   float4* sB0 = reinterpret_cast<float4*>(tile_smem);        // 2 x kTileCap
   float4* sA0 = sB0 + 2 * kTileCap;                           // 2 x kTileChunkA
   float4* sC0 = sA0 + 2 * kTileChunkA;                        // kTileWarps x kTileConv
+  uint32_t* sQ0 = reinterpret_cast<uint32_t*>(sC0 + kTileWarps * kTileConv);  // x kTileQueue
   __shared__ uint2 s_rows[kTileWarps][kTileRowCap];
   __shared__ uint2 s_band[kTileWarps][kTileBandCap];
   __shared__ __align__(8) uint64_t full[2], empty[2];
@@ -650,19 +691,23 @@ __global__ void __launch_bounds__(kTileThreads + 32) k_pair_tile(const TileArgs 
     const float4* sB = sB0 + (size_t)b * kTileCap;
     const float4* sA = sA0 + (size_t)b * kTileChunkA;
     float4* sC = sC0 + (size_t)cw * kTileConv;
+    uint32_t* sQ = sQ0 + (size_t)cw * kTileQueue;
     const uint32_t nc = D.ncell;  // the class is the whole cell's; KA never above the chunk's need
     int ka = nc <= 32 ? 1 : (int)ta.ka[nc <= 64 ? 0 : (nc <= 256 ? 1 : 2)];
     if (na <= 32) ka = 1;
     else if (na <= 64 && ka > 2) ka = 2;
     if (ka == 1)
-      tile_round<1, EQ4>(sB, sA, sC, D.nr, D.nrp, D.R0, D.rb, D.off, D.a0, na, D.lo32, D.hi32,
-                         lane, cw, wrows, wband, sink, ta.idxA, ta.idxB, ntest);
+      tile_round<1, EQ4>(sB, sA, sC, sQ, D.nr, D.nrp, D.R0, D.rb, D.off, D.a0, na, D.lo32,
+                         D.hi32, ta.rho_max, lane, cw, wrows, wband, sink, ta.idxA, ta.idxB,
+                         ntest);
     else if (ka == 2)
-      tile_round<2, EQ4>(sB, sA, sC, D.nr, D.nrp, D.R0, D.rb, D.off, D.a0, na, D.lo32, D.hi32,
-                         lane, cw, wrows, wband, sink, ta.idxA, ta.idxB, ntest);
+      tile_round<2, EQ4>(sB, sA, sC, sQ, D.nr, D.nrp, D.R0, D.rb, D.off, D.a0, na, D.lo32,
+                         D.hi32, ta.rho_max, lane, cw, wrows, wband, sink, ta.idxA, ta.idxB,
+                         ntest);
     else
-      tile_round<4, EQ4>(sB, sA, sC, D.nr, D.nrp, D.R0, D.rb, D.off, D.a0, na, D.lo32, D.hi32,
-                         lane, cw, wrows, wband, sink, ta.idxA, ta.idxB, ntest);
+      tile_round<4, EQ4>(sB, sA, sC, sQ, D.nr, D.nrp, D.R0, D.rb, D.off, D.a0, na, D.lo32,
+                         D.hi32, ta.rho_max, lane, cw, wrows, wband, sink, ta.idxA, ta.idxB,
+                         ntest);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[b]);
   }
