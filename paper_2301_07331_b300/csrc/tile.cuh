@@ -287,12 +287,20 @@ __device__ __forceinline__ void tile_round(const float4* __restrict__ sB,
                                            const uint32_t* __restrict__ idxA,
                                            const uint32_t* __restrict__ idxB,
                                            unsigned long long& ntest) {
+  // this warp's groups: warp, warp + kTileWarps, ... (dealt out in turn, so
+  // that every warp's share spans all the neighbour ranges of the round and
+  // the candidates spread evenly over the warps)
   const uint32_t ngroups = nrp / kTileGroup;
-  const uint32_t gper = (ngroups + kTileWarps - 1) / kTileWarps;
-  const uint32_t jbeg = min(ngroups, warp * gper) * kTileGroup;
-  const uint32_t jend = min(ngroups, (warp + 1) * gper) * kTileGroup;
-  if (jbeg >= jend) return;
-  const uint32_t jreal = jend <= nr ? jend - jbeg : (nr > jbeg ? nr - jbeg : 0u);
+  if ((uint32_t)warp >= ngroups) return;
+  const uint32_t nmine = (ngroups - (uint32_t)warp + kTileWarps - 1) / kTileWarps;
+  uint32_t jreal = 0;  // real B vectors among them
+  {
+    const uint32_t full_groups = nr / kTileGroup, part = nr % kTileGroup;
+    jreal = (full_groups > (uint32_t)warp
+                 ? (full_groups - (uint32_t)warp + kTileWarps - 1) / kTileWarps : 0u) *
+            kTileGroup;
+    if (part && full_groups % kTileWarps == (uint32_t)warp) jreal += part;
+  }
   const float4 c = sA[0];
   float mA = 0.f;
   for (uint32_t k = lane; k < na; k += 32) {
@@ -335,12 +343,15 @@ __device__ __forceinline__ void tile_round(const float4* __restrict__ sB,
       }
       ntest += k < na ? jreal : 0u;
     }
-    for (uint32_t s0 = jbeg; s0 < jend; s0 += kTileConv) {
-      const uint32_t s1 = min(jend, s0 + kTileConv);
-      // B vectors s0 .. s1 to (b', |b'|^2 + w_b) in sC; padding slots to a
-      // vector no A source comes near
-      __syncwarp();  // (the previous slice's tests are done with sC)
-      for (uint32_t j = s0 + lane; j < s1; j += 32) {
+    constexpr uint32_t kConvGroups = kTileConv / kTileGroup;
+    for (uint32_t t0 = 0; t0 < nmine; t0 += kConvGroups) {
+      const uint32_t tn = min(nmine - t0, kConvGroups);
+      // the B vectors of groups t0 .. t0 + tn to (b', |b'|^2 + w_b) in sC;
+      // padding slots to a vector no A source comes near
+      __syncwarp();  // (the previous groups' tests are done with sC)
+      for (uint32_t i = lane; i < tn * kTileGroup; i += 32) {
+        const uint32_t j =
+            ((uint32_t)warp + (t0 + i / kTileGroup) * kTileWarps) * kTileGroup + i % kTileGroup;
         float4 v = make_float4(0.f, 0.f, 0.f, kFarW);
         if (j < nr) {
           const float4 b = sB[j];
@@ -348,11 +359,12 @@ __device__ __forceinline__ void tile_round(const float4* __restrict__ sB,
           const float n2 = fmaf(z, z, fmaf(y, y, x * x));
           v = make_float4(x, y, z, EQ4 ? n2 + b.w : n2);
         }
-        sC[j - s0] = v;
+        sC[i] = v;
       }
       __syncwarp();
-      for (uint32_t j0 = s0; j0 < s1; j0 += kTileGroup) {
-        const float4* cg = sC + (j0 - s0);
+      for (uint32_t t = 0; t < tn; ++t) {
+        const uint32_t j0 = ((uint32_t)warp + (t0 + t) * kTileWarps) * kTileGroup;
+        const float4* cg = sC + t * kTileGroup;
         uint32_t gm = 0;  // bit g: some test of B vector j0 + g has r < 0
 #pragma unroll
         for (int g = 0; g < kTileGroup; ++g) {
