@@ -708,11 +708,16 @@ def dense_line(args, hlc, synth, dev, stream, rank, world):
                            "sm_mhz": f_mhz,
                            "basis": "SMs x 128 FP32 lanes x SM clock / 6 FP32 operations per "
                                     "test (3 differences, 1 square, 2 fused multiply-adds)"},
-            "tile_kernel": {"kernel": "k_pair_tile (dense cells, B staged in shared memory by "
-                                      "bulk copies, packed f32x2 arithmetic)",
+            "tile_kernel": {"kernel": "k_pair_tile (dense cells, A and B staged in shared "
+                                      "memory by bulk copies; local-frame test, one add and "
+                                      "three FMAs per pair on packed f32x2)",
                             "ms": ms_tile, "tests": last["tile_tests"],
                             "tests_per_s": tile_tps,
-                            "frac_of_fp32_bound": (tile_tps / peak) if tile_tps else None},
+                            "frac_of_fp32_bound": (tile_tps / peak) if tile_tps else None,
+                            "frac_of_own_form_bound": (tile_tps / (peak * 6 / 4))
+                            if tile_tps else None,
+                            "own_form_basis": "SMs x 128 FP32 lanes x SM clock / 4 FMA-pipe "
+                                              "operations per test of the local form"},
             "tile_items": last["tile_items"], "tile_entries_a": last["tile_entries_a"],
             "matches": last["matches"], "clocks": clk}
 

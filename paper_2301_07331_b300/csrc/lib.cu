@@ -2431,7 +2431,7 @@ static uint64_t chunk_from_fit(const TransferFit& f) {
 template <typename Fn>
 static int stream_catalog(const hlc_catalog* X, double* dra[2], double* ddec[2], uint64_t* did[2],
                           void* stage[2], cudaStream_t ss[2], cudaEvent_t done[2], float* ms_h2d,
-                          uint64_t chunk, uint64_t led[4], Fn fn) {
+                          uint64_t chunk, uint64_t led[4], Fn fn, bool with_id = true) {
   cudaPointerAttributes at;
   bool pinned = X->n && cudaPointerGetAttributes(&at, X->ra_deg) == cudaSuccess &&
                 at.type == cudaMemoryTypeHost;
@@ -2458,7 +2458,7 @@ static int stream_catalog(const hlc_catalog* X, double* dra[2], double* ddec[2],
       char* h = (char*)stage[b];
       memcpy(h, sra, n * 8);
       memcpy(h + chunk * 8, sdec, n * 8);
-      memcpy(h + chunk * 16, sid, n * 8);
+      if (with_id) memcpy(h + chunk * 16, sid, n * 8);
       sra = (const double*)h;
       sdec = (const double*)(h + chunk * 8);
       sid = (const uint64_t*)(h + chunk * 16);
@@ -2470,11 +2470,11 @@ static int stream_catalog(const hlc_catalog* X, double* dra[2], double* ddec[2],
     cudaEventRecord(t0, ss[b]);
     HLC_CUDA(cudaMemcpyAsync(dra[b], sra, n * 8, cudaMemcpyHostToDevice, ss[b]));
     HLC_CUDA(cudaMemcpyAsync(ddec[b], sdec, n * 8, cudaMemcpyHostToDevice, ss[b]));
-    HLC_CUDA(cudaMemcpyAsync(did[b], sid, n * 8, cudaMemcpyHostToDevice, ss[b]));
-    led[0] += 3 * n * 8;  // (the transfer ledger: bytes and copies host to device)
-    led[1] += 3;
+    if (with_id) HLC_CUDA(cudaMemcpyAsync(did[b], sid, n * 8, cudaMemcpyHostToDevice, ss[b]));
+    led[0] += (with_id ? 3 : 2) * n * 8;  // (the transfer ledger: bytes and copies host to device)
+    led[1] += with_id ? 3 : 2;
     cudaEventRecord(t1, ss[b]);
-    HLC_TRY(fn(dra[b], ddec[b], did[b], n, ss[b], c, b));
+    HLC_TRY(fn(dra[b], ddec[b], with_id ? did[b] : nullptr, n, ss[b], c, b));
     HLC_CUDA(cudaEventRecord(done[b], ss[b]));
   }
   HLC_CUDA(cudaStreamSynchronize(ss[0]));
@@ -2710,7 +2710,8 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
                               r, d, n, Lf, Lc, side, K, cnt, err);
                           HLC_LAUNCH_CHECK();
                           return HLC_OK;
-                        });
+                        },
+                        false);  // (the counts need positions only)
   }
   std::vector<unsigned long long> hc(2 * nparts);
   if (rc == HLC_OK) {

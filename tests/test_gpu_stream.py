@@ -90,9 +90,10 @@ def test_streamed_plan_reports_its_copies_and_their_model_time():
     st = res["stats"]
     hlc.hlc_free(plan)
     n = A.n + B.n
-    # inputs go in twice (counting, bucketing), the bucketed runs out once and
-    # back in by group (B's halo copies included), the rows out
-    assert st["h2d_bytes"] >= 3 * 24 * n and st["d2h_bytes"] >= 24 * n
+    # positions go in for the counts (16 B a source), whole records for the
+    # bucketing (24 B), the bucketed runs out once and back in by group (B's
+    # halo copies included), the rows out
+    assert st["h2d_bytes"] >= (16 + 24 + 24) * n and st["d2h_bytes"] >= 24 * n
     assert st["h2d_copies"] >= 9 and st["d2h_copies"] >= 3
     assert (1 << 20) <= st["stream_chunk"] <= (8 << 20) and st["stream_chunk"] % (1 << 20) == 0
     assert st["ms_model_h2d"] > 0 and st["ms_model_d2h"] > 0
