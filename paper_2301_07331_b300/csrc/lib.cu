@@ -654,7 +654,8 @@ static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
         ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, slow, P->ctr + C_SLOW, P->dev_err,
         P->eq4 ? perr : nullptr);
     HLC_LAUNCH_CHECK();
-    k_prep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key);
+    k_prep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key,
+                                                          X.rec);
     HLC_LAUNCH_CHECK();
     ar.drop(slow);
   }
@@ -682,9 +683,12 @@ static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
   }
   HLC_ALLOC(ar, X.v32, float4, n + 1);
   if (n) {
-    k_payload32<<<grid_for(n, kThreads), kThreads, 0, st>>>(
-        X.rec, X.idx, n, X.v32, is_b ? nullptr : P->ctr + C_IDDIFF,
-        P->eq4 ? (is_b ? -1.f : 1.f) : 0.f, P->k9);
+    if (P->eq4)
+      k_payload32<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+          X.rec, X.idx, n, X.v32, is_b ? nullptr : P->ctr + C_IDDIFF, is_b ? -1.f : 1.f, P->k9);
+    else
+      k_payload32<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+          X.rec, X.idx, n, X.v32, is_b ? nullptr : P->ctr + C_IDDIFF);
     HLC_LAUNCH_CHECK();
   }
   cudaEventRecord(ev[2], st);
@@ -754,7 +758,7 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
         P->ctr + C_SLOW_A, P->dev_err, P->eq4 ? inA->err_arcsec : nullptr);
     HLC_LAUNCH_CHECK();
     k_prep_fallback<<<num_sms() * 4u, kThreads, 0, ks>>>(inA->ra_deg, inA->dec_deg, L, slow_a,
-                                                  P->ctr + C_SLOW_A, XA.key);
+                                                  P->ctr + C_SLOW_A, XA.key, XA.rec);
     HLC_LAUNCH_CHECK();
   }
   HLC_CUDA(cudaEventRecord(ea[1], ks));
@@ -764,7 +768,7 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
         P->ctr + C_SLOW, P->dev_err, P->eq4 ? inB->err_arcsec : nullptr);
     HLC_LAUNCH_CHECK();
     k_prep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(inB->ra_deg, inB->dec_deg, L, slow_b,
-                                                  P->ctr + C_SLOW, XB.key);
+                                                  P->ctr + C_SLOW, XB.key, XB.rec);
     HLC_LAUNCH_CHECK();
   }
   HLC_CUDA(cudaEventRecord(eb[1], st));
@@ -809,15 +813,23 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
   // 3. the payloads side by side (A's on ks), then B's offset table and dense cells
   HLC_CUDA(cudaStreamWaitEvent(ks, e_sorted, 0));
   if (na) {
-    k_payload32<<<grid_for(na, kThreads), kThreads, 0, ks>>>(
-        XA.rec, XA.idx, na, XA.v32, P->ctr + C_IDDIFF, P->eq4 ? 1.f : 0.f, P->k9);
+    if (P->eq4)
+      k_payload32<true><<<grid_for(na, kThreads), kThreads, 0, ks>>>(
+          XA.rec, XA.idx, na, XA.v32, P->ctr + C_IDDIFF, 1.f, P->k9);
+    else
+      k_payload32<false><<<grid_for(na, kThreads), kThreads, 0, ks>>>(
+          XA.rec, XA.idx, na, XA.v32, P->ctr + C_IDDIFF);
     HLC_LAUNCH_CHECK();
   }
   HLC_CUDA(cudaEventRecord(ea[2], ks));
   HLC_ALLOC(ar, XB.v32, float4, nb + 1);
   if (nb) {
-    k_payload32<<<grid_for(nb, kThreads), kThreads, 0, st>>>(
-        XB.rec, XB.idx, nb, XB.v32, nullptr, P->eq4 ? -1.f : 0.f, P->k9);
+    if (P->eq4)
+      k_payload32<true><<<grid_for(nb, kThreads), kThreads, 0, st>>>(
+          XB.rec, XB.idx, nb, XB.v32, nullptr, -1.f, P->k9);
+    else
+      k_payload32<false><<<grid_for(nb, kThreads), kThreads, 0, st>>>(
+          XB.rec, XB.idx, nb, XB.v32, nullptr);
     HLC_LAUNCH_CHECK();
   }
   HLC_CUDA(cudaEventRecord(eb[2], st));
@@ -896,7 +908,8 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
             ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, slow, P->ctr + C_SLOW,
             P->dev_err);
         HLC_LAUNCH_CHECK();
-        k_prep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW, X.key);
+        k_prep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW,
+                                                              X.key, X.rec);
         HLC_LAUNCH_CHECK();
         ar.drop(slow);
       } else {
@@ -977,7 +990,8 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
   } else {
     HLC_ALLOC(ar, X.v32, float4, m + 1);
     if (m) {
-      k_payload32<<<grid_for(m, kThreads), kThreads, 0, st>>>(X.rec, X.idx, m, X.v32, nullptr);
+      k_payload32<false><<<grid_for(m, kThreads), kThreads, 0, st>>>(X.rec, X.idx, m, X.v32,
+                                                                      nullptr);
       HLC_LAUNCH_CHECK();
     }
   }

@@ -87,8 +87,9 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
       if (FAST) {
         if (!(bits_finite(a) && bits_abs_le(d, 90.0))) {
           atomicOr(err, DERR_INPUT);
+        } else if (!bits_in_ra_range(a)) {
+          defer = true;  // RA outside [0, 360): the binary64 path normalises key and record
         } else {
-          if (!bits_in_ra_range(a)) a = c_norm_ra(a);
           FastDec fd = f_dec_part(split_f64(d));
           defer = !f_pix(split_f64(a), fd, order, K, &k);
         }
@@ -124,16 +125,19 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
   }
 }
 
-// Binary64 ang2pix of the queued sources.
+// Binary64 ang2pix of the queued sources (and, with rec, the record's RA
+// normalised to [0, 360)).
 __global__ void k_prep_fallback(const double* __restrict__ ra, const double* __restrict__ dec,
                                 int order, const uint32_t* __restrict__ slow,
                                 const unsigned long long* __restrict__ nslow,
-                                uint32_t* __restrict__ key) {
+                                uint32_t* __restrict__ key, SrcRec* __restrict__ rec = nullptr) {
   uint64_t ns = *nslow;
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns;
        q += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t i = slow[q];
-    key[i] = c_ang2pix(c_norm_ra(ra[i]), dec[i], order);
+    const double a = c_norm_ra(ra[i]);
+    key[i] = c_ang2pix(a, dec[i], order);
+    if (rec) rec[i].ra = a;
   }
 }
 
@@ -313,6 +317,7 @@ __global__ void k_payload64(const SrcRec* __restrict__ rec, const uint32_t* __re
 // Eq. 4: w = wsign * rho with rho = k9 e^2, k9 = 9 (pi/648000)^2, the
 // source's share of the pair's squared radius in radians (+rho for A, -rho
 // for B, so that b.w - a.w = -(rho_a + rho_b)); otherwise w = 0.
+template <bool EQ4>
 __global__ void k_payload32(const SrcRec* __restrict__ rec, const uint32_t* __restrict__ idx,
                             uint64_t m, float4* __restrict__ v,
                             unsigned long long* __restrict__ iddiff, float wsign = 0.f,
@@ -324,7 +329,7 @@ __global__ void k_payload32(const SrcRec* __restrict__ rec, const uint32_t* __re
     SrcRec r = rec[idx[e]];
     float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
     if (bits_finite(r.ra) && bits_abs_le(r.dec, 90.0)) u = fp32_unitvec(r.ra, r.dec);
-    if (wsign != 0.f) {
+    if (EQ4) {  // (a compile-time branch: the single-radius form runs no FP64 instruction)
       const double er = rec_err(r);
       u.w = wsign * (float)(er * er * k9);
     }
