@@ -748,27 +748,48 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
   HLC_ALLOC(ar, slow_a, uint32_t, na + 1);
   HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st));
   HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW_A, 0, 8, st));
+  // the sort's scratch, whose digit histograms the preps count as they
+  // write the keys (when both catalogues need sorting: the one-sort form)
+  void *scrb = nullptr, *scra = nullptr;
+  const bool both = nb > 1 && na > 1;
+  if (nb > 1) {
+    scrb = ar.get(sort_scratch_bytes(nb, npass));
+    if (!scrb) return HLC_ENOMEM;
+  }
+  if (na > 1) {
+    scra = ar.get(sort_scratch_bytes(na, npass));
+    if (!scra) return HLC_ENOMEM;
+  }
+  if (both) {
+    HLC_CUDA(cudaMemsetAsync(scrb, 0, (size_t)npass * 256 * 4, st));
+    HLC_CUDA(cudaMemsetAsync(scra, 0, (size_t)npass * 256 * 4, st));
+  }
+  uint32_t* hist_b = both ? (uint32_t*)scrb : nullptr;
+  uint32_t* hist_a = both ? (uint32_t*)scra : nullptr;
   HLC_CUDA(cudaEventRecord(eb[0], st));
   HLC_CUDA(cudaEventRecord(ea[0], st));
   HLC_CUDA(cudaStreamWaitEvent(ks, ea[0], 0));
   // 1. the two preps, side by side
   if (na) {
-    k_prep_keys<true><<<grid_for(na, kThreads), kThreads, 0, ks>>>(
+    k_prep_keys<true><<<grid_for(na, kThreads, num_sms() * 8u), kThreads, 0, ks>>>(
         inA->ra_deg, inA->dec_deg, inA->id, na, L, pix_const(L), XA.key, XA.idx, XA.rec, slow_a,
-        P->ctr + C_SLOW_A, P->dev_err, P->eq4 ? inA->err_arcsec : nullptr);
+        P->ctr + C_SLOW_A, P->dev_err, P->eq4 ? inA->err_arcsec : nullptr, hist_a, shift,
+        npass);
     HLC_LAUNCH_CHECK();
     k_prep_fallback<<<num_sms() * 4u, kThreads, 0, ks>>>(inA->ra_deg, inA->dec_deg, L, slow_a,
-                                                  P->ctr + C_SLOW_A, XA.key, XA.rec);
+                                                  P->ctr + C_SLOW_A, XA.key, XA.rec, hist_a,
+                                                  shift, npass);
     HLC_LAUNCH_CHECK();
   }
   HLC_CUDA(cudaEventRecord(ea[1], ks));
   if (nb) {
-    k_prep_keys<true><<<grid_for(nb, kThreads), kThreads, 0, st>>>(
+    k_prep_keys<true><<<grid_for(nb, kThreads, num_sms() * 8u), kThreads, 0, st>>>(
         inB->ra_deg, inB->dec_deg, inB->id, nb, L, pix_const(L), XB.key, XB.idx, XB.rec, slow_b,
-        P->ctr + C_SLOW, P->dev_err, P->eq4 ? inB->err_arcsec : nullptr);
+        P->ctr + C_SLOW, P->dev_err, P->eq4 ? inB->err_arcsec : nullptr, hist_b, shift, npass);
     HLC_LAUNCH_CHECK();
     k_prep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(inB->ra_deg, inB->dec_deg, L, slow_b,
-                                                  P->ctr + C_SLOW, XB.key, XB.rec);
+                                                  P->ctr + C_SLOW, XB.key, XB.rec, hist_b, shift,
+                                                  npass);
     HLC_LAUNCH_CHECK();
   }
   HLC_CUDA(cudaEventRecord(eb[1], st));
@@ -777,18 +798,13 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
   ar.drop(slow_b);
   ar.drop(slow_a);
   uint32_t *tkb = nullptr, *tvb = nullptr, *tka = nullptr, *tva = nullptr;
-  void *scrb = nullptr, *scra = nullptr;
   if (nb > 1) {
     HLC_ALLOC(ar, tkb, uint32_t, nb);
     HLC_ALLOC(ar, tvb, uint32_t, nb);
-    scrb = ar.get(sort_scratch_bytes(nb, npass));
-    if (!scrb) return HLC_ENOMEM;
   }
   if (na > 1) {
     HLC_ALLOC(ar, tka, uint32_t, na);
     HLC_ALLOC(ar, tva, uint32_t, na);
-    scra = ar.get(sort_scratch_bytes(na, npass));
-    if (!scra) return HLC_ENOMEM;
   }
   {
     bool in_tmp = false;
@@ -796,7 +812,7 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
     cudaEvent_t* pev = P->events ? P->ev + 7 : nullptr;
     HLC_TRY(radix_sort_pairs2<uint32_t>(XB.key, XB.idx, tkb, tvb, nb, scrb, XA.key, XA.idx, tka,
                                         tva, na, scra, bits, P->dev_err, st, shift, &in_tmp, pev,
-                                        &np));
+                                        &np, both));
     P->sort_passes += np;
     P->sort_entries += (uint64_t)np * ((nb > 1 && na > 1) ? nb + na : (nb > 1 ? nb : na));
     if (pev && np) P->sort_timed[0] = true;

@@ -69,18 +69,31 @@ constexpr uint32_t kSparseCell = HLC_SPARSE_CELL;
 // evaluation with binary64 fallback (same pixels).
 // (FAST: sources the guarded estimate cannot decide are queued and finished
 // by k_prep_fallback, so that warps do not diverge into the binary64 path.)
+// hist (FAST only; null: none): the radix sort's digit histograms of the
+// keys, hist_np passes of 8 bits from bit hist_lo, counted here for every key
+// this kernel writes for good (the queued ones are counted by the fallback),
+// so the sort needs no pass of its own over the keys.
+constexpr int kPrepHistPasses = 4;
 template <bool FAST>
 __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restrict__ dec,
                             const uint64_t* __restrict__ id, uint64_t n, int order, PixConst K,
                             uint32_t* __restrict__ key, uint32_t* __restrict__ idx,
                             SrcRec* __restrict__ rec, uint32_t* __restrict__ slow,
                             unsigned long long* __restrict__ nslow, int* __restrict__ err,
-                            const double* __restrict__ perr = nullptr) {
+                            const double* __restrict__ perr = nullptr,
+                            uint32_t* __restrict__ hist = nullptr, int hist_lo = 0,
+                            int hist_np = 0) {
+  __shared__ uint32_t sh[kPrepHistPasses][256];
+  if (FAST && hist) {
+    for (int t = threadIdx.x; t < kPrepHistPasses * 256; t += blockDim.x) (&sh[0][0])[t] = 0u;
+    __syncthreads();
+  }
   for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n;
        i0 += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t i = i0 + threadIdx.x;
     bool live = i < n;
     bool defer = false;
+    uint32_t kfin = 0;  // the key written
     if (live) {
       double a = ra[i], d = dec[i];
       uint32_t k = 0;
@@ -102,6 +115,7 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
         }
       }
       key[i] = k;
+      kfin = k;
       if (idx) idx[i] = (uint32_t)i;
       if (rec) {
         SrcRec r;
@@ -121,23 +135,38 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
         base = __shfl_sync(0xffffffffu, base, __ffs(b) - 1);
         if (defer) slow[base + __popc(b & lanemask_lt())] = (uint32_t)i;
       }
+      if (hist && live && !defer)  // (an invalid source keeps key 0 and counts as such)
+        for (int p = 0; p < hist_np; ++p)
+          atomicAdd(&sh[p][(kfin >> (hist_lo + 8 * p)) & 255u], 1u);
+    }
+  }
+  if (FAST && hist) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < hist_np * 256; t += blockDim.x) {
+      const uint32_t c = (&sh[0][0])[t];
+      if (c) atomicAdd(hist + t, c);
     }
   }
 }
 
 // Binary64 ang2pix of the queued sources (and, with rec, the record's RA
-// normalised to [0, 360)).
+// normalised to [0, 360); with hist, their keys' digits counted).
 __global__ void k_prep_fallback(const double* __restrict__ ra, const double* __restrict__ dec,
                                 int order, const uint32_t* __restrict__ slow,
                                 const unsigned long long* __restrict__ nslow,
-                                uint32_t* __restrict__ key, SrcRec* __restrict__ rec = nullptr) {
+                                uint32_t* __restrict__ key, SrcRec* __restrict__ rec = nullptr,
+                                uint32_t* __restrict__ hist = nullptr, int hist_lo = 0,
+                                int hist_np = 0) {
   uint64_t ns = *nslow;
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns;
        q += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t i = slow[q];
     const double a = c_norm_ra(ra[i]);
-    key[i] = c_ang2pix(a, dec[i], order);
+    const uint32_t k = c_ang2pix(a, dec[i], order);
+    key[i] = k;
     if (rec) rec[i].ra = a;
+    for (int p = 0; hist && p < hist_np; ++p)
+      atomicAdd(hist + p * 256 + ((k >> (hist_lo + 8 * p)) & 255u), 1u);
   }
 }
 

@@ -368,11 +368,15 @@ int radix_sort_pairs(K* keys, uint32_t* vals, K* tmp_keys, uint32_t* tmp_vals, u
 // in_tmp set, an odd number of passes leaves both results in the temporary
 // buffers and *in_tmp says so (never when only one array needs sorting).
 // Either array may be empty.
+// hist_ready: each scratch's digit histograms (npass x 256 counts at its
+// start) were already counted by the producer of the keys (the prep kernels
+// count while they write the keys), so the histogram pass is skipped.
 template <typename K>
 int radix_sort_pairs2(K* keys0, uint32_t* vals0, K* tk0, uint32_t* tv0, uint64_t n0, void* scr0,
                       K* keys1, uint32_t* vals1, K* tk1, uint32_t* tv1, uint64_t n1, void* scr1,
                       int key_bits, int* dev_err, cudaStream_t st, int bit_lo, bool* in_tmp,
-                      cudaEvent_t* pass_ev = nullptr, int* npass_out = nullptr) {
+                      cudaEvent_t* pass_ev = nullptr, int* npass_out = nullptr,
+                      bool hist_ready = false) {
   if (in_tmp) *in_tmp = false;
   if (n0 <= 1 || n1 <= 1) {  // one array (or none) needs sorting: the single form,
     if (npass_out) *npass_out = 0;  // its result copied back in place
@@ -409,11 +413,13 @@ int radix_sort_pairs2(K* keys0, uint32_t* vals0, K* tk0, uint32_t* tv0, uint64_t
     uint32_t* hist = (uint32_t*)q.sp;
     uint32_t* offs = (uint32_t*)(q.sp + 8192);
     unsigned long long* lb = (unsigned long long*)(q.sp + kSortLookbackOffset);
-    HLC_CUDA(cudaMemsetAsync(hist, 0, (size_t)npass * rs::kRadix * 4, st));
     HLC_CUDA(cudaMemsetAsync(lb, 0, (size_t)npass * q.tiles * rs::kRadix * 8, st));
-    rs::k_digit_hist<K><<<grid_for(q.n, rs::kBlock, num_sms() * 8u), rs::kBlock, 0, st>>>(
-        q.keys, q.n, npass, bit_lo, hist);
-    HLC_LAUNCH_CHECK();
+    if (!hist_ready) {
+      HLC_CUDA(cudaMemsetAsync(hist, 0, (size_t)npass * rs::kRadix * 4, st));
+      rs::k_digit_hist<K><<<grid_for(q.n, rs::kBlock, num_sms() * 8u), rs::kBlock, 0, st>>>(
+          q.keys, q.n, npass, bit_lo, hist);
+      HLC_LAUNCH_CHECK();
+    }
     rs::k_hist_scan<<<npass, rs::kBlock, 0, st>>>(hist, offs);
     HLC_LAUNCH_CHECK();
   }
