@@ -749,7 +749,8 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
   HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st));
   HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW_A, 0, 8, st));
   // the sort's scratch, whose digit histograms the preps count as they
-  // write the keys (when both catalogues need sorting: the one-sort form)
+  // write the keys (when both catalogues need sorting: the one-sort form,
+  // whose first pass also makes the identity values the preps then skip)
   void *scrb = nullptr, *scra = nullptr;
   const bool both = nb > 1 && na > 1;
   if (nb > 1) {
@@ -772,9 +773,9 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
   // 1. the two preps, side by side
   if (na) {
     k_prep_keys<true><<<grid_for(na, kThreads, num_sms() * 8u), kThreads, 0, ks>>>(
-        inA->ra_deg, inA->dec_deg, inA->id, na, L, pix_const(L), XA.key, XA.idx, XA.rec, slow_a,
-        P->ctr + C_SLOW_A, P->dev_err, P->eq4 ? inA->err_arcsec : nullptr, hist_a, shift,
-        npass);
+        inA->ra_deg, inA->dec_deg, inA->id, na, L, pix_const(L), XA.key,
+        both ? nullptr : XA.idx, XA.rec, slow_a, P->ctr + C_SLOW_A, P->dev_err,
+        P->eq4 ? inA->err_arcsec : nullptr, hist_a, shift, npass);
     HLC_LAUNCH_CHECK();
     k_prep_fallback<<<num_sms() * 4u, kThreads, 0, ks>>>(inA->ra_deg, inA->dec_deg, L, slow_a,
                                                   P->ctr + C_SLOW_A, XA.key, XA.rec, hist_a,
@@ -784,8 +785,9 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
   HLC_CUDA(cudaEventRecord(ea[1], ks));
   if (nb) {
     k_prep_keys<true><<<grid_for(nb, kThreads, num_sms() * 8u), kThreads, 0, st>>>(
-        inB->ra_deg, inB->dec_deg, inB->id, nb, L, pix_const(L), XB.key, XB.idx, XB.rec, slow_b,
-        P->ctr + C_SLOW, P->dev_err, P->eq4 ? inB->err_arcsec : nullptr, hist_b, shift, npass);
+        inB->ra_deg, inB->dec_deg, inB->id, nb, L, pix_const(L), XB.key,
+        both ? nullptr : XB.idx, XB.rec, slow_b, P->ctr + C_SLOW, P->dev_err,
+        P->eq4 ? inB->err_arcsec : nullptr, hist_b, shift, npass);
     HLC_LAUNCH_CHECK();
     k_prep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(inB->ra_deg, inB->dec_deg, L, slow_b,
                                                   P->ctr + C_SLOW, XB.key, XB.rec, hist_b, shift,
@@ -812,7 +814,7 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
     cudaEvent_t* pev = P->events ? P->ev + 7 : nullptr;
     HLC_TRY(radix_sort_pairs2<uint32_t>(XB.key, XB.idx, tkb, tvb, nb, scrb, XA.key, XA.idx, tka,
                                         tva, na, scra, bits, P->dev_err, st, shift, &in_tmp, pev,
-                                        &np, both));
+                                        &np, both, both));
     P->sort_passes += np;
     P->sort_entries += (uint64_t)np * ((nb > 1 && na > 1) ? nb + na : (nb > 1 ? nb : na));
     if (pev && np) P->sort_timed[0] = true;

@@ -169,7 +169,7 @@ __device__ __forceinline__ void sweep_tile(SweepSmem<K>& S, const int t, const i
                                            const uint32_t* __restrict__ goff,
                                            unsigned long long* __restrict__ lookback,
                                            const uint32_t rem, const uint32_t wo, int shift,
-                                           int* __restrict__ err) {
+                                           int* __restrict__ err, const uint32_t vbase) {
 #define HLC_IN_TILE(o) (FULL || (o) < rem)
   K k[kIpt];
 #pragma unroll
@@ -234,7 +234,7 @@ __device__ __forceinline__ void sweep_tile(SweepSmem<K>& S, const int t, const i
       uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
       uint32_t pos = S.dstart[d] + S.whist[warp][d] + r[i];
       S.keys[pos] = k[i];
-      S.vals[pos] = vt[o];
+      S.vals[pos] = vt ? vt[o] : vbase + o;  // (null: the values are the positions)
     }
   }
   __syncthreads();
@@ -275,14 +275,14 @@ __global__ void __launch_bounds__(kBlock, sizeof(K) == 8 ? 3 : 4) k_onesweep(
   const uint32_t rem = (uint32_t)(n - base < (uint64_t)kTile ? n - base : (uint64_t)kTile);
   const uint32_t wo = (uint32_t)warp * (kIpt * 32) + (uint32_t)lane;
   const K* __restrict__ kt = kin + base;
-  const uint32_t* __restrict__ vt = vin + base;
+  const uint32_t* __restrict__ vt = vin ? vin + base : nullptr;
 
   if (rem == (uint32_t)kTile)
     sweep_tile<K, true>(S, t, lane, warp, tile, kt, vt, kout, vout, goff, lookback, rem, wo, shift,
-                        err);
+                        err, (uint32_t)base);
   else
     sweep_tile<K, false>(S, t, lane, warp, tile, kt, vt, kout, vout, goff, lookback, rem, wo,
-                         shift, err);
+                         shift, err, (uint32_t)base);
 }
 
 }  // namespace rs
@@ -371,12 +371,15 @@ int radix_sort_pairs(K* keys, uint32_t* vals, K* tmp_keys, uint32_t* tmp_vals, u
 // hist_ready: each scratch's digit histograms (npass x 256 counts at its
 // start) were already counted by the producer of the keys (the prep kernels
 // count while they write the keys), so the histogram pass is skipped.
+// vals_identity: the values are the positions 0, 1, ... (vals0/vals1 are not
+// read, only used as buffers), so the first pass makes them instead of
+// loading them.
 template <typename K>
 int radix_sort_pairs2(K* keys0, uint32_t* vals0, K* tk0, uint32_t* tv0, uint64_t n0, void* scr0,
                       K* keys1, uint32_t* vals1, K* tk1, uint32_t* tv1, uint64_t n1, void* scr1,
                       int key_bits, int* dev_err, cudaStream_t st, int bit_lo, bool* in_tmp,
                       cudaEvent_t* pass_ev = nullptr, int* npass_out = nullptr,
-                      bool hist_ready = false) {
+                      bool hist_ready = false, bool vals_identity = false) {
   if (in_tmp) *in_tmp = false;
   if (n0 <= 1 || n1 <= 1) {  // one array (or none) needs sorting: the single form,
     if (npass_out) *npass_out = 0;  // its result copied back in place
@@ -435,7 +438,8 @@ int radix_sort_pairs2(K* keys0, uint32_t* vals0, K* tk0, uint32_t* tv0, uint64_t
   for (int p = 0; p < npass; ++p) {
     rs::SweepDesc<K> d[2];
     for (int i = 0; i < 2; ++i)
-      d[i] = rs::SweepDesc<K>{ka[i], va[i], kb[i], vb[i], sd[i].n,
+      d[i] = rs::SweepDesc<K>{ka[i], (vals_identity && p == 0) ? nullptr : va[i], kb[i], vb[i],
+                              sd[i].n,
                               (uint32_t*)(sd[i].sp + 8192) + p * rs::kRadix,
                               (unsigned long long*)(sd[i].sp + kSortLookbackOffset) +
                                   (size_t)p * sd[i].tiles * rs::kRadix,
