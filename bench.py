@@ -283,16 +283,19 @@ def run_hlc(args):
     npass = last["sort_passes"]
     ms_passes = mean("ms_sort_passes", stats)
     if npass and ms_passes > 0:
-        # each pass reads and writes a 4-byte key and a 4-byte value per entry
-        # (a launch may cover both catalogues: sort_entries counts per launch)
-        per_pass = 16 * last["sort_entries"] / npass
+        # each pass reads and writes a 4-byte key and a 4-byte value per entry,
+        # the one-sort form's first makes its values (the library's sort_bytes;
+        # a launch may cover both catalogues)
+        per_pass = last["sort_bytes"] / npass
         gbs = per_pass * npass / (ms_passes / 1e3) / 1e9
         tr = _traffic("k_onesweep", wkey)
         roofline = {"kernel": "k_onesweep (cell-key radix sort digit pass)", "bound": "hbm",
                     "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(gbs / peak, 4), "traffic": tr, "peak_source": peak_src,
                     "bytes_per_launch": int(per_pass),
-                    "bytes_basis": "16 B per entry per pass (key and value read and written)",
+                    "bytes_basis": "16 B per entry per pass (key and value read and "
+                                   "written), 12 B in a first pass that makes its values "
+                                   "from the positions; per launch: the mean over the passes",
                     "launches_per_step": npass, "ms_per_launch": ms_passes / npass,
                     "timing": "CUDA events around the digit passes; with device inputs "
                               "one launch per pass sorts both catalogues"}

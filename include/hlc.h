@@ -238,8 +238,13 @@ typedef struct {
   uint64_t tile_tests;             /*   and the pair tests it ran */
   float ms_plan_presort;           /* FP32 complete form with device inputs:
                                       from the plan's start to the first digit
-                                      pass (both preps, side by side, and the
-                                      digit histograms); else 0 */
+                                      pass (both preps, side by side); else 0 */
+  uint64_t sort_bytes;             /* FP32 complete form: algorithmic bytes of
+                                      the timed digit passes, summed over the
+                                      launches (a 4-byte key and a 4-byte value
+                                      read and written per entry and pass; the
+                                      one-sort form's first pass makes its
+                                      values and reads 12 bytes) */
 } hlc_stats;
 
 typedef struct hlc_plan_s hlc_plan_t;
@@ -270,6 +275,13 @@ const char* hlc_last_error(void);
 
 /* Library version string. */
 const char* hlc_version(void);
+
+/* sizeof of the public structs, for bindings to check their layouts against:
+ * out[0..7] = hlc_catalog, hlc_tune, hlc_tune_trial, hlc_tune_report,
+ * hlc_params, hlc_result, hlc_stats, hlc_transfer_fit.  Writes min(n, 8)
+ * entries and returns 8 (the number of structs); out may be NULL when n is 0.
+ * Host only; never fails. */
+int hlc_abi_sizes(size_t* out, int n);
 
 /* The binary64 polynomial coefficients this library uses for sin/cos in
  * degrees: sin_c[k] = (-1)^k (pi/180)^(2k+1)/(2k+1)! and

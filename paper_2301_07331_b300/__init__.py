@@ -113,7 +113,7 @@ class Stats(C.Structure):
                                           "d2h_copies")] + [
                 ("ms_model_h2d", C.c_float), ("ms_model_d2h", C.c_float),
                 ("stream_chunk", C.c_uint64), ("ms_tile", C.c_float), ("tile_tests", C.c_uint64),
-                ("ms_plan_presort", C.c_float)]
+                ("ms_plan_presort", C.c_float), ("sort_bytes", C.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -145,6 +145,8 @@ def lib():
     L.hlc_result_to_host.argtypes = [P, P, P, P, P]
     L.hlc_last_error.restype = C.c_char_p
     L.hlc_version.restype = C.c_char_p
+    L.hlc_abi_sizes.argtypes = [C.POINTER(C.c_size_t), C.c_int]
+    L.hlc_abi_sizes.restype = C.c_int
     L.hlc_canonical_coefficients.argtypes = [P, P]
     L.hlc_ang2pix.argtypes = [P, P, u64, i32, i32, P, P]
     L.hlc_neighbours.argtypes = [P, u64, i32, P, P]

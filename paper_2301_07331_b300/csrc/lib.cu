@@ -346,6 +346,7 @@ struct hlc_plan_s {
   bool table_buckets = false;  // FP32 complete mode: entries bucketed by table cell
   uint32_t sort_passes = 0;    // radix passes of the table-cell sorts (ev 7-8: B, 9-10: A)
   uint64_t sort_entries = 0;   // entries those passes moved, summed over the launches
+  uint64_t sort_bytes = 0;     // and their algorithmic bytes
   bool sort_timed[2] = {false, false};
   unsigned long long plan_launches = 0;
   cudaEvent_t ev[12] = {};
@@ -673,6 +674,7 @@ static int bucket_catalog(hlc_plan_t* P, CatDev& X, bool is_b, const double* ra,
     P->sort_passes += np;
     if (pev) P->sort_timed[is_b ? 0 : 1] = true;
     P->sort_entries += (uint64_t)np * n;
+    P->sort_bytes += 16ull * np * n;
     ar.drop(scr);
     if (in_tmp) {
       std::swap(X.key, tk);
@@ -816,7 +818,10 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
                                         tva, na, scra, bits, P->dev_err, st, shift, &in_tmp, pev,
                                         &np, both, both));
     P->sort_passes += np;
-    P->sort_entries += (uint64_t)np * ((nb > 1 && na > 1) ? nb + na : (nb > 1 ? nb : na));
+    const uint64_t ne = (nb > 1 && na > 1) ? nb + na : (nb > 1 ? nb : na);
+    P->sort_entries += (uint64_t)np * ne;
+    // (the one-sort form's first pass makes its values: 12 bytes, not 16)
+    P->sort_bytes += (16ull * np - (both && np ? 4ull : 0ull)) * ne;
     if (pev && np) P->sort_timed[0] = true;
     if (in_tmp) {
       std::swap(XB.key, tkb);
@@ -1340,6 +1345,7 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   P->stats.ms_index = t[4] + t[5];
   P->stats.sort_passes = P->sort_passes;
   P->stats.sort_entries = P->sort_entries;
+  P->stats.sort_bytes = P->sort_bytes;
   for (int i = 0; i < 2; ++i)
     if (P->sort_timed[i]) P->stats.ms_sort_passes += ev_ms(P, 7 + 2 * i, 8 + 2 * i);
   if (side && P->sort_timed[0]) P->stats.ms_plan_presort = ev_ms(P, 0, 7);
@@ -3115,6 +3121,14 @@ extern "C" {
 
 const char* hlc_last_error(void) { return g_msg; }
 const char* hlc_version(void) { return "hlc-b300 0.1 (sm_103a)"; }
+
+extern "C" int hlc_abi_sizes(size_t* out, int n) {
+  const size_t sz[8] = {sizeof(hlc_catalog), sizeof(hlc_tune), sizeof(hlc_tune_trial),
+                        sizeof(hlc_tune_report), sizeof(hlc_params), sizeof(hlc_result),
+                        sizeof(hlc_stats), sizeof(hlc_transfer_fit)};
+  for (int i = 0; out && i < n && i < 8; ++i) out[i] = sz[i];
+  return 8;
+}
 
 int hlc_canonical_coefficients(double sin_c[10], double cos_c[11]) {
   if (!sin_c || !cos_c) {

@@ -32,6 +32,19 @@ def test_library_exports_every_declared_symbol():
         assert ctypes.cast(getattr(L, name), ctypes.c_void_p).value
 
 
+def test_binding_structs_match_the_library_layouts():
+    """Every ctypes struct of the binding has the size the library was built
+    with (a field added on one side only would shift the others)."""
+    L = hlc.lib()
+    out = (ctypes.c_size_t * 8)()
+    assert L.hlc_abi_sizes(out, 8) == 8
+    mine = [hlc.Catalog, hlc.Tune, hlc.TuneTrial, hlc.TuneReport, hlc.Params, hlc.Result,
+            hlc.Stats, hlc.TransferFit]
+    for s, cls in zip(out, mine):
+        assert s == ctypes.sizeof(cls), (cls.__name__, s, ctypes.sizeof(cls))
+    assert L.hlc_abi_sizes(None, 0) == 8
+
+
 def test_version_and_error_string():
     assert "sm_103a" in hlc.version()
     assert hlc.lib().hlc_last_error() is not None
