@@ -441,15 +441,15 @@ def run_hlc(args):
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture, with
 # the digest of the kernel sources it was taken on; a changed source voids it.
 TRAFFIC = {
-    # one launch each, captured on the default line's workload (full sky
-    # 10M x 10M, complete mode, FP32 form) with
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum:
-    # a sort pass (both catalogues in one launch): 160,439,040 B read +
-    # 122,616,832 B written
-    "k_onesweep": {"bytes_per_launch": 283055872, "sources": "4f1f57c20d9897a5",
+    # captured on the default line's workload (full sky 10M x 10M, complete
+    # mode, FP32 form) with ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum:
+    # the three sort passes of a step (both catalogues per launch), read +
+    # written: 80,632,832 + 120,901,376 (the first pass makes its values),
+    # 161,055,744 + 120,093,952 and 160,616,960 + 119,799,296 B; their mean
+    "k_onesweep": {"bytes_per_launch": 254366720, "sources": "5333daf1bd4fd395",
                    "files": ("sort.cuh", "common.cuh")},
-    # the pair test: 495,248,128 B read + 40,940,544 B written
-    "k_pair<1,0,0,1>": {"bytes_per_launch": 536188672, "sources": "c091b7e8428702ba",
+    # the pair test: 495,089,664 B read + 42,944,768 B written
+    "k_pair<1,0,0,1>": {"bytes_per_launch": 538034432, "sources": "642f2488d4f0e024",
                         "files": ("match.cuh", "canon.cuh", "index.cuh", "learned.cuh",
                                   "common.cuh", "fp32.cuh", "fastpix.cuh")},
 }
