@@ -857,9 +857,13 @@ def run_batched(args):
     spec = [{"A": j.A, "B": j.B, "radius_arcsec": j.r_arcsec} for j in jobs]
     total = sum(j.A.ra.numel() + j.B.ra.numel() for j in jobs)
     # the autotuner (form 2) on a sample of these jobs, outside the timed region
-    t0 = time.perf_counter()
-    tune, report = hlc.hlc_autotune(spec, sample_jobs=args.tune_sample, stream=stream)
-    report["seconds"] = time.perf_counter() - t0
+    # (--tune-sample 0: not run; the library's rule is timed twice)
+    if args.tune_sample > 0:
+        t0 = time.perf_counter()
+        tune, report = hlc.hlc_autotune(spec, sample_jobs=args.tune_sample, stream=stream)
+        report["seconds"] = time.perf_counter() - t0
+    else:
+        tune, report = None, {"skipped": "--tune-sample 0"}
 
     def batched(tn=None):
         plan = hlc.hlc_plan_batched(spec, stream=stream, tune=tn)
@@ -1084,7 +1088,7 @@ def main():
     ap.add_argument("--jobs", type=int, default=4096, help="batched: number of jobs")
     ap.add_argument("--scale", type=float, default=1.0, help="batched: source-count scale")
     ap.add_argument("--tune-sample", type=int, default=1024,
-                    help="batched: jobs in the autotuner's calibration sample")
+                    help="batched: jobs in the autotuner's calibration sample (0: skip it)")
     ap.add_argument("--budget-gb", type=int, default=16, help="streamed: device budget")
     ap.add_argument("--n", type=int, default=0, help="A sources (0: the workload's size)")
     ap.add_argument("--sizes", default="1000000,4000000,10000000,20000000",

@@ -157,7 +157,15 @@ __global__ void k_prep_fallback(const double* __restrict__ ra, const double* __r
                                 uint32_t* __restrict__ key, SrcRec* __restrict__ rec = nullptr,
                                 uint32_t* __restrict__ hist = nullptr, int hist_lo = 0,
                                 int hist_np = 0) {
-  uint64_t ns = *nslow;
+  __shared__ uint32_t sh[kPrepHistPasses][256];
+  const uint64_t ns = *nslow;
+  // (blocks beyond the queue's need return at once; the rest count in
+  // shared memory and flush once)
+  if ((uint64_t)blockIdx.x * blockDim.x >= ns) return;
+  if (hist) {
+    for (int t = threadIdx.x; t < kPrepHistPasses * 256; t += blockDim.x) (&sh[0][0])[t] = 0u;
+    __syncthreads();
+  }
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns;
        q += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t i = slow[q];
@@ -166,7 +174,14 @@ __global__ void k_prep_fallback(const double* __restrict__ ra, const double* __r
     key[i] = k;
     if (rec) rec[i].ra = a;
     for (int p = 0; hist && p < hist_np; ++p)
-      atomicAdd(hist + p * 256 + ((k >> (hist_lo + 8 * p)) & 255u), 1u);
+      atomicAdd(&sh[p][(k >> (hist_lo + 8 * p)) & 255u], 1u);
+  }
+  if (hist) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < hist_np * 256; t += blockDim.x) {
+      const uint32_t c = (&sh[0][0])[t];
+      if (c) atomicAdd(hist + t, c);
+    }
   }
 }
 
