@@ -2766,8 +2766,10 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
   // groups of consecutive coarse cells that fit the budget
   uint64_t budget = p->device_mem_budget;
   uint64_t fixed = 6 * chunk * 8 + 2 * nparts * 8 + (64ull << 20);
-  uint64_t cap_entries =
-      std::max<uint64_t>(4096, (budget > fixed ? budget - fixed : budget) / kStreamBytesPerEntry);
+  // (each entry of a group also has its slot in the prefetch buffers of the
+  // group after it: 24 bytes)
+  uint64_t cap_entries = std::max<uint64_t>(
+      4096, (budget > fixed ? budget - fixed : budget) / (kStreamBytesPerEntry + 24));
   std::vector<std::pair<uint32_t, uint32_t>> groups;
   uint64_t acc = 0;
   uint32_t g0 = 0;
@@ -2935,52 +2937,96 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
   }
   w_bucket = ms_since(tw);
   tw = wall();
-  // pass 2: per group, its slices of every chunk's run in, match in core, rows out
+  // pass 2: per group, its slices of every chunk's run in, match in core, rows
+  // out.  The next group's slices are copied in on a copy stream, into a
+  // second set of buffers, while the current group is matched (the groups
+  // are sized for that second set: kStreamBytesPerEntry + 24 bytes an entry).
   std::vector<HostRows> runs;
   hlc_stats agg{};
-  for (uint32_t gi = 0; gi < ngroups && rc == HLC_OK; ++gi) {
-    uint64_t gn[2] = {0, 0};
+  struct Slot {
+    double *ra[2] = {nullptr, nullptr}, *dec[2] = {nullptr, nullptr};
+    uint64_t* id[2] = {nullptr, nullptr};
+    uint64_t n[2] = {0, 0};
+  };
+  Slot slot[2];
+  cudaStream_t cps = nullptr;
+  cudaEvent_t cev0[2] = {nullptr, nullptr}, cev1[2] = {nullptr, nullptr}, stev = nullptr;
+  bool cps_ok = cudaStreamCreateWithFlags(&cps, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaEventCreateWithFlags(&stev, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < 2 && cps_ok; ++k)
+    cps_ok = cudaEventCreate(&cev0[k]) == cudaSuccess && cudaEventCreate(&cev1[k]) == cudaSuccess;
+  if (!cps_ok) {
+    cudaGetLastError();
+    rc = HLC_ECUDA;
+  }
+  auto group_size = [&](uint32_t g, uint64_t gn[2]) {
+    gn[0] = gn[1] = 0;
     for (int side = 0; side < 2; ++side)
-      for (auto& o : hoff[side]) gn[side] += o[gi + 1] - o[gi];
-    const uint64_t na = gn[0], nb = gn[1];
-    if (na == 0 || nb == 0) continue;
-    double *gra[2] = {nullptr, nullptr}, *gdec[2] = {nullptr, nullptr};
-    uint64_t* gid[2] = {nullptr, nullptr};
+      for (auto& o : hoff[side]) gn[side] += o[g + 1] - o[g];
+  };
+  auto next_group = [&](uint32_t from) {
+    for (uint32_t g = from; g < ngroups; ++g) {
+      uint64_t gn[2];
+      group_size(g, gn);
+      if (gn[0] && gn[1]) return g;
+    }
+    return ngroups;
+  };
+  auto release = [&](Slot& S) {
     for (int side = 0; side < 2; ++side) {
-      gra[side] = ar.get_n<double>(gn[side] + 1);
-      gdec[side] = ar.get_n<double>(gn[side] + 1);
-      gid[side] = ar.get_n<uint64_t>(gn[side] + 1);
-      if (!gra[side] || !gdec[side] || !gid[side]) {
-        rc = HLC_ENOMEM;
-        break;
-      }
-      cudaEvent_t t0, t1;
-      cudaEventCreate(&t0);
-      cudaEventCreate(&t1);
-      cudaEventRecord(t0, st);
+      if (S.ra[side]) ar.drop(S.ra[side]);
+      if (S.dec[side]) ar.drop(S.dec[side]);
+      if (S.id[side]) ar.drop(S.id[side]);
+      S.ra[side] = S.dec[side] = nullptr;
+      S.id[side] = nullptr;
+    }
+  };
+  // group g's slices of every chunk's run into slot k, on the copy stream
+  // (after everything issued on the plan stream so far)
+  auto fetch = [&](uint32_t g, int k) -> int {
+    Slot& S = slot[k];
+    group_size(g, S.n);
+    HLC_CUDA(cudaEventRecord(stev, st));
+    HLC_CUDA(cudaStreamWaitEvent(cps, stev, 0));
+    HLC_CUDA(cudaEventRecord(cev0[k], cps));
+    for (int side = 0; side < 2; ++side) {
+      S.ra[side] = ar.get_n<double>(S.n[side] + 1);
+      S.dec[side] = ar.get_n<double>(S.n[side] + 1);
+      S.id[side] = ar.get_n<uint64_t>(S.n[side] + 1);
+      if (!S.ra[side] || !S.dec[side] || !S.id[side]) return HLC_ENOMEM;
       uint64_t o = 0;
-      for (size_t c = 0; c < hoff[side].size() && rc == HLC_OK; ++c) {
-        const uint64_t s0 = hbase[side][c] + hoff[side][c][gi];
-        const uint64_t len = hoff[side][c][gi + 1] - hoff[side][c][gi];
+      for (size_t c = 0; c < hoff[side].size(); ++c) {
+        const uint64_t s0 = hbase[side][c] + hoff[side][c][g];
+        const uint64_t len = hoff[side][c][g + 1] - hoff[side][c][g];
         if (!len) continue;
-        if (cudaMemcpyAsync(gra[side] + o, hra[side] + s0, len * 8, cudaMemcpyHostToDevice, st) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(gdec[side] + o, hdec[side] + s0, len * 8, cudaMemcpyHostToDevice,
-                            st) != cudaSuccess ||
-            cudaMemcpyAsync(gid[side] + o, hid[side] + s0, len * 8, cudaMemcpyHostToDevice, st) !=
-                cudaSuccess)
-          rc = HLC_ECUDA;
+        HLC_CUDA(cudaMemcpyAsync(S.ra[side] + o, hra[side] + s0, len * 8,
+                                 cudaMemcpyHostToDevice, cps));
+        HLC_CUDA(cudaMemcpyAsync(S.dec[side] + o, hdec[side] + s0, len * 8,
+                                 cudaMemcpyHostToDevice, cps));
+        HLC_CUDA(cudaMemcpyAsync(S.id[side] + o, hid[side] + s0, len * 8,
+                                 cudaMemcpyHostToDevice, cps));
         led[0] += 3 * len * 8;
         led[1] += 3;
         o += len;
       }
-      cudaEventRecord(t1, st);
-      cudaEventSynchronize(t1);
-      float ms = 0;
-      cudaEventElapsedTime(&ms, t0, t1);
-      ms_h2d += ms;
-      cudaEventDestroy(t0);
-      cudaEventDestroy(t1);
+    }
+    HLC_CUDA(cudaEventRecord(cev1[k], cps));
+    return HLC_OK;
+  };
+  uint32_t gi = rc == HLC_OK ? next_group(0) : ngroups;
+  int cur = 0;
+  if (gi < ngroups) rc = fetch(gi, cur);
+  while (gi < ngroups && rc == HLC_OK) {
+    const uint32_t gnext = next_group(gi + 1);
+    if (gnext < ngroups) rc = fetch(gnext, cur ^ 1);  // (behind this group's copies)
+    if (rc != HLC_OK) break;
+    Slot& S = slot[cur];
+    const uint64_t na = S.n[0], nb = S.n[1];
+    double *gra[2] = {S.ra[0], S.ra[1]}, *gdec[2] = {S.dec[0], S.dec[1]};
+    uint64_t* gid[2] = {S.id[0], S.id[1]};
+    if (cudaStreamWaitEvent(st, cev1[cur], 0) != cudaSuccess) {
+      rc = HLC_ECUDA;
+      break;
     }
     hlc_plan_t* G = nullptr;
     if (rc == HLC_OK) {
@@ -3042,14 +3088,26 @@ static int plan_streamed(const hlc_catalog* A, const hlc_catalog* B, const hlc_p
       agg.tile_entries_a += gs.tile_entries_a;
       hlc_free(G);
     }
-    for (int side = 0; side < 2; ++side) {
-      if (gra[side]) ar.drop(gra[side]);
-      if (gdec[side]) ar.drop(gdec[side]);
-      if (gid[side]) ar.drop(gid[side]);
+    {  // this group's copy span (the copy stream ran ahead of the matches)
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, cev0[cur], cev1[cur]) == cudaSuccess) ms_h2d += ms;
+      cudaGetLastError();
     }
+    release(S);
     if (rc != HLC_OK) break;
     ++agg.partitions;
+    gi = gnext;
+    cur ^= 1;
   }
+  if (cps) cudaStreamSynchronize(cps);
+  release(slot[0]);
+  release(slot[1]);
+  if (cps) cudaStreamDestroy(cps);
+  for (int k = 0; k < 2; ++k) {
+    if (cev0[k]) cudaEventDestroy(cev0[k]);
+    if (cev1[k]) cudaEventDestroy(cev1[k]);
+  }
+  if (stev) cudaEventDestroy(stev);
   free_host();
   cleanup();
   w_groups = ms_since(tw);
