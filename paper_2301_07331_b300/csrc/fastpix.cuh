@@ -125,6 +125,101 @@ __device__ __forceinline__ bool f_pix(f2 ra, const FastDec& d, int order, const 
   return true;
 }
 
+// ---- float-float tier for the positions the FP32 estimate left undecided ----
+// The same decisions as c_pix, taken from float-float operands: the angles
+// split exactly, sin from f2_sin_deg (about 1e-14), the products and sums
+// in float-float, so each operand lies within about 1e-13 (ns + 1) of its
+// exact value, and the binary64 path's own operands within a few 1e-15
+// (ns + 1) of theirs.  A decision is taken only when the operand lies
+// farther than kFfMargin (ns + 1) from the threshold (the integer of a
+// floor, 2/3 for the zone), several hundred times both errors together, so a
+// decided pixel is the canonical one; false leaves the binary64 path to it.
+constexpr float kFfMargin = 1e-10f;
+
+// floor(v) when v is farther than e from an integer (v >= -1; the remainder
+// r is exact but for its own rounding, ulp(r)/2 <= 6e-8, which e covers).
+__device__ __forceinline__ bool ff_floor(f2 v, float e, int* out) {
+  const float fl = floorf(v.hi);
+  const float r = (v.hi - fl) + v.lo;
+  *out = (int)fl;
+  return r > e && r < 1.0f - e;
+}
+
+__device__ __forceinline__ bool ff_pix(double ra, double dec, int order, uint32_t* out) {
+  const PixConst K = pix_const(order);
+  const f2 a = split_f64(ra), d = split_f64(dec);
+  const f2 z = f2_sin_deg(d);
+  const f2 az = z.hi < 0.f ? f2{-z.hi, -z.lo} : z;
+  constexpr f2 two3 = f2_of(2.0 / 3.0);
+  const f2 dz = f2_add(az, f2{-two3.hi, -two3.lo});
+  if (fabsf(dz.hi) <= 1e-12f) return false;  // on the zone boundary
+  const bool polar = dz.hi > 0.f;
+  const float ns = pow2f(order);
+  const int nsi = 1 << order;
+  const float e = kFfMargin * (ns + 1.0f) + 2.4e-7f;
+  int face, ix, iy;
+  if (!polar) {
+    // ns (0.5 + ra/90) -/+ 0.75 ns z as floor(ns ra/90) + (fraction + 0.5 ns -/+ 0.75 ns z)
+    const f2 t = f2_mul(a, f2{K.kh, K.kl});
+    const float ih = floor_pos(t.hi);
+    const int iih = ifloor_pos(t.hi);
+    const f2 fa = two_sum(t.hi - ih, t.lo);  // (t.hi - ih exact)
+    const f2 t2 = f2_mulf(z, 0.75f * ns);
+    const f2 base = f2_add(fa, f2{0.5f * ns, 0.f});
+    int f1, f2i;
+    if (!ff_floor(f2_add(base, f2{-t2.hi, -t2.lo}), e, &f1)) return false;
+    if (!ff_floor(f2_add(base, t2), e, &f2i)) return false;
+    const int jp = iih + f1, jm = iih + f2i;
+    const int ifp = jp >> order, ifm = jm >> order;
+    face = (ifp == ifm) ? (ifp | 4) : (ifp < ifm ? ifp : ifm + 8);
+    ix = jm & (nsi - 1);
+    iy = nsi - (jp & (nsi - 1)) - 1;
+  } else {
+    const f2 tt = f2_mul(a, f2{K.inv90h, K.inv90l});
+    int ntt;
+    if (!ff_floor(tt, e, &ntt)) return false;  // RA near a multiple of 90
+    const float fh = (float)ntt;
+    const f2 fr = two_sum(tt.hi - fh, tt.lo);
+    f2 tp = fr;
+    if (ntt >= 4) {
+      ntt = 3;
+      tp = f2_add(fr, f2{fh - 3.0f, 0.f});
+    }
+    // cap = sqrt(6) sin((90 - |dec|) / 2), in float-float
+    const float ah = fabsf(d.hi), al = d.hi < 0.f ? -d.lo : d.lo;
+    f2 w = two_sum(90.0f, -ah);
+    w = fast_two_sum(w.hi, w.lo - al);
+    w = f2{0.5f * w.hi, 0.5f * w.lo};
+    constexpr f2 sq6 = f2_of(2.4494897427831780982);  // sqrt(6)
+    const f2 cap = f2_mul(f2_sin_small(f2_mul(w, kPiOver180)), sq6);
+    const f2 tmp = {cap.hi * ns, cap.lo * ns};  // (exact: ns is a power of two)
+    int jp, jm;
+    if (!ff_floor(f2_mul(tp, tmp), e, &jp)) return false;
+    if (!ff_floor(f2_mul(f2_add(f2{1.0f, 0.f}, f2{-tp.hi, -tp.lo}), tmp), e, &jm)) return false;
+    jp = min(jp, nsi - 1);
+    jm = min(jm, nsi - 1);
+    if (z.hi > 0.f) {
+      face = ntt;
+      ix = nsi - jm - 1;
+      iy = nsi - jp - 1;
+    } else {
+      face = ntt + 8;
+      ix = jp;
+      iy = jm;
+    }
+  }
+  *out = fxy_to_nest(face, ix, iy, order);
+  return true;
+}
+
+// The canonical pixel of (ra, dec) (ra in [0, 360)) for a position the FP32
+// estimate left undecided: the float-float tier, else binary64.
+__device__ __forceinline__ uint32_t ff_or_c_ang2pix(double ra, double dec, int order) {
+  uint32_t p;
+  if (ff_pix(ra, dec, order, &p)) return p;
+  return c_ang2pix(ra, dec, order);
+}
+
 // ra already normalised to [0, 360).
 __device__ __forceinline__ uint32_t g_ang2pix(double ra, double dec, int order,
                                               const PixConst& K) {

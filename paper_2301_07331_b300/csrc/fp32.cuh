@@ -193,6 +193,62 @@ __device__ __forceinline__ void f2_sincos_reduced(f2 p, f2* s, f2* c) {
   *c = f2_add(c0, f2{tail_c, 0.f});
 }
 
+// ---- full float-float sine and cosine (about 1e-14 absolute) ----
+// The float pair nearest a double constant (evaluated at compile time).
+__host__ __device__ constexpr f2 f2_of(double v) {
+  return f2{(float)v, (float)(v - (double)(float)v)};
+}
+constexpr double kFact[18] = {1.0, 1.0, 2.0, 6.0, 24.0, 120.0, 720.0, 5040.0, 40320.0,
+                              362880.0, 3628800.0, 39916800.0, 479001600.0, 6227020800.0,
+                              87178291200.0, 1307674368000.0, 20922789888000.0,
+                              355687428096000.0};
+constexpr f2 kPiOver180 = f2_of(0.017453292519943295769);  // pi / 180
+
+// sin p and cos p of a float-float angle |p| <= pi/4 (+ a little): Taylor
+// series, the terms to p^9 (p^8) summed in float-float (Horner in u = p^2),
+// the rest (below 2e-9 relative) in float.
+__device__ __forceinline__ f2 f2_sin_small(f2 p) {
+  const f2 u = f2_mul(p, p);
+  const float uh = u.hi;
+  constexpr float c17 = (float)(1.0 / kFact[17]), c15 = (float)(-1.0 / kFact[15]),
+                  c13 = (float)(1.0 / kFact[13]), c11 = (float)(-1.0 / kFact[11]);
+  float tail = fmaf(uh, c17, c15);
+  tail = fmaf(uh, tail, c13);
+  tail = fmaf(uh, tail, c11);
+  f2 acc = f2_add(f2_of(1.0 / kFact[9]), f2_mulf(u, tail));
+  acc = f2_add(f2_of(-1.0 / kFact[7]), f2_mul(u, acc));
+  acc = f2_add(f2_of(1.0 / kFact[5]), f2_mul(u, acc));
+  acc = f2_add(f2_of(-1.0 / kFact[3]), f2_mul(u, acc));
+  return f2_add(p, f2_mul(p, f2_mul(u, acc)));
+}
+__device__ __forceinline__ f2 f2_cos_small(f2 p) {
+  const f2 u = f2_mul(p, p);
+  const float uh = u.hi;
+  constexpr float c16 = (float)(1.0 / kFact[16]), c14 = (float)(-1.0 / kFact[14]),
+                  c12 = (float)(1.0 / kFact[12]), c10 = (float)(-1.0 / kFact[10]);
+  float tail = fmaf(uh, c16, c14);
+  tail = fmaf(uh, tail, c12);
+  tail = fmaf(uh, tail, c10);
+  f2 acc = f2_add(f2_of(1.0 / kFact[8]), f2_mulf(u, tail));
+  acc = f2_add(f2_of(-1.0 / kFact[6]), f2_mul(u, acc));
+  acc = f2_add(f2_of(1.0 / kFact[4]), f2_mul(u, acc));
+  acc = f2_add(f2_of(-1.0 / kFact[2]), f2_mul(u, acc));
+  return f2_add(f2{1.0f, 0.f}, f2_mul(u, acc));
+}
+
+// sin of a float-float number of degrees, |x| <= 90 (+ a little): reduced
+// by the nearest multiple of 90 (exact), converted to radians in
+// float-float, then the sine or cosine series.
+__device__ __forceinline__ f2 f2_sin_deg(f2 x) {
+  int qi;
+  const float q = round_near(x.hi * (1.0f / 90.0f), &qi);
+  const f2 t = two_sum(fmaf(-90.0f, q, x.hi), x.lo);  // (the first term exact)
+  const f2 p = f2_mul(t, kPiOver180);
+  if (qi == 0) return f2_sin_small(p);
+  const f2 c = f2_cos_small(p);
+  return qi > 0 ? c : f2{-c.hi, -c.lo};
+}
+
 // cos of an angle given as a float-float number of degrees, |x| <= 90,
 // to about 3e-8 relative (evaluated as sin(90 - |x|)).
 __device__ __forceinline__ f2 f2_cos_deg(f2 x) {

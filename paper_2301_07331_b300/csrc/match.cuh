@@ -170,7 +170,7 @@ __global__ void k_prep_fallback(const double* __restrict__ ra, const double* __r
        q += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t i = slow[q];
     const double a = c_norm_ra(ra[i]);
-    const uint32_t k = c_ang2pix(a, dec[i], order);
+    const uint32_t k = ff_or_c_ang2pix(a, dec[i], order);
     key[i] = k;
     if (rec) rec[i].ra = a;
     for (int p = 0; hist && p < hist_np; ++p)
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kThreads) k_quad_fallback(
           pd = __dadd_rn(sd, R);
           if (pd > 90.0) pd = 90.0;
         }
-        s_pix[w][src * 5 + e] = c_ang2pix(pa, pd, order);
+        s_pix[w][src * 5 + e] = ff_or_c_ang2pix(pa, pd, order);
       }
     }
     __syncwarp();

@@ -56,6 +56,86 @@ def test_ang2pix_bit_exact(order):
         np.testing.assert_array_equal(got.astype(np.uint64), want)
 
 
+# distances (in units of the floor's argument) at which points are placed
+# from pixel edges: beyond the FP32 estimate's guard margin, inside it but
+# beyond the float-float tier's, and inside both (binary64 decides)
+EDGE_DELTAS = [s * d for d in (1e-2, 1e-4, 1e-6, 3e-7, 1e-7, 1e-8, 1e-10, 1e-12, 1e-13)
+               for s in (1.0, -1.0)]
+
+
+def _edge_points(order, n, seed):
+    """Points a given distance from the decision thresholds of the nested
+    ang2pix: the two equatorial diagonals ns (1/2 + ra/90) -/+ 3/4 ns z, the
+    polar coordinates tp tmp and (1 - tp) tmp, RA multiples of 90 in the caps
+    and the zone boundary |z| = 2/3 (Gorski et al. 2005, written out here
+    from the definition, not from the library)."""
+    rng = np.random.default_rng(seed)
+    ns = 2.0 ** order
+    ras, decs = [], []
+    for dl in EDGE_DELTAS:
+        # equatorial: ns (0.5 + ra/90) - s 0.75 ns z = k + dl
+        z = rng.uniform(-0.66, 0.66, n)
+        sgn = np.where(rng.uniform(size=n) < 0.5, -1.0, 1.0)
+        ra0 = rng.uniform(0.0, 360.0, n)
+        k = np.round(ns * (0.5 + ra0 / 90.0) - sgn * 0.75 * ns * z)
+        ra = 90.0 * ((k + dl) / ns + sgn * 0.75 * z - 0.5)
+        ok = (ra >= 0.0) & (ra < 360.0)
+        ras.append(ra[ok]); decs.append(np.degrees(np.arcsin(z[ok])))
+        # polar: tp tmp = k + dl or (1 - tp) tmp = k + dl, tmp = ns sqrt(6) sin((90-|dec|)/2)
+        dec = rng.uniform(42.0, 89.999, n) * np.where(rng.uniform(size=n) < 0.5, -1.0, 1.0)
+        tmp = ns * math.sqrt(6.0) * np.sin(np.radians(0.5 * (90.0 - np.abs(dec))))
+        kk = np.floor(rng.uniform(0.0, 1.0, n) * tmp)
+        tp = (kk + dl) / tmp
+        tp = np.where(rng.uniform(size=n) < 0.5, tp, 1.0 - tp)
+        ntt = rng.integers(0, 4, n)
+        ra = 90.0 * (ntt + tp)
+        ok = (tp > 0.0) & (tp < 1.0) & (ra >= 0.0) & (ra < 360.0)
+        ras.append(ra[ok]); decs.append(dec[ok])
+        # polar caps at RA multiples of 90; the zone boundary
+        m = 64
+        ras.append(np.clip(90.0 * rng.integers(0, 4, m) + dl * 90.0, 0.0, np.nextafter(360.0, 0)))
+        decs.append(rng.uniform(42.0, 89.9, m))
+        zz = np.clip(2.0 / 3.0 + dl, -1.0, 1.0) * np.where(rng.uniform(size=m) < 0.5, -1.0, 1.0)
+        ras.append(rng.uniform(0.0, 360.0, m)); decs.append(np.degrees(np.arcsin(zz)))
+    return np.concatenate(ras), np.concatenate(decs)
+
+
+@pytest.mark.parametrize("order", [0, 2, 6, 10, 12, 13, 14])
+def test_ang2pix_near_pixel_edges(order):
+    """Points placed 1e-2 ... 1e-13 from every kind of pixel edge: the FP32
+    estimate, the float-float tier and binary64 each decide some, and every
+    pixel equals the oracle's."""
+    ra, dec = _edge_points(order, 2000, 100 + order)
+    assert ra.size > 30000
+    r, d = _cuda(ra, dec)
+    want = O.ang2pix(ra, dec, order)
+    for prec in (hlc.HLC_FP64, hlc.HLC_FP32_GUARD):
+        got = hlc.hlc_ang2pix(r, d, order, prec).cpu().numpy().view(np.uint32)
+        np.testing.assert_array_equal(got.astype(np.uint64), want)
+
+
+@pytest.mark.parametrize("order", [4, 12, 14])
+def test_quad_cells_of_sources_whose_copies_land_near_edges(order):
+    """Sources placed so that a shifted copy (ra + R, ra - R, dec - R or
+    dec + R) lands within 1e-2 ... 1e-13 of a pixel edge."""
+    r = 1.5
+    R = r / 3600.0
+    pr, pd = _edge_points(order, 300, 200 + order)
+    which = np.random.default_rng(order).integers(0, 4, pr.size)
+    ra = np.where(which == 0, pr - R, np.where(which == 1, pr + R, pr))
+    dec = np.where(which == 2, pd + R, np.where(which == 3, pd - R, pd))
+    ok = (ra >= 0.0) & (ra < 360.0) & (np.abs(dec) <= 90.0)
+    ra, dec = ra[ok], dec[ok]
+    rr, dd = _cuda(ra, dec)
+    want, wcnt = O.quad_cells(ra, dec, r, order, False)
+    w = want.copy()
+    w[w == np.uint64(2 ** 64 - 1)] = 0xFFFFFFFF
+    for prec in (hlc.HLC_FP64, hlc.HLC_FP32_GUARD):
+        got, cnt = hlc.hlc_quad_cells(rr, dd, r, order, prec, boundary=hlc.HLC_QUAD)
+        np.testing.assert_array_equal(cnt.cpu().numpy(), wcnt)
+        np.testing.assert_array_equal(got.cpu().numpy().view(np.uint32).astype(np.uint64), w)
+
+
 def test_ang2pix_rejects_bad_input():
     r, d = _cuda(np.array([1.0, 2.0]), np.array([0.0, 91.0]))
     with pytest.raises(hlc.HLCError) as e:
