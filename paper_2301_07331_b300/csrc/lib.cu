@@ -876,6 +876,8 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
                          cudaEvent_t ev[4]) {
   Arena& ar = *P->arena;
   cudaStream_t st = plan_stream(P);
+  // (A's id span for the output's bucketing, taken by its prep kernel)
+  unsigned long long* iddiff = is_b ? nullptr : P->ctr + C_IDDIFF;
   const int L = P->p.fine_level;
   const bool quad = P->p.boundary != HLC_COMPLETE8;
   const bool fp32 = P->p.precision == HLC_FP32_GUARD;
@@ -929,7 +931,7 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
         HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st));
         k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
             ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, slow, P->ctr + C_SLOW,
-            P->dev_err);
+            P->dev_err, nullptr, nullptr, 0, 0, iddiff);
         HLC_LAUNCH_CHECK();
         k_prep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW,
                                                               X.key, X.rec);
@@ -938,14 +940,16 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
       } else {
         k_prep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
             ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, nullptr, nullptr, P->dev_err,
-            perr);
+            perr, nullptr, 0, 0, iddiff);
         HLC_LAUNCH_CHECK();
       }
     }
   } else {
     HLC_ALLOC(ar, X.cells5, uint32_t, 5 * n + 5);
     uint32_t* cnt = ar.get_n<uint32_t>(n + 1);
-    uint64_t* off = ar.get_n<uint64_t>(n + 1);
+    // entry offsets: 32-bit while the entries (at most 5 per source) fit
+    const bool off32 = 5 * n < (1ull << 32);
+    void* off = ar.get((n + 1) * (off32 ? 4 : 8));
     void* scr = ar.get(scan_scratch_bytes(n));
     if (!cnt || !off || !scr) return HLC_ENOMEM;
     if (n) {
@@ -957,7 +961,7 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
         HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st));
         k_quad_cells<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
             ra, dec, id, n, R, L, pix_const(L), X.cells5, cnt, X.rec, slow, P->ctr + C_SLOW,
-            P->dev_err, cosdec);
+            P->dev_err, cosdec, iddiff);
         HLC_LAUNCH_CHECK();
         k_quad_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(ra, dec, R, L, slow, P->ctr + C_SLOW,
                                                       X.cells5, cnt, cosdec);
@@ -966,11 +970,16 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
       } else {
         k_quad_cells<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
             ra, dec, id, n, R, L, pix_const(L), X.cells5, cnt, X.rec, nullptr, nullptr,
-            P->dev_err, cosdec);
+            P->dev_err, cosdec, iddiff);
         HLC_LAUNCH_CHECK();
       }
     }
-    HLC_TRY(scan_exclusive<uint64_t>(cnt, off, n, P->ctr + C_TOTAL, scr, P->dev_err, st));
+    if (off32)
+      HLC_TRY(scan_exclusive<uint32_t>(cnt, (uint32_t*)off, n, P->ctr + C_TOTAL, scr, P->dev_err,
+                                       st));
+    else
+      HLC_TRY(scan_exclusive<uint64_t>(cnt, (uint64_t*)off, n, P->ctr + C_TOTAL, scr,
+                                       P->dev_err, st));
     unsigned long long m = 0;
     HLC_CUDA(cudaMemcpyAsync(&m, P->ctr + C_TOTAL, 8, cudaMemcpyDeviceToHost, st));
     HLC_CUDA(cudaStreamSynchronize(st));
@@ -978,8 +987,12 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     HLC_ALLOC(ar, X.key, uint32_t, X.m + 1);
     HLC_ALLOC(ar, X.idx, uint32_t, X.m + 1);
     if (n) {
-      k_quad_emit<<<grid_for(n, kThreads), kThreads, 0, st>>>(X.cells5, cnt, off, n, X.key,
-                                                               X.idx);
+      if (off32)
+        k_quad_emit<uint32_t><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+            X.cells5, cnt, (const uint32_t*)off, n, X.key, X.idx);
+      else
+        k_quad_emit<uint64_t><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+            X.cells5, cnt, (const uint64_t*)off, n, X.key, X.idx);
       HLC_LAUNCH_CHECK();
     }
     ar.drop(cnt);
@@ -1293,11 +1306,6 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
     for (int i = 0; i < 2; ++i)
       for (int k = 0; k < 4; ++k)
         if (stage[i][k]) P->arena->drop(stage[i][k]);
-  }
-  if (rc == HLC_OK && P->A.n && !P->table_buckets) {
-    k_id_diff_rec<<<grid_for(P->A.n, kThreads, num_sms() * 8u), kThreads, 0, st>>>(P->A.rec, P->A.n,
-                                                                              P->ctr + C_IDDIFF);
-    if (cudaGetLastError() != cudaSuccess) rc = HLC_ECUDA;
   }
   unsigned long long hc[C_N] = {0};
   if (rc == HLC_OK && cudaMemcpyAsync(hc, P->ctr, sizeof(hc), cudaMemcpyDeviceToHost, st) !=

@@ -64,6 +64,15 @@ constexpr uint32_t kSparseCell = HLC_SPARSE_CELL;
 // Preparation.
 // ---------------------------------------------------------------------------
 
+// The bits in which the ids differ (OR of id ^ id[0] over the sources, for
+// the output's bucketing), a warp's share added once; every thread calls it.
+__device__ __forceinline__ void id_span_flush(unsigned long long* iddiff,
+                                              unsigned long long acc) {
+  if (!iddiff) return;
+  for (int o = 16; o > 0; o >>= 1) acc |= __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicOr(iddiff, acc);
+}
+
 // Cell key and identity index of each source (complete mode), with input
 // validation (non-finite or |dec| > 90 sets DERR_INPUT).  FAST: guarded FP32
 // evaluation with binary64 fallback (same pixels).
@@ -82,8 +91,10 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
                             unsigned long long* __restrict__ nslow, int* __restrict__ err,
                             const double* __restrict__ perr = nullptr,
                             uint32_t* __restrict__ hist = nullptr, int hist_lo = 0,
-                            int hist_np = 0) {
+                            int hist_np = 0, unsigned long long* __restrict__ iddiff = nullptr) {
   __shared__ uint32_t sh[kPrepHistPasses][256];
+  const uint64_t id0 = (iddiff && n) ? id[0] : 0ull;
+  unsigned long long idacc = 0;
   if (FAST && hist) {
     for (int t = threadIdx.x; t < kPrepHistPasses * 256; t += blockDim.x) (&sh[0][0])[t] = 0u;
     __syncthreads();
@@ -117,6 +128,7 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
       key[i] = k;
       kfin = k;
       if (idx) idx[i] = (uint32_t)i;
+      if (iddiff) idacc |= id[i] ^ id0;
       if (rec) {
         SrcRec r;
         r.ra = a;
@@ -147,6 +159,7 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
       if (c) atomicAdd(hist + t, c);
     }
   }
+  id_span_flush(iddiff, idacc);
 }
 
 // Binary64 ang2pix of the queued sources (and, with rec, the record's RA
@@ -197,8 +210,11 @@ __global__ void k_quad_cells(const double* __restrict__ ra, const double* __rest
                              PixConst K, uint32_t* __restrict__ cells,
                              uint32_t* __restrict__ count, SrcRec* __restrict__ rec,
                              uint32_t* __restrict__ slow, unsigned long long* __restrict__ nslow,
-                             int* __restrict__ err, bool cosdec = false) {
+                             int* __restrict__ err, bool cosdec = false,
+                             unsigned long long* __restrict__ iddiff = nullptr) {
   const f2 Rd = split_f64(R);
+  const uint64_t id0 = (iddiff && id && n) ? id[0] : 0ull;
+  unsigned long long idacc = 0;
   for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n;
        i0 += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t i = i0 + threadIdx.x;
@@ -239,6 +255,7 @@ __global__ void k_quad_cells(const double* __restrict__ ra, const double* __rest
         r.pad = 0;
         rec[i] = r;
       }
+      if (iddiff && id) idacc |= id[i] ^ id0;
     }
     if (FAST) {
       unsigned b = __ballot_sync(0xffffffffu, defer);
@@ -251,6 +268,7 @@ __global__ void k_quad_cells(const double* __restrict__ ra, const double* __rest
       }
     }
   }
+  id_span_flush(iddiff, idacc);
 }
 
 // The queued sources of k_quad_cells<true>.  Each warp takes 32 of them,
@@ -323,12 +341,13 @@ __global__ void __launch_bounds__(kThreads) k_quad_fallback(
 }
 
 // One (cell, source) entry per distinct quad cell, at the scanned offsets.
+template <typename OffT>
 __global__ void k_quad_emit(const uint32_t* __restrict__ cells, const uint32_t* __restrict__ count,
-                            const uint64_t* __restrict__ off, uint64_t n,
+                            const OffT* __restrict__ off, uint64_t n,
                             uint32_t* __restrict__ key, uint32_t* __restrict__ idx) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t o = off[i];
+    const uint64_t o = off[i];
     uint32_t m = count[i];
     for (uint32_t e = 0; e < m; ++e) {
       key[o + e] = cells[5 * i + e];
@@ -830,19 +849,6 @@ __global__ void __launch_bounds__(kThreads) k_recheck(
   }
   for (int o = 16; o > 0; o >>= 1) slow += __shfl_down_sync(0xffffffffu, slow, o);
   if ((threadIdx.x & 31) == 0 && slow && n64) atomicAdd(n64, slow);
-}
-
-// Highest differing bit of the source ids (OR of id ^ id[0]).
-__global__ void k_id_diff_rec(const SrcRec* __restrict__ rec, uint64_t n,
-                              unsigned long long* __restrict__ out) {
-  if (n == 0) return;
-  uint64_t first = rec[0].id;
-  unsigned long long acc = 0;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x)
-    acc |= rec[i].id ^ first;
-  for (int o = 16; o > 0; o >>= 1) acc |= __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0 && acc) atomicOr(out, acc);
 }
 
 template <typename T>
