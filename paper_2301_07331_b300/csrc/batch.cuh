@@ -56,8 +56,8 @@ template <bool FAST>
 __global__ void k_bprep_keys(const JobDev* __restrict__ jobs, const uint64_t* __restrict__ off,
                              uint32_t njobs, int side, uint64_t total, int cell_bits,
                              uint64_t* __restrict__ key, uint32_t* __restrict__ idx,
-                             uint32_t* __restrict__ slow, unsigned long long* __restrict__ nslow,
-                             int* __restrict__ err) {
+                             SrcRec* __restrict__ rec, uint32_t* __restrict__ slow,
+                             unsigned long long* __restrict__ nslow, int* __restrict__ err) {
   for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < total;
        i0 += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t i = i0 + threadIdx.x;
@@ -81,6 +81,12 @@ __global__ void k_bprep_keys(const JobDev* __restrict__ jobs, const uint64_t* __
       }
       key[i] = ((uint64_t)j << cell_bits) | k;
       idx[i] = (uint32_t)i;
+      SrcRec r;  // (the payload gathers one 32-byte record, not three arrays)
+      r.ra = a;
+      r.dec = d;
+      r.id = J.id[side][l];
+      r.pad = 0;
+      rec[i] = r;
     }
     if (FAST) {
       unsigned b = __ballot_sync(0xffffffffu, defer);
@@ -107,35 +113,32 @@ __global__ void k_bprep_fallback(const JobDev* __restrict__ jobs, const uint64_t
     uint32_t j = job_of(off, njobs, i);
     const JobDev& J = jobs[j];
     uint64_t l = i - J.off[side];
-    key[i] = ((uint64_t)j << cell_bits) | c_ang2pix(c_norm_ra(J.ra[side][l]), J.dec[side][l], J.L);
+    key[i] = ((uint64_t)j << cell_bits) |
+             ff_or_c_ang2pix(c_norm_ra(J.ra[side][l]), J.dec[side][l], J.L);
   }
 }
 
+// Sorted payload from the records the prep wrote in input order (RA
+// normalised): one 32-byte gather per entry.
 template <bool FP32>
-__global__ void k_bpayload(const JobDev* __restrict__ jobs, const uint64_t* __restrict__ off,
-                           uint32_t njobs, int side, const uint32_t* __restrict__ idx, uint64_t m,
-                           float4* __restrict__ v32, double2* __restrict__ rd,
+__global__ void k_bpayload(const SrcRec* __restrict__ rec, const uint32_t* __restrict__ idx,
+                           uint64_t m, float4* __restrict__ v32, double2* __restrict__ rd,
                            double* __restrict__ vx, double* __restrict__ vy,
                            double* __restrict__ vz, uint64_t* __restrict__ id_s) {
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
        e += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t i = idx[e];
-    uint32_t j = job_of(off, njobs, i);
-    const JobDev& J = jobs[j];
-    uint64_t l = i - J.off[side];
-    double a = J.ra[side][l], d = J.dec[side][l];
-    if (!bits_in_ra_range(a)) a = c_norm_ra(a);
+    const SrcRec r = rec[idx[e]];
     if (FP32) {
-      v32[e] = fp32_unitvec(a, d);
-      rd[e] = make_double2(a, d);
+      v32[e] = fp32_unitvec(r.ra, r.dec);
+      rd[e] = make_double2(r.ra, r.dec);
     } else {
       double x, y, z;
-      c_unitvec(a, d, &x, &y, &z);
+      c_unitvec(r.ra, r.dec, &x, &y, &z);
       vx[e] = x;
       vy[e] = y;
       vz[e] = z;
     }
-    id_s[e] = J.id[side][l];
+    id_s[e] = r.id;
   }
 }
 

@@ -1930,21 +1930,22 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
     X.n = X.m = n;
     keys[s] = ar.get_n<uint64_t>(n + 1);
     X.idx = ar.get_n<uint32_t>(n + 1);
+    X.rec = ar.get_n<SrcRec>(n + 1);
     uint32_t* slow = ar.get_n<uint32_t>(n + 1);
-    if (!keys[s] || !X.idx || !slow) return fail(HLC_ENOMEM);
+    if (!keys[s] || !X.idx || !X.rec || !slow) return fail(HLC_ENOMEM);
     cudaEventRecord(ev[s][0], st);
     if (n) {
       cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st);
       if (fp32) {
         k_bprep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            P->jobs_d, offd[s], njobs, s, n, P->cell_bits, keys[s], X.idx, slow, P->ctr + C_SLOW,
-            P->dev_err);
+            P->jobs_d, offd[s], njobs, s, n, P->cell_bits, keys[s], X.idx, X.rec, slow,
+            P->ctr + C_SLOW, P->dev_err);
         k_bprep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(P->jobs_d, offd[s], njobs, s, P->cell_bits,
                                                        slow, P->ctr + C_SLOW, keys[s]);
       } else {
         k_bprep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            P->jobs_d, offd[s], njobs, s, n, P->cell_bits, keys[s], X.idx, nullptr, nullptr,
-            P->dev_err);
+            P->jobs_d, offd[s], njobs, s, n, P->cell_bits, keys[s], X.idx, X.rec, nullptr,
+            nullptr, P->dev_err);
       }
       g_launches += fp32 ? 2 : 1;
     }
@@ -1970,8 +1971,7 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
       if (!X.v32 || !X.rd) return fail(HLC_ENOMEM);
       if (n)
         k_bpayload<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            P->jobs_d, offd[s], njobs, s, X.idx, n, X.v32, X.rd, nullptr, nullptr, nullptr,
-            X.id_s);
+            X.rec, X.idx, n, X.v32, X.rd, nullptr, nullptr, nullptr, X.id_s);
     } else {
       X.vx = ar.get_n<double>(n + 1);
       X.vy = ar.get_n<double>(n + 1);
@@ -1979,9 +1979,11 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
       if (!X.vx || !X.vy || !X.vz) return fail(HLC_ENOMEM);
       if (n)
         k_bpayload<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            P->jobs_d, offd[s], njobs, s, X.idx, n, nullptr, nullptr, X.vx, X.vy, X.vz, X.id_s);
+            X.rec, X.idx, n, nullptr, nullptr, X.vx, X.vy, X.vz, X.id_s);
     }
     if (n) ++g_launches;
+    ar.drop(X.rec);  // (the later stages read the sorted payload only)
+    X.rec = nullptr;
     cudaEventRecord(ev[s][3], st);
   }
   P->keyA64 = keys[0];
