@@ -865,8 +865,13 @@ def run_batched(args):
     else:
         tune, report = None, {"skipped": "--tune-sample 0"}
 
+    # the C structs of the job list, built once as a C caller would (the
+    # tuned list and the rule's)
+    prepared = {id(tune): hlc.BatchedJobs(spec, stream=stream, tune=tune),
+                id(None): hlc.BatchedJobs(spec, stream=stream)}
+
     def batched(tn=None):
-        plan = hlc.hlc_plan_batched(spec, stream=stream, tune=tn)
+        plan = hlc.hlc_plan_batched(prepared[id(tn)], stream=stream)
         out = hlc.hlc_match(plan, copy=False)
         n_, st_ = out["n"], out["stats"]
         hlc.hlc_free(plan)

@@ -365,19 +365,36 @@ def hlc_autotune(jobs, sample_jobs: int = 256, precision: int = HLC_FP32_GUARD, 
                   "sample_jobs": rep.sample_jobs, "trials": trials}
 
 
+class BatchedJobs:
+    """A job list marshalled once into the C structs hlc_plan takes (what a C
+    caller builds once), for plans over the same catalogue buffers again and
+    again: building them costs about 10 us a job in Python.  The tensors must
+    stay alive and unchanged in place while plans are made from it."""
+
+    def __init__(self, jobs, precision: int = HLC_FP32_GUARD, want_sep: bool = True,
+                 stream=None, torch_alloc: bool = False, tune: Tune | None = None):
+        _require_cuda()
+        (self.n, self.cats_a, self.cats_b, self.params, self.keep,
+         self.alloc) = _batched_args(jobs, precision, want_sep, stream, torch_alloc, tune)
+        self.tune = tune
+
+
 def hlc_plan_batched(jobs, precision: int = HLC_FP32_GUARD, want_sep: bool = True,
                      stream=None, torch_alloc: bool = False, tune: Tune | None = None) -> Plan:
     """One plan over many independent jobs.  jobs: sequence of dicts with keys
     A, B ((ra, dec, id) triples or catalogue objects), radius_arcsec and
-    fine_level (-1 = chosen by the library from the job's density).  tune:
-    a Tune from hlc_autotune (None: the library's rule)."""
+    fine_level (-1 = chosen by the library from the job's density), or a
+    BatchedJobs (which carries its own precision, stream and tune; the other
+    arguments are then ignored).  tune: a Tune from hlc_autotune (None: the
+    library's rule)."""
     _require_cuda()
     L = lib()
-    n, cats_a, cats_b, params, keep, alloc = _batched_args(jobs, precision, want_sep, stream,
-                                                           torch_alloc, tune)
+    if not isinstance(jobs, BatchedJobs):
+        jobs = BatchedJobs(jobs, precision, want_sep, stream, torch_alloc, tune)
     h = C.c_void_p()
-    _check(L.hlc_plan(cats_a, cats_b, params, n, C.byref(h)))
-    return Plan(h, params[0], alloc, (keep, cats_a, cats_b, params, tune))
+    _check(L.hlc_plan(jobs.cats_a, jobs.cats_b, jobs.params, jobs.n, C.byref(h)))
+    return Plan(h, jobs.params[0], jobs.alloc, (jobs.keep, jobs.cats_a, jobs.cats_b, jobs.params,
+                                                jobs.tune))
 
 
 def _triple(X):

@@ -168,3 +168,23 @@ def test_4096_jobs_equal_oracle_on_sampled_jobs():
             assert np.max(np.abs(sep[m] - want["sep"])) <= 1e-6
     assert st["n_a"] == sum(j.A.n for j in jobs)
     assert ia.size > 1000
+
+
+def test_prepared_job_list_is_reusable_and_equals_the_list_form():
+    jobs = synth.cone_jobs(n_jobs=16, nmin=100, nmax=8000, seed=12)
+    spec = [dict(A=(j.A.ra.cuda(), j.A.dec.cuda(), j.A.id.cuda()),
+                 B=(j.B.ra.cuda(), j.B.dec.cuda(), j.B.id.cuda()), radius_arcsec=j.r_arcsec)
+            for j in jobs]
+
+    def rows(p):
+        plan = hlc.hlc_plan_batched(p)
+        r = hlc.hlc_match(plan)
+        hlc.hlc_free(plan)
+        return [r[k].cpu().numpy() for k in ("job", "id_a", "id_b", "sep")]
+    want = rows(spec)
+    prepared = hlc.BatchedJobs(spec)
+    for _ in range(3):
+        got = rows(prepared)
+        for g, w in zip(got, want):
+            np.testing.assert_array_equal(g, w)
+    assert want[0].size > 100
