@@ -334,22 +334,74 @@ def run_hlc(args):
         times = []
         ke = min(args.steps, 30)
         cap = 2 * max(nmatch, 1)  # pinned result buffers, allocated once
-        outb = tuple(torch.empty(cap, dtype=dt).pin_memory()
-                     for dt in (torch.int64, torch.int64, torch.float64))
-        for it in range(args.warmup + ke):
+        depth = max(1, args.e2e_depth)
+        outs = [tuple(torch.empty(cap, dtype=dt).pin_memory()
+                      for dt in (torch.int64, torch.int64, torch.float64)) for _ in range(depth)]
+
+        def e2e_step(s, outb):
+            plan = hlc.hlc_plan(Ah, Bh, r, L, coarse_level=Lc, boundary=mode, precision=prec,
+                                stream=s)
+            hlc.hlc_match(plan, copy=False)
+            # (copies on the plan's stream; hlc_free synchronises it)
+            ia_, ib_, sp_ = hlc.hlc_result_to_host(plan, out=outb, wait=False)
+            hlc.hlc_free(plan)
+            return ia_, ib_, sp_
+
+        # (a) one step at a time: the latency of a step
+        ks = min(ke, 10)
+        for it in range(args.warmup + ks):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            plan = hlc.hlc_plan(Ah, Bh, r, L, coarse_level=Lc, boundary=mode, precision=prec,
-                                stream=stream)
-            hlc.hlc_match(plan, copy=False)
-            ia, ib, sp = hlc.hlc_result_to_host(plan, out=outb)
-            hlc.hlc_free(plan)
+            ia, ib, sp = e2e_step(stream, outs[0])
             t1 = time.perf_counter()
             if it >= args.warmup:
                 times.append(t1 - t0)
-        t = sum(times) / len(times)
+        t_serial = sum(times) / len(times)
+        # (b) the throughput: `depth` steps in flight, one per host thread and
+        # stream (the library's calls release the interpreter lock), started a
+        # fraction of a step apart, so that the link carries one step's copies
+        # while the others build, match and order; each step still copies its
+        # inputs in and its rows out
+        import threading
+        streams = [torch.cuda.Stream() for _ in range(depth)]
+        counts = [ke // depth + (1 if w < ke % depth else 0) for w in range(depth)]
+        errs, rows_out = [], [0] * depth
+        go = threading.Barrier(depth + 1)
+
+        def worker(w):
+            try:
+                e2e_step(streams[w], outs[w])  # (warm the stream)
+                go.wait()
+                time.sleep(w * t_serial / depth)  # (staggered: not all copying at once)
+                for _ in range(counts[w]):
+                    ia_, _, _ = e2e_step(streams[w], outs[w])
+                    rows_out[w] = int(ia_.size)
+            except Exception as e:  # noqa: BLE001 (re-raised below)
+                errs.append(e)
+                go.abort()
+        ths = [threading.Thread(target=worker, args=(w,)) for w in range(depth)]
+        for th in ths:
+            th.start()
+        torch.cuda.synchronize()
+        try:
+            go.wait()
+        except threading.BrokenBarrierError:
+            pass  # (a worker failed; raised below)
+        t0 = time.perf_counter()
+        for th in ths:
+            th.join()
+        torch.cuda.synchronize()
+        t = (time.perf_counter() - t0) / ke
+        if errs:
+            raise errs[0]
+        assert all(n_ == int(ia.size) for n_ in rows_out)
         e2e = {"value": sources / t, "unit": "sources/s", "ms_per_step": t * 1e3, "steps": ke,
-               "h2d_bytes_per_step": (na + nb) * 24, "d2h_bytes_per_step": int(ia.size) * 24}
+               "h2d_bytes_per_step": (na + nb) * 24, "d2h_bytes_per_step": int(ia.size) * 24,
+               "in_flight": depth, "serial_ms_per_step": t_serial * 1e3,
+               "timing": "host wall clock over %d steps, %d at a time (one host thread and "
+                         "stream each, started 1/%d step apart): pinned host catalogues in "
+                         "through hlc_plan, rows copied to pinned host buffers by "
+                         "hlc_result_to_host" % (ke, depth, depth)}
 
     # CPU oracle on a bounded sample of the same workload (rank 0 only), and
     # this run's rows against it
@@ -1102,6 +1154,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--mode", default="complete", choices=["complete", "quad"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-depth", type=int, default=3,
+                    help="steps in flight in the end-to-end throughput run")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-other-mode", action="store_true",
                     help="skip the other boundary mode's sub-line")

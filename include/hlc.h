@@ -263,9 +263,23 @@ int hlc_plan(const hlc_catalog* A, const hlc_catalog* B, const hlc_params* p,
  * NULL.  Synchronises the plan's stream before returning. */
 int hlc_match(hlc_plan_t* plan, hlc_result* out, hlc_stats* stats);
 
-/* Copy a result to caller-owned host arrays (each may be NULL to skip). */
+/* Copy a result to caller-owned host arrays (each may be NULL to skip) and
+ * wait for the copies.  They run on the calling thread's own default stream
+ * (cudaStreamPerThread), so plans matched on other threads' streams are not
+ * held up.  Errors: HLC_EINVAL for a NULL result, HLC_ECUDA for a failed copy. */
 int hlc_result_to_host(const hlc_result* r, uint64_t* id_a, uint64_t* id_b,
                        double* sep_arcsec, uint32_t* job);
+
+/* The same copies, enqueued on `stream` (a cudaStream_t; NULL = the legacy
+ * default stream) and not waited for: the host arrays may be read once the
+ * stream has reached them (cudaStreamSynchronize, or hlc_free of the plan
+ * when `stream` is the plan's stream, which synchronises it).  Page-locked
+ * host arrays let the copies overlap other work on the link and the GPU;
+ * with pageable ones the call returns only after the copies.  The plan must
+ * not be freed on another stream before the copies are done.  Errors:
+ * HLC_EINVAL for a NULL result, HLC_ECUDA when a copy cannot be enqueued. */
+int hlc_result_to_host_async(const hlc_result* r, uint64_t* id_a, uint64_t* id_b,
+                             double* sep_arcsec, uint32_t* job, void* stream);
 
 /* Release the plan, its device memory and every result it returned. */
 void hlc_free(hlc_plan_t* plan);

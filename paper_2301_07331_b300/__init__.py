@@ -143,6 +143,7 @@ def lib():
     L.hlc_free.argtypes = [P]
     L.hlc_free.restype = None
     L.hlc_result_to_host.argtypes = [P, P, P, P, P]
+    L.hlc_result_to_host_async.argtypes = [P, P, P, P, P, P]
     L.hlc_last_error.restype = C.c_char_p
     L.hlc_version.restype = C.c_char_p
     L.hlc_abi_sizes.argtypes = [C.POINTER(C.c_size_t), C.c_int]
@@ -450,10 +451,13 @@ def hlc_match(plan: Plan, copy: bool = True) -> dict:
                 stats=s.as_dict())
 
 
-def hlc_result_to_host(plan: Plan, out=None):
+def hlc_result_to_host(plan: Plan, out=None, wait: bool = True):
     """Copy the last result's rows to host memory.  out: optional (id_a, id_b,
     sep) host buffers (numpy arrays or CPU tensors, pinned ones copy fastest)
-    with room for n rows; the returned arrays are views of their first n."""
+    with room for n rows; the returned arrays are views of their first n.
+    wait=False enqueues the copies on the plan's stream and returns at once
+    (read the arrays after synchronising that stream, or after hlc_free of
+    the plan, which does)."""
     r = plan.result
     n = int(r.n)
 
@@ -467,8 +471,12 @@ def hlc_result_to_host(plan: Plan, out=None):
         return b[:n].view(dt)
     ia, ib = buf(0, np.uint64), buf(1, np.uint64)
     sp = buf(2, np.float64) if r.sep_arcsec else None
-    _check(lib().hlc_result_to_host(C.byref(r), ia.ctypes.data, ib.ctypes.data,
-                                    sp.ctypes.data if sp is not None else None, None))
+    sp_ptr = sp.ctypes.data if sp is not None else None
+    if wait:
+        _check(lib().hlc_result_to_host(C.byref(r), ia.ctypes.data, ib.ctypes.data, sp_ptr, None))
+    else:
+        _check(lib().hlc_result_to_host_async(C.byref(r), ia.ctypes.data, ib.ctypes.data, sp_ptr,
+                                              None, plan.params.stream))
     return ia, ib, sp
 
 

@@ -3268,11 +3268,28 @@ int hlc_result_to_host(const hlc_result* r, uint64_t* id_a, uint64_t* id_b, doub
     return HLC_EINVAL;
   }
   if (r->n == 0) return HLC_OK;
+  // on the calling thread's own default stream (the result is complete once
+  // hlc_match has returned): a copy on the legacy default stream would also
+  // wait for, and hold up, the work other threads run on blocking streams
+  HLC_TRY(hlc_result_to_host_async(r, id_a, id_b, sep, job, (void*)cudaStreamPerThread));
+  HLC_CUDA(cudaStreamSynchronize(cudaStreamPerThread));
+  return HLC_OK;
+}
+
+int hlc_result_to_host_async(const hlc_result* r, uint64_t* id_a, uint64_t* id_b, double* sep,
+                             uint32_t* job, void* stream) {
+  clear_error();
+  if (!r) {
+    set_error("result is NULL");
+    return HLC_EINVAL;
+  }
+  if (r->n == 0) return HLC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
   cudaMemcpyKind k = r->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-  if (id_a) HLC_CUDA(cudaMemcpy(id_a, r->id_a, r->n * 8, k));
-  if (id_b) HLC_CUDA(cudaMemcpy(id_b, r->id_b, r->n * 8, k));
-  if (sep && r->sep_arcsec) HLC_CUDA(cudaMemcpy(sep, r->sep_arcsec, r->n * 8, k));
-  if (job && r->job) HLC_CUDA(cudaMemcpy(job, r->job, r->n * 4, k));
+  if (id_a) HLC_CUDA(cudaMemcpyAsync(id_a, r->id_a, r->n * 8, k, st));
+  if (id_b) HLC_CUDA(cudaMemcpyAsync(id_b, r->id_b, r->n * 8, k, st));
+  if (sep && r->sep_arcsec) HLC_CUDA(cudaMemcpyAsync(sep, r->sep_arcsec, r->n * 8, k, st));
+  if (job && r->job) HLC_CUDA(cudaMemcpyAsync(job, r->job, r->n * 4, k, st));
   return HLC_OK;
 }
 

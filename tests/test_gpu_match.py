@@ -232,3 +232,46 @@ def test_output_order_fallbacks(prec):
     assert want["id_a"].size >= nb
     same = np.full(ra_a.size, 12345, dtype=np.uint64)
     _check((ra_a, dec_a, same), (ra_b, dec_b, idb), 1.0, 12, hlc.HLC_COMPLETE8, prec)
+
+
+def test_plans_in_two_threads_and_stream_ordered_result_copies():
+    """Two host threads, each with its own stream, plan and match pinned host
+    catalogues at the same time; the rows copied back without waiting (read
+    after hlc_free, which synchronises the plan's stream) equal the oracle's."""
+    import threading
+    A, B = synth.fullsky_pair(na=300_000, nb=300_000)
+    An, Bn = A.numpy(), B.numpy()
+    want = O.match(*An, *Bn, 1.5, 12, O.COMPLETE)
+    n = want["id_a"].size
+    assert n > 50_000
+
+    def pinned(X):
+        return tuple(torch.as_tensor(np.asarray(v).view(np.int64) if v.dtype == np.uint64 else v)
+                     .pin_memory() for v in X)
+    Ah, Bh = pinned(An), pinned(Bn)
+    got, errs = {}, []
+
+    def worker(w):
+        try:
+            s = torch.cuda.Stream()
+            outb = tuple(torch.empty(n + 16, dtype=dt).pin_memory()
+                         for dt in (torch.int64, torch.int64, torch.float64))
+            for it in range(3):
+                plan = hlc.hlc_plan(Ah, Bh, 1.5, 12, precision=hlc.HLC_FP32_GUARD, stream=s)
+                hlc.hlc_match(plan, copy=False)
+                ia, ib, sp = hlc.hlc_result_to_host(plan, out=outb, wait=False)
+                hlc.hlc_free(plan)  # (synchronises the plan's stream: the copies are done)
+                got[(w, it)] = (ia.copy(), ib.copy(), sp.copy())
+        except Exception as e:  # noqa: BLE001 (reported below)
+            errs.append(e)
+    ths = [threading.Thread(target=worker, args=(w,)) for w in range(2)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    assert not errs, errs
+    assert len(got) == 6
+    for ia, ib, sp in got.values():
+        np.testing.assert_array_equal(ia, want["id_a"])
+        np.testing.assert_array_equal(ib, want["id_b"])
+        assert np.max(np.abs(sp - want["sep"])) <= SEP_TOL
