@@ -1396,21 +1396,26 @@ static int order_rows(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_t* bhist
     void* scr = ar.get(scan_scratch_bytes(nbk + 1));
     OutRow* t = ar.get_n<OutRow>(M + 1);
     uint32_t* big = ar.get_n<uint32_t>(nbk + 1);
-    if (!scr || !t || !big) return HLC_ENOMEM;
+    uint32_t* mid = ar.get_n<uint32_t>(nbk + 1);
+    if (!scr || !t || !big || !mid) return HLC_ENOMEM;
     HLC_TRY(scan_exclusive<uint32_t>(bhist, boff, nbk + 1, P->ctr + C_TOTAL, scr, P->dev_err, st));
-    HLC_CUDA(cudaMemsetAsync(P->ctr + C_MAXB, 0, 8, st));
+    uint32_t* nlist = (uint32_t*)(P->ctr + C_MAXB);  // [0] big buckets, [1] mid ones
+    HLC_CUDA(cudaMemsetAsync(nlist, 0, 8, st));
     k_bucket_scatter<<<g, kThreads, 0, st>>>(rows32, M, bshift, bmask, jbk, boff, t);
     HLC_LAUNCH_CHECK();
     k_bucket_small<<<g, kThreads, 0, st>>>(t, M, bshift, bmask, jbk, boff, a, b, sp, jb, big,
-                                           (uint32_t*)(P->ctr + C_MAXB), P->dev_err);
+                                           nlist, mid, P->dev_err);
     HLC_LAUNCH_CHECK();
-    k_bucket_sort<<<num_sms() * 8u, kBucketThreads, 0, st>>>(t, boff, big,
-                                                         (uint32_t*)(P->ctr + C_MAXB),
-                                                         want_sep ? 1 : 0, a, b, sp, jb);
+    k_bucket_sort<kBucketMid><<<num_sms() * 12u, kBucketThreads, 0, st>>>(
+        t, boff, mid, nlist + 1, want_sep ? 1 : 0, a, b, sp, jb);
+    HLC_LAUNCH_CHECK();
+    k_bucket_sort<kBucketCap><<<num_sms() * 4u, kBucketThreads, 0, st>>>(
+        t, boff, big, nlist, want_sep ? 1 : 0, a, b, sp, jb);
     HLC_LAUNCH_CHECK();
     ar.drop(scr);
     ar.drop(t);
     ar.drop(big);
+    ar.drop(mid);
     return HLC_OK;
   }
   // fallback: stable LSD radix sorts by id_b, id_a (and job)
@@ -2270,7 +2275,10 @@ static int match_batched(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   OutRow* rows32 = ar.get_n<OutRow>(M + 1);
   if (!rows32) return HLC_ENOMEM;
   // buckets: per job, bits of id_a enough for about four rows per bucket
-  // (the jobs' row counts differ by orders of magnitude)
+  // (the jobs' row counts differ by orders of magnitude), but no more than
+  // two to four buckets per A source of the job: a bucket cannot split the
+  // rows of one id_a, so more bits only add empty buckets (and keep the
+  // bucket counts out of L2)
   const int hb = P->id_high_bit;
   const uint32_t nj = P->njobs;
   std::vector<uint32_t> jrows(nj, 0u);
@@ -2290,6 +2298,9 @@ static int match_batched(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   for (uint32_t j = 0; j < nj; ++j) {
     int nb = 0;
     while (nb < 24 && (jrows[j] >> (nb + 2)) > 0) ++nb;
+    int na_bits = 1;
+    while (na_bits < 24 && (1ull << (na_bits - 1)) < P->jobs_h[j].n[0]) ++na_bits;
+    nb = std::min(nb, na_bits);
     if (nb > hb + 1) nb = std::max(hb + 1, 0);
     hjb[j] = make_uint4((uint32_t)nbk, hb >= 0 ? (uint32_t)(hb + 1 - nb) : 0u,
                         nb ? (uint32_t)((1ull << nb) - 1) : 0u, 0u);

@@ -18,6 +18,7 @@
 namespace hlc {
 
 constexpr int kBucketCap = 2048;
+constexpr int kBucketMid = 256;  // buckets up to this many rows: the small-array sort
 constexpr int kBucketThreads = 128;
 
 __device__ __forceinline__ double sep_arcsec_from_chord2(double s) {
@@ -163,16 +164,17 @@ __device__ __forceinline__ bool row_less(uint64_t a1, uint64_t b1, uint64_t s1, 
 // adjacent, so the comparisons read from L1.)
 constexpr uint32_t kSmallBucket = 32;
 
-// (The first row of each larger bucket appends it to `big` for
-// k_bucket_sort; one above kBucketCap sets DERR_BUCKET and the host orders
-// the rows another way.)
+// (The first row of each larger bucket appends it to `mid` (up to
+// kBucketMid rows) or `big` for k_bucket_sort; one above kBucketCap sets
+// DERR_BUCKET and the host orders the rows another way.  nbig[0] counts the
+// big ones, nbig[1] the mid ones.)
 __global__ void k_bucket_small(const OutRow* __restrict__ t, uint64_t M, int bshift,
                                uint32_t bmask, const uint4* __restrict__ jb,
                                const uint32_t* __restrict__ boff,
                                uint64_t* __restrict__ oa, uint64_t* __restrict__ ob,
                                double* __restrict__ os, uint32_t* __restrict__ oj,
                                uint32_t* __restrict__ big, uint32_t* __restrict__ nbig,
-                               int* __restrict__ err) {
+                               uint32_t* __restrict__ mid, int* __restrict__ err) {
   for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < M;
        p += (uint64_t)gridDim.x * blockDim.x) {
     const OutRow r = t[p];
@@ -183,6 +185,8 @@ __global__ void k_bucket_small(const OutRow* __restrict__ t, uint64_t M, int bsh
       if (p == lo) {
         if (n > kBucketCap)
           atomicOr(err, DERR_BUCKET);
+        else if (n <= kBucketMid)
+          mid[atomicAdd(nbig + 1, 1u)] = (uint32_t)bk;
         else
           big[atomicAdd(nbig, 1u)] = (uint32_t)bk;
       }
@@ -206,20 +210,22 @@ __global__ void k_bucket_small(const OutRow* __restrict__ t, uint64_t M, int bsh
   }
 }
 
-// One CTA per larger bucket (kSmallBucket < rows <= kBucketCap): bitonic
-// sort in shared memory.
+// One CTA per larger bucket (kSmallBucket < rows <= CAP): bitonic sort in
+// shared memory, each thread on one comparator of a stage at a time.  CAP =
+// kBucketMid keeps the arrays small (6 KB), so that many CTAs share an SM.
+template <int CAP>
 __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(
     const OutRow* __restrict__ t, const uint32_t* __restrict__ boff,
     const uint32_t* __restrict__ big, const uint32_t* __restrict__ nbig, int use_sep,
     uint64_t* __restrict__ oa, uint64_t* __restrict__ ob, double* __restrict__ os,
     uint32_t* __restrict__ oj) {
-  __shared__ uint64_t A[kBucketCap], B[kBucketCap], S[kBucketCap];
+  __shared__ uint64_t A[CAP], B[CAP], S[CAP];
   const uint32_t nb = *nbig;
   for (uint32_t q = blockIdx.x; q < nb; q += gridDim.x) {
     const uint32_t bk = big[q];
     uint32_t lo = boff[bk], hi = boff[bk + 1];
     uint32_t n = hi - lo;
-    if (n <= kSmallBucket || n > kBucketCap) continue;  // (listed ones are in range)
+    if (n <= kSmallBucket || n > (uint32_t)CAP) continue;  // (listed ones are in range)
     uint32_t np = 1;
     while (np < n) np <<= 1;
     for (uint32_t i = threadIdx.x; i < np; i += kBucketThreads) {
@@ -238,17 +244,17 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(
     __syncthreads();
     for (uint32_t k = 2; k <= np; k <<= 1) {
       for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-        for (uint32_t i = threadIdx.x; i < np; i += kBucketThreads) {
-          uint32_t l = i ^ j;
-          if (l > i) {
-            bool up = (i & k) == 0;
-            bool gt = row_less(A[l], B[l], S[l], A[i], B[i], S[i]);
-            if (gt == up) {
-              uint64_t t;
-              t = A[i]; A[i] = A[l]; A[l] = t;
-              t = B[i]; B[i] = B[l]; B[l] = t;
-              t = S[i]; S[i] = S[l]; S[l] = t;
-            }
+        for (uint32_t c = threadIdx.x; c < np / 2; c += kBucketThreads) {
+          // comparator c: the pair (i, i + j) with bit j of i clear
+          const uint32_t i = ((c & ~(j - 1)) << 1) | (c & (j - 1));
+          const uint32_t l = i | j;
+          bool up = (i & k) == 0;
+          bool gt = row_less(A[l], B[l], S[l], A[i], B[i], S[i]);
+          if (gt == up) {
+            uint64_t t;
+            t = A[i]; A[i] = A[l]; A[l] = t;
+            t = B[i]; B[i] = B[l]; B[l] = t;
+            t = S[i]; S[i] = S[l]; S[l] = t;
           }
         }
         __syncthreads();
