@@ -500,8 +500,8 @@ TRAFFIC = {
     # 161,055,744 + 120,093,952 and 160,616,960 + 119,799,296 B; their mean
     "k_onesweep": {"bytes_per_launch": 254366720, "sources": "5333daf1bd4fd395",
                    "files": ("sort.cuh", "common.cuh")},
-    # the pair test: 495,089,664 B read + 42,944,768 B written
-    "k_pair<1,0,0,1>": {"bytes_per_launch": 538034432, "sources": "642f2488d4f0e024",
+    # the pair test: 495,118,592 B read + 42,904,320 B written
+    "k_pair<1,0,0,1>": {"bytes_per_launch": 538022912, "sources": "b2b9718ea7763aa0",
                         "files": ("match.cuh", "canon.cuh", "index.cuh", "learned.cuh",
                                   "common.cuh", "fp32.cuh", "fastpix.cuh")},
 }
@@ -939,7 +939,7 @@ def run_batched(args):
             n_ += hlc.hlc_match(plan, copy=False)["n"]
             hlc.hlc_free(plan)
         return n_
-    ms_j, nj_ = _timed_loop(per_job, 1, 1, stream)
+    ms_j, nj_ = _timed_loop(per_job, 1, 1, stream) if not args.no_per_job else (float("nan"), 0)
     _line(args, "sources matched/s, batched cone jobs", total / (ms_b / 1e3), "sources/s", ms_b,
           {"workload": "%d cone-pair jobs (cone 0.1-2 deg, N log-uniform %g-%g per side, "
                        "r 0.5-5 arcsec), %d sources" % (njobs, 1e3 * args.scale, 1e6 * args.scale,
@@ -1157,6 +1157,8 @@ def main():
     ap.add_argument("--e2e-depth", type=int, default=3,
                     help="steps in flight in the end-to-end throughput run")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-per-job", action="store_true",
+                    help="batched: skip the one-plan-per-job comparison (profiling runs)")
     ap.add_argument("--no-other-mode", action="store_true",
                     help="skip the other boundary mode's sub-line")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense-cell sub-line")

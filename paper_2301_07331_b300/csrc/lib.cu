@@ -2192,7 +2192,9 @@ static int batched_pair_graph(hlc_plan_t* P, uint2* rows, uint64_t cap, uint2* b
         ta.cell_bits = P->cell_bits;
         for (int c = 0; c < 3; ++c) ta.ka[c] = P->tile_ka[c];
         ta.stage = P->tile_stage;
-        k_pair_tile<false><<<num_sms() * 3u, kTileThreads + 32, tile_smem, cs>>>(ta, sink);
+        PairSink tsink = sink;  // (its own test counter)
+        tsink.tests = P->ctr + C_TILE_TESTS;
+        k_pair_tile<false><<<num_sms() * 3u, kTileThreads + 32, tile_smem, cs>>>(ta, tsink);
       }
     }
     e = cudaStreamEndCapture(cs, &g);
@@ -2350,7 +2352,8 @@ static int match_batched(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   res->sep_arcsec = want_sep ? os : nullptr;
   res->job = oj;
   res->on_device = 1;
-  P->stats.pair_tests = h[C_TESTS];
+  P->stats.pair_tests = h[C_TESTS] + h[C_TILE_TESTS];
+  P->stats.tile_tests = h[C_TILE_TESTS];
   P->stats.band_candidates = fp32 ? h[C_BAND] : 0;
   P->stats.band_fp64 = fp32 ? band64 : 0;
   P->stats.matches = M;

@@ -60,7 +60,10 @@ namespace hlc {
 constexpr int kTileThreads = 256;                   // consumer threads (+1 producer warp)
 constexpr int kTileWarps = kTileThreads / 32;
 constexpr int kTileCap = 1536;                      // B vectors per stage buffer (24 KB)
-constexpr uint32_t kTileMinA = 32;                  // smaller cells stay with the lane kernels
+#ifndef HLC_TILE_MIN_A
+#define HLC_TILE_MIN_A 32
+#endif
+constexpr uint32_t kTileMinA = HLC_TILE_MIN_A;      // smaller cells stay with the lane kernels
 constexpr uint32_t kTileChunkA = 128;               // A sources per work item (a larger cell is split)
 constexpr uint32_t kTileChunkB = 1024;              // B vectors per work item's window
 constexpr uint32_t kTileItemDiv = 8;                // items per cell <= its A sources / 8
