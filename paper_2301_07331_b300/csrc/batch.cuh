@@ -317,18 +317,40 @@ struct BPairArgs {
 // work counter until all entries of all jobs are done.  As in k_pair, a lane
 // in a sparse region reads the (at most 4) table cells covering its fine 3x3
 // block whole, rows are staged per warp in shared memory, and lanes whose A
-// entry the dense-cell kernel takes (tiled) stay idle.
+// entry the dense-cell kernel takes (tiled) stay idle.  In a dense table cell
+// the 9 fine ranges (two binary searches each) are the same for every A
+// entry of a cell: they are looked up once per run of equal keys in the
+// chunk, the runs' lookups spread over the warp's lanes, and read back from
+// shared memory by each lane of the run.
+__device__ __forceinline__ int nth_set_bit(unsigned m, int r) {  // r < popc(m), 0-based
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const int c = __popc(m & ((1u << w) - 1u));
+    if (r >= c) {
+      r -= c;
+      m >>= w;
+      pos += w;
+    }
+  }
+  return pos;
+}
+
 template <bool FP32>
 __global__ void __launch_bounds__(kThreads) k_bpair(const BPairArgs pa, PairSink sink) {
   const uint64_t nchunks = (pa.mA + 31) / 32;
   const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   const uint64_t cmask = (1ull << pa.cell_bits) - 1;
   unsigned long long ntest = 0;
   constexpr int kRowCap = 256, kBandCap = FP32 ? 128 : 32;
   __shared__ uint2 s_rows[kThreads / 32][kRowCap];
   __shared__ uint2 s_band[kThreads / 32][kBandCap];
-  WarpRows<kRowCap> wrows{s_rows[threadIdx.x >> 5]};
-  WarpRows<kBandCap> wband{s_band[threadIdx.x >> 5]};
+  __shared__ uint32_t s_nbc[kThreads / 32][32 * 9];  // 9 cells of each run head
+  __shared__ uint2 s_rng[kThreads / 32][32 * 9];     // and their B ranges
+  __shared__ uint32_t s_job[kThreads / 32][32];
+  WarpRows<kRowCap> wrows{s_rows[warp]};
+  WarpRows<kBandCap> wband{s_band[warp]};
   for (;;) {
     unsigned long long chunk = 0;
     if (lane == 0) chunk = atomicAdd(pa.work, 1ull);
@@ -339,8 +361,8 @@ __global__ void __launch_bounds__(kThreads) k_bpair(const BPairArgs pa, PairSink
     if (live && pa.tiled && pa.tiled[k]) live = false;
     uint32_t j = 0, cell = 0;
     JobTab J = {0, 0, 0u, 0u, 0ull, 0.0, 0.f, 0.f};
+    const uint64_t key = live ? pa.keyA[k] : ~0ull;
     if (live) {
-      uint64_t key = pa.keyA[k];
       j = (uint32_t)(key >> pa.cell_bits);
       cell = (uint32_t)(key & cmask);
       J = load_job(pa.jobs, j);
@@ -367,6 +389,35 @@ __global__ void __launch_bounds__(kThreads) k_bpair(const BPairArgs pa, PairSink
       }
       if (!coarse) cell_neighbourhood9(cell, J.L, nb);
     }
+    // the fine ranges of the runs that need them: one lookup per (run, cell)
+    const uint64_t kprev = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool head = live && (lane == 0 || kprev != key);
+    const bool fine = live && !coarse;  // (the same for every lane of a run)
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const unsigned fine_heads = __ballot_sync(0xffffffffu, head && fine);
+    if (fine_heads) {
+      if (head && fine) {
+#pragma unroll
+        for (int s = 0; s < 9; ++s) s_nbc[warp][lane * 9 + s] = nb[s];
+        s_job[warp][lane] = j;
+      }
+      __syncwarp();
+      const int ntask = 9 * __popc(fine_heads);
+      for (int t = lane; t < ntask; t += 32) {
+        const int r = t / 9, s = t - 9 * r;
+        const int h = nth_set_bit(fine_heads, r);
+        const uint32_t c = s_nbc[warp][h * 9 + s];
+        uint2 rg = make_uint2(0u, 0u);
+        if (c != kNoCell) {
+          const uint32_t jh = s_job[warp][h];
+          rg = bcell_range(pa.keyB, pa.table, load_job(pa.jobs, jh), jh, pa.cell_bits, c);
+        }
+        s_rng[warp][h * 9 + s] = rg;
+      }
+      __syncwarp();
+    }
+    // (a live lane's run head: the highest head at or below it)
+    const int myhead = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
     uint32_t rb[9], re[9];
     uint32_t total = 0;
 #pragma unroll
@@ -380,7 +431,7 @@ __global__ void __launch_bounds__(kThreads) k_bpair(const BPairArgs pa, PairSink
             r = make_uint2(__ldg(pa.table + slot), __ldg(pa.table + slot + 1));
           }
         } else {
-          r = bcell_range(pa.keyB, pa.table, J, j, pa.cell_bits, nb[s]);
+          r = s_rng[warp][myhead * 9 + s];
         }
       }
       rb[s] = r.x;
