@@ -129,10 +129,7 @@ int ensure_device_tables() {
   return HLC_OK;
 }
 
-static int check_dev_err(const int* dev_err, cudaStream_t st, const char* what) {
-  int h = 0;
-  HLC_CUDA(cudaMemcpyAsync(&h, dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  HLC_CUDA(cudaStreamSynchronize(st));
+static int dev_err_status(int h, const char* what) {
   if (h & DERR_INPUT) {
     set_error("%s: invalid input (non-finite RA/Dec or |Dec| > 90)", what);
     return HLC_EINVAL;
@@ -146,6 +143,13 @@ static int check_dev_err(const int* dev_err, cudaStream_t st, const char* what) 
     return HLC_ECUDA;
   }
   return HLC_OK;
+}
+
+static int check_dev_err(const int* dev_err, cudaStream_t st, const char* what) {
+  int h = 0;
+  HLC_CUDA(cudaMemcpyAsync(&h, dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HLC_CUDA(cudaStreamSynchronize(st));
+  return dev_err_status(h, what);
 }
 
 // Theta_L / 8 in arcsec: the largest radius for which the complete rule is exact.
@@ -1366,10 +1370,12 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
 // bucket scatter + per-bucket sorts, or two or three stable radix sorts when
 // a bucket would not fit in shared memory.  jbk null: single job; else the
 // batched plan's per-job bucket table (row_bucket).
+// Mdev (bucketed form only): the rows are counted on the device, M being the
+// bound the buffers are sized by.
 static int order_rows(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_t* bhist,
                       uint32_t* boff, uint64_t nbk, const uint4* jbk, int bshift, uint32_t bmask,
                       bool bucketed, bool want_sep, uint64_t** oa, uint64_t** ob, double** os,
-                      uint32_t** oj) {
+                      uint32_t** oj, const unsigned long long* Mdev = nullptr) {
   Arena& ar = *P->out;
   cudaStream_t st = plan_stream(P);
   const bool batched = jbk != nullptr;
@@ -1384,7 +1390,11 @@ static int order_rows(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_t* bhist
   *oj = jb;
   if (M == 0) return HLC_OK;
   unsigned g = grid_for(M, kThreads);
-  if (M == 1) {
+  if (Mdev && !(bucketed && nbk < (1ull << 31))) {
+    set_error("row ordering: a device row count needs the bucketed form");
+    return HLC_EINVAL;
+  }
+  if (M == 1 && !Mdev) {
     k_rows_split<<<1, 32, 0, st>>>(rows32, M, a, b, sp, jb);
     HLC_LAUNCH_CHECK();
     return HLC_OK;
@@ -1401,10 +1411,10 @@ static int order_rows(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_t* bhist
     HLC_TRY(scan_exclusive<uint32_t>(bhist, boff, nbk + 1, P->ctr + C_TOTAL, scr, P->dev_err, st));
     uint32_t* nlist = (uint32_t*)(P->ctr + C_MAXB);  // [0] big buckets, [1] mid ones
     HLC_CUDA(cudaMemsetAsync(nlist, 0, 8, st));
-    k_bucket_scatter<<<g, kThreads, 0, st>>>(rows32, M, bshift, bmask, jbk, boff, t);
+    k_bucket_scatter<<<g, kThreads, 0, st>>>(rows32, M, bshift, bmask, jbk, boff, t, Mdev);
     HLC_LAUNCH_CHECK();
     k_bucket_small<<<g, kThreads, 0, st>>>(t, M, bshift, bmask, jbk, boff, a, b, sp, jb, big,
-                                           nlist, mid, P->dev_err);
+                                           nlist, mid, P->dev_err, Mdev);
     HLC_LAUNCH_CHECK();
     k_bucket_sort<kBucketMid><<<num_sms() * 12u, kBucketThreads, 0, st>>>(
         t, boff, mid, nlist + 1, want_sep ? 1 : 0, a, b, sp, jb);
@@ -1452,14 +1462,18 @@ static int order_rows(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_t* bhist
 }
 
 // order_rows, then (after the stream has drained) a repeat with the radix
-// sorts when a bucket was too large for the in-block sort.
+// sorts when a bucket was too large for the in-block sort.  With Mdev the
+// stream is not drained here: the caller checks DERR_BUCKET at its own final
+// synchronisation (see redo_order_rows).
 static int order_rows_checked(hlc_plan_t* P, OutRow* rows32, uint64_t M, uint32_t* bhist,
                               uint32_t* boff, uint64_t nbk, const uint4* jbk, int bshift,
                               uint32_t bmask, bool bucketed, bool want_sep, uint64_t** oa,
-                              uint64_t** ob, double** os, uint32_t** oj) {
+                              uint64_t** ob, double** os, uint32_t** oj,
+                              const unsigned long long* Mdev = nullptr) {
   cudaStream_t st = plan_stream(P);
   HLC_TRY(order_rows(P, rows32, M, bhist, boff, nbk, jbk, bshift, bmask, bucketed, want_sep,
-                     oa, ob, os, oj));
+                     oa, ob, os, oj, Mdev));
+  if (Mdev) return HLC_OK;
   int h = 0;
   HLC_CUDA(cudaMemcpyAsync(&h, P->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   HLC_CUDA(cudaStreamSynchronize(st));
@@ -1621,18 +1635,27 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
     HLC_LAUNCH_CHECK();
   }
   ev_record(P, 5);
+  // The recheck may still add rows when the output stage is issued: with
+  // bucketed output the kernels take the device's count, their buffers sized
+  // by the bound M (rows before the recheck plus every band candidate), and
+  // the count comes back with the final synchronisation.
   unsigned long long M = h[C_ROWS];
+  int hb = P->id_high_bit;
+  const unsigned long long* Mdev = nullptr;
   if (fp32 && h[C_BAND]) {
-    HLC_CUDA(cudaMemcpyAsync(&M, P->ctr + C_ROWS, 8, cudaMemcpyDeviceToHost, st));
-    HLC_CUDA(cudaStreamSynchronize(st));
+    if (M + h[C_BAND] > 1 && hb >= 0) {
+      M += h[C_BAND];
+      Mdev = P->ctr + C_ROWS;
+    } else {
+      HLC_CUDA(cudaMemcpyAsync(&M, P->ctr + C_ROWS, 8, cudaMemcpyDeviceToHost, st));
+      HLC_CUDA(cudaStreamSynchronize(st));
+    }
   }
-  HLC_TRY(check_dev_err(P->dev_err, st, "hlc_match"));
   ar.drop(band);
   // rows: ids, separations, bucket histogram of id_a (about four rows per bucket)
   const bool want_sep = P->p.want_sep != 0;
   OutRow* rows32 = ar.get_n<OutRow>(M + 1);
   if (!rows32) return HLC_ENOMEM;
-  int hb = P->id_high_bit;
   int nbits = 1;
   while (nbits < 24 && (M >> (nbits + 2)) > 0) ++nbits;
   if (hb >= 0 && nbits > hb + 1) nbits = hb + 1;
@@ -1655,7 +1678,7 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
                                             P->table_buckets ? nullptr : B.idx, A.rec, B.rec,
                                             nullptr, nullptr,
                                             nullptr, nullptr, nullptr, nullptr, want_sep, rows32,
-                                            bshift, bmask, bhist);
+                                            bshift, bmask, bhist, Mdev);
     else
       k_rows<false><<<g, kThreads, 0, st>>>(rows, M, A.idx, B.idx, A.rec, B.rec, A.vx, A.vy,
                                              A.vz, B.vx, B.vy, B.vz, want_sep, rows32, bshift,
@@ -1667,17 +1690,35 @@ static int match_single(hlc_plan_t* P, hlc_result* res, hlc_stats* stats) {
   double* os = nullptr;
   uint32_t* oj = nullptr;
   HLC_TRY(order_rows_checked(P, rows32, M, bhist, boff, nbk, nullptr, bshift, bmask, bucketed,
-                             want_sep, &oa, &ob, &os, &oj));
-  ar.drop(rows32);
+                             want_sep, &oa, &ob, &os, &oj, Mdev));
+  if (!Mdev) ar.drop(rows32);
   if (bhist) {
     ar.drop(bhist);
     ar.drop(boff);
   }
   ev_record(P, 6);
-  unsigned long long band64 = 0;
-  HLC_CUDA(cudaMemcpyAsync(&band64, P->ctr + C_BAND64, 8, cudaMemcpyDeviceToHost, st));
+  // one synchronisation: binary64 band decisions, the final row count, errors
+  unsigned long long fin[2] = {0, 0};
+  int e = 0;
+  HLC_CUDA(cudaMemcpyAsync(&fin[0], P->ctr + C_BAND64, 8, cudaMemcpyDeviceToHost, st));
+  if (Mdev) HLC_CUDA(cudaMemcpyAsync(&fin[1], Mdev, 8, cudaMemcpyDeviceToHost, st));
+  HLC_CUDA(cudaMemcpyAsync(&e, P->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   HLC_CUDA(cudaStreamSynchronize(st));
-  HLC_TRY(check_dev_err(P->dev_err, st, "hlc_match"));
+  HLC_TRY(dev_err_status(e, "hlc_match"));
+  const unsigned long long band64 = fin[0];
+  if (Mdev) {
+    M = fin[1];
+    if (e & DERR_BUCKET) {  // a bucket too large for the in-block sort: the radix sorts
+      for (void* q : {(void*)oa, (void*)ob, (void*)os, (void*)oj})
+        if (q) ar.drop(q);
+      e &= ~DERR_BUCKET;
+      HLC_CUDA(cudaMemcpyAsync(P->dev_err, &e, sizeof(int), cudaMemcpyHostToDevice, st));
+      HLC_TRY(order_rows(P, rows32, M, nullptr, nullptr, 0, nullptr, 0, 0u, false, want_sep, &oa,
+                         &ob, &os, &oj));
+      HLC_CUDA(cudaStreamSynchronize(st));
+    }
+    ar.drop(rows32);
+  }
   res->n = M;
   res->id_a = oa;
   res->id_b = ob;

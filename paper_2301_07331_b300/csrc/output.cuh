@@ -67,16 +67,25 @@ struct __align__(32) OutRow {
   uint32_t job, pad;
 };
 
+// The row count of the output kernels: M, or (Mdev given) the device's count
+// clamped to M, the bound the caller sized the buffers by (the recheck may
+// still have been adding rows when the launches were issued).
+__device__ __forceinline__ uint64_t row_count(uint64_t M, const unsigned long long* Mdev) {
+  return Mdev ? min((uint64_t)*Mdev, M) : M;
+}
+
 // ids + separation of each row, and the bucket histogram of id_a.
 template <bool FP32>
-__global__ void k_rows(const uint2* __restrict__ rows, uint64_t M,
+__global__ void k_rows(const uint2* __restrict__ rows, uint64_t Mb,
                        const uint32_t* __restrict__ idxA, const uint32_t* __restrict__ idxB,
                        const SrcRec* __restrict__ recA, const SrcRec* __restrict__ recB,
                        const double* __restrict__ axv, const double* __restrict__ ayv,
                        const double* __restrict__ azv, const double* __restrict__ bxv,
                        const double* __restrict__ byv, const double* __restrict__ bzv,
                        int want_sep, OutRow* __restrict__ out, int bshift, uint32_t bmask,
-                       uint32_t* __restrict__ bhist) {
+                       uint32_t* __restrict__ bhist,
+                       const unsigned long long* __restrict__ Mdev = nullptr) {
+  const uint64_t M = row_count(Mb, Mdev);
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
        m += (uint64_t)gridDim.x * blockDim.x) {
     uint2 p = rows[m];  // entry indices, or source indices when idxA/idxB are null
@@ -140,10 +149,12 @@ __device__ __forceinline__ uint64_t row_bucket(const OutRow& o, int bshift, uint
   return (uint32_t)(o.a >> bshift) & bmask;
 }
 
-__global__ void k_bucket_scatter(const OutRow* __restrict__ in, uint64_t M, int bshift,
+__global__ void k_bucket_scatter(const OutRow* __restrict__ in, uint64_t Mb, int bshift,
                                  uint32_t bmask, const uint4* __restrict__ jb,
                                  const uint32_t* __restrict__ boff,
-                                 OutRow* __restrict__ out) {
+                                 OutRow* __restrict__ out,
+                                 const unsigned long long* __restrict__ Mdev = nullptr) {
+  const uint64_t M = row_count(Mb, Mdev);
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M;
        m += (uint64_t)gridDim.x * blockDim.x) {
     OutRow o = in[m];
@@ -168,13 +179,15 @@ constexpr uint32_t kSmallBucket = 32;
 // kBucketMid rows) or `big` for k_bucket_sort; one above kBucketCap sets
 // DERR_BUCKET and the host orders the rows another way.  nbig[0] counts the
 // big ones, nbig[1] the mid ones.)
-__global__ void k_bucket_small(const OutRow* __restrict__ t, uint64_t M, int bshift,
+__global__ void k_bucket_small(const OutRow* __restrict__ t, uint64_t Mb, int bshift,
                                uint32_t bmask, const uint4* __restrict__ jb,
                                const uint32_t* __restrict__ boff,
                                uint64_t* __restrict__ oa, uint64_t* __restrict__ ob,
                                double* __restrict__ os, uint32_t* __restrict__ oj,
                                uint32_t* __restrict__ big, uint32_t* __restrict__ nbig,
-                               uint32_t* __restrict__ mid, int* __restrict__ err) {
+                               uint32_t* __restrict__ mid, int* __restrict__ err,
+                               const unsigned long long* __restrict__ Mdev = nullptr) {
+  const uint64_t M = row_count(Mb, Mdev);
   for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < M;
        p += (uint64_t)gridDim.x * blockDim.x) {
     const OutRow r = t[p];
