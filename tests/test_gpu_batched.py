@@ -188,3 +188,30 @@ def test_prepared_job_list_is_reusable_and_equals_the_list_form():
         for g, w in zip(got, want):
             np.testing.assert_array_equal(g, w)
     assert want[0].size > 100
+
+
+@pytest.mark.parametrize("prec", [hlc.HLC_FP32_GUARD, hlc.HLC_FP64])
+def test_output_bucket_size_classes_in_batched_plans(prec):
+    """Jobs whose A sources are matched 40 to 3000 times each (every bucket
+    size class, and the radix fallback for the whole output) give the
+    oracle's rows job by job, in (job, id_a, id_b) order."""
+    rng = np.random.default_rng(31)
+
+    def clumps(ks, ra0, dec0):
+        ra_a = np.array([ra0 + 2.0 * i for i in range(len(ks))])
+        dec_a = np.array([dec0 + 1.0 * i for i in range(len(ks))])
+        ra_b = np.concatenate([ra_a[i] + rng.uniform(-1, 1, k) * 0.3 / 3600
+                               for i, k in enumerate(ks)])
+        dec_b = np.concatenate([dec_a[i] + rng.uniform(-1, 1, k) * 0.3 / 3600
+                                for i, k in enumerate(ks)])
+        mk = lambda ra, dec: synth.Catalogue(
+            torch.as_tensor(ra), torch.as_tensor(dec),
+            torch.as_tensor(rng.integers(0, 2 ** 63, ra.size).astype(np.uint64).view(np.int64)))
+        return mk(ra_a, dec_a), mk(ra_b, dec_b)
+
+    class Job:
+        def __init__(self, A, B):
+            self.A, self.B, self.r_arcsec = A, B, 1.0
+    jobs = [Job(*clumps([40, 200], 30.0, 5.0)), Job(*clumps([300, 1500], 60.0, -5.0)),
+            Job(*clumps([3000], 90.0, 10.0))]
+    assert _check(jobs, prec, level=12) == 40 + 200 + 300 + 1500 + 3000

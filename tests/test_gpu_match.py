@@ -275,3 +275,38 @@ def test_plans_in_two_threads_and_stream_ordered_result_copies():
         np.testing.assert_array_equal(ia, want["id_a"])
         np.testing.assert_array_equal(ib, want["id_b"])
         assert np.max(np.abs(sp - want["sep"])) <= SEP_TOL
+
+
+def _clumped_pair(ks, seed, n_background=3000):
+    """A: one source per clump plus a sparse background; B: k sources within
+    0.3 arcsec of clump i's A source for k = ks[i], so that the A source's id
+    is matched exactly k times (an output bucket of at least k rows)."""
+    rng = np.random.default_rng(seed)
+    ra_a = [15.0 + 3.0 * i for i in range(len(ks))]
+    dec_a = [-10.0 + 2.0 * i for i in range(len(ks))]
+    ra_b, dec_b = [], []
+    for i, k in enumerate(ks):
+        ra_b.append(ra_a[i] + rng.uniform(-1, 1, k) * 0.3 / 3600)
+        dec_b.append(dec_a[i] + rng.uniform(-1, 1, k) * 0.3 / 3600)
+    ra_a = np.concatenate([ra_a, rng.uniform(0, 360, n_background)])
+    dec_a = np.concatenate([dec_a, rng.uniform(-60, 60, n_background)])
+    ra_b = np.concatenate(ra_b + [rng.uniform(0, 360, n_background)])
+    dec_b = np.concatenate(dec_b + [rng.uniform(-60, 60, n_background)])
+    ida = rng.integers(0, 2 ** 63, ra_a.size).astype(np.uint64)
+    idb = rng.integers(0, 2 ** 63, ra_b.size).astype(np.uint64)
+    return (ra_a, dec_a, ida), (ra_b, dec_b, idb)
+
+
+@pytest.mark.parametrize("prec", [hlc.HLC_FP64, hlc.HLC_FP32_GUARD])
+def test_output_bucket_size_classes(prec):
+    """Buckets ordered by rank counting (<= 32 rows), by the small-array
+    bitonic sort (33-256), by the large one (257-2048) and by the radix
+    fallback (3000 rows for one id) give the oracle's rows in order."""
+    ks = [40, 200, 300, 1500]
+    A, B = _clumped_pair(ks, seed=21)
+    want, st = _check(A, B, 1.0, 12, hlc.HLC_COMPLETE8, prec)
+    for i, k in enumerate(ks):
+        assert np.count_nonzero(want["id_a"] == A[2][i]) == k
+    A, B = _clumped_pair([3000, 300, 40], seed=22)
+    want, st = _check(A, B, 1.0, 12, hlc.HLC_COMPLETE8, prec)
+    assert np.count_nonzero(want["id_a"] == A[2][0]) == 3000
