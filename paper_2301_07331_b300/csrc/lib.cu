@@ -297,7 +297,7 @@ struct PinnedBuf {
 
 enum Ctr { C_ROWS = 0, C_BAND, C_TESTS, C_DUPS, C_M, C_TOTAL, C_HEADS_A, C_HEADS_B, C_DENSE,
            C_WORK, C_IDDIFF, C_MAXB, C_SLOW, C_LHITS, C_LLOOK, C_LMAXERR, C_SCRATCH, C_BAND64,
-           C_SLOW_A, C_EMAXA, C_EMAXB, C_TILE_TESTS, C_N };
+           C_SLOW_A, C_EMAXA, C_EMAXB, C_TILE_TESTS, C_DCELLS, C_N };
 
 }  // namespace hlc
 
@@ -347,6 +347,7 @@ struct hlc_plan_s {
   uint64_t *host_a = nullptr, *host_b = nullptr;
   double* host_s = nullptr;
   uint32_t sparse_cell = hlc::kSparseCell;
+  uint32_t* dcells = nullptr;  // dense cells of B's table, ascending (count at ctr[C_DCELLS])
   bool table_buckets = false;  // FP32 complete mode: entries bucketed by table cell
   uint32_t sort_passes = 0;    // radix passes of the table-cell sorts (ev 7-8: B, 9-10: A)
   uint64_t sort_entries = 0;   // entries those passes moved, summed over the launches
@@ -541,22 +542,43 @@ static int dense_fixup(hlc_plan_t* P, CatDev& X, const uint32_t* T, int shift, b
   cudaStream_t st = plan_stream(P);
   const uint64_t n = X.n;
   const int bits = 2 * P->p.fine_level + 4;
-  uint32_t* flag = ar.get_n<uint32_t>(n + 1);
-  uint32_t* off = ar.get_n<uint32_t>(n + 1);
-  void* scr = ar.get(scan_scratch_bytes(n));
-  if (!flag || !off || !scr) return HLC_ENOMEM;
-  k_dense_flags<<<grid_for(n, kThreads), kThreads, 0, st>>>(X.key, n, shift, T, P->sparse_cell,
-                                                            flag);
+  // the dense cells of B's table T (listed by B's pass, reused by A's):
+  // each holds more than sparse_cell of B's entries, which bounds their number
+  const uint64_t S = 12ull << (2 * P->B.table_order);
+  const uint64_t cap = P->B.n / ((uint64_t)P->sparse_cell + 1) + 1;
+  if (T == X.table || !P->dcells) {
+    const uint64_t nblk = (S + kDenseBlkSlots - 1) / kDenseBlkSlots;
+    uint32_t* blkcnt = ar.get_n<uint32_t>(nblk + 1);
+    uint32_t* blkoff = ar.get_n<uint32_t>(nblk + 1);
+    void* bscr = ar.get(scan_scratch_bytes(nblk));
+    P->dcells = ar.get_n<uint32_t>(cap);
+    if (!blkcnt || !blkoff || !bscr || !P->dcells) return HLC_ENOMEM;
+    k_dense_cell_blocks<<<(unsigned)nblk, 256, 0, st>>>(T, S, P->sparse_cell, blkcnt);
+    HLC_LAUNCH_CHECK();
+    HLC_TRY(scan_exclusive<uint32_t>(blkcnt, blkoff, nblk, P->ctr + C_DCELLS, bscr, P->dev_err,
+                                     st));
+    k_dense_cell_list<<<(unsigned)nblk, 256, 0, st>>>(T, S, P->sparse_cell, blkoff, P->dcells);
+    HLC_LAUNCH_CHECK();
+    for (void* q : {(void*)blkcnt, (void*)blkoff, bscr}) ar.drop(q);
+  }
+  // their entry ranges in X (from the table for B, by search in A's keys),
+  // offsets by a scan over the (bounded) list, the total read back
+  uint2* rng = ar.get_n<uint2>(cap);
+  uint32_t* len = ar.get_n<uint32_t>(cap + 1);
+  uint32_t* off = ar.get_n<uint32_t>(cap + 1);
+  void* scr = ar.get(scan_scratch_bytes(cap + 1));
+  if (!rng || !len || !off || !scr) return HLC_ENOMEM;
+  HLC_CUDA(cudaMemsetAsync(len, 0, (cap + 1) * 4, st));
+  k_dense_cell_ranges<<<grid_for(cap, kThreads), kThreads, 0, st>>>(
+      P->dcells, P->ctr + C_DCELLS, T, T == X.table ? nullptr : X.key, n, shift, rng, len);
   HLC_LAUNCH_CHECK();
-  HLC_TRY(scan_exclusive<uint32_t>(flag, off, n, P->ctr + C_TOTAL, scr, P->dev_err, st));
+  HLC_TRY(scan_exclusive<uint32_t>(len, off, cap + 1, P->ctr + C_TOTAL, scr, P->dev_err, st));
   unsigned long long nd = 0;
   HLC_CUDA(cudaMemcpyAsync(&nd, P->ctr + C_TOTAL, 8, cudaMemcpyDeviceToHost, st));
   HLC_CUDA(cudaStreamSynchronize(st));
   X.ndense = nd;
   if (nd == 0) {
-    ar.drop(flag);
-    ar.drop(off);
-    ar.drop(scr);
+    for (void* q : {(void*)rng, (void*)len, (void*)off, scr}) ar.drop(q);
     return HLC_OK;
   }
   uint32_t* dpos = ar.get_n<uint32_t>(nd);
@@ -567,8 +589,8 @@ static int dense_fixup(hlc_plan_t* P, CatDev& X, const uint32_t* T, int shift, b
   float4* tvec = ar.get_n<float4>(nd);
   void* sscr = ar.get(sort_scratch_bytes(nd, (bits + 7) / 8));
   if (!dpos || !dkey || !dval || !tk || !tv || !tvec || !sscr) return HLC_ENOMEM;
-  k_dense_compact<<<grid_for(n, kThreads), kThreads, 0, st>>>(X.key, n, flag, off, dpos, dkey,
-                                                              dval);
+  k_dense_fill<<<grid_for(32 * cap, kThreads, num_sms() * 16u), kThreads, 0, st>>>(
+      rng, off, P->ctr + C_DCELLS, X.key, dpos, dkey, dval);
   HLC_LAUNCH_CHECK();
   if (nd > 1)
     HLC_TRY(radix_sort_pairs<uint32_t>(dkey, dval, tk, tv, nd, bits, sscr, P->dev_err, st));
@@ -578,8 +600,8 @@ static int dense_fixup(hlc_plan_t* P, CatDev& X, const uint32_t* T, int shift, b
   k_dense_scatter<<<grid_for(nd, kThreads), kThreads, 0, st>>>(dpos, nd, dkey, tv, tvec, X.key,
                                                                X.idx, X.v32);
   HLC_LAUNCH_CHECK();
-  for (void* q : {(void*)flag, (void*)off, scr, (void*)dval, (void*)tk, (void*)tv, (void*)tvec,
-                  sscr})
+  for (void* q : {(void*)rng, (void*)len, (void*)off, scr, (void*)dval, (void*)tk, (void*)tv,
+                  (void*)tvec, sscr})
     ar.drop(q);
   if (!items) {
     ar.drop(dpos);
