@@ -152,6 +152,59 @@ static int check_dev_err(const int* dev_err, cudaStream_t st, const char* what) 
   return dev_err_status(h, what);
 }
 
+// Events and side streams of plans come from a per-device pool and go back
+// to it (creating and destroying about twenty per plan cost host time at the
+// points where the GPU waits for the next launch).  An object handed back
+// may still have work pending; reusing it only orders new work after that.
+namespace {
+std::mutex g_pool_mu;
+struct DevPool {
+  std::vector<cudaEvent_t> timed, plain;
+  std::vector<cudaStream_t> streams;
+};
+DevPool g_pool[64];
+DevPool& cur_pool() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) d = 0;
+  return g_pool[d];
+}
+}  // namespace
+
+static cudaError_t pool_event(cudaEvent_t* e, bool timed) {
+  {
+    std::lock_guard<std::mutex> g(g_pool_mu);
+    std::vector<cudaEvent_t>& v = timed ? cur_pool().timed : cur_pool().plain;
+    if (!v.empty()) {
+      *e = v.back();
+      v.pop_back();
+      return cudaSuccess;
+    }
+  }
+  return timed ? cudaEventCreate(e) : cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+}
+static void pool_event_back(cudaEvent_t e, bool timed) {
+  if (!e) return;
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  (timed ? cur_pool().timed : cur_pool().plain).push_back(e);
+}
+static cudaError_t pool_stream(cudaStream_t* s) {
+  {
+    std::lock_guard<std::mutex> g(g_pool_mu);
+    std::vector<cudaStream_t>& v = cur_pool().streams;
+    if (!v.empty()) {
+      *s = v.back();
+      v.pop_back();
+      return cudaSuccess;
+    }
+  }
+  return cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
+}
+static void pool_stream_back(cudaStream_t s) {
+  if (!s) return;
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  cur_pool().streams.push_back(s);
+}
+
 // Theta_L / 8 in arcsec: the largest radius for which the complete rule is exact.
 static double complete_max_radius(int order) {
   const double pi = 3.14159265358979323846;
@@ -798,9 +851,19 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
   HLC_CUDA(cudaEventRecord(eb[0], st));
   HLC_CUDA(cudaEventRecord(ea[0], st));
   HLC_CUDA(cudaStreamWaitEvent(ks, ea[0], 0));
-  // 1. the two preps, side by side
+  // 1. the two preps, side by side: each with half the blocks the GPU holds
+  // at once (one wave between them; each block flushes its digit counts once)
+  static const unsigned prep_grid = [] {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_prep_keys<true>, kThreads, 0) !=
+            cudaSuccess || b < 2) {
+      cudaGetLastError();
+      b = 2;
+    }
+    return (unsigned)(b / 2) * num_sms();
+  }();
   if (na) {
-    k_prep_keys<true><<<grid_for(na, kThreads, num_sms() * 8u), kThreads, 0, ks>>>(
+    k_prep_keys<true><<<grid_for(na, kThreads, prep_grid), kThreads, 0, ks>>>(
         inA->ra_deg, inA->dec_deg, inA->id, na, L, pix_const(L), XA.key,
         both ? nullptr : XA.idx, XA.rec, slow_a, P->ctr + C_SLOW_A, P->dev_err,
         P->eq4 ? inA->err_arcsec : nullptr, hist_a, shift, npass);
@@ -812,7 +875,7 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
   }
   HLC_CUDA(cudaEventRecord(ea[1], ks));
   if (nb) {
-    k_prep_keys<true><<<grid_for(nb, kThreads, num_sms() * 8u), kThreads, 0, st>>>(
+    k_prep_keys<true><<<grid_for(nb, kThreads, prep_grid), kThreads, 0, st>>>(
         inB->ra_deg, inB->dec_deg, inB->id, nb, L, pix_const(L), XB.key,
         both ? nullptr : XB.idx, XB.rec, slow_b, P->ctr + C_SLOW, P->dev_err,
         P->eq4 ? inB->err_arcsec : nullptr, hist_b, shift, npass);
@@ -1210,7 +1273,7 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
     if ((double)P->hi32 < P->C + G) P->hi32 = nextafterf(P->hi32, 1e30f);
     if (P->lo32 < 0) P->lo32 = -1.0f;
   }
-  for (int i = 0; i < 12; ++i) cudaEventCreate(&P->ev[i]);
+  for (int i = 0; i < 12; ++i) pool_event(&P->ev[i], true);
   P->events = true;
   auto fail = [&](int rc) {
     hlc_free(P);
@@ -1233,8 +1296,8 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   }
   cudaEvent_t ea[4], eb[4];
   for (int i = 0; i < 4; ++i) {
-    cudaEventCreate(&ea[i]);
-    cudaEventCreate(&eb[i]);
+    pool_event(&ea[i], true);
+    pool_event(&eb[i], true);
   }
   // (the FP32 complete form orders A by B's table cells: B first)
   const hlc_catalog* first = P->table_buckets ? B : A;
@@ -1248,9 +1311,9 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   cudaEvent_t cev[3] = {nullptr, nullptr, nullptr};
   int rc = HLC_OK;
   if (!first->on_device || !second->on_device) {
-    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) rc = HLC_ECUDA;
+    if (pool_stream(&cs) != cudaSuccess) rc = HLC_ECUDA;
     for (int i = 0; i < 3 && rc == HLC_OK; ++i)
-      if (cudaEventCreateWithFlags(&cev[i], cudaEventDisableTiming) != cudaSuccess) rc = HLC_ECUDA;
+      if (pool_event(&cev[i], false) != cudaSuccess) rc = HLC_ECUDA;
     for (int i = 0; i < 2 && rc == HLC_OK; ++i) {
       if (dv[i].on_device) continue;
       const uint64_t n = dv[i].n;
@@ -1293,10 +1356,10 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   cudaStream_t ks = nullptr;
   cudaEvent_t esorted = nullptr;  // both sorts done
   if (side && rc == HLC_OK) {
-    if (cudaStreamCreateWithFlags(&ks, cudaStreamNonBlocking) != cudaSuccess) {
+    if (pool_stream(&ks) != cudaSuccess) {
       ks = nullptr;
       rc = HLC_ECUDA;
-    } else if (cudaEventCreateWithFlags(&esorted, cudaEventDisableTiming) != cudaSuccess) {
+    } else if (pool_event(&esorted, false) != cudaSuccess) {
       rc = HLC_ECUDA;
     } else {
       rc = bucket_pair(P, &dv[0], &dv[1], ks, eb, ea, esorted);
@@ -1311,7 +1374,7 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
   cudaEvent_t ej = nullptr;  // (side form) the join: A's index stage starts here
   if (side) {
     if (rc == HLC_OK && (cudaStreamWaitEvent(st, ea[2], 0) != cudaSuccess ||
-                         cudaEventCreate(&ej) != cudaSuccess || cudaEventRecord(ej, st) != cudaSuccess))
+                         pool_event(&ej, true) != cudaSuccess || cudaEventRecord(ej, st) != cudaSuccess))
       rc = HLC_ECUDA;
     if (rc == HLC_OK) {
       if (P->A.n > 1 && P->B.ndense > 0)
@@ -1320,15 +1383,14 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
     }
     if (ks) {
       if (rc != HLC_OK) cudaStreamSynchronize(ks);  // nothing of A's still runs when freed
-      cudaStreamDestroy(ks);
+      pool_stream_back(ks);
     }
-    if (esorted) cudaEventDestroy(esorted);
+    pool_event_back(esorted, false);
   }
   if (cs) {
     cudaStreamSynchronize(cs);
-    cudaStreamDestroy(cs);
-    for (int i = 0; i < 3; ++i)
-      if (cev[i]) cudaEventDestroy(cev[i]);
+    pool_stream_back(cs);
+    for (int i = 0; i < 3; ++i) pool_event_back(cev[i], false);
     for (int i = 0; i < 2; ++i)
       for (int k = 0; k < 4; ++k)
         if (stage[i][k]) P->arena->drop(stage[i][k]);
@@ -1348,10 +1410,10 @@ static int plan_single(const hlc_catalog* A, const hlc_catalog* B, const hlc_par
     cudaEventElapsedTime(&t[5], eb[2], eb[3]);
   }
   for (int i = 0; i < 4; ++i) {
-    cudaEventDestroy(ea[i]);
-    cudaEventDestroy(eb[i]);
+    pool_event_back(ea[i], true);
+    pool_event_back(eb[i], true);
   }
-  if (ej) cudaEventDestroy(ej);
+  pool_event_back(ej, true);
   if (rc != HLC_OK) return fail(rc);
   ev_record(P, 1);
   unsigned long long diff = hc[C_IDDIFF];
@@ -1831,7 +1893,7 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
     P->tile_stage = p[0].tune->stage;
     P->target_per_cell = p[0].tune->target_per_cell;
   }
-  for (int i = 0; i < 12; ++i) cudaEventCreate(&P->ev[i]);
+  for (int i = 0; i < 12; ++i) pool_event(&P->ev[i], true);
   P->events = true;
   auto fail = [&](int rc) {
     hlc_free(P);
@@ -3377,8 +3439,7 @@ void hlc_free(hlc_plan_t* plan) {
   if (plan->pair_graph) cudaGraphExecDestroy(plan->pair_graph);
   delete plan->out;
   delete plan->arena;
-  for (int i = 0; i < 12; ++i)
-    if (plan->ev[i]) cudaEventDestroy(plan->ev[i]);
+  for (int i = 0; i < 12; ++i) pool_event_back(plan->ev[i], true);
   cudaStreamSynchronize(st);
   delete plan;
 }

@@ -99,14 +99,33 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
     for (int t = threadIdx.x; t < kPrepHistPasses * 256; t += blockDim.x) (&sh[0][0])[t] = 0u;
     __syncthreads();
   }
-  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n;
-       i0 += (uint64_t)gridDim.x * blockDim.x) {
+  // (a thread's next source's coordinates and id are loaded while the
+  // current one is processed)
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const bool want_id = rec || iddiff;
+  double pa = 0.0, pd = 0.0;
+  uint64_t pid = 0;
+  {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+      pa = ra[i];
+      pd = dec[i];
+      if (want_id) pid = id[i];
+    }
+  }
+  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
     uint64_t i = i0 + threadIdx.x;
     bool live = i < n;
     bool defer = false;
     uint32_t kfin = 0;  // the key written
+    double a = pa, d = pd;
+    const uint64_t idi = pid;
+    if (i + stride < n) {
+      pa = ra[i + stride];
+      pd = dec[i + stride];
+      if (want_id) pid = id[i + stride];
+    }
     if (live) {
-      double a = ra[i], d = dec[i];
       uint32_t k = 0;
       if (FAST) {
         if (!(bits_finite(a) && bits_abs_le(d, 90.0))) {
@@ -128,12 +147,12 @@ __global__ void k_prep_keys(const double* __restrict__ ra, const double* __restr
       key[i] = k;
       kfin = k;
       if (idx) idx[i] = (uint32_t)i;
-      if (iddiff) idacc |= id[i] ^ id0;
+      if (iddiff) idacc |= idi ^ id0;
       if (rec) {
         SrcRec r;
         r.ra = a;
         r.dec = d;
-        r.id = id[i];
+        r.id = idi;
         r.pad = perr ? (uint64_t)__double_as_longlong(perr[i]) : 0ull;  // Eq. 4 error radius
         rec[i] = r;
       }
