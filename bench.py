@@ -240,7 +240,7 @@ def run_hlc(args):
         ms, stats, nmatch = timed(prec, args.steps, args.warmup, clocks)
         clk = clocks.stop()
         clk["remeasured_after"] = why or "another rank's clock record"
-        # the second window is judged too: a throttled number is never
+        # the second window is checked too: a throttled number is never
         # reported unflagged
         clk["still_rejected"] = clocks_rejected(clk)
     other = hlc.HLC_FP64 if prec == hlc.HLC_FP32_GUARD else hlc.HLC_FP32_GUARD
