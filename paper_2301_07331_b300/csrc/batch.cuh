@@ -58,15 +58,32 @@ __global__ void k_bprep_keys(const JobDev* __restrict__ jobs, const uint64_t* __
                              uint64_t* __restrict__ key, uint32_t* __restrict__ idx,
                              SrcRec* __restrict__ rec, uint32_t* __restrict__ slow,
                              unsigned long long* __restrict__ nslow, int* __restrict__ err) {
-  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < total;
-       i0 += (uint64_t)gridDim.x * blockDim.x) {
+  // (a thread's next source -- its job, coordinates and id -- is looked up
+  // and loaded while the current one is processed)
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint32_t pj = 0;
+  double pa = 0.0, pd = 0.0;
+  uint64_t pid = 0;
+  auto fetch = [&](uint64_t ii) {
+    if (ii < total) {
+      pj = job_of(off, njobs, ii);
+      const JobDev& Jn = jobs[pj];
+      const uint64_t ln = ii - Jn.off[side];
+      pa = Jn.ra[side][ln];
+      pd = Jn.dec[side][ln];
+      pid = Jn.id[side][ln];
+    }
+  };
+  fetch((uint64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < total; i0 += stride) {
     uint64_t i = i0 + threadIdx.x;
     bool defer = false;
+    const uint32_t j = pj;
+    double a = pa, d = pd;
+    const uint64_t idv = pid;
+    fetch(i + stride);
     if (i < total) {
-      uint32_t j = job_of(off, njobs, i);
       const JobDev& J = jobs[j];
-      uint64_t l = i - J.off[side];
-      double a = J.ra[side][l], d = J.dec[side][l];
       uint32_t k = 0;
       if (!(bits_finite(a) && bits_abs_le(d, 90.0))) {
         atomicOr(err, DERR_INPUT);
@@ -84,7 +101,7 @@ __global__ void k_bprep_keys(const JobDev* __restrict__ jobs, const uint64_t* __
       SrcRec r;  // (the payload gathers one 32-byte record, not three arrays)
       r.ra = a;
       r.dec = d;
-      r.id = J.id[side][l];
+      r.id = idv;
       r.pad = 0;
       rec[i] = r;
     }
