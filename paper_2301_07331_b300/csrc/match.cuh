@@ -234,12 +234,26 @@ __global__ void k_quad_cells(const double* __restrict__ ra, const double* __rest
   const f2 Rd = split_f64(R);
   const uint64_t id0 = (iddiff && id && n) ? id[0] : 0ull;
   unsigned long long idacc = 0;
-  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n;
-       i0 += (uint64_t)gridDim.x * blockDim.x) {
+  // (a thread's next source's coordinates are loaded while the current one
+  // is processed)
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  double pa = 0.0, pd = 0.0;
+  {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+      pa = ra[i];
+      pd = dec[i];
+    }
+  }
+  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
     uint64_t i = i0 + threadIdx.x;
     bool defer = false;
+    double a = pa, d = pd;
+    if (i + stride < n) {
+      pa = ra[i + stride];
+      pd = dec[i + stride];
+    }
     if (i < n) {
-      double a = ra[i], d = dec[i];
       uint32_t c[5] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
       int m = 1;
       const bool valid = FAST ? (bits_finite(a) && bits_abs_le(d, 90.0)) : c_valid(a, d);
