@@ -704,6 +704,21 @@ static int dense_fixup(hlc_plan_t* P, CatDev& X, const uint32_t* T, int shift, b
   return HLC_OK;
 }
 
+// Blocks of the guarded prep the GPU holds at once (a grid of at most this
+// many runs in one wave, each block flushing its digit counts once).
+static unsigned prep_resident_blocks() {
+  static const unsigned blocks = [] {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_prep_keys<true>, kThreads, 0) !=
+            cudaSuccess || b < 1) {
+      cudaGetLastError();
+      b = 1;
+    }
+    return (unsigned)b * num_sms();
+  }();
+  return blocks;
+}
+
 // FP32 complete-mode build: entries sorted by table cell only (the radix sort
 // runs over the key bits above the fine bits of a table cell, one pass fewer
 // at the usual orders) and the FP32 payload gathered in that order.  B gets
@@ -853,15 +868,7 @@ static int bucket_pair(hlc_plan_t* P, const hlc_catalog* inB, const hlc_catalog*
   HLC_CUDA(cudaStreamWaitEvent(ks, ea[0], 0));
   // 1. the two preps, side by side: each with half the blocks the GPU holds
   // at once (one wave between them; each block flushes its digit counts once)
-  static const unsigned prep_grid = [] {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_prep_keys<true>, kThreads, 0) !=
-            cudaSuccess || b < 2) {
-      cudaGetLastError();
-      b = 2;
-    }
-    return (unsigned)(b / 2) * num_sms();
-  }();
+  const unsigned prep_grid = std::max(1u, prep_resident_blocks() / 2);
   if (na) {
     k_prep_keys<true><<<grid_for(na, kThreads, prep_grid), kThreads, 0, ks>>>(
         inA->ra_deg, inA->dec_deg, inA->id, na, L, pix_const(L), XA.key,
@@ -1009,6 +1016,11 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     cudaEventRecord(ev[3], st);
     return HLC_OK;
   }
+  // the sort's scratch, whose digit histograms the FP32 key writers count
+  // (the guarded preps, the quad-entry emit) as they write the keys
+  const int sort_bits = 2 * L + 4;
+  const int sort_np = (sort_bits + 7) / 8;
+  void* sscr = nullptr;
   if (!quad) {
     X.m = n;
     HLC_ALLOC(ar, X.key, uint32_t, n + 1);
@@ -1017,13 +1029,19 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
       if (fp32) {
         uint32_t* slow = ar.get_n<uint32_t>(n + 1);
         if (!slow) return HLC_ENOMEM;
+        if (n > 1) {
+          sscr = ar.get(sort_scratch_bytes(n, sort_np));
+          if (!sscr) return HLC_ENOMEM;
+          HLC_CUDA(cudaMemsetAsync(sscr, 0, (size_t)sort_np * 256 * 4, st));
+        }
         HLC_CUDA(cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st));
-        k_prep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+        k_prep_keys<true><<<grid_for(n, kThreads, prep_resident_blocks()), kThreads, 0, st>>>(
             ra, dec, id, n, L, pix_const(L), X.key, X.idx, X.rec, slow, P->ctr + C_SLOW,
-            P->dev_err, nullptr, nullptr, 0, 0, iddiff);
+            P->dev_err, nullptr, (uint32_t*)sscr, 0, sscr ? sort_np : 0, iddiff);
         HLC_LAUNCH_CHECK();
         k_prep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(ra, dec, L, slow, P->ctr + C_SLOW,
-                                                              X.key, X.rec);
+                                                              X.key, X.rec, (uint32_t*)sscr, 0,
+                                                              sscr ? sort_np : 0);
         HLC_LAUNCH_CHECK();
         ar.drop(slow);
       } else {
@@ -1075,13 +1093,21 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
     X.m = m;
     HLC_ALLOC(ar, X.key, uint32_t, X.m + 1);
     HLC_ALLOC(ar, X.idx, uint32_t, X.m + 1);
+    if (m > 1) {
+      sscr = ar.get(sort_scratch_bytes(m, sort_np));
+      if (!sscr) return HLC_ENOMEM;
+      HLC_CUDA(cudaMemsetAsync(sscr, 0, (size_t)sort_np * 256 * 4, st));
+    }
     if (n) {
+      const unsigned eg = grid_for(n, kThreads, sscr ? num_sms() * 8u : 0u);
       if (off32)
-        k_quad_emit<uint32_t><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            X.cells5, cnt, (const uint32_t*)off, n, X.key, X.idx);
+        k_quad_emit<uint32_t><<<eg, kThreads, 0, st>>>(X.cells5, cnt, (const uint32_t*)off, n,
+                                                        X.key, X.idx, (uint32_t*)sscr,
+                                                        sscr ? sort_np : 0);
       else
-        k_quad_emit<uint64_t><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            X.cells5, cnt, (const uint64_t*)off, n, X.key, X.idx);
+        k_quad_emit<uint64_t><<<eg, kThreads, 0, st>>>(X.cells5, cnt, (const uint64_t*)off, n,
+                                                        X.key, X.idx, (uint32_t*)sscr,
+                                                        sscr ? sort_np : 0);
       HLC_LAUNCH_CHECK();
     }
     ar.drop(cnt);
@@ -1093,10 +1119,11 @@ static int build_catalog(hlc_plan_t* P, const hlc_catalog* in, CatDev& X, bool i
   if (m > 1) {
     uint32_t* tk = ar.get_n<uint32_t>(m);
     uint32_t* tv = ar.get_n<uint32_t>(m);
-    int bits = 2 * L + 4;
-    void* scr = ar.get(sort_scratch_bytes(m, (bits + 7) / 8));
+    const bool counted = sscr != nullptr;
+    void* scr = counted ? sscr : ar.get(sort_scratch_bytes(m, sort_np));
     if (!tk || !tv || !scr) return HLC_ENOMEM;
-    HLC_TRY(radix_sort_pairs<uint32_t>(X.key, X.idx, tk, tv, m, bits, scr, P->dev_err, st));
+    HLC_TRY(radix_sort_pairs<uint32_t>(X.key, X.idx, tk, tv, m, sort_bits, scr, P->dev_err, st,
+                                       0, nullptr, nullptr, nullptr, counted));
     ar.drop(tk);
     ar.drop(tv);
     ar.drop(scr);

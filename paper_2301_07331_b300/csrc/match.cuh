@@ -375,16 +375,34 @@ __global__ void __launch_bounds__(kThreads) k_quad_fallback(
 
 // One (cell, source) entry per distinct quad cell, at the scanned offsets.
 template <typename OffT>
+// (hist: the radix sort's digit histograms of the keys written, hist_np
+// passes of 8 bits from bit 0, counted in shared memory and added once per
+// block)
 __global__ void k_quad_emit(const uint32_t* __restrict__ cells, const uint32_t* __restrict__ count,
                             const OffT* __restrict__ off, uint64_t n,
-                            uint32_t* __restrict__ key, uint32_t* __restrict__ idx) {
+                            uint32_t* __restrict__ key, uint32_t* __restrict__ idx,
+                            uint32_t* __restrict__ hist = nullptr, int hist_np = 0) {
+  __shared__ uint32_t sh[kPrepHistPasses][256];
+  if (hist) {
+    for (int t = threadIdx.x; t < kPrepHistPasses * 256; t += blockDim.x) (&sh[0][0])[t] = 0u;
+    __syncthreads();
+  }
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t o = off[i];
     uint32_t m = count[i];
     for (uint32_t e = 0; e < m; ++e) {
-      key[o + e] = cells[5 * i + e];
+      const uint32_t k = cells[5 * i + e];
+      key[o + e] = k;
       idx[o + e] = (uint32_t)i;
+      for (int p = 0; hist && p < hist_np; ++p) atomicAdd(&sh[p][(k >> (8 * p)) & 255u], 1u);
+    }
+  }
+  if (hist) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < hist_np * 256; t += blockDim.x) {
+      const uint32_t c = (&sh[0][0])[t];
+      if (c) atomicAdd(hist + t, c);
     }
   }
 }

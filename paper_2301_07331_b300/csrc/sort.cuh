@@ -303,11 +303,14 @@ inline size_t sort_scratch_bytes(uint64_t n, int npass) {
 // of passes leaves the result in (tmp_keys, tmp_vals) and *in_tmp says so;
 // otherwise it is copied back.
 // pass_ev, when given, receives events recorded around the digit passes.
+// hist_ready: the scratch's digit histograms (npass x 256 counts at its
+// start) were counted by the producer of the keys; the histogram pass is
+// skipped.
 template <typename K>
 int radix_sort_pairs(K* keys, uint32_t* vals, K* tmp_keys, uint32_t* tmp_vals, uint64_t n,
                      int key_bits, void* scratch, int* dev_err, cudaStream_t st,
                      int bit_lo = 0, bool* in_tmp = nullptr, cudaEvent_t* pass_ev = nullptr,
-                     int* npass_out = nullptr) {
+                     int* npass_out = nullptr, bool hist_ready = false) {
   if (in_tmp) *in_tmp = false;
   if (n <= 1) return HLC_OK;
   if (bit_lo < 0 || bit_lo >= key_bits) bit_lo = 0;
@@ -325,12 +328,14 @@ int radix_sort_pairs(K* keys, uint32_t* vals, K* tmp_keys, uint32_t* tmp_vals, u
   uint32_t* ctr = (uint32_t*)(sp + 16384);
   unsigned long long* lb = (unsigned long long*)(sp + kSortLookbackOffset);
   size_t lb_bytes = (size_t)npass * tiles * rs::kRadix * 8;
-  HLC_CUDA(cudaMemsetAsync(hist, 0, (size_t)npass * rs::kRadix * 4, st));
   HLC_CUDA(cudaMemsetAsync(ctr, 0, 64, st));
   HLC_CUDA(cudaMemsetAsync(lb, 0, lb_bytes, st));
-  rs::k_digit_hist<K><<<grid_for(n, rs::kBlock, num_sms() * 8u), rs::kBlock, 0, st>>>(keys, n, npass,
-                                                                               bit_lo, hist);
-  HLC_LAUNCH_CHECK();
+  if (!hist_ready) {
+    HLC_CUDA(cudaMemsetAsync(hist, 0, (size_t)npass * rs::kRadix * 4, st));
+    rs::k_digit_hist<K><<<grid_for(n, rs::kBlock, num_sms() * 8u), rs::kBlock, 0, st>>>(
+        keys, n, npass, bit_lo, hist);
+    HLC_LAUNCH_CHECK();
+  }
   rs::k_hist_scan<<<npass, rs::kBlock, 0, st>>>(hist, offs);
   HLC_LAUNCH_CHECK();
   size_t smem = sizeof(rs::SweepSmem<K>);
