@@ -2191,27 +2191,22 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
                                                                       P->ctr + C_IDDIFF);
     ++g_launches;
   }
-  // dense cells of every job for the tile kernel: runs of equal (job, cell)
-  // keys among the sorted A entries (FP32 form)
+  // dense cells of every job for the tile kernel: runs of at least
+  // kTileMinA equal (job, cell) keys among the sorted A entries (FP32 form),
+  // listed as (start, end) by one pass over the keys
   if (rc == HLC_OK && NA > 1 && NB && P->p.precision == HLC_FP32_GUARD) {
-    uint32_t* flag = ar.get_n<uint32_t>(NA + 1);
-    uint32_t* off = ar.get_n<uint32_t>(NA + 1);
-    void* scr = ar.get(scan_scratch_bytes(NA));
-    P->A.tile_start = ar.get_n<uint32_t>(NA + 2);
+    const uint64_t rcap = NA / kTileMinA + 1;  // (the runs are disjoint)
+    P->A.tile_start = ar.get_n<uint32_t>(rcap);
+    uint32_t* tile_end = ar.get_n<uint32_t>(rcap);
     P->A.tile_n = ar.get_n<unsigned long long>(4);
     P->A.tiled = ar.get_n<uint8_t>(NA + 1);
-    if (!flag || !off || !scr || !P->A.tile_start || !P->A.tile_n || !P->A.tiled)
-      return fail(HLC_ENOMEM);
+    if (!P->A.tile_start || !tile_end || !P->A.tile_n || !P->A.tiled) return fail(HLC_ENOMEM);
     cudaMemsetAsync(P->A.tile_n, 0, 32, st);
     cudaMemsetAsync(P->A.tiled, 0, NA + 1, st);
-    k_run_flags64<<<grid_for(NA, kThreads), kThreads, 0, st>>>(keys[0], NA, flag);
-    ++g_launches;
-    rc = scan_exclusive<uint32_t>(flag, off, NA, P->A.tile_n, scr, P->dev_err, st);
-    if (rc) return fail(rc);
-    k_run_starts<<<grid_for(NA, kThreads), kThreads, 0, st>>>(flag, off, NA, P->A.tile_n,
-                                                               P->A.tile_start);
-    k_mark_tiled<<<grid_for(NA, kThreads, num_sms() * 8u), kThreads, 0, st>>>(
-        P->A.tile_start, nullptr, P->A.tile_n, P->A.tiled);
+    k_long_runs<<<grid_for(NA, kThreads), kThreads, 0, st>>>(keys[0], NA, P->A.tile_start,
+                                                              tile_end, P->A.tile_n, rcap);
+    k_mark_runs<<<num_sms() * 16u, kThreads, 0, st>>>(P->A.tile_start, tile_end, P->A.tile_n,
+                                                     P->A.tiled);
     g_launches += 2;
     const uint64_t cap = NA / kTileItemDiv + 1;
     P->A.tile_icap = cap;
@@ -2221,6 +2216,7 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
     cudaMemsetAsync(P->A.tile_nprep, 0, 16, st);
     TileArgs tp{};
     tp.start = P->A.tile_start;
+    tp.end = tile_end;
     tp.nitems = P->A.tile_n;
     tp.keyA64 = keys[0];
     tp.keyB64 = keys[1];
@@ -2229,9 +2225,6 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
     tp.cell_bits = P->cell_bits;
     k_tile_items<true><<<num_sms() * 16u, 256, 0, st>>>(tp, P->A.tile_items, P->A.tile_nprep, cap);
     ++g_launches;
-    ar.drop(flag);
-    ar.drop(off);
-    ar.drop(scr);
   }
   unsigned long long hc[C_N] = {0};
   if (rc == HLC_OK &&

@@ -91,6 +91,7 @@ struct TileArgs {
   float rho_max;             // Eq. 4: bound on rho_a + rho_b (0 for the single radius)
   const uint32_t* cell;      // (single) item cells (fine ids)
   const uint32_t* start;     // item starts (single: in the dense-subset order), u + 1
+  const uint32_t* end = nullptr;  // (batched) each run's end, the runs listed in any order
   const uint32_t* dpos;      // (single) dense-subset index -> A entry
   const unsigned long long* nitems;  // k_tile_items: cells; k_pair_tile: items (front, back)
   uint64_t icap;             // k_pair_tile: capacity of items (the back ones count down from it)
@@ -133,6 +134,73 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
   return false;
 }
 
+// Runs of at least kTileMinA equal keys among sorted composite keys (the
+// batched form's dense cells): a thread per entry finds the run heads (the
+// key differs from the previous one and equals the one kTileMinA - 1 further
+// on) and the run's end by an exponential, then a binary search.  The runs
+// are listed as (start, end) in no particular order; nruns[1] and nruns[2]
+// receive their number and their entries, as k_mark_tiled counts them.
+__global__ void k_long_runs(const uint64_t* __restrict__ key, uint64_t n,
+                            uint32_t* __restrict__ rs, uint32_t* __restrict__ re,
+                            unsigned long long* __restrict__ nruns, uint64_t cap) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  unsigned long long nent = 0;
+  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n;
+       i0 += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = i0 + threadIdx.x;
+    bool head = false;
+    uint64_t e = 0;
+    if (i < n) {
+      const uint64_t k = key[i];
+      if ((i == 0 || key[i - 1] != k) && i + kTileMinA - 1 < n && key[i + kTileMinA - 1] == k) {
+        head = true;
+        uint64_t lo = i + kTileMinA - 1, step = kTileMinA;  // key[lo] == k
+        while (lo + step < n && key[lo + step] == k) {
+          lo += step;
+          step <<= 1;
+        }
+        uint64_t a = lo + 1, b = lo + step < n ? lo + step : n;  // first != k in [a, b]
+        while (a < b) {
+          const uint64_t mid = (a + b) >> 1;
+          if (key[mid] == k) a = mid + 1; else b = mid;
+        }
+        e = a;
+        nent += e - i;
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, head);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(nruns, (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (head) {
+        const uint64_t p = base + __popc(m & lt);
+        if (p < cap) {
+          rs[p] = (uint32_t)i;
+          re[p] = (uint32_t)e;
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) nent += __shfl_down_sync(0xffffffffu, nent, o);
+  if (lane == 0 && nent) atomicAdd(nruns + 2, nent);
+}
+
+// The A entries of listed runs marked for the tile kernel, a warp per run
+// (coalesced byte stores).
+__global__ void k_mark_runs(const uint32_t* __restrict__ rs, const uint32_t* __restrict__ re,
+                            unsigned long long* __restrict__ nruns, uint8_t* __restrict__ tiled) {
+  const uint64_t nr = nruns[0];
+  const int lane = threadIdx.x & 31;
+  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  if (w0 == 0 && lane == 0) nruns[1] = nr;
+  for (uint64_t r = w0; r < nr; r += nw)
+    for (uint32_t j = rs[r] + lane; j < re[r]; j += 32) tiled[j] = 1;
+}
+
 // Marks the A entries of the items the tile kernel takes; nitems[0] = runs,
 // nitems[1] += items taken, nitems[2] += their A entries.  dpos null: the
 // starts are A entries already.
@@ -155,24 +223,6 @@ __global__ void k_mark_tiled(const uint32_t* __restrict__ start, const uint32_t*
   }
 }
 
-// Run starts of sorted 64-bit keys: flag[i] = 1 where a run begins ...
-__global__ void k_run_flags64(const uint64_t* __restrict__ key, uint64_t n,
-                              uint32_t* __restrict__ flag) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x)
-    flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1u : 0u;
-}
-
-// ... and start[r] = first entry of run r, start[runs] = n (off = exclusive
-// scan of flag, *runs its total).
-__global__ void k_run_starts(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ off,
-                             uint64_t n, const unsigned long long* __restrict__ runs,
-                             uint32_t* __restrict__ start) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x)
-    if (flag[i]) start[off[i]] = (uint32_t)i;
-  if (blockIdx.x == 0 && threadIdx.x == 0) start[*runs] = (uint32_t)n;
-}
 
 // Upper edge of the local-form filter for one item.  hi is the guard band's
 // upper edge of the global-frame test (C + G for a single radius, G under
@@ -456,7 +506,7 @@ __global__ void k_tile_items(const TileArgs ta, TileItem* __restrict__ out,
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   for (uint64_t item = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
        item < nitems; item += warps) {
-    const uint32_t st0 = ta.start[item], st1 = ta.start[item + 1];
+    const uint32_t st0 = ta.start[item], st1 = ta.end ? ta.end[item] : ta.start[item + 1];
     const uint32_t na = st1 - st0;
     if (na < kTileMinA) continue;
     const uint32_t a0 = BATCH ? st0 : ta.dpos[st0];
