@@ -138,13 +138,19 @@ __global__ void k_bprep_fallback(const JobDev* __restrict__ jobs, const uint64_t
 // Sorted payload from the records the prep wrote in input order (RA
 // normalised): one 32-byte gather per entry.
 template <bool FP32>
+// (iddiff, when given: the OR of id ^ (an id of the catalogue) over its
+// entries, the bits in which its ids differ, for the output bucketing)
 __global__ void k_bpayload(const SrcRec* __restrict__ rec, const uint32_t* __restrict__ idx,
                            uint64_t m, float4* __restrict__ v32, double2* __restrict__ rd,
                            double* __restrict__ vx, double* __restrict__ vy,
-                           double* __restrict__ vz, uint64_t* __restrict__ id_s) {
+                           double* __restrict__ vz, uint64_t* __restrict__ id_s,
+                           unsigned long long* __restrict__ iddiff = nullptr) {
+  const uint64_t id0 = (iddiff && m) ? rec[idx[0]].id : 0ull;
+  unsigned long long idacc = 0;
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
        e += (uint64_t)gridDim.x * blockDim.x) {
     const SrcRec r = rec[idx[e]];
+    idacc |= r.id ^ id0;
     if (FP32) {
       v32[e] = fp32_unitvec(r.ra, r.dec);
       rd[e] = make_double2(r.ra, r.dec);
@@ -157,6 +163,7 @@ __global__ void k_bpayload(const SrcRec* __restrict__ rec, const uint32_t* __res
     }
     id_s[e] = r.id;
   }
+  id_span_flush(iddiff, idacc);
 }
 
 // Autotuner inputs, per job: the sum of the B unit vectors (FP32) and, in a

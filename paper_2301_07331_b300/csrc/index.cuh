@@ -227,17 +227,4 @@ inline int coarse_table_order(uint64_t m, int L) {
   return lt;
 }
 
-// Highest bit in which the ids differ (OR of id ^ id[0]).
-__global__ void k_id_diff(const uint64_t* __restrict__ id, uint64_t n,
-                          unsigned long long* __restrict__ out) {
-  unsigned long long acc = 0;
-  if (n == 0) return;
-  uint64_t first = id[0];
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x)
-    acc |= id[i] ^ first;
-  for (int o = 16; o > 0; o >>= 1) acc |= __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0 && acc) atomicOr(out, acc);
-}
-
 }  // namespace hlc

@@ -2128,7 +2128,8 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
       if (!X.v32 || !X.rd) return fail(HLC_ENOMEM);
       if (n)
         k_bpayload<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            X.rec, X.idx, n, X.v32, X.rd, nullptr, nullptr, nullptr, X.id_s);
+            X.rec, X.idx, n, X.v32, X.rd, nullptr, nullptr, nullptr, X.id_s,
+            s == 0 ? P->ctr + C_IDDIFF : nullptr);
     } else {
       X.vx = ar.get_n<double>(n + 1);
       X.vy = ar.get_n<double>(n + 1);
@@ -2136,7 +2137,8 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
       if (!X.vx || !X.vy || !X.vz) return fail(HLC_ENOMEM);
       if (n)
         k_bpayload<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            X.rec, X.idx, n, nullptr, nullptr, X.vx, X.vy, X.vz, X.id_s);
+            X.rec, X.idx, n, nullptr, nullptr, X.vx, X.vy, X.vz, X.id_s,
+            s == 0 ? P->ctr + C_IDDIFF : nullptr);
     }
     if (n) ++g_launches;
     ar.drop(X.rec);  // (the later stages read the sorted payload only)
@@ -2185,11 +2187,6 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
     if (rc) return fail(rc);
     ar.drop(counts);
     ar.drop(scr);
-  }
-  if (rc == HLC_OK && NA) {
-    k_id_diff<<<grid_for(NA, kThreads, num_sms() * 8u), kThreads, 0, st>>>(P->A.id_s, NA,
-                                                                      P->ctr + C_IDDIFF);
-    ++g_launches;
   }
   // dense cells of every job for the tile kernel: runs of at least
   // kTileMinA equal (job, cell) keys among the sorted A entries (FP32 form),
