@@ -112,24 +112,27 @@ __global__ void k_dense_cell_ranges(const uint32_t* __restrict__ cells,
   }
 }
 
-// The dense entries in table-cell order (a warp per cell): positions, keys,
-// identity values (the positions in the list).
+// The dense entries in table-cell order, a thread per entry (a cell may hold
+// most of a catalogue, so the work is split by entry, not by cell): entry p
+// finds its cell as the last offset <= p, then writes its position, key and
+// identity value (p itself).
 __global__ void k_dense_fill(const uint2* __restrict__ rng, const uint32_t* __restrict__ off,
-                             const unsigned long long* __restrict__ ncells,
+                             const unsigned long long* __restrict__ ncells, uint64_t nd,
                              const uint32_t* __restrict__ key, uint32_t* __restrict__ dpos,
                              uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval) {
   const uint64_t nc = *ncells;
-  const int lane = threadIdx.x & 31;
-  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t i = w0; i < nc; i += nw) {
-    const uint2 r = rng[i];
-    const uint32_t o = off[i];
-    for (uint32_t j = lane; j < r.y - r.x; j += 32) {
-      dpos[o + j] = r.x + j;
-      dkey[o + j] = key[r.x + j];
-      dval[o + j] = o + j;
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nd;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t lo = 0, hi = nc;  // first cell whose offset exceeds p
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if (__ldg(off + mid) <= p) lo = mid + 1; else hi = mid;
     }
+    const uint64_t i = lo - 1;  // off[0] = 0 <= p, so lo >= 1
+    const uint32_t pos = rng[i].x + (uint32_t)(p - __ldg(off + i));
+    dpos[p] = pos;
+    dkey[p] = key[pos];
+    dval[p] = (uint32_t)p;
   }
 }
 

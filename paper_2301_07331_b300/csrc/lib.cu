@@ -642,8 +642,8 @@ static int dense_fixup(hlc_plan_t* P, CatDev& X, const uint32_t* T, int shift, b
   float4* tvec = ar.get_n<float4>(nd);
   void* sscr = ar.get(sort_scratch_bytes(nd, (bits + 7) / 8));
   if (!dpos || !dkey || !dval || !tk || !tv || !tvec || !sscr) return HLC_ENOMEM;
-  k_dense_fill<<<grid_for(32 * cap, kThreads, num_sms() * 16u), kThreads, 0, st>>>(
-      rng, off, P->ctr + C_DCELLS, X.key, dpos, dkey, dval);
+  k_dense_fill<<<grid_for(nd, kThreads), kThreads, 0, st>>>(rng, off, P->ctr + C_DCELLS, nd,
+                                                             X.key, dpos, dkey, dval);
   HLC_LAUNCH_CHECK();
   if (nd > 1)
     HLC_TRY(radix_sort_pairs<uint32_t>(dkey, dval, tk, tv, nd, bits, sscr, P->dev_err, st));
