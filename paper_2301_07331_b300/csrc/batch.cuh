@@ -52,12 +52,51 @@ __device__ __forceinline__ uint32_t job_of(const uint64_t* __restrict__ off, uin
   return lo;
 }
 
+// The composite keys' digit histograms (hist_np passes of 8 bits from bit 0,
+// in shared memory, flushed once per block) for the radix sort, which then
+// makes no pass of its own over the keys.  The upper digits hold the job,
+// the same for most lanes of a warp: a digit common to every counted lane is
+// added once by the first of them.
+constexpr int kBHistPasses = 8;
+__device__ __forceinline__ void bhist_count(uint32_t (*sh)[256], int np, bool counted,
+                                            uint64_t k) {
+  const unsigned m = __ballot_sync(0xffffffffu, counted);
+  if (!m) return;
+  const int first = __ffs(m) - 1;
+  for (int p = 0; p < np; ++p) {
+    const uint32_t dig = (uint32_t)(k >> (8 * p)) & 255u;
+    const uint32_t d0 = __shfl_sync(0xffffffffu, dig, first);
+    if (__ballot_sync(0xffffffffu, counted && dig == d0) == m) {
+      if ((int)(threadIdx.x & 31) == first) atomicAdd(&sh[p][d0], (uint32_t)__popc(m));
+    } else if (counted) {
+      atomicAdd(&sh[p][dig], 1u);
+    }
+  }
+}
+
+__device__ __forceinline__ void bhist_flush(uint32_t (*sh)[256], int np,
+                                            uint32_t* __restrict__ hist) {
+  __syncthreads();
+  for (int t = threadIdx.x; t < np * 256; t += blockDim.x) {
+    const uint32_t c = (&sh[0][0])[t];
+    if (c) atomicAdd(hist + t, c);
+  }
+}
+
+// (hist, when given: the digit histograms of the keys written for good; the
+// queued ones are counted by k_bprep_fallback)
 template <bool FAST>
 __global__ void k_bprep_keys(const JobDev* __restrict__ jobs, const uint64_t* __restrict__ off,
                              uint32_t njobs, int side, uint64_t total, int cell_bits,
                              uint64_t* __restrict__ key, uint32_t* __restrict__ idx,
                              SrcRec* __restrict__ rec, uint32_t* __restrict__ slow,
-                             unsigned long long* __restrict__ nslow, int* __restrict__ err) {
+                             unsigned long long* __restrict__ nslow, int* __restrict__ err,
+                             uint32_t* __restrict__ hist = nullptr, int hist_np = 0) {
+  __shared__ uint32_t sh[kBHistPasses][256];
+  if (hist) {
+    for (int t = threadIdx.x; t < kBHistPasses * 256; t += blockDim.x) (&sh[0][0])[t] = 0u;
+    __syncthreads();
+  }
   // (a thread's next source -- its job, coordinates and id -- is looked up
   // and loaded while the current one is processed)
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -81,6 +120,7 @@ __global__ void k_bprep_keys(const JobDev* __restrict__ jobs, const uint64_t* __
     const uint32_t j = pj;
     double a = pa, d = pd;
     const uint64_t idv = pid;
+    uint64_t kw = 0;  // the key written
     fetch(i + stride);
     if (i < total) {
       const JobDev& J = jobs[j];
@@ -96,7 +136,8 @@ __global__ void k_bprep_keys(const JobDev* __restrict__ jobs, const uint64_t* __
           k = c_ang2pix(a, d, J.L);
         }
       }
-      key[i] = ((uint64_t)j << cell_bits) | k;
+      kw = ((uint64_t)j << cell_bits) | k;
+      key[i] = kw;
       idx[i] = (uint32_t)i;
       SrcRec r;  // (the payload gathers one 32-byte record, not three arrays)
       r.ra = a;
@@ -115,24 +156,41 @@ __global__ void k_bprep_keys(const JobDev* __restrict__ jobs, const uint64_t* __
         if (defer) slow[base + __popc(b & lanemask_lt())] = (uint32_t)i;
       }
     }
+    // (an invalid source keeps cell 0 and counts as such)
+    if (hist) bhist_count(sh, hist_np, i < total && !defer, kw);
   }
+  if (hist) bhist_flush(sh, hist_np, hist);
 }
 
 __global__ void k_bprep_fallback(const JobDev* __restrict__ jobs, const uint64_t* __restrict__ off,
                                  uint32_t njobs, int side, int cell_bits,
                                  const uint32_t* __restrict__ slow,
                                  const unsigned long long* __restrict__ nslow,
-                                 uint64_t* __restrict__ key) {
-  uint64_t ns = *nslow;
-  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns;
-       q += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t i = slow[q];
-    uint32_t j = job_of(off, njobs, i);
-    const JobDev& J = jobs[j];
-    uint64_t l = i - J.off[side];
-    key[i] = ((uint64_t)j << cell_bits) |
-             ff_or_c_ang2pix(c_norm_ra(J.ra[side][l]), J.dec[side][l], J.L);
+                                 uint64_t* __restrict__ key, uint32_t* __restrict__ hist = nullptr,
+                                 int hist_np = 0) {
+  __shared__ uint32_t sh[kBHistPasses][256];
+  if (hist) {
+    for (int t = threadIdx.x; t < kBHistPasses * 256; t += blockDim.x) (&sh[0][0])[t] = 0u;
+    __syncthreads();
   }
+  const uint64_t ns = *nslow;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  // (every lane runs the same number of rounds, for the warp-wide counting)
+  for (uint64_t q0 = (uint64_t)blockIdx.x * blockDim.x; q0 < ns; q0 += stride) {
+    const uint64_t q = q0 + threadIdx.x;
+    uint64_t kw = 0;
+    if (q < ns) {
+      uint32_t i = slow[q];
+      uint32_t j = job_of(off, njobs, i);
+      const JobDev& J = jobs[j];
+      uint64_t l = i - J.off[side];
+      kw = ((uint64_t)j << cell_bits) |
+           ff_or_c_ang2pix(c_norm_ra(J.ra[side][l]), J.dec[side][l], J.L);
+      key[i] = kw;
+    }
+    if (hist) bhist_count(sh, hist_np, q < ns, kw);
+  }
+  if (hist) bhist_flush(sh, hist_np, hist);
 }
 
 // Sorted payload from the records the prep wrote in input order (RA

@@ -704,6 +704,25 @@ static int dense_fixup(hlc_plan_t* P, CatDev& X, const uint32_t* T, int shift, b
   return HLC_OK;
 }
 
+// Blocks of the batched prep the GPU holds at once (its grid, so that each
+// block flushes its digit counts once).
+static unsigned bprep_resident_blocks(bool fast) {
+  static unsigned blocks[2] = {0, 0};
+  unsigned& r = blocks[fast ? 1 : 0];
+  if (!r) {
+    int b = 0;
+    const cudaError_t e =
+        fast ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bprep_keys<true>, kThreads, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bprep_keys<false>, kThreads, 0);
+    if (e != cudaSuccess || b < 1) {
+      cudaGetLastError();
+      b = 1;
+    }
+    r = (unsigned)b * num_sms();
+  }
+  return r;
+}
+
 // Blocks of the guarded prep the GPU holds at once (a grid of at most this
 // many runs in one wave, each block flushing its digit counts once).
 static unsigned prep_resident_blocks() {
@@ -2090,19 +2109,25 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
     X.rec = ar.get_n<SrcRec>(n + 1);
     uint32_t* slow = ar.get_n<uint32_t>(n + 1);
     if (!keys[s] || !X.idx || !X.rec || !slow) return fail(HLC_ENOMEM);
+    // the sort's scratch first: the preps count its digit histograms
+    const int np = std::min((key_bits + 7) / 8, 8);
+    void* scr = n > 1 ? ar.get(sort_scratch_bytes(n, np)) : nullptr;
+    if (n > 1 && !scr) return fail(HLC_ENOMEM);
+    uint32_t* hist = (uint32_t*)scr;
+    if (hist) cudaMemsetAsync(hist, 0, (size_t)np * 256 * 4, st);
     cudaEventRecord(ev[s][0], st);
     if (n) {
       cudaMemsetAsync(P->ctr + C_SLOW, 0, 8, st);
       if (fp32) {
-        k_bprep_keys<true><<<grid_for(n, kThreads), kThreads, 0, st>>>(
+        k_bprep_keys<true><<<grid_for(n, kThreads, bprep_resident_blocks(true)), kThreads, 0, st>>>(
             P->jobs_d, offd[s], njobs, s, n, P->cell_bits, keys[s], X.idx, X.rec, slow,
-            P->ctr + C_SLOW, P->dev_err);
+            P->ctr + C_SLOW, P->dev_err, hist, np);
         k_bprep_fallback<<<num_sms() * 4u, kThreads, 0, st>>>(P->jobs_d, offd[s], njobs, s, P->cell_bits,
-                                                       slow, P->ctr + C_SLOW, keys[s]);
+                                                       slow, P->ctr + C_SLOW, keys[s], hist, np);
       } else {
-        k_bprep_keys<false><<<grid_for(n, kThreads), kThreads, 0, st>>>(
-            P->jobs_d, offd[s], njobs, s, n, P->cell_bits, keys[s], X.idx, X.rec, nullptr,
-            nullptr, P->dev_err);
+        k_bprep_keys<false><<<grid_for(n, kThreads, bprep_resident_blocks(false)), kThreads, 0,
+                              st>>>(P->jobs_d, offd[s], njobs, s, n, P->cell_bits, keys[s],
+                                    X.idx, X.rec, nullptr, nullptr, P->dev_err, hist, np);
       }
       g_launches += fp32 ? 2 : 1;
     }
@@ -2111,9 +2136,9 @@ static int plan_batched(const hlc_catalog* A, const hlc_catalog* B, const hlc_pa
     if (n > 1) {
       uint64_t* tk = ar.get_n<uint64_t>(n);
       uint32_t* tv = ar.get_n<uint32_t>(n);
-      void* scr = ar.get(sort_scratch_bytes(n, (key_bits + 7) / 8));
-      if (!tk || !tv || !scr) return fail(HLC_ENOMEM);
-      rc = radix_sort_pairs<uint64_t>(keys[s], X.idx, tk, tv, n, key_bits, scr, P->dev_err, st);
+      if (!tk || !tv) return fail(HLC_ENOMEM);
+      rc = radix_sort_pairs<uint64_t>(keys[s], X.idx, tk, tv, n, key_bits, scr, P->dev_err, st,
+                                      0, nullptr, nullptr, nullptr, true);
       if (rc) return fail(rc);
       ar.drop(tk);
       ar.drop(tv);
