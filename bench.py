@@ -496,12 +496,12 @@ TRAFFIC = {
     # captured on the default line's workload (full sky 10M x 10M, complete
     # mode, FP32 form) with ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum:
     # the three sort passes of a step (both catalogues per launch), read +
-    # written: 80,632,832 + 120,901,376 (the first pass makes its values),
-    # 161,055,744 + 120,093,952 and 160,616,960 + 119,799,296 B; their mean
-    "k_onesweep": {"bytes_per_launch": 254366720, "sources": "5333daf1bd4fd395",
+    # written: 80,645,376 + 121,016,576 (the first pass makes its values),
+    # 160,946,432 + 120,703,488 and 160,590,336 + 119,894,016 B; their mean
+    "k_onesweep": {"bytes_per_launch": 254598741, "sources": "baeb5a5edf527796",
                    "files": ("sort.cuh", "common.cuh")},
-    # the pair test: 495,118,592 B read + 42,904,320 B written
-    "k_pair<1,0,0,1>": {"bytes_per_launch": 538022912, "sources": "b2b9718ea7763aa0",
+    # the pair test: 495,089,920 B read + 42,796,800 B written
+    "k_pair<1,0,0,1>": {"bytes_per_launch": 537886720, "sources": "0f5305cd4a23c775",
                         "files": ("match.cuh", "canon.cuh", "index.cuh", "learned.cuh",
                                   "common.cuh", "fp32.cuh", "fastpix.cuh")},
 }
@@ -777,13 +777,17 @@ def dense_line(args, hlc, synth, dev, stream, rank, world):
             "matches": last["matches"], "clocks": clk}
 
 
-def _timed_loop(fn, K, W, stream, collect=False):
+def _timed_loop(fn, K, W, stream, collect=False, clocks=None):
+    """W untimed steps, then K steps between CUDA events on `stream`; with
+    `clocks` (a started Clocks), its samples are kept for the timed steps."""
     import torch
     for _ in range(W):
         fn()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    if clocks is not None:
+        clocks.mark("t0")
     e0.record(stream)
     out = None
     outs = []
@@ -793,7 +797,19 @@ def _timed_loop(fn, K, W, stream, collect=False):
             outs.append(out)
     e1.record(stream)
     torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.mark("t1")
     return e0.elapsed_time(e1) / K, (outs if collect else out)
+
+
+def _sampled_loop(args, fn, K, W, stream, tag):
+    """_timed_loop with nvidia-smi clocks sampled over its timed steps."""
+    import torch
+    clocks = Clocks(torch.cuda.current_device(),
+                    args.clocks_out + "." + tag if args.clocks_out else "")
+    clocks.start()
+    ms, out = _timed_loop(fn, K, W, stream, clocks=clocks)
+    return ms, out, clocks.stop()
 
 
 def _line(args, metric, value, unit, ms, config, higher_is_better=True, **extra):
@@ -832,6 +848,11 @@ def run_learned(args):
     shift = 2 * (L - Lc)
     res = {}
     ref = None
+    clocks = Clocks(torch.cuda.current_device(),
+                    args.clocks_out + ".learned" if args.clocks_out else "")
+    clocks.start()
+    torch.cuda.synchronize()
+    clocks.mark("t0")
     for name, model in (("binary search", hlc.HLC_MODEL_NONE), ("pla", hlc.HLC_MODEL_PLA),
                         ("mlp", hlc.HLC_MODEL_MLP)):
         outs = []
@@ -849,6 +870,9 @@ def run_learned(args):
                      "max_err": outs[-1]["learned_max_err"], "models": outs[-1]["learned_models"],
                      "equal_to_binary_search": exact}
         del out
+    torch.cuda.synchronize()
+    clocks.mark("t1")
+    clk = clocks.stop()
     base = res["binary search"]["ms_lookup"]
     for k in ("pla", "mlp"):
         res[k]["speedup_vs_binary_search"] = base / res[k]["ms_lookup"]
@@ -880,7 +904,8 @@ def run_learned(args):
                        "%d unique B cells, %d queries" % (_mega(n), _mega(n),
                                                          res["pla"]["models"], uniq.numel(),
                                                          n),
-           "best_model": best}, lookups=res, match_slice={"n_a": nm, "n_b": nm, **match})
+           "best_model": best}, clocks=clk, lookups=res,
+          match_slice={"n_a": nm, "n_b": nm, **match})
 
 
 def _auto_order(nb, cone_deg, r_arcsec):
@@ -928,7 +953,8 @@ def run_batched(args):
         n_, st_ = out["n"], out["stats"]
         hlc.hlc_free(plan)
         return n_, st_
-    ms_b, (nb_, st_b) = _timed_loop(lambda: batched(tune), args.steps, args.warmup, stream)
+    ms_b, (nb_, st_b), clk = _sampled_loop(args, lambda: batched(tune), args.steps, args.warmup,
+                                           stream, "batched")
     ms_r, (nr_, st_r) = _timed_loop(lambda: batched(None), args.steps, args.warmup, stream)
     orders = [_auto_order(j.B.ra.numel(), j.cone_deg, j.r_arcsec) for j in jobs]
 
@@ -944,7 +970,7 @@ def run_batched(args):
           {"workload": "%d cone-pair jobs (cone 0.1-2 deg, N log-uniform %g-%g per side, "
                        "r 0.5-5 arcsec), %d sources" % (njobs, 1e3 * args.scale, 1e6 * args.scale,
                                                        total)},
-          matches=nb_, per_job={"ms": ms_j, "sources_per_s": total / (ms_j / 1e3), "matches": nj_},
+          matches=nb_, clocks=clk, per_job={"ms": ms_j, "sources_per_s": total / (ms_j / 1e3), "matches": nj_},
           speedup_vs_per_job=ms_j / ms_b, pair_tests=st_b["pair_tests"],
           autotune=report, rule={"ms": ms_r, "sources_per_s": total / (ms_r / 1e3),
                                  "matches": nr_, "ms_pair": st_r["ms_pair"]},
@@ -983,7 +1009,8 @@ def run_streamed(args):
         hlc.hlc_free(plan)
         return n_, st_
     t0 = time.perf_counter()
-    ms_s, (ns_, st_s) = _timed_loop(streamed, args.steps, args.warmup, stream)
+    ms_s, (ns_, st_s), clk = _sampled_loop(args, streamed, args.steps, args.warmup, stream,
+                                           "streamed")
 
     def in_core():
         plan = hlc.hlc_plan(A, B, r, L, coarse_level=Lc, stream=stream)
@@ -1020,7 +1047,7 @@ def run_streamed(args):
           {"workload": "clusters %s x %s (%d Plummer clusters), r=1 arcsec, fine order 13, "
                        "coarse order 3, device budget %d GiB" % (_mega(n), _mega(nb), ncl,
                                                                args.budget_gb)},
-          matches=ns_, partitions=st_s["partitions"], ms_h2d=st_s["ms_h2d"],
+          matches=ns_, clocks=clk, partitions=st_s["partitions"], ms_h2d=st_s["ms_h2d"],
           phases_ms={k: st_s[k] for k in ("ms_stream_count", "ms_stream_bucket",
                                           "ms_stream_groups", "ms_stream_merge", "ms_d2h",
                                           "ms_prep", "ms_sort", "ms_index", "ms_pair",
