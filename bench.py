@@ -86,6 +86,16 @@ class Clocks:
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # sampling live before the timed region starts (the first sample can
+        # take most of a second); a short region then falls between samples
+        # that stop() keeps by the margin around it
+        t_end = time.time() + 5.0
+        while time.time() < t_end and self.proc.poll() is None:
+            self.f.flush()
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def mark(self, which: str):
         setattr(self, which, time.time())
@@ -93,6 +103,9 @@ class Clocks:
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        t1 = getattr(self, "t1", None)
+        if t1 is not None:  # a sample after the region's end, within the margin
+            time.sleep(max(0.0, min(0.25, t1 + 0.12 - time.time())))
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -334,7 +347,7 @@ def run_hlc(args):
         times = []
         ke = min(args.steps, 30)
         cap = 2 * max(nmatch, 1)  # pinned result buffers, allocated once
-        depth = max(1, args.e2e_depth)
+        depth = max(1, min(args.e2e_depth, ke))  # (every worker runs at least one step)
         outs = [tuple(torch.empty(cap, dtype=dt).pin_memory()
                       for dt in (torch.int64, torch.int64, torch.float64)) for _ in range(depth)]
 
