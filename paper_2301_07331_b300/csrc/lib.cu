@@ -566,10 +566,6 @@ static int build_learned(Arena& ar, const uint32_t* uniq, uint64_t m, int shift,
   return HLC_OK;
 }
 
-// Fine order inside dense table cells: the entries flagged in `flag` (those
-// whose table cell of T holds more than sparse_cell B entries) are compacted
-// in order, radix sorted by key and written back.  With items set, the sorted
-// dense keys are also run-length encoded into the tile kernel's work items.
 // Offset table T[0..S] of m keys sorted by (key >> shift): tile bounds,
 // then one CTA per tile of slots.
 static int offset_table(hlc_plan_t* P, const uint32_t* keys, uint64_t m, int shift, uint64_t S,
@@ -590,6 +586,11 @@ static int offset_table(hlc_plan_t* P, const uint32_t* keys, uint64_t m, int shi
   return HLC_OK;
 }
 
+// Fine order inside dense table cells (those of B's table T holding more than
+// sparse_cell B entries): the dense cells are listed from T, their entries in
+// X gathered in cell order, radix sorted by fine key and written back.  With
+// items set, the sorted dense keys are also run-length encoded into the tile
+// kernel's work items.
 static int dense_fixup(hlc_plan_t* P, CatDev& X, const uint32_t* T, int shift, bool items) {
   Arena& ar = *P->arena;
   cudaStream_t st = plan_stream(P);
